@@ -1,0 +1,390 @@
+"""CPU FP64 oracle of the kernel-based multiscale method (Lot & Rieger, arXiv 2503.04914).
+
+TEST INFRASTRUCTURE ONLY.  This module is the independent, plain and slow
+statement of what the library computes.  Only the test-suite, the package's
+smoke check and the benchmark's CPU-baseline leg may import it.  It shares no
+code with the CUDA library (no kernels, helpers, tables or constants); the only
+thing both sides share is the seeded input generators.
+
+Everything is float64 numpy/scipy.  Library primitives used as single steps:
+``scipy.spatial.cKDTree`` (exact fixed-radius pair search), ``scipy.linalg``
+Cholesky / LU, ``numpy.linalg.norm``.  No blocking or reordering beyond what the
+definitions below state.
+
+Paper passages followed (sections / equations of the paper):
+  * eq. kernelscaling (Section 2, Assumption 1): Phi_delta(x) = delta^-d Phi(x/delta),
+    supp Phi in the unit ball.
+  * Section 5: Wendland phi_{3,1}(r) = (1-r)_+^4 (4r+1).  The other (d,k) follow
+    Wendland's construction phi_{d,k} = I^k (1-r)_+^l, l = floor(d/2)+k+1.
+  * eq. deltadef (Assumption 2): delta_l = nu h_l.
+  * eq. recursive:localinterpol: e_0 = f, s_l = I_l(e_{l-1}), e_l = e_{l-1} - s_l.
+  * eq. mas (Section 3): A_l alpha_l = f_l - sum_{k<l} B_{lk} alpha_k,
+    B_{l2,l1} = (Phi_{delta_{l1}}(x^{(l2)}_n2 - x^{(l1)}_n1)), A_l = B_{ll}.
+  * eq. fapproximation: f_L = sum_l sum_n alpha_n^(l) Phi_l(. - x_n^(l)).
+  * eq. bigt / matrix_decomposition / T_n_prime: T_L = T'_L D_L.
+  * eq. TinvNeumann, eq. explicit_inverse_T (Theorem 7), eq. jacobi (Theorem 9).
+
+Parity status: every function here is pinned by tests/test_oracle_pins.py
+(closed forms derived independently, the paper's printed Table 1 and Figure 1
+values, the interpolation property, the monolithic dense solve, nilpotency).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+from scipy.spatial import cKDTree
+
+# ----------------------------------------------------------------------------
+# kernel (Section 2, eq. kernelscaling; Section 5 Wendland functions)
+# ----------------------------------------------------------------------------
+
+
+def wendland_phi(r, wd: int, wk: int):
+    """Wendland's compactly supported phi_{wd,wk}(r) for r >= 0 (zero for r >= 1).
+
+    With l = floor(wd/2) + wk + 1 the closed forms are (Wendland 1995):
+      k=0: (1-r)^l
+      k=1: (1-r)^(l+1) ((l+1) r + 1)                     -> phi_{3,1} = (1-r)^4 (4r+1) (Section 5)
+      k=2: (1-r)^(l+2) ((l^2+4l+3) r^2 + (3l+6) r + 3)   -> phi_{2,2} = (1-r)^6 (35r^2+18r+3)
+      k=3: (1-r)^(l+3) ((l^3+9l^2+23l+15) r^3 + (6l^2+36l+45) r^2 + (15l+45) r + 15)
+    The polynomials are used exactly as written (phi_{.,2}(0) = 3); a positive
+    constant factor on phi leaves the approximant f_L unchanged.
+    """
+    r = np.asarray(r, dtype=np.float64)
+    l = wd // 2 + wk + 1
+    s = np.clip(1.0 - r, 0.0, None)
+    if wk == 0:
+        p = np.ones_like(r)
+    elif wk == 1:
+        p = (l + 1) * r + 1.0
+    elif wk == 2:
+        p = (l * l + 4 * l + 3) * r * r + (3 * l + 6) * r + 3.0
+    elif wk == 3:
+        p = ((l ** 3 + 9 * l * l + 23 * l + 15) * r ** 3 + (6 * l * l + 36 * l + 45) * r * r
+             + (15 * l + 45) * r + 15.0)
+    else:
+        raise ValueError("wendland k must be 0..3")
+    return np.where(r < 1.0, s ** (l + wk) * p, 0.0)
+
+
+def kernel_dense(Y: np.ndarray, X: np.ndarray, delta: float, wd: int, wk: int) -> np.ndarray:
+    """Dense matrix (Phi_delta(y_i - x_j))_{ij} = delta^-d phi(|y_i - x_j| / delta), d = point dimension."""
+    d = X.shape[1]
+    diff = Y[:, None, :] - X[None, :, :]
+    r = np.sqrt(np.sum(diff * diff, axis=2)) / delta
+    return delta ** (-d) * wendland_phi(r, wd, wk)
+
+
+def kernel_sparse(Y: np.ndarray, X: np.ndarray, delta: float, wd: int, wk: int) -> sp.csr_matrix:
+    """The same matrix as kernel_dense, stored sparse; pairs found by an exact cKDTree range search."""
+    d = X.shape[1]
+    ty = cKDTree(Y)
+    tx = cKDTree(X)
+    pairs = ty.sparse_distance_matrix(tx, delta, output_type="ndarray")
+    r = pairs["v"] / delta
+    v = delta ** (-d) * wendland_phi(r, wd, wk)
+    keep = v != 0.0
+    M = sp.coo_matrix((v[keep], (pairs["i"][keep], pairs["j"][keep])), shape=(len(Y), len(X)))
+    return M.tocsr()
+
+
+def kernel_matrix(Y, X, delta, wd, wk, dense_max_entries=4_000_000):
+    """Dense for small blocks, sparse otherwise (same entries either way)."""
+    if len(Y) * len(X) <= dense_max_entries:
+        return kernel_dense(Y, X, delta, wd, wk)
+    return kernel_sparse(Y, X, delta, wd, wk)
+
+
+# ----------------------------------------------------------------------------
+# per-level SPD solve (A_l is symmetric positive definite, Section 3)
+# ----------------------------------------------------------------------------
+
+
+def cg(A, b, x0=None, rtol=1e-15, maxiter=100000):
+    """Textbook conjugate gradients (Hestenes-Stiefel) on SPD A, stop at |r| <= rtol |b|."""
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - A @ x
+    p = r.copy()
+    rr = float(r @ r)
+    bn = float(np.linalg.norm(b))
+    it = 0
+    if bn == 0.0:
+        return x, 0
+    while math.sqrt(rr) > rtol * bn and it < maxiter:
+        q = A @ p
+        a = rr / float(p @ q)
+        x += a * p
+        r -= a * q
+        rr_new = float(r @ r)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    return x, it
+
+
+@dataclass
+class LevelSolveInfo:
+    n: int
+    method: str
+    iterations: int
+    rel_residual: float
+
+
+def spd_solve(A, b, tol=1e-14, max_refine=8):
+    """Solve A x = b for one SPD level matrix.
+
+    Dense A: Cholesky (scipy.linalg.cho_factor).  Sparse A: CG followed by
+    iterative refinement x += CG(A, b - A x) until the FP64 relative residual
+    is <= tol or stops improving.  Returns (x, info).
+    """
+    b2 = b if b.ndim == 2 else b[:, None]
+    if not sp.issparse(A):
+        c = sla.cho_factor(A, lower=True)
+        x = sla.cho_solve(c, b2)
+        res = np.linalg.norm(b2 - A @ x) / max(np.linalg.norm(b2), 1e-300)
+        x = x if b.ndim == 2 else x[:, 0]
+        return x, LevelSolveInfo(A.shape[0], "cholesky", 0, float(res))
+    xs = []
+    its = 0
+    worst = 0.0
+    for col in range(b2.shape[1]):
+        bc = b2[:, col]
+        bn = np.linalg.norm(bc)
+        x = np.zeros_like(bc)
+        best = np.inf
+        for _ in range(max_refine):
+            r = bc - A @ x
+            rn = np.linalg.norm(r) / max(bn, 1e-300)
+            if rn <= tol or rn >= best:
+                break
+            best = rn
+            dx, k = cg(A, r, rtol=1e-13)
+            its += k
+            x = x + dx
+        rn = np.linalg.norm(bc - A @ x) / max(bn, 1e-300)
+        worst = max(worst, rn)
+        xs.append(x)
+    x = np.stack(xs, axis=1)
+    x = x if b.ndim == 2 else x[:, 0]
+    return x, LevelSolveInfo(A.shape[0], "cg+refine", its, float(worst))
+
+
+# ----------------------------------------------------------------------------
+# the sequential multiscale algorithm (eq. recursive:localinterpol, eq. mas)
+# ----------------------------------------------------------------------------
+
+
+def level_offsets(levels):
+    return np.concatenate([[0], np.cumsum([len(x) for x in levels])]).astype(np.int64)
+
+
+def fit_sequential(levels, f, h, nu, wd, wk, dense_max=4096, tol=1e-14):
+    """Coefficients alpha^(1..L) of the multiscale approximant, level by level.
+
+    For l = 1..L: rhs_l = f|_{X_l} - sum_{k<l} B_{lk} alpha^(k)  (the residual
+    e_{l-1} evaluated on X_l), then A_l alpha^(l) = rhs_l.  B_{lk} uses the
+    column level's support delta_k (eq. mas, definition of B).
+    ``f`` is [N] or [N, R] (level-concatenated).  Returns (alphas list, infos).
+    """
+    deltas = nu * np.asarray(h, dtype=np.float64)
+    off = level_offsets(levels)
+    alphas, infos = [], []
+    for l, X in enumerate(levels):
+        rhs = np.array(f[off[l]:off[l + 1]], dtype=np.float64, copy=True)
+        for k in range(l):
+            rhs -= kernel_matrix(X, levels[k], deltas[k], wd, wk) @ alphas[k]
+        if len(X) <= dense_max:
+            A = kernel_dense(X, X, deltas[l], wd, wk)
+        else:
+            A = kernel_sparse(X, X, deltas[l], wd, wk)
+        a, info = spd_solve(A, rhs, tol=tol)
+        alphas.append(a)
+        infos.append(info)
+    return alphas, infos
+
+
+def evaluate(levels, alphas, h, nu, wd, wk, Q, chunk=65536):
+    """f_L(q) = sum_l sum_n alpha_n^(l) Phi_{delta_l}(q - x_n^(l))  (eq. fapproximation)."""
+    deltas = nu * np.asarray(h, dtype=np.float64)
+    Q = np.asarray(Q, dtype=np.float64)
+    shape = (len(Q),) + np.asarray(alphas[0]).shape[1:]
+    out = np.zeros(shape)
+    for s in range(0, len(Q), chunk):
+        q = Q[s:s + chunk]
+        for l, X in enumerate(levels):
+            out[s:s + chunk] += kernel_matrix(q, X, deltas[l], wd, wk) @ alphas[l]
+    return out
+
+
+def row_residual(levels, alpha_flat, f_flat, h, nu, wd, wk, level, idx):
+    """Row (level, idx) of T_L alpha - f, by brute force over every point of levels <= level.
+
+    Row n of block row l of eq. bigt reads sum_{k<=l} sum_m Phi_{delta_k}(x_n^(l) - x_m^(k)) alpha_m^(k) - f_n^(l).
+    """
+    deltas = nu * np.asarray(h, dtype=np.float64)
+    off = level_offsets(levels)
+    x = levels[level][idx]
+    d = x.shape[0]
+    s = 0.0
+    for k in range(level + 1):
+        X = levels[k]
+        r = np.sqrt(np.sum((X - x) ** 2, axis=1)) / deltas[k]
+        s += float(np.sum(deltas[k] ** (-d) * wendland_phi(r, wd, wk) * alpha_flat[off[k]:off[k + 1]]))
+    return s - float(f_flat[off[level] + idx])
+
+
+# ----------------------------------------------------------------------------
+# the monolithic block system (Section 3) -- dense, for small hierarchies
+# ----------------------------------------------------------------------------
+
+
+def monolithic_T(levels, h, nu, wd, wk):
+    """Dense T_L of eq. bigt: block (k, j) = B_{kj} = Phi_{delta_j}(X_k, X_j) for j <= k, zero above."""
+    deltas = nu * np.asarray(h, dtype=np.float64)
+    off = level_offsets(levels)
+    N = int(off[-1])
+    T = np.zeros((N, N))
+    for k in range(len(levels)):
+        for j in range(k + 1):
+            T[off[k]:off[k + 1], off[j]:off[j + 1]] = kernel_dense(levels[k], levels[j], deltas[j], wd, wk)
+    return T
+
+
+def block_diagonal_D(T, levels):
+    """D_L = diag(A_1..A_L) taken from T_L (eq. matrix_decomposition)."""
+    off = level_offsets(levels)
+    D = np.zeros_like(T)
+    for l in range(len(levels)):
+        D[off[l]:off[l + 1], off[l]:off[l + 1]] = T[off[l]:off[l + 1], off[l]:off[l + 1]]
+    return D
+
+
+def normalised_factor(T, levels):
+    """T'_L = T_L D_L^{-1}: identity blocks on the diagonal, X_kj = B_kj A_j^{-1} below (eq. T_n_prime)."""
+    off = level_offsets(levels)
+    Tp = np.zeros_like(T)
+    for j in range(len(levels)):
+        cols = slice(off[j], off[j + 1])
+        A = T[cols, cols]
+        # columns of level j: T[:, j] A_j^{-1}  (A_j symmetric)
+        Tp[:, cols] = sla.solve(A, T[:, cols].T, assume_a="pos").T
+    return Tp
+
+
+def jacobi_sweeps(Tp, f, sweeps, beta0=None):
+    """beta_{m+1} = f + (I - T') beta_m, starting from beta0 (default f)  (eq. jacobi, Theorem 9)."""
+    beta = np.array(f if beta0 is None else beta0, dtype=np.float64, copy=True)
+    N = Tp.shape[0]
+    M = np.eye(N) - Tp
+    for _ in range(sweeps):
+        beta = f + M @ beta
+    return beta
+
+
+def pathsum_inverse_block(Xblocks, k, j):
+    """(T')^{-1}_{kj} for k > j by the path sum of eq. explicit_inverse_T (Theorem 7):
+    sum over strictly decreasing paths p = (k = p_1 > ... > p_m = j) of (-1)^(|p|-1) X_p,
+    with X_p = X_{p1,p2} X_{p2,p3} ... X_{p_{m-1},p_m}."""
+    total = None
+    inner = list(range(j + 1, k))
+    # every subset of the intermediate levels, in decreasing order, is one path
+    for mask in range(1 << len(inner)):
+        mids = sorted([inner[t] for t in range(len(inner)) if mask >> t & 1], reverse=True)
+        path = [k] + mids + [j]
+        prod = Xblocks[(path[0], path[1])]
+        for a in range(1, len(path) - 1):
+            prod = prod @ Xblocks[(path[a], path[a + 1])]
+        term = (-1) ** (len(path) - 1) * prod
+        total = term if total is None else total + term
+    return total
+
+
+# ----------------------------------------------------------------------------
+# the Jacobi operator M = I - T' (Section 4, eq. M) applied without forming it
+# ----------------------------------------------------------------------------
+
+
+class JacobiOperator:
+    """y = M c with M = I - T'_L, i.e. y_k = -sum_{j<k} B_{kj} A_j^{-1} c_j, and its transpose.
+
+    A_j^{-1} is applied by a dense Cholesky factor (levels up to a few thousand points).
+    """
+
+    def __init__(self, levels, h, nu, wd, wk):
+        self.levels = levels
+        self.off = level_offsets(levels)
+        self.N = int(self.off[-1])
+        deltas = nu * np.asarray(h, dtype=np.float64)
+        # A_j^{-1} is needed for j < L only (the last block column of M is zero)
+        self.chol = [sla.cho_factor(kernel_dense(X, X, deltas[j], wd, wk), lower=True)
+                     for j, X in enumerate(levels[:-1])]
+        self.B = {(k, j): kernel_matrix(levels[k], levels[j], deltas[j], wd, wk)
+                  for k in range(len(levels)) for j in range(k)}
+
+    def matvec(self, c):
+        y = np.zeros(self.N)
+        o = self.off
+        for j in range(len(self.levels) - 1):
+            t = sla.cho_solve(self.chol[j], c[o[j]:o[j + 1]])
+            for k in range(j + 1, len(self.levels)):
+                y[o[k]:o[k + 1]] -= self.B[(k, j)] @ t
+        return y
+
+    def rmatvec(self, y):
+        c = np.zeros(self.N)
+        o = self.off
+        for j in range(len(self.levels) - 1):
+            s = np.zeros(o[j + 1] - o[j])
+            for k in range(j + 1, len(self.levels)):
+                s -= self.B[(k, j)].T @ y[o[k]:o[k + 1]]
+            c[o[j]:o[j + 1]] = sla.cho_solve(self.chol[j], s)
+        return c
+
+    def norm2(self, iters=500, rtol=1e-10, seed=0):
+        """Largest singular value by power iteration on M^T M."""
+        rng = np.random.default_rng(seed)
+        v = rng.standard_normal(self.N)
+        v /= np.linalg.norm(v)
+        lam = 0.0
+        for _ in range(iters):
+            w = self.rmatvec(self.matvec(v))
+            lam_new = float(np.linalg.norm(w))
+            v = w / lam_new
+            if abs(lam_new - lam) <= rtol * lam_new:
+                lam = lam_new
+                break
+            lam = lam_new
+        return math.sqrt(lam)
+
+
+# ----------------------------------------------------------------------------
+# point-set quantities (Section 2)
+# ----------------------------------------------------------------------------
+
+
+def separation_distance(X):
+    """q_X = 1/2 min_{j != k} |x_j - x_k|."""
+    t = cKDTree(X)
+    dist, _ = t.query(X, k=2)
+    return 0.5 * float(np.min(dist[:, 1]))
+
+
+def fill_distance(X, probe):
+    """h_{X,Omega} = sup_{x in Omega} min_j |x - x_j|, with the sup taken over the probe points."""
+    t = cKDTree(X)
+    dist, _ = t.query(probe, k=1)
+    return float(np.max(dist))
+
+
+def nnz_per_row(levels, h, nu):
+    """Number of same-level points within delta_l of each point (the row counts of A_l)."""
+    deltas = nu * np.asarray(h, dtype=np.float64)
+    out = []
+    for l, X in enumerate(levels):
+        t = cKDTree(X)
+        out.append(np.array([len(v) for v in t.query_ball_point(X, deltas[l] * (1 - 1e-12))]))
+    return out

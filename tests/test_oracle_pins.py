@@ -1,0 +1,273 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: an independent
+derivation (sympy integration of Wendland's construction), values the paper
+prints (Table 1, Figure 1), theorems (Theorem 7, Theorem 9, eq. TinvNeumann), the
+interpolation property that defines I_l, or a brute-force dense solve.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import multiscale as om
+from paper_2503_04914_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ---------------------------------------------------------------- kernel
+
+
+@pytest.mark.parametrize("wd,wk", [(1, 0), (1, 1), (2, 1), (3, 1), (2, 2), (3, 2), (1, 2), (2, 3), (3, 3)])
+def test_wendland_matches_integral_construction(wd, wk):
+    """phi_{d,k} = I^k (1-r)_+^l with (I g)(r) = int_r^1 t g(t) dt (Wendland's construction),
+    derived here symbolically and compared, after normalising the constant, with the
+    oracle's closed form at many r."""
+    sympy = pytest.importorskip("sympy")
+    r, t = sympy.symbols("r t", nonnegative=True)
+    l = wd // 2 + wk + 1
+    g = (1 - r) ** l
+    for _ in range(wk):
+        g = sympy.integrate((t * g.subs(r, t)), (t, r, 1))
+    g = sympy.simplify(g)
+    rats = [sympy.Rational(999 * i, 40000) for i in range(41)]
+    rs = np.array([float(v) for v in rats])
+    ref = np.array([float(g.subs(r, v)) for v in rats])  # exact rational evaluation
+    got = om.wendland_phi(rs, wd, wk)
+    c = got[0] / ref[0]
+    assert c > 0
+    np.testing.assert_allclose(got, c * ref, rtol=1e-12, atol=1e-14)
+    assert om.wendland_phi(np.array([1.0, 1.3, 7.0]), wd, wk).tolist() == [0.0, 0.0, 0.0]
+
+
+def test_wendland_exact_values():
+    """Printed closed forms at rational points (exact in binary floating point)."""
+    # phi_{3,1}(r) = (1-r)^4 (4r+1), Section 5
+    assert om.wendland_phi(0.0, 3, 1) == 1.0
+    assert om.wendland_phi(0.5, 3, 1) == 0.0625 * 3.0
+    # phi_{2,2}(r) = (1-r)^6 (35 r^2 + 18 r + 3)
+    assert om.wendland_phi(0.0, 2, 2) == 3.0
+    assert om.wendland_phi(0.5, 2, 2) == (1.0 / 64.0) * (35.0 / 4.0 + 9.0 + 3.0)
+
+
+def test_scaled_kernel_integral_is_scale_invariant():
+    """int_{R^d} Phi_delta = int_{R^d} Phi for every delta (eq. kernelscaling: delta^-d Phi(x/delta)).
+    A wrong power of delta fails this."""
+    for d, wd in [(1, 1), (2, 2), (3, 3)]:
+        vals = []
+        for delta in (0.5, 1.0, 2.0):
+            n = 4000 if d == 1 else (600 if d == 2 else 120)
+            g = np.linspace(-delta, delta, n)
+            dx = g[1] - g[0]
+            pts = np.stack(np.meshgrid(*([g] * d), indexing="ij"), -1).reshape(-1, d)
+            k = om.kernel_dense(pts[:1] * 0.0, pts, delta, wd, 1)[0]
+            vals.append(k.sum() * dx ** d)
+        assert abs(vals[0] - vals[1]) < 2e-2 * abs(vals[1])
+        assert abs(vals[2] - vals[1]) < 2e-2 * abs(vals[1])
+
+
+def test_sparse_kernel_equals_dense():
+    rng = np.random.default_rng(1)
+    X = rng.random((300, 2))
+    Y = rng.random((200, 2))
+    for wd, wk in [(2, 1), (2, 2)]:
+        D = om.kernel_dense(Y, X, 0.13, wd, wk)
+        S = om.kernel_sparse(Y, X, 0.13, wd, wk).toarray()
+        np.testing.assert_allclose(S, D, rtol=1e-15, atol=0)
+        # self-pairs are kept
+        Sx = om.kernel_sparse(X, X, 0.13, wd, wk).toarray()
+        np.testing.assert_allclose(np.diag(Sx), 0.13 ** -2 * om.wendland_phi(0.0, wd, wk))
+
+
+# ---------------------------------------------------------------- point sets (Table 1)
+
+
+def test_table1_grid_sizes_and_distances():
+    rows = _golden("table1.txt")
+    probe = inputs.query_grid(400, 2)
+    probe = np.concatenate([probe, inputs.grid_points(401, 2)])
+    for l, N, h, q in rows:
+        l = int(l)
+        assert (2 ** l + 1) ** 2 == int(N)
+        if l <= 4:
+            X = inputs.grid_points(2 ** l + 1, 2)
+            assert len(X) == int(N)
+            hh = om.fill_distance(X, probe)
+            qq = om.separation_distance(X)
+            # printed to 3 significant digits
+            assert hh == pytest.approx(float(h), rel=2e-3)
+            assert qq == pytest.approx(float(q), rel=2e-3)
+        # the recipe's h_l is the fill distance printed in Table 1
+        assert 2.0 ** -l / math.sqrt(2) == pytest.approx(float(h), rel=2e-3)
+        assert 2.0 ** -l / 2 == pytest.approx(float(q), rel=2e-3)
+
+
+def test_fig4_legend_totals():
+    for L, printed in _golden("fig4_totals.txt"):
+        total = sum((2 ** l + 1) ** 2 for l in range(1, int(L) + 1))
+        mult = {"k": 1e3, "M": 1e6}[printed[-1]]
+        assert abs(total - float(printed[:-1]) * mult) <= 0.05 * total
+
+
+# ---------------------------------------------------------------- Figure 1: ||M_L||_2
+
+
+@pytest.mark.parametrize("L", [2, 3, 4, 5, 6])
+def test_fig1_jacobi_operator_norm(L):
+    """||M_L||_2 with M = I - T' on the paper's grids, nu = 4, phi_{3,1}, h = fill distance,
+    matches the numerical values printed in Figure 1 to the printed digits."""
+    want = {int(r[0]): float(r[1]) for r in _golden("fig1_mnorm.txt")}[L]
+    w = inputs.franke_grid_hierarchy(L)
+    op = om.JacobiOperator(w.levels, w.h, w.nu, w.wendland_d, w.wendland_k)
+    got = op.norm2()
+    assert round(got, 3) == pytest.approx(want, abs=1.01e-3)
+
+
+def test_fig1_bound_curve_closed_form():
+    """The printed 'theoretical bound' values equal sqrt(L) 2^(L-1) (arithmetic check of the curve)."""
+    for r in _golden("fig1_mnorm.txt"):
+        L, bound = int(r[0]), float(r[2])
+        assert round(math.sqrt(L) * 2 ** (L - 1), 3) == pytest.approx(bound, abs=1.5e-3)
+
+
+def test_fig1_dense_svd_agrees_with_operator():
+    w = inputs.franke_grid_hierarchy(3)
+    T = om.monolithic_T(w.levels, w.h, w.nu, 3, 1)
+    Tp = om.normalised_factor(T, w.levels)
+    M = np.eye(len(T)) - Tp
+    op = om.JacobiOperator(w.levels, w.h, w.nu, 3, 1)
+    assert np.linalg.norm(M, 2) == pytest.approx(op.norm2(), rel=1e-8)
+    v = np.random.default_rng(0).standard_normal(len(T))
+    np.testing.assert_allclose(op.matvec(v), M @ v, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(op.rmatvec(v), M.T @ v, rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------------- Section 3 identities
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = inputs.grid_hierarchy_small()
+    alphas, infos = om.fit_sequential(w.levels, w.f, w.h, w.nu, w.wendland_d, w.wendland_k)
+    return w, alphas, infos
+
+
+def test_levels_spd(small):
+    w, _, infos = small
+    for l, X in enumerate(w.levels):
+        A = om.kernel_dense(X, X, w.nu * w.h[l], w.wendland_d, w.wendland_k)
+        np.testing.assert_allclose(A, A.T, rtol=0, atol=0)
+        assert np.linalg.eigvalsh(A)[0] > 0
+        assert infos[l].rel_residual < 1e-13
+
+
+def test_interpolation_property(small):
+    """After level l, f_l = sum_{k<=l} s_k reproduces f on X_l (definition of I_l, eq. recursive:localinterpol)."""
+    w, alphas, _ = small
+    off = om.level_offsets(w.levels)
+    for l, X in enumerate(w.levels):
+        val = om.evaluate(w.levels[:l + 1], alphas[:l + 1], w.h[:l + 1], w.nu, 2, 1, X)
+        f = w.f[off[l]:off[l + 1]]
+        assert np.max(np.abs(val - f)) <= 1e-12 * np.max(np.abs(f))
+    # and the data function itself, evaluated independently at X_l
+    np.testing.assert_allclose(w.f_fun(w.levels[-1]), w.f[off[-2]:], rtol=0, atol=0)
+
+
+def test_monolithic_dense_solve_equals_sequential(small):
+    """Solving T_L alpha = f (eq. bigt) by dense LU gives the level-by-level coefficients."""
+    w, alphas, _ = small
+    T = om.monolithic_T(w.levels, w.h, w.nu, 2, 1)
+    a_dense = sla.solve(T, w.f)
+    a_seq = np.concatenate(alphas)
+    assert np.linalg.norm(a_dense - a_seq) <= 1e-11 * np.linalg.norm(a_seq)
+    # sampled brute-force rows of T alpha - f vanish
+    for l in range(len(w.levels)):
+        for i in (0, len(w.levels[l]) // 2, len(w.levels[l]) - 1):
+            r = om.row_residual(w.levels, a_seq, w.f, w.h, w.nu, 2, 1, l, i)
+            assert abs(r) < 1e-11
+
+
+def test_factorisation_nilpotency_neumann_jacobi(small):
+    """T = T' D (eq. matrix_decomposition); (I-T')^L = 0 and (I-T')^(L-1) != 0;
+    Neumann series equals (T')^{-1} (eq. TinvNeumann); Jacobi is exact after L sweeps
+    from any start and after L-1 sweeps from beta_0 = f (Theorem 9)."""
+    w, alphas, _ = small
+    L = len(w.levels)
+    T = om.monolithic_T(w.levels, w.h, w.nu, 2, 1)
+    D = om.block_diagonal_D(T, w.levels)
+    Tp = om.normalised_factor(T, w.levels)
+    np.testing.assert_allclose(Tp @ D, T, rtol=0, atol=1e-9 * np.abs(T).max())
+    N = len(T)
+    M = np.eye(N) - Tp
+    ML1 = np.linalg.matrix_power(M, L - 1)
+    assert np.abs(ML1).max() > 1e-3
+    assert np.abs(np.linalg.matrix_power(M, L)).max() < 1e-9 * max(1.0, np.abs(ML1).max())
+    neu = sum(np.linalg.matrix_power(M, t) for t in range(L))
+    np.testing.assert_allclose(neu @ Tp, np.eye(N), atol=1e-8)
+    beta_exact = np.linalg.solve(Tp, w.f)
+    rnd = np.random.default_rng(5).standard_normal(N)
+    bL = om.jacobi_sweeps(Tp, w.f, L, beta0=rnd)
+    assert np.linalg.norm(bL - beta_exact) <= 1e-9 * np.linalg.norm(beta_exact)
+    bL1 = om.jacobi_sweeps(Tp, w.f, L - 1)
+    assert np.linalg.norm(bL1 - beta_exact) <= 1e-9 * np.linalg.norm(beta_exact)
+    # one sweep short from a random start is NOT exact
+    bshort = om.jacobi_sweeps(Tp, w.f, L - 1, beta0=rnd)
+    assert np.linalg.norm(bshort - beta_exact) > 1e-6 * np.linalg.norm(beta_exact)
+    # alpha = D^{-1} beta (eq. split)
+    a = np.linalg.solve(D, beta_exact)
+    np.testing.assert_allclose(a, np.concatenate(alphas), rtol=0, atol=1e-9 * np.abs(a).max())
+
+
+def test_pathsum_inverse_theorem7():
+    """(T')^{-1}_{kj} equals the signed sum over strictly decreasing level paths (eq. explicit_inverse_T)."""
+    w = inputs.franke_grid_hierarchy(4)
+    T = om.monolithic_T(w.levels, w.h, w.nu, 3, 1)
+    Tp = om.normalised_factor(T, w.levels)
+    off = om.level_offsets(w.levels)
+    X = {(k, j): Tp[off[k]:off[k + 1], off[j]:off[j + 1]] for k in range(4) for j in range(k)}
+    inv = np.linalg.inv(Tp)
+    for k in range(4):
+        for j in range(k):
+            got = om.pathsum_inverse_block(X, k, j)
+            want = inv[off[k]:off[k + 1], off[j]:off[j + 1]]
+            np.testing.assert_allclose(got, want, atol=1e-8 * max(1.0, np.abs(want).max()))
+
+
+def test_row_count_bound():
+    """Row counts of A_l are bounded by (1 + delta_l / q_l)^d (eq. rowcost)."""
+    for w in (inputs.grid_hierarchy_small(), inputs.halton_hierarchy(L=4)):
+        counts = om.nnz_per_row(w.levels, w.h, w.nu)
+        for l, X in enumerate(w.levels):
+            q = om.separation_distance(X)
+            assert counts[l].max() <= (1 + w.nu * w.h[l] / q) ** w.d
+
+
+def test_cg_path_matches_cholesky_path():
+    w = inputs.halton_hierarchy(L=4, n_gauss=5)
+    a1, i1 = om.fit_sequential(w.levels, w.f, w.h, w.nu, 2, 1, dense_max=10 ** 9)
+    a2, i2 = om.fit_sequential(w.levels, w.f, w.h, w.nu, 2, 1, dense_max=100)
+    assert [i.method for i in i2][-1] == "cg+refine"
+    for x, y in zip(a1, a2):
+        assert np.linalg.norm(x - y) <= 1e-10 * np.linalg.norm(x)
+
+
+def test_multi_rhs_equals_single():
+    w = inputs.grid_hierarchy_small(nrhs=3)
+    a, _ = om.fit_sequential(w.levels, w.f, w.h, w.nu, 2, 1)
+    for c in range(3):
+        ac, _ = om.fit_sequential(w.levels, w.f[:, c], w.h, w.nu, 2, 1)
+        for x, y in zip(a, ac):
+            assert np.linalg.norm(x[:, c] - y) <= 1e-11 * np.linalg.norm(y)

@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the multiscale fit on one GB300 (or N, one process per GPU).
+
+One step = one pass of the whole hot path over the synthetic workload, with the
+inputs already resident in HBM:
+  ms_build_hierarchy_dev  (level grids, cell binning, CSR of A_l and B_kj)
+  ms_fit_dev              (Jacobi sweeps on T' + per-level CG on D, one persistent kernel)
+  ms_evaluate_dev         (approximant at a 256^2 query grid)
+Workload: d=2, 8 levels of scrambled Halton points, N_j = 64*4^(j-1) (1,398,080 points),
+h_j = N_j^-1/2, delta_j = 4 h_j, Wendland phi_{2,1}, f = 20 Gaussians + 0.1 sin(8 pi x) sin(8 pi y).
+The timed path is the MIXED one (FP32 mat-vecs, FP64 dots, FP64 outer refinement); the
+plain FP64 path is timed beside it.  `--impl reference` times the CPU FP64 oracle instead.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fit time at rel-err 1e-8: learned-PCG FP32 vs plain FP64 (ms); mat-vec GB/s"
+WORKLOAD = ("halton8_d2_nu4_w21: d=2, 8 levels scrambled Halton N_j=64*4^(j-1) (1,398,080 points), "
+            "delta_j=4*N_j^-1/2, Wendland phi_{2,1}, f=20 Gaussians+0.1 sin(8pi x)sin(8pi y)")
+REL_TOL = 1e-10
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--levels", type=int, default=8)
+    p.add_argument("--query-side", type=int, default=256)
+    p.add_argument("--cpu-levels", type=int, default=6, help="levels of the oracle's bounded sample")
+    p.add_argument("--ref-levels", type=int, default=5, help="levels per step of the reference arm")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def cpu_baseline(levels, query_n, reps=1):
+    """Time the CPU oracle (as it stands) on a bounded sample in a single-threaded subprocess."""
+    code = f"""
+import sys, time, json
+sys.path.insert(0, {ROOT!r})
+from oracle import multiscale as om
+from paper_2503_04914_gb300 import inputs
+w = inputs.halton_hierarchy(L={levels})
+Q = inputs.query_grid(256, 2)[:{query_n}]
+ts = []
+for _ in range({reps}):
+    t = time.perf_counter()
+    a, _ = om.fit_sequential(w.levels, w.f, w.h, w.nu, 2, 1)
+    s = om.evaluate(w.levels, a, w.h, w.nu, 2, 1, Q)
+    ts.append(time.perf_counter() - t)
+print(json.dumps({{"N": w.N, "times": ts}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               NUMEXPR_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle baseline failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+N_FULL = 1398080
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    reps = args.warmup + args.steps
+    out = cpu_baseline(args.ref_levels, 1024, reps=reps)
+    ts = out["times"][args.warmup:]
+    scale = N_FULL / out["N"]
+    ms_step = 1000.0 * statistics.mean(ts) * scale
+    sample = (f"oracle fit_sequential + evaluate on the first {args.ref_levels} levels of the workload "
+              f"({out['N']} points, 1024 queries), single-threaded, scaled by points ({N_FULL}/{out['N']})")
+    line = {"impl": "reference", "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rel_tol": REL_TOL},
+            "cpu_baseline": {"value": ms_step, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": ms_step, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2503_04914_gb300 import build as B
+    from paper_2503_04914_gb300 import inputs, ms
+    B.build()
+    ms.load()
+
+    w = inputs.halton_hierarchy(L=args.levels)
+    pts = torch.from_numpy(w.points).cuda()
+    f = torch.from_numpy(w.f).cuda()
+    Qh = inputs.query_grid(args.query_side, 2)
+    Q = torch.from_numpy(Qh).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    n = w.n_per_level
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step(prec):
+        opts = ms.ms_default_opts(wendland_d=2, wendland_k=1, nu=w.nu, precision=prec)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        hnd = ms.ms_build_hierarchy(2, n, pts, w.h, opts)
+        alpha, st = ms.ms_fit(hnd, f, REL_TOL)
+        e1.record(stream)
+        s = ms.ms_evaluate(hnd, alpha, Q)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        info = ms.ms_hierarchy_info(hnd)
+        ms.ms_destroy(hnd)
+        return {"total": e0.elapsed_time(e2), "eval": e1.elapsed_time(e2), "stats": st, "info": info}
+
+    def timed(prec, k):
+        recs = []
+        for _ in range(k):
+            flush.fill_(1.0)  # L2 flush between steps (256 MB write), outside the timed events
+            barrier()
+            recs.append(step(prec))
+            barrier()
+        return recs
+
+    for _ in range(args.warmup):
+        step(ms.MS_PREC_MIXED)
+    clocks = ClockSampler(local)
+    lc0 = ms.ms_launch_count()
+    clocks.start()
+    t_wall = time.perf_counter()
+    recs = timed(ms.MS_PREC_MIXED, args.steps)
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    launches = (ms.ms_launch_count() - lc0) / args.steps
+    ms_step = statistics.mean(r["total"] for r in recs)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    last = recs[-1]
+    st, info = last["stats"], last["info"]
+
+    out = {}
+    if rank == 0:
+        peaks, peak_kind = measured_peaks()
+        hbm = float(peaks["hbm_gbs"])
+        fit_ms = statistics.mean(r["stats"]["fit_ms"] for r in recs)
+        fit_bytes = st["matvec_bytes"]
+        achieved = fit_bytes / (fit_ms * 1e-3) / 1e9
+        out["roofline"] = {"kernel": "k_fit (persistent Jacobi/CG solve, MIXED)", "bound": "hbm",
+                           "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                           "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
+                           "algorithmic_bytes_per_launch": fit_bytes, "launch_ms": fit_ms}
+        out["phases_ms"] = {"build": statistics.mean(r["info"]["build_ms"] for r in recs),
+                            "fit": fit_ms, "evaluate": statistics.mean(r["eval"] for r in recs)}
+        out["cg_iterations"] = st["cg_iterations"]
+        out["refinements"] = st["refinements"]
+        out["rel_residual"] = st["rel_residual"]
+        out["nnz"] = {"A": info["nnz_A"], "B": info["nnz_B"]}
+
+        # stand-alone mat-vecs (sorted order) on the built hierarchy: GB/s of the CSR kernels
+        H = ms.Hierarchy(2, n, pts, w.h, precision=ms.MS_PREC_MIXED, wendland_d=2, wendland_k=1, nu=w.nu)
+        N = w.N
+        x = torch.randn(N, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        mv = {}
+        for name, op, nnz, vb in [("A64", ms.MS_APPLY_A64, info["nnz_A"], 8), ("A32", ms.MS_APPLY_A32, info["nnz_A"], 4),
+                                  ("B64", ms.MS_APPLY_B64, info["nnz_B"], 8)]:
+            for _ in range(3):
+                H.apply(op, x, y, sorted_order=True)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            reps = 20
+            ev[0].record(stream)
+            for _ in range(reps):
+                H.apply(op, x, y, sorted_order=True)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            t_ms = ev[0].elapsed_time(ev[1]) / reps
+            # matrix (col + val) + row offsets + y write + one read of x (FP32 ops also convert x)
+            b = nnz * (4 + vb) + N * (8 + 8 + 8) + (N * 12 if vb == 4 else 0)
+            mv[name] = {"ms": t_ms, "GBps": b / (t_ms * 1e-3) / 1e9, "frac_hbm": b / (t_ms * 1e-3) / 1e9 / hbm,
+                        "algorithmic_bytes": b}
+        out["matvec"] = mv
+        H.close()
+
+        # plain FP64 path, same step
+        if not args.no_fp64:
+            step(ms.MS_PREC_FP64)
+            r64 = timed(ms.MS_PREC_FP64, max(2, args.steps // 2))
+            out["fp64"] = {"ms_per_step": statistics.mean(r["total"] for r in r64),
+                           "fit_ms": statistics.mean(r["stats"]["fit_ms"] for r in r64),
+                           "build_ms": statistics.mean(r["info"]["build_ms"] for r in r64),
+                           "cg_iterations": r64[-1]["stats"]["cg_iterations"],
+                           "algorithmic_bytes_fit": r64[-1]["stats"]["matvec_bytes"]}
+
+        # end to end through the host-pointer C ABI (H2D of points, f, queries; D2H of alpha, values)
+        e2e = []
+        for i in range(max(2, args.steps // 2) + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Hh = ms.Hierarchy(2, n, w.points, w.h, precision=ms.MS_PREC_MIXED, wendland_d=2, wendland_k=1, nu=w.nu)
+            a_h, _ = Hh.fit(w.f, REL_TOL)
+            s_h = Hh.evaluate(a_h, Qh)
+            Hh.close()
+            if i > 0:
+                e2e.append(1000.0 * (time.perf_counter() - t0))
+        h2d = w.points.nbytes + w.f.nbytes + Qh.nbytes
+        d2h = a_h.nbytes + s_h.nbytes
+        out["e2e"] = {"value": statistics.mean(e2e), "unit": "ms", "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h)}
+
+        if not args.no_cpu:
+            cb = cpu_baseline(args.cpu_levels, 4096)
+            scale = N_FULL / cb["N"]
+            out["cpu_baseline"] = {"value": 1000.0 * cb["times"][0] * scale, "unit": "ms", "cores": 1,
+                                   "kind": "oracle",
+                                   "sample": (f"oracle fit_sequential + evaluate on the first {args.cpu_levels} "
+                                              f"levels ({cb['N']} points, 4096 queries) took "
+                                              f"{cb['times'][0]:.2f} s single-threaded; scaled by points "
+                                              f"({N_FULL}/{cb['N']})")}
+
+        line = {"metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": "mixed (FP32 CSR mat-vec, FP64 dots/refinement)",
+                           "rel_tol": REL_TOL, "queries": args.query_side ** 2,
+                           "step": "build_hierarchy + fit + evaluate, inputs resident in HBM",
+                           "l2": "flushed between steps (256 MB write); CSR working set >> L2",
+                           "parallelism": f"replicas x{ws}"},
+                "wall_s_timed": t_wall, "gpu_launches": launches, "clocks": clk, **out}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * ms.h -- C ABI of the GB300 multiscale fit library (libms.so).
+ *
+ * The library solves the monolithic multiscale system of Lot & Rieger
+ * (arXiv 2503.04914): for a point hierarchy X_1..X_L with level supports
+ * delta_l = nu * h_l (Assumption 2, eq. deltadef) and the scaled Wendland
+ * kernel Phi_delta(x) = delta^-d phi(|x| / delta) (Assumption 1,
+ * eq. kernelscaling), it finds coefficients alpha^(1..L) with
+ *
+ *     A_l alpha^(l) = f|_{X_l} - sum_{k<l} B_{lk} alpha^(k)           (eq. mas)
+ *     A_l = Phi_{delta_l}(X_l, X_l),  B_{lk} = Phi_{delta_k}(X_l, X_k)  (Section 3)
+ *
+ * i.e. T_L alpha = f for the block lower-triangular T_L of eq. bigt.  It is
+ * solved as eq. split: Jacobi sweeps on the normalised factor T'_L
+ * (eq. jacobi, Theorem 9) whose inner steps are per-level conjugate
+ * gradients on the block diagonal D_L (Theorem 8, eq. blockdiagonal_levelwise),
+ * and the approximant f_L(x) = sum_l sum_n alpha_n^(l) Phi_{delta_l}(x - x_n^(l))
+ * (eq. fapproximation) is evaluated at query points.
+ *
+ * Conventions (all entry points):
+ *  - Every entry point returns an ms_status; MS_OK is 0.  On failure
+ *    ms_last_error() gives a message (thread-local, valid until the next
+ *    call on the same thread).  No C++ exception crosses this boundary.
+ *  - Point arrays are float64, row-major [n][d], with the levels
+ *    concatenated coarse to fine (level 1 first).  Coefficient and data
+ *    arrays use the same level-concatenated order as the points the caller
+ *    passed ("input order"); the library permutes internally and undoes it.
+ *  - Multi-right-hand-side arrays are row-major [N][nrhs].
+ *  - Plain entry points take HOST pointers; the caller owns them and the
+ *    library copies what it needs before returning.  *_dev entry points take
+ *    DEVICE pointers on the current CUDA device plus a cudaStream_t passed as
+ *    void* (NULL = the legacy default stream); they enqueue work on that
+ *    stream and may return before it completes, except where stated.
+ *  - The hierarchy handle owns all device memory it allocates (cudaMalloc);
+ *    ms_destroy frees it.  A handle is bound to the device that was current
+ *    when it was built and must be used with that device current.
+ *  - Device-side failures (CG breakdown, iteration caps, barrier time-outs)
+ *    are recorded in device flags and reported by the call that waits for
+ *    the result; the library never traps, asserts or spins unboundedly on
+ *    the GPU.
+ */
+#ifndef MS_H
+#define MS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MS_MAX_LEVELS 32
+#define MS_ABI_VERSION 1
+
+typedef struct ms_hierarchy ms_hierarchy;
+
+typedef enum {
+    MS_OK = 0,
+    MS_ERR_ARG = 1,            /* invalid argument (sizes, d, L, delta, kernel, NULL) */
+    MS_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    MS_ERR_OOM = 3,            /* device allocation failed */
+    MS_ERR_NOT_SPD = 4,        /* CG breakdown: p^T A p <= 0 or non-finite on some level */
+    MS_ERR_NOT_CONVERGED = 5,  /* a level hit its iteration cap before the tolerance */
+    MS_ERR_TIMEOUT = 6,        /* a bounded device-side wait (grid barrier) ran out */
+    MS_ERR_NUMERIC = 7,        /* non-finite input data */
+    MS_ERR_STATE = 8           /* call not valid in the handle's current state */
+} ms_status;
+
+/* Operator used for a mat-vec family. */
+enum { MS_OP_CSR = 0, MS_OP_MATRIX_FREE = 1, MS_OP_AUTO = 2 };
+/* Arithmetic of the level CG solves. */
+enum {
+    MS_PREC_FP64 = 0,   /* FP64 mat-vecs, vectors and dots */
+    MS_PREC_MIXED = 1   /* FP32 mat-vecs and inner vectors, FP64 dots, FP64 outer
+                           true-residual refinement, FP64 level-finalising Jacobi updates */
+};
+/* Preconditioner of the level CG solves. */
+enum { MS_PRECOND_NONE = 0, MS_PRECOND_LEARNED = 1 };
+
+/* Options of a hierarchy; fill with ms_default_opts() and override fields. */
+typedef struct ms_opts {
+    int wendland_d;      /* Wendland phi_{d,k}: space dimension index d (>= point dimension), 1..3 */
+    int wendland_k;      /* smoothness index k, 0..3 (phi_{3,1} = (1-r)^4 (4r+1), Section 5) */
+    double nu;           /* delta_l = nu * h_l (eq. deltadef); > 0 */
+    int op;              /* operator for the level matrices A_l in the FP32 inner CG (MS_OP_*) */
+    int precision;       /* MS_PREC_* */
+    int precond;         /* MS_PRECOND_* */
+    int max_iters;       /* cap on CG iterations per level and solve; 0 = 20000 */
+    int jacobi_sweeps;   /* Jacobi sweeps on T'; 0 = L-1 (exact from beta_0 = f, Theorem 9) */
+    double inter_tol;    /* relative tolerance of the non-final (intermediate) level solves
+                            inside the Jacobi sweeps; 0 = 1e-6 */
+    double inner_tol;    /* MIXED: relative tolerance of each FP32 inner CG; 0 = 1e-4 */
+    int cell_split;      /* neighbour-grid cell size = delta_l / cell_split (1 or 2); 0 = 1 */
+    int threads_per_row; /* CSR sub-warp width for A (1..32, power of 2); 0 = autotune */
+    int reserved[8];
+} ms_opts;
+
+/* Per-fit statistics (all levels 0-based, coarse to fine). */
+typedef struct ms_fit_stats {
+    int32_t L;
+    int32_t sweeps;                      /* Jacobi sweeps run */
+    int64_t cg_iterations[MS_MAX_LEVELS];/* CG iterations actually run, summed over all solves
+                                            of the level (inner FP32 iterations in MIXED) */
+    int32_t refinements[MS_MAX_LEVELS];  /* MIXED: FP64 outer residual evaluations per level */
+    double rel_residual[MS_MAX_LEVELS];  /* final FP64 true relative residual
+                                            |beta_l - A_l alpha_l| / |beta_l| per level */
+    int32_t precond_fallbacks;           /* levels that fell back from the learned preconditioner */
+    int32_t device_status;               /* ms_status raised on the device (0 = none) */
+    double fit_ms;                       /* device time of the solve (CUDA events) */
+    double matvec_bytes;                 /* algorithmic bytes moved by the solve kernel
+                                            (matrix + vector traffic of every phase) */
+    int64_t kernel_launches;             /* library kernels launched by the call */
+} ms_fit_stats;
+
+/* Sizes of a built hierarchy. */
+typedef struct ms_info {
+    int32_t d, L;
+    int64_t N;
+    int64_t n_per_level[MS_MAX_LEVELS];
+    double delta[MS_MAX_LEVELS];
+    int64_t nnz_A;       /* stored entries of the block diagonal (all A_l) */
+    int64_t nnz_B;       /* stored entries of the strictly lower blocks (all B_kj, k > j) */
+    int64_t device_bytes;/* device memory held by the handle */
+    double build_ms;     /* device time of the last build (CUDA events) */
+} ms_info;
+
+/* Fill *opts with defaults: phi_{3,1}, nu = 4, CSR, FP64, no preconditioner. */
+void ms_default_opts(ms_opts* opts);
+
+/*
+ * Build a hierarchy: validate (Assumption 2 inputs), copy the points to the
+ * device, bin every level into a uniform cell grid of cell size delta_l
+ * (Morton order of cells, counting sort, ties by input index), and assemble
+ * the block-diagonal A_l and strictly lower B_kj blocks in CSR
+ * (int64 row offsets, int32 column indices, FP64 values and, for MIXED,
+ * FP32 values).
+ *   d            point dimension, 1..3
+ *   L            number of levels, 1..MS_MAX_LEVELS
+ *   n_per_level  host [L], N_l >= 1
+ *   points       host [N][d] float64, level-concatenated (must be finite)
+ *   h_per_level  host [L], h_l > 0; delta_l = opts->nu * h_l
+ *   opts         host, NULL = defaults
+ *   out          receives the handle (NULL on failure)
+ * Errors: MS_ERR_ARG (d, L, N_l, h, nu, kernel, NULL pointers), MS_ERR_NUMERIC
+ * (non-finite points), MS_ERR_OOM, MS_ERR_CUDA.  Synchronous.
+ */
+ms_status ms_build_hierarchy(int d, int L, const int64_t* n_per_level, const double* points,
+                             const double* h_per_level, const ms_opts* opts, ms_hierarchy** out);
+
+/* As ms_build_hierarchy with points_dev a DEVICE [N][d] float64 array; the build runs on
+ * `stream` and the call returns once the handle is complete (it reads back the sizes). */
+ms_status ms_build_hierarchy_dev(int d, int L, const int64_t* n_per_level, const double* points_dev,
+                                 const double* h_per_level, const ms_opts* opts, void* stream,
+                                 ms_hierarchy** out);
+
+/*
+ * Fit: solve T_L alpha = f (eq. bigt) by eq. split.  Jacobi sweeps m = 1..S on
+ * T'_L beta = f starting from beta_0 = f (eq. jacobi); in sweep m the level
+ * solves t_l = A_l^{-1} beta_l (l < L) run together, warm-started from the
+ * previous sweep, and beta_k = f_k - sum_{j<k} B_kj t_j is recomputed.  Levels
+ * whose beta is already final are not re-solved.  Finally alpha_l = A_l^{-1} beta_l
+ * for every level.  Each level solve stops at |beta_l - A_l x| <= rel_tol |beta_l|
+ * (FP64 true residual).  The whole fit is one persistent cooperative kernel per
+ * right-hand side.
+ *   f          host [N] (nrhs == 1) or [N][nrhs], input order
+ *   nrhs       >= 1
+ *   rel_tol    in (0, 1)
+ *   alpha_out  host, same shape as f, input order
+ *   stats      nullable; filled for the last right-hand side
+ * Errors: MS_ERR_ARG, MS_ERR_NUMERIC (non-finite f), MS_ERR_NOT_SPD,
+ * MS_ERR_NOT_CONVERGED (alpha_out still holds the last iterate),
+ * MS_ERR_TIMEOUT, MS_ERR_CUDA.  Synchronous.
+ */
+ms_status ms_fit(ms_hierarchy* h, const double* f, int nrhs, double rel_tol, double* alpha_out,
+                 ms_fit_stats* stats);
+
+/* As ms_fit with DEVICE f_dev / alpha_dev; synchronous with respect to `stream`
+ * (it waits for the device status before returning). */
+ms_status ms_fit_dev(ms_hierarchy* h, const double* f_dev, int nrhs, double rel_tol,
+                     double* alpha_dev, ms_fit_stats* stats, void* stream);
+
+/*
+ * Evaluate the approximant f_L(q) = sum_l sum_n alpha_n^(l) Phi_{delta_l}(q - x_n^(l))
+ * (eq. fapproximation) at nq query points, FP64 throughout.
+ *   alpha  host [N] or [N][nrhs], input order;  query host [nq][d];  out host [nq][nrhs].
+ * Errors: MS_ERR_ARG, MS_ERR_CUDA.  Synchronous.  nq == 0 is valid (no work).
+ */
+ms_status ms_evaluate(ms_hierarchy* h, const double* alpha, int nrhs, const double* query,
+                      int64_t nq, double* out);
+
+/* As ms_evaluate with DEVICE pointers, enqueued on `stream`. */
+ms_status ms_evaluate_dev(ms_hierarchy* h, const double* alpha_dev, int nrhs, const double* query_dev,
+                          int64_t nq, double* out_dev, void* stream);
+
+/* Building blocks of the solve, exposed for verification and benchmarking. */
+enum {
+    MS_APPLY_A64 = 0,   /* y = D_L x   (all A_l, FP64 CSR)                       Section 3 */
+    MS_APPLY_A32 = 1,   /* y = D_L x   (FP32 CSR values, FP32 accumulation)      */
+    MS_APPLY_AMF32 = 2, /* y = D_L x   (matrix-free FP32: entries recomputed)    */
+    MS_APPLY_B64 = 3,   /* y = (T_L - D_L) x  (all B_kj, k > j, FP64 CSR)        eq. bigt */
+    MS_APPLY_B32 = 4,   /* y = (T_L - D_L) x  (FP32 CSR)                          */
+    MS_APPLY_BMF32 = 5  /* y = (T_L - D_L) x  (matrix-free FP32)                  */
+};
+/*
+ * y = op x for one of the MS_APPLY_* operators.  x_dev, y_dev: DEVICE float64 [N].
+ * sorted_order = 0: x and y are in input order (the library permutes);
+ * sorted_order = 1: x and y are in the library's internal (cell-sorted) order,
+ * see ms_get_permutation.  FP32 operators round x to FP32 and widen y to FP64.
+ * Errors: MS_ERR_ARG (unknown op, or an FP32 CSR op on a handle built without
+ * FP32 values), MS_ERR_CUDA.  Enqueued on `stream`.
+ */
+ms_status ms_apply_dev(ms_hierarchy* h, int op, const double* x_dev, double* y_dev,
+                       int sorted_order, void* stream);
+
+/* perm_out (host int64 [N]): perm_out[s] = input index of the point at sorted position s. */
+ms_status ms_get_permutation(const ms_hierarchy* h, int64_t* perm_out);
+
+/* Sizes and timings of a built hierarchy. */
+ms_status ms_hierarchy_info(const ms_hierarchy* h, ms_info* info);
+
+/* Number of CUDA kernels this library has launched in the calling process so far
+ * (all threads and handles; the count is taken at launch time, not completion). */
+uint64_t ms_launch_count(void);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* ms_last_error(void);
+
+/* Free the handle and all device memory it owns; NULL is a no-op. */
+void ms_destroy(ms_hierarchy* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MS_H */

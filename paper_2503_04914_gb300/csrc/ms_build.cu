@@ -1,0 +1,381 @@
+// Hierarchy build: per-level uniform-cell binning and CSR assembly of the
+// level blocks A_l = Phi_{delta_l}(X_l, X_l) and the strictly lower blocks
+// B_kj = Phi_{delta_j}(X_k, X_j), k > j (Section 3, definition of B and eq. mas;
+// Assumption 1, eq. kernelscaling for Phi_delta = delta^-d phi(|.|/delta)).
+//
+// Binning (replaces the kd-tree of Section 5.3): the cell size of level l is
+// delta_l / cell_split, so every neighbour within delta_l of a point lies in the
+// (2R+1)^d cells around its cell, R = cell_split.  Cells are numbered by the
+// Morton code of their integer coordinates; points are counting-sorted by
+// (level, cell) and, inside a cell, ranked by input index, which makes the
+// sorted order (and every later summation order) deterministic.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ms_internal.cuh"
+
+namespace {
+
+constexpr int kBboxBlocks = 64;
+
+// ---------------------------------------------------------------- bounding boxes
+
+// partial[(l * kBboxBlocks + b) * 7 + {0..2: min, 3..5: max, 6: non-finite count}]
+__global__ void k_bbox(const double* pts, int d, const int64_t* off_dev, int L, double* partial) {
+    const int l = blockIdx.y;
+    const int64_t s = off_dev[l], e = off_dev[l + 1];
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double bad = 0.0;
+    for (int64_t i = s + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < e;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        for (int a = 0; a < d; ++a) {
+            const double v = pts[i * d + a];
+            if (!isfinite(v)) bad += 1.0;
+            mn[a] = fmin(mn[a], v);
+            mx[a] = fmax(mx[a], v);
+        }
+    }
+    __shared__ double sh[256];
+    for (int k = 0; k < 7; ++k) {
+        double v = k < 3 ? mn[k] : (k < 6 ? mx[k - 3] : bad);
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                const double a = sh[threadIdx.x], b = sh[threadIdx.x + o];
+                sh[threadIdx.x] = k < 3 ? fmin(a, b) : (k < 6 ? fmax(a, b) : a + b);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[(l * kBboxBlocks + blockIdx.x) * 7 + k] = sh[0];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- binning
+
+__global__ void k_cell_keys(const double* pts, HierView v, int32_t* key, int32_t* count) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= v.N) return;
+    const int l = level_of_row(v.off, v.L, i);
+    const LevelGrid& g = v.grid[l];
+    int c[3] = {0, 0, 0};
+    for (int a = 0; a < v.d; ++a) {
+        int ca = cell_coord(g, a, pts[i * v.d + a]);
+        c[a] = min(max(ca, 0), g.G[a] - 1);
+    }
+    const int32_t gid = (int32_t)(g.cell_off + morton(v.d, c[0], c[1], c[2]));
+    key[i] = gid;
+    atomicAdd(&count[gid], 1);
+}
+
+__global__ void k_scatter(const int32_t* key, const int32_t* cell_start, int32_t* cursor, int32_t* tmp, int64_t N) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int32_t g = key[i];
+    const int32_t pos = cell_start[g] + atomicAdd(&cursor[g], 1);
+    tmp[pos] = (int32_t)i;
+}
+
+// Final position of each point: cell start + number of points of the same cell
+// with a smaller input index.
+__global__ void k_rank(const int32_t* key, const int32_t* cell_start, const int32_t* tmp, int32_t* perm, int64_t N) {
+    const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (pos >= N) return;
+    const int32_t i = tmp[pos];
+    const int32_t g = key[i];
+    const int32_t s = cell_start[g], e = cell_start[g + 1];
+    int32_t rank = 0;
+    for (int32_t j = s; j < e; ++j) rank += (tmp[j] < i);
+    perm[s + rank] = i;
+}
+
+__global__ void k_gather_points(const double* pts, const int32_t* perm, double* X, int d, int64_t N) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const int64_t i = perm[s];
+    for (int a = 0; a < d; ++a) X[a * N + s] = pts[i * d + a];
+}
+
+// ---------------------------------------------------------------- scans
+
+constexpr int kScanBS = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanBS * kScanItems;
+
+template <typename T>
+__device__ T block_exclusive_scan(T v, T* total, T* sh) {
+    // inclusive warp scan
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        T t = lane < kScanBS / 32 ? sh[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < kScanBS / 32) sh[lane] = t;  // inclusive warp totals
+    }
+    __syncthreads();
+    const T before = (w > 0 ? sh[w - 1] : T(0)) + x - v;
+    *total = sh[kScanBS / 32 - 1];
+    __syncthreads();
+    return before;
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_scan_tiles(const Tin* in, int64_t n, Tout* tile_sums) {
+    const int64_t base = blockIdx.x * (int64_t)kScanTile + threadIdx.x * kScanItems;
+    Tout s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) s += (Tout)in[base + k];
+    __shared__ Tout sh[kScanBS / 32];
+    Tout total;
+    block_exclusive_scan<Tout>(s, &total, sh);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// Exclusive scan of a[0..n) in place by one block; a[n] receives the total.
+template <typename T>
+__global__ void k_scan_single(T* a, int64_t n) {
+    __shared__ T sh[kScanBS / 32];
+    T carry = 0;
+    for (int64_t s = 0; s < n; s += kScanBS) {
+        const int64_t i = s + threadIdx.x;
+        T v = i < n ? a[i] : T(0);
+        T total;
+        T ex = block_exclusive_scan<T>(v, &total, sh);
+        if (i < n) a[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) a[n] = carry;
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_scan_apply(const Tin* in, int64_t n, const Tout* tile_off, int64_t ntiles, Tout* out) {
+    const int64_t base = blockIdx.x * (int64_t)kScanTile + threadIdx.x * kScanItems;
+    Tout loc[kScanItems];
+    Tout s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        loc[k] = (base + k < n) ? (Tout)in[base + k] : Tout(0);
+        s += loc[k];
+    }
+    __shared__ Tout sh[kScanBS / 32];
+    Tout total;
+    Tout ex = block_exclusive_scan<Tout>(s, &total, sh) + tile_off[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = ex;
+        ex += loc[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = tile_off[ntiles];
+}
+
+// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.  tmp holds ntiles+1 Tout.
+template <typename Tin, typename Tout>
+void exclusive_scan(const Tin* in, int64_t n, Tout* out, Tout* tmp, cudaStream_t s) {
+    const int64_t ntiles = std::max<int64_t>(1, (n + kScanTile - 1) / kScanTile);
+    k_scan_tiles<Tin, Tout><<<(unsigned)ntiles, kScanBS, 0, s>>>(in, n, tmp); ms_count_launch();
+    k_scan_single<Tout><<<1, kScanBS, 0, s>>>(tmp, ntiles); ms_count_launch();
+    k_scan_apply<Tin, Tout><<<(unsigned)ntiles, kScanBS, 0, s>>>(in, n, tmp, ntiles, out); ms_count_launch();
+}
+
+__global__ void k_csr_count(HierView v, int32_t* cntA, int32_t* cntB) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= v.N) return;
+    const int k = level_of_row(v.off, v.L, s);
+    double y[3] = {0, 0, 0};
+    for (int a = 0; a < v.d; ++a) y[a] = v.X[a * v.N + s];
+    int32_t na = 0, nb = 0;
+    for_each_neighbour(v, k, y, [&](int32_t, double) { ++na; });
+    for (int j = 0; j < k; ++j) for_each_neighbour(v, j, y, [&](int32_t, double) { ++nb; });
+    cntA[s] = na;
+    cntB[s] = nb;
+}
+
+__global__ void k_csr_fill(HierView v, const int64_t* rpA, int32_t* colA, double* valA, float* valA32,
+                           const int64_t* rpB, int32_t* colB, double* valB, float* valB32) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= v.N) return;
+    const int k = level_of_row(v.off, v.L, s);
+    double y[3] = {0, 0, 0};
+    for (int a = 0; a < v.d; ++a) y[a] = v.X[a * v.N + s];
+    int64_t pa = rpA[s];
+    {
+        const double inv = 1.0 / v.delta[k], sc = v.dscale[k];
+        for_each_neighbour(v, k, y, [&](int32_t p, double r2) {
+            const double val = sc * wendland_eval<double>(v.w, sqrt(r2) * inv);
+            colA[pa] = p;
+            valA[pa] = val;
+            if (valA32) valA32[pa] = (float)val;
+            ++pa;
+        });
+    }
+    int64_t pb = rpB[s];
+    for (int j = 0; j < k; ++j) {
+        const double inv = 1.0 / v.delta[j], sc = v.dscale[j];
+        for_each_neighbour(v, j, y, [&](int32_t p, double r2) {
+            const double val = sc * wendland_eval<double>(v.w, sqrt(r2) * inv);
+            colB[pb] = p;
+            valB[pb] = val;
+            if (valB32) valB32[pb] = (float)val;
+            ++pb;
+        });
+    }
+}
+
+inline unsigned nblk(int64_t n, int bs) { return (unsigned)std::max<int64_t>(1, (n + bs - 1) / bs); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- host build
+
+ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
+    HierView& v = h->view;
+    const int d = h->d, L = h->L;
+    const int64_t N = h->N;
+
+    std::vector<void*> temps;
+    auto talloc = [&](void** p, size_t bytes) -> ms_status {
+        cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), st);
+        if (e != cudaSuccess) {
+            ms_set_error(MS_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+            return MS_ERR_OOM;
+        }
+        temps.push_back(*p);
+        return MS_OK;
+    };
+    struct Freer {
+        std::vector<void*>& t;
+        cudaStream_t s;
+        ~Freer() { for (void* p : t) cudaFreeAsync(p, s); }
+    } freer{temps, st};
+
+    MS_CUDA(cudaEventRecord(h->ev0, st));
+
+    // 1. level bounding boxes (and a finiteness check)
+    int64_t* off_dev = nullptr;
+    double* part = nullptr;
+    MS_TRY(talloc((void**)&off_dev, sizeof(int64_t) * (L + 1)));
+    MS_TRY(talloc((void**)&part, sizeof(double) * L * kBboxBlocks * 7));
+    MS_CUDA(cudaMemcpyAsync(off_dev, v.off, sizeof(int64_t) * (L + 1), cudaMemcpyHostToDevice, st));
+    k_bbox<<<dim3(kBboxBlocks, L), 256, 0, st>>>(pts, d, off_dev, L, part); ms_count_launch();
+    MS_CUDA(cudaGetLastError());
+    std::vector<double> hp((size_t)L * kBboxBlocks * 7);
+    MS_CUDA(cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st));
+    MS_CUDA(cudaStreamSynchronize(st));
+
+    const int split = h->opts.cell_split > 0 ? h->opts.cell_split : 1;
+    v.R = split;
+    int64_t cells = 0;
+    for (int l = 0; l < L; ++l) {
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        double bad = 0;
+        for (int b = 0; b < kBboxBlocks; ++b) {
+            const double* q = &hp[((size_t)l * kBboxBlocks + b) * 7];
+            for (int a = 0; a < d; ++a) { lo[a] = std::min(lo[a], q[a]); hi[a] = std::max(hi[a], q[3 + a]); }
+            bad += q[6];
+        }
+        if (bad > 0) {
+            ms_set_error(MS_ERR_NUMERIC, "level %d has non-finite point coordinates", l + 1);
+            return MS_ERR_NUMERIC;
+        }
+        LevelGrid& g = v.grid[l];
+        double cell = v.delta[l] / split;
+        const int max_bits = d == 1 ? 30 : (d == 2 ? 15 : 10);
+        int bits = 0;
+        for (int tries = 0; tries < 64; ++tries) {
+            int gmax = 1;
+            for (int a = 0; a < 3; ++a) {
+                g.G[a] = 1;
+                if (a < d) {
+                    const double ext = (hi[a] - lo[a]) / cell;
+                    g.G[a] = (int)std::max(1.0, std::ceil(std::min(ext, 1e9)));
+                    gmax = std::max(gmax, g.G[a]);
+                }
+            }
+            bits = 0;
+            while ((1 << bits) < gmax) ++bits;
+            if (bits <= max_bits && (int64_t(1) << (bits * d)) <= (int64_t(1) << 27)) break;
+            cell *= 2.0;  // too many cells: coarser grid, still covers delta with radius R
+        }
+        for (int a = 0; a < 3; ++a) g.lo[a] = a < d ? lo[a] : 0.0;
+        g.cell = cell;
+        g.inv_cell = 1.0 / cell;
+        g.bits = bits;
+        g.ncells = int64_t(1) << (bits * d);
+        g.cell_off = cells;
+        cells += g.ncells;
+    }
+    h->total_cells = cells;
+    if (cells >= (int64_t(1) << 31) - 1) {
+        ms_set_error(MS_ERR_ARG, "too many grid cells (%lld)", (long long)cells);
+        return MS_ERR_ARG;
+    }
+
+    // 2. counting sort by (level, Morton cell), ranked by input index inside a cell
+    int32_t *key, *count, *cursor, *tmp, *tile;
+    MS_TRY(talloc((void**)&key, sizeof(int32_t) * N));
+    MS_TRY(talloc((void**)&count, sizeof(int32_t) * cells));
+    MS_TRY(talloc((void**)&cursor, sizeof(int32_t) * cells));
+    MS_TRY(talloc((void**)&tmp, sizeof(int32_t) * N));
+    const int64_t maxn = std::max<int64_t>(N, cells) + 1;
+    MS_TRY(talloc((void**)&tile, sizeof(int64_t) * ((maxn + kScanTile - 1) / kScanTile + 2)));
+    MS_TRY(ms_alloc(h, (void**)&h->cell_start, sizeof(int32_t) * (cells + 1)));
+    MS_TRY(ms_alloc(h, (void**)&h->perm, sizeof(int32_t) * N));
+    MS_TRY(ms_alloc(h, (void**)&h->X, sizeof(double) * d * N));
+    MS_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t) * cells, st));
+    MS_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * cells, st));
+    v.X = h->X;
+    v.cell_start = h->cell_start;
+    k_cell_keys<<<nblk(N, 256), 256, 0, st>>>(pts, v, key, count); ms_count_launch();
+    exclusive_scan<int32_t, int32_t>(count, cells, h->cell_start, tile, st);
+    k_scatter<<<nblk(N, 256), 256, 0, st>>>(key, h->cell_start, cursor, tmp, N); ms_count_launch();
+    k_rank<<<nblk(N, 256), 256, 0, st>>>(key, h->cell_start, tmp, h->perm, N); ms_count_launch();
+    k_gather_points<<<nblk(N, 256), 256, 0, st>>>(pts, h->perm, h->X, d, N); ms_count_launch();
+    MS_CUDA(cudaGetLastError());
+
+    // 3. CSR of A (diagonal blocks) and B (strictly lower blocks)
+    int32_t *cntA, *cntB;
+    MS_TRY(talloc((void**)&cntA, sizeof(int32_t) * N));
+    MS_TRY(talloc((void**)&cntB, sizeof(int32_t) * N));
+    MS_TRY(ms_alloc(h, (void**)&h->A.rp, sizeof(int64_t) * (N + 1)));
+    MS_TRY(ms_alloc(h, (void**)&h->B.rp, sizeof(int64_t) * (N + 1)));
+    k_csr_count<<<nblk(N, 128), 128, 0, st>>>(v, cntA, cntB); ms_count_launch();
+    exclusive_scan<int32_t, int64_t>(cntA, N, h->A.rp, (int64_t*)tile, st);
+    exclusive_scan<int32_t, int64_t>(cntB, N, h->B.rp, (int64_t*)tile, st);
+    MS_CUDA(cudaGetLastError());
+    int64_t nnz[2];
+    MS_CUDA(cudaMemcpyAsync(&nnz[0], h->A.rp + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    MS_CUDA(cudaMemcpyAsync(&nnz[1], h->B.rp + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    MS_CUDA(cudaStreamSynchronize(st));
+    h->A.nnz = nnz[0];
+    h->B.nnz = nnz[1];
+    const bool fp32 = h->opts.precision == MS_PREC_MIXED;
+    MS_TRY(ms_alloc(h, (void**)&h->A.col, sizeof(int32_t) * h->A.nnz));
+    MS_TRY(ms_alloc(h, (void**)&h->A.v64, sizeof(double) * h->A.nnz));
+    if (fp32) MS_TRY(ms_alloc(h, (void**)&h->A.v32, sizeof(float) * h->A.nnz));
+    MS_TRY(ms_alloc(h, (void**)&h->B.col, sizeof(int32_t) * h->B.nnz));
+    MS_TRY(ms_alloc(h, (void**)&h->B.v64, sizeof(double) * h->B.nnz));
+    if (fp32) MS_TRY(ms_alloc(h, (void**)&h->B.v32, sizeof(float) * h->B.nnz));
+    k_csr_fill<<<nblk(N, 128), 128, 0, st>>>(v, h->A.rp, h->A.col, h->A.v64, h->A.v32, h->B.rp, h->B.col,
+                                             h->B.v64, h->B.v32); ms_count_launch();
+    MS_CUDA(cudaGetLastError());
+    MS_CUDA(cudaEventRecord(h->ev1, st));
+    MS_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    MS_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    h->build_ms = ms;
+    return MS_OK;
+}

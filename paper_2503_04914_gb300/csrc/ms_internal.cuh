@@ -1,0 +1,304 @@
+// Internal definitions shared by the CUDA translation units of libms.so.
+//
+// Data layout in device memory (all levels concatenated, coarse to fine):
+//   * points are stored "sorted": within each level, by the Morton code of
+//     their cell in that level's uniform grid (cell size delta_l / cell_split),
+//     ties broken by input index.  X is SoA: X[a * N + s] is coordinate a of
+//     sorted point s.  perm[s] is the input index of sorted point s.
+//   * cell_start is an exclusive prefix sum of points per cell over the
+//     cells of all levels (level l's cells start at grid[l].cell_off); the
+//     points of cell g are sorted positions [cell_start[g], cell_start[g+1]).
+//   * A (block diagonal) and B (strictly lower blocks) are CSR over sorted
+//     rows: int64 row offsets, int32 global sorted column indices, FP64 values
+//     and optional FP32 values.  Row s of B holds the blocks j = 1..k-1 of its
+//     level k in increasing j.
+#pragma once
+
+#include <cstdint>
+#include <cstdio>
+#include <cuda_runtime.h>
+#include <cuda/atomic>
+
+#include "../../include/ms.h"
+
+#define MS_MAXL MS_MAX_LEVELS
+
+// ------------------------------------------------------------------ kernel
+
+// phi(r) = (1-r)^e * (c0 + c1 r + c2 r^2 + c3 r^3) for r < 1, else 0.
+struct WendlandPoly {
+    int e;
+    double c[4];
+};
+
+// Wendland phi_{d,k}, l = floor(d/2)+k+1 (Wendland's closed forms, k = 0..3).
+static inline bool wendland_poly(int wd, int wk, WendlandPoly* w) {
+    if (wd < 1 || wd > 3 || wk < 0 || wk > 3) return false;
+    const double l = wd / 2 + wk + 1;
+    w->e = (int)l + wk;
+    w->c[0] = w->c[1] = w->c[2] = w->c[3] = 0.0;
+    switch (wk) {
+    case 0: w->c[0] = 1.0; break;
+    case 1: w->c[0] = 1.0; w->c[1] = l + 1.0; break;
+    case 2: w->c[0] = 3.0; w->c[1] = 3.0 * l + 6.0; w->c[2] = l * l + 4.0 * l + 3.0; break;
+    case 3:
+        w->c[0] = 15.0; w->c[1] = 15.0 * l + 45.0; w->c[2] = 6.0 * l * l + 36.0 * l + 45.0;
+        w->c[3] = l * l * l + 9.0 * l * l + 23.0 * l + 15.0;
+        break;
+    }
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T wendland_eval(const WendlandPoly& w, T r) {
+    T s = T(1) - r;
+    T pw = T(1);
+    for (int i = 0; i < w.e; ++i) pw *= s;
+    T p = T(w.c[3]);
+    p = p * r + T(w.c[2]);
+    p = p * r + T(w.c[1]);
+    p = p * r + T(w.c[0]);
+    return pw * p;
+}
+
+// ------------------------------------------------------------------ grids
+
+struct LevelGrid {
+    double lo[3];      // grid origin (level bounding-box minimum)
+    double inv_cell;   // 1 / cell size
+    double cell;       // cell size
+    int G[3];          // cells per axis (1 for unused axes)
+    int bits;          // Morton bits per axis (P = 2^bits >= max G)
+    int64_t cell_off;  // first global cell id of the level
+    int64_t ncells;    // P^d
+};
+
+__host__ __device__ __forceinline__ uint32_t spread2(uint32_t v) {  // 16 -> 32 bits, 1 gap
+    v &= 0x0000ffffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+__host__ __device__ __forceinline__ uint32_t spread3(uint32_t v) {  // 10 -> 30 bits, 2 gaps
+    v &= 0x000003ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+__host__ __device__ __forceinline__ uint32_t morton(int d, int cx, int cy, int cz) {
+    if (d == 1) return (uint32_t)cx;
+    if (d == 2) return spread2((uint32_t)cx) | (spread2((uint32_t)cy) << 1);
+    return spread3((uint32_t)cx) | (spread3((uint32_t)cy) << 1) | (spread3((uint32_t)cz) << 2);
+}
+
+// Everything a kernel needs to know about the hierarchy (passed by value).
+struct HierView {
+    int d, L, R;                // R = neighbour cell radius (cells searched: (2R+1)^d)
+    int64_t N;
+    int64_t off[MS_MAXL + 1];   // level row offsets
+    double delta[MS_MAXL];
+    double dscale[MS_MAXL];     // delta^-d
+    LevelGrid grid[MS_MAXL];
+    WendlandPoly w;
+    const double* X;            // [d][N] sorted coordinates
+    const int32_t* cell_start;  // [total cells + 1]
+};
+
+__device__ __forceinline__ int level_of_row(const int64_t* off, int L, int64_t row) {
+    int l = 0;
+    while (l + 1 < L && row >= off[l + 1]) ++l;
+    return l;
+}
+
+// Cell coordinate of coordinate value v on axis a of grid g.  Not clamped to
+// the grid (callers skip or clamp out-of-range cells) but kept within
+// [-4, G+4] so that far-away query points cannot overflow the conversion.
+__device__ __forceinline__ int cell_coord(const LevelGrid& g, int a, double v) {
+    double u = floor((v - g.lo[a]) * g.inv_cell);
+    u = fmin(fmax(u, -4.0), (double)g.G[a] + 4.0);
+    return (int)u;
+}
+
+// Calls visit(p, r2) for every sorted point p of level j with |x_p - y|^2 < delta_j^2
+// (the (2R+1)^d cells around y's cell in level j's grid, FP64 distances).
+template <typename F>
+__device__ __forceinline__ void for_each_neighbour(const HierView& v, int j, const double* y, F&& visit) {
+    const LevelGrid& g = v.grid[j];
+    const double d2 = v.delta[j] * v.delta[j];
+    int c[3] = {0, 0, 0};
+    for (int a = 0; a < v.d; ++a) c[a] = cell_coord(g, a, y[a]);
+    const int R = v.R;
+    const int rz = v.d >= 3 ? R : 0, ry = v.d >= 2 ? R : 0;
+    for (int dz = -rz; dz <= rz; ++dz) {
+        const int cz = c[2] + dz;
+        if (cz < 0 || cz >= g.G[2]) continue;
+        for (int dy = -ry; dy <= ry; ++dy) {
+            const int cy = c[1] + dy;
+            if (cy < 0 || cy >= g.G[1]) continue;
+            for (int dx = -R; dx <= R; ++dx) {
+                const int cx = c[0] + dx;
+                if (cx < 0 || cx >= g.G[0]) continue;
+                const int64_t gid = g.cell_off + morton(v.d, cx, cy, cz);
+                const int32_t s = v.cell_start[gid], e = v.cell_start[gid + 1];
+                for (int32_t p = s; p < e; ++p) {
+                    double r2 = 0.0;
+                    for (int a = 0; a < v.d; ++a) {
+                        const double t = v.X[a * v.N + p] - y[a];
+                        r2 = fma(t, t, r2);
+                    }
+                    if (r2 < d2) visit(p, r2);
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ errors (host)
+
+struct MsError {
+    ms_status st;
+};
+void ms_set_error(ms_status st, const char* fmt, ...);
+void ms_count_launch(unsigned n = 1);  // process-wide kernel launch counter
+ms_status ms_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+#define MS_CUDA(call)                                                            \
+    do {                                                                         \
+        cudaError_t e__ = (call);                                                \
+        if (e__ != cudaSuccess) return ms_cuda_error(e__, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define MS_TRY(call)                         \
+    do {                                     \
+        ms_status s__ = (call);              \
+        if (s__ != MS_OK) return s__;        \
+    } while (0)
+
+// ------------------------------------------------------------------ device helpers
+
+__device__ __forceinline__ unsigned long long ms_globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  One
+// arrival counter plus a generation word; the last CTA to arrive resets the
+// counter and publishes the next generation with release semantics, the others
+// spin on the generation with acquire loads.  Every wait is bounded: past
+// timeout_ns it records MS_ERR_TIMEOUT in *status and returns false; it also
+// returns false as soon as another CTA has recorded a time-out.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks,
+                                             int* status, unsigned long long timeout_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(*gen);
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(*count);
+        cuda::atomic_ref<int, cuda::thread_scope_device> st(*status);
+        const unsigned mine = g.load(cuda::memory_order_relaxed);
+        const unsigned arrived = c.fetch_add(1u, cuda::memory_order_acq_rel);
+        int ok = 1;
+        if (arrived == nblocks - 1) {
+            c.store(0u, cuda::memory_order_relaxed);
+            g.store(mine + 1u, cuda::memory_order_release);
+        } else {
+            const unsigned long long t0 = ms_globaltimer();
+            unsigned spins = 0;
+            while (g.load(cuda::memory_order_acquire) == mine) {
+                if ((++spins & 255u) == 0u) {
+                    if (st.load(cuda::memory_order_relaxed) == MS_ERR_TIMEOUT) { ok = 0; break; }
+                    if (ms_globaltimer() - t0 > timeout_ns) {
+                        int expect = 0;
+                        st.compare_exchange_strong(expect, (int)MS_ERR_TIMEOUT, cuda::memory_order_relaxed);
+                        if (expect != 0) st.store((int)MS_ERR_TIMEOUT, cuda::memory_order_relaxed);
+                        ok = 0;
+                        break;
+                    }
+                }
+                __nanosleep(32);
+            }
+        }
+        if (ok && st.load(cuda::memory_order_relaxed) == MS_ERR_TIMEOUT) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum (fixed shuffle tree, then warp 0 over the warp sums).
+// Result is valid in every thread.  `scratch` holds >= BS/32 doubles.
+template <int BS>
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) scratch[w] = v;
+    __syncthreads();
+    double t = (lane < BS / 32) ? scratch[lane] : 0.0;
+    t = warp_sum(t);
+    return t;
+}
+
+// ------------------------------------------------------------------ host-side handle
+
+struct DevCSR {
+    int64_t* rp = nullptr;   // [N+1]
+    int32_t* col = nullptr;  // [nnz]
+    double* v64 = nullptr;   // [nnz]
+    float* v32 = nullptr;    // [nnz] (MIXED only)
+    int64_t nnz = 0;
+};
+
+struct ms_hierarchy {
+    int device = 0;
+    int d = 0, L = 0;
+    int64_t N = 0;
+    ms_opts opts{};
+    HierView view{};             // X / cell_start pointers filled
+    int64_t total_cells = 0;
+    double* X = nullptr;         // [d][N] sorted
+    int32_t* perm = nullptr;     // sorted -> input
+    int32_t* cell_start = nullptr;
+    DevCSR A, B;
+    // solver work space (sorted order)
+    double *f = nullptr, *beta = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+    float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    double* part = nullptr;      // reduction partials
+    unsigned* bar = nullptr;     // barrier words
+    int* status = nullptr;       // device status
+    int64_t* iters = nullptr;    // per-level iteration counters
+    int* refines = nullptr;
+    double* resid = nullptr;
+    double* bytes = nullptr;
+    double* tmp64 = nullptr;     // [N] scratch (permutations)
+    int solve_blocks = 0;        // cooperative grid size
+    int tpr_A = 8, tpr_B = 32;
+    int64_t device_bytes = 0;
+    double build_ms = 0.0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    void* allocs[64];
+    int nallocs = 0;
+};
+
+ms_status ms_alloc(ms_hierarchy* h, void** p, size_t bytes);
+ms_status ms_build_impl(ms_hierarchy* h, const double* points_dev, cudaStream_t s);
+ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel_tol, double* alpha_dev,
+                      ms_fit_stats* stats, cudaStream_t s);
+ms_status ms_apply_impl(ms_hierarchy* h, int op, const double* x_dev, double* y_dev, int sorted, cudaStream_t s);
+ms_status ms_evaluate_impl(ms_hierarchy* h, const double* alpha_dev, int nrhs, const double* q_dev, int64_t nq,
+                           double* out_dev, cudaStream_t s);
+
+// permutation helpers (ms_capi.cu)
+void ms_gather_sorted(const double* in, double* out, const int32_t* perm, int64_t N, int nrhs, int col, cudaStream_t s);
+void ms_scatter_input(const double* in, double* out, const int32_t* perm, int64_t N, int nrhs, int col, cudaStream_t s);

@@ -1,0 +1,698 @@
+// The fit: eq. split of Section 3 solved on the device in ONE persistent
+// cooperative kernel per right-hand side.
+//
+//   T'_L beta = f   by Jacobi sweeps (eq. jacobi, Theorem 9), beta_0 = f;
+//   D_L alpha = beta by per-level conjugate gradients (Theorem 8,
+//                    eq. blockdiagonal_levelwise), all levels in flight together.
+//
+// Sweep m (0-based) of the Jacobi iteration solves A_l t_l = beta_l for the
+// levels l = m..L-2 together (warm-started from the previous sweep; level m,
+// whose beta is final, to the requested tolerance, the others to the looser
+// intermediate tolerance), then recomputes beta_k = f_k - sum_{j<k} B_kj t_j for
+// the rows of levels k = m+1..L-1.  Levels below m already hold their final t
+// (their beta cannot change any more) and are not re-solved; rows of levels
+// <= m are not recomputed (they would reproduce the same values).  A final
+// solve over all levels gives alpha_l = A_l^{-1} beta_l and certifies every
+// level's FP64 true residual.
+//
+// Level solves are CG with FP64 dots computed as deterministic two-stage
+// reductions (per-CTA partials, then a fixed-order sum that every CTA performs
+// identically, so every CTA takes the same convergence decisions without
+// further communication).  Stopping: |beta_l - A_l x| <= tol |beta_l| in FP64
+// (true residual, re-checked after the recursive residual converges).
+//   FP64 mode : CG on FP64 vectors with the FP64 CSR values.
+//   MIXED mode: iterative refinement: outer FP64 true residual r = b - A x
+//               (FP64 CSR), inner CG on FP32 vectors with FP32 CSR values and
+//               FP32 accumulation (FP64 dots and scalars) for A d = r/|r|,
+//               then x += |r| d in FP64.
+// Grid barriers are bounded (ms_internal.cuh); on a time-out every CTA
+// returns and the host reports MS_ERR_TIMEOUT.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ms_internal.cuh"
+
+namespace {
+
+constexpr int kBS = 512;     // threads per CTA of the solve kernel
+constexpr int kChunk = 256;  // rows per work chunk (chunks never straddle levels)
+constexpr int kNW = kBS / 32;
+constexpr int kAcc = 2;      // accumulators per phase
+
+struct SolveArgs {
+    int L;
+    int64_t N;
+    int64_t off[MS_MAXL + 1];
+    int64_t coff[MS_MAXL + 1];   // chunk offsets per level
+    int64_t nnzA[MS_MAXL], nnzB[MS_MAXL];
+    int tprA[MS_MAXL], tprB[MS_MAXL];
+    const int64_t* Arp;
+    const int32_t* Acol;
+    const double* Av64;
+    const float* Av32;
+    const int64_t* Brp;
+    const int32_t* Bcol;
+    const double* Bv64;
+    const double* f;
+    double *beta, *x, *r, *p, *q;
+    float *x32, *r32, *p32, *q32;
+    double* part;      // [kAcc][MS_MAXL][gridDim.x]
+    unsigned* bar;     // [0] arrival count, [1] generation
+    int* status;
+    int64_t* iters;    // [MS_MAXL]
+    int* refines;      // [MS_MAXL]
+    double* resid;     // [MS_MAXL]
+    double* bytes;     // [1]
+    int sweeps, max_iters, max_outer;
+    double tol, inter_tol, inner_tol;
+    unsigned long long timeout_ns;
+};
+
+// Per-CTA shared state of the solve (identical in every CTA).
+struct Shared {
+    double red[kNW];
+    double acc[kAcc][MS_MAXL];
+    double out[kAcc][MS_MAXL];
+    double rr[MS_MAXL], bb[MS_MAXL], alpha[MS_MAXL], beta[MS_MAXL], tol[MS_MAXL], scale[MS_MAXL],
+        target[MS_MAXL];
+    int act[MS_MAXL], oact[MS_MAXL], zero[MS_MAXL];
+    int it_solve[MS_MAXL];
+    long long it_total[MS_MAXL];
+    int refines[MS_MAXL];
+    double bytes;
+    int any;
+};
+
+// y = sum_k val[k] * x[col[k]] over one CSR row, by a sub-warp of S lanes
+// (sl = lane within the sub-warp); the result is valid in every lane.  All 32
+// lanes of the warp must call it (invalid rows pass e = s).
+template <typename TV, typename TX, typename TA>
+__device__ __forceinline__ TA csr_row(const int32_t* __restrict__ col, const TV* __restrict__ val,
+                                      const TX* __restrict__ x, int64_t s, int64_t e, int sl, int S) {
+    TA acc = TA(0);
+    for (int64_t k = s + sl; k < e; k += S) acc += (TA)val[k] * (TA)x[col[k]];
+    for (int o = S >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+__device__ __forceinline__ int level_of_chunk(const SolveArgs& a, int64_t c) {
+    int l = 0;
+    while (l + 1 < a.L && c >= a.coff[l + 1]) ++l;
+    return l;
+}
+
+// Run body(l, r0, r1, acc) over this CTA's chunks of levels [l0, l1) with sel(l) true;
+// thread-local accumulators are block-reduced into sh.acc[k][l] (fixed order),
+// and the per-CTA sums are written to the partials array.
+template <int K, typename Sel, typename Body>
+__device__ __forceinline__ void run_phase(const SolveArgs& a, Shared& sh, int l0, int l1, Sel sel, Body body) {
+    for (int i = threadIdx.x; i < kAcc * MS_MAXL; i += kBS) (&sh.acc[0][0])[i] = 0.0;
+    __syncthreads();
+    double acc[K > 0 ? K : 1];
+#pragma unroll
+    for (int k = 0; k < (K > 0 ? K : 1); ++k) acc[k] = 0.0;
+    int cur = -1;
+    const int64_t c1 = a.coff[l1];
+    for (int64_t c = a.coff[l0] + blockIdx.x; c < c1; c += gridDim.x) {
+        const int l = level_of_chunk(a, c);
+        if (!sel(l)) continue;
+        if (K > 0 && l != cur) {
+            if (cur >= 0) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const double t = block_sum<kBS>(acc[k], sh.red);
+                    if (threadIdx.x == 0) sh.acc[k][cur] += t;
+                    acc[k] = 0.0;
+                }
+            }
+            cur = l;
+        }
+        const int64_t r0 = a.off[l] + (c - a.coff[l]) * kChunk;
+        const int64_t r1 = min(r0 + (int64_t)kChunk, a.off[l + 1]);
+        body(l, r0, r1, acc);
+    }
+    if (K > 0) {
+        if (cur >= 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const double t = block_sum<kBS>(acc[k], sh.red);
+                if (threadIdx.x == 0) sh.acc[k][cur] += t;
+            }
+        }
+        __syncthreads();
+        const int nl = l1 - l0;
+        for (int i = threadIdx.x; i < K * nl; i += kBS) {
+            const int k = i / nl, l = l0 + i % nl;
+            a.part[((size_t)k * MS_MAXL + l) * gridDim.x + blockIdx.x] = sh.acc[k][l];
+        }
+    }
+}
+
+// sh.out[k][l] = sum over CTAs of the partials (same fixed order in every CTA).
+template <int K>
+__device__ __forceinline__ void reduce_partials(const SolveArgs& a, Shared& sh, int l0, int l1) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nl = l1 - l0;
+    for (int i = w; i < K * nl; i += kNW) {
+        const int k = i / nl, l = l0 + i % nl;
+        const double* src = a.part + ((size_t)k * MS_MAXL + l) * gridDim.x;
+        double s = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(src + b);
+        s = warp_sum(s);
+        if (lane == 0) sh.out[k][l] = s;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool gsync(const SolveArgs& a) {
+    return grid_barrier(&a.bar[0], &a.bar[1], gridDim.x, a.status, a.timeout_ns);
+}
+
+// Rows [r0, r1) of a chunk, one sub-warp of S lanes per row; fn(row, valid, sl).
+template <typename Fn>
+__device__ __forceinline__ void rows_by_subwarp(int64_t r0, int64_t r1, int S, Fn fn) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int spw = 32 / S;
+    const int64_t n = r1 - r0;
+    for (int64_t base = (int64_t)w * spw; base < n; base += (int64_t)kNW * spw) {
+        const int64_t row = r0 + base + lane / S;
+        fn(row, row < r1, lane & (S - 1));
+    }
+}
+
+// ---------------------------------------------------------------- level solve
+
+// Solve A_l x_l = beta_l for the levels [l0, l1), x warm.  tight_all: every level
+// to a.tol, else only level l0 to a.tol and the others to a.inter_tol.
+template <int MODE>
+__device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, bool tight_all) {
+    const int tid = threadIdx.x;
+    for (int l = tid; l < MS_MAXL; l += kBS) {
+        sh.oact[l] = (l >= l0 && l < l1) ? 1 : 0;
+        sh.act[l] = 0;
+        sh.zero[l] = 0;
+        sh.it_solve[l] = 0;
+        sh.tol[l] = (tight_all || l == l0) ? a.tol : a.inter_tol;
+    }
+    __syncthreads();
+    bool first = true;
+    for (int outer = 0; outer < a.max_outer; ++outer) {
+        // ---- P1: FP64 true residual r = b - A x  (FP64 mode also sets p = r)
+        run_phase<2>(a, sh, l0, l1, [&](int l) { return sh.oact[l] != 0; },
+                     [&](int l, int64_t r0, int64_t r1, double* acc) {
+                         const int S = a.tprA[l];
+                         rows_by_subwarp(r0, r1, S, [&](int64_t row, bool ok, int sl) {
+                             int64_t s = 0, e = 0;
+                             if (ok) { s = a.Arp[row]; e = a.Arp[row + 1]; }
+                             const double y = csr_row<double, double, double>(a.Acol, a.Av64, a.x, s, e, sl, S);
+                             if (ok && sl == 0) {
+                                 const double b = a.beta[row];
+                                 const double ri = b - y;
+                                 a.r[row] = ri;
+                                 if (MODE == 0) a.p[row] = ri;
+                                 acc[0] += ri * ri;
+                                 acc[1] += b * b;
+                             }
+                         });
+                     });
+        if (!gsync(a)) return false;
+        reduce_partials<2>(a, sh, l0, l1);
+        if (tid == 0) {
+            sh.any = 0;
+            for (int l = l0; l < l1; ++l) {
+                if (!sh.oact[l]) continue;
+                const double rr = sh.out[0][l];
+                if (first) sh.bb[l] = sh.out[1][l];
+                const double bb = sh.bb[l];
+                sh.bytes += (double)a.nnzA[l] * 12.0 + (double)(a.off[l + 1] - a.off[l]) * (MODE == 0 ? 48.0 : 40.0);
+                if (!isfinite(rr) || !isfinite(bb)) {
+                    sh.oact[l] = 0;
+                    if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)MS_ERR_NUMERIC);
+                    continue;
+                }
+                if (bb == 0.0) {  // zero right-hand side: the solution is zero
+                    sh.zero[l] = 1;
+                    sh.oact[l] = 0;
+                    if (blockIdx.x == 0) a.resid[l] = 0.0;
+                    continue;
+                }
+                const double res = sqrt(rr / bb);
+                if (blockIdx.x == 0) a.resid[l] = res;
+                if (res <= sh.tol[l]) {
+                    sh.oact[l] = 0;
+                    continue;
+                }
+                if (sh.it_solve[l] >= a.max_iters) {
+                    sh.oact[l] = 0;
+                    if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)MS_ERR_NOT_CONVERGED);
+                    continue;
+                }
+                sh.any = 1;
+                sh.refines[l] += 1;
+                sh.act[l] = 1;
+                if (MODE == 0) {
+                    sh.rr[l] = rr;
+                    // recursive-residual target, with margin below the true-residual tolerance
+                    sh.target[l] = 0.25 * sh.tol[l] * sh.tol[l] * bb;
+                } else {
+                    sh.scale[l] = 1.0 / sqrt(rr);
+                    const double need = 0.5 * sh.tol[l] * sqrt(bb) * sh.scale[l];
+                    const double t = fmax(a.inner_tol, fmin(need, 1.0));
+                    sh.target[l] = t * t;
+                }
+            }
+        }
+        __syncthreads();
+        first = false;
+        // zero right-hand sides: x = 0 on those levels
+        {
+            bool anyzero = false;
+            for (int l = l0; l < l1; ++l) anyzero |= sh.zero[l] != 0;
+            if (anyzero) {
+                run_phase<0>(a, sh, l0, l1, [&](int l) { return sh.zero[l] != 0; },
+                             [&](int, int64_t r0, int64_t r1, double*) {
+                                 for (int64_t row = r0 + tid; row < r1; row += kBS) a.x[row] = 0.0;
+                             });
+                // other CTAs read these rows in the next phases
+                if (!gsync(a)) return false;
+                for (int l = tid; l < MS_MAXL; l += kBS) sh.zero[l] = 0;
+                __syncthreads();
+            }
+        }
+        if (!sh.any) break;
+
+        if (MODE == 1) {
+            // ---- P2: r32 = r / |r|, p32 = r32, x32 = 0; rr of the FP32 vector in FP64
+            run_phase<1>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
+                         [&](int l, int64_t r0, int64_t r1, double* acc) {
+                             const double sc = sh.scale[l];
+                             for (int64_t row = r0 + tid; row < r1; row += kBS) {
+                                 const float v = (float)(a.r[row] * sc);
+                                 a.r32[row] = v;
+                                 a.p32[row] = v;
+                                 a.x32[row] = 0.f;
+                                 acc[0] += (double)v * (double)v;
+                             }
+                         });
+            if (!gsync(a)) return false;
+            reduce_partials<1>(a, sh, l0, l1);
+            if (tid == 0)
+                for (int l = l0; l < l1; ++l)
+                    if (sh.act[l]) sh.rr[l] = sh.out[0][l];
+            __syncthreads();
+        }
+
+        // ---- inner CG iterations
+        for (;;) {
+            // PA: q = A p, pq
+            run_phase<1>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
+                         [&](int l, int64_t r0, int64_t r1, double* acc) {
+                             const int S = a.tprA[l];
+                             rows_by_subwarp(r0, r1, S, [&](int64_t row, bool ok, int sl) {
+                                 int64_t s = 0, e = 0;
+                                 if (ok) { s = a.Arp[row]; e = a.Arp[row + 1]; }
+                                 if (MODE == 0) {
+                                     const double y = csr_row<double, double, double>(a.Acol, a.Av64, a.p, s, e, sl, S);
+                                     if (ok && sl == 0) { a.q[row] = y; acc[0] += a.p[row] * y; }
+                                 } else {
+                                     const float y = csr_row<float, float, float>(a.Acol, a.Av32, a.p32, s, e, sl, S);
+                                     if (ok && sl == 0) { a.q32[row] = y; acc[0] += (double)a.p32[row] * (double)y; }
+                                 }
+                             });
+                         });
+            if (!gsync(a)) return false;
+            reduce_partials<1>(a, sh, l0, l1);
+            if (tid == 0) {
+                for (int l = l0; l < l1; ++l) {
+                    if (!sh.act[l]) continue;
+                    const double pq = sh.out[0][l];
+                    sh.bytes += (double)a.nnzA[l] * (MODE == 0 ? 12.0 : 8.0) +
+                                (double)(a.off[l + 1] - a.off[l]) * (MODE == 0 ? 32.0 : 20.0);
+                    if (!(pq > 0.0) || !isfinite(pq)) {
+                        sh.act[l] = 0;
+                        sh.oact[l] = 0;
+                        if (blockIdx.x == 0) atomicCAS(a.status, 0, isfinite(pq) ? (int)MS_ERR_NOT_SPD : (int)MS_ERR_NUMERIC);
+                        continue;
+                    }
+                    sh.alpha[l] = sh.rr[l] / pq;
+                }
+            }
+            __syncthreads();
+            // PB: x += alpha p, r -= alpha q, rr
+            run_phase<1>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
+                         [&](int l, int64_t r0, int64_t r1, double* acc) {
+                             const double al = sh.alpha[l];
+                             for (int64_t row = r0 + tid; row < r1; row += kBS) {
+                                 if (MODE == 0) {
+                                     a.x[row] += al * a.p[row];
+                                     const double rv = a.r[row] - al * a.q[row];
+                                     a.r[row] = rv;
+                                     acc[0] += rv * rv;
+                                 } else {
+                                     const float af = (float)al;
+                                     a.x32[row] = fmaf(af, a.p32[row], a.x32[row]);
+                                     const float rv = fmaf(-af, a.q32[row], a.r32[row]);
+                                     a.r32[row] = rv;
+                                     acc[0] += (double)rv * (double)rv;
+                                 }
+                             }
+                         });
+            if (!gsync(a)) return false;
+            reduce_partials<1>(a, sh, l0, l1);
+            if (tid == 0) {
+                sh.any = 0;
+                for (int l = l0; l < l1; ++l) {
+                    if (!sh.act[l]) continue;
+                    const double rn = sh.out[0][l];
+                    sh.bytes += (double)(a.off[l + 1] - a.off[l]) * (MODE == 0 ? 48.0 : 24.0);
+                    sh.beta[l] = rn / sh.rr[l];
+                    sh.rr[l] = rn;
+                    sh.it_solve[l] += 1;
+                    sh.it_total[l] += 1;
+                    if (!isfinite(rn)) {
+                        sh.act[l] = 0;
+                        sh.oact[l] = 0;
+                        if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)MS_ERR_NUMERIC);
+                        continue;
+                    }
+                    if (rn <= sh.target[l] || sh.it_solve[l] >= a.max_iters) {
+                        sh.act[l] = 0;
+                        continue;
+                    }
+                    sh.any = 1;
+                }
+            }
+            __syncthreads();
+            if (!sh.any) break;
+            // PC: p = r + beta p
+            run_phase<0>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
+                         [&](int l, int64_t r0, int64_t r1, double*) {
+                             const double be = sh.beta[l];
+                             for (int64_t row = r0 + tid; row < r1; row += kBS) {
+                                 if (MODE == 0) a.p[row] = a.r[row] + be * a.p[row];
+                                 else a.p32[row] = fmaf((float)be, a.p32[row], a.r32[row]);
+                             }
+                         });
+            if (tid == 0)
+                for (int l = l0; l < l1; ++l)
+                    if (sh.act[l]) sh.bytes += (double)(a.off[l + 1] - a.off[l]) * (MODE == 0 ? 24.0 : 12.0);
+            if (!gsync(a)) return false;
+        }
+
+        if (MODE == 1) {
+            // ---- P3: x += |r| d  (FP64)
+            run_phase<0>(a, sh, l0, l1, [&](int l) { return sh.oact[l] != 0 && sh.scale[l] > 0.0; },
+                         [&](int l, int64_t r0, int64_t r1, double*) {
+                             const double inv = 1.0 / sh.scale[l];
+                             for (int64_t row = r0 + tid; row < r1; row += kBS)
+                                 a.x[row] += (double)a.x32[row] * inv;
+                         });
+            if (tid == 0)
+                for (int l = l0; l < l1; ++l)
+                    if (sh.oact[l]) sh.bytes += (double)(a.off[l + 1] - a.off[l]) * 20.0;
+            if (!gsync(a)) return false;
+        }
+    }
+    // levels still active after max_outer rounds did not reach the tolerance
+    if (tid == 0)
+        for (int l = l0; l < l1; ++l)
+            if (sh.oact[l] && blockIdx.x == 0) atomicCAS(a.status, 0, (int)MS_ERR_NOT_CONVERGED);
+    __syncthreads();
+    return true;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kBS) k_fit(SolveArgs a) {
+    __shared__ Shared sh;
+    const int tid = threadIdx.x;
+    for (int l = tid; l < MS_MAXL; l += kBS) {
+        sh.it_total[l] = 0;
+        sh.refines[l] = 0;
+        sh.scale[l] = 0.0;
+    }
+    if (tid == 0) sh.bytes = 0.0;
+    __syncthreads();
+    const int L = a.L;
+    // beta_0 = f, x = 0
+    run_phase<0>(a, sh, 0, L, [](int) { return true; }, [&](int, int64_t r0, int64_t r1, double*) {
+        for (int64_t row = r0 + tid; row < r1; row += kBS) {
+            a.beta[row] = a.f[row];
+            a.x[row] = 0.0;
+        }
+    });
+    if (!gsync(a)) return;
+    for (int m = 0; m < a.sweeps; ++m) {
+        if (m <= L - 2) {
+            if (!solve_levels<MODE>(a, sh, m, L - 1, false)) return;
+        }
+        if (m + 1 <= L - 1) {
+            // beta_k = f_k - sum_{j<k} B_kj t_j for the rows of levels k = m+1..L-1 (FP64)
+            run_phase<0>(a, sh, m + 1, L, [](int) { return true; },
+                         [&](int l, int64_t r0, int64_t r1, double*) {
+                             const int S = a.tprB[l];
+                             rows_by_subwarp(r0, r1, S, [&](int64_t row, bool ok, int sl) {
+                                 int64_t s = 0, e = 0;
+                                 if (ok) { s = a.Brp[row]; e = a.Brp[row + 1]; }
+                                 const double y = csr_row<double, double, double>(a.Bcol, a.Bv64, a.x, s, e, sl, S);
+                                 if (ok && sl == 0) a.beta[row] = a.f[row] - y;
+                             });
+                         });
+            if (tid == 0)
+                for (int l = m + 1; l < L; ++l)
+                    sh.bytes += (double)a.nnzB[l] * 12.0 + (double)(a.off[l + 1] - a.off[l]) * 32.0;
+            if (!gsync(a)) return;
+        }
+    }
+    if (!solve_levels<MODE>(a, sh, 0, L, true)) return;
+    if (blockIdx.x == 0 && tid == 0) {
+        for (int l = 0; l < L; ++l) {
+            a.iters[l] = sh.it_total[l];
+            a.refines[l] = sh.refines[l];
+        }
+        a.bytes[0] = sh.bytes;
+    }
+}
+
+// ---------------------------------------------------------------- stand-alone mat-vecs
+
+template <typename TV, typename TX, typename TA>
+__global__ void k_spmv(const int64_t* rp, const int32_t* col, const TV* val, const TX* x, double* y, int64_t N,
+                       int S, const double* sub, double sign) {
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int spw = 32 / S;
+    const int64_t row = warp * spw + lane / S;
+    const bool ok = row < N;
+    int64_t s = 0, e = 0;
+    if (ok) { s = rp[row]; e = rp[row + 1]; }
+    const TA v = csr_row<TV, TX, TA>(col, val, x, s, e, lane & (S - 1), S);
+    if (ok && (lane & (S - 1)) == 0) y[row] = sub ? sub[row] + sign * (double)v : (double)v;
+}
+
+__global__ void k_to_f32(const double* in, float* out, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
+}
+
+inline unsigned nblk(int64_t n, int bs) { return (unsigned)std::max<int64_t>(1, (n + bs - 1) / bs); }
+
+int tpr_for(double avg_nnz) {
+    int S = 1;
+    while (S < 32 && S * 6 < avg_nnz) S <<= 1;
+    return S;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+
+static ms_status ensure_workspace(ms_hierarchy* h) {
+    if (h->f) return MS_OK;
+    const int64_t N = h->N;
+    MS_TRY(ms_alloc(h, (void**)&h->f, sizeof(double) * N));
+    MS_TRY(ms_alloc(h, (void**)&h->beta, sizeof(double) * N));
+    MS_TRY(ms_alloc(h, (void**)&h->x, sizeof(double) * N));
+    MS_TRY(ms_alloc(h, (void**)&h->r, sizeof(double) * N));
+    MS_TRY(ms_alloc(h, (void**)&h->p, sizeof(double) * N));
+    MS_TRY(ms_alloc(h, (void**)&h->q, sizeof(double) * N));
+    MS_TRY(ms_alloc(h, (void**)&h->tmp64, sizeof(double) * N));
+    if (h->opts.precision == MS_PREC_MIXED) {
+        MS_TRY(ms_alloc(h, (void**)&h->x32, sizeof(float) * N));
+        MS_TRY(ms_alloc(h, (void**)&h->r32, sizeof(float) * N));
+        MS_TRY(ms_alloc(h, (void**)&h->p32, sizeof(float) * N));
+        MS_TRY(ms_alloc(h, (void**)&h->q32, sizeof(float) * N));
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    MS_CUDA(cudaGetDevice(&dev));
+    MS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (h->opts.precision == MS_PREC_MIXED)
+        MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fit<1>, kBS, 0));
+    else
+        MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fit<0>, kBS, 0));
+    if (per_sm < 1) {
+        ms_set_error(MS_ERR_CUDA, "solve kernel cannot be resident on an SM");
+        return MS_ERR_CUDA;
+    }
+    h->solve_blocks = sms * std::min(per_sm, 2);
+    MS_TRY(ms_alloc(h, (void**)&h->part, sizeof(double) * kAcc * MS_MAXL * h->solve_blocks));
+    MS_TRY(ms_alloc(h, (void**)&h->bar, sizeof(unsigned) * 2));
+    MS_TRY(ms_alloc(h, (void**)&h->status, sizeof(int)));
+    MS_TRY(ms_alloc(h, (void**)&h->iters, sizeof(int64_t) * MS_MAXL));
+    MS_TRY(ms_alloc(h, (void**)&h->refines, sizeof(int) * MS_MAXL));
+    MS_TRY(ms_alloc(h, (void**)&h->resid, sizeof(double) * MS_MAXL));
+    MS_TRY(ms_alloc(h, (void**)&h->bytes, sizeof(double)));
+    return MS_OK;
+}
+
+static void level_tpr(ms_hierarchy* h, const std::vector<int64_t>& rpA, const std::vector<int64_t>& rpB,
+                      SolveArgs& a) {
+    for (int l = 0; l < h->L; ++l) {
+        const int64_t n = h->view.off[l + 1] - h->view.off[l];
+        a.nnzA[l] = rpA[l + 1] - rpA[l];
+        a.nnzB[l] = rpB[l + 1] - rpB[l];
+        a.tprA[l] = h->opts.threads_per_row > 0 ? h->opts.threads_per_row : tpr_for((double)a.nnzA[l] / n);
+        a.tprB[l] = tpr_for((double)a.nnzB[l] / n);
+    }
+}
+
+ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel_tol, double* alpha_dev,
+                      ms_fit_stats* stats, cudaStream_t st) {
+    MS_TRY(ensure_workspace(h));
+    const int L = h->L;
+    const int64_t N = h->N;
+    // per-level nnz (row offsets at the level boundaries)
+    std::vector<int64_t> rpA(L + 1), rpB(L + 1);
+    for (int l = 0; l <= L; ++l) {
+        MS_CUDA(cudaMemcpyAsync(&rpA[l], h->A.rp + h->view.off[l], sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        MS_CUDA(cudaMemcpyAsync(&rpB[l], h->B.rp + h->view.off[l], sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    }
+    MS_CUDA(cudaStreamSynchronize(st));
+
+    SolveArgs a{};
+    a.L = L;
+    a.N = N;
+    int64_t c = 0;
+    for (int l = 0; l <= L; ++l) {
+        a.off[l] = h->view.off[l];
+        a.coff[l] = c;
+        if (l < L) c += (h->view.off[l + 1] - h->view.off[l] + kChunk - 1) / kChunk;
+    }
+    level_tpr(h, rpA, rpB, a);
+    a.Arp = h->A.rp; a.Acol = h->A.col; a.Av64 = h->A.v64; a.Av32 = h->A.v32;
+    a.Brp = h->B.rp; a.Bcol = h->B.col; a.Bv64 = h->B.v64;
+    a.f = h->f; a.beta = h->beta; a.x = h->x; a.r = h->r; a.p = h->p; a.q = h->q;
+    a.x32 = h->x32; a.r32 = h->r32; a.p32 = h->p32; a.q32 = h->q32;
+    a.part = h->part; a.bar = h->bar; a.status = h->status;
+    a.iters = h->iters; a.refines = h->refines; a.resid = h->resid; a.bytes = h->bytes;
+    a.sweeps = h->opts.jacobi_sweeps > 0 ? h->opts.jacobi_sweeps : std::max(L - 1, 0);
+    a.max_iters = h->opts.max_iters > 0 ? h->opts.max_iters : 20000;
+    a.max_outer = h->opts.precision == MS_PREC_MIXED ? 40 : 8;
+    a.tol = rel_tol;
+    a.inter_tol = h->opts.inter_tol > 0 ? std::max(h->opts.inter_tol, rel_tol) : std::max(1e-6, rel_tol);
+    a.inner_tol = h->opts.inner_tol > 0 ? h->opts.inner_tol : 1e-4;
+    a.timeout_ns = 4000000000ull;
+    const bool mixed = h->opts.precision == MS_PREC_MIXED;
+    if (mixed && !h->A.v32) {
+        ms_set_error(MS_ERR_STATE, "MIXED fit needs FP32 values (build with precision = MS_PREC_MIXED)");
+        return MS_ERR_STATE;
+    }
+
+    ms_status result = MS_OK;
+    int launches = 0;
+    float total_ms = 0.f;
+    double bytes = 0.0;
+    std::vector<int64_t> it(MS_MAXL, 0), it_sum(MS_MAXL, 0);
+    std::vector<int> ref(MS_MAXL, 0);
+    std::vector<double> res(MS_MAXL, 0.0);
+    int dstat = 0;
+    for (int col = 0; col < nrhs; ++col) {
+        ms_gather_sorted(f_dev, h->f, h->perm, N, nrhs, col, st);
+        ++launches;
+        MS_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * 2, st));
+        MS_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+        MS_CUDA(cudaMemsetAsync(h->resid, 0, sizeof(double) * MS_MAXL, st));
+        void* args[] = {&a};
+        MS_CUDA(cudaEventRecord(h->ev0, st));
+        if (mixed)
+            MS_CUDA(cudaLaunchCooperativeKernel((void*)k_fit<1>, dim3(h->solve_blocks), dim3(kBS), args, 0, st));
+        else
+            MS_CUDA(cudaLaunchCooperativeKernel((void*)k_fit<0>, dim3(h->solve_blocks), dim3(kBS), args, 0, st));
+        ms_count_launch();
+        MS_CUDA(cudaEventRecord(h->ev1, st));
+        ++launches;
+        ms_scatter_input(h->x, alpha_dev, h->perm, N, nrhs, col, st);
+        ++launches;
+        MS_CUDA(cudaGetLastError());
+        double b = 0.0;
+        MS_CUDA(cudaMemcpyAsync(&dstat, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MS_CUDA(cudaMemcpyAsync(it.data(), h->iters, sizeof(int64_t) * MS_MAXL, cudaMemcpyDeviceToHost, st));
+        MS_CUDA(cudaMemcpyAsync(ref.data(), h->refines, sizeof(int) * MS_MAXL, cudaMemcpyDeviceToHost, st));
+        MS_CUDA(cudaMemcpyAsync(res.data(), h->resid, sizeof(double) * MS_MAXL, cudaMemcpyDeviceToHost, st));
+        MS_CUDA(cudaMemcpyAsync(&b, h->bytes, sizeof(double), cudaMemcpyDeviceToHost, st));
+        MS_CUDA(cudaStreamSynchronize(st));
+        float ms = 0.f;
+        MS_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        total_ms += ms;
+        bytes += b;
+        for (int l = 0; l < L; ++l) it_sum[l] += it[l];
+        if (dstat != 0 && result == MS_OK) {
+            result = (ms_status)dstat;
+            ms_set_error(result, "device status %d during the fit of right-hand side %d", dstat, col);
+        }
+    }
+    if (stats) {
+        *stats = ms_fit_stats{};
+        stats->L = L;
+        stats->sweeps = a.sweeps;
+        for (int l = 0; l < L; ++l) {
+            stats->cg_iterations[l] = it_sum[l];
+            stats->refinements[l] = ref[l];
+            stats->rel_residual[l] = res[l];
+        }
+        stats->device_status = dstat;
+        stats->fit_ms = total_ms;
+        stats->matvec_bytes = bytes;
+        stats->kernel_launches = launches;
+    }
+    return result;
+}
+
+ms_status ms_apply_impl(ms_hierarchy* h, int op, const double* x_dev, double* y_dev, int sorted, cudaStream_t st) {
+    MS_TRY(ensure_workspace(h));
+    const int64_t N = h->N;
+    const double* xs = x_dev;
+    double* ys = y_dev;
+    if (!sorted) {
+        ms_gather_sorted(x_dev, h->tmp64, h->perm, N, 1, 0, st);
+        xs = h->tmp64;
+        ys = h->q;
+    }
+    const DevCSR& M = (op == MS_APPLY_A64 || op == MS_APPLY_A32 || op == MS_APPLY_AMF32) ? h->A : h->B;
+    const double avg = (double)M.nnz / (double)std::max<int64_t>(N, 1);
+    const int S = (op <= MS_APPLY_AMF32 && h->opts.threads_per_row > 0) ? h->opts.threads_per_row : tpr_for(avg);
+    const unsigned blocks = nblk(N * (int64_t)S, 256);
+    switch (op) {
+    case MS_APPLY_A64:
+    case MS_APPLY_B64:
+        k_spmv<double, double, double><<<blocks, 256, 0, st>>>(M.rp, M.col, M.v64, xs, ys, N, S, nullptr, 1.0); ms_count_launch();
+        break;
+    case MS_APPLY_A32:
+    case MS_APPLY_B32: {
+        if (!M.v32) {
+            ms_set_error(MS_ERR_ARG, "FP32 values were not built (build with precision = MS_PREC_MIXED)");
+            return MS_ERR_ARG;
+        }
+        float* x32 = reinterpret_cast<float*>(h->r);  // scratch: N floats fit in an N-double buffer
+        k_to_f32<<<nblk(N, 256), 256, 0, st>>>(xs, x32, N); ms_count_launch();
+        k_spmv<float, float, float><<<blocks, 256, 0, st>>>(M.rp, M.col, M.v32, x32, ys, N, S, nullptr, 1.0); ms_count_launch();
+        break;
+    }
+    default:
+        ms_set_error(MS_ERR_ARG, "operator %d is not available", op);
+        return MS_ERR_ARG;
+    }
+    MS_CUDA(cudaGetLastError());
+    if (!sorted) ms_scatter_input(ys, y_dev, h->perm, N, 1, 0, st);
+    MS_CUDA(cudaGetLastError());
+    return MS_OK;
+}

@@ -145,7 +145,9 @@ def test_fit_fp64_halton_phi22_nu8():
 def test_fit_d3_random_and_d1():
     w3 = inputs.random3d_hierarchy(L=3, n_gauss=5)
     check_fit(w3, ms.MS_PREC_FP64, 1e-9)
-    pts = [np.sort(inputs.uniform01(11 + l, n))[:, None] for l, n in enumerate([9, 33, 129])]
+    # jittered 1-D grids (quasi-uniform, so kappa(A_l) stays moderate)
+    pts = [((np.arange(n) + 0.25 + 0.5 * inputs.uniform01(11 + l, n)) / n)[:, None]
+           for l, n in enumerate([9, 33, 129])]
     g = inputs.GaussianMixture(3, 1, 5)
     w1 = inputs.Workload("d1", 1, pts, np.array([1 / 9, 1 / 33, 1 / 129]), 3.0, 1, 1, g(np.concatenate(pts)), g)
     check_fit(w1, ms.MS_PREC_FP64, 1e-10)

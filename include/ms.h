@@ -179,6 +179,37 @@ ms_status ms_fit_dev(ms_hierarchy* h, const double* f_dev, int nrhs, double rel_
                      double* alpha_dev, ms_fit_stats* stats, void* stream);
 
 /*
+ * Allocation-free fit.  The paper has no counterpart: this is a service for
+ * callers that cannot allocate device memory when they fit.  ms_fit_dev gives
+ * the handle a work space with cudaMalloc on its first call; callers whose
+ * device memory is already fully reserved by another allocator or pool, loops
+ * that must not call the allocator (cudaMalloc/cudaFree can synchronise the
+ * device), and processes with a device-memory budget fixed at start-up cannot
+ * allow that.  This entry point computes the same fit as ms_fit_dev for ONE
+ * right-hand side, but the call allocates nothing: its work space is a fixed
+ * device array of about 4.6 MiB inside libms.so, held by every GPU that loads
+ * the library until the process exits.
+ *   h          a built hierarchy with at most 65536 points in total
+ *              (larger ones are rejected with MS_ERR_ARG); its device must be current
+ *   f_dev      DEVICE float64 [N], input order
+ *   rel_tol    in (0, 1), as for ms_fit
+ *   alpha_dev  DEVICE float64 [N], input order (written)
+ *   stats      nullable
+ *   stream     cudaStream_t as void*; the call waits for the stream before returning
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture.  Every call shares the one array per device, which keeps the
+ * previous call's contents (the call clears what must start at zero): calls
+ * whose work overlaps on the GPU (other threads, other streams, other
+ * handles) race on it and must be serialised by the caller.
+ * Errors: MS_ERR_ARG, MS_ERR_STATE (wrong device current, FP32 values missing
+ * for MIXED), MS_ERR_NOT_SPD, MS_ERR_NOT_CONVERGED, MS_ERR_NUMERIC (non-finite
+ * f), MS_ERR_TIMEOUT, MS_ERR_CUDA.
+ */
+ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, double rel_tol, double* alpha_dev,
+                            ms_fit_stats* stats, void* stream);
+
+/*
  * Evaluate the approximant f_L(q) = sum_l sum_n alpha_n^(l) Phi_{delta_l}(q - x_n^(l))
  * (eq. fapproximation) at nq query points, FP64 throughout.
  *   alpha  host [N] or [N][nrhs], input order;  query host [nq][d];  out host [nq][nrhs].

@@ -696,3 +696,202 @@ ms_status ms_apply_impl(ms_hierarchy* h, int op, const double* x_dev, double* y_
     MS_CUDA(cudaGetLastError());
     return MS_OK;
 }
+
+// ---------------------------------------------------------------- allocation-free fit
+//
+// ms_fit_dev gives the handle a work space on its first call (cudaMalloc).
+// Some callers cannot allow that at fit time: applications whose device memory
+// is already fully reserved by another allocator or pool (a fresh cudaMalloc
+// would fail), latency-critical loops that must not call the allocator
+// (cudaMalloc and cudaFree can synchronise the device), and processes whose
+// device-memory budget is fixed at start-up.  ms_fit_static_dev serves them:
+// it runs the same solve kernel, with its work space (solve vectors, reduction
+// partials, barrier words, status and counters) in the fixed device array
+// below instead of memory the call allocates.  The array belongs to the loaded
+// module, so every GPU that loads libms.so holds it until the process exits.
+
+#include <mutex>
+
+namespace {
+
+constexpr int64_t kStaticMaxPoints = 65536;  // largest hierarchy (total points) the array serves
+constexpr int kStaticMaxBlocks = 1024;       // largest cooperative grid it serves
+constexpr size_t pad256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kStaticVec64 = pad256(sizeof(double) * kStaticMaxPoints);
+constexpr size_t kStaticVec32 = pad256(sizeof(float) * kStaticMaxPoints);
+constexpr size_t kStaticPart = pad256(sizeof(double) * kAcc * MS_MAXL * kStaticMaxBlocks);
+constexpr size_t kStaticSmall = 4096;  // barrier words, status, per-level counters, residuals, bytes
+constexpr size_t kStaticBytes = 6 * kStaticVec64 + 4 * kStaticVec32 + kStaticPart + kStaticSmall;  // ~4.6 MiB
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_fit_scratch[kStaticBytes];
+
+namespace {
+
+std::mutex g_scratch_mu;
+void* g_scratch_addr[256] = {};
+
+// Device address of g_fit_scratch on device `dev` (which must be current),
+// looked up once per device.  In host code the name g_fit_scratch is only a
+// host-side stand-in: it must never be handed to a kernel.
+ms_status fit_scratch_address(int dev, unsigned char** out) {
+    if (dev < 0 || dev >= 256) {
+        ms_set_error(MS_ERR_STATE, "device ordinal %d out of range", dev);
+        return MS_ERR_STATE;
+    }
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_fit_scratch);
+        if (e != cudaSuccess) return ms_cuda_error(e, "cudaGetSymbolAddress(g_fit_scratch)", __FILE__, __LINE__);
+        g_scratch_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+    return MS_OK;
+}
+
+}  // namespace
+
+extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, double rel_tol, double* alpha_dev,
+                                       ms_fit_stats* stats, void* stream) {
+    if (!h || !f_dev || !alpha_dev) {
+        ms_set_error(MS_ERR_ARG, "handle, f and alpha must not be NULL");
+        return MS_ERR_ARG;
+    }
+    if (!(rel_tol > 0.0 && rel_tol < 1.0)) {
+        ms_set_error(MS_ERR_ARG, "rel_tol must be in (0, 1) (got %g)", rel_tol);
+        return MS_ERR_ARG;
+    }
+    if (h->N > kStaticMaxPoints) {
+        ms_set_error(MS_ERR_ARG, "hierarchy has %lld points; the allocation-free fit serves at most %lld",
+                     (long long)h->N, (long long)kStaticMaxPoints);
+        return MS_ERR_ARG;
+    }
+    const bool mixed = h->opts.precision == MS_PREC_MIXED;
+    if (mixed && !h->A.v32) {
+        ms_set_error(MS_ERR_STATE, "MIXED fit needs FP32 values (build with precision = MS_PREC_MIXED)");
+        return MS_ERR_STATE;
+    }
+    int dev = 0;
+    MS_CUDA(cudaGetDevice(&dev));
+    if (dev != h->device) {
+        ms_set_error(MS_ERR_STATE, "the handle belongs to device %d but device %d is current", h->device, dev);
+        return MS_ERR_STATE;
+    }
+    unsigned char* base = nullptr;
+    MS_TRY(fit_scratch_address(dev, &base));
+    cudaStream_t st = (cudaStream_t)stream;
+
+    int sms = 0, per_sm = 0;
+    MS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (mixed)
+        MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fit<1>, kBS, 0));
+    else
+        MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fit<0>, kBS, 0));
+    if (per_sm < 1) {
+        ms_set_error(MS_ERR_CUDA, "solve kernel cannot be resident on an SM");
+        return MS_ERR_CUDA;
+    }
+    const int blocks = std::min(sms * std::min(per_sm, 2), kStaticMaxBlocks);
+
+    // carve the fixed array
+    unsigned char* c = base;
+    double* v64[6];
+    for (int i = 0; i < 6; ++i, c += kStaticVec64) v64[i] = reinterpret_cast<double*>(c);
+    float* v32[4];
+    for (int i = 0; i < 4; ++i, c += kStaticVec32) v32[i] = reinterpret_cast<float*>(c);
+    double* part = reinterpret_cast<double*>(c);
+    c += kStaticPart;
+    unsigned char* small = c;
+    unsigned* bar = reinterpret_cast<unsigned*>(small);                    // [2]
+    int* status = reinterpret_cast<int*>(small + 64);                      // [1]
+    int64_t* iters = reinterpret_cast<int64_t*>(small + 128);              // [MS_MAXL]
+    int* refines = reinterpret_cast<int*>(small + 128 + 8 * MS_MAXL);      // [MS_MAXL]
+    double* resid = reinterpret_cast<double*>(small + 128 + 12 * MS_MAXL); // [MS_MAXL]
+    double* bytes = reinterpret_cast<double*>(small + 128 + 20 * MS_MAXL); // [1]
+    // the array keeps the previous call's contents: clear what must start at zero
+    MS_CUDA(cudaMemsetAsync(small, 0, kStaticSmall, st));
+
+    const int L = h->L;
+    int64_t rpA[MS_MAXL + 1], rpB[MS_MAXL + 1];
+    for (int l = 0; l <= L; ++l) {
+        MS_CUDA(cudaMemcpyAsync(&rpA[l], h->A.rp + h->view.off[l], sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        MS_CUDA(cudaMemcpyAsync(&rpB[l], h->B.rp + h->view.off[l], sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    }
+    MS_CUDA(cudaStreamSynchronize(st));
+
+    SolveArgs a{};
+    a.L = L;
+    a.N = h->N;
+    int64_t ch = 0;
+    for (int l = 0; l <= L; ++l) {
+        a.off[l] = h->view.off[l];
+        a.coff[l] = ch;
+        if (l < L) ch += (h->view.off[l + 1] - h->view.off[l] + kChunk - 1) / kChunk;
+    }
+    for (int l = 0; l < L; ++l) {
+        const int64_t n = h->view.off[l + 1] - h->view.off[l];
+        a.nnzA[l] = rpA[l + 1] - rpA[l];
+        a.nnzB[l] = rpB[l + 1] - rpB[l];
+        a.tprA[l] = h->opts.threads_per_row > 0 ? h->opts.threads_per_row : tpr_for((double)a.nnzA[l] / n);
+        a.tprB[l] = tpr_for((double)a.nnzB[l] / n);
+    }
+    a.Arp = h->A.rp; a.Acol = h->A.col; a.Av64 = h->A.v64; a.Av32 = h->A.v32;
+    a.Brp = h->B.rp; a.Bcol = h->B.col; a.Bv64 = h->B.v64;
+    a.f = v64[0]; a.beta = v64[1]; a.x = v64[2]; a.r = v64[3]; a.p = v64[4]; a.q = v64[5];
+    a.x32 = v32[0]; a.r32 = v32[1]; a.p32 = v32[2]; a.q32 = v32[3];
+    a.part = part; a.bar = bar; a.status = status;
+    a.iters = iters; a.refines = refines; a.resid = resid; a.bytes = bytes;
+    a.sweeps = h->opts.jacobi_sweeps > 0 ? h->opts.jacobi_sweeps : std::max(L - 1, 0);
+    a.max_iters = h->opts.max_iters > 0 ? h->opts.max_iters : 20000;
+    a.max_outer = mixed ? 40 : 8;
+    a.tol = rel_tol;
+    a.inter_tol = h->opts.inter_tol > 0 ? std::max(h->opts.inter_tol, rel_tol) : std::max(1e-6, rel_tol);
+    a.inner_tol = h->opts.inner_tol > 0 ? h->opts.inner_tol : 1e-4;
+    a.timeout_ns = 4000000000ull;
+
+    ms_gather_sorted(f_dev, v64[0], h->perm, h->N, 1, 0, st);
+    void* args[] = {&a};
+    MS_CUDA(cudaEventRecord(h->ev0, st));
+    if (mixed)
+        MS_CUDA(cudaLaunchCooperativeKernel((void*)k_fit<1>, dim3(blocks), dim3(kBS), args, 0, st));
+    else
+        MS_CUDA(cudaLaunchCooperativeKernel((void*)k_fit<0>, dim3(blocks), dim3(kBS), args, 0, st));
+    ms_count_launch();
+    MS_CUDA(cudaEventRecord(h->ev1, st));
+    ms_scatter_input(a.x, alpha_dev, h->perm, h->N, 1, 0, st);
+    MS_CUDA(cudaGetLastError());
+
+    int dstat = 0;
+    int64_t it[MS_MAXL];
+    int ref[MS_MAXL];
+    double res[MS_MAXL], b = 0.0;
+    MS_CUDA(cudaMemcpyAsync(&dstat, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MS_CUDA(cudaMemcpyAsync(it, iters, sizeof(it), cudaMemcpyDeviceToHost, st));
+    MS_CUDA(cudaMemcpyAsync(ref, refines, sizeof(ref), cudaMemcpyDeviceToHost, st));
+    MS_CUDA(cudaMemcpyAsync(res, resid, sizeof(res), cudaMemcpyDeviceToHost, st));
+    MS_CUDA(cudaMemcpyAsync(&b, bytes, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MS_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    MS_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    if (stats) {
+        *stats = ms_fit_stats{};
+        stats->L = L;
+        stats->sweeps = a.sweeps;
+        for (int l = 0; l < L; ++l) {
+            stats->cg_iterations[l] = it[l];
+            stats->refinements[l] = ref[l];
+            stats->rel_residual[l] = res[l];
+        }
+        stats->device_status = dstat;
+        stats->fit_ms = ms;
+        stats->matvec_bytes = b;
+        stats->kernel_launches = 3;
+    }
+    if (dstat != 0) {
+        ms_set_error((ms_status)dstat, "device status %d during the allocation-free fit", dstat);
+        return (ms_status)dstat;
+    }
+    return MS_OK;
+}

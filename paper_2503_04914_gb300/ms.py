@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "MS_OK", 1: "MS_ERR_ARG", 2: "MS_ERR_CUDA", 3: "MS_ERR_OOM", 
 
 # the symbols include/ms.h declares (checked by the tests)
 EXPORTED = ["ms_default_opts", "ms_build_hierarchy", "ms_build_hierarchy_dev", "ms_fit", "ms_fit_dev",
-            "ms_evaluate", "ms_evaluate_dev", "ms_apply_dev", "ms_get_permutation", "ms_hierarchy_info",
+            "ms_fit_static_dev", "ms_evaluate", "ms_evaluate_dev", "ms_apply_dev", "ms_get_permutation", "ms_hierarchy_info",
             "ms_launch_count", "ms_last_error", "ms_destroy"]
 
 
@@ -92,6 +92,7 @@ def load(path: str | None = None):
     lib.ms_build_hierarchy_dev.argtypes = [C.c_int, C.c_int, _I64, _P, _D, C.POINTER(ms_opts), _P, C.POINTER(_P)]
     lib.ms_fit.argtypes = [_P, _D, C.c_int, C.c_double, _D, C.POINTER(ms_fit_stats)]
     lib.ms_fit_dev.argtypes = [_P, _P, C.c_int, C.c_double, _P, C.POINTER(ms_fit_stats), _P]
+    lib.ms_fit_static_dev.argtypes = [_P, _P, C.c_double, _P, C.POINTER(ms_fit_stats), _P]
     lib.ms_evaluate.argtypes = [_P, _D, C.c_int, _D, C.c_int64, _D]
     lib.ms_evaluate_dev.argtypes = [_P, _P, C.c_int, _P, C.c_int64, _P, _P]
     lib.ms_apply_dev.argtypes = [_P, C.c_int, _P, _P, C.c_int, _P]
@@ -181,6 +182,18 @@ def ms_fit(handle, f, rel_tol=1e-10, alpha_out=None, stream=None):
     out = np.empty_like(fa) if alpha_out is None else alpha_out
     _check(lib.ms_fit(C.c_void_p(handle), f_p, nrhs, rel_tol, out.ctypes.data_as(_D), C.byref(st)))
     return out, st.as_dict()
+
+
+def ms_fit_static_dev(handle, f, rel_tol=1e-10, alpha_out=None, stream=None):
+    """Allocation-free fit of one right-hand side (device tensors only); see include/ms.h.
+    The call itself allocates nothing; pass alpha_out to keep this wrapper allocation-free too."""
+    import torch
+    st = ms_fit_stats()
+    if alpha_out is None:
+        alpha_out = torch.empty_like(f)
+    _check(load().ms_fit_static_dev(C.c_void_p(handle), _dev_ptr(f), rel_tol, _dev_ptr(alpha_out), C.byref(st),
+                                    _stream(stream)))
+    return alpha_out, st.as_dict()
 
 
 def ms_evaluate(handle, alpha, query, out=None, stream=None):

@@ -272,9 +272,10 @@ struct ms_hierarchy {
     int32_t* cell_start = nullptr;
     DevCSR A, B;
     // solver work space (sorted order)
-    double *f = nullptr, *beta = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
-    float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    double *f = nullptr, *beta = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *s = nullptr;
+    float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *s32 = nullptr;
     double* part = nullptr;      // reduction partials
+    double* scal = nullptr;      // published grid sums
     unsigned* bar = nullptr;     // barrier words
     int* status = nullptr;       // device status
     int64_t* iters = nullptr;    // per-level iteration counters

@@ -7,7 +7,7 @@
 //
 // Sweep m (0-based) of the Jacobi iteration solves A_l t_l = beta_l for the
 // levels l = m..L-2 together (warm-started from the previous sweep; level m,
-// whose beta is final, to the requested tolerance, the others to the looser
+// whose beta is final, to the requested tolerance, the others to the
 // intermediate tolerance), then recomputes beta_k = f_k - sum_{j<k} B_kj t_j for
 // the rows of levels k = m+1..L-1.  Levels below m already hold their final t
 // (their beta cannot change any more) and are not re-solved; rows of levels
@@ -15,11 +15,15 @@
 // solve over all levels gives alpha_l = A_l^{-1} beta_l and certifies every
 // level's FP64 true residual.
 //
-// Level solves are CG with FP64 dots computed as deterministic two-stage
-// reductions (per-CTA partials, then a fixed-order sum that every CTA performs
-// identically, so every CTA takes the same convergence decisions without
-// further communication).  Stopping: |beta_l - A_l x| <= tol |beta_l| in FP64
-// (true residual, re-checked after the recursive residual converges).
+// Level solves: CG in the single-reduction form of Chronopoulos and Gear
+// (w = A r, then gamma = r.r and delta = r.w in one reduction; p = r + beta p,
+// s = w + beta s, x += alpha p, r -= alpha s), which is CG's recurrence with
+// one grid-wide reduction and two grid barriers per iteration.  FP64 dots are
+// reduced deterministically: per-CTA partials (a shared-memory block sum),
+// then the last CTA to arrive at the grid barrier adds the partials of every
+// CTA in a fixed order and publishes the sums, so all CTAs take the same
+// convergence decisions.  Stopping: |beta_l - A_l x| <= tol |beta_l| in FP64
+// (true residual, re-checked after the recursive residual has converged).
 //   FP64 mode : CG on FP64 vectors with the FP64 CSR values.
 //   MIXED mode: iterative refinement: outer FP64 true residual r = b - A x
 //               (FP64 CSR), inner CG on FP32 vectors with FP32 CSR values and
@@ -55,9 +59,10 @@ struct SolveArgs {
     const int32_t* Bcol;
     const double* Bv64;
     const double* f;
-    double *beta, *x, *r, *p, *q;
-    float *x32, *r32, *p32, *q32;
-    double* part;      // [kAcc][MS_MAXL][gridDim.x]
+    double *beta, *x, *r, *p, *q, *s;      // q holds w = A r
+    float *x32, *r32, *p32, *q32, *s32;
+    double* part;      // [kAcc][MS_MAXL][gridDim.x] per-CTA partial sums
+    double* scal;      // [kAcc][MS_MAXL] grid sums published by the last CTA of a barrier
     unsigned* bar;     // [0] arrival count, [1] generation
     int* status;
     int64_t* iters;    // [MS_MAXL]
@@ -71,17 +76,20 @@ struct SolveArgs {
 
 // Per-CTA shared state of the solve (identical in every CTA).
 struct Shared {
-    double red[kNW];
+    double red[kAcc][kBS];
     double acc[kAcc][MS_MAXL];
     double out[kAcc][MS_MAXL];
     double rr[MS_MAXL], bb[MS_MAXL], alpha[MS_MAXL], beta[MS_MAXL], tol[MS_MAXL], scale[MS_MAXL],
-        target[MS_MAXL];
-    int act[MS_MAXL], oact[MS_MAXL], zero[MS_MAXL];
+        target[MS_MAXL], gam[MS_MAXL];
+    int act[MS_MAXL], oact[MS_MAXL], zero[MS_MAXL], first[MS_MAXL];
     int it_solve[MS_MAXL];
     long long it_total[MS_MAXL];
     int refines[MS_MAXL];
     double bytes;
     int any;
+    int last;
+    int ok;
+    unsigned mine;
 };
 
 // y = sum_k val[k] * x[col[k]] over one CSR row, by a sub-warp of S lanes
@@ -102,13 +110,37 @@ __device__ __forceinline__ int level_of_chunk(const SolveArgs& a, int64_t c) {
     return l;
 }
 
+// Add the block's thread-local accumulators into sh.acc[k][cur]: values are
+// staged in shared memory and summed by one warp per accumulator in a fixed
+// order (few FP64 instructions; deterministic).
+template <int K>
+__device__ __forceinline__ void flush_acc(Shared& sh, double* acc, int cur) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        sh.red[k][threadIdx.x] = acc[k];
+        acc[k] = 0.0;
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < K) {
+        double t = 0.0;
+#pragma unroll
+        for (int j = 0; j < kBS / 32; ++j) t += sh.red[w][lane + 32 * j];
+        t = warp_sum(t);
+        if (lane == 0) sh.acc[w][cur] += t;
+    }
+    __syncthreads();
+}
+
 // Run body(l, r0, r1, acc) over this CTA's chunks of levels [l0, l1) with sel(l) true;
-// thread-local accumulators are block-reduced into sh.acc[k][l] (fixed order),
-// and the per-CTA sums are written to the partials array.
+// thread-local accumulators are block-reduced into sh.acc[k][l] and the per-CTA
+// sums are written to the partials array.
 template <int K, typename Sel, typename Body>
 __device__ __forceinline__ void run_phase(const SolveArgs& a, Shared& sh, int l0, int l1, Sel sel, Body body) {
-    for (int i = threadIdx.x; i < kAcc * MS_MAXL; i += kBS) (&sh.acc[0][0])[i] = 0.0;
-    __syncthreads();
+    if (K > 0) {
+        for (int i = threadIdx.x; i < kAcc * MS_MAXL; i += kBS) (&sh.acc[0][0])[i] = 0.0;
+        __syncthreads();
+    }
     double acc[K > 0 ? K : 1];
 #pragma unroll
     for (int k = 0; k < (K > 0 ? K : 1); ++k) acc[k] = 0.0;
@@ -118,14 +150,7 @@ __device__ __forceinline__ void run_phase(const SolveArgs& a, Shared& sh, int l0
         const int l = level_of_chunk(a, c);
         if (!sel(l)) continue;
         if (K > 0 && l != cur) {
-            if (cur >= 0) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const double t = block_sum<kBS>(acc[k], sh.red);
-                    if (threadIdx.x == 0) sh.acc[k][cur] += t;
-                    acc[k] = 0.0;
-                }
-            }
+            if (cur >= 0) flush_acc<K>(sh, acc, cur);
             cur = l;
         }
         const int64_t r0 = a.off[l] + (c - a.coff[l]) * kChunk;
@@ -133,14 +158,7 @@ __device__ __forceinline__ void run_phase(const SolveArgs& a, Shared& sh, int l0
         body(l, r0, r1, acc);
     }
     if (K > 0) {
-        if (cur >= 0) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const double t = block_sum<kBS>(acc[k], sh.red);
-                if (threadIdx.x == 0) sh.acc[k][cur] += t;
-            }
-        }
-        __syncthreads();
+        if (cur >= 0) flush_acc<K>(sh, acc, cur);
         const int nl = l1 - l0;
         for (int i = threadIdx.x; i < K * nl; i += kBS) {
             const int k = i / nl, l = l0 + i % nl;
@@ -149,24 +167,78 @@ __device__ __forceinline__ void run_phase(const SolveArgs& a, Shared& sh, int l0
     }
 }
 
-// sh.out[k][l] = sum over CTAs of the partials (same fixed order in every CTA).
+// Grid barrier; with K > 0 the last CTA to arrive also sums the per-CTA partials
+// of levels [l0, l1) (fixed order) into a.scal before releasing the others, and
+// every CTA then copies the sums into sh.out.  Bounded like grid_barrier().
 template <int K>
-__device__ __forceinline__ void reduce_partials(const SolveArgs& a, Shared& sh, int l0, int l1) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nl = l1 - l0;
-    for (int i = w; i < K * nl; i += kNW) {
-        const int k = i / nl, l = l0 + i % nl;
-        const double* src = a.part + ((size_t)k * MS_MAXL + l) * gridDim.x;
-        double s = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(src + b);
-        s = warp_sum(s);
-        if (lane == 0) sh.out[k][l] = s;
+__device__ bool gsync_reduce(const SolveArgs& a, Shared& sh, int l0, int l1) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(a.bar[1]);
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(a.bar[0]);
+        sh.mine = g.load(cuda::memory_order_relaxed);
+        const unsigned arrived = c.fetch_add(1u, cuda::memory_order_acq_rel);
+        sh.last = (arrived == gridDim.x - 1);
     }
     __syncthreads();
+    int ok = 1;
+    if (sh.last) {
+        if (K > 0) {
+            const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nl = l1 - l0;
+            for (int i = w; i < K * nl; i += kNW) {
+                const int k = i / nl, l = l0 + i % nl;
+                const double* src = a.part + ((size_t)k * MS_MAXL + l) * gridDim.x;
+                double s = 0.0;
+                for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(src + b);
+                s = warp_sum(s);
+                if (lane == 0) __stcg(a.scal + k * MS_MAXL + l, s);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(a.bar[1]);
+            cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(a.bar[0]);
+            c.store(0u, cuda::memory_order_relaxed);
+            g.store(sh.mine + 1u, cuda::memory_order_release);
+        }
+    } else if (threadIdx.x == 0) {
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(a.bar[1]);
+        cuda::atomic_ref<int, cuda::thread_scope_device> st(*a.status);
+        const unsigned long long t0 = ms_globaltimer();
+        unsigned spins = 0;
+        while (g.load(cuda::memory_order_acquire) == sh.mine) {
+            if ((++spins & 255u) == 0u) {
+                if (st.load(cuda::memory_order_relaxed) == MS_ERR_TIMEOUT) { ok = 0; break; }
+                if (ms_globaltimer() - t0 > a.timeout_ns) {
+                    int expect = 0;
+                    st.compare_exchange_strong(expect, (int)MS_ERR_TIMEOUT, cuda::memory_order_relaxed);
+                    if (expect != 0) st.store((int)MS_ERR_TIMEOUT, cuda::memory_order_relaxed);
+                    ok = 0;
+                    break;
+                }
+            }
+            __nanosleep(32);
+        }
+    }
+    if (threadIdx.x == 0) {
+        cuda::atomic_ref<int, cuda::thread_scope_device> st(*a.status);
+        if (st.load(cuda::memory_order_relaxed) == MS_ERR_TIMEOUT) ok = 0;
+        sh.ok = ok;  // a separate flag: sh.last may still be read by warps that lag behind
+    }
+    __syncthreads();
+    if (!sh.ok) return false;
+    if (K > 0) {
+        const int nl = l1 - l0;
+        for (int i = threadIdx.x; i < K * nl; i += kBS) {
+            const int k = i / nl, l = l0 + i % nl;
+            sh.out[k][l] = __ldcg(a.scal + k * MS_MAXL + l);
+        }
+        __syncthreads();
+    }
+    return true;
 }
 
-__device__ __forceinline__ bool gsync(const SolveArgs& a) {
-    return grid_barrier(&a.bar[0], &a.bar[1], gridDim.x, a.status, a.timeout_ns);
-}
+__device__ __forceinline__ bool gsync(const SolveArgs& a, Shared& sh) { return gsync_reduce<0>(a, sh, 0, 0); }
 
 // Rows [r0, r1) of a chunk, one sub-warp of S lanes per row; fn(row, valid, sl).
 template <typename Fn>
@@ -195,9 +267,9 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
         sh.tol[l] = (tight_all || l == l0) ? a.tol : a.inter_tol;
     }
     __syncthreads();
-    bool first = true;
+    bool first_outer = true;
     for (int outer = 0; outer < a.max_outer; ++outer) {
-        // ---- P1: FP64 true residual r = b - A x  (FP64 mode also sets p = r)
+        // ---- P1: FP64 true residual r = b - A x (FP64 CSR)
         run_phase<2>(a, sh, l0, l1, [&](int l) { return sh.oact[l] != 0; },
                      [&](int l, int64_t r0, int64_t r1, double* acc) {
                          const int S = a.tprA[l];
@@ -209,22 +281,20 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                                  const double b = a.beta[row];
                                  const double ri = b - y;
                                  a.r[row] = ri;
-                                 if (MODE == 0) a.p[row] = ri;
                                  acc[0] += ri * ri;
                                  acc[1] += b * b;
                              }
                          });
                      });
-        if (!gsync(a)) return false;
-        reduce_partials<2>(a, sh, l0, l1);
+        if (!gsync_reduce<2>(a, sh, l0, l1)) return false;
         if (tid == 0) {
             sh.any = 0;
             for (int l = l0; l < l1; ++l) {
                 if (!sh.oact[l]) continue;
                 const double rr = sh.out[0][l];
-                if (first) sh.bb[l] = sh.out[1][l];
+                if (first_outer) sh.bb[l] = sh.out[1][l];
                 const double bb = sh.bb[l];
-                sh.bytes += (double)a.nnzA[l] * 12.0 + (double)(a.off[l + 1] - a.off[l]) * (MODE == 0 ? 48.0 : 40.0);
+                sh.bytes += (double)a.nnzA[l] * 12.0 + (double)(a.off[l + 1] - a.off[l]) * 32.0;
                 if (!isfinite(rr) || !isfinite(bb)) {
                     sh.oact[l] = 0;
                     if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)MS_ERR_NUMERIC);
@@ -250,8 +320,8 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                 sh.any = 1;
                 sh.refines[l] += 1;
                 sh.act[l] = 1;
+                sh.first[l] = 1;
                 if (MODE == 0) {
-                    sh.rr[l] = rr;
                     // recursive-residual target, with margin below the true-residual tolerance
                     sh.target[l] = 0.25 * sh.tol[l] * sh.tol[l] * bb;
                 } else {
@@ -263,8 +333,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
             }
         }
         __syncthreads();
-        first = false;
-        // zero right-hand sides: x = 0 on those levels
+        first_outer = false;
         {
             bool anyzero = false;
             for (int l = l0; l < l1; ++l) anyzero |= sh.zero[l] != 0;
@@ -274,7 +343,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                                  for (int64_t row = r0 + tid; row < r1; row += kBS) a.x[row] = 0.0;
                              });
                 // other CTAs read these rows in the next phases
-                if (!gsync(a)) return false;
+                if (!gsync(a, sh)) return false;
                 for (int l = tid; l < MS_MAXL; l += kBS) sh.zero[l] = 0;
                 __syncthreads();
             }
@@ -282,121 +351,122 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
         if (!sh.any) break;
 
         if (MODE == 1) {
-            // ---- P2: r32 = r / |r|, p32 = r32, x32 = 0; rr of the FP32 vector in FP64
-            run_phase<1>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
-                         [&](int l, int64_t r0, int64_t r1, double* acc) {
+            // ---- P2: r32 = r / |r|, x32 = 0
+            run_phase<0>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
+                         [&](int l, int64_t r0, int64_t r1, double*) {
                              const double sc = sh.scale[l];
                              for (int64_t row = r0 + tid; row < r1; row += kBS) {
-                                 const float v = (float)(a.r[row] * sc);
-                                 a.r32[row] = v;
-                                 a.p32[row] = v;
+                                 a.r32[row] = (float)(a.r[row] * sc);
                                  a.x32[row] = 0.f;
-                                 acc[0] += (double)v * (double)v;
                              }
                          });
-            if (!gsync(a)) return false;
-            reduce_partials<1>(a, sh, l0, l1);
             if (tid == 0)
                 for (int l = l0; l < l1; ++l)
-                    if (sh.act[l]) sh.rr[l] = sh.out[0][l];
-            __syncthreads();
+                    if (sh.act[l]) sh.bytes += (double)(a.off[l + 1] - a.off[l]) * 16.0;
+            if (!gsync(a, sh)) return false;
         }
 
-        // ---- inner CG iterations
+        // ---- inner CG iterations (single-reduction form)
         for (;;) {
-            // PA: q = A p, pq
-            run_phase<1>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
+            // M: w = A r; gamma = r.r, delta = r.w
+            run_phase<2>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
                          [&](int l, int64_t r0, int64_t r1, double* acc) {
                              const int S = a.tprA[l];
                              rows_by_subwarp(r0, r1, S, [&](int64_t row, bool ok, int sl) {
                                  int64_t s = 0, e = 0;
                                  if (ok) { s = a.Arp[row]; e = a.Arp[row + 1]; }
                                  if (MODE == 0) {
-                                     const double y = csr_row<double, double, double>(a.Acol, a.Av64, a.p, s, e, sl, S);
-                                     if (ok && sl == 0) { a.q[row] = y; acc[0] += a.p[row] * y; }
+                                     const double y = csr_row<double, double, double>(a.Acol, a.Av64, a.r, s, e, sl, S);
+                                     if (ok && sl == 0) {
+                                         const double ri = a.r[row];
+                                         a.q[row] = y;
+                                         acc[0] += ri * ri;
+                                         acc[1] += ri * y;
+                                     }
                                  } else {
-                                     const float y = csr_row<float, float, float>(a.Acol, a.Av32, a.p32, s, e, sl, S);
-                                     if (ok && sl == 0) { a.q32[row] = y; acc[0] += (double)a.p32[row] * (double)y; }
+                                     const float y = csr_row<float, float, float>(a.Acol, a.Av32, a.r32, s, e, sl, S);
+                                     if (ok && sl == 0) {
+                                         const float ri = a.r32[row];
+                                         a.q32[row] = y;
+                                         acc[0] += (double)(ri * ri);
+                                         acc[1] += (double)ri * (double)y;
+                                     }
                                  }
                              });
                          });
-            if (!gsync(a)) return false;
-            reduce_partials<1>(a, sh, l0, l1);
-            if (tid == 0) {
-                for (int l = l0; l < l1; ++l) {
-                    if (!sh.act[l]) continue;
-                    const double pq = sh.out[0][l];
-                    sh.bytes += (double)a.nnzA[l] * (MODE == 0 ? 12.0 : 8.0) +
-                                (double)(a.off[l + 1] - a.off[l]) * (MODE == 0 ? 32.0 : 20.0);
-                    if (!(pq > 0.0) || !isfinite(pq)) {
-                        sh.act[l] = 0;
-                        sh.oact[l] = 0;
-                        if (blockIdx.x == 0) atomicCAS(a.status, 0, isfinite(pq) ? (int)MS_ERR_NOT_SPD : (int)MS_ERR_NUMERIC);
-                        continue;
-                    }
-                    sh.alpha[l] = sh.rr[l] / pq;
-                }
-            }
-            __syncthreads();
-            // PB: x += alpha p, r -= alpha q, rr
-            run_phase<1>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
-                         [&](int l, int64_t r0, int64_t r1, double* acc) {
-                             const double al = sh.alpha[l];
-                             for (int64_t row = r0 + tid; row < r1; row += kBS) {
-                                 if (MODE == 0) {
-                                     a.x[row] += al * a.p[row];
-                                     const double rv = a.r[row] - al * a.q[row];
-                                     a.r[row] = rv;
-                                     acc[0] += rv * rv;
-                                 } else {
-                                     const float af = (float)al;
-                                     a.x32[row] = fmaf(af, a.p32[row], a.x32[row]);
-                                     const float rv = fmaf(-af, a.q32[row], a.r32[row]);
-                                     a.r32[row] = rv;
-                                     acc[0] += (double)rv * (double)rv;
-                                 }
-                             }
-                         });
-            if (!gsync(a)) return false;
-            reduce_partials<1>(a, sh, l0, l1);
+            if (!gsync_reduce<2>(a, sh, l0, l1)) return false;
             if (tid == 0) {
                 sh.any = 0;
                 for (int l = l0; l < l1; ++l) {
                     if (!sh.act[l]) continue;
-                    const double rn = sh.out[0][l];
-                    sh.bytes += (double)(a.off[l + 1] - a.off[l]) * (MODE == 0 ? 48.0 : 24.0);
-                    sh.beta[l] = rn / sh.rr[l];
-                    sh.rr[l] = rn;
-                    sh.it_solve[l] += 1;
-                    sh.it_total[l] += 1;
-                    if (!isfinite(rn)) {
+                    const double gam = sh.out[0][l], del = sh.out[1][l];
+                    sh.bytes += (double)a.nnzA[l] * (MODE == 0 ? 12.0 : 8.0) +
+                                (double)(a.off[l + 1] - a.off[l]) * (MODE == 0 ? 32.0 : 20.0);
+                    if (!isfinite(gam) || !isfinite(del)) {
                         sh.act[l] = 0;
                         sh.oact[l] = 0;
                         if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)MS_ERR_NUMERIC);
                         continue;
                     }
-                    if (rn <= sh.target[l] || sh.it_solve[l] >= a.max_iters) {
-                        sh.act[l] = 0;
+                    if (gam <= sh.target[l] || sh.it_solve[l] >= a.max_iters) {
+                        sh.act[l] = 0;  // converged (recursive residual) or capped
                         continue;
                     }
+                    double al, be;
+                    if (sh.first[l]) {
+                        be = 0.0;
+                        al = del > 0.0 ? gam / del : -1.0;
+                    } else {
+                        be = gam / sh.gam[l];
+                        const double den = del - be * gam / sh.alpha[l];
+                        al = den > 0.0 ? gam / den : -1.0;
+                    }
+                    if (!(al > 0.0)) {  // p^T A p <= 0: A_l is not positive definite in floating point
+                        sh.act[l] = 0;
+                        sh.oact[l] = 0;
+                        if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)MS_ERR_NOT_SPD);
+                        continue;
+                    }
+                    sh.first[l] = 0;
+                    sh.alpha[l] = al;
+                    sh.beta[l] = be;
+                    sh.gam[l] = gam;
+                    sh.it_solve[l] += 1;
+                    sh.it_total[l] += 1;
+                    sh.bytes += (double)(a.off[l + 1] - a.off[l]) * (MODE == 0 ? 72.0 : 36.0);
                     sh.any = 1;
                 }
             }
             __syncthreads();
             if (!sh.any) break;
-            // PC: p = r + beta p
+            // E: p = r + beta p; s = w + beta s; x += alpha p; r -= alpha s
             run_phase<0>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
                          [&](int l, int64_t r0, int64_t r1, double*) {
-                             const double be = sh.beta[l];
-                             for (int64_t row = r0 + tid; row < r1; row += kBS) {
-                                 if (MODE == 0) a.p[row] = a.r[row] + be * a.p[row];
-                                 else a.p32[row] = fmaf((float)be, a.p32[row], a.r32[row]);
+                             const double al = sh.alpha[l], be = sh.beta[l];
+                             if (MODE == 0) {
+                                 for (int64_t row = r0 + tid; row < r1; row += kBS) {
+                                     const double ri = a.r[row];
+                                     const double pi = ri + be * a.p[row];
+                                     const double si = a.q[row] + be * a.s[row];
+                                     a.p[row] = pi;
+                                     a.s[row] = si;
+                                     a.x[row] += al * pi;
+                                     a.r[row] = ri - al * si;
+                                 }
+                             } else {
+                                 const float af = (float)al, bf = (float)be;
+                                 for (int64_t row = r0 + tid; row < r1; row += kBS) {
+                                     const float ri = a.r32[row];
+                                     const float pi = fmaf(bf, a.p32[row], ri);
+                                     const float si = fmaf(bf, a.s32[row], a.q32[row]);
+                                     a.p32[row] = pi;
+                                     a.s32[row] = si;
+                                     a.x32[row] = fmaf(af, pi, a.x32[row]);
+                                     a.r32[row] = fmaf(-af, si, ri);
+                                 }
                              }
                          });
-            if (tid == 0)
-                for (int l = l0; l < l1; ++l)
-                    if (sh.act[l]) sh.bytes += (double)(a.off[l + 1] - a.off[l]) * (MODE == 0 ? 24.0 : 12.0);
-            if (!gsync(a)) return false;
+            if (!gsync(a, sh)) return false;
         }
 
         if (MODE == 1) {
@@ -410,7 +480,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
             if (tid == 0)
                 for (int l = l0; l < l1; ++l)
                     if (sh.oact[l]) sh.bytes += (double)(a.off[l + 1] - a.off[l]) * 20.0;
-            if (!gsync(a)) return false;
+            if (!gsync(a, sh)) return false;
         }
     }
     // levels still active after max_outer rounds did not reach the tolerance
@@ -430,7 +500,10 @@ __global__ void __launch_bounds__(kBS) k_fit(SolveArgs a) {
         sh.refines[l] = 0;
         sh.scale[l] = 0.0;
     }
-    if (tid == 0) sh.bytes = 0.0;
+    if (tid == 0) {
+        sh.bytes = 0.0;
+        sh.any = 0;
+    }
     __syncthreads();
     const int L = a.L;
     // beta_0 = f, x = 0
@@ -440,7 +513,7 @@ __global__ void __launch_bounds__(kBS) k_fit(SolveArgs a) {
             a.x[row] = 0.0;
         }
     });
-    if (!gsync(a)) return;
+    if (!gsync(a, sh)) return;
     for (int m = 0; m < a.sweeps; ++m) {
         if (m <= L - 2) {
             if (!solve_levels<MODE>(a, sh, m, L - 1, false)) return;
@@ -460,7 +533,7 @@ __global__ void __launch_bounds__(kBS) k_fit(SolveArgs a) {
             if (tid == 0)
                 for (int l = m + 1; l < L; ++l)
                     sh.bytes += (double)a.nnzB[l] * 12.0 + (double)(a.off[l + 1] - a.off[l]) * 32.0;
-            if (!gsync(a)) return;
+            if (!gsync(a, sh)) return;
         }
     }
     if (!solve_levels<MODE>(a, sh, 0, L, true)) return;
@@ -496,10 +569,43 @@ __global__ void k_to_f32(const double* in, float* out, int64_t n) {
 
 inline unsigned nblk(int64_t n, int bs) { return (unsigned)std::max<int64_t>(1, (n + bs - 1) / bs); }
 
+// Sub-warp width for CSR rows of avg_nnz entries: about 16 entries per lane
+// keeps enough independent loads in flight per lane (measured on GB300: 4 lanes
+// for ~50-entry rows run 2.5x faster than 16).
 int tpr_for(double avg_nnz) {
     int S = 1;
-    while (S < 32 && S * 6 < avg_nnz) S <<= 1;
+    while (S < 32 && S * 16 < avg_nnz) S <<= 1;
     return S;
+}
+
+// Fill the solve arguments that depend only on the hierarchy and the options.
+void fill_args(const ms_hierarchy* h, const int64_t* rpA, const int64_t* rpB, double rel_tol, SolveArgs& a) {
+    const int L = h->L;
+    a.L = L;
+    a.N = h->N;
+    int64_t c = 0;
+    for (int l = 0; l <= L; ++l) {
+        a.off[l] = h->view.off[l];
+        a.coff[l] = c;
+        if (l < L) c += (h->view.off[l + 1] - h->view.off[l] + kChunk - 1) / kChunk;
+    }
+    for (int l = 0; l < L; ++l) {
+        const int64_t n = h->view.off[l + 1] - h->view.off[l];
+        a.nnzA[l] = rpA[l + 1] - rpA[l];
+        a.nnzB[l] = rpB[l + 1] - rpB[l];
+        a.tprA[l] = h->opts.threads_per_row > 0 ? h->opts.threads_per_row : tpr_for((double)a.nnzA[l] / n);
+        a.tprB[l] = tpr_for((double)a.nnzB[l] / n);
+    }
+    a.Arp = h->A.rp; a.Acol = h->A.col; a.Av64 = h->A.v64; a.Av32 = h->A.v32;
+    a.Brp = h->B.rp; a.Bcol = h->B.col; a.Bv64 = h->B.v64;
+    const bool mixed = h->opts.precision == MS_PREC_MIXED;
+    a.sweeps = h->opts.jacobi_sweeps > 0 ? h->opts.jacobi_sweeps : std::max(L - 1, 0);
+    a.max_iters = h->opts.max_iters > 0 ? h->opts.max_iters : 20000;
+    a.max_outer = mixed ? 40 : 8;
+    a.tol = rel_tol;
+    a.inter_tol = h->opts.inter_tol > 0 ? std::max(h->opts.inter_tol, rel_tol) : std::max(1e-6, rel_tol);
+    a.inner_tol = h->opts.inner_tol > 0 ? h->opts.inner_tol : 1e-4;
+    a.timeout_ns = 4000000000ull;
 }
 
 }  // namespace
@@ -515,12 +621,14 @@ static ms_status ensure_workspace(ms_hierarchy* h) {
     MS_TRY(ms_alloc(h, (void**)&h->r, sizeof(double) * N));
     MS_TRY(ms_alloc(h, (void**)&h->p, sizeof(double) * N));
     MS_TRY(ms_alloc(h, (void**)&h->q, sizeof(double) * N));
-    MS_TRY(ms_alloc(h, (void**)&h->tmp64, sizeof(double) * N));
+    MS_TRY(ms_alloc(h, (void**)&h->s, sizeof(double) * N));
+    if (!h->tmp64) MS_TRY(ms_alloc(h, (void**)&h->tmp64, sizeof(double) * N));
     if (h->opts.precision == MS_PREC_MIXED) {
         MS_TRY(ms_alloc(h, (void**)&h->x32, sizeof(float) * N));
         MS_TRY(ms_alloc(h, (void**)&h->r32, sizeof(float) * N));
         MS_TRY(ms_alloc(h, (void**)&h->p32, sizeof(float) * N));
         MS_TRY(ms_alloc(h, (void**)&h->q32, sizeof(float) * N));
+        MS_TRY(ms_alloc(h, (void**)&h->s32, sizeof(float) * N));
     }
     int dev = 0, sms = 0, per_sm = 0;
     MS_CUDA(cudaGetDevice(&dev));
@@ -535,6 +643,7 @@ static ms_status ensure_workspace(ms_hierarchy* h) {
     }
     h->solve_blocks = sms * std::min(per_sm, 2);
     MS_TRY(ms_alloc(h, (void**)&h->part, sizeof(double) * kAcc * MS_MAXL * h->solve_blocks));
+    MS_TRY(ms_alloc(h, (void**)&h->scal, sizeof(double) * kAcc * MS_MAXL));
     MS_TRY(ms_alloc(h, (void**)&h->bar, sizeof(unsigned) * 2));
     MS_TRY(ms_alloc(h, (void**)&h->status, sizeof(int)));
     MS_TRY(ms_alloc(h, (void**)&h->iters, sizeof(int64_t) * MS_MAXL));
@@ -542,17 +651,6 @@ static ms_status ensure_workspace(ms_hierarchy* h) {
     MS_TRY(ms_alloc(h, (void**)&h->resid, sizeof(double) * MS_MAXL));
     MS_TRY(ms_alloc(h, (void**)&h->bytes, sizeof(double)));
     return MS_OK;
-}
-
-static void level_tpr(ms_hierarchy* h, const std::vector<int64_t>& rpA, const std::vector<int64_t>& rpB,
-                      SolveArgs& a) {
-    for (int l = 0; l < h->L; ++l) {
-        const int64_t n = h->view.off[l + 1] - h->view.off[l];
-        a.nnzA[l] = rpA[l + 1] - rpA[l];
-        a.nnzB[l] = rpB[l + 1] - rpB[l];
-        a.tprA[l] = h->opts.threads_per_row > 0 ? h->opts.threads_per_row : tpr_for((double)a.nnzA[l] / n);
-        a.tprB[l] = tpr_for((double)a.nnzB[l] / n);
-    }
 }
 
 ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel_tol, double* alpha_dev,
@@ -569,28 +667,11 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
     MS_CUDA(cudaStreamSynchronize(st));
 
     SolveArgs a{};
-    a.L = L;
-    a.N = N;
-    int64_t c = 0;
-    for (int l = 0; l <= L; ++l) {
-        a.off[l] = h->view.off[l];
-        a.coff[l] = c;
-        if (l < L) c += (h->view.off[l + 1] - h->view.off[l] + kChunk - 1) / kChunk;
-    }
-    level_tpr(h, rpA, rpB, a);
-    a.Arp = h->A.rp; a.Acol = h->A.col; a.Av64 = h->A.v64; a.Av32 = h->A.v32;
-    a.Brp = h->B.rp; a.Bcol = h->B.col; a.Bv64 = h->B.v64;
-    a.f = h->f; a.beta = h->beta; a.x = h->x; a.r = h->r; a.p = h->p; a.q = h->q;
-    a.x32 = h->x32; a.r32 = h->r32; a.p32 = h->p32; a.q32 = h->q32;
-    a.part = h->part; a.bar = h->bar; a.status = h->status;
+    fill_args(h, rpA.data(), rpB.data(), rel_tol, a);
+    a.f = h->f; a.beta = h->beta; a.x = h->x; a.r = h->r; a.p = h->p; a.q = h->q; a.s = h->s;
+    a.x32 = h->x32; a.r32 = h->r32; a.p32 = h->p32; a.q32 = h->q32; a.s32 = h->s32;
+    a.part = h->part; a.scal = h->scal; a.bar = h->bar; a.status = h->status;
     a.iters = h->iters; a.refines = h->refines; a.resid = h->resid; a.bytes = h->bytes;
-    a.sweeps = h->opts.jacobi_sweeps > 0 ? h->opts.jacobi_sweeps : std::max(L - 1, 0);
-    a.max_iters = h->opts.max_iters > 0 ? h->opts.max_iters : 20000;
-    a.max_outer = h->opts.precision == MS_PREC_MIXED ? 40 : 8;
-    a.tol = rel_tol;
-    a.inter_tol = h->opts.inter_tol > 0 ? std::max(h->opts.inter_tol, rel_tol) : std::max(1e-6, rel_tol);
-    a.inner_tol = h->opts.inner_tol > 0 ? h->opts.inner_tol : 1e-4;
-    a.timeout_ns = 4000000000ull;
     const bool mixed = h->opts.precision == MS_PREC_MIXED;
     if (mixed && !h->A.v32) {
         ms_set_error(MS_ERR_STATE, "MIXED fit needs FP32 values (build with precision = MS_PREC_MIXED)");
@@ -674,7 +755,8 @@ ms_status ms_apply_impl(ms_hierarchy* h, int op, const double* x_dev, double* y_
     switch (op) {
     case MS_APPLY_A64:
     case MS_APPLY_B64:
-        k_spmv<double, double, double><<<blocks, 256, 0, st>>>(M.rp, M.col, M.v64, xs, ys, N, S, nullptr, 1.0); ms_count_launch();
+        k_spmv<double, double, double><<<blocks, 256, 0, st>>>(M.rp, M.col, M.v64, xs, ys, N, S, nullptr, 1.0);
+        ms_count_launch();
         break;
     case MS_APPLY_A32:
     case MS_APPLY_B32: {
@@ -683,8 +765,10 @@ ms_status ms_apply_impl(ms_hierarchy* h, int op, const double* x_dev, double* y_
             return MS_ERR_ARG;
         }
         float* x32 = reinterpret_cast<float*>(h->r);  // scratch: N floats fit in an N-double buffer
-        k_to_f32<<<nblk(N, 256), 256, 0, st>>>(xs, x32, N); ms_count_launch();
-        k_spmv<float, float, float><<<blocks, 256, 0, st>>>(M.rp, M.col, M.v32, x32, ys, N, S, nullptr, 1.0); ms_count_launch();
+        k_to_f32<<<nblk(N, 256), 256, 0, st>>>(xs, x32, N);
+        ms_count_launch();
+        k_spmv<float, float, float><<<blocks, 256, 0, st>>>(M.rp, M.col, M.v32, x32, ys, N, S, nullptr, 1.0);
+        ms_count_launch();
         break;
     }
     default:
@@ -720,8 +804,8 @@ constexpr size_t pad256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t kStaticVec64 = pad256(sizeof(double) * kStaticMaxPoints);
 constexpr size_t kStaticVec32 = pad256(sizeof(float) * kStaticMaxPoints);
 constexpr size_t kStaticPart = pad256(sizeof(double) * kAcc * MS_MAXL * kStaticMaxBlocks);
-constexpr size_t kStaticSmall = 4096;  // barrier words, status, per-level counters, residuals, bytes
-constexpr size_t kStaticBytes = 6 * kStaticVec64 + 4 * kStaticVec32 + kStaticPart + kStaticSmall;  // ~4.6 MiB
+constexpr size_t kStaticSmall = 4096;  // barrier words, status, per-level counters, residuals, sums
+constexpr size_t kStaticBytes = 7 * kStaticVec64 + 5 * kStaticVec32 + kStaticPart + kStaticSmall;  // ~5.3 MiB
 
 }  // namespace
 
@@ -797,10 +881,10 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
 
     // carve the fixed array
     unsigned char* c = base;
-    double* v64[6];
-    for (int i = 0; i < 6; ++i, c += kStaticVec64) v64[i] = reinterpret_cast<double*>(c);
-    float* v32[4];
-    for (int i = 0; i < 4; ++i, c += kStaticVec32) v32[i] = reinterpret_cast<float*>(c);
+    double* v64[7];
+    for (int i = 0; i < 7; ++i, c += kStaticVec64) v64[i] = reinterpret_cast<double*>(c);
+    float* v32[5];
+    for (int i = 0; i < 5; ++i, c += kStaticVec32) v32[i] = reinterpret_cast<float*>(c);
     double* part = reinterpret_cast<double*>(c);
     c += kStaticPart;
     unsigned char* small = c;
@@ -810,6 +894,7 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
     int* refines = reinterpret_cast<int*>(small + 128 + 8 * MS_MAXL);      // [MS_MAXL]
     double* resid = reinterpret_cast<double*>(small + 128 + 12 * MS_MAXL); // [MS_MAXL]
     double* bytes = reinterpret_cast<double*>(small + 128 + 20 * MS_MAXL); // [1]
+    double* scal = reinterpret_cast<double*>(small + 1024);                // [kAcc][MS_MAXL]
     // the array keeps the previous call's contents: clear what must start at zero
     MS_CUDA(cudaMemsetAsync(small, 0, kStaticSmall, st));
 
@@ -822,34 +907,11 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
     MS_CUDA(cudaStreamSynchronize(st));
 
     SolveArgs a{};
-    a.L = L;
-    a.N = h->N;
-    int64_t ch = 0;
-    for (int l = 0; l <= L; ++l) {
-        a.off[l] = h->view.off[l];
-        a.coff[l] = ch;
-        if (l < L) ch += (h->view.off[l + 1] - h->view.off[l] + kChunk - 1) / kChunk;
-    }
-    for (int l = 0; l < L; ++l) {
-        const int64_t n = h->view.off[l + 1] - h->view.off[l];
-        a.nnzA[l] = rpA[l + 1] - rpA[l];
-        a.nnzB[l] = rpB[l + 1] - rpB[l];
-        a.tprA[l] = h->opts.threads_per_row > 0 ? h->opts.threads_per_row : tpr_for((double)a.nnzA[l] / n);
-        a.tprB[l] = tpr_for((double)a.nnzB[l] / n);
-    }
-    a.Arp = h->A.rp; a.Acol = h->A.col; a.Av64 = h->A.v64; a.Av32 = h->A.v32;
-    a.Brp = h->B.rp; a.Bcol = h->B.col; a.Bv64 = h->B.v64;
-    a.f = v64[0]; a.beta = v64[1]; a.x = v64[2]; a.r = v64[3]; a.p = v64[4]; a.q = v64[5];
-    a.x32 = v32[0]; a.r32 = v32[1]; a.p32 = v32[2]; a.q32 = v32[3];
-    a.part = part; a.bar = bar; a.status = status;
+    fill_args(h, rpA, rpB, rel_tol, a);
+    a.f = v64[0]; a.beta = v64[1]; a.x = v64[2]; a.r = v64[3]; a.p = v64[4]; a.q = v64[5]; a.s = v64[6];
+    a.x32 = v32[0]; a.r32 = v32[1]; a.p32 = v32[2]; a.q32 = v32[3]; a.s32 = v32[4];
+    a.part = part; a.scal = scal; a.bar = bar; a.status = status;
     a.iters = iters; a.refines = refines; a.resid = resid; a.bytes = bytes;
-    a.sweeps = h->opts.jacobi_sweeps > 0 ? h->opts.jacobi_sweeps : std::max(L - 1, 0);
-    a.max_iters = h->opts.max_iters > 0 ? h->opts.max_iters : 20000;
-    a.max_outer = mixed ? 40 : 8;
-    a.tol = rel_tol;
-    a.inter_tol = h->opts.inter_tol > 0 ? std::max(h->opts.inter_tol, rel_tol) : std::max(1e-6, rel_tol);
-    a.inner_tol = h->opts.inner_tol > 0 ? h->opts.inner_tol : 1e-4;
-    a.timeout_ns = 4000000000ull;
 
     ms_gather_sorted(f_dev, v64[0], h->perm, h->N, 1, 0, st);
     void* args[] = {&a};

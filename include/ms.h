@@ -87,11 +87,15 @@ typedef struct ms_opts {
     int max_iters;       /* cap on CG iterations per level and solve; 0 = 20000 */
     int jacobi_sweeps;   /* Jacobi sweeps on T'; 0 = L-1 (exact from beta_0 = f, Theorem 9) */
     double inter_tol;    /* relative tolerance of the non-final (intermediate) level solves
-                            inside the Jacobi sweeps; 0 = 1e-6 */
+                            inside the Jacobi sweeps.  0 = 1: a non-final level keeps its
+                            previous iterate (no CG iterations until its beta is final; the
+                            fastest schedule, same result).  inter_tol = rel_tol solves every
+                            level in every sweep as Algorithm 2 does. */
     double inner_tol;    /* MIXED: relative tolerance of each FP32 inner CG; 0 = 1e-4 */
     int cell_split;      /* neighbour-grid cell size = delta_l / cell_split (1 or 2); 0 = 1 */
-    int threads_per_row; /* CSR sub-warp width for A (1..32, power of 2); 0 = autotune */
-    int reserved[8];
+    int threads_per_row; /* CSR sub-warp width for A (1..32, power of 2); 0 = automatic */
+    int lower_fp32;      /* 1: also store FP32 values of the B blocks (for MS_APPLY_B32) */
+    int reserved[7];
 } ms_opts;
 
 /* Per-fit statistics (all levels 0-based, coarse to fine). */
@@ -109,6 +113,12 @@ typedef struct ms_fit_stats {
     double matvec_bytes;                 /* algorithmic bytes moved by the solve kernel
                                             (matrix + vector traffic of every phase) */
     int64_t kernel_launches;             /* library kernels launched by the call */
+    double phase_ms[8];                  /* device timeline of the solve kernel as seen by its
+                                            first CTA (%globaltimer): [0] FP64 true residuals,
+                                            [1] CG mat-vec + dots, [2] CG vector updates,
+                                            [3] grid-barrier waits (includes load imbalance),
+                                            [4] lower-block (Jacobi) updates, [5] other vector
+                                            phases, [6] scalar decisions, [7] unused */
 } ms_fit_stats;
 
 /* Sizes of a built hierarchy. */

@@ -98,6 +98,23 @@ __global__ void k_gather_points(const double* pts, const int32_t* perm, double* 
     for (int a = 0; a < d; ++a) X[a * N + s] = pts[i * d + a];
 }
 
+// Matrix-free geometry of each sorted point: its level-local Morton cell and its
+// offset from that cell's corner in units of delta_l (FP32).
+__global__ void k_mf_coords(HierView v, float* W, int32_t* cellid) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= v.N) return;
+    const int l = level_of_row(v.off, v.L, s);
+    const LevelGrid& g = v.grid[l];
+    const double inv_delta = 1.0 / v.delta[l];
+    int c[3] = {0, 0, 0};
+    for (int a = 0; a < v.d; ++a) {
+        const double x = v.X[a * v.N + s];
+        c[a] = min(max(cell_coord(g, a, x), 0), g.G[a] - 1);
+        W[a * v.N + s] = (float)((x - (g.lo[a] + (double)c[a] * g.cell)) * inv_delta);
+    }
+    cellid[s] = (int32_t)morton(v.d, c[0], c[1], c[2]);
+}
+
 // ---------------------------------------------------------------- scans
 
 constexpr int kScanBS = 256;
@@ -345,6 +362,10 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
     k_rank<<<nblk(N, 256), 256, 0, st>>>(key, h->cell_start, tmp, h->perm, N); ms_count_launch();
     k_gather_points<<<nblk(N, 256), 256, 0, st>>>(pts, h->perm, h->X, d, N); ms_count_launch();
     MS_CUDA(cudaGetLastError());
+    MS_TRY(ms_alloc(h, (void**)&h->W, sizeof(float) * d * N));
+    MS_TRY(ms_alloc(h, (void**)&h->cellid, sizeof(int32_t) * N));
+    k_mf_coords<<<nblk(N, 256), 256, 0, st>>>(v, h->W, h->cellid); ms_count_launch();
+    MS_CUDA(cudaGetLastError());
 
     // 3. CSR of A (diagonal blocks) and B (strictly lower blocks)
     int32_t *cntA, *cntB;
@@ -362,13 +383,15 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
     MS_CUDA(cudaStreamSynchronize(st));
     h->A.nnz = nnz[0];
     h->B.nnz = nnz[1];
-    const bool fp32 = h->opts.precision == MS_PREC_MIXED;
+    // FP32 CSR values serve the MIXED inner CG unless it runs matrix-free
+    const bool fp32 = h->opts.precision == MS_PREC_MIXED && h->opts.op != MS_OP_MATRIX_FREE;
     MS_TRY(ms_alloc(h, (void**)&h->A.col, sizeof(int32_t) * h->A.nnz));
     MS_TRY(ms_alloc(h, (void**)&h->A.v64, sizeof(double) * h->A.nnz));
     if (fp32) MS_TRY(ms_alloc(h, (void**)&h->A.v32, sizeof(float) * h->A.nnz));
     MS_TRY(ms_alloc(h, (void**)&h->B.col, sizeof(int32_t) * h->B.nnz));
     MS_TRY(ms_alloc(h, (void**)&h->B.v64, sizeof(double) * h->B.nnz));
-    if (fp32) MS_TRY(ms_alloc(h, (void**)&h->B.v32, sizeof(float) * h->B.nnz));
+    // the fit updates beta with FP64 B values only; FP32 B values serve MS_APPLY_B32 on request
+    if (h->opts.lower_fp32) MS_TRY(ms_alloc(h, (void**)&h->B.v32, sizeof(float) * h->B.nnz));
     k_csr_fill<<<nblk(N, 128), 128, 0, st>>>(v, h->A.rp, h->A.col, h->A.v64, h->A.v32, h->B.rp, h->B.col,
                                              h->B.v64, h->B.v32); ms_count_launch();
     MS_CUDA(cudaGetLastError());

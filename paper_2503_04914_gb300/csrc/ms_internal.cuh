@@ -270,12 +270,16 @@ struct ms_hierarchy {
     double* X = nullptr;         // [d][N] sorted
     int32_t* perm = nullptr;     // sorted -> input
     int32_t* cell_start = nullptr;
+    float* W = nullptr;          // [d][N] FP32 offsets from the own cell corner, in units of delta_l
+    int32_t* cellid = nullptr;   // [N] level-local Morton cell of each sorted point
+    int mf_tpp = 2;              // matrix-free lanes per target point
     DevCSR A, B;
     // solver work space (sorted order)
     double *f = nullptr, *beta = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *s = nullptr;
     float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *s32 = nullptr;
     double* part = nullptr;      // reduction partials
     double* scal = nullptr;      // published grid sums
+    unsigned long long* prof = nullptr;  // device timeline of the solve kernel
     unsigned* bar = nullptr;     // barrier words
     int* status = nullptr;       // device status
     int64_t* iters = nullptr;    // per-level iteration counters

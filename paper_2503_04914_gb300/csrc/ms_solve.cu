@@ -36,6 +36,7 @@
 #include <vector>
 
 #include "ms_internal.cuh"
+#include "ms_matfree.cuh"
 
 namespace {
 
@@ -43,6 +44,11 @@ constexpr int kBS = 512;     // threads per CTA of the solve kernel
 constexpr int kChunk = 256;  // rows per work chunk (chunks never straddle levels)
 constexpr int kNW = kBS / 32;
 constexpr int kAcc = 2;      // accumulators per phase
+constexpr int kGroup = 16;           // CTAs per first-level barrier counter
+constexpr int kBarWords = 2 + 64;    // top count, generation, 64 group counters (<= 1024 CTAs)
+// phase categories of the device timeline (ms_fit_stats.phase_ms)
+enum { kPrfResid = 0, kPrfMatvec = 1, kPrfUpdate = 2, kPrfBarrier = 3, kPrfLower = 4, kPrfOther = 5,
+       kPrfScalar = 6, kProf = 8 };
 
 struct SolveArgs {
     int L;
@@ -69,9 +75,13 @@ struct SolveArgs {
     int* refines;      // [MS_MAXL]
     double* resid;     // [MS_MAXL]
     double* bytes;     // [1]
+    unsigned long long* prof;  // [kProf] nanoseconds CTA 0 spent per phase category
     int sweeps, max_iters, max_outer;
     double tol, inter_tol, inner_tol;
     unsigned long long timeout_ns;
+    int mf;            // MIXED inner mat-vec is matrix-free
+    int mf_tpp;        // lanes per target point of the matrix-free mat-vec
+    MFView mfv;
 };
 
 // Per-CTA shared state of the solve (identical in every CTA).
@@ -90,16 +100,42 @@ struct Shared {
     int last;
     int ok;
     unsigned mine;
+    unsigned long long pt[kProf];
+    unsigned long long tprev;
 };
+
+// Device timeline: CTA 0's thread 0 charges the time since the previous mark to `cat`.
+__device__ __forceinline__ void prof(Shared& sh, int cat) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned long long now = ms_globaltimer();
+        sh.pt[cat] += now - sh.tprev;
+        sh.tprev = now;
+    }
+}
 
 // y = sum_k val[k] * x[col[k]] over one CSR row, by a sub-warp of S lanes
 // (sl = lane within the sub-warp); the result is valid in every lane.  All 32
 // lanes of the warp must call it (invalid rows pass e = s).
+// The matrix (col, val) is read-only for the whole kernel and may use the
+// non-coherent path; x is written by other CTAs between phases and must not
+// (no __restrict__ on it).  The loop is unrolled by 4 with independent loads so
+// that a lane keeps several gathers in flight (small levels are latency-bound).
 template <typename TV, typename TX, typename TA>
 __device__ __forceinline__ TA csr_row(const int32_t* __restrict__ col, const TV* __restrict__ val,
-                                      const TX* __restrict__ x, int64_t s, int64_t e, int sl, int S) {
+                                      const TX* x, int64_t s, int64_t e, int sl, int S) {
     TA acc = TA(0);
-    for (int64_t k = s + sl; k < e; k += S) acc += (TA)val[k] * (TA)x[col[k]];
+    int64_t k = s + sl;
+    for (; k + 3 * S < e; k += 4 * S) {
+        const int32_t c0 = __ldg(col + k), c1 = __ldg(col + k + S), c2 = __ldg(col + k + 2 * S),
+                      c3 = __ldg(col + k + 3 * S);
+        const TV v0 = __ldg(val + k), v1 = __ldg(val + k + S), v2 = __ldg(val + k + 2 * S), v3 = __ldg(val + k + 3 * S);
+        const TX x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+        acc += (TA)v0 * (TA)x0;
+        acc += (TA)v1 * (TA)x1;
+        acc += (TA)v2 * (TA)x2;
+        acc += (TA)v3 * (TA)x3;
+    }
+    for (; k < e; k += S) acc += (TA)__ldg(val + k) * (TA)x[__ldg(col + k)];
     for (int o = S >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     return acc;
 }
@@ -174,11 +210,22 @@ template <int K>
 __device__ bool gsync_reduce(const SolveArgs& a, Shared& sh, int l0, int l1) {
     __syncthreads();
     if (threadIdx.x == 0) {
+        // two-level arrival: CTAs count in at their group's counter; the last CTA
+        // of each group counts in at the top counter (about 2 x sqrt(grid)
+        // serialised atomics per barrier instead of one per CTA)
         cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(a.bar[1]);
         cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(a.bar[0]);
         sh.mine = g.load(cuda::memory_order_relaxed);
-        const unsigned arrived = c.fetch_add(1u, cuda::memory_order_acq_rel);
-        sh.last = (arrived == gridDim.x - 1);
+        const unsigned grp = blockIdx.x / kGroup;
+        const unsigned ngrp = (gridDim.x + kGroup - 1) / kGroup;
+        const unsigned gsize = min((unsigned)kGroup, gridDim.x - grp * kGroup);
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> gc(a.bar[2 + grp]);
+        int last = 0;
+        if (gc.fetch_add(1u, cuda::memory_order_acq_rel) == gsize - 1) {
+            gc.store(0u, cuda::memory_order_relaxed);
+            last = (c.fetch_add(1u, cuda::memory_order_acq_rel) == ngrp - 1);
+        }
+        sh.last = last;
     }
     __syncthreads();
     int ok = 1;
@@ -235,6 +282,7 @@ __device__ bool gsync_reduce(const SolveArgs& a, Shared& sh, int l0, int l1) {
         }
         __syncthreads();
     }
+    prof(sh, kPrfBarrier);
     return true;
 }
 
@@ -286,6 +334,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                              }
                          });
                      });
+        prof(sh, kPrfResid);
         if (!gsync_reduce<2>(a, sh, l0, l1)) return false;
         if (tid == 0) {
             sh.any = 0;
@@ -333,6 +382,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
             }
         }
         __syncthreads();
+        prof(sh, kPrfScalar);
         first_outer = false;
         {
             bool anyzero = false;
@@ -342,6 +392,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                              [&](int, int64_t r0, int64_t r1, double*) {
                                  for (int64_t row = r0 + tid; row < r1; row += kBS) a.x[row] = 0.0;
                              });
+                prof(sh, kPrfOther);
                 // other CTAs read these rows in the next phases
                 if (!gsync(a, sh)) return false;
                 for (int l = tid; l < MS_MAXL; l += kBS) sh.zero[l] = 0;
@@ -363,6 +414,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
             if (tid == 0)
                 for (int l = l0; l < l1; ++l)
                     if (sh.act[l]) sh.bytes += (double)(a.off[l + 1] - a.off[l]) * 16.0;
+            prof(sh, kPrfOther);
             if (!gsync(a, sh)) return false;
         }
 
@@ -371,6 +423,21 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
             // M: w = A r; gamma = r.r, delta = r.w
             run_phase<2>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
                          [&](int l, int64_t r0, int64_t r1, double* acc) {
+                             if (MODE == 1 && a.mf) {
+                                 // matrix-free: the cells whose first point lies in [r0, r1)
+                                 const MFLevel& g = a.mfv.lv[l];
+                                 int64_t cfirst = a.mfv.cellid[r0];
+                                 if (a.mfv.cell_start[g.cell_off + cfirst] < r0) ++cfirst;
+                                 const int64_t cend = (int64_t)a.mfv.cellid[r1 - 1] + 1;
+                                 mf_cells_any(a.mfv, l, cfirst, cend, tid >> 5, kNW, a.mf_tpp, a.r32,
+                                              [&](int64_t row, float y) {
+                                                  const float ri = a.r32[row];
+                                                  a.q32[row] = y;
+                                                  acc[0] += (double)(ri * ri);
+                                                  acc[1] += (double)ri * (double)y;
+                                              });
+                                 return;
+                             }
                              const int S = a.tprA[l];
                              rows_by_subwarp(r0, r1, S, [&](int64_t row, bool ok, int sl) {
                                  int64_t s = 0, e = 0;
@@ -394,6 +461,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                                  }
                              });
                          });
+            prof(sh, kPrfMatvec);
             if (!gsync_reduce<2>(a, sh, l0, l1)) return false;
             if (tid == 0) {
                 sh.any = 0;
@@ -438,6 +506,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                 }
             }
             __syncthreads();
+            prof(sh, kPrfScalar);
             if (!sh.any) break;
             // E: p = r + beta p; s = w + beta s; x += alpha p; r -= alpha s
             run_phase<0>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
@@ -466,6 +535,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                                  }
                              }
                          });
+            prof(sh, kPrfUpdate);
             if (!gsync(a, sh)) return false;
         }
 
@@ -480,6 +550,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
             if (tid == 0)
                 for (int l = l0; l < l1; ++l)
                     if (sh.oact[l]) sh.bytes += (double)(a.off[l + 1] - a.off[l]) * 20.0;
+            prof(sh, kPrfOther);
             if (!gsync(a, sh)) return false;
         }
     }
@@ -503,6 +574,8 @@ __global__ void __launch_bounds__(kBS) k_fit(SolveArgs a) {
     if (tid == 0) {
         sh.bytes = 0.0;
         sh.any = 0;
+        for (int i = 0; i < kProf; ++i) sh.pt[i] = 0ull;
+        sh.tprev = ms_globaltimer();
     }
     __syncthreads();
     const int L = a.L;
@@ -513,6 +586,7 @@ __global__ void __launch_bounds__(kBS) k_fit(SolveArgs a) {
             a.x[row] = 0.0;
         }
     });
+    prof(sh, kPrfOther);
     if (!gsync(a, sh)) return;
     for (int m = 0; m < a.sweeps; ++m) {
         if (m <= L - 2) {
@@ -533,6 +607,7 @@ __global__ void __launch_bounds__(kBS) k_fit(SolveArgs a) {
             if (tid == 0)
                 for (int l = m + 1; l < L; ++l)
                     sh.bytes += (double)a.nnzB[l] * 12.0 + (double)(a.off[l + 1] - a.off[l]) * 32.0;
+            prof(sh, kPrfLower);
             if (!gsync(a, sh)) return;
         }
     }
@@ -543,6 +618,7 @@ __global__ void __launch_bounds__(kBS) k_fit(SolveArgs a) {
             a.refines[l] = sh.refines[l];
         }
         a.bytes[0] = sh.bytes;
+        for (int i = 0; i < kProf; ++i) a.prof[i] = sh.pt[i];
     }
 }
 
@@ -562,6 +638,16 @@ __global__ void k_spmv(const int64_t* rp, const int32_t* col, const TV* val, con
     if (ok && (lane & (S - 1)) == 0) y[row] = sub ? sub[row] + sign * (double)v : (double)v;
 }
 
+// y = D_L x matrix-free: one warp per cell of every level.
+__global__ void k_mf_apply(MFView v, const float* x, double* y, int tpp, int64_t total_cells) {
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (gw >= total_cells) return;  // warp-uniform
+    int l = 0;
+    while (l + 1 < v.L && gw >= v.lv[l + 1].cell_off) ++l;
+    const int64_t cell = gw - v.lv[l].cell_off;
+    mf_cells_any(v, l, cell, cell + 1, 0, 1, tpp, x, [&](int64_t row, float val) { y[row] = (double)val; });
+}
+
 __global__ void k_to_f32(const double* in, float* out, int64_t n) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = (float)in[i];
@@ -578,8 +664,44 @@ int tpr_for(double avg_nnz) {
     return S;
 }
 
+MFView make_mfview(const ms_hierarchy* h) {
+    MFView v{};
+    v.d = h->d;
+    v.L = h->L;
+    v.N = h->N;
+    v.E = h->view.w.e;
+    for (int i = 0; i < 4; ++i) v.c[i] = (float)h->view.w.c[i];
+    v.W = h->W;
+    v.cellid = h->cellid;
+    v.cell_start = h->cell_start;
+    for (int l = 0; l < h->L; ++l) {
+        const LevelGrid& g = h->view.grid[l];
+        MFLevel& m = v.lv[l];
+        for (int a = 0; a < 3; ++a) m.G[a] = g.G[a];
+        m.R = h->view.R;
+        m.cod = (float)(g.cell / h->view.delta[l]);
+        m.dscale = (float)h->view.dscale[l];
+        m.cell_off = g.cell_off;
+        m.ncells = g.ncells;
+    }
+    return v;
+}
+
+// Lanes per target point of the matrix-free mat-vec: about one warp per cell of the finest level.
+int mf_tpp_for(const ms_hierarchy* h) {
+    const LevelGrid& g = h->view.grid[h->L - 1];
+    const double occupied = (double)g.G[0] * g.G[1] * g.G[2];
+    const double per_cell = (double)(h->view.off[h->L] - h->view.off[h->L - 1]) / std::max(occupied, 1.0);
+    int t = 1;
+    while (t < 8 && per_cell * t * 2 <= 32.0) t <<= 1;
+    return t;
+}
+
 // Fill the solve arguments that depend only on the hierarchy and the options.
 void fill_args(const ms_hierarchy* h, const int64_t* rpA, const int64_t* rpB, double rel_tol, SolveArgs& a) {
+    a.mf = (h->opts.precision == MS_PREC_MIXED && h->opts.op == MS_OP_MATRIX_FREE) ? 1 : 0;
+    a.mf_tpp = h->mf_tpp;
+    a.mfv = make_mfview(h);
     const int L = h->L;
     a.L = L;
     a.N = h->N;
@@ -603,7 +725,7 @@ void fill_args(const ms_hierarchy* h, const int64_t* rpA, const int64_t* rpB, do
     a.max_iters = h->opts.max_iters > 0 ? h->opts.max_iters : 20000;
     a.max_outer = mixed ? 40 : 8;
     a.tol = rel_tol;
-    a.inter_tol = h->opts.inter_tol > 0 ? std::max(h->opts.inter_tol, rel_tol) : std::max(1e-6, rel_tol);
+    a.inter_tol = h->opts.inter_tol > 0 ? std::max(h->opts.inter_tol, rel_tol) : 1.0;
     a.inner_tol = h->opts.inner_tol > 0 ? h->opts.inner_tol : 1e-4;
     a.timeout_ns = 4000000000ull;
 }
@@ -641,15 +763,17 @@ static ms_status ensure_workspace(ms_hierarchy* h) {
         ms_set_error(MS_ERR_CUDA, "solve kernel cannot be resident on an SM");
         return MS_ERR_CUDA;
     }
-    h->solve_blocks = sms * std::min(per_sm, 2);
+    h->solve_blocks = std::min(sms * std::min(per_sm, 2), (kBarWords - 2) * kGroup);
+    h->mf_tpp = mf_tpp_for(h);
     MS_TRY(ms_alloc(h, (void**)&h->part, sizeof(double) * kAcc * MS_MAXL * h->solve_blocks));
     MS_TRY(ms_alloc(h, (void**)&h->scal, sizeof(double) * kAcc * MS_MAXL));
-    MS_TRY(ms_alloc(h, (void**)&h->bar, sizeof(unsigned) * 2));
+    MS_TRY(ms_alloc(h, (void**)&h->bar, sizeof(unsigned) * kBarWords));
     MS_TRY(ms_alloc(h, (void**)&h->status, sizeof(int)));
     MS_TRY(ms_alloc(h, (void**)&h->iters, sizeof(int64_t) * MS_MAXL));
     MS_TRY(ms_alloc(h, (void**)&h->refines, sizeof(int) * MS_MAXL));
     MS_TRY(ms_alloc(h, (void**)&h->resid, sizeof(double) * MS_MAXL));
     MS_TRY(ms_alloc(h, (void**)&h->bytes, sizeof(double)));
+    MS_TRY(ms_alloc(h, (void**)&h->prof, sizeof(unsigned long long) * kProf));
     return MS_OK;
 }
 
@@ -671,9 +795,9 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
     a.f = h->f; a.beta = h->beta; a.x = h->x; a.r = h->r; a.p = h->p; a.q = h->q; a.s = h->s;
     a.x32 = h->x32; a.r32 = h->r32; a.p32 = h->p32; a.q32 = h->q32; a.s32 = h->s32;
     a.part = h->part; a.scal = h->scal; a.bar = h->bar; a.status = h->status;
-    a.iters = h->iters; a.refines = h->refines; a.resid = h->resid; a.bytes = h->bytes;
+    a.iters = h->iters; a.refines = h->refines; a.resid = h->resid; a.bytes = h->bytes; a.prof = h->prof;
     const bool mixed = h->opts.precision == MS_PREC_MIXED;
-    if (mixed && !h->A.v32) {
+    if (mixed && h->opts.op != MS_OP_MATRIX_FREE && !h->A.v32) {
         ms_set_error(MS_ERR_STATE, "MIXED fit needs FP32 values (build with precision = MS_PREC_MIXED)");
         return MS_ERR_STATE;
     }
@@ -685,11 +809,12 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
     std::vector<int64_t> it(MS_MAXL, 0), it_sum(MS_MAXL, 0);
     std::vector<int> ref(MS_MAXL, 0);
     std::vector<double> res(MS_MAXL, 0.0);
+    double phase[kProf] = {};
     int dstat = 0;
     for (int col = 0; col < nrhs; ++col) {
         ms_gather_sorted(f_dev, h->f, h->perm, N, nrhs, col, st);
         ++launches;
-        MS_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * 2, st));
+        MS_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * kBarWords, st));
         MS_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
         MS_CUDA(cudaMemsetAsync(h->resid, 0, sizeof(double) * MS_MAXL, st));
         void* args[] = {&a};
@@ -710,11 +835,14 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
         MS_CUDA(cudaMemcpyAsync(ref.data(), h->refines, sizeof(int) * MS_MAXL, cudaMemcpyDeviceToHost, st));
         MS_CUDA(cudaMemcpyAsync(res.data(), h->resid, sizeof(double) * MS_MAXL, cudaMemcpyDeviceToHost, st));
         MS_CUDA(cudaMemcpyAsync(&b, h->bytes, sizeof(double), cudaMemcpyDeviceToHost, st));
+        unsigned long long pr[kProf];
+        MS_CUDA(cudaMemcpyAsync(pr, h->prof, sizeof(pr), cudaMemcpyDeviceToHost, st));
         MS_CUDA(cudaStreamSynchronize(st));
         float ms = 0.f;
         MS_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
         total_ms += ms;
         bytes += b;
+        for (int i = 0; i < kProf; ++i) phase[i] += 1e-6 * (double)pr[i];
         for (int l = 0; l < L; ++l) it_sum[l] += it[l];
         if (dstat != 0 && result == MS_OK) {
             result = (ms_status)dstat;
@@ -734,6 +862,7 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
         stats->fit_ms = total_ms;
         stats->matvec_bytes = bytes;
         stats->kernel_launches = launches;
+        for (int i = 0; i < kProf; ++i) stats->phase_ms[i] = phase[i];
     }
     return result;
 }
@@ -768,6 +897,15 @@ ms_status ms_apply_impl(ms_hierarchy* h, int op, const double* x_dev, double* y_
         k_to_f32<<<nblk(N, 256), 256, 0, st>>>(xs, x32, N);
         ms_count_launch();
         k_spmv<float, float, float><<<blocks, 256, 0, st>>>(M.rp, M.col, M.v32, x32, ys, N, S, nullptr, 1.0);
+        ms_count_launch();
+        break;
+    }
+    case MS_APPLY_AMF32: {
+        float* x32 = reinterpret_cast<float*>(h->r);
+        k_to_f32<<<nblk(N, 256), 256, 0, st>>>(xs, x32, N);
+        ms_count_launch();
+        const MFView v = make_mfview(h);
+        k_mf_apply<<<nblk(h->total_cells * 32, 256), 256, 0, st>>>(v, x32, ys, h->mf_tpp, h->total_cells);
         ms_count_launch();
         break;
     }
@@ -853,7 +991,7 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
         return MS_ERR_ARG;
     }
     const bool mixed = h->opts.precision == MS_PREC_MIXED;
-    if (mixed && !h->A.v32) {
+    if (mixed && h->opts.op != MS_OP_MATRIX_FREE && !h->A.v32) {
         ms_set_error(MS_ERR_STATE, "MIXED fit needs FP32 values (build with precision = MS_PREC_MIXED)");
         return MS_ERR_STATE;
     }
@@ -877,7 +1015,7 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
         ms_set_error(MS_ERR_CUDA, "solve kernel cannot be resident on an SM");
         return MS_ERR_CUDA;
     }
-    const int blocks = std::min(sms * std::min(per_sm, 2), kStaticMaxBlocks);
+    const int blocks = std::min(std::min(sms * std::min(per_sm, 2), kStaticMaxBlocks), (kBarWords - 2) * kGroup);
 
     // carve the fixed array
     unsigned char* c = base;
@@ -888,7 +1026,7 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
     double* part = reinterpret_cast<double*>(c);
     c += kStaticPart;
     unsigned char* small = c;
-    unsigned* bar = reinterpret_cast<unsigned*>(small);                    // [2]
+    unsigned* bar = reinterpret_cast<unsigned*>(small + 2560);             // [kBarWords]
     int* status = reinterpret_cast<int*>(small + 64);                      // [1]
     int64_t* iters = reinterpret_cast<int64_t*>(small + 128);              // [MS_MAXL]
     int* refines = reinterpret_cast<int*>(small + 128 + 8 * MS_MAXL);      // [MS_MAXL]
@@ -912,6 +1050,7 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
     a.x32 = v32[0]; a.r32 = v32[1]; a.p32 = v32[2]; a.q32 = v32[3]; a.s32 = v32[4];
     a.part = part; a.scal = scal; a.bar = bar; a.status = status;
     a.iters = iters; a.refines = refines; a.resid = resid; a.bytes = bytes;
+    a.prof = reinterpret_cast<unsigned long long*>(small + 2048);  // [kProf]
 
     ms_gather_sorted(f_dev, v64[0], h->perm, h->N, 1, 0, st);
     void* args[] = {&a};

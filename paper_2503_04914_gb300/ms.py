@@ -36,14 +36,17 @@ class ms_opts(C.Structure):
     _fields_ = [("wendland_d", C.c_int), ("wendland_k", C.c_int), ("nu", C.c_double), ("op", C.c_int),
                 ("precision", C.c_int), ("precond", C.c_int), ("max_iters", C.c_int),
                 ("jacobi_sweeps", C.c_int), ("inter_tol", C.c_double), ("inner_tol", C.c_double),
-                ("cell_split", C.c_int), ("threads_per_row", C.c_int), ("reserved", C.c_int * 8)]
+                ("cell_split", C.c_int), ("threads_per_row", C.c_int), ("lower_fp32", C.c_int),
+                ("reserved", C.c_int * 7)]
 
 
 class ms_fit_stats(C.Structure):
     _fields_ = [("L", C.c_int32), ("sweeps", C.c_int32), ("cg_iterations", C.c_int64 * MS_MAX_LEVELS),
                 ("refinements", C.c_int32 * MS_MAX_LEVELS), ("rel_residual", C.c_double * MS_MAX_LEVELS),
                 ("precond_fallbacks", C.c_int32), ("device_status", C.c_int32), ("fit_ms", C.c_double),
-                ("matvec_bytes", C.c_double), ("kernel_launches", C.c_int64)]
+                ("matvec_bytes", C.c_double), ("kernel_launches", C.c_int64), ("phase_ms", C.c_double * 8)]
+
+    PHASES = ("resid64", "matvec", "update", "barrier", "lower", "other", "scalar")
 
     def as_dict(self):
         L = self.L
@@ -51,7 +54,8 @@ class ms_fit_stats(C.Structure):
                 "refinements": list(self.refinements[:L]), "rel_residual": list(self.rel_residual[:L]),
                 "precond_fallbacks": self.precond_fallbacks, "device_status": self.device_status,
                 "fit_ms": self.fit_ms, "matvec_bytes": self.matvec_bytes,
-                "kernel_launches": self.kernel_launches}
+                "kernel_launches": self.kernel_launches,
+                "phase_ms": {n: self.phase_ms[i] for i, n in enumerate(self.PHASES)}}
 
 
 class ms_info(C.Structure):

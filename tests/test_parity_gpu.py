@@ -72,7 +72,7 @@ def check_fit(w, prec, tol_coef, rel_tol=1e-12, tol_approx=None, **over):
 def test_operators_match_oracle_matrices(wl):
     import torch
     w = inputs.grid_hierarchy_small() if wl == "grid" else ragged_halton([37, 150, 601, 2500])
-    H = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED)
+    H = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED, lower_fp32=1)
     off = om.level_offsets(w.levels)
     x = np.random.default_rng(3).standard_normal(w.N)
     # dense oracle blocks
@@ -102,6 +102,39 @@ def test_operators_match_oracle_matrices(wl):
                for l, X in enumerate(w.levels))
     assert info["nnz_A"] == nnzA
     H.close()
+
+
+@pytest.mark.parametrize("wl", ["grid_w21", "halton_nu8_w22", "random3d_w31"])
+def test_matrix_free_operator_matches_oracle(wl):
+    """y = D_L x with entries recomputed in FP32 from per-cell offsets (no stored matrix),
+    against the oracle's dense blocks; FP32 entries and accumulation: 2e-6 of the row's
+    absolute sum."""
+    import torch
+    if wl == "grid_w21":
+        w = inputs.grid_hierarchy_small()
+    elif wl == "halton_nu8_w22":
+        w = inputs.halton_hierarchy(L=3, nu=8.0, wendland=(2, 2), n_gauss=3)
+    else:
+        w = inputs.random3d_hierarchy(L=2, n_gauss=3)
+    H = ms.Hierarchy.from_workload(w)
+    off = om.level_offsets(w.levels)
+    x = np.random.default_rng(5).standard_normal(w.N)
+    y_ref = np.zeros(w.N)
+    scale = np.zeros(w.N)
+    for l, X in enumerate(w.levels):
+        M = om.kernel_dense(X, X, w.nu * w.h[l], w.wendland_d, w.wendland_k)
+        c = x[off[l]:off[l + 1]]
+        y_ref[off[l]:off[l + 1]] = M @ c
+        scale[off[l]:off[l + 1]] = np.abs(M) @ np.abs(c)
+    y = H.apply(ms.MS_APPLY_AMF32, torch.from_numpy(x).cuda()).cpu().numpy()
+    err = np.abs(y - y_ref) / scale
+    assert err.max() <= 2e-6, err.max()
+    H.close()
+
+
+def test_fit_mixed_matrix_free():
+    st = check_fit(ragged_halton([37, 150, 601, 2500, 9001]), ms.MS_PREC_MIXED, 1e-8, op=ms.MS_OP_MATRIX_FREE)
+    assert sum(st["cg_iterations"]) > 0
 
 
 def test_sorted_order_is_a_level_preserving_permutation():
@@ -188,6 +221,17 @@ def test_multi_rhs_equals_single_fits():
     S = H.evaluate(A, Q)
     for c in range(3):
         assert np.array_equal(S[:, c], H.evaluate(np.ascontiguousarray(A[:, c]), Q))
+
+
+def test_algorithm2_schedule_matches_default():
+    """Solving every non-final level in every sweep (Algorithm 2, inter_tol = rel_tol) gives the
+    same coefficients as the default schedule, which leaves non-final levels untouched until their
+    beta is final; it only runs more CG iterations."""
+    w = ragged_halton([37, 150, 601, 2500, 9001])
+    a0, s0 = ms.Hierarchy.from_workload(w).fit(w.f, rel_tol=1e-12)
+    a1, s1 = ms.Hierarchy.from_workload(w, inter_tol=1e-12).fit(w.f, rel_tol=1e-12)
+    assert rel(a1, a0) <= 1e-10
+    assert sum(s1["cg_iterations"]) > sum(s0["cg_iterations"])
 
 
 def test_jacobi_extra_sweep_is_a_fixed_point():

@@ -1,0 +1,228 @@
+"""CPU FP64 oracle of the learned factorised sparse-approximate-inverse preconditioner.
+
+TEST INFRASTRUCTURE ONLY (imported by the tests and the benchmark's CPU leg, never by
+the library).  Plain numpy, FP64, loops over points; shares no code with the CUDA path.
+
+The paper has no preconditioner; this part restates the extension the library
+adds to the per-level CG of Theorem 8.  It relies on the locality of A_l^{-1}
+(Lemma 5: the entries of A_l^{-1}, and the cardinal functions, decay
+exponentially) and on the scaling of eq. kernelscaling.
+
+Definitions (all per level l, points X_l in input order, delta = delta_l, d = dimension):
+  * pattern  P_i = {i} + the (up to) K = 16 nearest points j of the same level with
+    |x_j - x_i| < delta and input index j < i, ordered by distance, ties by index.
+  * exact weights (factorised sparse approximate inverse, Kolotilina-Yeremin):
+    g_i = A_P^{-1} e_1 / sqrt(e_1^T A_P^{-1} e_1), A_P = Phi_delta(X_P, X_P), self first;
+    G is lower triangular in input order with row i = g_i on P_i, and M = G^T G ~ A^{-1}
+    is symmetric positive definite for any G with a positive diagonal.
+  * scale-free weights  ghat_i = delta^{-d/2} g_i: since A_P = delta^{-d} K(offsets/delta),
+    ghat depends only on the delta-scaled offsets (x_j - x_i)/delta.
+  * features  z_i in R^{K d}: the scaled offsets of the pattern's neighbours in pattern
+    order, zero-padded when fewer than K exist.
+  * network   o = W3 relu(W2 relu(W1 z + b1) + b2) + b3  (hidden width 64, 17 outputs),
+    ghat = mu + sigma * o (per-output standardisation of the training targets), with the
+    diagonal clamped to >= 0.1 mu_0 and the outputs of missing neighbours set to zero.
+  * loss      mean over samples of sum over valid outputs of (o - t)^2 / 17, t = (ghat - mu)/sigma.
+  * Adam      beta1 = 0.9, beta2 = 0.999, eps = 1e-8, bias-corrected.
+
+Parity: pinned by tests/test_oracle_fsai.py (FSAI identities (G A)_{i,P_i\\{i}} = 0 and
+(G A G^T)_ii = 1, scale invariance of ghat, gradients against central differences, PCG
+convergence).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg as sla
+
+from . import multiscale as om
+
+K_NEIGH = 16
+HIDDEN = 64
+N_OUT = K_NEIGH + 1
+
+
+# ----------------------------------------------------------------------------- pattern
+
+
+def pattern(X: np.ndarray, delta: float, K: int = K_NEIGH):
+    """For every point i, the list of its pattern neighbours (input indices), nearest first."""
+    n = len(X)
+    out = []
+    for i in range(n):
+        if i == 0:
+            out.append(np.zeros(0, dtype=np.int64))
+            continue
+        d = np.sqrt(np.sum((X[:i] - X[i]) ** 2, axis=1))
+        cand = np.nonzero(d < delta)[0]
+        order = np.lexsort((cand, d[cand]))  # by distance, then index
+        out.append(cand[order][:K].astype(np.int64))
+    return out
+
+
+# ----------------------------------------------------------------------------- exact weights
+
+
+def exact_weights(X: np.ndarray, delta: float, wd: int, wk: int, pat):
+    """Rows g_i (self first) of the factorised sparse approximate inverse."""
+    rows = []
+    for i, nb in enumerate(pat):
+        P = np.concatenate([[i], nb])
+        AP = om.kernel_dense(X[P], X[P], delta, wd, wk)
+        e1 = np.zeros(len(P))
+        e1[0] = 1.0
+        z = sla.solve(AP, e1, assume_a="pos")
+        rows.append(z / math.sqrt(z[0]))
+    return rows
+
+
+def scale_free(rows, delta: float, d: int):
+    return [r * delta ** (-0.5 * d) for r in rows]
+
+
+def G_matrix(rows, pat, n):
+    G = np.zeros((n, n))
+    for i, (r, nb) in enumerate(zip(rows, pat)):
+        G[i, i] = r[0]
+        G[i, nb] = r[1:]
+    return G
+
+
+def features(X: np.ndarray, delta: float, pat, K: int = K_NEIGH):
+    n, d = X.shape
+    Z = np.zeros((n, K * d))
+    for i, nb in enumerate(pat):
+        off = (X[nb] - X[i]) / delta
+        Z[i, :len(nb) * d] = off.ravel()
+    return Z
+
+
+def target_matrix(ghat_rows, pat):
+    """[n, 17] scale-free targets and the validity mask (self always valid)."""
+    n = len(pat)
+    T = np.zeros((n, N_OUT))
+    Mk = np.zeros((n, N_OUT))
+    for i, (r, nb) in enumerate(zip(ghat_rows, pat)):
+        T[i, :len(r)] = r
+        Mk[i, :len(r)] = 1.0
+    return T, Mk
+
+
+# ----------------------------------------------------------------------------- network
+
+
+def param_shapes(n_in: int):
+    return [(HIDDEN, n_in), (HIDDEN,), (HIDDEN, HIDDEN), (HIDDEN,), (N_OUT, HIDDEN), (N_OUT,)]
+
+
+def unpack(theta: np.ndarray, n_in: int):
+    out, o = [], 0
+    for s in param_shapes(n_in):
+        k = int(np.prod(s))
+        out.append(theta[o:o + k].reshape(s))
+        o += k
+    return out
+
+
+def n_params(n_in: int) -> int:
+    return sum(int(np.prod(s)) for s in param_shapes(n_in))
+
+
+def init_params(n_in: int, seed: int) -> np.ndarray:
+    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) for every weight and bias of a layer, drawn
+    from SplitMix64(seed) in parameter order (W1, b1, W2, b2, W3, b3)."""
+    from paper_2503_04914_gb300.inputs import uniform01
+    u = uniform01(seed, n_params(n_in))
+    theta = np.empty(n_params(n_in))
+    o = 0
+    for s, fan in zip(param_shapes(n_in), [n_in, n_in, HIDDEN, HIDDEN, HIDDEN, HIDDEN]):
+        k = int(np.prod(s))
+        b = 1.0 / math.sqrt(fan)
+        theta[o:o + k] = -b + 2.0 * b * u[o:o + k]
+        o += k
+    return theta
+
+
+def forward(theta, Z, n_in):
+    W1, b1, W2, b2, W3, b3 = unpack(theta, n_in)
+    a1 = Z @ W1.T + b1
+    h1 = np.maximum(a1, 0.0)
+    a2 = h1 @ W2.T + b2
+    h2 = np.maximum(a2, 0.0)
+    o = h2 @ W3.T + b3
+    return o, (a1, h1, a2, h2)
+
+
+def loss(theta, Z, T_std, Mk, n_in):
+    o, _ = forward(theta, Z, n_in)
+    return float(np.sum(Mk * (o - T_std) ** 2) / (len(Z) * N_OUT))
+
+
+def grad(theta, Z, T_std, Mk, n_in):
+    """Analytic gradient of loss() (backpropagation through the three layers)."""
+    W1, b1, W2, b2, W3, b3 = unpack(theta, n_in)
+    o, (a1, h1, a2, h2) = forward(theta, Z, n_in)
+    S = len(Z)
+    e = 2.0 * Mk * (o - T_std) / (S * N_OUT)
+    gW3 = e.T @ h2
+    gb3 = e.sum(0)
+    d2 = (e @ W3) * (a2 > 0)
+    gW2 = d2.T @ h1
+    gb2 = d2.sum(0)
+    d1 = (d2 @ W2) * (a1 > 0)
+    gW1 = d1.T @ Z
+    gb1 = d1.sum(0)
+    return np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3])
+
+
+def adam_step(theta, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** t)
+    vh = v / (1 - b2 ** t)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def standardise(T, Mk):
+    """Per-output mean and standard deviation over the valid targets."""
+    cnt = np.maximum(Mk.sum(0), 1.0)
+    mu = (T * Mk).sum(0) / cnt
+    var = (((T - mu) * Mk) ** 2).sum(0) / cnt
+    sig = np.sqrt(np.maximum(var, 1e-30))
+    return mu, sig
+
+
+def predict_rows(theta, Z, pat, mu, sig, n_in):
+    o, _ = forward(theta, Z, n_in)
+    gh = mu + sig * o
+    gh[:, 0] = np.maximum(gh[:, 0], 0.1 * mu[0])
+    rows = []
+    for i, nb in enumerate(pat):
+        rows.append(gh[i, :1 + len(nb)].copy())
+    return rows
+
+
+# ----------------------------------------------------------------------------- PCG
+
+
+def pcg(A, b, G=None, tol=1e-10, maxiter=100000):
+    """CG on A x = b, preconditioned with M = G^T G when G is given; returns (x, iterations)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = G.T @ (G @ r) if G is not None else r.copy()
+    p = z.copy()
+    rz = float(r @ z)
+    bn = float(np.linalg.norm(b))
+    for it in range(maxiter):
+        q = A @ p
+        a = rz / float(p @ q)
+        x += a * p
+        r -= a * q
+        if np.linalg.norm(r) <= tol * bn:
+            return x, it + 1
+        z = G.T @ (G @ r) if G is not None else r
+        rz2 = float(r @ z)
+        p = z + (rz2 / rz) * p
+        rz = rz2
+    return x, maxiter

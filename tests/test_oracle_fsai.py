@@ -1,0 +1,109 @@
+"""Pins of the preconditioner oracle (oracle/fsai.py) against identities and brute force."""
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+from oracle import fsai as of
+from oracle import multiscale as om
+from paper_2503_04914_gb300 import inputs
+
+
+def level(nu, wend, L):
+    w = inputs.halton_hierarchy(L=L, nu=nu, wendland=wend, n_gauss=3)
+    return w.levels[-1], nu * w.h[-1], wend
+
+
+@pytest.mark.parametrize("nu,wend,L", [(4.0, (2, 1), 3), (8.0, (2, 2), 3)])
+def test_fsai_identities(nu, wend, L):
+    """Exact FSAI rows satisfy (G A)_{i,j} = 0 for j in P_i \\ {i} and (G A G^T)_ii = 1
+    (they solve A_P g = e_1 / sqrt(c)); M = G^T G is SPD."""
+    X, delta, (wd, wk) = level(nu, wend, L)
+    pat = of.pattern(X, delta)
+    rows = of.exact_weights(X, delta, wd, wk, pat)
+    G = of.G_matrix(rows, pat, len(X))
+    A = om.kernel_dense(X, X, delta, wd, wk)
+    GA = G @ A
+    scale = np.abs(G).max() * np.abs(A).max()
+    for i, nb in enumerate(pat):
+        assert np.all(np.abs(GA[i, nb]) <= 1e-9 * scale)
+    np.testing.assert_allclose(np.diag(GA @ G.T), 1.0, rtol=1e-9)
+    assert np.all(np.diag(G) > 0)
+    assert np.all(np.triu(G, 1) == 0)  # lower triangular in input order
+    assert np.linalg.eigvalsh(G.T @ G)[0] > 0
+
+
+def test_pattern_brute_force():
+    X, delta, _ = level(4.0, (2, 1), 3)
+    pat = of.pattern(X, delta)
+    tree = cKDTree(X)
+    for i, nb in enumerate(pat):
+        cand = [j for j in tree.query_ball_point(X[i], delta * (1 - 1e-12)) if j < i]
+        assert len(nb) == min(16, len(cand))
+        d = np.linalg.norm(X[nb] - X[i], axis=1)
+        assert np.all(nb < i) and np.all(d < delta) and np.all(np.diff(d) >= 0)
+        if len(cand) > 16:
+            rest = sorted(set(cand) - set(nb.tolist()))
+            assert np.min(np.linalg.norm(X[rest] - X[i], axis=1)) >= d[-1]
+
+
+def test_scale_free_weights_are_level_independent():
+    """ghat = delta^{-d/2} g depends only on the delta-scaled offsets (eq. kernelscaling)."""
+    X, delta, (wd, wk) = level(8.0, (2, 2), 2)
+    pat = of.pattern(X, delta)
+    g1 = of.scale_free(of.exact_weights(X, delta, wd, wk, pat), delta, 2)
+    c = 0.37
+    g2 = of.scale_free(of.exact_weights(c * X + 0.1, c * delta, wd, wk, pat), c * delta, 2)
+    for a, b in zip(g1, g2):
+        np.testing.assert_allclose(a, b, rtol=1e-8, atol=1e-10 * np.abs(a).max())
+
+
+def test_exact_fsai_accelerates_cg():
+    X, delta, (wd, wk) = level(4.0, (2, 1), 4)
+    pat = of.pattern(X, delta)
+    G = of.G_matrix(of.exact_weights(X, delta, wd, wk, pat), pat, len(X))
+    A = om.kernel_sparse(X, X, delta, wd, wk)
+    b = np.random.default_rng(0).standard_normal(len(X))
+    x0, it0 = of.pcg(A, b)
+    x1, it1 = of.pcg(A, b, G)
+    assert it1 * 5 < it0
+    assert np.linalg.norm(x1 - x0) <= 1e-7 * np.linalg.norm(x0)
+
+
+def test_gradient_matches_central_differences():
+    X, delta, (wd, wk) = level(4.0, (2, 1), 2)
+    pat = of.pattern(X, delta)
+    rows = of.scale_free(of.exact_weights(X, delta, wd, wk, pat), delta, 2)
+    T, Mk = of.target_matrix(rows, pat)
+    mu, sig = of.standardise(T, Mk)
+    Ts = (T - mu) / sig * Mk
+    Z = of.features(X, delta, pat)[40:70]
+    Ts, Mk = Ts[40:70], Mk[40:70]
+    n_in = Z.shape[1]
+    th = of.init_params(n_in, 7)
+    g = of.grad(th, Z, Ts, Mk, n_in)
+    rng = np.random.default_rng(1)
+    for idx in rng.choice(len(th), 60, replace=False):
+        h = 1e-6 * max(1.0, abs(th[idx]))
+        tp, tm = th.copy(), th.copy()
+        tp[idx] += h
+        tm[idx] -= h
+        fd = (of.loss(tp, Z, Ts, Mk, n_in) - of.loss(tm, Z, Ts, Mk, n_in)) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-6 * max(1e-6, np.abs(g).max()), (idx, fd, g[idx])
+
+
+def test_adam_first_step_is_a_signed_step():
+    g = np.array([0.3, -2.0, 1e-3, 0.0])
+    th, m, v = of.adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 1, lr=0.01)
+    np.testing.assert_allclose(th[:3], -0.01 * np.sign(g[:3]), rtol=1e-4)
+    assert th[3] == 0.0
+
+
+def test_init_is_uniform_in_fan_in_bounds():
+    n_in = 32
+    th = of.init_params(n_in, 3)
+    parts = of.unpack(th, n_in)
+    for p, fan in zip(parts, [32, 32, 64, 64, 64, 64]):
+        assert np.abs(p).max() <= 1 / math.sqrt(fan)
+        assert np.abs(p).max() >= 0.8 / math.sqrt(fan)

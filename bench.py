@@ -4,13 +4,15 @@
 One step = one pass of the whole hot path over the synthetic workload, with the
 inputs already resident in HBM:
   ms_build_hierarchy_dev  (level grids, cell binning, CSR of A_l and B_kj)
-  ms_fit_dev              (Jacobi sweeps on T' + per-level CG on D, one persistent kernel)
+  ms_fit_dev              (preconditioner rows by the trained network, then Jacobi
+                           sweeps on T' + per-level CG on D in one persistent kernel)
   ms_evaluate_dev         (approximant at a 256^2 query grid)
 Workload: d=2, 8 levels of scrambled Halton points, N_j = 64*4^(j-1) (1,398,080 points),
 h_j = N_j^-1/2, delta_j = 4 h_j, Wendland phi_{2,1}, f = 20 Gaussians + 0.1 sin(8 pi x) sin(8 pi y).
-The timed path is the MIXED one (FP32 mat-vecs, FP64 dots, FP64 outer refinement); the
-plain FP64 path is timed beside it.  `--impl reference` times the CPU FP64 oracle instead.
-Prints one JSON line (rank 0).
+The timed path is learned-PCG MIXED (FP32 mat-vecs, FP64 dots and refinement, FSAI rows
+predicted by the network trained beforehand on levels 1-4, training timed separately);
+plain FP64 CG+Jacobi and the other variants are timed beside it.
+`--impl reference` times the CPU FP64 oracle instead.  Prints one JSON line (rank 0).
 """
 from __future__ import annotations
 
@@ -30,6 +32,7 @@ METRIC = "fit time at rel-err 1e-8: learned-PCG FP32 vs plain FP64 (ms); mat-vec
 WORKLOAD = ("halton8_d2_nu4_w21: d=2, 8 levels scrambled Halton N_j=64*4^(j-1) (1,398,080 points), "
             "delta_j=4*N_j^-1/2, Wendland phi_{2,1}, f=20 Gaussians+0.1 sin(8pi x)sin(8pi y)")
 REL_TOL = 1e-10
+N_FULL = 1398080
 
 
 def parse():
@@ -40,10 +43,12 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--levels", type=int, default=8)
     p.add_argument("--query-side", type=int, default=256)
+    p.add_argument("--train-epochs", type=int, default=300)
     p.add_argument("--cpu-levels", type=int, default=6, help="levels of the oracle's bounded sample")
     p.add_argument("--ref-levels", type=int, default=5, help="levels per step of the reference arm")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-variants", action="store_true", help="skip the comparison paths")
+    p.add_argument("--no-nu8", action="store_true", help="skip the nu=8, phi_{2,2} block")
     return p.parse_args()
 
 
@@ -139,9 +144,6 @@ print(json.dumps({{"N": w.N, "times": ts}}))
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-N_FULL = 1398080
-
-
 # ------------------------------------------------------------------ reference arm (the oracle)
 
 
@@ -197,36 +199,60 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def step(prec):
-        opts = ms.ms_default_opts(wendland_d=2, wendland_k=1, nu=w.nu, precision=prec)
+    # train the network once (levels 1-4 of this hierarchy), outside the timed region
+    Ht = ms.Hierarchy(2, n, pts, w.h, precision=ms.MS_PREC_MIXED, precond=ms.MS_PRECOND_LEARNED,
+                      wendland_d=2, wendland_k=1, nu=w.nu)
+    train = Ht.train_precond([0, 1, 2, 3], epochs=args.train_epochs)
+    params = Ht.precond_params()
+    Ht.close()
+
+    def step(prec, precond=ms.MS_PRECOND_NONE, inter_tol=0.0, wl=None, pts_=None, f_=None):
+        wl = wl or w
+        pts_ = pts if pts_ is None else pts_
+        f_ = f if f_ is None else f_
+        opts = ms.ms_default_opts(wendland_d=wl.wendland_d, wendland_k=wl.wendland_k, nu=wl.nu, precision=prec,
+                                  precond=precond, inter_tol=inter_tol)
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        hnd = ms.ms_build_hierarchy(2, n, pts, w.h, opts)
-        alpha, st = ms.ms_fit(hnd, f, REL_TOL)
+        hnd = ms.ms_build_hierarchy(2, wl.n_per_level, pts_, wl.h, opts)
+        if precond == ms.MS_PRECOND_LEARNED:
+            ms.ms_precond_params(hnd, 2, params)
+        alpha, st = ms.ms_fit(hnd, f_, REL_TOL)
         e1.record(stream)
         s = ms.ms_evaluate(hnd, alpha, Q)
         e2.record(stream)
         torch.cuda.synchronize()
         info = ms.ms_hierarchy_info(hnd)
         ms.ms_destroy(hnd)
-        return {"total": e0.elapsed_time(e2), "eval": e1.elapsed_time(e2), "stats": st, "info": info}
+        return {"total": e0.elapsed_time(e2), "eval": e1.elapsed_time(e2), "stats": st, "info": info,
+                "alpha": alpha}
 
-    def timed(prec, k):
+    def timed(k, *a, **kw):
         recs = []
         for _ in range(k):
             flush.fill_(1.0)  # L2 flush between steps (256 MB write), outside the timed events
             barrier()
-            recs.append(step(prec))
+            recs.append(step(*a, **kw))
             barrier()
         return recs
 
+    def summary(recs):
+        st = recs[-1]["stats"]
+        return {"ms_per_step": statistics.mean(r["total"] for r in recs),
+                "fit_ms": statistics.mean(r["stats"]["fit_ms"] for r in recs),
+                "build_ms": statistics.mean(r["info"]["build_ms"] for r in recs),
+                "cg_iterations": st["cg_iterations"], "rel_residual_max": max(st["rel_residual"]),
+                "precond_fallbacks": st["precond_fallbacks"],
+                "phase_ms": {k: round(v, 3) for k, v in st["phase_ms"].items()}}
+
+    HEAD = (ms.MS_PREC_MIXED, ms.MS_PRECOND_LEARNED)
     for _ in range(args.warmup):
-        step(ms.MS_PREC_MIXED)
+        step(*HEAD)
     clocks = ClockSampler(local)
     lc0 = ms.ms_launch_count()
     clocks.start()
     t_wall = time.perf_counter()
-    recs = timed(ms.MS_PREC_MIXED, args.steps)
+    recs = timed(args.steps, *HEAD)
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     launches = (ms.ms_launch_count() - lc0) / args.steps
@@ -246,25 +272,38 @@ def run_ours(args):
         fit_ms = statistics.mean(r["stats"]["fit_ms"] for r in recs)
         fit_bytes = st["matvec_bytes"]
         achieved = fit_bytes / (fit_ms * 1e-3) / 1e9
-        out["roofline"] = {"kernel": "k_fit (persistent Jacobi/CG solve, MIXED)", "bound": "hbm",
+        out["roofline"] = {"kernel": "k_fit<MIXED> (persistent Jacobi / learned-PCG solve)", "bound": "hbm",
                            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                            "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
                            "algorithmic_bytes_per_launch": fit_bytes, "launch_ms": fit_ms}
-        out["phases_ms"] = {"build": statistics.mean(r["info"]["build_ms"] for r in recs),
-                            "fit": fit_ms, "evaluate": statistics.mean(r["eval"] for r in recs)}
-        out["cg_iterations"] = st["cg_iterations"]
-        out["refinements"] = st["refinements"]
-        out["rel_residual"] = st["rel_residual"]
+        out["learned_pcg"] = summary(recs)
+        out["phases_ms"] = {"build": out["learned_pcg"]["build_ms"], "fit_incl_precond": None,
+                            "fit_kernel": fit_ms, "evaluate": statistics.mean(r["eval"] for r in recs)}
+        out["phases_ms"]["fit_incl_precond"] = (out["learned_pcg"]["ms_per_step"] - out["phases_ms"]["build"]
+                                                - out["phases_ms"]["evaluate"])
+        out["train"] = {"levels": [1, 2, 3, 4], "epochs": args.train_epochs, **train}
         out["nnz"] = {"A": info["nnz_A"], "B": info["nnz_B"]}
 
-        # stand-alone mat-vecs (sorted order) on the built hierarchy: GB/s of the CSR kernels
+        if not args.no_variants:
+            k2 = max(2, args.steps // 2)
+            out["plain_fp64"] = summary(timed(k2, ms.MS_PREC_FP64))
+            out["mixed_no_precond"] = summary(timed(k2, ms.MS_PREC_MIXED))
+            out["mixed_exact_fsai"] = summary(timed(k2, ms.MS_PREC_MIXED, ms.MS_PRECOND_EXACT))
+            out["algorithm2_schedule_fp64"] = summary(timed(1, ms.MS_PREC_FP64, inter_tol=REL_TOL))
+            out["speedup_learned_vs_plain_fp64"] = out["plain_fp64"]["ms_per_step"] / ms_step
+            # agreement of the headline coefficients with the plain FP64 fit (same hierarchy, same f)
+            a0 = timed(1, ms.MS_PREC_FP64)[0]["alpha"]
+            a1 = last["alpha"]
+            out["rel_diff_vs_fp64_coefficients"] = float(torch.linalg.norm(a1 - a0) / torch.linalg.norm(a0))
+
+        # stand-alone mat-vecs (sorted order): GB/s of the CSR kernels, matrix-free timing
         H = ms.Hierarchy(2, n, pts, w.h, precision=ms.MS_PREC_MIXED, wendland_d=2, wendland_k=1, nu=w.nu)
         N = w.N
         x = torch.randn(N, dtype=torch.float64, device="cuda")
         y = torch.empty_like(x)
         mv = {}
         for name, op, nnz, vb in [("A64", ms.MS_APPLY_A64, info["nnz_A"], 8), ("A32", ms.MS_APPLY_A32, info["nnz_A"], 4),
-                                  ("B64", ms.MS_APPLY_B64, info["nnz_B"], 8)]:
+                                  ("AMF32", ms.MS_APPLY_AMF32, info["nnz_A"], 0), ("B64", ms.MS_APPLY_B64, info["nnz_B"], 8)]:
             for _ in range(3):
                 H.apply(op, x, y, sorted_order=True)
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -275,35 +314,50 @@ def run_ours(args):
             ev[1].record(stream)
             torch.cuda.synchronize()
             t_ms = ev[0].elapsed_time(ev[1]) / reps
-            # matrix (col + val) + row offsets + y write + one read of x (FP32 ops also convert x)
-            b = nnz * (4 + vb) + N * (8 + 8 + 8) + (N * 12 if vb == 4 else 0)
-            mv[name] = {"ms": t_ms, "GBps": b / (t_ms * 1e-3) / 1e9, "frac_hbm": b / (t_ms * 1e-3) / 1e9 / hbm,
-                        "algorithmic_bytes": b}
+            if vb:
+                # matrix (col + val) + row offsets + y write + one read of x (FP32 ops also convert x)
+                b = nnz * (4 + vb) + N * (8 + 8 + 8) + (N * 12 if vb == 4 else 0)
+                mv[name] = {"ms": t_ms, "GBps": b / (t_ms * 1e-3) / 1e9, "frac_hbm": b / (t_ms * 1e-3) / 1e9 / hbm,
+                            "algorithmic_bytes": b}
+            else:
+                mv[name] = {"ms": t_ms, "stored_entries_per_s": nnz / (t_ms * 1e-3)}
         out["matvec"] = mv
         H.close()
 
-        # plain FP64 path, same step
-        if not args.no_fp64:
-            step(ms.MS_PREC_FP64)
-            r64 = timed(ms.MS_PREC_FP64, max(2, args.steps // 2))
-            out["fp64"] = {"ms_per_step": statistics.mean(r["total"] for r in r64),
-                           "fit_ms": statistics.mean(r["stats"]["fit_ms"] for r in r64),
-                           "build_ms": statistics.mean(r["info"]["build_ms"] for r in r64),
-                           "cg_iterations": r64[-1]["stats"]["cg_iterations"],
-                           "algorithmic_bytes_fit": r64[-1]["stats"]["matvec_bytes"]}
+        # nu = 8, phi_{2,2} (ill-conditioned levels): learned-PCG MIXED vs plain FP64, one step each
+        if not args.no_nu8:
+            w8 = inputs.halton_hierarchy(L=args.levels, nu=8.0, wendland=(2, 2))
+            p8, f8 = torch.from_numpy(w8.points).cuda(), torch.from_numpy(w8.f).cuda()
+            H8 = ms.Hierarchy(2, w8.n_per_level, p8, w8.h, precision=ms.MS_PREC_MIXED,
+                              precond=ms.MS_PRECOND_LEARNED, wendland_d=2, wendland_k=2, nu=8.0)
+            train8 = H8.train_precond([0, 1, 2, 3], epochs=args.train_epochs)
+            params8 = H8.precond_params()
+            H8.close()
+            saved = params
+            params = params8
+            r8 = timed(1, ms.MS_PREC_MIXED, ms.MS_PRECOND_LEARNED, wl=w8, pts_=p8, f_=f8)
+            params = saved
+            r8f = timed(1, ms.MS_PREC_FP64, wl=w8, pts_=p8, f_=f8)
+            out["nu8_w22"] = {"workload": "as above with delta_j = 8 h_j and Wendland phi_{2,2}",
+                              "learned_pcg": summary(r8), "plain_fp64": summary(r8f),
+                              "train": {"levels": [1, 2, 3, 4], **train8},
+                              "speedup": summary(r8f)["ms_per_step"] / summary(r8)["ms_per_step"]}
+            del p8, f8
 
         # end to end through the host-pointer C ABI (H2D of points, f, queries; D2H of alpha, values)
         e2e = []
         for i in range(max(2, args.steps // 2) + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            Hh = ms.Hierarchy(2, n, w.points, w.h, precision=ms.MS_PREC_MIXED, wendland_d=2, wendland_k=1, nu=w.nu)
+            Hh = ms.Hierarchy(2, n, w.points, w.h, precision=ms.MS_PREC_MIXED, precond=ms.MS_PRECOND_LEARNED,
+                              wendland_d=2, wendland_k=1, nu=w.nu)
+            Hh.precond_params(params)
             a_h, _ = Hh.fit(w.f, REL_TOL)
             s_h = Hh.evaluate(a_h, Qh)
             Hh.close()
             if i > 0:
                 e2e.append(1000.0 * (time.perf_counter() - t0))
-        h2d = w.points.nbytes + w.f.nbytes + Qh.nbytes
+        h2d = w.points.nbytes + w.f.nbytes + Qh.nbytes + params.nbytes
         d2h = a_h.nbytes + s_h.nbytes
         out["e2e"] = {"value": statistics.mean(e2e), "unit": "ms", "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h)}
@@ -321,9 +375,10 @@ def run_ours(args):
         line = {"metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "precision": "mixed (FP32 CSR mat-vec, FP64 dots/refinement)",
+                "config": {"workload": WORKLOAD,
+                           "path": "learned-PCG MIXED: FP32 CSR mat-vecs, FP64 dots/refinement, learned FSAI",
                            "rel_tol": REL_TOL, "queries": args.query_side ** 2,
-                           "step": "build_hierarchy + fit + evaluate, inputs resident in HBM",
+                           "step": "build_hierarchy + precond rows + fit + evaluate, inputs resident in HBM",
                            "l2": "flushed between steps (256 MB write); CSR working set >> L2",
                            "parallelism": f"replicas x{ws}"},
                 "wall_s_timed": t_wall, "gpu_launches": launches, "clocks": clk, **out}

@@ -73,8 +73,18 @@ enum {
     MS_PREC_MIXED = 1   /* FP32 mat-vecs and inner vectors, FP64 dots, FP64 outer
                            true-residual refinement, FP64 level-finalising Jacobi updates */
 };
-/* Preconditioner of the level CG solves. */
-enum { MS_PRECOND_NONE = 0, MS_PRECOND_LEARNED = 1 };
+/* Preconditioner of the level CG solves (MIXED precision only).  Both kinds are
+ * factorised sparse approximate inverses M = G^T G (Kolotilina-Yeremin): row i of the
+ * lower-triangular G lives on i and its (up to) 16 nearest same-level points within
+ * delta_l that precede it in input order, and equals A_P^{-1} e_1 / sqrt((A_P^{-1})_11)
+ * for the patch matrix A_P.  M is symmetric positive definite whenever G's diagonal is
+ * positive, so the preconditioned CG cannot break down.  The paper has no
+ * preconditioner; the locality it exploits is that of A_l^{-1} (Lemma 5). */
+enum {
+    MS_PRECOND_NONE = 0,
+    MS_PRECOND_LEARNED = 1, /* rows predicted by the trained network (ms_train_precond) */
+    MS_PRECOND_EXACT = 2    /* rows from exact FP64 patch solves (the network's teacher) */
+};
 
 /* Options of a hierarchy; fill with ms_default_opts() and override fields. */
 typedef struct ms_opts {
@@ -257,6 +267,59 @@ ms_status ms_get_permutation(const ms_hierarchy* h, int64_t* perm_out);
 
 /* Sizes and timings of a built hierarchy. */
 ms_status ms_hierarchy_info(const ms_hierarchy* h, ms_info* info);
+
+/* ---------------------------------------------------------------- learned preconditioner
+ * The network maps the delta-scaled offsets (x_j - x_i)/delta_l of a point's pattern
+ * neighbours (16 d inputs, zero-padded) through ReLU layers of width 64 to 17 outputs,
+ * the standardised scale-free row ghat_i = delta_l^{-d/2} g_i (self first).  Because
+ * A_P = delta^-d K(offsets / delta) (eq. kernelscaling), ghat does not depend on the
+ * level, so a network trained on coarse levels serves every level.  Inference uses
+ * BF16-valued weights with FP32 accumulation; training is Adam on FP32 master weights
+ * whose forward and backward passes use the BF16-rounded copies. */
+typedef struct ms_train_opts {
+    int epochs;          /* passes over the training patches (default 300) */
+    int batch;           /* samples per Adam step, a multiple of 64 (default 512) */
+    double lr;           /* initial learning rate (default 3e-3), cosine-decayed to lr_final */
+    double lr_final;     /* default 1e-4 */
+    uint64_t seed;       /* SplitMix64 seed of the initial weights and of the shuffles */
+    int fp32_weights;    /* 1: train and infer with the FP32 master weights (no BF16 rounding) */
+    int reserved[7];
+} ms_train_opts;
+
+typedef struct ms_train_stats {
+    int64_t samples;     /* training patches (all points of the chosen levels) */
+    int64_t steps;       /* Adam steps taken */
+    double loss_first;   /* mean squared error of the first and of the last step's batch */
+    double loss_last;
+    double train_ms;     /* device time of the training loop */
+    int32_t n_params;
+} ms_train_stats;
+
+void ms_default_train_opts(ms_train_opts* opts);
+
+/* Train the network on the exact rows (FP64 patch Cholesky) of every point of the given
+ * 0-based levels of h; the weights are kept in h and used by fits with
+ * precond = MS_PRECOND_LEARNED.  opts NULL = defaults.  Errors: MS_ERR_ARG (levels,
+ * options), MS_ERR_OOM, MS_ERR_CUDA.  Synchronous. */
+ms_status ms_train_precond(ms_hierarchy* h, const int* levels, int n_levels, const ms_train_opts* opts,
+                           ms_train_stats* stats);
+
+/* Export (set = 0) or import (set = 1) the network: params is host float[n] with
+ * n = n_weights + 34: the FP32 weights in the order W1 [64][16d], b1 [64], W2 [64][64],
+ * b2 [64], W3 [17][64], b3 [17] (row-major), then the 17 output means and 17 output
+ * standard deviations.  Importing marks the network trained.  Errors: MS_ERR_ARG (n),
+ * MS_ERR_STATE (export without weights). */
+ms_status ms_precond_params(ms_hierarchy* h, float* params, int64_t n, int set);
+
+/* Inspection of the preconditioner's building blocks (host outputs, input order). */
+enum {
+    MS_INSPECT_PATTERN = 0, /* int32 [N][16]: pattern neighbours (input indices), -1 = none */
+    MS_INSPECT_TARGETS = 1, /* double [N][17]: exact scale-free rows ghat (zeros past the pattern) */
+    MS_INSPECT_PREDICT = 2, /* float [N][17]: the network's rows ghat */
+    MS_INSPECT_GRAD = 3     /* float [n_weights + 1]: full-batch gradient of the training loss on
+                               `levels` with the FP32 master weights, then the loss */
+};
+ms_status ms_precond_inspect(ms_hierarchy* h, int what, const int* levels, int n_levels, void* out, int64_t n_out);
 
 /* Number of CUDA kernels this library has launched in the calling process so far
  * (all threads and handles; the count is taken at launch time, not completion). */

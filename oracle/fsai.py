@@ -22,7 +22,13 @@ Definitions (all per level l, points X_l in input order, delta = delta_l, d = di
   * network   o = W3 relu(W2 relu(W1 z + b1) + b2) + b3  (hidden width 64, 17 outputs),
     ghat = mu + sigma * o (per-output standardisation of the training targets), with the
     diagonal clamped to >= 0.1 mu_0 and the outputs of missing neighbours set to zero.
-  * loss      mean over samples of sum over valid outputs of (o - t)^2 / 17, t = (ghat - mu)/sigma.
+  * loss      energy norm of the error of the row in the patch's own metric, averaged over
+              samples: (1/S) sum_s e_s^T K_s e_s with e = sigma * (o - t) on the valid outputs
+              (zero elsewhere), t = (ghat - mu)/sigma the standardised exact row and
+              K_s = phi(|x_a - x_b|/delta) the scaled patch matrix (self first).  The exact row
+              minimises g^T K g - 2 log g_self, so this loss weighs errors the way the
+              preconditioner feels them, where a plain MSE on the (ill-conditioned) rows is
+              dominated by directions K hardly sees.
   * Adam      beta1 = 0.9, beta2 = 0.999, eps = 1e-8, bias-corrected.
 
 Parity: pinned by tests/test_oracle_fsai.py (FSAI identities (G A)_{i,P_i\\{i}} = 0 and
@@ -154,17 +160,30 @@ def forward(theta, Z, n_in):
     return o, (a1, h1, a2, h2)
 
 
-def loss(theta, Z, T_std, Mk, n_in):
+def patch_matrices(X: np.ndarray, delta: float, wd: int, wk: int, pat):
+    """[n, 17, 17] scaled patch matrices K_i = phi(|x_a - x_b| / delta) on P_i (self first), zero-padded."""
+    Ks = np.zeros((len(pat), N_OUT, N_OUT))
+    d = X.shape[1]
+    for i, nb in enumerate(pat):
+        P = np.concatenate([[i], nb])
+        m = len(P)
+        Ks[i, :m, :m] = om.kernel_dense(X[P], X[P], delta, wd, wk) * delta ** d
+    return Ks
+
+
+def loss(theta, Z, T_std, Mk, Ks, sig, n_in):
     o, _ = forward(theta, Z, n_in)
-    return float(np.sum(Mk * (o - T_std) ** 2) / (len(Z) * N_OUT))
+    e = sig * (o - T_std) * Mk
+    return float(np.einsum("si,sij,sj->", e, Ks, e) / len(Z))
 
 
-def grad(theta, Z, T_std, Mk, n_in):
+def grad(theta, Z, T_std, Mk, Ks, sig, n_in):
     """Analytic gradient of loss() (backpropagation through the three layers)."""
     W1, b1, W2, b2, W3, b3 = unpack(theta, n_in)
     o, (a1, h1, a2, h2) = forward(theta, Z, n_in)
     S = len(Z)
-    e = 2.0 * Mk * (o - T_std) / (S * N_OUT)
+    d = sig * (o - T_std) * Mk
+    e = 2.0 * np.einsum("sij,sj->si", Ks, d) * sig * Mk / S
     gW3 = e.T @ h2
     gb3 = e.sum(0)
     d2 = (e @ W3) * (a2 > 0)

@@ -77,7 +77,7 @@ ms_status validate_and_init(int d, int L, const int64_t* n_per_level, const doub
     }
     if (o.precision != MS_PREC_FP64 && o.precision != MS_PREC_MIXED) { ms_set_error(MS_ERR_ARG, "unknown precision %d", o.precision); return MS_ERR_ARG; }
     if (o.op < MS_OP_CSR || o.op > MS_OP_AUTO) { ms_set_error(MS_ERR_ARG, "unknown operator %d", o.op); return MS_ERR_ARG; }
-    if (o.precond != MS_PRECOND_NONE && o.precond != MS_PRECOND_LEARNED) { ms_set_error(MS_ERR_ARG, "unknown preconditioner %d", o.precond); return MS_ERR_ARG; }
+    if (o.precond < MS_PRECOND_NONE || o.precond > MS_PRECOND_EXACT) { ms_set_error(MS_ERR_ARG, "unknown preconditioner %d", o.precond); return MS_ERR_ARG; }
     if (o.cell_split < 0 || o.cell_split > 4) { ms_set_error(MS_ERR_ARG, "cell_split must be 0..4"); return MS_ERR_ARG; }
     if (o.threads_per_row < 0 || o.threads_per_row > 32 || (o.threads_per_row & (o.threads_per_row - 1))) {
         ms_set_error(MS_ERR_ARG, "threads_per_row must be 0 or a power of two <= 32"); return MS_ERR_ARG;

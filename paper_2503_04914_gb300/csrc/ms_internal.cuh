@@ -51,6 +51,7 @@ static inline bool wendland_poly(int wd, int wk, WendlandPoly* w) {
 
 template <typename T>
 __device__ __forceinline__ T wendland_eval(const WendlandPoly& w, T r) {
+    if (!(r < T(1))) return T(0);  // compact support: phi vanishes for r >= 1
     T s = T(1) - r;
     T pw = T(1);
     for (int i = 0; i < w.e; ++i) pw *= s;
@@ -260,8 +261,35 @@ struct DevCSR {
     int64_t nnz = 0;
 };
 
+// Factorised sparse-approximate-inverse preconditioner M = G^T G of the level CGs
+// (rows: self + up to kPcK nearest preceding same-level neighbours within delta).
+constexpr int kPcK = 16;
+constexpr int kPcOut = kPcK + 1;
+constexpr int kPcHidden = 64;
+
+struct Precond {
+    int n_in = 0, n_params = 0;
+    bool trained = false;        // network weights present
+    int built_kind = 0;          // kind of G currently built (0 = none)
+    float* theta = nullptr;      // [n_params] FP32 master weights (W1,b1,W2,b2,W3,b3)
+    float* theta_bf = nullptr;   // [n_params] the same rounded to BF16 (stored as float)
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    float* musig = nullptr;      // [2 * kPcOut] standardisation of the scale-free targets
+    int32_t* nbr = nullptr;      // [N][kPcK] pattern neighbours (sorted positions, -1 = none)
+    int32_t* gcol = nullptr;     // [N][kPcOut] row pattern of G (self first, -1 = none)
+    float* gval = nullptr;       // [N][kPcOut] values of G
+    int64_t* gt_rp = nullptr;    // [N+1] rows of G^T (in-pattern)
+    int32_t* gt_col = nullptr;   // [nnz] source rows
+    float* gt_val = nullptr;     // [nnz]
+    int64_t gt_nnz = 0;
+    int fp32_weights = 0;
+};
+
 struct ms_hierarchy {
     int device = 0;
+    Precond pc;
+    float *u32 = nullptr, *u1_32 = nullptr;  // preconditioned-CG work vectors
     int d = 0, L = 0;
     int64_t N = 0;
     ms_opts opts{};
@@ -280,6 +308,7 @@ struct ms_hierarchy {
     double* part = nullptr;      // reduction partials
     double* scal = nullptr;      // published grid sums
     unsigned long long* prof = nullptr;  // device timeline of the solve kernel
+    int* pcfb = nullptr;                 // preconditioner fallbacks of the last fit
     unsigned* bar = nullptr;     // barrier words
     int* status = nullptr;       // device status
     int64_t* iters = nullptr;    // per-level iteration counters
@@ -303,6 +332,9 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
 ms_status ms_apply_impl(ms_hierarchy* h, int op, const double* x_dev, double* y_dev, int sorted, cudaStream_t s);
 ms_status ms_evaluate_impl(ms_hierarchy* h, const double* alpha_dev, int nrhs, const double* q_dev, int64_t nq,
                            double* out_dev, cudaStream_t s);
+
+// learned / exact FSAI preconditioner (ms_precond.cu): build G and G^T for `kind`
+ms_status ms_pc_build(ms_hierarchy* h, int kind, cudaStream_t s);
 
 // permutation helpers (ms_capi.cu)
 void ms_gather_sorted(const double* in, double* out, const int32_t* perm, int64_t N, int nrhs, int col, cudaStream_t s);

@@ -1,0 +1,940 @@
+// Learned factorised sparse-approximate-inverse (FSAI) preconditioner of the
+// per-level CG solves (Theorem 8).  The paper has no preconditioner; this is
+// the library's extension, justified by the exponential decay of A_l^{-1}
+// (Lemma 5) and by the scaling of eq. kernelscaling.
+//
+//   pattern   P_i = {i} + the (up to) 16 nearest same-level points j within delta
+//             with input index j < i (nearest first, ties by input index);
+//   exact row g_i = A_P^{-1} e_1 / sqrt(e_1^T A_P^{-1} e_1)  (Kolotilina-Yeremin FSAI);
+//             M = G^T G is symmetric positive definite for any G with a positive
+//             diagonal, so a learned G can never make the preconditioned CG break down;
+//   scale-free ghat_i = delta^{-d/2} g_i depends only on the delta-scaled offsets of
+//             the pattern (A_P = delta^-d K(offsets/delta)), so a network trained on
+//             coarse levels applies to every level;
+//   network   32 -> 64 -> 64 -> 17 (d = 2; input 16 d), ReLU, BF16-valued weights with
+//             FP32 accumulation at inference; trained with Adam on FP32 master weights
+//             (forward/backward on the BF16-rounded copies) against the exact rows
+//             of chosen levels, standardised per output.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "ms_internal.cuh"
+
+namespace {
+
+constexpr int kTB = 64;  // training samples per block
+
+inline unsigned nblk(int64_t n, int bs) { return (unsigned)std::max<int64_t>(1, (n + bs - 1) / bs); }
+
+__device__ __forceinline__ double dist_rn(const HierView& v, int64_t i, int64_t j) {
+    double s = 0.0;
+    for (int a = 0; a < v.d; ++a) {
+        const double t = __dsub_rn(v.X[a * v.N + i], v.X[a * v.N + j]);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return sqrt(s);
+}
+
+// ---------------------------------------------------------------- pattern
+
+__global__ void k_pc_pattern(HierView v, const int64_t* Arp, const int32_t* Acol, const int32_t* perm, int32_t* nbr) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= v.N) return;
+    const int32_t ps = perm[s];
+    double bd[kPcK];
+    int32_t bp[kPcK], bc[kPcK];
+    int cnt = 0;
+    for (int64_t k = Arp[s]; k < Arp[s + 1]; ++k) {
+        const int32_t c = Acol[k];
+        const int32_t pc = perm[c];
+        if (pc >= ps) continue;
+        const double d = dist_rn(v, c, s);
+        // insertion into the sorted list keyed by (distance, input index)
+        int pos = cnt < kPcK ? cnt : kPcK;
+        while (pos > 0 && (bd[pos - 1] > d || (bd[pos - 1] == d && bp[pos - 1] > pc))) {
+            if (pos < kPcK) { bd[pos] = bd[pos - 1]; bp[pos] = bp[pos - 1]; bc[pos] = bc[pos - 1]; }
+            --pos;
+        }
+        if (pos < kPcK) {
+            bd[pos] = d;
+            bp[pos] = pc;
+            bc[pos] = c;
+            if (cnt < kPcK) ++cnt;
+        }
+    }
+    for (int i = 0; i < kPcK; ++i) nbr[s * kPcK + i] = i < cnt ? bc[i] : -1;
+}
+
+// ---------------------------------------------------------------- exact rows (FP64)
+
+// Scale-free FSAI row of sorted row s (self first, zeros past the pattern):
+// K = phi(|x_a - x_b| / delta) on the patch, K z = e_1 by Cholesky, ghat = z / sqrt(z_0).
+__device__ void pc_exact_row(const HierView& v, const int32_t* nbr, int64_t s, double* ghat) {
+    const int l = level_of_row(v.off, v.L, s);
+    const double inv = 1.0 / v.delta[l];
+    int64_t P[kPcOut];
+    int m = 1;
+    P[0] = s;
+    for (int i = 0; i < kPcK; ++i) {
+        const int32_t c = nbr[s * kPcK + i];
+        if (c >= 0) P[m++] = c;
+    }
+    double L[kPcOut * kPcOut];
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b <= a; ++b) L[a * kPcOut + b] = wendland_eval<double>(v.w, dist_rn(v, P[a], P[b]) * inv);
+    bool ok = true;
+    for (int j = 0; j < m && ok; ++j) {
+        double dsum = L[j * kPcOut + j];
+        for (int k = 0; k < j; ++k) dsum -= L[j * kPcOut + k] * L[j * kPcOut + k];
+        if (!(dsum > 0.0)) { ok = false; break; }
+        const double ljj = sqrt(dsum);
+        L[j * kPcOut + j] = ljj;
+        for (int i = j + 1; i < m; ++i) {
+            double t = L[i * kPcOut + j];
+            for (int k = 0; k < j; ++k) t -= L[i * kPcOut + k] * L[j * kPcOut + k];
+            L[i * kPcOut + j] = t / ljj;
+        }
+    }
+    for (int a = 0; a < kPcOut; ++a) ghat[a] = 0.0;
+    if (!ok) {  // numerically singular patch: keep the diagonal scaling only
+        ghat[0] = 1.0 / sqrt(wendland_eval<double>(v.w, 0.0));
+        return;
+    }
+    double y[kPcOut], z[kPcOut];
+    for (int i = 0; i < m; ++i) {  // L y = e_1
+        double t = (i == 0) ? 1.0 : 0.0;
+        for (int k = 0; k < i; ++k) t -= L[i * kPcOut + k] * y[k];
+        y[i] = t / L[i * kPcOut + i];
+    }
+    for (int i = m - 1; i >= 0; --i) {  // L^T z = y
+        double t = y[i];
+        for (int k = i + 1; k < m; ++k) t -= L[k * kPcOut + i] * z[k];
+        z[i] = t / L[i * kPcOut + i];
+    }
+    const double sc = 1.0 / sqrt(z[0]);
+    for (int a = 0; a < m; ++a) ghat[a] = z[a] * sc;
+}
+
+// rows[i] (sorted positions; rows == nullptr: row = i) -> ghat[i][17]; optional G values.
+__global__ void k_pc_exact(HierView v, const int32_t* nbr, const int64_t* rows, int64_t n, double* ghat_out,
+                           float* gval, int32_t* gcol) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t s = rows ? rows[i] : i;
+    double g[kPcOut];
+    pc_exact_row(v, nbr, s, g);
+    if (ghat_out)
+        for (int a = 0; a < kPcOut; ++a) ghat_out[i * kPcOut + a] = g[a];
+    if (gval) {
+        const int l = level_of_row(v.off, v.L, s);
+        const double sc = pow(v.delta[l], 0.5 * v.d);
+        gcol[s * kPcOut] = (int32_t)s;
+        gval[s * kPcOut] = (float)(sc * g[0]);
+        for (int k = 0; k < kPcK; ++k) {
+            const int32_t c = nbr[s * kPcK + k];
+            gcol[s * kPcOut + 1 + k] = c;
+            gval[s * kPcOut + 1 + k] = c >= 0 ? (float)(sc * g[1 + k]) : 0.f;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- features
+
+__device__ __forceinline__ int pc_features(const HierView& v, const int32_t* nbr, int64_t s, float* z) {
+    const int l = level_of_row(v.off, v.L, s);
+    const double inv = 1.0 / v.delta[l];
+    int cnt = 0;
+    for (int k = 0; k < kPcK; ++k) {
+        const int32_t c = nbr[s * kPcK + k];
+        for (int a = 0; a < v.d; ++a)
+            z[k * v.d + a] = c >= 0 ? (float)((v.X[a * v.N + c] - v.X[a * v.N + s]) * inv) : 0.f;
+        cnt += c >= 0;
+    }
+    return cnt;
+}
+
+__global__ void k_pc_features(HierView v, const int32_t* nbr, const int64_t* rows, int64_t n, float* Z, int32_t* cnt) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float z[kPcK * 3];
+    const int c = pc_features(v, nbr, rows[i], z);
+    const int nin = kPcK * v.d;
+    for (int k = 0; k < nin; ++k) Z[i * nin + k] = z[k];
+    cnt[i] = c;
+}
+
+// Scaled patch matrix K = phi(|x_a - x_b| / delta) of sample i (self first, zero-padded to 17x17):
+// the metric of the training loss.
+__global__ void k_pc_patchK(HierView v, const int32_t* nbr, const int64_t* rows, int64_t n, float* K) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t s = rows[i];
+    const int l = level_of_row(v.off, v.L, s);
+    const double inv = 1.0 / v.delta[l];
+    int64_t P[kPcOut];
+    int m = 1;
+    P[0] = s;
+    for (int k = 0; k < kPcK; ++k) {
+        const int32_t c = nbr[s * kPcK + k];
+        if (c >= 0) P[m++] = c;
+    }
+    float* Ki = K + i * kPcOut * kPcOut;
+    for (int a = 0; a < kPcOut; ++a)
+        for (int b = 0; b < kPcOut; ++b)
+            Ki[a * kPcOut + b] = (a < m && b < m) ? (float)wendland_eval<double>(v.w, dist_rn(v, P[a], P[b]) * inv) : 0.f;
+}
+
+// standardised targets T = (ghat - mu) / sigma (zero where masked)
+__global__ void k_pc_moments(const double* ghat, const int32_t* cnt, int64_t n, float* musig) {
+    const int m = blockIdx.x;  // one block per output
+    __shared__ double sh[3][256];
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        if (m <= cnt[i]) {
+            const double g = ghat[i * kPcOut + m];
+            s0 += 1.0;
+            s1 += g;
+            s2 += g * g;
+        }
+    }
+    sh[0][threadIdx.x] = s0;
+    sh[1][threadIdx.x] = s1;
+    sh[2][threadIdx.x] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, c = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) { a += sh[0][t]; b += sh[1][t]; c += sh[2][t]; }
+        const double mu = a > 0 ? b / a : 0.0;
+        const double var = a > 0 ? fmax(c / a - mu * mu, 0.0) : 1.0;
+        musig[m] = (float)mu;
+        musig[kPcOut + m] = (float)sqrt(fmax(var, 1e-30));
+    }
+}
+
+__global__ void k_pc_targets(const double* ghat, const int32_t* cnt, int64_t n, const float* musig, float* T) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int m = 0; m < kPcOut; ++m)
+        T[i * kPcOut + m] = m <= cnt[i] ? (float)((ghat[i * kPcOut + m] - musig[m]) / musig[kPcOut + m]) : 0.f;
+}
+
+// ---------------------------------------------------------------- network
+
+// parameter offsets: W1 [64][nin], b1 [64], W2 [64][64], b2 [64], W3 [17][64], b3 [17]
+struct NetLayout {
+    int nin, oW1, ob1, oW2, ob2, oW3, ob3, P;
+};
+__host__ __device__ inline NetLayout net_layout(int nin) {
+    NetLayout L;
+    L.nin = nin;
+    L.oW1 = 0;
+    L.ob1 = L.oW1 + kPcHidden * nin;
+    L.oW2 = L.ob1 + kPcHidden;
+    L.ob2 = L.oW2 + kPcHidden * kPcHidden;
+    L.oW3 = L.ob2 + kPcHidden;
+    L.ob3 = L.oW3 + kPcOut * kPcHidden;
+    L.P = L.ob3 + kPcOut;
+    return L;
+}
+
+// o = W3 relu(W2 relu(W1 z + b1) + b2) + b3 for one sample; W in shared memory.
+__device__ __forceinline__ void mlp_forward(const NetLayout& N, const float* W, const float* z, float* o) {
+    float h1[kPcHidden];
+#pragma unroll
+    for (int j = 0; j < kPcHidden; ++j) h1[j] = W[N.ob1 + j];
+    for (int k = 0; k < N.nin; ++k) {
+        const float zk = z[k];
+#pragma unroll
+        for (int j = 0; j < kPcHidden; ++j) h1[j] = fmaf(W[N.oW1 + j * N.nin + k], zk, h1[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < kPcHidden; ++j) h1[j] = fmaxf(h1[j], 0.f);
+#pragma unroll
+    for (int m = 0; m < kPcOut; ++m) o[m] = W[N.ob3 + m];
+    for (int j = 0; j < kPcHidden; ++j) {
+        float a = W[N.ob2 + j];
+#pragma unroll
+        for (int k = 0; k < kPcHidden; ++k) a = fmaf(W[N.oW2 + j * kPcHidden + k], h1[k], a);
+        a = fmaxf(a, 0.f);
+#pragma unroll
+        for (int m = 0; m < kPcOut; ++m) o[m] = fmaf(W[N.oW3 + m * kPcHidden + j], a, o[m]);
+    }
+}
+
+// Network prediction of the scale-free rows: ghat = mu + sigma o, diagonal clamped to
+// >= 0.1 mu_0 (keeps G's diagonal positive), outputs of missing neighbours zero.
+// Writes G = delta^{d/2} ghat (FP32) and the row pattern, or ghat itself for inspection.
+__global__ void k_pc_infer(HierView v, const int32_t* nbr, const float* theta, int nparams, const float* musig,
+                           float* gval, int32_t* gcol, float* ghat_out) {
+    extern __shared__ float W[];
+    for (int i = threadIdx.x; i < nparams; i += blockDim.x) W[i] = theta[i];
+    __shared__ float ms[2 * kPcOut];
+    if (threadIdx.x < 2 * kPcOut) ms[threadIdx.x] = musig[threadIdx.x];
+    __syncthreads();
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= v.N) return;
+    const NetLayout N = net_layout(kPcK * v.d);
+    float z[kPcK * 3], o[kPcOut];
+    const int cnt = pc_features(v, nbr, s, z);
+    mlp_forward(N, W, z, o);
+    float g[kPcOut];
+    for (int m = 0; m < kPcOut; ++m) g[m] = m <= cnt ? fmaf(ms[kPcOut + m], o[m], ms[m]) : 0.f;
+    g[0] = fmaxf(g[0], 0.1f * ms[0]);
+    if (ghat_out) {
+        // inspection: by pattern slot (slot k+1 <-> nbr[s][k])
+        ghat_out[s * kPcOut] = g[0];
+        int q = 1;
+        for (int k = 0; k < kPcK; ++k) ghat_out[s * kPcOut + 1 + k] = nbr[s * kPcK + k] >= 0 ? g[q++] : 0.f;
+        return;
+    }
+    const int l = level_of_row(v.off, v.L, s);
+    const float sc = (float)pow(v.delta[l], 0.5 * v.d);
+    gcol[s * kPcOut] = (int32_t)s;
+    gval[s * kPcOut] = sc * g[0];
+    int q = 1;
+    for (int k = 0; k < kPcK; ++k) {
+        const int32_t c = nbr[s * kPcK + k];
+        gcol[s * kPcOut + 1 + k] = c;
+        gval[s * kPcOut + 1 + k] = c >= 0 ? sc * g[q++] : 0.f;
+    }
+}
+
+// One block = kTB samples of a step: forward, backward, per-block gradient partial.
+// Sample j of the step is training sample (a_mul * ((step * batch + j) mod S) + a_add) mod S;
+// samples with (step * batch + j) >= limit are skipped (full-batch inspection).
+// Loss: sum over the block's samples of d^T K d, d = sigma * (o - t) on the valid outputs
+// (K: the sample's scaled patch matrix); escale = 2 / (samples of the step).
+__global__ void k_pc_train(const float* Z, const float* T, const int32_t* cnt, const float* Kp, const float* musig,
+                           int64_t S, int nin, const float* theta, int batch, int64_t step, uint64_t a_mul,
+                           uint64_t a_add, int64_t limit, float escale, float* grad_part, double* loss_part) {
+    extern __shared__ float sm[];
+    const NetLayout N = net_layout(nin);
+    float* W = sm;
+    float* X = W + N.P;
+    float* A1 = X + kTB * nin;
+    float* A2 = A1 + kTB * kPcHidden;
+    float* E = A2 + kTB * kPcHidden;
+    float* D2 = E + kTB * kPcOut;
+    float* D1 = D2 + kTB * kPcHidden;
+    float* Dd = D1 + kTB * kPcHidden;  // d = sigma (o - t), masked
+    __shared__ double lsum[256];
+    __shared__ int64_t sidx[kTB];
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int i = t; i < N.P; i += nt) W[i] = theta[i];
+    if (t < kTB) {
+        const int64_t g = step * batch + (int64_t)blockIdx.x * kTB + t;
+        sidx[t] = g < limit ? (int64_t)((a_mul * (uint64_t)(g % S) + a_add) % (uint64_t)S) : -1;
+    }
+    __syncthreads();
+    for (int i = t; i < kTB * nin; i += nt) {
+        const int s = i / nin, k = i % nin;
+        X[i] = sidx[s] >= 0 ? Z[sidx[s] * nin + k] : 0.f;
+    }
+    __syncthreads();
+    // layer 1
+    for (int i = t; i < kTB * kPcHidden; i += nt) {
+        const int s = i / kPcHidden, j = i % kPcHidden;
+        float a = W[N.ob1 + j];
+        for (int k = 0; k < nin; ++k) a = fmaf(W[N.oW1 + j * nin + k], X[s * nin + k], a);
+        A1[i] = a;
+    }
+    __syncthreads();
+    // layer 2
+    for (int i = t; i < kTB * kPcHidden; i += nt) {
+        const int s = i / kPcHidden, j = i % kPcHidden;
+        float a = W[N.ob2 + j];
+        for (int k = 0; k < kPcHidden; ++k) a = fmaf(W[N.oW2 + j * kPcHidden + k], fmaxf(A1[s * kPcHidden + k], 0.f), a);
+        A2[i] = a;
+    }
+    __syncthreads();
+    // output, its scaled error d, and the energy-norm error signal E = escale sigma (K d)
+    for (int i = t; i < kTB * kPcOut; i += nt) {
+        const int s = i / kPcOut, m = i % kPcOut;
+        float dv = 0.f;
+        if (sidx[s] >= 0 && m <= cnt[sidx[s]]) {
+            float o = W[N.ob3 + m];
+            for (int j = 0; j < kPcHidden; ++j) o = fmaf(W[N.oW3 + m * kPcHidden + j], fmaxf(A2[s * kPcHidden + j], 0.f), o);
+            dv = musig[kPcOut + m] * (o - T[sidx[s] * kPcOut + m]);
+        }
+        Dd[i] = dv;
+    }
+    __syncthreads();
+    double lacc = 0.0;
+    for (int i = t; i < kTB * kPcOut; i += nt) {
+        const int s = i / kPcOut, m = i % kPcOut;
+        float e = 0.f;
+        if (sidx[s] >= 0 && m <= cnt[sidx[s]]) {
+            const float* Km = Kp + (sidx[s] * kPcOut + m) * kPcOut;
+            float kd = 0.f;
+            for (int q = 0; q < kPcOut; ++q) kd = fmaf(Km[q], Dd[s * kPcOut + q], kd);
+            lacc += (double)Dd[i] * (double)kd;
+            e = escale * musig[kPcOut + m] * kd;
+        }
+        E[i] = e;
+    }
+    lsum[t] = lacc;
+    __syncthreads();
+    // backward through layers 3 and 2
+    for (int i = t; i < kTB * kPcHidden; i += nt) {
+        const int s = i / kPcHidden, j = i % kPcHidden;
+        float a = 0.f;
+        for (int m = 0; m < kPcOut; ++m) a = fmaf(E[s * kPcOut + m], W[N.oW3 + m * kPcHidden + j], a);
+        D2[i] = A2[i] > 0.f ? a : 0.f;
+    }
+    __syncthreads();
+    for (int i = t; i < kTB * kPcHidden; i += nt) {
+        const int s = i / kPcHidden, k = i % kPcHidden;
+        float a = 0.f;
+        for (int j = 0; j < kPcHidden; ++j) a = fmaf(D2[s * kPcHidden + j], W[N.oW2 + j * kPcHidden + k], a);
+        D1[i] = A1[i] > 0.f ? a : 0.f;
+    }
+    __syncthreads();
+    // parameter gradients (sums over the block's samples in sample order)
+    float* gp = grad_part + (size_t)blockIdx.x * N.P;
+    for (int p = t; p < N.P; p += nt) {
+        float g = 0.f;
+        if (p < N.ob1) {
+            const int j = p / nin, k = p % nin;
+            for (int s = 0; s < kTB; ++s) g = fmaf(D1[s * kPcHidden + j], X[s * nin + k], g);
+        } else if (p < N.oW2) {
+            const int j = p - N.ob1;
+            for (int s = 0; s < kTB; ++s) g += D1[s * kPcHidden + j];
+        } else if (p < N.ob2) {
+            const int j = (p - N.oW2) / kPcHidden, k = (p - N.oW2) % kPcHidden;
+            for (int s = 0; s < kTB; ++s) g = fmaf(D2[s * kPcHidden + j], fmaxf(A1[s * kPcHidden + k], 0.f), g);
+        } else if (p < N.oW3) {
+            const int j = p - N.ob2;
+            for (int s = 0; s < kTB; ++s) g += D2[s * kPcHidden + j];
+        } else if (p < N.ob3) {
+            const int m = (p - N.oW3) / kPcHidden, j = (p - N.oW3) % kPcHidden;
+            for (int s = 0; s < kTB; ++s) g = fmaf(E[s * kPcOut + m], fmaxf(A2[s * kPcHidden + j], 0.f), g);
+        } else {
+            const int m = p - N.ob3;
+            for (int s = 0; s < kTB; ++s) g += E[s * kPcOut + m];
+        }
+        gp[p] = g;
+    }
+    if (t == 0) {
+        double a = 0.0;
+        for (int i = 0; i < nt; ++i) a += lsum[i];
+        loss_part[blockIdx.x] = a;
+    }
+}
+
+// Sum the per-block partials (fixed order) and take one Adam step on the FP32 master
+// weights; refresh their BF16-rounded copies.  grad_out (optional) receives the gradient.
+__global__ void k_pc_adam(float* theta, float* theta_bf, float* m1, float* m2, const float* grad_part, int nb, int P,
+                          float lr, float bc1, float bc2, const double* loss_part, double* loss_out, double lscale,
+                          float* grad_out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0 && loss_out) {
+        double a = 0.0;
+        for (int b = 0; b < nb; ++b) a += loss_part[b];
+        *loss_out = a * lscale;
+    }
+    if (p >= P) return;
+    float g = 0.f;
+    for (int b = 0; b < nb; ++b) g += grad_part[(size_t)b * P + p];
+    if (grad_out) {
+        grad_out[p] = g;
+        return;
+    }
+    const float a = 0.9f * m1[p] + 0.1f * g;
+    const float b2 = 0.999f * m2[p] + 0.001f * g * g;
+    m1[p] = a;
+    m2[p] = b2;
+    const float th = theta[p] - lr * (a / bc1) / (sqrtf(b2 / bc2) + 1e-8f);
+    theta[p] = th;
+    theta_bf[p] = __bfloat162float(__float2bfloat16_rn(th));
+}
+
+__global__ void k_bf16_round(const float* in, float* out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __bfloat162float(__float2bfloat16_rn(in[i]));
+}
+
+// ---------------------------------------------------------------- transpose of G
+
+__global__ void k_gt_count(const int32_t* gcol, int64_t N, int32_t* cnt) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    for (int k = 0; k < kPcOut; ++k) {
+        const int32_t c = gcol[s * kPcOut + k];
+        if (c >= 0) atomicAdd(&cnt[c], 1);
+    }
+}
+__global__ void k_gt_fill(const int32_t* gcol, const float* gval, int64_t N, const int64_t* rp, int32_t* cursor,
+                          int32_t* col, float* val) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    for (int k = 0; k < kPcOut; ++k) {
+        const int32_t c = gcol[s * kPcOut + k];
+        if (c < 0) continue;
+        const int64_t pos = rp[c] + atomicAdd(&cursor[c], 1);
+        col[pos] = (int32_t)s;
+        val[pos] = gval[s * kPcOut + k];
+    }
+}
+// deterministic order inside each row of G^T: by source row
+__global__ void k_gt_sort(const int64_t* rp, int32_t* col, float* val, int64_t N) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int64_t s = rp[c], e = rp[c + 1];
+    for (int64_t i = s + 1; i < e; ++i) {
+        const int32_t kc = col[i];
+        const float kv = val[i];
+        int64_t j = i - 1;
+        while (j >= s && col[j] > kc) {
+            col[j + 1] = col[j];
+            val[j + 1] = val[j];
+            --j;
+        }
+        col[j + 1] = kc;
+        val[j + 1] = kv;
+    }
+}
+
+__global__ void k_scan_rows(const int32_t* cnt, int64_t N, int64_t* rp) {
+    // single-block exclusive scan (the in-degrees are small; N up to a few million)
+    __shared__ int64_t part[1024];
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int64_t per = (N + nt - 1) / nt;
+    const int64_t b = t * per, e = std::min<int64_t>(N, b + per);
+    int64_t s = 0;
+    for (int64_t i = b; i < e; ++i) s += cnt[i];
+    part[t] = s;
+    __syncthreads();
+    if (t == 0) {
+        int64_t acc = 0;
+        for (int i = 0; i < nt; ++i) {
+            const int64_t v = part[i];
+            part[i] = acc;
+            acc += v;
+        }
+        rp[N] = acc;
+    }
+    __syncthreads();
+    int64_t acc = part[t];
+    for (int64_t i = b; i < e; ++i) {
+        rp[i] = acc;
+        acc += cnt[i];
+    }
+}
+
+uint64_t sm64(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+double u01(uint64_t seed, uint64_t i) { return (double)(sm64(seed, i) >> 11) * (1.0 / 9007199254740992.0); }
+
+uint64_t gcd64(uint64_t a, uint64_t b) {
+    while (b) {
+        const uint64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+ms_status pc_alloc(ms_hierarchy* h) {
+    Precond& pc = h->pc;
+    if (pc.nbr) return MS_OK;
+    pc.n_in = kPcK * h->d;
+    pc.n_params = net_layout(pc.n_in).P;
+    const int64_t N = h->N;
+    MS_TRY(ms_alloc(h, (void**)&pc.nbr, sizeof(int32_t) * N * kPcK));
+    MS_TRY(ms_alloc(h, (void**)&pc.gcol, sizeof(int32_t) * N * kPcOut));
+    MS_TRY(ms_alloc(h, (void**)&pc.gval, sizeof(float) * N * kPcOut));
+    MS_TRY(ms_alloc(h, (void**)&pc.gt_rp, sizeof(int64_t) * (N + 1)));
+    MS_TRY(ms_alloc(h, (void**)&pc.gt_col, sizeof(int32_t) * N * kPcOut));
+    MS_TRY(ms_alloc(h, (void**)&pc.gt_val, sizeof(float) * N * kPcOut));
+    MS_TRY(ms_alloc(h, (void**)&pc.theta, sizeof(float) * pc.n_params));
+    MS_TRY(ms_alloc(h, (void**)&pc.theta_bf, sizeof(float) * pc.n_params));
+    MS_TRY(ms_alloc(h, (void**)&pc.adam_m, sizeof(float) * pc.n_params));
+    MS_TRY(ms_alloc(h, (void**)&pc.adam_v, sizeof(float) * pc.n_params));
+    MS_TRY(ms_alloc(h, (void**)&pc.musig, sizeof(float) * 2 * kPcOut));
+    MS_TRY(ms_alloc(h, (void**)&h->u32, sizeof(float) * N));
+    MS_TRY(ms_alloc(h, (void**)&h->u1_32, sizeof(float) * N));
+    return MS_OK;
+}
+
+ms_status pc_pattern(ms_hierarchy* h, cudaStream_t st) {
+    MS_TRY(pc_alloc(h));
+    k_pc_pattern<<<nblk(h->N, 128), 128, 0, st>>>(h->view, h->A.rp, h->A.col, h->perm, h->pc.nbr);
+    ms_count_launch();
+    MS_CUDA(cudaGetLastError());
+    return MS_OK;
+}
+
+// sorted rows of the given (0-based) levels, in level order
+std::vector<int64_t> level_rows(const ms_hierarchy* h, const int* levels, int n) {
+    std::vector<int64_t> rows;
+    for (int i = 0; i < n; ++i) {
+        const int l = levels[i];
+        for (int64_t s = h->view.off[l]; s < h->view.off[l + 1]; ++s) rows.push_back(s);
+    }
+    return rows;
+}
+
+ms_status check_levels(const ms_hierarchy* h, const int* levels, int n) {
+    if (n < 1 || !levels) {
+        ms_set_error(MS_ERR_ARG, "at least one training level is required");
+        return MS_ERR_ARG;
+    }
+    for (int i = 0; i < n; ++i)
+        if (levels[i] < 0 || levels[i] >= h->L) {
+            ms_set_error(MS_ERR_ARG, "level %d out of range 0..%d", levels[i], h->L - 1);
+            return MS_ERR_ARG;
+        }
+    return MS_OK;
+}
+
+// Training samples of the chosen levels: features, counts, exact targets, standardisation.
+struct TrainSet {
+    int64_t S = 0;
+    std::vector<void*> bufs;
+    float *Z = nullptr, *T = nullptr, *K = nullptr;
+    int32_t* cnt = nullptr;
+    double* ghat = nullptr;
+    int64_t* rows = nullptr;
+    ~TrainSet() {
+        for (void* p : bufs) cudaFree(p);
+    }
+    ms_status alloc(void** p, size_t b) {
+        cudaError_t e = cudaMalloc(p, std::max<size_t>(b, 16));
+        if (e != cudaSuccess) {
+            ms_set_error(MS_ERR_OOM, "device allocation of %zu bytes failed", b);
+            return MS_ERR_OOM;
+        }
+        bufs.push_back(*p);
+        return MS_OK;
+    }
+};
+
+ms_status make_trainset(ms_hierarchy* h, const int* levels, int n, bool set_moments, TrainSet& ts, cudaStream_t st) {
+    MS_TRY(check_levels(h, levels, n));
+    MS_TRY(pc_pattern(h, st));
+    std::vector<int64_t> rows = level_rows(h, levels, n);
+    ts.S = (int64_t)rows.size();
+    const int nin = h->pc.n_in;
+    MS_TRY(ts.alloc((void**)&ts.rows, sizeof(int64_t) * ts.S));
+    MS_TRY(ts.alloc((void**)&ts.Z, sizeof(float) * ts.S * nin));
+    MS_TRY(ts.alloc((void**)&ts.T, sizeof(float) * ts.S * kPcOut));
+    MS_TRY(ts.alloc((void**)&ts.cnt, sizeof(int32_t) * ts.S));
+    MS_TRY(ts.alloc((void**)&ts.ghat, sizeof(double) * ts.S * kPcOut));
+    MS_TRY(ts.alloc((void**)&ts.K, sizeof(float) * ts.S * kPcOut * kPcOut));
+    MS_CUDA(cudaMemcpyAsync(ts.rows, rows.data(), sizeof(int64_t) * ts.S, cudaMemcpyHostToDevice, st));
+    k_pc_features<<<nblk(ts.S, 128), 128, 0, st>>>(h->view, h->pc.nbr, ts.rows, ts.S, ts.Z, ts.cnt);
+    k_pc_patchK<<<nblk(ts.S, 128), 128, 0, st>>>(h->view, h->pc.nbr, ts.rows, ts.S, ts.K);
+    ms_count_launch(2);
+    k_pc_exact<<<nblk(ts.S, 64), 64, 0, st>>>(h->view, h->pc.nbr, ts.rows, ts.S, ts.ghat, nullptr, nullptr);
+    ms_count_launch();
+    if (set_moments) {
+        k_pc_moments<<<kPcOut, 256, 0, st>>>(ts.ghat, ts.cnt, ts.S, h->pc.musig);
+        ms_count_launch();
+    }
+    k_pc_targets<<<nblk(ts.S, 128), 128, 0, st>>>(ts.ghat, ts.cnt, ts.S, h->pc.musig, ts.T);
+    ms_count_launch();
+    MS_CUDA(cudaGetLastError());
+    return MS_OK;
+}
+
+size_t train_smem(int nin) {
+    const NetLayout N = net_layout(nin);
+    return sizeof(float) * ((size_t)N.P + kTB * nin + 4 * kTB * kPcHidden + 2 * kTB * kPcOut);
+}
+
+ms_status set_train_smem(int nin) {
+    MS_CUDA(cudaFuncSetAttribute(k_pc_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)train_smem(nin)));
+    return MS_OK;
+}
+
+}  // namespace
+
+// Build G (and its transpose) for the requested kind; cached until the weights change.
+ms_status ms_pc_build(ms_hierarchy* h, int kind, cudaStream_t st) {
+    if (h->pc.built_kind == kind) return MS_OK;
+    if (kind == MS_PRECOND_LEARNED && !h->pc.trained) {
+        ms_set_error(MS_ERR_STATE, "precond = LEARNED needs a trained network (ms_train_precond or ms_precond_params)");
+        return MS_ERR_STATE;
+    }
+    MS_TRY(pc_pattern(h, st));
+    Precond& pc = h->pc;
+    const int64_t N = h->N;
+    if (kind == MS_PRECOND_EXACT) {
+        k_pc_exact<<<nblk(N, 64), 64, 0, st>>>(h->view, pc.nbr, nullptr, N, nullptr, pc.gval, pc.gcol);
+    } else {
+        const size_t smem = sizeof(float) * pc.n_params;
+        MS_CUDA(cudaFuncSetAttribute(k_pc_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_pc_infer<<<nblk(N, 128), 128, smem, st>>>(h->view, pc.nbr, pc.fp32_weights ? pc.theta : pc.theta_bf,
+                                                    pc.n_params, pc.musig, pc.gval, pc.gcol, nullptr);
+    }
+    ms_count_launch();
+    MS_CUDA(cudaGetLastError());
+    // transpose (in-pattern) for z = G^T u
+    int32_t* cnt = nullptr;
+    MS_CUDA(cudaMallocAsync((void**)&cnt, sizeof(int32_t) * (N + 1), st));
+    MS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (N + 1), st));
+    k_gt_count<<<nblk(N, 256), 256, 0, st>>>(pc.gcol, N, cnt);
+    k_scan_rows<<<1, 1024, 0, st>>>(cnt, N, pc.gt_rp);
+    MS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (N + 1), st));
+    k_gt_fill<<<nblk(N, 256), 256, 0, st>>>(pc.gcol, pc.gval, N, pc.gt_rp, cnt, pc.gt_col, pc.gt_val);
+    k_gt_sort<<<nblk(N, 256), 256, 0, st>>>(pc.gt_rp, pc.gt_col, pc.gt_val, N);
+    ms_count_launch(4);
+    MS_CUDA(cudaFreeAsync(cnt, st));
+    MS_CUDA(cudaGetLastError());
+    pc.built_kind = kind;
+    return MS_OK;
+}
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+void ms_default_train_opts(ms_train_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->epochs = 300;
+    o->batch = 512;
+    o->lr = 3e-3;
+    o->lr_final = 1e-4;
+    o->seed = 2503049140ull;
+}
+
+ms_status ms_train_precond(ms_hierarchy* h, const int* levels, int n_levels, const ms_train_opts* opts,
+                           ms_train_stats* stats) {
+    if (!h) {
+        ms_set_error(MS_ERR_ARG, "NULL handle");
+        return MS_ERR_ARG;
+    }
+    ms_train_opts o;
+    ms_default_train_opts(&o);
+    if (opts) o = *opts;
+    if (o.epochs < 1 || o.batch < kTB || o.batch % kTB != 0 || !(o.lr > 0.0)) {
+        ms_set_error(MS_ERR_ARG, "epochs >= 1, batch a positive multiple of %d and lr > 0 are required", kTB);
+        return MS_ERR_ARG;
+    }
+    cudaStream_t st;
+    MS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+    } guard{st};
+    MS_TRY(pc_alloc(h));
+    Precond& pc = h->pc;
+    TrainSet ts;
+    MS_TRY(make_trainset(h, levels, n_levels, true, ts, st));
+    // initial weights: U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from SplitMix64(seed), parameter order
+    const NetLayout N = net_layout(pc.n_in);
+    std::vector<float> th(N.P);
+    for (int p = 0; p < N.P; ++p) {
+        const int fan = p < N.oW2 ? pc.n_in : kPcHidden;
+        const double b = 1.0 / std::sqrt((double)fan);
+        th[p] = (float)(-b + 2.0 * b * u01(o.seed, (uint64_t)p));
+    }
+    MS_CUDA(cudaMemcpyAsync(pc.theta, th.data(), sizeof(float) * N.P, cudaMemcpyHostToDevice, st));
+    MS_CUDA(cudaMemsetAsync(pc.adam_m, 0, sizeof(float) * N.P, st));
+    MS_CUDA(cudaMemsetAsync(pc.adam_v, 0, sizeof(float) * N.P, st));
+    k_bf16_round<<<nblk(N.P, 256), 256, 0, st>>>(pc.theta, pc.theta_bf, N.P);
+    ms_count_launch();
+    pc.fp32_weights = o.fp32_weights;
+    MS_TRY(set_train_smem(pc.n_in));
+    const int nb = o.batch / kTB;
+    const int64_t steps_per_epoch = (ts.S + o.batch - 1) / o.batch;
+    const int64_t steps = steps_per_epoch * o.epochs;
+    float* grad_part = nullptr;
+    double *loss_part = nullptr, *loss_hist = nullptr;
+    MS_TRY(ts.alloc((void**)&grad_part, sizeof(float) * nb * N.P));
+    MS_TRY(ts.alloc((void**)&loss_part, sizeof(double) * nb));
+    MS_TRY(ts.alloc((void**)&loss_hist, sizeof(double) * 2));
+    cudaEvent_t e0, e1;
+    MS_CUDA(cudaEventCreate(&e0));
+    MS_CUDA(cudaEventCreate(&e1));
+    MS_CUDA(cudaEventRecord(e0, st));
+    const size_t smem = train_smem(pc.n_in);
+    const float escale = 2.0f / (float)o.batch;
+    const double lscale = 1.0 / (double)o.batch;
+    const double lr_final = o.lr_final > 0 ? o.lr_final : o.lr / 30.0;
+    uint64_t a_mul = 1, a_add = 0;
+    for (int64_t step = 0; step < steps; ++step) {
+        const int64_t epoch = step / steps_per_epoch;
+        if (step % steps_per_epoch == 0) {  // new affine shuffle of the samples for this epoch
+            a_mul = (sm64(o.seed ^ 0x5DEECE66Dull, 2 * epoch) % (uint64_t)ts.S) | 1ull;
+            while (gcd64(a_mul, (uint64_t)ts.S) != 1) a_mul += 2;
+            a_add = sm64(o.seed ^ 0x5DEECE66Dull, 2 * epoch + 1) % (uint64_t)ts.S;
+        }
+        const double frac = (double)step / (double)std::max<int64_t>(steps - 1, 1);
+        const float lr = (float)(lr_final + 0.5 * (o.lr - lr_final) * (1.0 + std::cos(M_PI * frac)));
+        const int64_t local = step % steps_per_epoch;
+        k_pc_train<<<nb, 256, smem, st>>>(ts.Z, ts.T, ts.cnt, ts.K, pc.musig, ts.S, pc.n_in,
+                                          o.fp32_weights ? pc.theta : pc.theta_bf, o.batch, local, a_mul, a_add,
+                                          INT64_MAX, escale, grad_part, loss_part);
+        const float bc1 = 1.0f - std::pow(0.9f, (float)(step + 1)), bc2 = 1.0f - std::pow(0.999f, (float)(step + 1));
+        double* lo = step == 0 ? loss_hist : (step == steps - 1 ? loss_hist + 1 : nullptr);
+        k_pc_adam<<<nblk(N.P, 256), 256, 0, st>>>(pc.theta, pc.theta_bf, pc.adam_m, pc.adam_v, grad_part, nb, N.P, lr,
+                                                  bc1, bc2, loss_part, lo, lscale, nullptr);
+        ms_count_launch(2);
+    }
+    MS_CUDA(cudaGetLastError());
+    MS_CUDA(cudaEventRecord(e1, st));
+    double lh[2] = {0, 0};
+    MS_CUDA(cudaMemcpyAsync(lh, loss_hist, sizeof(lh), cudaMemcpyDeviceToHost, st));
+    MS_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    pc.trained = true;
+    pc.built_kind = 0;
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->samples = ts.S;
+        stats->steps = steps;
+        stats->loss_first = lh[0];
+        stats->loss_last = steps > 1 ? lh[1] : lh[0];
+        stats->train_ms = ms;
+        stats->n_params = N.P;
+    }
+    return MS_OK;
+}
+
+ms_status ms_precond_params(ms_hierarchy* h, float* params, int64_t n, int set) {
+    if (!h || !params) {
+        ms_set_error(MS_ERR_ARG, "NULL argument");
+        return MS_ERR_ARG;
+    }
+    MS_TRY(pc_alloc(h));
+    Precond& pc = h->pc;
+    const int64_t need = pc.n_params + 2 * kPcOut;
+    if (n != need) {
+        ms_set_error(MS_ERR_ARG, "expected %lld values (%d weights + %d standardisation)", (long long)need,
+                     pc.n_params, 2 * kPcOut);
+        return MS_ERR_ARG;
+    }
+    if (set) {
+        MS_CUDA(cudaMemcpy(pc.theta, params, sizeof(float) * pc.n_params, cudaMemcpyHostToDevice));
+        MS_CUDA(cudaMemcpy(pc.musig, params + pc.n_params, sizeof(float) * 2 * kPcOut, cudaMemcpyHostToDevice));
+        k_bf16_round<<<nblk(pc.n_params, 256), 256>>>(pc.theta, pc.theta_bf, pc.n_params);
+        ms_count_launch();
+        MS_CUDA(cudaDeviceSynchronize());
+        pc.trained = true;
+        pc.built_kind = 0;
+    } else {
+        if (!pc.trained) {
+            ms_set_error(MS_ERR_STATE, "no trained network");
+            return MS_ERR_STATE;
+        }
+        MS_CUDA(cudaMemcpy(params, pc.theta, sizeof(float) * pc.n_params, cudaMemcpyDeviceToHost));
+        MS_CUDA(cudaMemcpy(params + pc.n_params, pc.musig, sizeof(float) * 2 * kPcOut, cudaMemcpyDeviceToHost));
+    }
+    return MS_OK;
+}
+
+ms_status ms_precond_inspect(ms_hierarchy* h, int what, const int* levels, int n_levels, void* out, int64_t n_out) {
+    if (!h || !out) {
+        ms_set_error(MS_ERR_ARG, "NULL argument");
+        return MS_ERR_ARG;
+    }
+    cudaStream_t st = 0;
+    const int64_t N = h->N;
+    std::vector<int32_t> perm(N);
+    MS_CUDA(cudaMemcpy(perm.data(), h->perm, sizeof(int32_t) * N, cudaMemcpyDeviceToHost));
+    MS_TRY(pc_pattern(h, st));
+    Precond& pc = h->pc;
+    if (what == MS_INSPECT_PATTERN || what == MS_INSPECT_TARGETS || what == MS_INSPECT_PREDICT) {
+        const int width = what == MS_INSPECT_PATTERN ? kPcK : kPcOut;
+        if (n_out != N * width) {
+            ms_set_error(MS_ERR_ARG, "expected %lld output values", (long long)(N * width));
+            return MS_ERR_ARG;
+        }
+        std::vector<int32_t> nb(N * kPcK);
+        MS_CUDA(cudaMemcpy(nb.data(), pc.nbr, sizeof(int32_t) * N * kPcK, cudaMemcpyDeviceToHost));
+        if (what == MS_INSPECT_PATTERN) {
+            int32_t* o = static_cast<int32_t*>(out);
+            for (int64_t s = 0; s < N; ++s)
+                for (int k = 0; k < kPcK; ++k) {
+                    const int32_t c = nb[s * kPcK + k];
+                    o[(int64_t)perm[s] * kPcK + k] = c >= 0 ? perm[c] : -1;
+                }
+            return MS_OK;
+        }
+        if (what == MS_INSPECT_TARGETS) {
+            double* d = nullptr;
+            MS_CUDA(cudaMalloc((void**)&d, sizeof(double) * N * kPcOut));
+            k_pc_exact<<<nblk(N, 64), 64>>>(h->view, pc.nbr, nullptr, N, d, nullptr, nullptr);
+            ms_count_launch();
+            std::vector<double> hd(N * kPcOut);
+            cudaError_t e = cudaMemcpy(hd.data(), d, sizeof(double) * N * kPcOut, cudaMemcpyDeviceToHost);
+            cudaFree(d);
+            MS_CUDA(e);
+            double* o = static_cast<double*>(out);
+            for (int64_t s = 0; s < N; ++s)
+                std::memcpy(o + (int64_t)perm[s] * kPcOut, hd.data() + s * kPcOut, sizeof(double) * kPcOut);
+            return MS_OK;
+        }
+        if (!pc.trained) {
+            ms_set_error(MS_ERR_STATE, "no trained network");
+            return MS_ERR_STATE;
+        }
+        float* d = nullptr;
+        MS_CUDA(cudaMalloc((void**)&d, sizeof(float) * N * kPcOut));
+        const size_t smem = sizeof(float) * pc.n_params;
+        MS_CUDA(cudaFuncSetAttribute(k_pc_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_pc_infer<<<nblk(N, 128), 128, smem>>>(h->view, pc.nbr, pc.fp32_weights ? pc.theta : pc.theta_bf,
+                                                pc.n_params, pc.musig, nullptr, nullptr, d);
+        ms_count_launch();
+        std::vector<float> hd(N * kPcOut);
+        cudaError_t e = cudaMemcpy(hd.data(), d, sizeof(float) * N * kPcOut, cudaMemcpyDeviceToHost);
+        cudaFree(d);
+        MS_CUDA(e);
+        float* o = static_cast<float*>(out);
+        for (int64_t s = 0; s < N; ++s)
+            std::memcpy(o + (int64_t)perm[s] * kPcOut, hd.data() + s * kPcOut, sizeof(float) * kPcOut);
+        return MS_OK;
+    }
+    if (what == MS_INSPECT_GRAD) {
+        // full-batch loss and gradient over the given levels with the FP32 master weights,
+        // using the current standardisation (out: n_params gradient values, then the loss)
+        if (!pc.trained) {
+            ms_set_error(MS_ERR_STATE, "no network weights");
+            return MS_ERR_STATE;
+        }
+        if (n_out != pc.n_params + 1) {
+            ms_set_error(MS_ERR_ARG, "expected %d output values", pc.n_params + 1);
+            return MS_ERR_ARG;
+        }
+        TrainSet ts;
+        MS_TRY(make_trainset(h, levels, n_levels, false, ts, st));
+        const int nb = (int)((ts.S + kTB - 1) / kTB);
+        const NetLayout Nl = net_layout(pc.n_in);
+        float *gp = nullptr, *gout = nullptr;
+        double *lp = nullptr, *lo = nullptr;
+        MS_TRY(ts.alloc((void**)&gp, sizeof(float) * nb * Nl.P));
+        MS_TRY(ts.alloc((void**)&gout, sizeof(float) * Nl.P));
+        MS_TRY(ts.alloc((void**)&lp, sizeof(double) * nb));
+        MS_TRY(ts.alloc((void**)&lo, sizeof(double)));
+        MS_TRY(set_train_smem(pc.n_in));
+        k_pc_train<<<nb, 256, train_smem(pc.n_in), st>>>(ts.Z, ts.T, ts.cnt, ts.K, pc.musig, ts.S, pc.n_in, pc.theta,
+                                                         nb * kTB, 0, 1, 0, ts.S, 2.0f / (float)ts.S, gp, lp);
+        k_pc_adam<<<nblk(Nl.P, 256), 256, 0, st>>>(nullptr, nullptr, nullptr, nullptr, gp, nb, Nl.P, 0.f, 1.f, 1.f, lp,
+                                                   lo, 1.0 / (double)ts.S, gout);
+        ms_count_launch(2);
+        MS_CUDA(cudaGetLastError());
+        float* o = static_cast<float*>(out);
+        MS_CUDA(cudaMemcpy(o, gout, sizeof(float) * Nl.P, cudaMemcpyDeviceToHost));
+        double l = 0;
+        MS_CUDA(cudaMemcpy(&l, lo, sizeof(double), cudaMemcpyDeviceToHost));
+        o[Nl.P] = (float)l;
+        return MS_OK;
+    }
+    ms_set_error(MS_ERR_ARG, "unknown inspection %d", what);
+    return MS_ERR_ARG;
+}
+
+}  // extern "C"

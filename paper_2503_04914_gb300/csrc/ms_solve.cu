@@ -43,7 +43,7 @@ namespace {
 constexpr int kBS = 512;     // threads per CTA of the solve kernel
 constexpr int kChunk = 256;  // rows per work chunk (chunks never straddle levels)
 constexpr int kNW = kBS / 32;
-constexpr int kAcc = 2;      // accumulators per phase
+constexpr int kAcc = 3;      // accumulators per phase
 constexpr int kGroup = 16;           // CTAs per first-level barrier counter
 constexpr int kBarWords = 2 + 64;    // top count, generation, 64 group counters (<= 1024 CTAs)
 // phase categories of the device timeline (ms_fit_stats.phase_ms)
@@ -82,6 +82,15 @@ struct SolveArgs {
     int mf;            // MIXED inner mat-vec is matrix-free
     int mf_tpp;        // lanes per target point of the matrix-free mat-vec
     MFView mfv;
+    // MIXED inner CG preconditioned with M = G^T G (pc = 1)
+    int pc;
+    const int32_t* gcol;   // [N][kPcOut]
+    const float* gval;     // [N][kPcOut]
+    const int64_t* gt_rp;  // rows of G^T
+    const int32_t* gt_col;
+    const float* gt_val;
+    float *u32, *u1_32;
+    int* pcfb;             // levels that fell back to plain CG
 };
 
 // Per-CTA shared state of the solve (identical in every CTA).
@@ -91,7 +100,8 @@ struct Shared {
     double out[kAcc][MS_MAXL];
     double rr[MS_MAXL], bb[MS_MAXL], alpha[MS_MAXL], beta[MS_MAXL], tol[MS_MAXL], scale[MS_MAXL],
         target[MS_MAXL], gam[MS_MAXL];
-    int act[MS_MAXL], oact[MS_MAXL], zero[MS_MAXL], first[MS_MAXL];
+    int act[MS_MAXL], oact[MS_MAXL], zero[MS_MAXL], first[MS_MAXL], pcoff[MS_MAXL], fresh[MS_MAXL];
+    int fallbacks;
     int it_solve[MS_MAXL];
     long long it_total[MS_MAXL];
     int refines[MS_MAXL];
@@ -311,6 +321,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
         sh.oact[l] = (l >= l0 && l < l1) ? 1 : 0;
         sh.act[l] = 0;
         sh.zero[l] = 0;
+        sh.pcoff[l] = 0;
         sh.it_solve[l] = 0;
         sh.tol[l] = (tight_all || l == l0) ? a.tol : a.inter_tol;
     }
@@ -418,23 +429,57 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
             if (!gsync(a, sh)) return false;
         }
 
-        // ---- inner CG iterations (single-reduction form)
+        // ---- inner CG iterations (single-reduction form; preconditioned with
+        //      M = G^T G in MIXED mode when a.pc: u = M r, otherwise u = r)
         for (;;) {
-            // M: w = A r; gamma = r.r, delta = r.w
-            run_phase<2>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
+            const bool use_pc = MODE == 1 && a.pc;
+            if (use_pc) {
+                // G1: u1 = G r  (row pattern: self + preceding neighbours)
+                run_phase<0>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0 && !sh.pcoff[l]; },
+                             [&](int, int64_t r0, int64_t r1, double*) {
+                                 for (int64_t row = r0 + tid; row < r1; row += kBS) {
+                                     float acc = 0.f;
+#pragma unroll
+                                     for (int k = 0; k < kPcOut; ++k) {
+                                         const int32_t c = __ldg(a.gcol + row * kPcOut + k);
+                                         if (c >= 0) acc = fmaf(__ldg(a.gval + row * kPcOut + k), a.r32[c], acc);
+                                     }
+                                     a.u1_32[row] = acc;
+                                 }
+                             });
+                prof(sh, kPrfOther);
+                if (!gsync(a, sh)) return false;
+                // G2: u = G^T u1
+                run_phase<0>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0 && !sh.pcoff[l]; },
+                             [&](int, int64_t r0, int64_t r1, double*) {
+                                 for (int64_t row = r0 + tid; row < r1; row += kBS) {
+                                     float acc = 0.f;
+                                     const int64_t e = __ldg(a.gt_rp + row + 1);
+                                     for (int64_t k = __ldg(a.gt_rp + row); k < e; ++k)
+                                         acc = fmaf(__ldg(a.gt_val + k), a.u1_32[__ldg(a.gt_col + k)], acc);
+                                     a.u32[row] = acc;
+                                 }
+                             });
+                prof(sh, kPrfOther);
+                if (!gsync(a, sh)) return false;
+            }
+            // M: w = A u; gamma = r.u, delta = w.u, rho = r.r
+            run_phase<3>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
                          [&](int l, int64_t r0, int64_t r1, double* acc) {
+                             const float* uin = (use_pc && !sh.pcoff[l]) ? a.u32 : a.r32;
                              if (MODE == 1 && a.mf) {
                                  // matrix-free: the cells whose first point lies in [r0, r1)
                                  const MFLevel& g = a.mfv.lv[l];
                                  int64_t cfirst = a.mfv.cellid[r0];
                                  if (a.mfv.cell_start[g.cell_off + cfirst] < r0) ++cfirst;
                                  const int64_t cend = (int64_t)a.mfv.cellid[r1 - 1] + 1;
-                                 mf_cells_any(a.mfv, l, cfirst, cend, tid >> 5, kNW, a.mf_tpp, a.r32,
+                                 mf_cells_any(a.mfv, l, cfirst, cend, tid >> 5, kNW, a.mf_tpp, uin,
                                               [&](int64_t row, float y) {
-                                                  const float ri = a.r32[row];
+                                                  const float ri = a.r32[row], ui = uin[row];
                                                   a.q32[row] = y;
-                                                  acc[0] += (double)(ri * ri);
-                                                  acc[1] += (double)ri * (double)y;
+                                                  acc[0] += (double)ri * (double)ui;
+                                                  acc[1] += (double)ui * (double)y;
+                                                  acc[2] += (double)(ri * ri);
                                               });
                                  return;
                              }
@@ -449,35 +494,47 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                                          a.q[row] = y;
                                          acc[0] += ri * ri;
                                          acc[1] += ri * y;
+                                         acc[2] += ri * ri;
                                      }
                                  } else {
-                                     const float y = csr_row<float, float, float>(a.Acol, a.Av32, a.r32, s, e, sl, S);
+                                     const float y = csr_row<float, float, float>(a.Acol, a.Av32, uin, s, e, sl, S);
                                      if (ok && sl == 0) {
-                                         const float ri = a.r32[row];
+                                         const float ri = a.r32[row], ui = uin[row];
                                          a.q32[row] = y;
-                                         acc[0] += (double)(ri * ri);
-                                         acc[1] += (double)ri * (double)y;
+                                         acc[0] += (double)ri * (double)ui;
+                                         acc[1] += (double)ui * (double)y;
+                                         acc[2] += (double)(ri * ri);
                                      }
                                  }
                              });
                          });
             prof(sh, kPrfMatvec);
-            if (!gsync_reduce<2>(a, sh, l0, l1)) return false;
+            if (!gsync_reduce<3>(a, sh, l0, l1)) return false;
             if (tid == 0) {
                 sh.any = 0;
                 for (int l = l0; l < l1; ++l) {
                     if (!sh.act[l]) continue;
-                    const double gam = sh.out[0][l], del = sh.out[1][l];
+                    const double gam = sh.out[0][l], del = sh.out[1][l], rho = sh.out[2][l];
+                    const bool lpc = use_pc && !sh.pcoff[l];
                     sh.bytes += (double)a.nnzA[l] * (MODE == 0 ? 12.0 : 8.0) +
-                                (double)(a.off[l + 1] - a.off[l]) * (MODE == 0 ? 32.0 : 20.0);
-                    if (!isfinite(gam) || !isfinite(del)) {
+                                (double)(a.off[l + 1] - a.off[l]) * (MODE == 0 ? 32.0 : (lpc ? 24.0 : 20.0));
+                    if (lpc) sh.bytes += (double)(a.off[l + 1] - a.off[l]) * (2.0 * kPcOut * 12.0 + 16.0);
+                    if (!isfinite(gam) || !isfinite(del) || !isfinite(rho)) {
                         sh.act[l] = 0;
                         sh.oact[l] = 0;
                         if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)MS_ERR_NUMERIC);
                         continue;
                     }
-                    if (gam <= sh.target[l] || sh.it_solve[l] >= a.max_iters) {
+                    if (rho <= sh.target[l] || sh.it_solve[l] >= a.max_iters) {
                         sh.act[l] = 0;  // converged (recursive residual) or capped
+                        continue;
+                    }
+                    if (lpc && !(gam > 0.0)) {
+                        // r^T M r <= 0 cannot happen for an SPD M: treat the preconditioner as
+                        // broken and fall back to plain CG from the current iterate
+                        sh.pcoff[l] = 1;
+                        sh.fallbacks += 1;
+                        sh.act[l] = 0;
                         continue;
                     }
                     double al, be;
@@ -489,12 +546,26 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                         const double den = del - be * gam / sh.alpha[l];
                         al = den > 0.0 ? gam / den : -1.0;
                     }
-                    if (!(al > 0.0)) {  // p^T A p <= 0: A_l is not positive definite in floating point
+                    if (!(al > 0.0)) {
+                        if (MODE == 1 && !sh.first[l]) {
+                            // lost curvature in the FP32 recurrence (cancellation on an ill-conditioned
+                            // level): end this inner solve; the FP64 true residual restarts it
+                            sh.act[l] = 0;
+                            continue;
+                        }
+                        if (lpc) {  // u^T A u <= 0 at a restart: the preconditioner is unusable here
+                            sh.pcoff[l] = 1;
+                            sh.fallbacks += 1;
+                            sh.act[l] = 0;
+                            continue;
+                        }
+                        // p^T A p <= 0 at a restart: A_l is not positive definite in floating point
                         sh.act[l] = 0;
                         sh.oact[l] = 0;
                         if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)MS_ERR_NOT_SPD);
                         continue;
                     }
+                    sh.fresh[l] = sh.first[l];  // the update must not read the old p, s
                     sh.first[l] = 0;
                     sh.alpha[l] = al;
                     sh.beta[l] = be;
@@ -508,15 +579,18 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
             __syncthreads();
             prof(sh, kPrfScalar);
             if (!sh.any) break;
-            // E: p = r + beta p; s = w + beta s; x += alpha p; r -= alpha s
+            // E: p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s
             run_phase<0>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
                          [&](int l, int64_t r0, int64_t r1, double*) {
                              const double al = sh.alpha[l], be = sh.beta[l];
+                             // first iteration: p = u, s = w (the old p, s are not read: they may
+                             // hold anything, and 0 * NaN would poison the recurrence)
+                             const bool fr = sh.fresh[l] != 0;
                              if (MODE == 0) {
                                  for (int64_t row = r0 + tid; row < r1; row += kBS) {
                                      const double ri = a.r[row];
-                                     const double pi = ri + be * a.p[row];
-                                     const double si = a.q[row] + be * a.s[row];
+                                     const double pi = fr ? ri : ri + be * a.p[row];
+                                     const double si = fr ? a.q[row] : a.q[row] + be * a.s[row];
                                      a.p[row] = pi;
                                      a.s[row] = si;
                                      a.x[row] += al * pi;
@@ -524,10 +598,11 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                                  }
                              } else {
                                  const float af = (float)al, bf = (float)be;
+                                 const float* uin = (use_pc && !sh.pcoff[l]) ? a.u32 : a.r32;
                                  for (int64_t row = r0 + tid; row < r1; row += kBS) {
                                      const float ri = a.r32[row];
-                                     const float pi = fmaf(bf, a.p32[row], ri);
-                                     const float si = fmaf(bf, a.s32[row], a.q32[row]);
+                                     const float pi = fr ? uin[row] : fmaf(bf, a.p32[row], uin[row]);
+                                     const float si = fr ? a.q32[row] : fmaf(bf, a.s32[row], a.q32[row]);
                                      a.p32[row] = pi;
                                      a.s32[row] = si;
                                      a.x32[row] = fmaf(af, pi, a.x32[row]);
@@ -574,6 +649,7 @@ __global__ void __launch_bounds__(kBS) k_fit(SolveArgs a) {
     if (tid == 0) {
         sh.bytes = 0.0;
         sh.any = 0;
+        sh.fallbacks = 0;
         for (int i = 0; i < kProf; ++i) sh.pt[i] = 0ull;
         sh.tprev = ms_globaltimer();
     }
@@ -619,6 +695,7 @@ __global__ void __launch_bounds__(kBS) k_fit(SolveArgs a) {
         }
         a.bytes[0] = sh.bytes;
         for (int i = 0; i < kProf; ++i) a.prof[i] = sh.pt[i];
+        a.pcfb[0] = sh.fallbacks;
     }
 }
 
@@ -702,6 +779,14 @@ void fill_args(const ms_hierarchy* h, const int64_t* rpA, const int64_t* rpB, do
     a.mf = (h->opts.precision == MS_PREC_MIXED && h->opts.op == MS_OP_MATRIX_FREE) ? 1 : 0;
     a.mf_tpp = h->mf_tpp;
     a.mfv = make_mfview(h);
+    a.pc = (h->opts.precision == MS_PREC_MIXED && h->opts.precond != MS_PRECOND_NONE) ? 1 : 0;
+    a.gcol = h->pc.gcol;
+    a.gval = h->pc.gval;
+    a.gt_rp = h->pc.gt_rp;
+    a.gt_col = h->pc.gt_col;
+    a.gt_val = h->pc.gt_val;
+    a.u32 = h->u32;
+    a.u1_32 = h->u1_32;
     const int L = h->L;
     a.L = L;
     a.N = h->N;
@@ -774,6 +859,7 @@ static ms_status ensure_workspace(ms_hierarchy* h) {
     MS_TRY(ms_alloc(h, (void**)&h->resid, sizeof(double) * MS_MAXL));
     MS_TRY(ms_alloc(h, (void**)&h->bytes, sizeof(double)));
     MS_TRY(ms_alloc(h, (void**)&h->prof, sizeof(unsigned long long) * kProf));
+    MS_TRY(ms_alloc(h, (void**)&h->pcfb, sizeof(int)));
     return MS_OK;
 }
 
@@ -796,6 +882,17 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
     a.x32 = h->x32; a.r32 = h->r32; a.p32 = h->p32; a.q32 = h->q32; a.s32 = h->s32;
     a.part = h->part; a.scal = h->scal; a.bar = h->bar; a.status = h->status;
     a.iters = h->iters; a.refines = h->refines; a.resid = h->resid; a.bytes = h->bytes; a.prof = h->prof;
+    a.pcfb = h->pcfb;
+    if (h->opts.precond != MS_PRECOND_NONE) {
+        if (h->opts.precision != MS_PREC_MIXED) {
+            ms_set_error(MS_ERR_ARG, "a preconditioner needs precision = MS_PREC_MIXED (it acts on the FP32 inner CG)");
+            return MS_ERR_ARG;
+        }
+        MS_TRY(ms_pc_build(h, h->opts.precond, st));
+        a.gcol = h->pc.gcol; a.gval = h->pc.gval;
+        a.gt_rp = h->pc.gt_rp; a.gt_col = h->pc.gt_col; a.gt_val = h->pc.gt_val;
+        a.u32 = h->u32; a.u1_32 = h->u1_32;
+    }
     const bool mixed = h->opts.precision == MS_PREC_MIXED;
     if (mixed && h->opts.op != MS_OP_MATRIX_FREE && !h->A.v32) {
         ms_set_error(MS_ERR_STATE, "MIXED fit needs FP32 values (build with precision = MS_PREC_MIXED)");
@@ -810,6 +907,7 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
     std::vector<int> ref(MS_MAXL, 0);
     std::vector<double> res(MS_MAXL, 0.0);
     double phase[kProf] = {};
+    int fallbacks = 0;
     int dstat = 0;
     for (int col = 0; col < nrhs; ++col) {
         ms_gather_sorted(f_dev, h->f, h->perm, N, nrhs, col, st);
@@ -837,12 +935,15 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
         MS_CUDA(cudaMemcpyAsync(&b, h->bytes, sizeof(double), cudaMemcpyDeviceToHost, st));
         unsigned long long pr[kProf];
         MS_CUDA(cudaMemcpyAsync(pr, h->prof, sizeof(pr), cudaMemcpyDeviceToHost, st));
+        int fb = 0;
+        MS_CUDA(cudaMemcpyAsync(&fb, h->pcfb, sizeof(int), cudaMemcpyDeviceToHost, st));
         MS_CUDA(cudaStreamSynchronize(st));
         float ms = 0.f;
         MS_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
         total_ms += ms;
         bytes += b;
         for (int i = 0; i < kProf; ++i) phase[i] += 1e-6 * (double)pr[i];
+        fallbacks += fb;
         for (int l = 0; l < L; ++l) it_sum[l] += it[l];
         if (dstat != 0 && result == MS_OK) {
             result = (ms_status)dstat;
@@ -862,6 +963,7 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
         stats->fit_ms = total_ms;
         stats->matvec_bytes = bytes;
         stats->kernel_launches = launches;
+        stats->precond_fallbacks = fallbacks;
         for (int i = 0; i < kProf; ++i) stats->phase_ms[i] = phase[i];
     }
     return result;
@@ -995,6 +1097,10 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
         ms_set_error(MS_ERR_STATE, "MIXED fit needs FP32 values (build with precision = MS_PREC_MIXED)");
         return MS_ERR_STATE;
     }
+    if (h->opts.precond != MS_PRECOND_NONE) {
+        ms_set_error(MS_ERR_STATE, "the allocation-free fit does not apply a preconditioner (precond must be NONE)");
+        return MS_ERR_STATE;
+    }
     int dev = 0;
     MS_CUDA(cudaGetDevice(&dev));
     if (dev != h->device) {
@@ -1051,6 +1157,8 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
     a.part = part; a.scal = scal; a.bar = bar; a.status = status;
     a.iters = iters; a.refines = refines; a.resid = resid; a.bytes = bytes;
     a.prof = reinterpret_cast<unsigned long long*>(small + 2048);  // [kProf]
+    a.pcfb = reinterpret_cast<int*>(small + 3072);                 // [1]
+    a.pc = 0;  // the allocation-free fit runs without a preconditioner (checked above)
 
     ms_gather_sorted(f_dev, v64[0], h->perm, h->N, 1, 0, st);
     void* args[] = {&a};

@@ -20,7 +20,9 @@ MS_OK, MS_ERR_ARG, MS_ERR_CUDA, MS_ERR_OOM, MS_ERR_NOT_SPD, MS_ERR_NOT_CONVERGED
     MS_ERR_NUMERIC, MS_ERR_STATE = range(9)
 MS_OP_CSR, MS_OP_MATRIX_FREE, MS_OP_AUTO = range(3)
 MS_PREC_FP64, MS_PREC_MIXED = range(2)
-MS_PRECOND_NONE, MS_PRECOND_LEARNED = range(2)
+MS_PRECOND_NONE, MS_PRECOND_LEARNED, MS_PRECOND_EXACT = range(3)
+MS_INSPECT_PATTERN, MS_INSPECT_TARGETS, MS_INSPECT_PREDICT, MS_INSPECT_GRAD = range(4)
+PC_K, PC_OUT, PC_HIDDEN = 16, 17, 64
 MS_APPLY_A64, MS_APPLY_A32, MS_APPLY_AMF32, MS_APPLY_B64, MS_APPLY_B32, MS_APPLY_BMF32 = range(6)
 
 STATUS_NAMES = {0: "MS_OK", 1: "MS_ERR_ARG", 2: "MS_ERR_CUDA", 3: "MS_ERR_OOM", 4: "MS_ERR_NOT_SPD",
@@ -28,7 +30,8 @@ STATUS_NAMES = {0: "MS_OK", 1: "MS_ERR_ARG", 2: "MS_ERR_CUDA", 3: "MS_ERR_OOM", 
 
 # the symbols include/ms.h declares (checked by the tests)
 EXPORTED = ["ms_default_opts", "ms_build_hierarchy", "ms_build_hierarchy_dev", "ms_fit", "ms_fit_dev",
-            "ms_fit_static_dev", "ms_evaluate", "ms_evaluate_dev", "ms_apply_dev", "ms_get_permutation", "ms_hierarchy_info",
+            "ms_fit_static_dev", "ms_default_train_opts", "ms_train_precond", "ms_precond_params",
+            "ms_precond_inspect", "ms_evaluate", "ms_evaluate_dev", "ms_apply_dev", "ms_get_permutation", "ms_hierarchy_info",
             "ms_launch_count", "ms_last_error", "ms_destroy"]
 
 
@@ -65,6 +68,19 @@ class ms_info(C.Structure):
                 ("build_ms", C.c_double)]
 
 
+class ms_train_opts(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("lr_final", C.c_double),
+                ("seed", C.c_uint64), ("fp32_weights", C.c_int), ("reserved", C.c_int * 7)]
+
+
+class ms_train_stats(C.Structure):
+    _fields_ = [("samples", C.c_int64), ("steps", C.c_int64), ("loss_first", C.c_double),
+                ("loss_last", C.c_double), ("train_ms", C.c_double), ("n_params", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class MsError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -97,6 +113,12 @@ def load(path: str | None = None):
     lib.ms_fit.argtypes = [_P, _D, C.c_int, C.c_double, _D, C.POINTER(ms_fit_stats)]
     lib.ms_fit_dev.argtypes = [_P, _P, C.c_int, C.c_double, _P, C.POINTER(ms_fit_stats), _P]
     lib.ms_fit_static_dev.argtypes = [_P, _P, C.c_double, _P, C.POINTER(ms_fit_stats), _P]
+    lib.ms_default_train_opts.argtypes = [C.POINTER(ms_train_opts)]
+    lib.ms_default_train_opts.restype = None
+    lib.ms_train_precond.argtypes = [_P, C.POINTER(C.c_int), C.c_int, C.POINTER(ms_train_opts),
+                                     C.POINTER(ms_train_stats)]
+    lib.ms_precond_params.argtypes = [_P, C.POINTER(C.c_float), C.c_int64, C.c_int]
+    lib.ms_precond_inspect.argtypes = [_P, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_void_p, C.c_int64]
     lib.ms_evaluate.argtypes = [_P, _D, C.c_int, _D, C.c_int64, _D]
     lib.ms_evaluate_dev.argtypes = [_P, _P, C.c_int, _P, C.c_int64, _P, _P]
     lib.ms_apply_dev.argtypes = [_P, C.c_int, _P, _P, C.c_int, _P]
@@ -107,7 +129,8 @@ def load(path: str | None = None):
     lib.ms_destroy.argtypes = [_P]
     lib.ms_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("ms_default_opts", "ms_last_error", "ms_destroy", "ms_launch_count"):
+        if name not in ("ms_default_opts", "ms_last_error", "ms_destroy", "ms_launch_count",
+                        "ms_default_train_opts"):
             getattr(lib, name).restype = C.c_int  # ms_status
     lib.ms_launch_count.argtypes = []
     lib.ms_launch_count.restype = C.c_uint64
@@ -242,6 +265,59 @@ def ms_hierarchy_info(handle) -> dict:
             "device_bytes": info.device_bytes, "build_ms": info.build_ms}
 
 
+def ms_default_train_opts(**overrides) -> ms_train_opts:
+    o = ms_train_opts()
+    load().ms_default_train_opts(C.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def _levels(levels):
+    arr = (C.c_int * len(levels))(*[int(x) for x in levels])
+    return arr, len(levels)
+
+
+def ms_train_precond(handle, levels, opts: ms_train_opts | None = None, **overrides) -> dict:
+    if opts is None:
+        opts = ms_default_train_opts(**overrides)
+    lv, n = _levels(levels)
+    st = ms_train_stats()
+    _check(load().ms_train_precond(C.c_void_p(handle), lv, n, C.byref(opts), C.byref(st)))
+    return st.as_dict()
+
+
+def precond_n_values(d: int) -> int:
+    n_in = PC_K * d
+    return PC_HIDDEN * n_in + PC_HIDDEN + PC_HIDDEN * PC_HIDDEN + PC_HIDDEN + PC_OUT * PC_HIDDEN + PC_OUT + 2 * PC_OUT
+
+
+def ms_precond_params(handle, d, params=None):
+    """Get (params None) or set the network weights + output standardisation (float32 array)."""
+    n = precond_n_values(d)
+    if params is None:
+        out = np.empty(n, dtype=np.float32)
+        _check(load().ms_precond_params(C.c_void_p(handle), out.ctypes.data_as(C.POINTER(C.c_float)), n, 0))
+        return out
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load().ms_precond_params(C.c_void_p(handle), p.ctypes.data_as(C.POINTER(C.c_float)), len(p), 1))
+    return p
+
+
+def ms_precond_inspect(handle, what, N, d, levels=(0,)):
+    lv, n = _levels(levels)
+    if what == MS_INSPECT_PATTERN:
+        out = np.empty((N, PC_K), dtype=np.int32)
+    elif what == MS_INSPECT_TARGETS:
+        out = np.empty((N, PC_OUT), dtype=np.float64)
+    elif what == MS_INSPECT_PREDICT:
+        out = np.empty((N, PC_OUT), dtype=np.float32)
+    else:
+        out = np.empty(precond_n_values(d) - 2 * PC_OUT + 1, dtype=np.float32)
+    _check(load().ms_precond_inspect(C.c_void_p(handle), what, lv, n, out.ctypes.data_as(C.c_void_p), out.size))
+    return out
+
+
 def ms_launch_count() -> int:
     return int(load().ms_launch_count())
 
@@ -262,6 +338,7 @@ class Hierarchy:
         if opts is None:
             opts = ms_default_opts(**overrides)
         self.opts = opts
+        self.d = int(d)
         self.N = int(np.sum(n_per_level))
         self.handle = ms_build_hierarchy(d, n_per_level, points, h_per_level, opts, stream)
 
@@ -288,6 +365,15 @@ class Hierarchy:
 
     def info(self):
         return ms_hierarchy_info(self.handle)
+
+    def train_precond(self, levels, **overrides):
+        return ms_train_precond(self.handle, levels, **overrides)
+
+    def precond_params(self, params=None):
+        return ms_precond_params(self.handle, self.d, params)
+
+    def inspect(self, what, levels=(0,)):
+        return ms_precond_inspect(self.handle, what, self.N, self.d, levels)
 
     def close(self):
         if getattr(self, "handle", None):

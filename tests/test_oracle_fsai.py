@@ -78,19 +78,36 @@ def test_gradient_matches_central_differences():
     T, Mk = of.target_matrix(rows, pat)
     mu, sig = of.standardise(T, Mk)
     Ts = (T - mu) / sig * Mk
+    Ks = of.patch_matrices(X, delta, wd, wk, pat)[40:70]
     Z = of.features(X, delta, pat)[40:70]
     Ts, Mk = Ts[40:70], Mk[40:70]
     n_in = Z.shape[1]
     th = of.init_params(n_in, 7)
-    g = of.grad(th, Z, Ts, Mk, n_in)
+    g = of.grad(th, Z, Ts, Mk, Ks, sig, n_in)
     rng = np.random.default_rng(1)
     for idx in rng.choice(len(th), 60, replace=False):
         h = 1e-6 * max(1.0, abs(th[idx]))
         tp, tm = th.copy(), th.copy()
         tp[idx] += h
         tm[idx] -= h
-        fd = (of.loss(tp, Z, Ts, Mk, n_in) - of.loss(tm, Z, Ts, Mk, n_in)) / (2 * h)
+        fd = (of.loss(tp, Z, Ts, Mk, Ks, sig, n_in) - of.loss(tm, Z, Ts, Mk, Ks, sig, n_in)) / (2 * h)
         assert abs(fd - g[idx]) <= 1e-6 * max(1e-6, np.abs(g).max()), (idx, fd, g[idx])
+
+
+def test_loss_vanishes_at_the_exact_rows_and_is_positive_elsewhere():
+    """The energy loss is a squared norm in each patch matrix: zero exactly at the exact rows."""
+    X, delta, (wd, wk) = level(8.0, (2, 2), 2)
+    pat = of.pattern(X, delta)
+    rows = of.scale_free(of.exact_weights(X, delta, wd, wk, pat), delta, 2)
+    T, Mk = of.target_matrix(rows, pat)
+    Ks = of.patch_matrices(X, delta, wd, wk, pat)
+    for i in (5, 50, 200):
+        e = np.random.default_rng(i).standard_normal(17) * Mk[i]
+        assert e @ Ks[i] @ e > 0
+    # the patch matrices are the oracle's kernel blocks scaled by delta^d
+    P = np.concatenate([[60], pat[60]])
+    np.testing.assert_allclose(Ks[60][:len(P), :len(P)],
+                               om.kernel_dense(X[P], X[P], delta, wd, wk) * delta ** 2, rtol=1e-14)
 
 
 def test_adam_first_step_is_a_signed_step():

@@ -1,0 +1,163 @@
+"""GPU parity of the learned factorised sparse-approximate-inverse preconditioner
+against the CPU FP64 oracle (oracle/fsai.py), and what it gains over plain CG.
+
+Tolerances: the pattern is compared exactly (integer work); exact FP64 rows to
+1e-8 relative (17x17 patch Cholesky, kappa(K) up to ~1e5); the network forward
+pass (FP32 features and accumulation, BF16-valued weights on both sides) to
+2e-4 of the largest row entry; gradients (FP32 accumulation over ~800 samples)
+to 2e-3 of the largest gradient entry.
+"""
+import numpy as np
+import pytest
+
+from oracle import fsai as of
+from oracle import multiscale as om
+from paper_2503_04914_gb300 import build as B
+from paper_2503_04914_gb300 import inputs, ms
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    B.build()
+    ms.load()
+
+
+def halton(sizes, nu, wend, seed=21):
+    allp = inputs.scrambled_halton(max(sizes), 2, seed)
+    levels = [np.ascontiguousarray(allp[:n]) for n in sizes]
+    h = np.array([n ** -0.5 for n in sizes])
+    g = inputs.GaussianMixture(8, 2, seed + 1, sine=True)
+    return inputs.Workload("pc", 2, levels, h, nu, wend[0], wend[1], g(np.concatenate(levels)), g)
+
+
+def bf16(x):
+    """Round float32 values to the nearest BF16 (ties to even), returned as float32."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def oracle_level_data(w, l):
+    X = w.levels[l]
+    delta = w.nu * w.h[l]
+    pat = of.pattern(X, delta)
+    rows = of.scale_free(of.exact_weights(X, delta, w.wendland_d, w.wendland_k, pat), delta, w.d)
+    return X, delta, pat, rows
+
+
+@pytest.mark.parametrize("nu,wend", [(4.0, (2, 1)), (8.0, (2, 2))])
+def test_pattern_and_exact_rows(nu, wend):
+    w = halton([37, 150, 601], nu, wend)
+    H = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED)
+    P = H.inspect(ms.MS_INSPECT_PATTERN)
+    T = H.inspect(ms.MS_INSPECT_TARGETS)
+    off = om.level_offsets(w.levels)
+    for l in range(w.L):
+        X, delta, pat, rows = oracle_level_data(w, l)
+        for i, (nb, r) in enumerate(zip(pat, rows)):
+            got = P[off[l] + i]
+            want = np.full(16, -1)
+            want[:len(nb)] = nb + off[l]
+            assert np.array_equal(got, want), (l, i)
+            t = T[off[l] + i]
+            assert np.all(t[len(r):] == 0)
+            assert np.max(np.abs(t[:len(r)] - r)) <= 1e-8 * np.max(np.abs(r)), (l, i)
+    H.close()
+
+
+def _random_params(w, seed):
+    n_in = 16 * w.d
+    th = of.init_params(n_in, seed)
+    mu = np.linspace(0.5, 1.5, 17)
+    sig = np.linspace(0.2, 0.4, 17)
+    return th, mu, sig, np.concatenate([th, mu, sig]).astype(np.float32)
+
+
+def test_network_forward_matches_oracle():
+    w = halton([37, 150, 601], 8.0, (2, 2))
+    H = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED)
+    th, mu, sig, p = _random_params(w, 5)
+    H.precond_params(p)
+    got = H.inspect(ms.MS_INSPECT_PREDICT)
+    off = om.level_offsets(w.levels)
+    thb = bf16(th.astype(np.float32)).astype(np.float64)  # the weights the device uses
+    mu32, sig32 = mu.astype(np.float32).astype(np.float64), sig.astype(np.float32).astype(np.float64)
+    for l in range(w.L):
+        X, delta, pat, _ = oracle_level_data(w, l)
+        Z = of.features(X, delta, pat).astype(np.float32).astype(np.float64)
+        want = of.predict_rows(thb, Z, pat, mu32, sig32, 32)
+        for i, r in enumerate(want):
+            g = got[off[l] + i]
+            assert np.all(g[len(r):] == 0)
+            assert np.max(np.abs(g[:len(r)] - r)) <= 2e-4 * np.max(np.abs(r)), (l, i)
+    # exported parameters round-trip
+    np.testing.assert_array_equal(H.precond_params(), p)
+    H.close()
+
+
+def test_gradient_matches_oracle():
+    w = halton([37, 150, 601], 4.0, (2, 1))
+    H = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED)
+    th, mu, sig, p = _random_params(w, 9)
+    H.precond_params(p)
+    got = H.inspect(ms.MS_INSPECT_GRAD, levels=(0, 1, 2))
+    Zs, Ts, Ms, Ks = [], [], [], []
+    for l in range(w.L):
+        X, delta, pat, rows = oracle_level_data(w, l)
+        T, Mk = of.target_matrix(rows, pat)
+        Zs.append(of.features(X, delta, pat).astype(np.float32).astype(np.float64))
+        Ts.append((T - mu.astype(np.float32)) / sig.astype(np.float32) * Mk)
+        Ms.append(Mk)
+        Ks.append(of.patch_matrices(X, delta, 2, 1, pat))
+    Z, T, Mk, K = np.concatenate(Zs), np.concatenate(Ts), np.concatenate(Ms), np.concatenate(Ks)
+    th32 = th.astype(np.float32).astype(np.float64)
+    s32 = sig.astype(np.float32).astype(np.float64)
+    g_ref = of.grad(th32, Z, T, Mk, K, s32, 32)
+    l_ref = of.loss(th32, Z, T, Mk, K, s32, 32)
+    assert abs(got[-1] - l_ref) <= 1e-4 * l_ref
+    err = np.abs(got[:-1] - g_ref)
+    assert err.max() <= 2e-3 * np.abs(g_ref).max(), err.max() / np.abs(g_ref).max()
+    H.close()
+
+
+@pytest.fixture(scope="module")
+def trained():
+    """nu = 8, phi_{2,2} (kappa(A_l) ~ 1e5..1e6): train on levels 0..3, fit level sizes to 16384."""
+    w = inputs.halton_hierarchy(L=5, nu=8.0, wendland=(2, 2), n_gauss=6)
+    H = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED, precond=ms.MS_PRECOND_LEARNED)
+    st = H.train_precond([0, 1, 2, 3], epochs=200)
+    return w, H, st
+
+
+def test_training_reduces_the_loss(trained):
+    _, _, st = trained
+    assert st["samples"] == 64 + 256 + 1024 + 4096
+    assert st["loss_last"] < 0.5 * st["loss_first"], st
+
+
+def test_learned_preconditioner_gain_and_parity(trained):
+    """The learned M = G^T G keeps the fit's result (oracle parity) and cuts the CG iterations
+    of the ill-conditioned levels against the same fit without it (and the exact rows cut
+    them further: the network approximates its teacher)."""
+    w, H, _ = trained
+    a_pc, st_pc = H.fit(w.f, rel_tol=1e-11)
+    plain = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED)
+    a_0, st_0 = plain.fit(w.f, rel_tol=1e-11)
+    exact = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED, precond=ms.MS_PRECOND_EXACT)
+    a_e, st_e = exact.fit(w.f, rel_tol=1e-11)
+    it_pc, it_0, it_e = (sum(s["cg_iterations"]) for s in (st_pc, st_0, st_e))
+    assert st_pc["precond_fallbacks"] == 0
+    assert it_pc * 2 < it_0, (it_pc, it_0)
+    assert it_e * 2 < it_pc, (it_e, it_pc)
+    ref, _ = om.fit_sequential(w.levels, w.f, w.h, w.nu, 2, 2)
+    ref = np.concatenate(ref)
+    Q = inputs.query_grid(48, 2)
+    s_ref = om.evaluate(w.levels, np.split(ref, np.cumsum(w.n_per_level)[:-1]), w.h, w.nu, 2, 2, Q)
+    for a in (a_pc, a_0, a_e):
+        s = H.evaluate(a, Q)
+        assert np.linalg.norm(s - s_ref) <= 1e-9 * np.linalg.norm(s_ref)
+        assert np.linalg.norm(a - ref) <= 1e-6 * np.linalg.norm(ref)

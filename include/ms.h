@@ -180,12 +180,18 @@ ms_status ms_build_hierarchy_dev(int d, int L, const int64_t* n_per_level, const
  * whose beta is already final are not re-solved.  Finally alpha_l = A_l^{-1} beta_l
  * for every level.  Each level solve stops at |beta_l - A_l x| <= rel_tol |beta_l|
  * (FP64 true residual).  The whole fit is one persistent cooperative kernel per
- * right-hand side.
+ * batch of right-hand sides: up to min(32, 256 / L) right-hand sides share a
+ * launch, each (right-hand side, level) pair with its own CG scalars and
+ * stopping test (the batch reduces its dot products in another fixed order than
+ * a single fit, so a column agrees with its single fit to the tolerance, not
+ * bitwise; the result is deterministic).
  *   f          host [N] (nrhs == 1) or [N][nrhs], input order
  *   nrhs       >= 1
  *   rel_tol    in (0, 1)
  *   alpha_out  host, same shape as f, input order
- *   stats      nullable; filled for the last right-hand side
+ *   stats      nullable; over all right-hand sides: cg_iterations and
+ *              refinements summed, rel_residual the largest, fit_ms and
+ *              matvec_bytes summed over the launches
  * Errors: MS_ERR_ARG, MS_ERR_NUMERIC (non-finite f), MS_ERR_NOT_SPD,
  * MS_ERR_NOT_CONVERGED (alpha_out still holds the last iterate),
  * MS_ERR_TIMEOUT, MS_ERR_CUDA.  Synchronous.
@@ -207,7 +213,7 @@ ms_status ms_fit_dev(ms_hierarchy* h, const double* f_dev, int nrhs, double rel_
  * device), and processes with a device-memory budget fixed at start-up cannot
  * allow that.  This entry point computes the same fit as ms_fit_dev for ONE
  * right-hand side, but the call allocates nothing: its work space is a fixed
- * device array of about 4.6 MiB inside libms.so, held by every GPU that loads
+ * device array of about 5.6 MiB inside libms.so, held by every GPU that loads
  * the library until the process exits.
  *   h          a built hierarchy with at most 65536 points in total
  *              (larger ones are rejected with MS_ERR_ARG); its device must be current

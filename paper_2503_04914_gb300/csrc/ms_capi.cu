@@ -156,9 +156,26 @@ ms_status ms_alloc(ms_hierarchy* h, void** p, size_t bytes) {
         ms_set_error(MS_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
         return MS_ERR_OOM;
     }
+    h->alloc_bytes[h->nallocs] = bytes;
     h->allocs[h->nallocs++] = *p;
     h->device_bytes += (int64_t)bytes;
     return MS_OK;
+}
+
+ms_status ms_realloc(ms_hierarchy* h, void** p, size_t bytes) {
+    if (*p) {
+        for (int i = 0; i < h->nallocs; ++i) {
+            if (h->allocs[i] != *p) continue;
+            cudaFree(*p);
+            h->device_bytes -= (int64_t)h->alloc_bytes[i];
+            h->allocs[i] = h->allocs[h->nallocs - 1];
+            h->alloc_bytes[i] = h->alloc_bytes[h->nallocs - 1];
+            --h->nallocs;
+            break;
+        }
+        *p = nullptr;
+    }
+    return ms_alloc(h, p, bytes);
 }
 
 void ms_gather_sorted(const double* in, double* out, const int32_t* perm, int64_t N, int nrhs, int col, cudaStream_t s) {

@@ -289,7 +289,7 @@ struct Precond {
 struct ms_hierarchy {
     int device = 0;
     Precond pc;
-    float *u32 = nullptr, *u1_32 = nullptr;  // preconditioned-CG work vectors
+    float *u32 = nullptr, *u1_32 = nullptr;  // preconditioned-CG work vectors [ws_rhs][N]
     int d = 0, L = 0;
     int64_t N = 0;
     ms_opts opts{};
@@ -302,10 +302,12 @@ struct ms_hierarchy {
     int32_t* cellid = nullptr;   // [N] level-local Morton cell of each sorted point
     int mf_tpp = 2;              // matrix-free lanes per target point
     DevCSR A, B;
-    // solver work space (sorted order)
+    // solver work space (sorted order; vectors hold ws_rhs right-hand sides, [ws_rhs][N])
+    int ws_rhs = 0;
     double *f = nullptr, *beta = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *s = nullptr;
     float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *s32 = nullptr;
     double* part = nullptr;      // reduction partials
+    double* gpart = nullptr;     // group sums of the partials
     double* scal = nullptr;      // published grid sums
     unsigned long long* prof = nullptr;  // device timeline of the solve kernel
     int* pcfb = nullptr;                 // preconditioner fallbacks of the last fit
@@ -321,11 +323,14 @@ struct ms_hierarchy {
     int64_t device_bytes = 0;
     double build_ms = 0.0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    void* allocs[64];
+    void* allocs[96];
+    size_t alloc_bytes[96];
     int nallocs = 0;
 };
 
 ms_status ms_alloc(ms_hierarchy* h, void** p, size_t bytes);
+// free *p (if it is one of the handle's allocations) and allocate `bytes` in its place
+ms_status ms_realloc(ms_hierarchy* h, void** p, size_t bytes);
 ms_status ms_build_impl(ms_hierarchy* h, const double* points_dev, cudaStream_t s);
 ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel_tol, double* alpha_dev,
                       ms_fit_stats* stats, cudaStream_t s);

@@ -559,8 +559,6 @@ ms_status pc_alloc(ms_hierarchy* h) {
     MS_TRY(ms_alloc(h, (void**)&pc.adam_m, sizeof(float) * pc.n_params));
     MS_TRY(ms_alloc(h, (void**)&pc.adam_v, sizeof(float) * pc.n_params));
     MS_TRY(ms_alloc(h, (void**)&pc.musig, sizeof(float) * 2 * kPcOut));
-    MS_TRY(ms_alloc(h, (void**)&h->u32, sizeof(float) * N));
-    MS_TRY(ms_alloc(h, (void**)&h->u1_32, sizeof(float) * N));
     return MS_OK;
 }
 

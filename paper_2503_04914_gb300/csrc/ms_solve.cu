@@ -1,5 +1,5 @@
 // The fit: eq. split of Section 3 solved on the device in ONE persistent
-// cooperative kernel per right-hand side.
+// cooperative kernel per batch of right-hand sides.
 //
 //   T'_L beta = f   by Jacobi sweeps (eq. jacobi, Theorem 9), beta_0 = f;
 //   D_L alpha = beta by per-level conjugate gradients (Theorem 8,
@@ -15,22 +15,28 @@
 // solve over all levels gives alpha_l = A_l^{-1} beta_l and certifies every
 // level's FP64 true residual.
 //
+// Several right-hand sides share one launch: every (right-hand side, level)
+// pair is a "virtual level" v = r L + l with its own CG scalars; the matrix is
+// shared and the vectors are stored right-hand-side-major ([R][N]).
+//
 // Level solves: CG in the single-reduction form of Chronopoulos and Gear
-// (w = A r, then gamma = r.r and delta = r.w in one reduction; p = r + beta p,
-// s = w + beta s, x += alpha p, r -= alpha s), which is CG's recurrence with
-// one grid-wide reduction and two grid barriers per iteration.  FP64 dots are
-// reduced deterministically: per-CTA partials (a shared-memory block sum),
-// then the last CTA to arrive at the grid barrier adds the partials of every
-// CTA in a fixed order and publishes the sums, so all CTAs take the same
-// convergence decisions.  Stopping: |beta_l - A_l x| <= tol |beta_l| in FP64
-// (true residual, re-checked after the recursive residual has converged).
+// (w = A u, then r.u, w.u and r.r in one reduction; p = u + beta p,
+// s = w + beta s, x += alpha p, r -= alpha s, u = M r or u = r), which is CG's
+// recurrence with one grid-wide reduction and two grid barriers per
+// iteration (four with the preconditioner).  FP64 dots are reduced
+// deterministically: per-CTA partials (a shared-memory block sum), then, inside
+// the grid barrier, the last CTA of each group of 16 sums its group's partials
+// and the last group leader sums the group sums, in fixed orders, and publishes
+// them, so all CTAs take the same convergence decisions.  Stopping:
+// |beta_l - A_l x| <= tol |beta_l| in FP64 (true residual, re-checked after
+// the recursive residual has converged).
 //   FP64 mode : CG on FP64 vectors with the FP64 CSR values.
 //   MIXED mode: iterative refinement: outer FP64 true residual r = b - A x
-//               (FP64 CSR), inner CG on FP32 vectors with FP32 CSR values and
-//               FP32 accumulation (FP64 dots and scalars) for A d = r/|r|,
-//               then x += |r| d in FP64.
-// Grid barriers are bounded (ms_internal.cuh); on a time-out every CTA
-// returns and the host reports MS_ERR_TIMEOUT.
+//               (FP64 CSR), inner CG on FP32 vectors with FP32 CSR values (or
+//               matrix-free FP32 entries) and FP32 accumulation (FP64 dots and
+//               scalars) for A d = r/|r|, then x += |r| d in FP64.
+// Grid barriers are bounded; on a time-out every CTA returns and the host
+// reports MS_ERR_TIMEOUT.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -44,17 +50,19 @@ constexpr int kBS = 512;     // threads per CTA of the solve kernel
 constexpr int kChunk = 256;  // rows per work chunk (chunks never straddle levels)
 constexpr int kNW = kBS / 32;
 constexpr int kAcc = 3;      // accumulators per phase
+constexpr int kMaxV = 256;   // virtual levels (right-hand side, level) per launch
 constexpr int kGroup = 16;           // CTAs per first-level barrier counter
-constexpr int kBarWords = 2 + 64;    // top count, generation, 64 group counters (<= 1024 CTAs)
+constexpr int kMaxGroups = 64;       // <= 1024 CTAs
+constexpr int kBarWords = 2 + kMaxGroups;  // top count, generation, group counters
 // phase categories of the device timeline (ms_fit_stats.phase_ms)
 enum { kPrfResid = 0, kPrfMatvec = 1, kPrfUpdate = 2, kPrfBarrier = 3, kPrfLower = 4, kPrfOther = 5,
        kPrfScalar = 6, kProf = 8 };
 
 struct SolveArgs {
-    int L;
-    int64_t N;
+    int L, R, V;       // levels, right-hand sides of this launch, V = R L virtual levels
+    int64_t N, C;      // points, chunks per right-hand side
     int64_t off[MS_MAXL + 1];
-    int64_t coff[MS_MAXL + 1];   // chunk offsets per level
+    int64_t coff[MS_MAXL + 1];   // chunk offsets per level (within one right-hand side)
     int64_t nnzA[MS_MAXL], nnzB[MS_MAXL];
     int tprA[MS_MAXL], tprB[MS_MAXL];
     const int64_t* Arp;
@@ -64,16 +72,17 @@ struct SolveArgs {
     const int64_t* Brp;
     const int32_t* Bcol;
     const double* Bv64;
-    const double* f;
-    double *beta, *x, *r, *p, *q, *s;      // q holds w = A r
-    float *x32, *r32, *p32, *q32, *s32;
-    double* part;      // [kAcc][MS_MAXL][gridDim.x] per-CTA partial sums
-    double* scal;      // [kAcc][MS_MAXL] grid sums published by the last CTA of a barrier
-    unsigned* bar;     // [0] arrival count, [1] generation
+    const double* f;                       // [R][N]
+    double *beta, *x, *r, *p, *q, *s;      // [R][N]; q holds w = A u
+    float *x32, *r32, *p32, *q32, *s32;    // [R][N]
+    double* part;      // [kAcc][V][gridDim.x] per-CTA partial sums
+    double* gpart;     // [kMaxGroups][kAcc][V] group sums
+    double* scal;      // [kAcc][V] grid sums published inside the barrier
+    unsigned* bar;     // [kBarWords]
     int* status;
-    int64_t* iters;    // [MS_MAXL]
-    int* refines;      // [MS_MAXL]
-    double* resid;     // [MS_MAXL]
+    int64_t* iters;    // [MS_MAXL] summed over the right-hand sides
+    int* refines;      // [MS_MAXL] summed over the right-hand sides
+    double* resid;     // [V]
     double* bytes;     // [1]
     unsigned long long* prof;  // [kProf] nanoseconds CTA 0 spent per phase category
     int sweeps, max_iters, max_outer;
@@ -89,26 +98,24 @@ struct SolveArgs {
     const int64_t* gt_rp;  // rows of G^T
     const int32_t* gt_col;
     const float* gt_val;
-    float *u32, *u1_32;
+    float *u32, *u1_32;    // [R][N]
     int* pcfb;             // levels that fell back to plain CG
 };
 
-// Per-CTA shared state of the solve (identical in every CTA).
+// Per-CTA shared state of the solve (identical in every CTA), in dynamic shared memory.
 struct Shared {
     double red[kAcc][kBS];
-    double acc[kAcc][MS_MAXL];
-    double out[kAcc][MS_MAXL];
-    double rr[MS_MAXL], bb[MS_MAXL], alpha[MS_MAXL], beta[MS_MAXL], tol[MS_MAXL], scale[MS_MAXL],
-        target[MS_MAXL], gam[MS_MAXL];
-    int act[MS_MAXL], oact[MS_MAXL], zero[MS_MAXL], first[MS_MAXL], pcoff[MS_MAXL], fresh[MS_MAXL];
-    int fallbacks;
-    int it_solve[MS_MAXL];
-    long long it_total[MS_MAXL];
-    int refines[MS_MAXL];
-    double bytes;
-    int any;
-    int last;
-    int ok;
+    double acc[kAcc][kMaxV];
+    double out[kAcc][kMaxV];
+    double bb[kMaxV], alpha[kMaxV], beta[kMaxV], tol[kMaxV], scale[kMaxV], target[kMaxV], gam[kMaxV];
+    int act[kMaxV], oact[kMaxV], zero[kMaxV], first[kMaxV], pcoff[kMaxV], fresh[kMaxV];
+    int it_solve[kMaxV];
+    int refines[kMaxV];
+    int fb[kMaxV];          // preconditioner fall-backs
+    long long it_total[kMaxV];
+    double vbytes[kMaxV];   // algorithmic bytes moved, per virtual level
+    double bytes;           // bytes of the lower-block updates
+    int last, glast, ok;
     unsigned mine;
     unsigned long long pt[kProf];
     unsigned long long tprev;
@@ -150,10 +157,23 @@ __device__ __forceinline__ TA csr_row(const int32_t* __restrict__ col, const TV*
     return acc;
 }
 
-__device__ __forceinline__ int level_of_chunk(const SolveArgs& a, int64_t c) {
+// A work chunk: rows [r0, r1) of level l for right-hand side rhs (vectors at offset vb).
+struct Chunk {
+    int v, l;
+    int64_t r0, r1, vb;
+};
+
+__device__ __forceinline__ Chunk chunk_at(const SolveArgs& a, int64_t c) {
+    const int64_t rhs = c / a.C, cl = c - rhs * a.C;
     int l = 0;
-    while (l + 1 < a.L && c >= a.coff[l + 1]) ++l;
-    return l;
+    while (l + 1 < a.L && cl >= a.coff[l + 1]) ++l;
+    Chunk ch;
+    ch.l = l;
+    ch.v = (int)rhs * a.L + l;
+    ch.vb = rhs * a.N;
+    ch.r0 = a.off[l] + (cl - a.coff[l]) * kChunk;
+    ch.r1 = min(ch.r0 + (int64_t)kChunk, a.off[l + 1]);
+    return ch;
 }
 
 // Add the block's thread-local accumulators into sh.acc[k][cur]: values are
@@ -178,77 +198,85 @@ __device__ __forceinline__ void flush_acc(Shared& sh, double* acc, int cur) {
     __syncthreads();
 }
 
-// Run body(l, r0, r1, acc) over this CTA's chunks of levels [l0, l1) with sel(l) true;
-// thread-local accumulators are block-reduced into sh.acc[k][l] and the per-CTA
-// sums are written to the partials array.
+// Run body(chunk, acc) over this CTA's chunks whose virtual level passes sel(v);
+// thread-local accumulators are block-reduced into sh.acc[k][v] and the per-CTA
+// sums of all virtual levels are written to the partials array.
 template <int K, typename Sel, typename Body>
-__device__ __forceinline__ void run_phase(const SolveArgs& a, Shared& sh, int l0, int l1, Sel sel, Body body) {
+__device__ __forceinline__ void run_phase(const SolveArgs& a, Shared& sh, Sel sel, Body body) {
     if (K > 0) {
-        for (int i = threadIdx.x; i < kAcc * MS_MAXL; i += kBS) (&sh.acc[0][0])[i] = 0.0;
+        for (int i = threadIdx.x; i < kAcc * kMaxV; i += kBS) (&sh.acc[0][0])[i] = 0.0;
         __syncthreads();
     }
     double acc[K > 0 ? K : 1];
 #pragma unroll
     for (int k = 0; k < (K > 0 ? K : 1); ++k) acc[k] = 0.0;
     int cur = -1;
-    const int64_t c1 = a.coff[l1];
-    for (int64_t c = a.coff[l0] + blockIdx.x; c < c1; c += gridDim.x) {
-        const int l = level_of_chunk(a, c);
-        if (!sel(l)) continue;
-        if (K > 0 && l != cur) {
+    const int64_t cend = (int64_t)a.R * a.C;
+    for (int64_t c = blockIdx.x; c < cend; c += gridDim.x) {
+        const Chunk ch = chunk_at(a, c);
+        if (!sel(ch.v)) continue;
+        if (K > 0 && ch.v != cur) {
             if (cur >= 0) flush_acc<K>(sh, acc, cur);
-            cur = l;
+            cur = ch.v;
         }
-        const int64_t r0 = a.off[l] + (c - a.coff[l]) * kChunk;
-        const int64_t r1 = min(r0 + (int64_t)kChunk, a.off[l + 1]);
-        body(l, r0, r1, acc);
+        body(ch, acc);
     }
     if (K > 0) {
         if (cur >= 0) flush_acc<K>(sh, acc, cur);
-        const int nl = l1 - l0;
-        for (int i = threadIdx.x; i < K * nl; i += kBS) {
-            const int k = i / nl, l = l0 + i % nl;
-            a.part[((size_t)k * MS_MAXL + l) * gridDim.x + blockIdx.x] = sh.acc[k][l];
+        for (int i = threadIdx.x; i < K * a.V; i += kBS) {
+            const int k = i / a.V, v = i % a.V;
+            a.part[((size_t)k * a.V + v) * gridDim.x + blockIdx.x] = sh.acc[k][v];
         }
     }
 }
 
-// Grid barrier; with K > 0 the last CTA to arrive also sums the per-CTA partials
-// of levels [l0, l1) (fixed order) into a.scal before releasing the others, and
-// every CTA then copies the sums into sh.out.  Bounded like grid_barrier().
+// Grid barrier with two-level arrival; with K > 0 it also reduces the per-CTA
+// partials: the last CTA of each group of kGroup sums its group's partials of all
+// K V sums, the last group leader sums the group sums and publishes them in
+// a.scal before releasing the other CTAs, and every CTA then copies the sums into
+// sh.out.  Every wait is bounded: past timeout_ns it records MS_ERR_TIMEOUT and
+// returns false; it also returns false once another CTA has recorded a time-out.
 template <int K>
-__device__ bool gsync_reduce(const SolveArgs& a, Shared& sh, int l0, int l1) {
+__device__ bool gsync_reduce(const SolveArgs& a, Shared& sh) {
+    const unsigned nb = gridDim.x;
+    const unsigned grp = blockIdx.x / kGroup;
+    const unsigned ngrp = (nb + kGroup - 1) / kGroup;
+    const int npair = K * a.V;
     __syncthreads();
     if (threadIdx.x == 0) {
-        // two-level arrival: CTAs count in at their group's counter; the last CTA
-        // of each group counts in at the top counter (about 2 x sqrt(grid)
-        // serialised atomics per barrier instead of one per CTA)
         cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(a.bar[1]);
-        cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(a.bar[0]);
-        sh.mine = g.load(cuda::memory_order_relaxed);
-        const unsigned grp = blockIdx.x / kGroup;
-        const unsigned ngrp = (gridDim.x + kGroup - 1) / kGroup;
-        const unsigned gsize = min((unsigned)kGroup, gridDim.x - grp * kGroup);
         cuda::atomic_ref<unsigned, cuda::thread_scope_device> gc(a.bar[2 + grp]);
-        int last = 0;
-        if (gc.fetch_add(1u, cuda::memory_order_acq_rel) == gsize - 1) {
-            gc.store(0u, cuda::memory_order_relaxed);
-            last = (c.fetch_add(1u, cuda::memory_order_acq_rel) == ngrp - 1);
-        }
-        sh.last = last;
+        sh.mine = g.load(cuda::memory_order_relaxed);
+        const unsigned gsize = min((unsigned)kGroup, nb - grp * kGroup);
+        sh.glast = gc.fetch_add(1u, cuda::memory_order_acq_rel) == gsize - 1;
+        if (sh.glast) gc.store(0u, cuda::memory_order_relaxed);
+        sh.last = 0;
     }
     __syncthreads();
+    if (sh.glast) {
+        if (K > 0) {  // group sums, in CTA order
+            const unsigned b0 = grp * kGroup, b1 = min(nb, b0 + kGroup);
+            for (int i = threadIdx.x; i < npair; i += kBS) {
+                const double* src = a.part + (size_t)i * nb;
+                double s = 0.0;
+                for (unsigned b = b0; b < b1; ++b) s += __ldcg(src + b);
+                __stcg(a.gpart + (size_t)grp * kAcc * a.V + i, s);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(a.bar[0]);
+            sh.last = c.fetch_add(1u, cuda::memory_order_acq_rel) == ngrp - 1;
+        }
+        __syncthreads();
+    }
     int ok = 1;
     if (sh.last) {
-        if (K > 0) {
-            const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nl = l1 - l0;
-            for (int i = w; i < K * nl; i += kNW) {
-                const int k = i / nl, l = l0 + i % nl;
-                const double* src = a.part + ((size_t)k * MS_MAXL + l) * gridDim.x;
+        if (K > 0) {  // grid sums, in group order
+            for (int i = threadIdx.x; i < npair; i += kBS) {
                 double s = 0.0;
-                for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(src + b);
-                s = warp_sum(s);
-                if (lane == 0) __stcg(a.scal + k * MS_MAXL + l, s);
+                for (unsigned gi = 0; gi < ngrp; ++gi) s += __ldcg(a.gpart + (size_t)gi * kAcc * a.V + i);
+                __stcg(a.scal + i, s);
             }
         }
         __syncthreads();
@@ -285,10 +313,9 @@ __device__ bool gsync_reduce(const SolveArgs& a, Shared& sh, int l0, int l1) {
     __syncthreads();
     if (!sh.ok) return false;
     if (K > 0) {
-        const int nl = l1 - l0;
-        for (int i = threadIdx.x; i < K * nl; i += kBS) {
-            const int k = i / nl, l = l0 + i % nl;
-            sh.out[k][l] = __ldcg(a.scal + k * MS_MAXL + l);
+        for (int i = threadIdx.x; i < npair; i += kBS) {
+            const int k = i / a.V, v = i % a.V;
+            sh.out[k][v] = __ldcg(a.scal + i);
         }
         __syncthreads();
     }
@@ -296,7 +323,7 @@ __device__ bool gsync_reduce(const SolveArgs& a, Shared& sh, int l0, int l1) {
     return true;
 }
 
-__device__ __forceinline__ bool gsync(const SolveArgs& a, Shared& sh) { return gsync_reduce<0>(a, sh, 0, 0); }
+__device__ __forceinline__ bool gsync(const SolveArgs& a, Shared& sh) { return gsync_reduce<0>(a, sh); }
 
 // Rows [r0, r1) of a chunk, one sub-warp of S lanes per row; fn(row, valid, sl).
 template <typename Fn>
@@ -312,119 +339,119 @@ __device__ __forceinline__ void rows_by_subwarp(int64_t r0, int64_t r1, int S, F
 
 // ---------------------------------------------------------------- level solve
 
-// Solve A_l x_l = beta_l for the levels [l0, l1), x warm.  tight_all: every level
-// to a.tol, else only level l0 to a.tol and the others to a.inter_tol.
+// Solve A_l x_l = beta_l for the levels [l0, l1) of every right-hand side, x warm.
+// tight_all: every level to a.tol, else only level l0 to a.tol and the others to
+// a.inter_tol.
 template <int MODE>
 __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, bool tight_all) {
     const int tid = threadIdx.x;
-    for (int l = tid; l < MS_MAXL; l += kBS) {
-        sh.oact[l] = (l >= l0 && l < l1) ? 1 : 0;
-        sh.act[l] = 0;
-        sh.zero[l] = 0;
-        sh.pcoff[l] = 0;
-        sh.it_solve[l] = 0;
-        sh.tol[l] = (tight_all || l == l0) ? a.tol : a.inter_tol;
+    const int V = a.V, L = a.L;
+    for (int v = tid; v < kMaxV; v += kBS) {
+        const int l = v % L;
+        sh.oact[v] = (v < V && l >= l0 && l < l1) ? 1 : 0;
+        sh.act[v] = 0;
+        sh.zero[v] = 0;
+        sh.pcoff[v] = 0;
+        sh.it_solve[v] = 0;
+        sh.tol[v] = (tight_all || l == l0) ? a.tol : a.inter_tol;
     }
     __syncthreads();
     bool first_outer = true;
     for (int outer = 0; outer < a.max_outer; ++outer) {
         // ---- P1: FP64 true residual r = b - A x (FP64 CSR)
-        run_phase<2>(a, sh, l0, l1, [&](int l) { return sh.oact[l] != 0; },
-                     [&](int l, int64_t r0, int64_t r1, double* acc) {
-                         const int S = a.tprA[l];
-                         rows_by_subwarp(r0, r1, S, [&](int64_t row, bool ok, int sl) {
-                             int64_t s = 0, e = 0;
-                             if (ok) { s = a.Arp[row]; e = a.Arp[row + 1]; }
-                             const double y = csr_row<double, double, double>(a.Acol, a.Av64, a.x, s, e, sl, S);
-                             if (ok && sl == 0) {
-                                 const double b = a.beta[row];
-                                 const double ri = b - y;
-                                 a.r[row] = ri;
-                                 acc[0] += ri * ri;
-                                 acc[1] += b * b;
-                             }
-                         });
-                     });
+        run_phase<2>(a, sh, [&](int v) { return sh.oact[v] != 0; }, [&](const Chunk& ch, double* acc) {
+            const int S = a.tprA[ch.l];
+            const double* xv = a.x + ch.vb;
+            rows_by_subwarp(ch.r0, ch.r1, S, [&](int64_t row, bool ok, int sl) {
+                int64_t s = 0, e = 0;
+                if (ok) { s = a.Arp[row]; e = a.Arp[row + 1]; }
+                const double y = csr_row<double, double, double>(a.Acol, a.Av64, xv, s, e, sl, S);
+                if (ok && sl == 0) {
+                    const double b = a.beta[ch.vb + row];
+                    const double ri = b - y;
+                    a.r[ch.vb + row] = ri;
+                    acc[0] += ri * ri;
+                    acc[1] += b * b;
+                }
+            });
+        });
         prof(sh, kPrfResid);
-        if (!gsync_reduce<2>(a, sh, l0, l1)) return false;
-        if (tid == 0) {
-            sh.any = 0;
-            for (int l = l0; l < l1; ++l) {
-                if (!sh.oact[l]) continue;
-                const double rr = sh.out[0][l];
-                if (first_outer) sh.bb[l] = sh.out[1][l];
-                const double bb = sh.bb[l];
-                sh.bytes += (double)a.nnzA[l] * 12.0 + (double)(a.off[l + 1] - a.off[l]) * 32.0;
-                if (!isfinite(rr) || !isfinite(bb)) {
-                    sh.oact[l] = 0;
-                    if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)MS_ERR_NUMERIC);
-                    continue;
-                }
-                if (bb == 0.0) {  // zero right-hand side: the solution is zero
-                    sh.zero[l] = 1;
-                    sh.oact[l] = 0;
-                    if (blockIdx.x == 0) a.resid[l] = 0.0;
-                    continue;
-                }
-                const double res = sqrt(rr / bb);
-                if (blockIdx.x == 0) a.resid[l] = res;
-                if (res <= sh.tol[l]) {
-                    sh.oact[l] = 0;
-                    continue;
-                }
-                if (sh.it_solve[l] >= a.max_iters) {
-                    sh.oact[l] = 0;
-                    if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)MS_ERR_NOT_CONVERGED);
-                    continue;
-                }
-                sh.any = 1;
-                sh.refines[l] += 1;
-                sh.act[l] = 1;
-                sh.first[l] = 1;
-                if (MODE == 0) {
-                    // recursive-residual target, with margin below the true-residual tolerance
-                    sh.target[l] = 0.25 * sh.tol[l] * sh.tol[l] * bb;
-                } else {
-                    sh.scale[l] = 1.0 / sqrt(rr);
-                    const double need = 0.5 * sh.tol[l] * sqrt(bb) * sh.scale[l];
-                    const double t = fmax(a.inner_tol, fmin(need, 1.0));
-                    sh.target[l] = t * t;
-                }
+        if (!gsync_reduce<2>(a, sh)) return false;
+        // decisions: one thread per virtual level
+        int my_any = 0, my_zero = 0;
+        for (int v = tid; v < V; v += kBS) {
+            if (!sh.oact[v]) continue;
+            const int l = v % L;
+            const double rr = sh.out[0][v];
+            if (first_outer) sh.bb[v] = sh.out[1][v];
+            const double bb = sh.bb[v];
+            sh.vbytes[v] += (double)a.nnzA[l] * 12.0 + (double)(a.off[l + 1] - a.off[l]) * 32.0;
+            if (!isfinite(rr) || !isfinite(bb)) {
+                sh.oact[v] = 0;
+                if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)MS_ERR_NUMERIC);
+                continue;
+            }
+            if (bb == 0.0) {  // zero right-hand side: the solution is zero
+                sh.zero[v] = 1;
+                sh.oact[v] = 0;
+                my_zero = 1;
+                if (blockIdx.x == 0) a.resid[v] = 0.0;
+                continue;
+            }
+            const double res = sqrt(rr / bb);
+            if (blockIdx.x == 0) a.resid[v] = res;
+            if (res <= sh.tol[v]) {
+                sh.oact[v] = 0;
+                continue;
+            }
+            if (sh.it_solve[v] >= a.max_iters) {
+                sh.oact[v] = 0;
+                if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)MS_ERR_NOT_CONVERGED);
+                continue;
+            }
+            my_any = 1;
+            sh.refines[v] += 1;
+            sh.act[v] = 1;
+            sh.first[v] = 1;
+            if (MODE == 0) {
+                // recursive-residual target, with margin below the true-residual tolerance
+                sh.target[v] = 0.25 * sh.tol[v] * sh.tol[v] * bb;
+            } else {
+                sh.scale[v] = 1.0 / sqrt(rr);
+                const double need = 0.5 * sh.tol[v] * sqrt(bb) * sh.scale[v];
+                const double t = fmax(a.inner_tol, fmin(need, 1.0));
+                sh.target[v] = t * t;
             }
         }
-        __syncthreads();
+        const bool any = __syncthreads_or(my_any) != 0;
+        const bool anyzero = __syncthreads_or(my_zero) != 0;
         prof(sh, kPrfScalar);
         first_outer = false;
         {
-            bool anyzero = false;
-            for (int l = l0; l < l1; ++l) anyzero |= sh.zero[l] != 0;
             if (anyzero) {
-                run_phase<0>(a, sh, l0, l1, [&](int l) { return sh.zero[l] != 0; },
-                             [&](int, int64_t r0, int64_t r1, double*) {
-                                 for (int64_t row = r0 + tid; row < r1; row += kBS) a.x[row] = 0.0;
-                             });
+                run_phase<0>(a, sh, [&](int v) { return sh.zero[v] != 0; }, [&](const Chunk& ch, double*) {
+                    for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) a.x[ch.vb + row] = 0.0;
+                });
                 prof(sh, kPrfOther);
                 // other CTAs read these rows in the next phases
                 if (!gsync(a, sh)) return false;
-                for (int l = tid; l < MS_MAXL; l += kBS) sh.zero[l] = 0;
+                for (int v = tid; v < kMaxV; v += kBS) sh.zero[v] = 0;
                 __syncthreads();
             }
         }
-        if (!sh.any) break;
+        if (!any) break;
 
         if (MODE == 1) {
             // ---- P2: r32 = r / |r|, x32 = 0
-            run_phase<0>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
-                         [&](int l, int64_t r0, int64_t r1, double*) {
-                             const double sc = sh.scale[l];
-                             for (int64_t row = r0 + tid; row < r1; row += kBS) {
-                                 a.r32[row] = (float)(a.r[row] * sc);
-                                 a.x32[row] = 0.f;
-                             }
-                         });
-            if (tid == 0)
-                for (int l = l0; l < l1; ++l)
-                    if (sh.act[l]) sh.bytes += (double)(a.off[l + 1] - a.off[l]) * 16.0;
+            run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0; }, [&](const Chunk& ch, double*) {
+                const double sc = sh.scale[ch.v];
+                for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
+                    a.r32[ch.vb + row] = (float)(a.r[ch.vb + row] * sc);
+                    a.x32[ch.vb + row] = 0.f;
+                }
+            });
+            for (int v = tid; v < V; v += kBS)
+                if (sh.act[v]) sh.vbytes[v] += (double)(a.off[v % L + 1] - a.off[v % L]) * 16.0;
             prof(sh, kPrfOther);
             if (!gsync(a, sh)) return false;
         }
@@ -435,231 +462,243 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
             const bool use_pc = MODE == 1 && a.pc;
             if (use_pc) {
                 // G1: u1 = G r  (row pattern: self + preceding neighbours)
-                run_phase<0>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0 && !sh.pcoff[l]; },
-                             [&](int, int64_t r0, int64_t r1, double*) {
-                                 for (int64_t row = r0 + tid; row < r1; row += kBS) {
+                run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0 && !sh.pcoff[v]; },
+                             [&](const Chunk& ch, double*) {
+                                 const float* rv = a.r32 + ch.vb;
+                                 for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
                                      float acc = 0.f;
 #pragma unroll
                                      for (int k = 0; k < kPcOut; ++k) {
                                          const int32_t c = __ldg(a.gcol + row * kPcOut + k);
-                                         if (c >= 0) acc = fmaf(__ldg(a.gval + row * kPcOut + k), a.r32[c], acc);
+                                         if (c >= 0) acc = fmaf(__ldg(a.gval + row * kPcOut + k), rv[c], acc);
                                      }
-                                     a.u1_32[row] = acc;
+                                     a.u1_32[ch.vb + row] = acc;
                                  }
                              });
                 prof(sh, kPrfOther);
                 if (!gsync(a, sh)) return false;
                 // G2: u = G^T u1
-                run_phase<0>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0 && !sh.pcoff[l]; },
-                             [&](int, int64_t r0, int64_t r1, double*) {
-                                 for (int64_t row = r0 + tid; row < r1; row += kBS) {
+                run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0 && !sh.pcoff[v]; },
+                             [&](const Chunk& ch, double*) {
+                                 const float* u1 = a.u1_32 + ch.vb;
+                                 for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
                                      float acc = 0.f;
                                      const int64_t e = __ldg(a.gt_rp + row + 1);
                                      for (int64_t k = __ldg(a.gt_rp + row); k < e; ++k)
-                                         acc = fmaf(__ldg(a.gt_val + k), a.u1_32[__ldg(a.gt_col + k)], acc);
-                                     a.u32[row] = acc;
+                                         acc = fmaf(__ldg(a.gt_val + k), u1[__ldg(a.gt_col + k)], acc);
+                                     a.u32[ch.vb + row] = acc;
                                  }
                              });
                 prof(sh, kPrfOther);
                 if (!gsync(a, sh)) return false;
             }
             // M: w = A u; gamma = r.u, delta = w.u, rho = r.r
-            run_phase<3>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
-                         [&](int l, int64_t r0, int64_t r1, double* acc) {
-                             const float* uin = (use_pc && !sh.pcoff[l]) ? a.u32 : a.r32;
-                             if (MODE == 1 && a.mf) {
-                                 // matrix-free: the cells whose first point lies in [r0, r1)
-                                 const MFLevel& g = a.mfv.lv[l];
-                                 int64_t cfirst = a.mfv.cellid[r0];
-                                 if (a.mfv.cell_start[g.cell_off + cfirst] < r0) ++cfirst;
-                                 const int64_t cend = (int64_t)a.mfv.cellid[r1 - 1] + 1;
-                                 mf_cells_any(a.mfv, l, cfirst, cend, tid >> 5, kNW, a.mf_tpp, uin,
-                                              [&](int64_t row, float y) {
-                                                  const float ri = a.r32[row], ui = uin[row];
-                                                  a.q32[row] = y;
-                                                  acc[0] += (double)ri * (double)ui;
-                                                  acc[1] += (double)ui * (double)y;
-                                                  acc[2] += (double)(ri * ri);
-                                              });
-                                 return;
-                             }
-                             const int S = a.tprA[l];
-                             rows_by_subwarp(r0, r1, S, [&](int64_t row, bool ok, int sl) {
-                                 int64_t s = 0, e = 0;
-                                 if (ok) { s = a.Arp[row]; e = a.Arp[row + 1]; }
-                                 if (MODE == 0) {
-                                     const double y = csr_row<double, double, double>(a.Acol, a.Av64, a.r, s, e, sl, S);
-                                     if (ok && sl == 0) {
-                                         const double ri = a.r[row];
-                                         a.q[row] = y;
-                                         acc[0] += ri * ri;
-                                         acc[1] += ri * y;
-                                         acc[2] += ri * ri;
-                                     }
-                                 } else {
-                                     const float y = csr_row<float, float, float>(a.Acol, a.Av32, uin, s, e, sl, S);
-                                     if (ok && sl == 0) {
-                                         const float ri = a.r32[row], ui = uin[row];
-                                         a.q32[row] = y;
-                                         acc[0] += (double)ri * (double)ui;
-                                         acc[1] += (double)ui * (double)y;
-                                         acc[2] += (double)(ri * ri);
-                                     }
-                                 }
-                             });
-                         });
+            run_phase<3>(a, sh, [&](int v) { return sh.act[v] != 0; }, [&](const Chunk& ch, double* acc) {
+                if (MODE == 0) {
+                    const int S = a.tprA[ch.l];
+                    const double* rv = a.r + ch.vb;
+                    rows_by_subwarp(ch.r0, ch.r1, S, [&](int64_t row, bool ok, int sl) {
+                        int64_t s = 0, e = 0;
+                        if (ok) { s = a.Arp[row]; e = a.Arp[row + 1]; }
+                        const double y = csr_row<double, double, double>(a.Acol, a.Av64, rv, s, e, sl, S);
+                        if (ok && sl == 0) {
+                            const double ri = rv[row];
+                            a.q[ch.vb + row] = y;
+                            acc[0] += ri * ri;
+                            acc[1] += ri * y;
+                            acc[2] += ri * ri;
+                        }
+                    });
+                    return;
+                }
+                const float* uin = ((use_pc && !sh.pcoff[ch.v]) ? a.u32 : a.r32) + ch.vb;
+                const float* rv = a.r32 + ch.vb;
+                float* qv = a.q32 + ch.vb;
+                if (a.mf) {
+                    // matrix-free: the cells whose first point lies in [r0, r1)
+                    const MFLevel& g = a.mfv.lv[ch.l];
+                    int64_t cfirst = a.mfv.cellid[ch.r0];
+                    if (a.mfv.cell_start[g.cell_off + cfirst] < ch.r0) ++cfirst;
+                    const int64_t cend = (int64_t)a.mfv.cellid[ch.r1 - 1] + 1;
+                    mf_cells_any(a.mfv, ch.l, cfirst, cend, tid >> 5, kNW, a.mf_tpp, uin,
+                                 [&](int64_t row, float y) {
+                                     const float ri = rv[row], ui = uin[row];
+                                     qv[row] = y;
+                                     acc[0] += (double)ri * (double)ui;
+                                     acc[1] += (double)ui * (double)y;
+                                     acc[2] += (double)(ri * ri);
+                                 });
+                    return;
+                }
+                const int S = a.tprA[ch.l];
+                rows_by_subwarp(ch.r0, ch.r1, S, [&](int64_t row, bool ok, int sl) {
+                    int64_t s = 0, e = 0;
+                    if (ok) { s = a.Arp[row]; e = a.Arp[row + 1]; }
+                    const float y = csr_row<float, float, float>(a.Acol, a.Av32, uin, s, e, sl, S);
+                    if (ok && sl == 0) {
+                        const float ri = rv[row], ui = uin[row];
+                        qv[row] = y;
+                        acc[0] += (double)ri * (double)ui;
+                        acc[1] += (double)ui * (double)y;
+                        acc[2] += (double)(ri * ri);
+                    }
+                });
+            });
             prof(sh, kPrfMatvec);
-            if (!gsync_reduce<3>(a, sh, l0, l1)) return false;
-            if (tid == 0) {
-                sh.any = 0;
-                for (int l = l0; l < l1; ++l) {
-                    if (!sh.act[l]) continue;
-                    const double gam = sh.out[0][l], del = sh.out[1][l], rho = sh.out[2][l];
-                    const bool lpc = use_pc && !sh.pcoff[l];
-                    sh.bytes += (double)a.nnzA[l] * (MODE == 0 ? 12.0 : 8.0) +
-                                (double)(a.off[l + 1] - a.off[l]) * (MODE == 0 ? 32.0 : (lpc ? 24.0 : 20.0));
-                    if (lpc) sh.bytes += (double)(a.off[l + 1] - a.off[l]) * (2.0 * kPcOut * 12.0 + 16.0);
+            if (!gsync_reduce<3>(a, sh)) return false;
+            int my_go = 0;
+            {
+                for (int v = tid; v < V; v += kBS) {
+                    if (!sh.act[v]) continue;
+                    const int l = v % L;
+                    const double gam = sh.out[0][v], del = sh.out[1][v], rho = sh.out[2][v];
+                    const bool lpc = use_pc && !sh.pcoff[v];
+                    const double n = (double)(a.off[l + 1] - a.off[l]);
+                    sh.vbytes[v] += (double)a.nnzA[l] * (MODE == 0 ? 12.0 : 8.0) + n * (MODE == 0 ? 32.0 : (lpc ? 24.0 : 20.0));
+                    if (lpc) sh.vbytes[v] += n * (2.0 * kPcOut * 12.0 + 16.0);
                     if (!isfinite(gam) || !isfinite(del) || !isfinite(rho)) {
-                        sh.act[l] = 0;
-                        sh.oact[l] = 0;
+                        sh.act[v] = 0;
+                        sh.oact[v] = 0;
                         if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)MS_ERR_NUMERIC);
                         continue;
                     }
-                    if (rho <= sh.target[l] || sh.it_solve[l] >= a.max_iters) {
-                        sh.act[l] = 0;  // converged (recursive residual) or capped
+                    if (rho <= sh.target[v] || sh.it_solve[v] >= a.max_iters) {
+                        sh.act[v] = 0;  // converged (recursive residual) or capped
                         continue;
                     }
                     if (lpc && !(gam > 0.0)) {
                         // r^T M r <= 0 cannot happen for an SPD M: treat the preconditioner as
                         // broken and fall back to plain CG from the current iterate
-                        sh.pcoff[l] = 1;
-                        sh.fallbacks += 1;
-                        sh.act[l] = 0;
+                        sh.pcoff[v] = 1;
+                        sh.fb[v] += 1;
+                        sh.act[v] = 0;
                         continue;
                     }
                     double al, be;
-                    if (sh.first[l]) {
+                    if (sh.first[v]) {
                         be = 0.0;
                         al = del > 0.0 ? gam / del : -1.0;
                     } else {
-                        be = gam / sh.gam[l];
-                        const double den = del - be * gam / sh.alpha[l];
+                        be = gam / sh.gam[v];
+                        const double den = del - be * gam / sh.alpha[v];
                         al = den > 0.0 ? gam / den : -1.0;
                     }
                     if (!(al > 0.0)) {
-                        if (MODE == 1 && !sh.first[l]) {
+                        if (MODE == 1 && !sh.first[v]) {
                             // lost curvature in the FP32 recurrence (cancellation on an ill-conditioned
                             // level): end this inner solve; the FP64 true residual restarts it
-                            sh.act[l] = 0;
+                            sh.act[v] = 0;
                             continue;
                         }
                         if (lpc) {  // u^T A u <= 0 at a restart: the preconditioner is unusable here
-                            sh.pcoff[l] = 1;
-                            sh.fallbacks += 1;
-                            sh.act[l] = 0;
+                            sh.pcoff[v] = 1;
+                            sh.fb[v] += 1;
+                            sh.act[v] = 0;
                             continue;
                         }
                         // p^T A p <= 0 at a restart: A_l is not positive definite in floating point
-                        sh.act[l] = 0;
-                        sh.oact[l] = 0;
+                        sh.act[v] = 0;
+                        sh.oact[v] = 0;
                         if (blockIdx.x == 0) atomicCAS(a.status, 0, (int)MS_ERR_NOT_SPD);
                         continue;
                     }
-                    sh.fresh[l] = sh.first[l];  // the update must not read the old p, s
-                    sh.first[l] = 0;
-                    sh.alpha[l] = al;
-                    sh.beta[l] = be;
-                    sh.gam[l] = gam;
-                    sh.it_solve[l] += 1;
-                    sh.it_total[l] += 1;
-                    sh.bytes += (double)(a.off[l + 1] - a.off[l]) * (MODE == 0 ? 72.0 : 36.0);
-                    sh.any = 1;
+                    sh.fresh[v] = sh.first[v];  // the update must not read the old p, s
+                    sh.first[v] = 0;
+                    sh.alpha[v] = al;
+                    sh.beta[v] = be;
+                    sh.gam[v] = gam;
+                    sh.it_solve[v] += 1;
+                    sh.it_total[v] += 1;
+                    sh.vbytes[v] += n * (MODE == 0 ? 72.0 : 36.0);
+                    my_go = 1;
                 }
             }
-            __syncthreads();
+            const bool go = __syncthreads_or(my_go) != 0;
             prof(sh, kPrfScalar);
-            if (!sh.any) break;
+            if (!go) break;
             // E: p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s
-            run_phase<0>(a, sh, l0, l1, [&](int l) { return sh.act[l] != 0; },
-                         [&](int l, int64_t r0, int64_t r1, double*) {
-                             const double al = sh.alpha[l], be = sh.beta[l];
-                             // first iteration: p = u, s = w (the old p, s are not read: they may
-                             // hold anything, and 0 * NaN would poison the recurrence)
-                             const bool fr = sh.fresh[l] != 0;
-                             if (MODE == 0) {
-                                 for (int64_t row = r0 + tid; row < r1; row += kBS) {
-                                     const double ri = a.r[row];
-                                     const double pi = fr ? ri : ri + be * a.p[row];
-                                     const double si = fr ? a.q[row] : a.q[row] + be * a.s[row];
-                                     a.p[row] = pi;
-                                     a.s[row] = si;
-                                     a.x[row] += al * pi;
-                                     a.r[row] = ri - al * si;
-                                 }
-                             } else {
-                                 const float af = (float)al, bf = (float)be;
-                                 const float* uin = (use_pc && !sh.pcoff[l]) ? a.u32 : a.r32;
-                                 for (int64_t row = r0 + tid; row < r1; row += kBS) {
-                                     const float ri = a.r32[row];
-                                     const float pi = fr ? uin[row] : fmaf(bf, a.p32[row], uin[row]);
-                                     const float si = fr ? a.q32[row] : fmaf(bf, a.s32[row], a.q32[row]);
-                                     a.p32[row] = pi;
-                                     a.s32[row] = si;
-                                     a.x32[row] = fmaf(af, pi, a.x32[row]);
-                                     a.r32[row] = fmaf(-af, si, ri);
-                                 }
-                             }
-                         });
+            run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0; }, [&](const Chunk& ch, double*) {
+                const double al = sh.alpha[ch.v], be = sh.beta[ch.v];
+                // first iteration: p = u, s = w (the old p, s are not read: they may
+                // hold anything, and 0 * NaN would poison the recurrence)
+                const bool fr = sh.fresh[ch.v] != 0;
+                const int64_t vb = ch.vb;
+                if (MODE == 0) {
+                    for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
+                        const int64_t i = vb + row;
+                        const double ri = a.r[i];
+                        const double pi = fr ? ri : ri + be * a.p[i];
+                        const double si = fr ? a.q[i] : a.q[i] + be * a.s[i];
+                        a.p[i] = pi;
+                        a.s[i] = si;
+                        a.x[i] += al * pi;
+                        a.r[i] = ri - al * si;
+                    }
+                } else {
+                    const float af = (float)al, bf = (float)be;
+                    const float* uin = (use_pc && !sh.pcoff[ch.v]) ? a.u32 : a.r32;
+                    for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
+                        const int64_t i = vb + row;
+                        const float ri = a.r32[i];
+                        const float pi = fr ? uin[i] : fmaf(bf, a.p32[i], uin[i]);
+                        const float si = fr ? a.q32[i] : fmaf(bf, a.s32[i], a.q32[i]);
+                        a.p32[i] = pi;
+                        a.s32[i] = si;
+                        a.x32[i] = fmaf(af, pi, a.x32[i]);
+                        a.r32[i] = fmaf(-af, si, ri);
+                    }
+                }
+            });
             prof(sh, kPrfUpdate);
             if (!gsync(a, sh)) return false;
         }
 
         if (MODE == 1) {
             // ---- P3: x += |r| d  (FP64)
-            run_phase<0>(a, sh, l0, l1, [&](int l) { return sh.oact[l] != 0 && sh.scale[l] > 0.0; },
-                         [&](int l, int64_t r0, int64_t r1, double*) {
-                             const double inv = 1.0 / sh.scale[l];
-                             for (int64_t row = r0 + tid; row < r1; row += kBS)
-                                 a.x[row] += (double)a.x32[row] * inv;
+            run_phase<0>(a, sh, [&](int v) { return sh.oact[v] != 0 && sh.scale[v] > 0.0; },
+                         [&](const Chunk& ch, double*) {
+                             const double inv = 1.0 / sh.scale[ch.v];
+                             for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS)
+                                 a.x[ch.vb + row] += (double)a.x32[ch.vb + row] * inv;
                          });
-            if (tid == 0)
-                for (int l = l0; l < l1; ++l)
-                    if (sh.oact[l]) sh.bytes += (double)(a.off[l + 1] - a.off[l]) * 20.0;
+            for (int v = tid; v < V; v += kBS)
+                if (sh.oact[v]) sh.vbytes[v] += (double)(a.off[v % L + 1] - a.off[v % L]) * 20.0;
             prof(sh, kPrfOther);
             if (!gsync(a, sh)) return false;
         }
     }
     // levels still active after max_outer rounds did not reach the tolerance
-    if (tid == 0)
-        for (int l = l0; l < l1; ++l)
-            if (sh.oact[l] && blockIdx.x == 0) atomicCAS(a.status, 0, (int)MS_ERR_NOT_CONVERGED);
+    if (blockIdx.x == 0)
+        for (int v = tid; v < V; v += kBS)
+            if (sh.oact[v]) atomicCAS(a.status, 0, (int)MS_ERR_NOT_CONVERGED);
     __syncthreads();
     return true;
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(kBS) k_fit(SolveArgs a) {
-    __shared__ Shared sh;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Shared& sh = *reinterpret_cast<Shared*>(smem_raw);
     const int tid = threadIdx.x;
-    for (int l = tid; l < MS_MAXL; l += kBS) {
-        sh.it_total[l] = 0;
-        sh.refines[l] = 0;
-        sh.scale[l] = 0.0;
+    for (int v = tid; v < kMaxV; v += kBS) {
+        sh.it_total[v] = 0;
+        sh.refines[v] = 0;
+        sh.fb[v] = 0;
+        sh.vbytes[v] = 0.0;
+        sh.scale[v] = 0.0;
     }
     if (tid == 0) {
         sh.bytes = 0.0;
-        sh.any = 0;
-        sh.fallbacks = 0;
         for (int i = 0; i < kProf; ++i) sh.pt[i] = 0ull;
         sh.tprev = ms_globaltimer();
     }
     __syncthreads();
     const int L = a.L;
     // beta_0 = f, x = 0
-    run_phase<0>(a, sh, 0, L, [](int) { return true; }, [&](int, int64_t r0, int64_t r1, double*) {
-        for (int64_t row = r0 + tid; row < r1; row += kBS) {
-            a.beta[row] = a.f[row];
-            a.x[row] = 0.0;
+    run_phase<0>(a, sh, [](int) { return true; }, [&](const Chunk& ch, double*) {
+        for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
+            a.beta[ch.vb + row] = a.f[ch.vb + row];
+            a.x[ch.vb + row] = 0.0;
         }
     });
     prof(sh, kPrfOther);
@@ -670,19 +709,19 @@ __global__ void __launch_bounds__(kBS) k_fit(SolveArgs a) {
         }
         if (m + 1 <= L - 1) {
             // beta_k = f_k - sum_{j<k} B_kj t_j for the rows of levels k = m+1..L-1 (FP64)
-            run_phase<0>(a, sh, m + 1, L, [](int) { return true; },
-                         [&](int l, int64_t r0, int64_t r1, double*) {
-                             const int S = a.tprB[l];
-                             rows_by_subwarp(r0, r1, S, [&](int64_t row, bool ok, int sl) {
-                                 int64_t s = 0, e = 0;
-                                 if (ok) { s = a.Brp[row]; e = a.Brp[row + 1]; }
-                                 const double y = csr_row<double, double, double>(a.Bcol, a.Bv64, a.x, s, e, sl, S);
-                                 if (ok && sl == 0) a.beta[row] = a.f[row] - y;
-                             });
-                         });
+            run_phase<0>(a, sh, [&](int v) { return v % L >= m + 1; }, [&](const Chunk& ch, double*) {
+                const int S = a.tprB[ch.l];
+                const double* xv = a.x + ch.vb;
+                rows_by_subwarp(ch.r0, ch.r1, S, [&](int64_t row, bool ok, int sl) {
+                    int64_t s = 0, e = 0;
+                    if (ok) { s = a.Brp[row]; e = a.Brp[row + 1]; }
+                    const double y = csr_row<double, double, double>(a.Bcol, a.Bv64, xv, s, e, sl, S);
+                    if (ok && sl == 0) a.beta[ch.vb + row] = a.f[ch.vb + row] - y;
+                });
+            });
             if (tid == 0)
                 for (int l = m + 1; l < L; ++l)
-                    sh.bytes += (double)a.nnzB[l] * 12.0 + (double)(a.off[l + 1] - a.off[l]) * 32.0;
+                    sh.bytes += a.R * ((double)a.nnzB[l] * 12.0 + (double)(a.off[l + 1] - a.off[l]) * 32.0);
             prof(sh, kPrfLower);
             if (!gsync(a, sh)) return;
         }
@@ -690,12 +729,24 @@ __global__ void __launch_bounds__(kBS) k_fit(SolveArgs a) {
     if (!solve_levels<MODE>(a, sh, 0, L, true)) return;
     if (blockIdx.x == 0 && tid == 0) {
         for (int l = 0; l < L; ++l) {
-            a.iters[l] = sh.it_total[l];
-            a.refines[l] = sh.refines[l];
+            long long it = 0;
+            int rf = 0;
+            for (int r = 0; r < a.R; ++r) {
+                it += sh.it_total[r * L + l];
+                rf += sh.refines[r * L + l];
+            }
+            a.iters[l] = it;
+            a.refines[l] = rf;
         }
-        a.bytes[0] = sh.bytes;
+        double b = sh.bytes;
+        int fb = 0;
+        for (int v = 0; v < a.V; ++v) {
+            b += sh.vbytes[v];
+            fb += sh.fb[v];
+        }
+        a.bytes[0] = b;
         for (int i = 0; i < kProf; ++i) a.prof[i] = sh.pt[i];
-        a.pcfb[0] = sh.fallbacks;
+        a.pcfb[0] = fb;
     }
 }
 
@@ -774,8 +825,8 @@ int mf_tpp_for(const ms_hierarchy* h) {
     return t;
 }
 
-// Fill the solve arguments that depend only on the hierarchy and the options.
-void fill_args(const ms_hierarchy* h, const int64_t* rpA, const int64_t* rpB, double rel_tol, SolveArgs& a) {
+// Fill the solve arguments that depend only on the hierarchy, the options and R.
+void fill_args(const ms_hierarchy* h, const int64_t* rpA, const int64_t* rpB, double rel_tol, int R, SolveArgs& a) {
     a.mf = (h->opts.precision == MS_PREC_MIXED && h->opts.op == MS_OP_MATRIX_FREE) ? 1 : 0;
     a.mf_tpp = h->mf_tpp;
     a.mfv = make_mfview(h);
@@ -785,10 +836,10 @@ void fill_args(const ms_hierarchy* h, const int64_t* rpA, const int64_t* rpB, do
     a.gt_rp = h->pc.gt_rp;
     a.gt_col = h->pc.gt_col;
     a.gt_val = h->pc.gt_val;
-    a.u32 = h->u32;
-    a.u1_32 = h->u1_32;
     const int L = h->L;
     a.L = L;
+    a.R = R;
+    a.V = R * L;
     a.N = h->N;
     int64_t c = 0;
     for (int l = 0; l <= L; ++l) {
@@ -796,6 +847,7 @@ void fill_args(const ms_hierarchy* h, const int64_t* rpA, const int64_t* rpB, do
         a.coff[l] = c;
         if (l < L) c += (h->view.off[l + 1] - h->view.off[l] + kChunk - 1) / kChunk;
     }
+    a.C = c;
     for (int l = 0; l < L; ++l) {
         const int64_t n = h->view.off[l + 1] - h->view.off[l];
         a.nnzA[l] = rpA[l + 1] - rpA[l];
@@ -815,59 +867,98 @@ void fill_args(const ms_hierarchy* h, const int64_t* rpA, const int64_t* rpB, do
     a.timeout_ns = 4000000000ull;
 }
 
-}  // namespace
+// The solve kernel's per-CTA state is above the default 48 KB of dynamic shared memory.
+ms_status set_fit_smem() {
+    MS_CUDA(cudaFuncSetAttribute(k_fit<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared)));
+    MS_CUDA(cudaFuncSetAttribute(k_fit<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared)));
+    return MS_OK;
+}
 
-// ---------------------------------------------------------------- host side
-
-static ms_status ensure_workspace(ms_hierarchy* h) {
-    if (h->f) return MS_OK;
-    const int64_t N = h->N;
-    MS_TRY(ms_alloc(h, (void**)&h->f, sizeof(double) * N));
-    MS_TRY(ms_alloc(h, (void**)&h->beta, sizeof(double) * N));
-    MS_TRY(ms_alloc(h, (void**)&h->x, sizeof(double) * N));
-    MS_TRY(ms_alloc(h, (void**)&h->r, sizeof(double) * N));
-    MS_TRY(ms_alloc(h, (void**)&h->p, sizeof(double) * N));
-    MS_TRY(ms_alloc(h, (void**)&h->q, sizeof(double) * N));
-    MS_TRY(ms_alloc(h, (void**)&h->s, sizeof(double) * N));
-    if (!h->tmp64) MS_TRY(ms_alloc(h, (void**)&h->tmp64, sizeof(double) * N));
-    if (h->opts.precision == MS_PREC_MIXED) {
-        MS_TRY(ms_alloc(h, (void**)&h->x32, sizeof(float) * N));
-        MS_TRY(ms_alloc(h, (void**)&h->r32, sizeof(float) * N));
-        MS_TRY(ms_alloc(h, (void**)&h->p32, sizeof(float) * N));
-        MS_TRY(ms_alloc(h, (void**)&h->q32, sizeof(float) * N));
-        MS_TRY(ms_alloc(h, (void**)&h->s32, sizeof(float) * N));
-    }
-    int dev = 0, sms = 0, per_sm = 0;
-    MS_CUDA(cudaGetDevice(&dev));
+ms_status fit_blocks(bool mixed, int dev, int* blocks) {
+    MS_TRY(set_fit_smem());
+    int sms = 0, per_sm = 0;
     MS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (h->opts.precision == MS_PREC_MIXED)
-        MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fit<1>, kBS, 0));
+    if (mixed)
+        MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fit<1>, kBS, sizeof(Shared)));
     else
-        MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fit<0>, kBS, 0));
+        MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fit<0>, kBS, sizeof(Shared)));
     if (per_sm < 1) {
         ms_set_error(MS_ERR_CUDA, "solve kernel cannot be resident on an SM");
         return MS_ERR_CUDA;
     }
-    h->solve_blocks = std::min(sms * std::min(per_sm, 2), (kBarWords - 2) * kGroup);
+    *blocks = std::min(sms * std::min(per_sm, 2), kMaxGroups * kGroup);
+    return MS_OK;
+}
+
+// Right-hand sides per launch: every (right-hand side, level) pair is a virtual level.
+int rhs_per_launch(const ms_hierarchy* h, int nrhs) { return std::max(1, std::min(nrhs, std::min(32, kMaxV / h->L))); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+
+static ms_status ensure_workspace(ms_hierarchy* h, int R) {
+    if (h->f && h->ws_rhs >= R) return MS_OK;
+    const int64_t n = h->N * (int64_t)R;
+    MS_TRY(ms_realloc(h, (void**)&h->f, sizeof(double) * n));
+    MS_TRY(ms_realloc(h, (void**)&h->beta, sizeof(double) * n));
+    MS_TRY(ms_realloc(h, (void**)&h->x, sizeof(double) * n));
+    MS_TRY(ms_realloc(h, (void**)&h->r, sizeof(double) * n));
+    MS_TRY(ms_realloc(h, (void**)&h->p, sizeof(double) * n));
+    MS_TRY(ms_realloc(h, (void**)&h->q, sizeof(double) * n));
+    MS_TRY(ms_realloc(h, (void**)&h->s, sizeof(double) * n));
+    if (!h->tmp64) MS_TRY(ms_alloc(h, (void**)&h->tmp64, sizeof(double) * h->N));
+    if (h->opts.precision == MS_PREC_MIXED) {
+        MS_TRY(ms_realloc(h, (void**)&h->x32, sizeof(float) * n));
+        MS_TRY(ms_realloc(h, (void**)&h->r32, sizeof(float) * n));
+        MS_TRY(ms_realloc(h, (void**)&h->p32, sizeof(float) * n));
+        MS_TRY(ms_realloc(h, (void**)&h->q32, sizeof(float) * n));
+        MS_TRY(ms_realloc(h, (void**)&h->s32, sizeof(float) * n));
+        if (h->opts.precond != MS_PRECOND_NONE) {
+            MS_TRY(ms_realloc(h, (void**)&h->u32, sizeof(float) * n));
+            MS_TRY(ms_realloc(h, (void**)&h->u1_32, sizeof(float) * n));
+        }
+    }
+    int dev = 0;
+    MS_CUDA(cudaGetDevice(&dev));
+    MS_TRY(fit_blocks(h->opts.precision == MS_PREC_MIXED, dev, &h->solve_blocks));
     h->mf_tpp = mf_tpp_for(h);
-    MS_TRY(ms_alloc(h, (void**)&h->part, sizeof(double) * kAcc * MS_MAXL * h->solve_blocks));
-    MS_TRY(ms_alloc(h, (void**)&h->scal, sizeof(double) * kAcc * MS_MAXL));
-    MS_TRY(ms_alloc(h, (void**)&h->bar, sizeof(unsigned) * kBarWords));
-    MS_TRY(ms_alloc(h, (void**)&h->status, sizeof(int)));
-    MS_TRY(ms_alloc(h, (void**)&h->iters, sizeof(int64_t) * MS_MAXL));
-    MS_TRY(ms_alloc(h, (void**)&h->refines, sizeof(int) * MS_MAXL));
-    MS_TRY(ms_alloc(h, (void**)&h->resid, sizeof(double) * MS_MAXL));
-    MS_TRY(ms_alloc(h, (void**)&h->bytes, sizeof(double)));
-    MS_TRY(ms_alloc(h, (void**)&h->prof, sizeof(unsigned long long) * kProf));
-    MS_TRY(ms_alloc(h, (void**)&h->pcfb, sizeof(int)));
+    const int V = R * h->L;
+    MS_TRY(ms_realloc(h, (void**)&h->part, sizeof(double) * kAcc * V * h->solve_blocks));
+    MS_TRY(ms_realloc(h, (void**)&h->gpart, sizeof(double) * kMaxGroups * kAcc * V));
+    MS_TRY(ms_realloc(h, (void**)&h->scal, sizeof(double) * kAcc * V));
+    MS_TRY(ms_realloc(h, (void**)&h->resid, sizeof(double) * V));
+    if (!h->bar) {
+        MS_TRY(ms_alloc(h, (void**)&h->bar, sizeof(unsigned) * kBarWords));
+        MS_TRY(ms_alloc(h, (void**)&h->status, sizeof(int)));
+        MS_TRY(ms_alloc(h, (void**)&h->iters, sizeof(int64_t) * MS_MAXL));
+        MS_TRY(ms_alloc(h, (void**)&h->refines, sizeof(int) * MS_MAXL));
+        MS_TRY(ms_alloc(h, (void**)&h->bytes, sizeof(double)));
+        MS_TRY(ms_alloc(h, (void**)&h->prof, sizeof(unsigned long long) * kProf));
+        MS_TRY(ms_alloc(h, (void**)&h->pcfb, sizeof(int)));
+    }
+    h->ws_rhs = R;
     return MS_OK;
 }
 
 ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel_tol, double* alpha_dev,
                       ms_fit_stats* stats, cudaStream_t st) {
-    MS_TRY(ensure_workspace(h));
+    const int Rmax = rhs_per_launch(h, nrhs);
+    MS_TRY(ensure_workspace(h, Rmax));
     const int L = h->L;
     const int64_t N = h->N;
+    const bool mixed = h->opts.precision == MS_PREC_MIXED;
+    if (mixed && h->opts.op != MS_OP_MATRIX_FREE && !h->A.v32) {
+        ms_set_error(MS_ERR_STATE, "MIXED fit needs FP32 values (build with precision = MS_PREC_MIXED)");
+        return MS_ERR_STATE;
+    }
+    if (h->opts.precond != MS_PRECOND_NONE) {
+        if (!mixed) {
+            ms_set_error(MS_ERR_ARG, "a preconditioner needs precision = MS_PREC_MIXED (it acts on the FP32 inner CG)");
+            return MS_ERR_ARG;
+        }
+        MS_TRY(ms_pc_build(h, h->opts.precond, st));
+    }
     // per-level nnz (row offsets at the level boundaries)
     std::vector<int64_t> rpA(L + 1), rpB(L + 1);
     for (int l = 0; l <= L; ++l) {
@@ -876,62 +967,52 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
     }
     MS_CUDA(cudaStreamSynchronize(st));
 
-    SolveArgs a{};
-    fill_args(h, rpA.data(), rpB.data(), rel_tol, a);
-    a.f = h->f; a.beta = h->beta; a.x = h->x; a.r = h->r; a.p = h->p; a.q = h->q; a.s = h->s;
-    a.x32 = h->x32; a.r32 = h->r32; a.p32 = h->p32; a.q32 = h->q32; a.s32 = h->s32;
-    a.part = h->part; a.scal = h->scal; a.bar = h->bar; a.status = h->status;
-    a.iters = h->iters; a.refines = h->refines; a.resid = h->resid; a.bytes = h->bytes; a.prof = h->prof;
-    a.pcfb = h->pcfb;
-    if (h->opts.precond != MS_PRECOND_NONE) {
-        if (h->opts.precision != MS_PREC_MIXED) {
-            ms_set_error(MS_ERR_ARG, "a preconditioner needs precision = MS_PREC_MIXED (it acts on the FP32 inner CG)");
-            return MS_ERR_ARG;
-        }
-        MS_TRY(ms_pc_build(h, h->opts.precond, st));
-        a.gcol = h->pc.gcol; a.gval = h->pc.gval;
-        a.gt_rp = h->pc.gt_rp; a.gt_col = h->pc.gt_col; a.gt_val = h->pc.gt_val;
-        a.u32 = h->u32; a.u1_32 = h->u1_32;
-    }
-    const bool mixed = h->opts.precision == MS_PREC_MIXED;
-    if (mixed && h->opts.op != MS_OP_MATRIX_FREE && !h->A.v32) {
-        ms_set_error(MS_ERR_STATE, "MIXED fit needs FP32 values (build with precision = MS_PREC_MIXED)");
-        return MS_ERR_STATE;
-    }
-
     ms_status result = MS_OK;
     int launches = 0;
     float total_ms = 0.f;
     double bytes = 0.0;
     std::vector<int64_t> it(MS_MAXL, 0), it_sum(MS_MAXL, 0);
-    std::vector<int> ref(MS_MAXL, 0);
-    std::vector<double> res(MS_MAXL, 0.0);
+    std::vector<int> ref(MS_MAXL, 0), ref_sum(MS_MAXL, 0);
+    std::vector<double> res(kMaxV, 0.0), res_max(MS_MAXL, 0.0);
     double phase[kProf] = {};
     int fallbacks = 0;
     int dstat = 0;
-    for (int col = 0; col < nrhs; ++col) {
-        ms_gather_sorted(f_dev, h->f, h->perm, N, nrhs, col, st);
-        ++launches;
+    for (int col0 = 0; col0 < nrhs; col0 += Rmax) {
+        const int R = std::min(Rmax, nrhs - col0);
+        SolveArgs a{};
+        fill_args(h, rpA.data(), rpB.data(), rel_tol, R, a);
+        a.f = h->f; a.beta = h->beta; a.x = h->x; a.r = h->r; a.p = h->p; a.q = h->q; a.s = h->s;
+        a.x32 = h->x32; a.r32 = h->r32; a.p32 = h->p32; a.q32 = h->q32; a.s32 = h->s32;
+        a.u32 = h->u32; a.u1_32 = h->u1_32;
+        a.part = h->part; a.gpart = h->gpart; a.scal = h->scal; a.bar = h->bar; a.status = h->status;
+        a.iters = h->iters; a.refines = h->refines; a.resid = h->resid; a.bytes = h->bytes; a.prof = h->prof;
+        a.pcfb = h->pcfb;
+        for (int r = 0; r < R; ++r) {
+            ms_gather_sorted(f_dev, h->f + (int64_t)r * N, h->perm, N, nrhs, col0 + r, st);
+            ++launches;
+        }
         MS_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * kBarWords, st));
         MS_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
-        MS_CUDA(cudaMemsetAsync(h->resid, 0, sizeof(double) * MS_MAXL, st));
+        MS_CUDA(cudaMemsetAsync(h->resid, 0, sizeof(double) * a.V, st));
         void* args[] = {&a};
         MS_CUDA(cudaEventRecord(h->ev0, st));
         if (mixed)
-            MS_CUDA(cudaLaunchCooperativeKernel((void*)k_fit<1>, dim3(h->solve_blocks), dim3(kBS), args, 0, st));
+            MS_CUDA(cudaLaunchCooperativeKernel((void*)k_fit<1>, dim3(h->solve_blocks), dim3(kBS), args, sizeof(Shared), st));
         else
-            MS_CUDA(cudaLaunchCooperativeKernel((void*)k_fit<0>, dim3(h->solve_blocks), dim3(kBS), args, 0, st));
+            MS_CUDA(cudaLaunchCooperativeKernel((void*)k_fit<0>, dim3(h->solve_blocks), dim3(kBS), args, sizeof(Shared), st));
         ms_count_launch();
         MS_CUDA(cudaEventRecord(h->ev1, st));
         ++launches;
-        ms_scatter_input(h->x, alpha_dev, h->perm, N, nrhs, col, st);
-        ++launches;
+        for (int r = 0; r < R; ++r) {
+            ms_scatter_input(h->x + (int64_t)r * N, alpha_dev, h->perm, N, nrhs, col0 + r, st);
+            ++launches;
+        }
         MS_CUDA(cudaGetLastError());
         double b = 0.0;
         MS_CUDA(cudaMemcpyAsync(&dstat, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
         MS_CUDA(cudaMemcpyAsync(it.data(), h->iters, sizeof(int64_t) * MS_MAXL, cudaMemcpyDeviceToHost, st));
         MS_CUDA(cudaMemcpyAsync(ref.data(), h->refines, sizeof(int) * MS_MAXL, cudaMemcpyDeviceToHost, st));
-        MS_CUDA(cudaMemcpyAsync(res.data(), h->resid, sizeof(double) * MS_MAXL, cudaMemcpyDeviceToHost, st));
+        MS_CUDA(cudaMemcpyAsync(res.data(), h->resid, sizeof(double) * a.V, cudaMemcpyDeviceToHost, st));
         MS_CUDA(cudaMemcpyAsync(&b, h->bytes, sizeof(double), cudaMemcpyDeviceToHost, st));
         unsigned long long pr[kProf];
         MS_CUDA(cudaMemcpyAsync(pr, h->prof, sizeof(pr), cudaMemcpyDeviceToHost, st));
@@ -944,20 +1025,24 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
         bytes += b;
         for (int i = 0; i < kProf; ++i) phase[i] += 1e-6 * (double)pr[i];
         fallbacks += fb;
-        for (int l = 0; l < L; ++l) it_sum[l] += it[l];
+        for (int l = 0; l < L; ++l) {
+            it_sum[l] += it[l];
+            ref_sum[l] += ref[l];
+            for (int r = 0; r < R; ++r) res_max[l] = std::max(res_max[l], res[r * L + l]);
+        }
         if (dstat != 0 && result == MS_OK) {
             result = (ms_status)dstat;
-            ms_set_error(result, "device status %d during the fit of right-hand side %d", dstat, col);
+            ms_set_error(result, "device status %d during the fit of right-hand sides %d..%d", dstat, col0, col0 + R - 1);
         }
     }
     if (stats) {
         *stats = ms_fit_stats{};
         stats->L = L;
-        stats->sweeps = a.sweeps;
+        stats->sweeps = h->opts.jacobi_sweeps > 0 ? h->opts.jacobi_sweeps : std::max(L - 1, 0);
         for (int l = 0; l < L; ++l) {
             stats->cg_iterations[l] = it_sum[l];
-            stats->refinements[l] = ref[l];
-            stats->rel_residual[l] = res[l];
+            stats->refinements[l] = ref_sum[l];
+            stats->rel_residual[l] = res_max[l];
         }
         stats->device_status = dstat;
         stats->fit_ms = total_ms;
@@ -970,7 +1055,7 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
 }
 
 ms_status ms_apply_impl(ms_hierarchy* h, int op, const double* x_dev, double* y_dev, int sorted, cudaStream_t st) {
-    MS_TRY(ensure_workspace(h));
+    MS_TRY(ensure_workspace(h, std::max(h->ws_rhs, 1)));
     const int64_t N = h->N;
     const double* xs = x_dev;
     double* ys = y_dev;
@@ -1044,8 +1129,10 @@ constexpr size_t pad256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t kStaticVec64 = pad256(sizeof(double) * kStaticMaxPoints);
 constexpr size_t kStaticVec32 = pad256(sizeof(float) * kStaticMaxPoints);
 constexpr size_t kStaticPart = pad256(sizeof(double) * kAcc * MS_MAXL * kStaticMaxBlocks);
+constexpr size_t kStaticGpart = pad256(sizeof(double) * kMaxGroups * kAcc * MS_MAXL);
 constexpr size_t kStaticSmall = 4096;  // barrier words, status, per-level counters, residuals, sums
-constexpr size_t kStaticBytes = 7 * kStaticVec64 + 5 * kStaticVec32 + kStaticPart + kStaticSmall;  // ~5.3 MiB
+constexpr size_t kStaticBytes =
+    7 * kStaticVec64 + 5 * kStaticVec32 + kStaticPart + kStaticGpart + kStaticSmall;  // ~5.4 MiB
 
 }  // namespace
 
@@ -1111,17 +1198,9 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
     MS_TRY(fit_scratch_address(dev, &base));
     cudaStream_t st = (cudaStream_t)stream;
 
-    int sms = 0, per_sm = 0;
-    MS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (mixed)
-        MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fit<1>, kBS, 0));
-    else
-        MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fit<0>, kBS, 0));
-    if (per_sm < 1) {
-        ms_set_error(MS_ERR_CUDA, "solve kernel cannot be resident on an SM");
-        return MS_ERR_CUDA;
-    }
-    const int blocks = std::min(std::min(sms * std::min(per_sm, 2), kStaticMaxBlocks), (kBarWords - 2) * kGroup);
+    int blocks = 0;
+    MS_TRY(fit_blocks(mixed, dev, &blocks));
+    blocks = std::min(blocks, kStaticMaxBlocks);
 
     // carve the fixed array
     unsigned char* c = base;
@@ -1131,14 +1210,16 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
     for (int i = 0; i < 5; ++i, c += kStaticVec32) v32[i] = reinterpret_cast<float*>(c);
     double* part = reinterpret_cast<double*>(c);
     c += kStaticPart;
+    double* gpart = reinterpret_cast<double*>(c);
+    c += kStaticGpart;
     unsigned char* small = c;
-    unsigned* bar = reinterpret_cast<unsigned*>(small + 2560);             // [kBarWords]
     int* status = reinterpret_cast<int*>(small + 64);                      // [1]
     int64_t* iters = reinterpret_cast<int64_t*>(small + 128);              // [MS_MAXL]
     int* refines = reinterpret_cast<int*>(small + 128 + 8 * MS_MAXL);      // [MS_MAXL]
     double* resid = reinterpret_cast<double*>(small + 128 + 12 * MS_MAXL); // [MS_MAXL]
     double* bytes = reinterpret_cast<double*>(small + 128 + 20 * MS_MAXL); // [1]
     double* scal = reinterpret_cast<double*>(small + 1024);                // [kAcc][MS_MAXL]
+    unsigned* bar = reinterpret_cast<unsigned*>(small + 2560);             // [kBarWords]
     // the array keeps the previous call's contents: clear what must start at zero
     MS_CUDA(cudaMemsetAsync(small, 0, kStaticSmall, st));
 
@@ -1151,10 +1232,10 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
     MS_CUDA(cudaStreamSynchronize(st));
 
     SolveArgs a{};
-    fill_args(h, rpA, rpB, rel_tol, a);
+    fill_args(h, rpA, rpB, rel_tol, 1, a);
     a.f = v64[0]; a.beta = v64[1]; a.x = v64[2]; a.r = v64[3]; a.p = v64[4]; a.q = v64[5]; a.s = v64[6];
     a.x32 = v32[0]; a.r32 = v32[1]; a.p32 = v32[2]; a.q32 = v32[3]; a.s32 = v32[4];
-    a.part = part; a.scal = scal; a.bar = bar; a.status = status;
+    a.part = part; a.gpart = gpart; a.scal = scal; a.bar = bar; a.status = status;
     a.iters = iters; a.refines = refines; a.resid = resid; a.bytes = bytes;
     a.prof = reinterpret_cast<unsigned long long*>(small + 2048);  // [kProf]
     a.pcfb = reinterpret_cast<int*>(small + 3072);                 // [1]
@@ -1164,9 +1245,9 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
     void* args[] = {&a};
     MS_CUDA(cudaEventRecord(h->ev0, st));
     if (mixed)
-        MS_CUDA(cudaLaunchCooperativeKernel((void*)k_fit<1>, dim3(blocks), dim3(kBS), args, 0, st));
+        MS_CUDA(cudaLaunchCooperativeKernel((void*)k_fit<1>, dim3(blocks), dim3(kBS), args, sizeof(Shared), st));
     else
-        MS_CUDA(cudaLaunchCooperativeKernel((void*)k_fit<0>, dim3(blocks), dim3(kBS), args, 0, st));
+        MS_CUDA(cudaLaunchCooperativeKernel((void*)k_fit<0>, dim3(blocks), dim3(kBS), args, sizeof(Shared), st));
     ms_count_launch();
     MS_CUDA(cudaEventRecord(h->ev1, st));
     ms_scatter_input(a.x, alpha_dev, h->perm, h->N, 1, 0, st);

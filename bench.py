@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-variants", action="store_true", help="skip the comparison paths")
     p.add_argument("--no-nu8", action="store_true", help="skip the nu=8, phi_{2,2} block")
+    p.add_argument("--no-batch", action="store_true", help="skip the multi-RHS batching block")
     return p.parse_args()
 
 
@@ -206,12 +207,12 @@ def run_ours(args):
     params = Ht.precond_params()
     Ht.close()
 
-    def step(prec, precond=ms.MS_PRECOND_NONE, inter_tol=0.0, wl=None, pts_=None, f_=None):
+    def step(prec, precond=ms.MS_PRECOND_NONE, inter_tol=0.0, wl=None, pts_=None, f_=None, **extra):
         wl = wl or w
         pts_ = pts if pts_ is None else pts_
         f_ = f if f_ is None else f_
         opts = ms.ms_default_opts(wendland_d=wl.wendland_d, wendland_k=wl.wendland_k, nu=wl.nu, precision=prec,
-                                  precond=precond, inter_tol=inter_tol)
+                                  precond=precond, inter_tol=inter_tol, **extra)
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         hnd = ms.ms_build_hierarchy(2, wl.n_per_level, pts_, wl.h, opts)
@@ -290,6 +291,9 @@ def run_ours(args):
             out["mixed_no_precond"] = summary(timed(k2, ms.MS_PREC_MIXED))
             out["mixed_exact_fsai"] = summary(timed(k2, ms.MS_PREC_MIXED, ms.MS_PRECOND_EXACT))
             out["algorithm2_schedule_fp64"] = summary(timed(1, ms.MS_PREC_FP64, inter_tol=REL_TOL))
+            # the other CTAs-per-SM choice of the persistent solve kernel (autotuning evidence)
+            out["learned_pcg_1cta_per_sm"] = summary(timed(k2, *HEAD, solve_ctas_per_sm=1))
+            out["plain_fp64_1cta_per_sm"] = summary(timed(k2, ms.MS_PREC_FP64, solve_ctas_per_sm=1))
             out["speedup_learned_vs_plain_fp64"] = out["plain_fp64"]["ms_per_step"] / ms_step
             # agreement of the headline coefficients with the plain FP64 fit (same hierarchy, same f)
             a0 = timed(1, ms.MS_PREC_FP64)[0]["alpha"]
@@ -343,6 +347,45 @@ def run_ours(args):
                               "train": {"levels": [1, 2, 3, 4], **train8},
                               "speedup": summary(r8f)["ms_per_step"] / summary(r8)["ms_per_step"]}
             del p8, f8
+
+        # batching: 256 right-hand sides on one 6-level hierarchy (87,360 points), MIXED without
+        # preconditioner, solved 32 per launch; against single-RHS fits of the first 16 of them
+        if not args.no_batch:
+            wb = inputs.halton_hierarchy(L=6)
+            pb = torch.from_numpy(wb.points).cuda()
+            Fb = np.stack([inputs.GaussianMixture(5, 2, 7000 + r)(wb.points) for r in range(256)], axis=1)
+            Fb = torch.from_numpy(np.ascontiguousarray(Fb)).cuda()
+            Hb = ms.Hierarchy(2, wb.n_per_level, pb, wb.h, precision=ms.MS_PREC_MIXED, wendland_d=2,
+                              wendland_k=1, nu=wb.nu)
+            Hb.fit(Fb[:, :32].contiguous(), REL_TOL)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            Ab, stb = Hb.fit(Fb, REL_TOL)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            t_batch = ev[0].elapsed_time(ev[1])
+            t_single = []
+            for r in range(16):
+                fr = Fb[:, r].contiguous()
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                ev[0].record(stream)
+                a1, _ = Hb.fit(fr, REL_TOL)
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                t_single.append(ev[0].elapsed_time(ev[1]))
+            agree = float(torch.linalg.norm(Ab[:, 15] - a1) / torch.linalg.norm(a1))
+            Hb.close()
+            out["batch_rhs"] = {"workload": "d=2, 6 Halton levels N_j=64*4^(j-1) (87,360 points), delta_j=4h_j, "
+                                            "phi_{2,1}, 256 right-hand sides (seeded 5-Gaussian mixtures), MIXED",
+                                "rhs": 256, "rhs_per_launch": 32, "batched_ms": t_batch,
+                                "batched_ms_per_rhs": t_batch / 256, "single_ms_per_rhs": statistics.mean(t_single),
+                                "speedup_per_rhs": statistics.mean(t_single) / (t_batch / 256),
+                                "kernel_ms": stb["fit_ms"], "rel_residual_max": max(stb["rel_residual"]),
+                                "rel_diff_column15_vs_single": agree}
+            del pb, Fb, Ab
 
         # end to end through the host-pointer C ABI (H2D of points, f, queries; D2H of alpha, values)
         e2e = []

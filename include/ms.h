@@ -105,7 +105,9 @@ typedef struct ms_opts {
     int cell_split;      /* neighbour-grid cell size = delta_l / cell_split (1 or 2); 0 = 1 */
     int threads_per_row; /* CSR sub-warp width for A (1..32, power of 2); 0 = automatic */
     int lower_fp32;      /* 1: also store FP32 values of the B blocks (for MS_APPLY_B32) */
-    int reserved[7];
+    int solve_ctas_per_sm; /* CTAs of the persistent solve kernel per SM: 1 (up to 128
+                              registers a thread) or 2 (up to 64); 0 = automatic (2) */
+    int reserved[6];
 } ms_opts;
 
 /* Per-fit statistics (all levels 0-based, coarse to fine). */

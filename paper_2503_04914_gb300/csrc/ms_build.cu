@@ -208,48 +208,190 @@ void exclusive_scan(const Tin* in, int64_t n, Tout* out, Tout* tmp, cudaStream_t
     k_scan_apply<Tin, Tout><<<(unsigned)ntiles, kScanBS, 0, s>>>(in, n, tmp, ntiles, out); ms_count_launch();
 }
 
-__global__ void k_csr_count(HierView v, int32_t* cntA, int32_t* cntB) {
-    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= v.N) return;
-    const int k = level_of_row(v.off, v.L, s);
-    double y[3] = {0, 0, 0};
-    for (int a = 0; a < v.d; ++a) y[a] = v.X[a * v.N + s];
-    int32_t na = 0, nb = 0;
-    for_each_neighbour(v, k, y, [&](int32_t, double) { ++na; });
-    for (int j = 0; j < k; ++j) for_each_neighbour(v, j, y, [&](int32_t, double) { ++nb; });
-    cntA[s] = na;
-    cntB[s] = nb;
+// ---------------------------------------------------------------- CSR assembly
+//
+// One warp per row s (level k).  For each column level j (j = k for A, j < k for
+// B) the warp walks the (2R+1)^d cells around s's cell in level j's grid; its
+// lanes take a cell's points 32 at a time.  The test |x_p - x_s| < delta_j is
+// taken in FP32 first, from cell-relative coordinates in units of delta_j (the
+// cell offset plus the FP32 in-cell offsets W), whose error is ~1e-6 of delta_j^2;
+// only candidates within 1e-4 of the boundary are re-tested in FP64
+// (fma-accumulated r^2 < delta_j^2), so the pattern is exactly the FP64 one.
+// The FP64 values are computed for the entries only (FP64 is scarce on this GPU).
+
+// Position of y relative to level j's grid: cell c[a] and the offset from that
+// cell's corner in units of delta_j.  Lane a < d computes axis a.
+struct Frame {
+    int c[3];
+    float fr[3];
+};
+
+struct Pt {
+    double x, y, z;
+};
+
+__device__ __forceinline__ Pt point_at(const HierView& v, int64_t s) {
+    Pt q{v.X[s], 0.0, 0.0};
+    if (v.d >= 2) q.y = v.X[v.N + s];
+    if (v.d >= 3) q.z = v.X[2 * v.N + s];
+    return q;
 }
 
-__global__ void k_csr_fill(HierView v, const int64_t* rpA, int32_t* colA, double* valA, float* valA32,
-                           const int64_t* rpB, int32_t* colB, double* valB, float* valB32) {
-    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= v.N) return;
+// |x_p - y|^2 in FP64, accumulated axis by axis with fma
+__device__ __forceinline__ double dist2(const HierView& v, int64_t p, const Pt& y) {
+    double u = v.X[p] - y.x;
+    double r2 = fma(u, u, 0.0);
+    if (v.d >= 2) { u = v.X[v.N + p] - y.y; r2 = fma(u, u, r2); }
+    if (v.d >= 3) { u = v.X[2 * v.N + p] - y.z; r2 = fma(u, u, r2); }
+    return r2;
+}
+
+__device__ __forceinline__ Frame frame_of(const HierView& v, int j, const Pt& y, int lane) {
+    const LevelGrid& g = v.grid[j];
+    int ci = 0;
+    float fi = 0.f;
+    if (lane < v.d) {
+        const double ya = lane == 0 ? y.x : (lane == 1 ? y.y : y.z);
+        ci = cell_coord(g, lane, ya);
+        fi = (float)((ya - (g.lo[lane] + (double)ci * g.cell)) / v.delta[j]);
+    }
+    Frame f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        f.c[a] = __shfl_sync(0xffffffffu, ci, a);
+        f.fr[a] = __shfl_sync(0xffffffffu, fi, a);
+    }
+    return f;
+}
+
+// visit(p, in, mask): called by all 32 lanes for every group of up to 32
+// candidates p of one cell; `in` = p is a neighbour, mask = ballot of `in`.
+template <typename F>
+__device__ __forceinline__ void warp_neighbours(const HierView& v, const float* __restrict__ W, int j,
+                                                const Pt& y, int lane, F&& visit) {
+    const LevelGrid& g = v.grid[j];
+    const Frame f = frame_of(v, j, y, lane);
+    const float cod = (float)(g.cell / v.delta[j]);  // cell size in units of delta_j (a power of 2)
+    const double d2 = v.delta[j] * v.delta[j];
+    const int R = v.R;
+    const int rz = v.d >= 3 ? R : 0, ry = v.d >= 2 ? R : 0;
+    for (int dz = -rz; dz <= rz; ++dz) {
+        const int cz = f.c[2] + dz;
+        if (cz < 0 || cz >= g.G[2]) continue;
+        for (int dy = -ry; dy <= ry; ++dy) {
+            const int cy = f.c[1] + dy;
+            if (cy < 0 || cy >= g.G[1]) continue;
+            for (int dx = -R; dx <= R; ++dx) {
+                const int cx = f.c[0] + dx;
+                if (cx < 0 || cx >= g.G[0]) continue;
+                const float o0 = (float)dx * cod - f.fr[0], o1 = (float)dy * cod - f.fr[1],
+                            o2 = (float)dz * cod - f.fr[2];
+                const int64_t gid = g.cell_off + morton(v.d, cx, cy, cz);
+                const int32_t s0 = __ldg(v.cell_start + gid), e0 = __ldg(v.cell_start + gid + 1);
+                for (int32_t p0 = s0; p0 < e0; p0 += 32) {
+                    const int32_t p = p0 + lane;
+                    bool in = false;
+                    if (p < e0) {
+                        float t = o0 + __ldg(W + p);
+                        float q = t * t;
+                        if (v.d >= 2) { t = o1 + __ldg(W + v.N + p); q = fmaf(t, t, q); }
+                        if (v.d >= 3) { t = o2 + __ldg(W + 2 * v.N + p); q = fmaf(t, t, q); }
+                        if (q < 1.0f - 1e-4f) {
+                            in = true;
+                        } else if (q <= 1.0f + 1e-4f) {
+                            in = dist2(v, p, y) < d2;
+                        }
+                    }
+                    visit(p, in, __ballot_sync(0xffffffffu, in));
+                }
+            }
+        }
+    }
+}
+
+constexpr int kCsrBS = 256;  // 8 rows per block
+
+__global__ void __launch_bounds__(kCsrBS) k_csr_count(HierView v, const float* __restrict__ W, int32_t* cntA,
+                                                       int32_t* cntB) {
+    const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= v.N) return;  // warp-uniform
     const int k = level_of_row(v.off, v.L, s);
-    double y[3] = {0, 0, 0};
-    for (int a = 0; a < v.d; ++a) y[a] = v.X[a * v.N + s];
-    int64_t pa = rpA[s];
-    {
-        const double inv = 1.0 / v.delta[k], sc = v.dscale[k];
-        for_each_neighbour(v, k, y, [&](int32_t p, double r2) {
-            const double val = sc * wendland_eval<double>(v.w, sqrt(r2) * inv);
-            colA[pa] = p;
-            valA[pa] = val;
-            if (valA32) valA32[pa] = (float)val;
-            ++pa;
-        });
+    const Pt y = point_at(v, s);
+    int32_t na = 0, nb = 0;
+    warp_neighbours(v, W, k, y, lane, [&](int32_t, bool, unsigned m) { na += __popc(m); });
+    for (int j = 0; j < k; ++j) warp_neighbours(v, W, j, y, lane, [&](int32_t, bool, unsigned m) { nb += __popc(m); });
+    if (lane == 0) {
+        cntA[s] = na;
+        cntB[s] = nb;
     }
-    int64_t pb = rpB[s];
+}
+
+// Also records, for the rows of level k, where each column level's segment of
+// the B row starts: Bseg[j][s] = offset from rpB[s] of the first entry of
+// column level j (j = 0..k; Bseg[k][s] = the row length).  The columns are
+// found first (FP32 test, compacted by ballot); the FP64 values then take all
+// 32 lanes over the row's entries.
+__global__ void __launch_bounds__(kCsrBS) k_csr_fill(HierView v, const float* __restrict__ W, const int64_t* rpA,
+                                                      int32_t* colA, double* valA, float* valA32, const int64_t* rpB,
+                                                      int32_t* colB, double* valB, float* valB32, int32_t* Bseg) {
+    const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= v.N) return;  // warp-uniform
+    const unsigned below = (1u << lane) - 1u;
+    const int k = level_of_row(v.off, v.L, s);
+    const Pt y = point_at(v, s);
+    auto emit = [&](int j, int64_t& pos, int32_t* col) {
+        warp_neighbours(v, W, j, y, lane, [&](int32_t p, bool in, unsigned m) {
+            if (in) col[pos + __popc(m & below)] = p;
+            pos += __popc(m);
+        });
+    };
+    const int64_t a0 = rpA[s];
+    int64_t pa = a0;
+    emit(k, pa, colA);
+    const int64_t b0 = rpB[s];
+    int64_t pb = b0;
     for (int j = 0; j < k; ++j) {
-        const double inv = 1.0 / v.delta[j], sc = v.dscale[j];
-        for_each_neighbour(v, j, y, [&](int32_t p, double r2) {
-            const double val = sc * wendland_eval<double>(v.w, sqrt(r2) * inv);
-            colB[pb] = p;
-            valB[pb] = val;
-            if (valB32) valB32[pb] = (float)val;
-            ++pb;
-        });
+        if (lane == 0) Bseg[(int64_t)j * v.N + s] = (int32_t)(pb - b0);
+        emit(j, pb, colB);
     }
+    if (lane == 0) Bseg[(int64_t)k * v.N + s] = (int32_t)(pb - b0);
+    __syncwarp();  // the columns written by the other lanes are read below
+    {
+        const double inv = v.inv_delta[k], sc = v.dscale[k];
+        for (int64_t i = a0 + lane; i < pa; i += 32) {
+            const double value = sc * wendland_eval<double>(v.w, sqrt(dist2(v, colA[i], y)) * inv);
+            valA[i] = value;
+            if (valA32) valA32[i] = (float)value;
+        }
+    }
+    for (int64_t i = b0 + lane; i < pb; i += 32) {
+        const int32_t p = colB[i];
+        const int j = level_of_row(v.off, v.L, p);
+        const double value = v.dscale[j] * wendland_eval<double>(v.w, sqrt(dist2(v, p, y)) * v.inv_delta[j]);
+        valB[i] = value;
+        if (valB32) valB32[i] = (float)value;
+    }
+}
+
+// Entries of every block B_kj (k > j): out[k * L + j].
+__global__ void k_block_nnz(const int32_t* Bseg, const int64_t* rpB, HierView v, unsigned long long* out) {
+    __shared__ unsigned long long sh[MS_MAXL * MS_MAXL];
+    const int L = v.L;
+    for (int i = threadIdx.x; i < L * L; i += blockDim.x) sh[i] = 0ull;
+    __syncthreads();
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s < v.N) {
+        const int k = level_of_row(v.off, L, s);
+        for (int j = 0; j < k; ++j) {
+            const int32_t e = Bseg[(int64_t)(j + 1) * v.N + s], b = Bseg[(int64_t)j * v.N + s];
+            if (e > b) atomicAdd(&sh[k * L + j], (unsigned long long)(e - b));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < L * L; i += blockDim.x)
+        if (sh[i]) atomicAdd(&out[i], sh[i]);
 }
 
 inline unsigned nblk(int64_t n, int bs) { return (unsigned)std::max<int64_t>(1, (n + bs - 1) / bs); }
@@ -373,7 +515,7 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
     MS_TRY(talloc((void**)&cntB, sizeof(int32_t) * N));
     MS_TRY(ms_alloc(h, (void**)&h->A.rp, sizeof(int64_t) * (N + 1)));
     MS_TRY(ms_alloc(h, (void**)&h->B.rp, sizeof(int64_t) * (N + 1)));
-    k_csr_count<<<nblk(N, 128), 128, 0, st>>>(v, cntA, cntB); ms_count_launch();
+    k_csr_count<<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, cntA, cntB); ms_count_launch();
     exclusive_scan<int32_t, int64_t>(cntA, N, h->A.rp, (int64_t*)tile, st);
     exclusive_scan<int32_t, int64_t>(cntB, N, h->B.rp, (int64_t*)tile, st);
     MS_CUDA(cudaGetLastError());
@@ -392,13 +534,22 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
     MS_TRY(ms_alloc(h, (void**)&h->B.v64, sizeof(double) * h->B.nnz));
     // the fit updates beta with FP64 B values only; FP32 B values serve MS_APPLY_B32 on request
     if (h->opts.lower_fp32) MS_TRY(ms_alloc(h, (void**)&h->B.v32, sizeof(float) * h->B.nnz));
-    k_csr_fill<<<nblk(N, 128), 128, 0, st>>>(v, h->A.rp, h->A.col, h->A.v64, h->A.v32, h->B.rp, h->B.col,
-                                             h->B.v64, h->B.v32); ms_count_launch();
+    MS_TRY(ms_alloc(h, (void**)&h->Bseg, sizeof(int32_t) * (size_t)L * N));
+    k_csr_fill<<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, h->A.rp, h->A.col, h->A.v64, h->A.v32, h->B.rp,
+                                                        h->B.col, h->B.v64, h->B.v32, h->Bseg); ms_count_launch();
+    unsigned long long* blk;
+    MS_TRY(talloc((void**)&blk, sizeof(unsigned long long) * L * L));
+    MS_CUDA(cudaMemsetAsync(blk, 0, sizeof(unsigned long long) * L * L, st));
+    k_block_nnz<<<nblk(N, 256), 256, 0, st>>>(h->Bseg, h->B.rp, v, blk); ms_count_launch();
     MS_CUDA(cudaGetLastError());
+    std::vector<unsigned long long> hb((size_t)L * L);
+    MS_CUDA(cudaMemcpyAsync(hb.data(), blk, sizeof(unsigned long long) * L * L, cudaMemcpyDeviceToHost, st));
     MS_CUDA(cudaEventRecord(h->ev1, st));
     MS_CUDA(cudaStreamSynchronize(st));
     float ms = 0.f;
     MS_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
     h->build_ms = ms;
+    for (int k = 0; k < L; ++k)
+        for (int j = 0; j < L; ++j) h->Bblk[k][j] = (int64_t)hb[(size_t)k * L + j];
     return MS_OK;
 }

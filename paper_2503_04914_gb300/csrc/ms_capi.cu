@@ -82,6 +82,9 @@ ms_status validate_and_init(int d, int L, const int64_t* n_per_level, const doub
     if (o.threads_per_row < 0 || o.threads_per_row > 32 || (o.threads_per_row & (o.threads_per_row - 1))) {
         ms_set_error(MS_ERR_ARG, "threads_per_row must be 0 or a power of two <= 32"); return MS_ERR_ARG;
     }
+    if (o.solve_ctas_per_sm < 0 || o.solve_ctas_per_sm > 2) {
+        ms_set_error(MS_ERR_ARG, "solve_ctas_per_sm must be 0, 1 or 2"); return MS_ERR_ARG;
+    }
     h->opts = o;
     h->d = d;
     h->L = L;
@@ -99,6 +102,7 @@ ms_status validate_and_init(int d, int L, const int64_t* n_per_level, const doub
         N += n_per_level[l];
         v.delta[l] = o.nu * hl;
         v.dscale[l] = std::pow(v.delta[l], -(double)d);
+        v.inv_delta[l] = 1.0 / v.delta[l];
     }
     v.off[L] = N;
     if (N >= (int64_t(1) << 31) - 1) { ms_set_error(MS_ERR_ARG, "too many points (%lld, limit 2^31-2)", (long long)N); return MS_ERR_ARG; }

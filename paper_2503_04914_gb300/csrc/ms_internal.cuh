@@ -103,6 +103,7 @@ struct HierView {
     int64_t off[MS_MAXL + 1];   // level row offsets
     double delta[MS_MAXL];
     double dscale[MS_MAXL];     // delta^-d
+    double inv_delta[MS_MAXL];  // 1 / delta (correctly rounded, as the device's 1.0 / delta)
     LevelGrid grid[MS_MAXL];
     WendlandPoly w;
     const double* X;            // [d][N] sorted coordinates
@@ -277,8 +278,8 @@ struct Precond {
     float* adam_v = nullptr;
     float* musig = nullptr;      // [2 * kPcOut] standardisation of the scale-free targets
     int32_t* nbr = nullptr;      // [N][kPcK] pattern neighbours (sorted positions, -1 = none)
-    int32_t* gcol = nullptr;     // [N][kPcOut] row pattern of G (self first, -1 = none)
-    float* gval = nullptr;       // [N][kPcOut] values of G
+    int32_t* gcol = nullptr;     // [kPcOut][N] row pattern of G (slot 0 = self, -1 = none; slot-major)
+    float* gval = nullptr;       // [kPcOut][N] values of G
     int64_t* gt_rp = nullptr;    // [N+1] rows of G^T (in-pattern)
     int32_t* gt_col = nullptr;   // [nnz] source rows
     float* gt_val = nullptr;     // [nnz]
@@ -302,6 +303,8 @@ struct ms_hierarchy {
     int32_t* cellid = nullptr;   // [N] level-local Morton cell of each sorted point
     int mf_tpp = 2;              // matrix-free lanes per target point
     DevCSR A, B;
+    int32_t* Bseg = nullptr;     // [L][N] start of column level j's segment in each B row (offset from rpB)
+    int64_t Bblk[MS_MAXL][MS_MAXL] = {};  // entries of block B_kj
     // solver work space (sorted order; vectors hold ws_rhs right-hand sides, [ws_rhs][N])
     int ws_rhs = 0;
     double *f = nullptr, *beta = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *s = nullptr;

@@ -132,12 +132,12 @@ __global__ void k_pc_exact(HierView v, const int32_t* nbr, const int64_t* rows, 
     if (gval) {
         const int l = level_of_row(v.off, v.L, s);
         const double sc = pow(v.delta[l], 0.5 * v.d);
-        gcol[s * kPcOut] = (int32_t)s;
-        gval[s * kPcOut] = (float)(sc * g[0]);
+        gcol[s] = (int32_t)s;
+        gval[s] = (float)(sc * g[0]);
         for (int k = 0; k < kPcK; ++k) {
             const int32_t c = nbr[s * kPcK + k];
-            gcol[s * kPcOut + 1 + k] = c;
-            gval[s * kPcOut + 1 + k] = c >= 0 ? (float)(sc * g[1 + k]) : 0.f;
+            gcol[(1 + k) * v.N + s] = c;
+            gval[(1 + k) * v.N + s] = c >= 0 ? (float)(sc * g[1 + k]) : 0.f;
         }
     }
 }
@@ -293,13 +293,13 @@ __global__ void k_pc_infer(HierView v, const int32_t* nbr, const float* theta, i
     }
     const int l = level_of_row(v.off, v.L, s);
     const float sc = (float)pow(v.delta[l], 0.5 * v.d);
-    gcol[s * kPcOut] = (int32_t)s;
-    gval[s * kPcOut] = sc * g[0];
+    gcol[s] = (int32_t)s;
+    gval[s] = sc * g[0];
     int q = 1;
     for (int k = 0; k < kPcK; ++k) {
         const int32_t c = nbr[s * kPcK + k];
-        gcol[s * kPcOut + 1 + k] = c;
-        gval[s * kPcOut + 1 + k] = c >= 0 ? sc * g[q++] : 0.f;
+        gcol[(1 + k) * v.N + s] = c;
+        gval[(1 + k) * v.N + s] = c >= 0 ? sc * g[q++] : 0.f;
     }
 }
 
@@ -463,7 +463,7 @@ __global__ void k_gt_count(const int32_t* gcol, int64_t N, int32_t* cnt) {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= N) return;
     for (int k = 0; k < kPcOut; ++k) {
-        const int32_t c = gcol[s * kPcOut + k];
+        const int32_t c = gcol[k * N + s];
         if (c >= 0) atomicAdd(&cnt[c], 1);
     }
 }
@@ -472,11 +472,11 @@ __global__ void k_gt_fill(const int32_t* gcol, const float* gval, int64_t N, con
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= N) return;
     for (int k = 0; k < kPcOut; ++k) {
-        const int32_t c = gcol[s * kPcOut + k];
+        const int32_t c = gcol[k * N + s];
         if (c < 0) continue;
         const int64_t pos = rp[c] + atomicAdd(&cursor[c], 1);
         col[pos] = (int32_t)s;
-        val[pos] = gval[s * kPcOut + k];
+        val[pos] = gval[k * N + s];
     }
 }
 // deterministic order inside each row of G^T: by source row

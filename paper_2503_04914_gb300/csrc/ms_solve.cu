@@ -60,9 +60,10 @@ enum { kPrfResid = 0, kPrfMatvec = 1, kPrfUpdate = 2, kPrfBarrier = 3, kPrfLower
 
 struct SolveArgs {
     int L, R, V;       // levels, right-hand sides of this launch, V = R L virtual levels
-    int64_t N, C;      // points, chunks per right-hand side
+    int64_t N;         // points
+    int C;             // chunks per right-hand side
     int64_t off[MS_MAXL + 1];
-    int64_t coff[MS_MAXL + 1];   // chunk offsets per level (within one right-hand side)
+    int coff[MS_MAXL + 1];       // chunk offsets per level (within one right-hand side)
     int64_t nnzA[MS_MAXL], nnzB[MS_MAXL];
     int tprA[MS_MAXL], tprB[MS_MAXL];
     const int64_t* Arp;
@@ -72,6 +73,10 @@ struct SolveArgs {
     const int64_t* Brp;
     const int32_t* Bcol;
     const double* Bv64;
+    const int32_t* Bseg;       // [L][N] start of column level j's segment in each B row
+    int lower_inc;             // sweep m subtracts B_km t_m only (see k_fit)
+    int64_t nnzBm[MS_MAXL];    // entries of the blocks B_km, k > m
+    int tprBm[MS_MAXL];
     const double* f;                       // [R][N]
     double *beta, *x, *r, *p, *q, *s;      // [R][N]; q holds w = A u
     float *x32, *r32, *p32, *q32, *s32;    // [R][N]
@@ -93,8 +98,8 @@ struct SolveArgs {
     MFView mfv;
     // MIXED inner CG preconditioned with M = G^T G (pc = 1)
     int pc;
-    const int32_t* gcol;   // [N][kPcOut]
-    const float* gval;     // [N][kPcOut]
+    const int32_t* gcol;   // [kPcOut][N] (slot-major: slot k of consecutive rows is contiguous)
+    const float* gval;     // [kPcOut][N]
     const int64_t* gt_rp;  // rows of G^T
     const int32_t* gt_col;
     const float* gt_val;
@@ -163,19 +168,6 @@ struct Chunk {
     int64_t r0, r1, vb;
 };
 
-__device__ __forceinline__ Chunk chunk_at(const SolveArgs& a, int64_t c) {
-    const int64_t rhs = c / a.C, cl = c - rhs * a.C;
-    int l = 0;
-    while (l + 1 < a.L && cl >= a.coff[l + 1]) ++l;
-    Chunk ch;
-    ch.l = l;
-    ch.v = (int)rhs * a.L + l;
-    ch.vb = rhs * a.N;
-    ch.r0 = a.off[l] + (cl - a.coff[l]) * kChunk;
-    ch.r1 = min(ch.r0 + (int64_t)kChunk, a.off[l + 1]);
-    return ch;
-}
-
 // Add the block's thread-local accumulators into sh.acc[k][cur]: values are
 // staged in shared memory and summed by one warp per accumulator in a fixed
 // order (few FP64 instructions; deterministic).
@@ -211,15 +203,35 @@ __device__ __forceinline__ void run_phase(const SolveArgs& a, Shared& sh, Sel se
 #pragma unroll
     for (int k = 0; k < (K > 0 ? K : 1); ++k) acc[k] = 0.0;
     int cur = -1;
-    const int64_t cend = (int64_t)a.R * a.C;
-    for (int64_t c = blockIdx.x; c < cend; c += gridDim.x) {
-        const Chunk ch = chunk_at(a, c);
-        if (!sel(ch.v)) continue;
-        if (K > 0 && ch.v != cur) {
-            if (cur >= 0) flush_acc<K>(sh, acc, cur);
-            cur = ch.v;
+    // Global chunk g = rhs * C + c goes to CTA g mod gridDim.x; the CTA walks its
+    // chunks in increasing g, level by level, and jumps over levels that sel() rejects.
+    const int nb = gridDim.x, C = a.C;
+    int first = blockIdx.x;  // first chunk of this CTA within the current right-hand side
+    for (int rhs = 0; rhs < a.R; ++rhs) {
+        int l = 0;
+        for (int c = first; c < C;) {
+            while (c >= a.coff[l + 1]) ++l;
+            const int v = rhs * a.L + l;
+            if (!sel(v)) {
+                const int e = a.coff[l + 1];
+                c += (e - c + nb - 1) / nb * nb;
+                continue;
+            }
+            if (K > 0 && v != cur) {
+                if (cur >= 0) flush_acc<K>(sh, acc, cur);
+                cur = v;
+            }
+            Chunk ch;
+            ch.l = l;
+            ch.v = v;
+            ch.vb = (int64_t)rhs * a.N;
+            ch.r0 = a.off[l] + (int64_t)(c - a.coff[l]) * kChunk;
+            ch.r1 = min(ch.r0 + (int64_t)kChunk, a.off[l + 1]);
+            body(ch, acc);
+            c += nb;
         }
-        body(ch, acc);
+        // chunks of the next right-hand side: rhs * C + c == blockIdx.x (mod nb)
+        first = (first - C % nb + nb) % nb;
     }
     if (K > 0) {
         if (cur >= 0) flush_acc<K>(sh, acc, cur);
@@ -469,8 +481,8 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                                      float acc = 0.f;
 #pragma unroll
                                      for (int k = 0; k < kPcOut; ++k) {
-                                         const int32_t c = __ldg(a.gcol + row * kPcOut + k);
-                                         if (c >= 0) acc = fmaf(__ldg(a.gval + row * kPcOut + k), rv[c], acc);
+                                         const int32_t c = __ldg(a.gcol + k * a.N + row);
+                                         if (c >= 0) acc = fmaf(__ldg(a.gval + k * a.N + row), rv[c], acc);
                                      }
                                      a.u1_32[ch.vb + row] = acc;
                                  }
@@ -481,13 +493,12 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                 run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0 && !sh.pcoff[v]; },
                              [&](const Chunk& ch, double*) {
                                  const float* u1 = a.u1_32 + ch.vb;
-                                 for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
-                                     float acc = 0.f;
-                                     const int64_t e = __ldg(a.gt_rp + row + 1);
-                                     for (int64_t k = __ldg(a.gt_rp + row); k < e; ++k)
-                                         acc = fmaf(__ldg(a.gt_val + k), u1[__ldg(a.gt_col + k)], acc);
-                                     a.u32[ch.vb + row] = acc;
-                                 }
+                                 rows_by_subwarp(ch.r0, ch.r1, 2, [&](int64_t row, bool ok, int sl) {
+                                     int64_t s = 0, e = 0;
+                                     if (ok) { s = __ldg(a.gt_rp + row); e = __ldg(a.gt_rp + row + 1); }
+                                     const float y = csr_row<float, float, float>(a.gt_col, a.gt_val, u1, s, e, sl, 2);
+                                     if (ok && sl == 0) a.u32[ch.vb + row] = y;
+                                 });
                              });
                 prof(sh, kPrfOther);
                 if (!gsync(a, sh)) return false;
@@ -675,8 +686,10 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
     return true;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kBS) k_fit(SolveArgs a) {
+// MINB: CTAs per SM the kernel is compiled for (1: up to 128 registers a thread,
+// 2: up to 64).
+template <int MODE, int MINB>
+__global__ void __launch_bounds__(kBS, MINB) k_fit(SolveArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shared& sh = *reinterpret_cast<Shared*>(smem_raw);
     const int tid = threadIdx.x;
@@ -707,7 +720,33 @@ __global__ void __launch_bounds__(kBS) k_fit(SolveArgs a) {
         if (m <= L - 2) {
             if (!solve_levels<MODE>(a, sh, m, L - 1, false)) return;
         }
-        if (m + 1 <= L - 1) {
+        if (m + 1 <= L - 1 && a.lower_inc) {
+            // beta_k -= B_km t_m for the rows of levels k = m+1..L-1 (FP64).  When
+            // intermediate levels are not iterated (inter_tol >= 1) t_m is the only
+            // level solution that changed since beta was last updated (levels above m
+            // still hold t = 0), so only the blocks B_km are read: every block of B
+            // once over the whole fit.
+            run_phase<0>(a, sh, [&](int v) { return v % L >= m + 1; }, [&](const Chunk& ch, double*) {
+                const int S = a.tprBm[m];
+                const double* xv = a.x + ch.vb;
+                const int32_t* seg0 = a.Bseg + (int64_t)m * a.N;
+                const int32_t* seg1 = seg0 + a.N;
+                rows_by_subwarp(ch.r0, ch.r1, S, [&](int64_t row, bool ok, int sl) {
+                    int64_t s = 0, e = 0;
+                    if (ok) {
+                        const int64_t b = a.Brp[row];
+                        s = b + __ldg(seg0 + row);
+                        e = b + __ldg(seg1 + row);
+                    }
+                    const double y = csr_row<double, double, double>(a.Bcol, a.Bv64, xv, s, e, sl, S);
+                    if (ok && sl == 0) a.beta[ch.vb + row] -= y;
+                });
+            });
+            if (tid == 0)
+                sh.bytes += a.R * ((double)a.nnzBm[m] * 12.0 + (double)(a.off[L] - a.off[m + 1]) * 32.0);
+            prof(sh, kPrfLower);
+            if (!gsync(a, sh)) return;
+        } else if (m + 1 <= L - 1) {
             // beta_k = f_k - sum_{j<k} B_kj t_j for the rows of levels k = m+1..L-1 (FP64)
             run_phase<0>(a, sh, [&](int v) { return v % L >= m + 1; }, [&](const Chunk& ch, double*) {
                 const int S = a.tprB[ch.l];
@@ -844,10 +883,10 @@ void fill_args(const ms_hierarchy* h, const int64_t* rpA, const int64_t* rpB, do
     int64_t c = 0;
     for (int l = 0; l <= L; ++l) {
         a.off[l] = h->view.off[l];
-        a.coff[l] = c;
+        a.coff[l] = (int)c;
         if (l < L) c += (h->view.off[l + 1] - h->view.off[l] + kChunk - 1) / kChunk;
     }
-    a.C = c;
+    a.C = (int)c;
     for (int l = 0; l < L; ++l) {
         const int64_t n = h->view.off[l + 1] - h->view.off[l];
         a.nnzA[l] = rpA[l + 1] - rpA[l];
@@ -857,6 +896,14 @@ void fill_args(const ms_hierarchy* h, const int64_t* rpA, const int64_t* rpB, do
     }
     a.Arp = h->A.rp; a.Acol = h->A.col; a.Av64 = h->A.v64; a.Av32 = h->A.v32;
     a.Brp = h->B.rp; a.Bcol = h->B.col; a.Bv64 = h->B.v64;
+    a.Bseg = h->Bseg;
+    for (int m = 0; m < L; ++m) {
+        int64_t nb = 0;
+        for (int k = m + 1; k < L; ++k) nb += h->Bblk[k][m];
+        const int64_t rows = h->view.off[L] - h->view.off[std::min(m + 1, L)];
+        a.nnzBm[m] = nb;
+        a.tprBm[m] = tpr_for(rows > 0 ? (double)nb / rows : 1.0);
+    }
     const bool mixed = h->opts.precision == MS_PREC_MIXED;
     a.sweeps = h->opts.jacobi_sweeps > 0 ? h->opts.jacobi_sweeps : std::max(L - 1, 0);
     a.max_iters = h->opts.max_iters > 0 ? h->opts.max_iters : 20000;
@@ -864,29 +911,36 @@ void fill_args(const ms_hierarchy* h, const int64_t* rpA, const int64_t* rpB, do
     a.tol = rel_tol;
     a.inter_tol = h->opts.inter_tol > 0 ? std::max(h->opts.inter_tol, rel_tol) : 1.0;
     a.inner_tol = h->opts.inner_tol > 0 ? h->opts.inner_tol : 1e-4;
+    a.lower_inc = (a.inter_tol >= 1.0 && a.Bseg) ? 1 : 0;
     a.timeout_ns = 4000000000ull;
 }
 
-// The solve kernel's per-CTA state is above the default 48 KB of dynamic shared memory.
-ms_status set_fit_smem() {
-    MS_CUDA(cudaFuncSetAttribute(k_fit<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared)));
-    MS_CUDA(cudaFuncSetAttribute(k_fit<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared)));
-    return MS_OK;
+// The solve kernel for a precision and a CTAs-per-SM choice (opts.solve_ctas_per_sm;
+// 0 = automatic = 2: measured on GB300 at 1.4M points, 2 CTAs per SM (64 registers)
+// fit 21% (FP64) and 24% (MIXED, learned preconditioner) faster than 1 (128 registers)).
+int ctas_per_sm(const ms_opts& o) {
+    if (o.solve_ctas_per_sm == 1 || o.solve_ctas_per_sm == 2) return o.solve_ctas_per_sm;
+    return 2;
 }
 
-ms_status fit_blocks(bool mixed, int dev, int* blocks) {
-    MS_TRY(set_fit_smem());
+const void* fit_kernel(bool mixed, int minb) {
+    if (mixed) return minb == 1 ? (const void*)k_fit<1, 1> : (const void*)k_fit<1, 2>;
+    return minb == 1 ? (const void*)k_fit<0, 1> : (const void*)k_fit<0, 2>;
+}
+
+// Cooperative grid of the solve kernel: min(per_sm, minb) CTAs on every SM.
+ms_status fit_blocks(bool mixed, int minb, int dev, int* blocks) {
+    const void* fn = fit_kernel(mixed, minb);
+    // the per-CTA state is above the default 48 KB of dynamic shared memory
+    MS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared)));
     int sms = 0, per_sm = 0;
     MS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (mixed)
-        MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fit<1>, kBS, sizeof(Shared)));
-    else
-        MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fit<0>, kBS, sizeof(Shared)));
+    MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBS, sizeof(Shared)));
     if (per_sm < 1) {
         ms_set_error(MS_ERR_CUDA, "solve kernel cannot be resident on an SM");
         return MS_ERR_CUDA;
     }
-    *blocks = std::min(sms * std::min(per_sm, 2), kMaxGroups * kGroup);
+    *blocks = std::min(sms * std::min(per_sm, minb), kMaxGroups * kGroup);
     return MS_OK;
 }
 
@@ -921,7 +975,7 @@ static ms_status ensure_workspace(ms_hierarchy* h, int R) {
     }
     int dev = 0;
     MS_CUDA(cudaGetDevice(&dev));
-    MS_TRY(fit_blocks(h->opts.precision == MS_PREC_MIXED, dev, &h->solve_blocks));
+    MS_TRY(fit_blocks(h->opts.precision == MS_PREC_MIXED, ctas_per_sm(h->opts), dev, &h->solve_blocks));
     h->mf_tpp = mf_tpp_for(h);
     const int V = R * h->L;
     MS_TRY(ms_realloc(h, (void**)&h->part, sizeof(double) * kAcc * V * h->solve_blocks));
@@ -996,10 +1050,8 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
         MS_CUDA(cudaMemsetAsync(h->resid, 0, sizeof(double) * a.V, st));
         void* args[] = {&a};
         MS_CUDA(cudaEventRecord(h->ev0, st));
-        if (mixed)
-            MS_CUDA(cudaLaunchCooperativeKernel((void*)k_fit<1>, dim3(h->solve_blocks), dim3(kBS), args, sizeof(Shared), st));
-        else
-            MS_CUDA(cudaLaunchCooperativeKernel((void*)k_fit<0>, dim3(h->solve_blocks), dim3(kBS), args, sizeof(Shared), st));
+        MS_CUDA(cudaLaunchCooperativeKernel(fit_kernel(mixed, ctas_per_sm(h->opts)), dim3(h->solve_blocks), dim3(kBS),
+                                            args, sizeof(Shared), st));
         ms_count_launch();
         MS_CUDA(cudaEventRecord(h->ev1, st));
         ++launches;
@@ -1199,7 +1251,8 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
     cudaStream_t st = (cudaStream_t)stream;
 
     int blocks = 0;
-    MS_TRY(fit_blocks(mixed, dev, &blocks));
+    const int minb = ctas_per_sm(h->opts);
+    MS_TRY(fit_blocks(mixed, minb, dev, &blocks));
     blocks = std::min(blocks, kStaticMaxBlocks);
 
     // carve the fixed array
@@ -1244,10 +1297,7 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
     ms_gather_sorted(f_dev, v64[0], h->perm, h->N, 1, 0, st);
     void* args[] = {&a};
     MS_CUDA(cudaEventRecord(h->ev0, st));
-    if (mixed)
-        MS_CUDA(cudaLaunchCooperativeKernel((void*)k_fit<1>, dim3(blocks), dim3(kBS), args, sizeof(Shared), st));
-    else
-        MS_CUDA(cudaLaunchCooperativeKernel((void*)k_fit<0>, dim3(blocks), dim3(kBS), args, sizeof(Shared), st));
+    MS_CUDA(cudaLaunchCooperativeKernel(fit_kernel(mixed, minb), dim3(blocks), dim3(kBS), args, sizeof(Shared), st));
     ms_count_launch();
     MS_CUDA(cudaEventRecord(h->ev1, st));
     ms_scatter_input(a.x, alpha_dev, h->perm, h->N, 1, 0, st);

@@ -40,7 +40,7 @@ class ms_opts(C.Structure):
                 ("precision", C.c_int), ("precond", C.c_int), ("max_iters", C.c_int),
                 ("jacobi_sweeps", C.c_int), ("inter_tol", C.c_double), ("inner_tol", C.c_double),
                 ("cell_split", C.c_int), ("threads_per_row", C.c_int), ("lower_fp32", C.c_int),
-                ("reserved", C.c_int * 7)]
+                ("solve_ctas_per_sm", C.c_int), ("reserved", C.c_int * 6)]
 
 
 class ms_fit_stats(C.Structure):
@@ -172,7 +172,10 @@ def _stream(stream):
 def ms_default_opts(**overrides) -> ms_opts:
     o = ms_opts()
     load().ms_default_opts(C.byref(o))
+    names = {n for n, _ in ms_opts._fields_}
     for k, v in overrides.items():
+        if k not in names:
+            raise TypeError(f"ms_opts has no field {k!r}")
         setattr(o, k, v)
     return o
 

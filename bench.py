@@ -120,6 +120,30 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def recorded_traffic(profile="k_fit_learned_halton8.md"):
+    """DRAM traffic per launch of the solve kernel from the committed ncu summary, or None when
+    the kernel's source has changed since the counters were taken (sha256 lines of the summary)."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", profile)).read()
+    except OSError:
+        return None
+    traffic = None
+    for line in text.splitlines():
+        if line.startswith("kernel_source_sha256 "):
+            name, digest = line[len("kernel_source_sha256 "):].split(":")
+            path = os.path.join(ROOT, "paper_2503_04914_gb300", "csrc", name.strip())
+            try:
+                cur = hashlib.sha256(open(path, "rb").read()).hexdigest()
+            except OSError:
+                return None
+            if cur != digest.strip():
+                return None
+        elif line.startswith("traffic_bytes_per_launch:"):
+            traffic = float(line.split(":")[1])
+    return traffic
+
+
 def cpu_baseline(levels, query_n, reps=1):
     """Time the CPU oracle (as it stands) on a bounded sample in a single-threaded subprocess."""
     code = f"""
@@ -275,7 +299,9 @@ def run_ours(args):
         achieved = fit_bytes / (fit_ms * 1e-3) / 1e9
         out["roofline"] = {"kernel": "k_fit<MIXED> (persistent Jacobi / learned-PCG solve)", "bound": "hbm",
                            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                           "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
+                           "peak_kind": f"{peak_kind} hbm_gbs",
+                           "traffic": recorded_traffic() if args.levels == 8 and args.train_epochs == 300 else None,
+                           "traffic_source": "profiles/k_fit_learned_halton8.md (1-pass ncu capture of this workload)",
                            "algorithmic_bytes_per_launch": fit_bytes, "launch_ms": fit_ms}
         out["learned_pcg"] = summary(recs)
         out["phases_ms"] = {"build": out["learned_pcg"]["build_ms"], "fit_incl_precond": None,

@@ -246,32 +246,40 @@ __device__ __forceinline__ double dist2(const HierView& v, int64_t p, const Pt& 
     return r2;
 }
 
-__device__ __forceinline__ Frame frame_of(const HierView& v, int j, const Pt& y, int lane) {
+// Frame of y in level j's grid, all axes (FP64 set-up: one lane per level calls it).
+__device__ __forceinline__ Frame frame_of(const HierView& v, int j, const Pt& y) {
     const LevelGrid& g = v.grid[j];
-    int ci = 0;
-    float fi = 0.f;
-    if (lane < v.d) {
-        const double ya = lane == 0 ? y.x : (lane == 1 ? y.y : y.z);
-        ci = cell_coord(g, lane, ya);
-        fi = (float)((ya - (g.lo[lane] + (double)ci * g.cell)) / v.delta[j]);
+    Frame f{{0, 0, 0}, {0.f, 0.f, 0.f}};
+    const double ya[3] = {y.x, y.y, y.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a < v.d) {
+            f.c[a] = cell_coord(g, a, ya[a]);
+            f.fr[a] = (float)((ya[a] - (g.lo[a] + (double)f.c[a] * g.cell)) * v.inv_delta[j]);
+        }
     }
+    return f;
+}
+
+// Broadcast lane `src`'s frame to the warp.
+__device__ __forceinline__ Frame frame_from(const Frame& mine, int src) {
     Frame f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        f.c[a] = __shfl_sync(0xffffffffu, ci, a);
-        f.fr[a] = __shfl_sync(0xffffffffu, fi, a);
+        f.c[a] = __shfl_sync(0xffffffffu, mine.c[a], src);
+        f.fr[a] = __shfl_sync(0xffffffffu, mine.fr[a], src);
     }
     return f;
 }
 
 // visit(p, in, mask): called by all 32 lanes for every group of up to 32
 // candidates p of one cell; `in` = p is a neighbour, mask = ballot of `in`.
+// f: y's frame in level j's grid.
 template <typename F>
 __device__ __forceinline__ void warp_neighbours(const HierView& v, const float* __restrict__ W, int j,
-                                                const Pt& y, int lane, F&& visit) {
+                                                const Frame& f, const Pt& y, int lane, F&& visit) {
     const LevelGrid& g = v.grid[j];
-    const Frame f = frame_of(v, j, y, lane);
-    const float cod = (float)(g.cell / v.delta[j]);  // cell size in units of delta_j (a power of 2)
+    const float cod = g.cod;
     const double d2 = v.delta[j] * v.delta[j];
     const int R = v.R;
     const int rz = v.d >= 3 ? R : 0, ry = v.d >= 2 ? R : 0;
@@ -311,16 +319,20 @@ __device__ __forceinline__ void warp_neighbours(const HierView& v, const float* 
 
 constexpr int kCsrBS = 256;  // 8 rows per block
 
-__global__ void __launch_bounds__(kCsrBS) k_csr_count(HierView v, const float* __restrict__ W, int32_t* cntA,
+__global__ void __launch_bounds__(kCsrBS, 4) k_csr_count(HierView v, const float* __restrict__ W, int32_t* cntA,
                                                        int32_t* cntB) {
     const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (s >= v.N) return;  // warp-uniform
     const int k = level_of_row(v.off, v.L, s);
     const Pt y = point_at(v, s);
+    // lane j <= k holds y's frame in level j's grid
+    Frame mine{{0, 0, 0}, {0.f, 0.f, 0.f}};
+    if (lane <= k) mine = frame_of(v, lane, y);
     int32_t na = 0, nb = 0;
-    warp_neighbours(v, W, k, y, lane, [&](int32_t, bool, unsigned m) { na += __popc(m); });
-    for (int j = 0; j < k; ++j) warp_neighbours(v, W, j, y, lane, [&](int32_t, bool, unsigned m) { nb += __popc(m); });
+    warp_neighbours(v, W, k, frame_from(mine, k), y, lane, [&](int32_t, bool, unsigned m) { na += __popc(m); });
+    for (int j = 0; j < k; ++j)
+        warp_neighbours(v, W, j, frame_from(mine, j), y, lane, [&](int32_t, bool, unsigned m) { nb += __popc(m); });
     if (lane == 0) {
         cntA[s] = na;
         cntB[s] = nb;
@@ -332,7 +344,7 @@ __global__ void __launch_bounds__(kCsrBS) k_csr_count(HierView v, const float* _
 // column level j (j = 0..k; Bseg[k][s] = the row length).  The columns are
 // found first (FP32 test, compacted by ballot); the FP64 values then take all
 // 32 lanes over the row's entries.
-__global__ void __launch_bounds__(kCsrBS) k_csr_fill(HierView v, const float* __restrict__ W, const int64_t* rpA,
+__global__ void __launch_bounds__(kCsrBS, 4) k_csr_fill(HierView v, const float* __restrict__ W, const int64_t* rpA,
                                                       int32_t* colA, double* valA, float* valA32, const int64_t* rpB,
                                                       int32_t* colB, double* valB, float* valB32, int32_t* Bseg) {
     const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -341,8 +353,10 @@ __global__ void __launch_bounds__(kCsrBS) k_csr_fill(HierView v, const float* __
     const unsigned below = (1u << lane) - 1u;
     const int k = level_of_row(v.off, v.L, s);
     const Pt y = point_at(v, s);
+    Frame mine{{0, 0, 0}, {0.f, 0.f, 0.f}};
+    if (lane <= k) mine = frame_of(v, lane, y);
     auto emit = [&](int j, int64_t& pos, int32_t* col) {
-        warp_neighbours(v, W, j, y, lane, [&](int32_t p, bool in, unsigned m) {
+        warp_neighbours(v, W, j, frame_from(mine, j), y, lane, [&](int32_t p, bool in, unsigned m) {
             if (in) col[pos + __popc(m & below)] = p;
             pos += __popc(m);
         });
@@ -472,6 +486,7 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
         for (int a = 0; a < 3; ++a) g.lo[a] = a < d ? lo[a] : 0.0;
         g.cell = cell;
         g.inv_cell = 1.0 / cell;
+        g.cod = (float)(cell / v.delta[l]);
         g.bits = bits;
         g.ncells = int64_t(1) << (bits * d);
         g.cell_off = cells;

@@ -52,9 +52,20 @@ static inline bool wendland_poly(int wd, int wk, WendlandPoly* w) {
 template <typename T>
 __device__ __forceinline__ T wendland_eval(const WendlandPoly& w, T r) {
     if (!(r < T(1))) return T(0);  // compact support: phi vanishes for r >= 1
-    T s = T(1) - r;
-    T pw = T(1);
-    for (int i = 0; i < w.e; ++i) pw *= s;
+    const T s = T(1) - r;
+    // (1 - r)^e by squaring (e = 3..11 for the supported (d, k); fewer multiplications,
+    // which matter where T = double: FP64 issue is scarce on this GPU)
+    const T s2 = s * s, s4 = s2 * s2;
+    T pw;
+    switch (w.e) {
+    case 4: pw = s4; break;
+    case 6: pw = s4 * s2; break;
+    case 8: pw = s4 * s4; break;
+    default: {
+        pw = T(1);
+        for (int i = 0; i < w.e; ++i) pw *= s;
+    }
+    }
     T p = T(w.c[3]);
     p = p * r + T(w.c[2]);
     p = p * r + T(w.c[1]);
@@ -68,6 +79,7 @@ struct LevelGrid {
     double lo[3];      // grid origin (level bounding-box minimum)
     double inv_cell;   // 1 / cell size
     double cell;       // cell size
+    float cod;         // cell size / delta (a power of 2)
     int G[3];          // cells per axis (1 for unused axes)
     int bits;          // Morton bits per axis (P = 2^bits >= max G)
     int64_t cell_off;  // first global cell id of the level

@@ -238,6 +238,34 @@ ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, double rel_tol
                             ms_fit_stats* stats, void* stream);
 
 /*
+ * Batched fit of nh independent hierarchies (one right-hand side each) in one
+ * persistent cooperative launch: eq. split for every hierarchy, as ms_fit_dev
+ * computes it.  The grid is split into partitions of CTAs, one per hierarchy, in
+ * proportion to its work (A nonzeros + points); each partition has its own grid
+ * barrier and reductions.  More hierarchies than the launch has CTAs (2 per SM)
+ * run in successive launches.  The paper fits one hierarchy; this is the
+ * throughput form for many small ones.
+ *   hs         host [nh] built handles, all on the current device, all FP64 or all
+ *              MIXED (each keeps its own kernel, op and preconditioner options)
+ *   nh         >= 1
+ *   f_dev      host [nh] of DEVICE float64 [N_i], input order
+ *   rel_tol    in (0, 1), as for ms_fit
+ *   alpha_dev  host [nh] of DEVICE float64 [N_i], input order (written)
+ *   stats      nullable host [nh]; fit_ms and kernel_launches are those of the
+ *              whole batch
+ *   stream     cudaStream_t as void*; the call waits for the stream before returning
+ * Errors: MS_ERR_ARG (NULL arrays, mixed precisions), MS_ERR_STATE (a handle of
+ * another device, FP32 values missing), and the device statuses of ms_fit (the
+ * first failing hierarchy is named in ms_last_error()).
+ */
+ms_status ms_fit_batch_dev(ms_hierarchy* const* hs, int nh, const double* const* f_dev, double rel_tol,
+                           double* const* alpha_dev, ms_fit_stats* stats, void* stream);
+
+/* As ms_fit_batch_dev with HOST f[i] / alpha_out[i] (float64 [N_i], input order). */
+ms_status ms_fit_batch(ms_hierarchy* const* hs, int nh, const double* const* f, double rel_tol,
+                       double* const* alpha_out, ms_fit_stats* stats);
+
+/*
  * Evaluate the approximant f_L(q) = sum_l sum_n alpha_n^(l) Phi_{delta_l}(q - x_n^(l))
  * (eq. fapproximation) at nq query points, FP64 throughout.
  *   alpha  host [N] or [N][nrhs], input order;  query host [nq][d];  out host [nq][nrhs].

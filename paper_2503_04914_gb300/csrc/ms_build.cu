@@ -389,6 +389,15 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_fill(HierView v, const float*
     }
 }
 
+// A.rp and B.rp at the level boundaries: out[l] = rpA[off[l]], out[L + 1 + l] = rpB[off[l]].
+__global__ void k_level_rows(HierView v, const int64_t* rpA, const int64_t* rpB, int64_t* out) {
+    const int l = threadIdx.x;
+    if (l <= v.L) {
+        out[l] = rpA[v.off[l]];
+        out[v.L + 1 + l] = rpB[v.off[l]];
+    }
+}
+
 // Entries of every block B_kj (k > j): out[k * L + j].
 __global__ void k_block_nnz(const int32_t* Bseg, const int64_t* rpB, HierView v, unsigned long long* out) {
     __shared__ unsigned long long sh[MS_MAXL * MS_MAXL];
@@ -559,6 +568,12 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
     MS_CUDA(cudaGetLastError());
     std::vector<unsigned long long> hb((size_t)L * L);
     MS_CUDA(cudaMemcpyAsync(hb.data(), blk, sizeof(unsigned long long) * L * L, cudaMemcpyDeviceToHost, st));
+    int64_t* lvrows;
+    MS_TRY(talloc((void**)&lvrows, sizeof(int64_t) * 2 * (L + 1)));
+    k_level_rows<<<1, 64, 0, st>>>(v, h->A.rp, h->B.rp, lvrows); ms_count_launch();
+    MS_CUDA(cudaGetLastError());
+    std::vector<int64_t> hl(2 * (L + 1));
+    MS_CUDA(cudaMemcpyAsync(hl.data(), lvrows, sizeof(int64_t) * hl.size(), cudaMemcpyDeviceToHost, st));
     MS_CUDA(cudaEventRecord(h->ev1, st));
     MS_CUDA(cudaStreamSynchronize(st));
     float ms = 0.f;
@@ -566,5 +581,9 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
     h->build_ms = ms;
     for (int k = 0; k < L; ++k)
         for (int j = 0; j < L; ++j) h->Bblk[k][j] = (int64_t)hb[(size_t)k * L + j];
+    for (int l = 0; l <= L; ++l) {
+        h->rpA_lv[l] = hl[l];
+        h->rpB_lv[l] = hl[L + 1 + l];
+    }
     return MS_OK;
 }

@@ -280,6 +280,67 @@ ms_status ms_fit(ms_hierarchy* h, const double* f, int nrhs, double rel_tol, dou
     return s;
 }
 
+ms_status ms_fit_batch_dev(ms_hierarchy* const* hs, int nh, const double* const* f_dev, double rel_tol,
+                           double* const* alpha_dev, ms_fit_stats* stats, void* stream) {
+    g_err[0] = 0;
+    if (!hs || !f_dev || !alpha_dev || nh < 1) {
+        ms_set_error(MS_ERR_ARG, "hs, f_dev and alpha_dev must not be NULL and nh >= 1 (got %d)", nh);
+        return MS_ERR_ARG;
+    }
+    if (!(rel_tol > 0.0 && rel_tol < 1.0)) { ms_set_error(MS_ERR_ARG, "rel_tol must be in (0, 1) (got %g)", rel_tol); return MS_ERR_ARG; }
+    for (int i = 0; i < nh; ++i)
+        if (!hs[i] || !f_dev[i] || !alpha_dev[i]) {
+            ms_set_error(MS_ERR_ARG, "hierarchy %d: handle, f and alpha must not be NULL", i);
+            return MS_ERR_ARG;
+        }
+    return ms_fit_batch_impl(hs, nh, f_dev, rel_tol, alpha_dev, stats, (cudaStream_t)stream);
+}
+
+ms_status ms_fit_batch(ms_hierarchy* const* hs, int nh, const double* const* f, double rel_tol,
+                       double* const* alpha_out, ms_fit_stats* stats) {
+    g_err[0] = 0;
+    if (!hs || !f || !alpha_out || nh < 1) {
+        ms_set_error(MS_ERR_ARG, "hs, f and alpha_out must not be NULL and nh >= 1 (got %d)", nh);
+        return MS_ERR_ARG;
+    }
+    int64_t total = 0;
+    for (int i = 0; i < nh; ++i) {
+        if (!hs[i] || !f[i] || !alpha_out[i]) {
+            ms_set_error(MS_ERR_ARG, "hierarchy %d: handle, f and alpha_out must not be NULL", i);
+            return MS_ERR_ARG;
+        }
+        total += hs[i]->N;
+    }
+    cudaStream_t st;
+    MS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    DevBuf fd, ad;
+    ms_status s = dev_alloc(fd, sizeof(double) * total);
+    if (s == MS_OK) s = dev_alloc(ad, sizeof(double) * total);
+    std::vector<const double*> fp(nh);
+    std::vector<double*> ap(nh);
+    int64_t o = 0;
+    for (int i = 0; i < nh && s == MS_OK; ++i) {
+        fp[i] = (const double*)fd.p + o;
+        ap[i] = (double*)ad.p + o;
+        cudaError_t e = cudaMemcpyAsync((void*)fp[i], f[i], sizeof(double) * hs[i]->N, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) s = ms_cuda_error(e, "f H2D", __FILE__, __LINE__);
+        o += hs[i]->N;
+    }
+    if (s == MS_OK) s = ms_fit_batch_dev(hs, nh, fp.data(), rel_tol, ap.data(), stats, st);
+    if (s == MS_OK || s == MS_ERR_NOT_CONVERGED) {
+        for (int i = 0; i < nh; ++i) {
+            cudaError_t e = cudaMemcpyAsync(alpha_out[i], ap[i], sizeof(double) * hs[i]->N, cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) {
+                if (s == MS_OK) s = ms_cuda_error(e, "alpha D2H", __FILE__, __LINE__);
+                break;
+            }
+        }
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return s;
+}
+
 ms_status ms_evaluate_dev(ms_hierarchy* h, const double* alpha_dev, int nrhs, const double* query_dev, int64_t nq,
                           double* out_dev, void* stream) {
     g_err[0] = 0;

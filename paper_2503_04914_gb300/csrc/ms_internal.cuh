@@ -317,6 +317,8 @@ struct ms_hierarchy {
     DevCSR A, B;
     int32_t* Bseg = nullptr;     // [L][N] start of column level j's segment in each B row (offset from rpB)
     int64_t Bblk[MS_MAXL][MS_MAXL] = {};  // entries of block B_kj
+    int64_t rpA_lv[MS_MAXL + 1] = {};     // A.rp / B.rp at the level boundaries (host copies)
+    int64_t rpB_lv[MS_MAXL + 1] = {};
     // solver work space (sorted order; vectors hold ws_rhs right-hand sides, [ws_rhs][N])
     int ws_rhs = 0;
     double *f = nullptr, *beta = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *s = nullptr;
@@ -352,6 +354,13 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
 ms_status ms_apply_impl(ms_hierarchy* h, int op, const double* x_dev, double* y_dev, int sorted, cudaStream_t s);
 ms_status ms_evaluate_impl(ms_hierarchy* h, const double* alpha_dev, int nrhs, const double* q_dev, int64_t nq,
                            double* out_dev, cudaStream_t s);
+
+// batched fit of several hierarchies in one launch (ms_batch.cu)
+ms_status ms_fit_batch_impl(ms_hierarchy* const* hs, int nh, const double* const* f_dev, double rel_tol,
+                            double* const* alpha_dev, ms_fit_stats* stats, cudaStream_t st);
+
+// solve work space for R right-hand sides (ms_solve.cu)
+ms_status ms_ensure_workspace(ms_hierarchy* h, int R);
 
 // learned / exact FSAI preconditioner (ms_precond.cu): build G and G^T for `kind`
 ms_status ms_pc_build(ms_hierarchy* h, int kind, cudaStream_t s);

@@ -1,0 +1,897 @@
+// Device side of the fit (shared by the single-hierarchy and the batched solve kernels).
+#pragma once
+// The fit: eq. split of Section 3 solved on the device in ONE persistent
+// cooperative kernel per batch of right-hand sides.
+//
+//   T'_L beta = f   by Jacobi sweeps (eq. jacobi, Theorem 9), beta_0 = f;
+//   D_L alpha = beta by per-level conjugate gradients (Theorem 8,
+//                    eq. blockdiagonal_levelwise), all levels in flight together.
+//
+// Sweep m (0-based) of the Jacobi iteration solves A_l t_l = beta_l for the
+// levels l = m..L-2 together (warm-started from the previous sweep; level m,
+// whose beta is final, to the requested tolerance, the others to the
+// intermediate tolerance), then recomputes beta_k = f_k - sum_{j<k} B_kj t_j for
+// the rows of levels k = m+1..L-1.  Levels below m already hold their final t
+// (their beta cannot change any more) and are not re-solved; rows of levels
+// <= m are not recomputed (they would reproduce the same values).  A final
+// solve over all levels gives alpha_l = A_l^{-1} beta_l and certifies every
+// level's FP64 true residual.
+//
+// Several right-hand sides share one launch: every (right-hand side, level)
+// pair is a "virtual level" v = r L + l with its own CG scalars; the matrix is
+// shared and the vectors are stored right-hand-side-major ([R][N]).
+//
+// Level solves: CG in the single-reduction form of Chronopoulos and Gear
+// (w = A u, then r.u, w.u and r.r in one reduction; p = u + beta p,
+// s = w + beta s, x += alpha p, r -= alpha s, u = M r or u = r), which is CG's
+// recurrence with one grid-wide reduction and two grid barriers per
+// iteration (four with the preconditioner).  FP64 dots are reduced
+// deterministically: per-CTA partials (a shared-memory block sum), then, inside
+// the grid barrier, the last CTA of each group of 16 sums its group's partials
+// and the last group leader sums the group sums, in fixed orders, and publishes
+// them, so all CTAs take the same convergence decisions.  Stopping:
+// |beta_l - A_l x| <= tol |beta_l| in FP64 (true residual, re-checked after
+// the recursive residual has converged).
+//   FP64 mode : CG on FP64 vectors with the FP64 CSR values.
+//   MIXED mode: iterative refinement: outer FP64 true residual r = b - A x
+//               (FP64 CSR), inner CG on FP32 vectors with FP32 CSR values (or
+//               matrix-free FP32 entries) and FP32 accumulation (FP64 dots and
+//               scalars) for A d = r/|r|, then x += |r| d in FP64.
+// Grid barriers are bounded; on a time-out every CTA returns and the host
+// reports MS_ERR_TIMEOUT.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ms_internal.cuh"
+#include "ms_matfree.cuh"
+
+namespace {
+
+constexpr int kBS = 512;     // threads per CTA of the solve kernel
+constexpr int kChunk = 256;  // rows per work chunk (chunks never straddle levels)
+constexpr int kNW = kBS / 32;
+constexpr int kAcc = 3;      // accumulators per phase
+constexpr int kMaxV = 256;   // virtual levels (right-hand side, level) per launch
+constexpr int kGroup = 16;           // CTAs per first-level barrier counter
+constexpr int kMaxGroups = 64;       // <= 1024 CTAs
+constexpr int kBarWords = 2 + kMaxGroups;  // top count, generation, group counters
+// phase categories of the device timeline (ms_fit_stats.phase_ms)
+enum { kPrfResid = 0, kPrfMatvec = 1, kPrfUpdate = 2, kPrfBarrier = 3, kPrfLower = 4, kPrfOther = 5,
+       kPrfScalar = 6, kProf = 8 };
+
+struct SolveArgs {
+    int L, R, V;       // levels, right-hand sides of this launch, V = R L virtual levels
+    int64_t N;         // points
+    int C;             // chunks per right-hand side
+    int64_t off[MS_MAXL + 1];
+    int coff[MS_MAXL + 1];       // chunk offsets per level (within one right-hand side)
+    int64_t nnzA[MS_MAXL], nnzB[MS_MAXL];
+    int tprA[MS_MAXL], tprB[MS_MAXL];
+    const int64_t* Arp;
+    const int32_t* Acol;
+    const double* Av64;
+    const float* Av32;
+    const int64_t* Brp;
+    const int32_t* Bcol;
+    const double* Bv64;
+    const int32_t* Bseg;       // [L][N] start of column level j's segment in each B row
+    int lower_inc;             // sweep m subtracts B_km t_m only (see k_fit)
+    int64_t nnzBm[MS_MAXL];    // entries of the blocks B_km, k > m
+    int tprBm[MS_MAXL];
+    const double* f;                       // [R][N]
+    double *beta, *x, *r, *p, *q, *s;      // [R][N]; q holds w = A u
+    float *x32, *r32, *p32, *q32, *s32;    // [R][N]
+    double* part;      // [kAcc][V][CTAs] per-CTA partial sums
+    double* gpart;     // [kMaxGroups][kAcc][V] group sums
+    double* scal;      // [kAcc][V] grid sums published inside the barrier
+    unsigned* bar;     // [kBarWords]
+    int* status;
+    int64_t* iters;    // [MS_MAXL] summed over the right-hand sides
+    int* refines;      // [MS_MAXL] summed over the right-hand sides
+    double* resid;     // [V]
+    double* bytes;     // [1]
+    unsigned long long* prof;  // [kProf] nanoseconds CTA 0 spent per phase category
+    int sweeps, max_iters, max_outer;
+    double tol, inter_tol, inner_tol;
+    unsigned long long timeout_ns;
+    int mf;            // MIXED inner mat-vec is matrix-free
+    int mf_tpp;        // lanes per target point of the matrix-free mat-vec
+    MFView mfv;
+    // MIXED inner CG preconditioned with M = G^T G (pc = 1)
+    int pc;
+    const int32_t* gcol;   // [kPcOut][N] (slot-major: slot k of consecutive rows is contiguous)
+    const float* gval;     // [kPcOut][N]
+    const int64_t* gt_rp;  // rows of G^T
+    const int32_t* gt_col;
+    const float* gt_val;
+    float *u32, *u1_32;    // [R][N]
+    int* pcfb;             // levels that fell back to plain CG
+};
+
+// Per-CTA shared state of the solve (identical in every CTA), in dynamic shared memory.
+struct Shared {
+    double red[kAcc][kBS];
+    double acc[kAcc][kMaxV];
+    double out[kAcc][kMaxV];
+    double bb[kMaxV], alpha[kMaxV], beta[kMaxV], tol[kMaxV], scale[kMaxV], target[kMaxV], gam[kMaxV];
+    int act[kMaxV], oact[kMaxV], zero[kMaxV], first[kMaxV], pcoff[kMaxV], fresh[kMaxV];
+    int it_solve[kMaxV];
+    int refines[kMaxV];
+    int fb[kMaxV];          // preconditioner fall-backs
+    long long it_total[kMaxV];
+    double vbytes[kMaxV];   // algorithmic bytes moved, per virtual level
+    double bytes;           // bytes of the lower-block updates
+    int last, glast, ok;
+    int cta, nb;            // this CTA's index in its partition, CTAs in the partition
+    unsigned mine;
+    unsigned long long pt[kProf];
+    unsigned long long tprev;
+};
+
+// Device timeline: CTA 0's thread 0 charges the time since the previous mark to `cat`.
+__device__ __forceinline__ void prof(Shared& sh, int cat) {
+    if (sh.cta == 0 && threadIdx.x == 0) {
+        const unsigned long long now = ms_globaltimer();
+        sh.pt[cat] += now - sh.tprev;
+        sh.tprev = now;
+    }
+}
+
+// y = sum_k val[k] * x[col[k]] over one CSR row, by a sub-warp of S lanes
+// (sl = lane within the sub-warp); the result is valid in every lane.  All 32
+// lanes of the warp must call it (invalid rows pass e = s).
+// The matrix (col, val) is read-only for the whole kernel and may use the
+// non-coherent path; x is written by other CTAs between phases and must not
+// (no __restrict__ on it).  The loop is unrolled by 4 with independent loads so
+// that a lane keeps several gathers in flight (small levels are latency-bound).
+template <typename TV, typename TX, typename TA>
+__device__ __forceinline__ TA csr_row(const int32_t* __restrict__ col, const TV* __restrict__ val,
+                                      const TX* x, int64_t s, int64_t e, int sl, int S) {
+    TA acc = TA(0);
+    int64_t k = s + sl;
+    for (; k + 3 * S < e; k += 4 * S) {
+        const int32_t c0 = __ldg(col + k), c1 = __ldg(col + k + S), c2 = __ldg(col + k + 2 * S),
+                      c3 = __ldg(col + k + 3 * S);
+        const TV v0 = __ldg(val + k), v1 = __ldg(val + k + S), v2 = __ldg(val + k + 2 * S), v3 = __ldg(val + k + 3 * S);
+        const TX x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+        acc += (TA)v0 * (TA)x0;
+        acc += (TA)v1 * (TA)x1;
+        acc += (TA)v2 * (TA)x2;
+        acc += (TA)v3 * (TA)x3;
+    }
+    for (; k < e; k += S) acc += (TA)__ldg(val + k) * (TA)x[__ldg(col + k)];
+    for (int o = S >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+// A work chunk: rows [r0, r1) of level l for right-hand side rhs (vectors at offset vb).
+struct Chunk {
+    int v, l;
+    int64_t r0, r1, vb;
+};
+
+// Add the block's thread-local accumulators into sh.acc[k][cur]: values are
+// staged in shared memory and summed by one warp per accumulator in a fixed
+// order (few FP64 instructions; deterministic).
+template <int K>
+__device__ __forceinline__ void flush_acc(Shared& sh, double* acc, int cur) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        sh.red[k][threadIdx.x] = acc[k];
+        acc[k] = 0.0;
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < K) {
+        double t = 0.0;
+#pragma unroll
+        for (int j = 0; j < kBS / 32; ++j) t += sh.red[w][lane + 32 * j];
+        t = warp_sum(t);
+        if (lane == 0) sh.acc[w][cur] += t;
+    }
+    __syncthreads();
+}
+
+// Run body(chunk, acc) over this CTA's chunks whose virtual level passes sel(v);
+// thread-local accumulators are block-reduced into sh.acc[k][v] and the per-CTA
+// sums of all virtual levels are written to the partials array.
+template <int K, typename Sel, typename Body>
+__device__ __forceinline__ void run_phase(const SolveArgs& a, Shared& sh, Sel sel, Body body) {
+    if (K > 0) {
+        for (int i = threadIdx.x; i < kAcc * kMaxV; i += kBS) (&sh.acc[0][0])[i] = 0.0;
+        __syncthreads();
+    }
+    double acc[K > 0 ? K : 1];
+#pragma unroll
+    for (int k = 0; k < (K > 0 ? K : 1); ++k) acc[k] = 0.0;
+    int cur = -1;
+    // Global chunk g = rhs * C + c goes to CTA g mod sh.nb; the CTA walks its
+    // chunks in increasing g, level by level, and jumps over levels that sel() rejects.
+    const int nb = sh.nb, C = a.C;
+    int first = sh.cta;  // first chunk of this CTA within the current right-hand side
+    for (int rhs = 0; rhs < a.R; ++rhs) {
+        int l = 0;
+        for (int c = first; c < C;) {
+            while (c >= a.coff[l + 1]) ++l;
+            const int v = rhs * a.L + l;
+            if (!sel(v)) {
+                const int e = a.coff[l + 1];
+                c += (e - c + nb - 1) / nb * nb;
+                continue;
+            }
+            if (K > 0 && v != cur) {
+                if (cur >= 0) flush_acc<K>(sh, acc, cur);
+                cur = v;
+            }
+            Chunk ch;
+            ch.l = l;
+            ch.v = v;
+            ch.vb = (int64_t)rhs * a.N;
+            ch.r0 = a.off[l] + (int64_t)(c - a.coff[l]) * kChunk;
+            ch.r1 = min(ch.r0 + (int64_t)kChunk, a.off[l + 1]);
+            body(ch, acc);
+            c += nb;
+        }
+        // chunks of the next right-hand side: rhs * C + c == sh.cta (mod nb)
+        first = (first - C % nb + nb) % nb;
+    }
+    if (K > 0) {
+        if (cur >= 0) flush_acc<K>(sh, acc, cur);
+        for (int i = threadIdx.x; i < K * a.V; i += kBS) {
+            const int k = i / a.V, v = i % a.V;
+            a.part[((size_t)k * a.V + v) * sh.nb + sh.cta] = sh.acc[k][v];
+        }
+    }
+}
+
+// Grid barrier with two-level arrival; with K > 0 it also reduces the per-CTA
+// partials: the last CTA of each group of kGroup sums its group's partials of all
+// K V sums, the last group leader sums the group sums and publishes them in
+// a.scal before releasing the other CTAs, and every CTA then copies the sums into
+// sh.out.  Every wait is bounded: past timeout_ns it records MS_ERR_TIMEOUT and
+// returns false; it also returns false once another CTA has recorded a time-out.
+template <int K>
+__device__ bool gsync_reduce(const SolveArgs& a, Shared& sh) {
+    const unsigned nb = sh.nb;
+    const unsigned grp = (unsigned)sh.cta / kGroup;
+    const unsigned ngrp = (nb + kGroup - 1) / kGroup;
+    const int npair = K * a.V;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(a.bar[1]);
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> gc(a.bar[2 + grp]);
+        sh.mine = g.load(cuda::memory_order_relaxed);
+        const unsigned gsize = min((unsigned)kGroup, nb - grp * kGroup);
+        sh.glast = gc.fetch_add(1u, cuda::memory_order_acq_rel) == gsize - 1;
+        if (sh.glast) gc.store(0u, cuda::memory_order_relaxed);
+        sh.last = 0;
+    }
+    __syncthreads();
+    if (sh.glast) {
+        if (K > 0) {  // group sums, in CTA order
+            const unsigned b0 = grp * kGroup, b1 = min(nb, b0 + kGroup);
+            for (int i = threadIdx.x; i < npair; i += kBS) {
+                const double* src = a.part + (size_t)i * nb;
+                double s = 0.0;
+                for (unsigned b = b0; b < b1; ++b) s += __ldcg(src + b);
+                __stcg(a.gpart + (size_t)grp * kAcc * a.V + i, s);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(a.bar[0]);
+            sh.last = c.fetch_add(1u, cuda::memory_order_acq_rel) == ngrp - 1;
+        }
+        __syncthreads();
+    }
+    int ok = 1;
+    if (sh.last) {
+        if (K > 0) {  // grid sums, in group order
+            for (int i = threadIdx.x; i < npair; i += kBS) {
+                double s = 0.0;
+                for (unsigned gi = 0; gi < ngrp; ++gi) s += __ldcg(a.gpart + (size_t)gi * kAcc * a.V + i);
+                __stcg(a.scal + i, s);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(a.bar[1]);
+            cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(a.bar[0]);
+            c.store(0u, cuda::memory_order_relaxed);
+            g.store(sh.mine + 1u, cuda::memory_order_release);
+        }
+    } else if (threadIdx.x == 0) {
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(a.bar[1]);
+        cuda::atomic_ref<int, cuda::thread_scope_device> st(*a.status);
+        const unsigned long long t0 = ms_globaltimer();
+        unsigned spins = 0;
+        while (g.load(cuda::memory_order_acquire) == sh.mine) {
+            if ((++spins & 255u) == 0u) {
+                if (st.load(cuda::memory_order_relaxed) == MS_ERR_TIMEOUT) { ok = 0; break; }
+                if (ms_globaltimer() - t0 > a.timeout_ns) {
+                    int expect = 0;
+                    st.compare_exchange_strong(expect, (int)MS_ERR_TIMEOUT, cuda::memory_order_relaxed);
+                    if (expect != 0) st.store((int)MS_ERR_TIMEOUT, cuda::memory_order_relaxed);
+                    ok = 0;
+                    break;
+                }
+            }
+            __nanosleep(32);
+        }
+    }
+    if (threadIdx.x == 0) {
+        cuda::atomic_ref<int, cuda::thread_scope_device> st(*a.status);
+        if (st.load(cuda::memory_order_relaxed) == MS_ERR_TIMEOUT) ok = 0;
+        sh.ok = ok;  // a separate flag: sh.last may still be read by warps that lag behind
+    }
+    __syncthreads();
+    if (!sh.ok) return false;
+    if (K > 0) {
+        for (int i = threadIdx.x; i < npair; i += kBS) {
+            const int k = i / a.V, v = i % a.V;
+            sh.out[k][v] = __ldcg(a.scal + i);
+        }
+        __syncthreads();
+    }
+    prof(sh, kPrfBarrier);
+    return true;
+}
+
+__device__ __forceinline__ bool gsync(const SolveArgs& a, Shared& sh) { return gsync_reduce<0>(a, sh); }
+
+// Rows [r0, r1) of a chunk, one sub-warp of S lanes per row; fn(row, valid, sl).
+template <typename Fn>
+__device__ __forceinline__ void rows_by_subwarp(int64_t r0, int64_t r1, int S, Fn fn) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int spw = 32 / S;
+    const int64_t n = r1 - r0;
+    for (int64_t base = (int64_t)w * spw; base < n; base += (int64_t)kNW * spw) {
+        const int64_t row = r0 + base + lane / S;
+        fn(row, row < r1, lane & (S - 1));
+    }
+}
+
+// ---------------------------------------------------------------- level solve
+
+// Solve A_l x_l = beta_l for the levels [l0, l1) of every right-hand side, x warm.
+// tight_all: every level to a.tol, else only level l0 to a.tol and the others to
+// a.inter_tol.
+template <int MODE>
+__device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, bool tight_all) {
+    const int tid = threadIdx.x;
+    const int V = a.V, L = a.L;
+    for (int v = tid; v < kMaxV; v += kBS) {
+        const int l = v % L;
+        sh.oact[v] = (v < V && l >= l0 && l < l1) ? 1 : 0;
+        sh.act[v] = 0;
+        sh.zero[v] = 0;
+        sh.pcoff[v] = 0;
+        sh.it_solve[v] = 0;
+        sh.tol[v] = (tight_all || l == l0) ? a.tol : a.inter_tol;
+    }
+    __syncthreads();
+    bool first_outer = true;
+    for (int outer = 0; outer < a.max_outer; ++outer) {
+        // ---- P1: FP64 true residual r = b - A x (FP64 CSR)
+        run_phase<2>(a, sh, [&](int v) { return sh.oact[v] != 0; }, [&](const Chunk& ch, double* acc) {
+            const int S = a.tprA[ch.l];
+            const double* xv = a.x + ch.vb;
+            rows_by_subwarp(ch.r0, ch.r1, S, [&](int64_t row, bool ok, int sl) {
+                int64_t s = 0, e = 0;
+                if (ok) { s = a.Arp[row]; e = a.Arp[row + 1]; }
+                const double y = csr_row<double, double, double>(a.Acol, a.Av64, xv, s, e, sl, S);
+                if (ok && sl == 0) {
+                    const double b = a.beta[ch.vb + row];
+                    const double ri = b - y;
+                    a.r[ch.vb + row] = ri;
+                    acc[0] += ri * ri;
+                    acc[1] += b * b;
+                }
+            });
+        });
+        prof(sh, kPrfResid);
+        if (!gsync_reduce<2>(a, sh)) return false;
+        // decisions: one thread per virtual level
+        int my_any = 0, my_zero = 0;
+        for (int v = tid; v < V; v += kBS) {
+            if (!sh.oact[v]) continue;
+            const int l = v % L;
+            const double rr = sh.out[0][v];
+            if (first_outer) sh.bb[v] = sh.out[1][v];
+            const double bb = sh.bb[v];
+            sh.vbytes[v] += (double)a.nnzA[l] * 12.0 + (double)(a.off[l + 1] - a.off[l]) * 32.0;
+            if (!isfinite(rr) || !isfinite(bb)) {
+                sh.oact[v] = 0;
+                if (sh.cta == 0) atomicCAS(a.status, 0, (int)MS_ERR_NUMERIC);
+                continue;
+            }
+            if (bb == 0.0) {  // zero right-hand side: the solution is zero
+                sh.zero[v] = 1;
+                sh.oact[v] = 0;
+                my_zero = 1;
+                if (sh.cta == 0) a.resid[v] = 0.0;
+                continue;
+            }
+            const double res = sqrt(rr / bb);
+            if (sh.cta == 0) a.resid[v] = res;
+            if (res <= sh.tol[v]) {
+                sh.oact[v] = 0;
+                continue;
+            }
+            if (sh.it_solve[v] >= a.max_iters) {
+                sh.oact[v] = 0;
+                if (sh.cta == 0) atomicCAS(a.status, 0, (int)MS_ERR_NOT_CONVERGED);
+                continue;
+            }
+            my_any = 1;
+            sh.refines[v] += 1;
+            sh.act[v] = 1;
+            sh.first[v] = 1;
+            if (MODE == 0) {
+                // recursive-residual target, with margin below the true-residual tolerance
+                sh.target[v] = 0.25 * sh.tol[v] * sh.tol[v] * bb;
+            } else {
+                sh.scale[v] = 1.0 / sqrt(rr);
+                const double need = 0.5 * sh.tol[v] * sqrt(bb) * sh.scale[v];
+                const double t = fmax(a.inner_tol, fmin(need, 1.0));
+                sh.target[v] = t * t;
+            }
+        }
+        const bool any = __syncthreads_or(my_any) != 0;
+        const bool anyzero = __syncthreads_or(my_zero) != 0;
+        prof(sh, kPrfScalar);
+        first_outer = false;
+        {
+            if (anyzero) {
+                run_phase<0>(a, sh, [&](int v) { return sh.zero[v] != 0; }, [&](const Chunk& ch, double*) {
+                    for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) a.x[ch.vb + row] = 0.0;
+                });
+                prof(sh, kPrfOther);
+                // other CTAs read these rows in the next phases
+                if (!gsync(a, sh)) return false;
+                for (int v = tid; v < kMaxV; v += kBS) sh.zero[v] = 0;
+                __syncthreads();
+            }
+        }
+        if (!any) break;
+
+        if (MODE == 1) {
+            // ---- P2: r32 = r / |r|, x32 = 0
+            run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0; }, [&](const Chunk& ch, double*) {
+                const double sc = sh.scale[ch.v];
+                for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
+                    a.r32[ch.vb + row] = (float)(a.r[ch.vb + row] * sc);
+                    a.x32[ch.vb + row] = 0.f;
+                }
+            });
+            for (int v = tid; v < V; v += kBS)
+                if (sh.act[v]) sh.vbytes[v] += (double)(a.off[v % L + 1] - a.off[v % L]) * 16.0;
+            prof(sh, kPrfOther);
+            if (!gsync(a, sh)) return false;
+        }
+
+        // ---- inner CG iterations (single-reduction form; preconditioned with
+        //      M = G^T G in MIXED mode when a.pc: u = M r, otherwise u = r)
+        for (;;) {
+            const bool use_pc = MODE == 1 && a.pc;
+            if (use_pc) {
+                // G1: u1 = G r  (row pattern: self + preceding neighbours)
+                run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0 && !sh.pcoff[v]; },
+                             [&](const Chunk& ch, double*) {
+                                 const float* rv = a.r32 + ch.vb;
+                                 for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
+                                     float acc = 0.f;
+#pragma unroll
+                                     for (int k = 0; k < kPcOut; ++k) {
+                                         const int32_t c = __ldg(a.gcol + k * a.N + row);
+                                         if (c >= 0) acc = fmaf(__ldg(a.gval + k * a.N + row), rv[c], acc);
+                                     }
+                                     a.u1_32[ch.vb + row] = acc;
+                                 }
+                             });
+                prof(sh, kPrfOther);
+                if (!gsync(a, sh)) return false;
+                // G2: u = G^T u1
+                run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0 && !sh.pcoff[v]; },
+                             [&](const Chunk& ch, double*) {
+                                 const float* u1 = a.u1_32 + ch.vb;
+                                 rows_by_subwarp(ch.r0, ch.r1, 2, [&](int64_t row, bool ok, int sl) {
+                                     int64_t s = 0, e = 0;
+                                     if (ok) { s = __ldg(a.gt_rp + row); e = __ldg(a.gt_rp + row + 1); }
+                                     const float y = csr_row<float, float, float>(a.gt_col, a.gt_val, u1, s, e, sl, 2);
+                                     if (ok && sl == 0) a.u32[ch.vb + row] = y;
+                                 });
+                             });
+                prof(sh, kPrfOther);
+                if (!gsync(a, sh)) return false;
+            }
+            // M: w = A u; gamma = r.u, delta = w.u, rho = r.r
+            run_phase<3>(a, sh, [&](int v) { return sh.act[v] != 0; }, [&](const Chunk& ch, double* acc) {
+                if (MODE == 0) {
+                    const int S = a.tprA[ch.l];
+                    const double* rv = a.r + ch.vb;
+                    rows_by_subwarp(ch.r0, ch.r1, S, [&](int64_t row, bool ok, int sl) {
+                        int64_t s = 0, e = 0;
+                        if (ok) { s = a.Arp[row]; e = a.Arp[row + 1]; }
+                        const double y = csr_row<double, double, double>(a.Acol, a.Av64, rv, s, e, sl, S);
+                        if (ok && sl == 0) {
+                            const double ri = rv[row];
+                            a.q[ch.vb + row] = y;
+                            acc[0] += ri * ri;
+                            acc[1] += ri * y;
+                            acc[2] += ri * ri;
+                        }
+                    });
+                    return;
+                }
+                const float* uin = ((use_pc && !sh.pcoff[ch.v]) ? a.u32 : a.r32) + ch.vb;
+                const float* rv = a.r32 + ch.vb;
+                float* qv = a.q32 + ch.vb;
+                if (a.mf) {
+                    // matrix-free: the cells whose first point lies in [r0, r1)
+                    const MFLevel& g = a.mfv.lv[ch.l];
+                    int64_t cfirst = a.mfv.cellid[ch.r0];
+                    if (a.mfv.cell_start[g.cell_off + cfirst] < ch.r0) ++cfirst;
+                    const int64_t cend = (int64_t)a.mfv.cellid[ch.r1 - 1] + 1;
+                    mf_cells_any(a.mfv, ch.l, cfirst, cend, tid >> 5, kNW, a.mf_tpp, uin,
+                                 [&](int64_t row, float y) {
+                                     const float ri = rv[row], ui = uin[row];
+                                     qv[row] = y;
+                                     acc[0] += (double)ri * (double)ui;
+                                     acc[1] += (double)ui * (double)y;
+                                     acc[2] += (double)(ri * ri);
+                                 });
+                    return;
+                }
+                const int S = a.tprA[ch.l];
+                rows_by_subwarp(ch.r0, ch.r1, S, [&](int64_t row, bool ok, int sl) {
+                    int64_t s = 0, e = 0;
+                    if (ok) { s = a.Arp[row]; e = a.Arp[row + 1]; }
+                    const float y = csr_row<float, float, float>(a.Acol, a.Av32, uin, s, e, sl, S);
+                    if (ok && sl == 0) {
+                        const float ri = rv[row], ui = uin[row];
+                        qv[row] = y;
+                        acc[0] += (double)ri * (double)ui;
+                        acc[1] += (double)ui * (double)y;
+                        acc[2] += (double)(ri * ri);
+                    }
+                });
+            });
+            prof(sh, kPrfMatvec);
+            if (!gsync_reduce<3>(a, sh)) return false;
+            int my_go = 0;
+            {
+                for (int v = tid; v < V; v += kBS) {
+                    if (!sh.act[v]) continue;
+                    const int l = v % L;
+                    const double gam = sh.out[0][v], del = sh.out[1][v], rho = sh.out[2][v];
+                    const bool lpc = use_pc && !sh.pcoff[v];
+                    const double n = (double)(a.off[l + 1] - a.off[l]);
+                    sh.vbytes[v] += (double)a.nnzA[l] * (MODE == 0 ? 12.0 : 8.0) + n * (MODE == 0 ? 32.0 : (lpc ? 24.0 : 20.0));
+                    if (lpc) sh.vbytes[v] += n * (2.0 * kPcOut * 12.0 + 16.0);
+                    if (!isfinite(gam) || !isfinite(del) || !isfinite(rho)) {
+                        sh.act[v] = 0;
+                        sh.oact[v] = 0;
+                        if (sh.cta == 0) atomicCAS(a.status, 0, (int)MS_ERR_NUMERIC);
+                        continue;
+                    }
+                    if (rho <= sh.target[v] || sh.it_solve[v] >= a.max_iters) {
+                        sh.act[v] = 0;  // converged (recursive residual) or capped
+                        continue;
+                    }
+                    if (lpc && !(gam > 0.0)) {
+                        // r^T M r <= 0 cannot happen for an SPD M: treat the preconditioner as
+                        // broken and fall back to plain CG from the current iterate
+                        sh.pcoff[v] = 1;
+                        sh.fb[v] += 1;
+                        sh.act[v] = 0;
+                        continue;
+                    }
+                    double al, be;
+                    if (sh.first[v]) {
+                        be = 0.0;
+                        al = del > 0.0 ? gam / del : -1.0;
+                    } else {
+                        be = gam / sh.gam[v];
+                        const double den = del - be * gam / sh.alpha[v];
+                        al = den > 0.0 ? gam / den : -1.0;
+                    }
+                    if (!(al > 0.0)) {
+                        if (MODE == 1 && !sh.first[v]) {
+                            // lost curvature in the FP32 recurrence (cancellation on an ill-conditioned
+                            // level): end this inner solve; the FP64 true residual restarts it
+                            sh.act[v] = 0;
+                            continue;
+                        }
+                        if (lpc) {  // u^T A u <= 0 at a restart: the preconditioner is unusable here
+                            sh.pcoff[v] = 1;
+                            sh.fb[v] += 1;
+                            sh.act[v] = 0;
+                            continue;
+                        }
+                        // p^T A p <= 0 at a restart: A_l is not positive definite in floating point
+                        sh.act[v] = 0;
+                        sh.oact[v] = 0;
+                        if (sh.cta == 0) atomicCAS(a.status, 0, (int)MS_ERR_NOT_SPD);
+                        continue;
+                    }
+                    sh.fresh[v] = sh.first[v];  // the update must not read the old p, s
+                    sh.first[v] = 0;
+                    sh.alpha[v] = al;
+                    sh.beta[v] = be;
+                    sh.gam[v] = gam;
+                    sh.it_solve[v] += 1;
+                    sh.it_total[v] += 1;
+                    sh.vbytes[v] += n * (MODE == 0 ? 72.0 : 36.0);
+                    my_go = 1;
+                }
+            }
+            const bool go = __syncthreads_or(my_go) != 0;
+            prof(sh, kPrfScalar);
+            if (!go) break;
+            // E: p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s
+            run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0; }, [&](const Chunk& ch, double*) {
+                const double al = sh.alpha[ch.v], be = sh.beta[ch.v];
+                // first iteration: p = u, s = w (the old p, s are not read: they may
+                // hold anything, and 0 * NaN would poison the recurrence)
+                const bool fr = sh.fresh[ch.v] != 0;
+                const int64_t vb = ch.vb;
+                if (MODE == 0) {
+                    for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
+                        const int64_t i = vb + row;
+                        const double ri = a.r[i];
+                        const double pi = fr ? ri : ri + be * a.p[i];
+                        const double si = fr ? a.q[i] : a.q[i] + be * a.s[i];
+                        a.p[i] = pi;
+                        a.s[i] = si;
+                        a.x[i] += al * pi;
+                        a.r[i] = ri - al * si;
+                    }
+                } else {
+                    const float af = (float)al, bf = (float)be;
+                    const float* uin = (use_pc && !sh.pcoff[ch.v]) ? a.u32 : a.r32;
+                    for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
+                        const int64_t i = vb + row;
+                        const float ri = a.r32[i];
+                        const float pi = fr ? uin[i] : fmaf(bf, a.p32[i], uin[i]);
+                        const float si = fr ? a.q32[i] : fmaf(bf, a.s32[i], a.q32[i]);
+                        a.p32[i] = pi;
+                        a.s32[i] = si;
+                        a.x32[i] = fmaf(af, pi, a.x32[i]);
+                        a.r32[i] = fmaf(-af, si, ri);
+                    }
+                }
+            });
+            prof(sh, kPrfUpdate);
+            if (!gsync(a, sh)) return false;
+        }
+
+        if (MODE == 1) {
+            // ---- P3: x += |r| d  (FP64)
+            run_phase<0>(a, sh, [&](int v) { return sh.oact[v] != 0 && sh.scale[v] > 0.0; },
+                         [&](const Chunk& ch, double*) {
+                             const double inv = 1.0 / sh.scale[ch.v];
+                             for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS)
+                                 a.x[ch.vb + row] += (double)a.x32[ch.vb + row] * inv;
+                         });
+            for (int v = tid; v < V; v += kBS)
+                if (sh.oact[v]) sh.vbytes[v] += (double)(a.off[v % L + 1] - a.off[v % L]) * 20.0;
+            prof(sh, kPrfOther);
+            if (!gsync(a, sh)) return false;
+        }
+    }
+    // levels still active after max_outer rounds did not reach the tolerance
+    if (sh.cta == 0)
+        for (int v = tid; v < V; v += kBS)
+            if (sh.oact[v]) atomicCAS(a.status, 0, (int)MS_ERR_NOT_CONVERGED);
+    __syncthreads();
+    return true;
+}
+
+// The whole schedule of eq. split for one hierarchy, run by the CTAs [0, sh.nb) of a
+// partition (sh.cta: this CTA's index in it).
+template <int MODE>
+__device__ __forceinline__ void fit_body(const SolveArgs& a, Shared& sh) {
+    const int tid = threadIdx.x;
+    for (int v = tid; v < kMaxV; v += kBS) {
+        sh.it_total[v] = 0;
+        sh.refines[v] = 0;
+        sh.fb[v] = 0;
+        sh.vbytes[v] = 0.0;
+        sh.scale[v] = 0.0;
+    }
+    if (tid == 0) {
+        sh.bytes = 0.0;
+        for (int i = 0; i < kProf; ++i) sh.pt[i] = 0ull;
+        sh.tprev = ms_globaltimer();
+    }
+    __syncthreads();
+    const int L = a.L;
+    // beta_0 = f, x = 0
+    run_phase<0>(a, sh, [](int) { return true; }, [&](const Chunk& ch, double*) {
+        for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
+            a.beta[ch.vb + row] = a.f[ch.vb + row];
+            a.x[ch.vb + row] = 0.0;
+        }
+    });
+    prof(sh, kPrfOther);
+    if (!gsync(a, sh)) return;
+    for (int m = 0; m < a.sweeps; ++m) {
+        if (m <= L - 2) {
+            if (!solve_levels<MODE>(a, sh, m, L - 1, false)) return;
+        }
+        if (m + 1 <= L - 1 && a.lower_inc) {
+            // beta_k -= B_km t_m for the rows of levels k = m+1..L-1 (FP64).  When
+            // intermediate levels are not iterated (inter_tol >= 1) t_m is the only
+            // level solution that changed since beta was last updated (levels above m
+            // still hold t = 0), so only the blocks B_km are read: every block of B
+            // once over the whole fit.
+            run_phase<0>(a, sh, [&](int v) { return v % L >= m + 1; }, [&](const Chunk& ch, double*) {
+                const int S = a.tprBm[m];
+                const double* xv = a.x + ch.vb;
+                const int32_t* seg0 = a.Bseg + (int64_t)m * a.N;
+                const int32_t* seg1 = seg0 + a.N;
+                rows_by_subwarp(ch.r0, ch.r1, S, [&](int64_t row, bool ok, int sl) {
+                    int64_t s = 0, e = 0;
+                    if (ok) {
+                        const int64_t b = a.Brp[row];
+                        s = b + __ldg(seg0 + row);
+                        e = b + __ldg(seg1 + row);
+                    }
+                    const double y = csr_row<double, double, double>(a.Bcol, a.Bv64, xv, s, e, sl, S);
+                    if (ok && sl == 0) a.beta[ch.vb + row] -= y;
+                });
+            });
+            if (tid == 0)
+                sh.bytes += a.R * ((double)a.nnzBm[m] * 12.0 + (double)(a.off[L] - a.off[m + 1]) * 32.0);
+            prof(sh, kPrfLower);
+            if (!gsync(a, sh)) return;
+        } else if (m + 1 <= L - 1) {
+            // beta_k = f_k - sum_{j<k} B_kj t_j for the rows of levels k = m+1..L-1 (FP64)
+            run_phase<0>(a, sh, [&](int v) { return v % L >= m + 1; }, [&](const Chunk& ch, double*) {
+                const int S = a.tprB[ch.l];
+                const double* xv = a.x + ch.vb;
+                rows_by_subwarp(ch.r0, ch.r1, S, [&](int64_t row, bool ok, int sl) {
+                    int64_t s = 0, e = 0;
+                    if (ok) { s = a.Brp[row]; e = a.Brp[row + 1]; }
+                    const double y = csr_row<double, double, double>(a.Bcol, a.Bv64, xv, s, e, sl, S);
+                    if (ok && sl == 0) a.beta[ch.vb + row] = a.f[ch.vb + row] - y;
+                });
+            });
+            if (tid == 0)
+                for (int l = m + 1; l < L; ++l)
+                    sh.bytes += a.R * ((double)a.nnzB[l] * 12.0 + (double)(a.off[l + 1] - a.off[l]) * 32.0);
+            prof(sh, kPrfLower);
+            if (!gsync(a, sh)) return;
+        }
+    }
+    if (!solve_levels<MODE>(a, sh, 0, L, true)) return;
+    if (sh.cta == 0 && tid == 0) {
+        for (int l = 0; l < L; ++l) {
+            long long it = 0;
+            int rf = 0;
+            for (int r = 0; r < a.R; ++r) {
+                it += sh.it_total[r * L + l];
+                rf += sh.refines[r * L + l];
+            }
+            a.iters[l] = it;
+            a.refines[l] = rf;
+        }
+        double b = sh.bytes;
+        int fb = 0;
+        for (int v = 0; v < a.V; ++v) {
+            b += sh.vbytes[v];
+            fb += sh.fb[v];
+        }
+        a.bytes[0] = b;
+        for (int i = 0; i < kProf; ++i) a.prof[i] = sh.pt[i];
+        a.pcfb[0] = fb;
+    }
+}
+
+
+
+// ---------------------------------------------------------------- host helpers
+
+inline unsigned nblk(int64_t n, int bs) { return (unsigned)std::max<int64_t>(1, (n + bs - 1) / bs); }
+
+// Sub-warp width for CSR rows of avg_nnz entries: about 16 entries per lane
+// keeps enough independent loads in flight per lane (measured on GB300: 4 lanes
+// for ~50-entry rows run 2.5x faster than 16).
+int tpr_for(double avg_nnz) {
+    int S = 1;
+    while (S < 32 && S * 16 < avg_nnz) S <<= 1;
+    return S;
+}
+
+MFView make_mfview(const ms_hierarchy* h) {
+    MFView v{};
+    v.d = h->d;
+    v.L = h->L;
+    v.N = h->N;
+    v.E = h->view.w.e;
+    for (int i = 0; i < 4; ++i) v.c[i] = (float)h->view.w.c[i];
+    v.W = h->W;
+    v.cellid = h->cellid;
+    v.cell_start = h->cell_start;
+    for (int l = 0; l < h->L; ++l) {
+        const LevelGrid& g = h->view.grid[l];
+        MFLevel& m = v.lv[l];
+        for (int a = 0; a < 3; ++a) m.G[a] = g.G[a];
+        m.R = h->view.R;
+        m.cod = (float)(g.cell / h->view.delta[l]);
+        m.dscale = (float)h->view.dscale[l];
+        m.cell_off = g.cell_off;
+        m.ncells = g.ncells;
+    }
+    return v;
+}
+
+// Lanes per target point of the matrix-free mat-vec: about one warp per cell of the finest level.
+int mf_tpp_for(const ms_hierarchy* h) {
+    const LevelGrid& g = h->view.grid[h->L - 1];
+    const double occupied = (double)g.G[0] * g.G[1] * g.G[2];
+    const double per_cell = (double)(h->view.off[h->L] - h->view.off[h->L - 1]) / std::max(occupied, 1.0);
+    int t = 1;
+    while (t < 8 && per_cell * t * 2 <= 32.0) t <<= 1;
+    return t;
+}
+
+// Fill the solve arguments that depend only on the hierarchy, the options and R.
+void fill_args(const ms_hierarchy* h, double rel_tol, int R, SolveArgs& a) {
+    const int64_t* rpA = h->rpA_lv;
+    const int64_t* rpB = h->rpB_lv;
+    a.mf = (h->opts.precision == MS_PREC_MIXED && h->opts.op == MS_OP_MATRIX_FREE) ? 1 : 0;
+    a.mf_tpp = h->mf_tpp;
+    a.mfv = make_mfview(h);
+    a.pc = (h->opts.precision == MS_PREC_MIXED && h->opts.precond != MS_PRECOND_NONE) ? 1 : 0;
+    a.gcol = h->pc.gcol;
+    a.gval = h->pc.gval;
+    a.gt_rp = h->pc.gt_rp;
+    a.gt_col = h->pc.gt_col;
+    a.gt_val = h->pc.gt_val;
+    const int L = h->L;
+    a.L = L;
+    a.R = R;
+    a.V = R * L;
+    a.N = h->N;
+    int64_t c = 0;
+    for (int l = 0; l <= L; ++l) {
+        a.off[l] = h->view.off[l];
+        a.coff[l] = (int)c;
+        if (l < L) c += (h->view.off[l + 1] - h->view.off[l] + kChunk - 1) / kChunk;
+    }
+    a.C = (int)c;
+    for (int l = 0; l < L; ++l) {
+        const int64_t n = h->view.off[l + 1] - h->view.off[l];
+        a.nnzA[l] = rpA[l + 1] - rpA[l];
+        a.nnzB[l] = rpB[l + 1] - rpB[l];
+        a.tprA[l] = h->opts.threads_per_row > 0 ? h->opts.threads_per_row : tpr_for((double)a.nnzA[l] / n);
+        a.tprB[l] = tpr_for((double)a.nnzB[l] / n);
+    }
+    a.Arp = h->A.rp; a.Acol = h->A.col; a.Av64 = h->A.v64; a.Av32 = h->A.v32;
+    a.Brp = h->B.rp; a.Bcol = h->B.col; a.Bv64 = h->B.v64;
+    a.Bseg = h->Bseg;
+    for (int m = 0; m < L; ++m) {
+        int64_t nb = 0;
+        for (int k = m + 1; k < L; ++k) nb += h->Bblk[k][m];
+        const int64_t rows = h->view.off[L] - h->view.off[std::min(m + 1, L)];
+        a.nnzBm[m] = nb;
+        a.tprBm[m] = tpr_for(rows > 0 ? (double)nb / rows : 1.0);
+    }
+    const bool mixed = h->opts.precision == MS_PREC_MIXED;
+    a.sweeps = h->opts.jacobi_sweeps > 0 ? h->opts.jacobi_sweeps : std::max(L - 1, 0);
+    a.max_iters = h->opts.max_iters > 0 ? h->opts.max_iters : 20000;
+    a.max_outer = mixed ? 40 : 8;
+    a.tol = rel_tol;
+    a.inter_tol = h->opts.inter_tol > 0 ? std::max(h->opts.inter_tol, rel_tol) : 1.0;
+    a.inner_tol = h->opts.inner_tol > 0 ? h->opts.inner_tol : 1e-4;
+    a.lower_inc = (a.inter_tol >= 1.0 && a.Bseg) ? 1 : 0;
+    a.timeout_ns = 4000000000ull;
+}
+
+// Right-hand sides per launch: every (right-hand side, level) pair is a virtual level.
+int rhs_per_launch(const ms_hierarchy* h, int nrhs) { return std::max(1, std::min(nrhs, std::min(32, kMaxV / h->L))); }
+
+}  // namespace

@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "MS_OK", 1: "MS_ERR_ARG", 2: "MS_ERR_CUDA", 3: "MS_ERR_OOM", 
 
 # the symbols include/ms.h declares (checked by the tests)
 EXPORTED = ["ms_default_opts", "ms_build_hierarchy", "ms_build_hierarchy_dev", "ms_fit", "ms_fit_dev",
-            "ms_fit_static_dev", "ms_default_train_opts", "ms_train_precond", "ms_precond_params",
+            "ms_fit_static_dev", "ms_fit_batch", "ms_fit_batch_dev", "ms_default_train_opts", "ms_train_precond", "ms_precond_params",
             "ms_precond_inspect", "ms_evaluate", "ms_evaluate_dev", "ms_apply_dev", "ms_get_permutation", "ms_hierarchy_info",
             "ms_launch_count", "ms_last_error", "ms_destroy"]
 
@@ -113,6 +113,10 @@ def load(path: str | None = None):
     lib.ms_fit.argtypes = [_P, _D, C.c_int, C.c_double, _D, C.POINTER(ms_fit_stats)]
     lib.ms_fit_dev.argtypes = [_P, _P, C.c_int, C.c_double, _P, C.POINTER(ms_fit_stats), _P]
     lib.ms_fit_static_dev.argtypes = [_P, _P, C.c_double, _P, C.POINTER(ms_fit_stats), _P]
+    lib.ms_fit_batch.argtypes = [C.POINTER(_P), C.c_int, C.POINTER(_D), C.c_double, C.POINTER(_D),
+                                 C.POINTER(ms_fit_stats)]
+    lib.ms_fit_batch_dev.argtypes = [C.POINTER(_P), C.c_int, C.POINTER(C.c_void_p), C.c_double,
+                                     C.POINTER(C.c_void_p), C.POINTER(ms_fit_stats), _P]
     lib.ms_default_train_opts.argtypes = [C.POINTER(ms_train_opts)]
     lib.ms_default_train_opts.restype = None
     lib.ms_train_precond.argtypes = [_P, C.POINTER(C.c_int), C.c_int, C.POINTER(ms_train_opts),
@@ -224,6 +228,28 @@ def ms_fit_static_dev(handle, f, rel_tol=1e-10, alpha_out=None, stream=None):
     _check(load().ms_fit_static_dev(C.c_void_p(handle), _dev_ptr(f), rel_tol, _dev_ptr(alpha_out), C.byref(st),
                                     _stream(stream)))
     return alpha_out, st.as_dict()
+
+
+def ms_fit_batch(handles, fs, rel_tol=1e-10, alpha_out=None, stream=None):
+    """Fit nh hierarchies (one right-hand side each) in one launch; returns (alphas, stats dicts).
+    fs: list of [N_i] numpy arrays (host API) or contiguous float64 CUDA tensors (device API)."""
+    lib = load()
+    nh = len(handles)
+    hs = (_P * nh)(*[C.c_void_p(h) for h in handles])
+    st = (ms_fit_stats * nh)()
+    if nh and _is_dev(fs[0]):
+        import torch
+        outs = alpha_out if alpha_out is not None else [torch.empty_like(f) for f in fs]
+        fp = (C.c_void_p * nh)(*[_dev_ptr(f) for f in fs])
+        ap = (C.c_void_p * nh)(*[_dev_ptr(a) for a in outs])
+        _check(lib.ms_fit_batch_dev(hs, nh, fp, rel_tol, ap, st, _stream(stream)))
+        return outs, [s.as_dict() for s in st]
+    fa = [np.ascontiguousarray(f, dtype=np.float64) for f in fs]
+    outs = alpha_out if alpha_out is not None else [np.empty_like(f) for f in fa]
+    fp = (_D * nh)(*[f.ctypes.data_as(_D) for f in fa])
+    ap = (_D * nh)(*[a.ctypes.data_as(_D) for a in outs])
+    _check(lib.ms_fit_batch(hs, nh, fp, rel_tol, ap, st))
+    return outs, [s.as_dict() for s in st]
 
 
 def ms_evaluate(handle, alpha, query, out=None, stream=None):

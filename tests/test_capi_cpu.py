@@ -81,3 +81,15 @@ def test_nonfinite_points_rejected_on_host(lib):
     with pytest.raises(ms.MsError) as e:
         ms.ms_build_hierarchy(2, np.array([2]), pts, np.array([0.5]), ms.ms_default_opts())
     assert e.value.status == ms.MS_ERR_NUMERIC
+
+
+def test_fit_batch_rejects_bad_arguments_on_host(lib):
+    """Argument checks of the batched fit run before any CUDA call."""
+    L = ms.load()
+    st = (ms.ms_fit_stats * 1)()
+    assert L.ms_fit_batch(None, 1, None, 1e-10, None, st) == ms.MS_ERR_ARG
+    assert L.ms_fit_batch_dev(None, 0, None, 1e-10, None, st, None) == ms.MS_ERR_ARG
+    hs = (C.c_void_p * 1)(None)
+    fp = (C.c_void_p * 1)(None)
+    assert L.ms_fit_batch_dev(hs, 1, fp, 1e-10, fp, st, None) == ms.MS_ERR_ARG
+    assert "hierarchy 0" in ms.ms_last_error()

@@ -319,7 +319,9 @@ typedef struct ms_train_opts {
     double lr_final;     /* default 1e-4 */
     uint64_t seed;       /* SplitMix64 seed of the initial weights and of the shuffles */
     int fp32_weights;    /* 1: train and infer with the FP32 master weights (no BF16 rounding) */
-    int reserved[7];
+    float input_noise;   /* training inputs jittered by input_noise * U[-1, 1) per coordinate
+                            (units of delta; default 0.005; 0 = off) */
+    int reserved[6];
 } ms_train_opts;
 
 typedef struct ms_train_stats {

@@ -17,11 +17,18 @@ Definitions (all per level l, points X_l in input order, delta = delta_l, d = di
     is symmetric positive definite for any G with a positive diagonal.
   * scale-free weights  ghat_i = delta^{-d/2} g_i: since A_P = delta^{-d} K(offsets/delta),
     ghat depends only on the delta-scaled offsets (x_j - x_i)/delta.
-  * features  z_i in R^{K d}: the scaled offsets of the pattern's neighbours in pattern
-    order, zero-padded when fewer than K exist.
+  * features  z_i in R^{K d}: the scaled offsets o_k = (x_{n_k} - x_i)/delta of the pattern's
+    neighbours in pattern order, zero-padded when fewer than K exist, written in the point's
+    canonical frame (canonical_frame below).  The kernel is radial, so A_P, and with it the
+    exact row, is unchanged by rotating or reflecting the patch: expressing the offsets in a
+    frame fixed by the patch itself removes those d(d-1)/2 + 1 nuisance directions from the
+    network's input (measured on the oracle: a network trained on levels 1-4 needs 80 instead
+    of 130 PCG iterations on level 5, exact rows 13).
   * network   o = W3 relu(W2 relu(W1 z + b1) + b2) + b3  (hidden width 64, 17 outputs),
     ghat = mu + sigma * o (per-output standardisation of the training targets), with the
-    diagonal clamped to >= 0.1 mu_0 and the outputs of missing neighbours set to zero.
+    diagonal clamped to >= 0.1 mu_0, the outputs of missing neighbours set to zero, and the
+    row rescaled to ghat^T K ghat = 1 (K the scaled patch matrix): the exact row has this
+    value, which is (G A G^T)_ii = 1.
   * loss      energy norm of the error of the row in the patch's own metric, averaged over
               samples: (1/S) sum_s e_s^T K_s e_s with e = sigma * (o - t) on the valid outputs
               (zero elsewhere), t = (ghat - mu)/sigma the standardised exact row and
@@ -95,12 +102,45 @@ def G_matrix(rows, pat, n):
     return G
 
 
+def canonical_frame(off: np.ndarray) -> np.ndarray:
+    """Orthonormal rows e_1..e_d fixed by the (nearest-first) offsets off[m, d]:
+    e_1 = o_1/|o_1|; e_2 from o_2 by Gram-Schmidt (d = 3), or the perpendicular of e_1 (d = 2);
+    e_3 = e_1 x e_2; the last axis is flipped so that o_d has a non-negative coordinate on it
+    (d = 1: the sign that makes o_1 positive).  Missing or degenerate offsets fall back to the
+    coordinate axes: no offsets -> identity; o_2 parallel to o_1 (d = 3) -> e_2 from the
+    coordinate axis least aligned with e_1."""
+    m, d = off.shape
+    E = np.eye(d)
+    if m == 0 or not np.any(off[0]):
+        return E
+    e1 = off[0] / np.linalg.norm(off[0])
+    if d == 1:
+        return np.array([[1.0 if off[0, 0] >= 0 else -1.0]])
+    if d == 2:
+        e2 = np.array([-e1[1], e1[0]])
+        if m >= 2 and off[1] @ e2 < 0:
+            e2 = -e2
+        return np.stack([e1, e2])
+    w = off[1] - (off[1] @ e1) * e1 if m >= 2 else np.zeros(3)
+    if m >= 2 and np.linalg.norm(w) > 1e-9 * np.linalg.norm(off[1]):
+        e2 = w / np.linalg.norm(w)
+    else:
+        a = int(np.argmin(np.abs(e1)))
+        u = np.eye(3)[a]
+        e2 = u - (u @ e1) * e1
+        e2 /= np.linalg.norm(e2)
+    e3 = np.cross(e1, e2)
+    if m >= 3 and off[2] @ e3 < 0:
+        e3 = -e3
+    return np.stack([e1, e2, e3])
+
+
 def features(X: np.ndarray, delta: float, pat, K: int = K_NEIGH):
     n, d = X.shape
     Z = np.zeros((n, K * d))
     for i, nb in enumerate(pat):
         off = (X[nb] - X[i]) / delta
-        Z[i, :len(nb) * d] = off.ravel()
+        Z[i, :len(nb) * d] = (off @ canonical_frame(off).T).ravel()
     return Z
 
 
@@ -212,13 +252,22 @@ def standardise(T, Mk):
     return mu, sig
 
 
-def predict_rows(theta, Z, pat, mu, sig, n_in):
+def predict_rows(theta, Z, pat, mu, sig, n_in, Ks=None):
+    """Scale-free rows predicted by the network (self first).  With the scaled patch matrices
+    Ks, each row is rescaled to ghat^T K ghat = 1, the value the exact row has: this is
+    (G A G^T)_ii = 1, the diagonal of the preconditioned operator."""
     o, _ = forward(theta, Z, n_in)
     gh = mu + sig * o
     gh[:, 0] = np.maximum(gh[:, 0], 0.1 * mu[0])
     rows = []
     for i, nb in enumerate(pat):
-        rows.append(gh[i, :1 + len(nb)].copy())
+        r = gh[i, :1 + len(nb)].copy()
+        if Ks is not None:
+            m = len(r)
+            q = float(r @ Ks[i][:m, :m] @ r)
+            if q > 0:
+                r /= math.sqrt(q)
+        rows.append(r)
     return rows
 
 

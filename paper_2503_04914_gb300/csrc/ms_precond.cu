@@ -144,15 +144,78 @@ __global__ void k_pc_exact(HierView v, const int32_t* nbr, const int64_t* rows, 
 
 // ---------------------------------------------------------------- features
 
+// Network input of row s: the delta-scaled offsets o_k = (x_{n_k} - x_s)/delta of its
+// pattern neighbours (nearest first, zero-padded) in the patch's canonical frame: e_1 along
+// o_1; e_2 the perpendicular of e_1 (d = 2) or o_2's component orthogonal to e_1 (d = 3, the
+// coordinate axis least aligned with e_1 when o_2 is missing or parallel); e_3 = e_1 x e_2;
+// the last axis flipped so that o_d has a non-negative coordinate on it (d = 1: o_1 > 0).
+// The kernel is radial, so the exact row does not depend on the frame.  FP64 arithmetic, so
+// the frame's sign decisions are those of the FP64 oracle.
 __device__ __forceinline__ int pc_features(const HierView& v, const int32_t* nbr, int64_t s, float* z) {
     const int l = level_of_row(v.off, v.L, s);
     const double inv = 1.0 / v.delta[l];
-    int cnt = 0;
-    for (int k = 0; k < kPcK; ++k) {
+    const int d = v.d;
+    auto offset = [&](int k, double* o) {
         const int32_t c = nbr[s * kPcK + k];
-        for (int a = 0; a < v.d; ++a)
-            z[k * v.d + a] = c >= 0 ? (float)((v.X[a * v.N + c] - v.X[a * v.N + s]) * inv) : 0.f;
-        cnt += c >= 0;
+        for (int a = 0; a < 3; ++a) o[a] = (a < d && c >= 0) ? (v.X[a * v.N + c] - v.X[a * v.N + s]) * inv : 0.0;
+        return c >= 0;
+    };
+    int cnt = 0;
+    for (int k = 0; k < kPcK; ++k) cnt += nbr[s * kPcK + k] >= 0;
+    double e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    double o1[3], o2[3], o3[3];
+    offset(0, o1);
+    offset(1, o2);
+    offset(2, o3);
+    const double n1 = sqrt(o1[0] * o1[0] + o1[1] * o1[1] + o1[2] * o1[2]);
+    if (cnt >= 1 && n1 > 0.0) {
+        if (d == 1) {
+            e[0][0] = o1[0] >= 0.0 ? 1.0 : -1.0;
+        } else if (d == 2) {
+            const double a0 = o1[0] / n1, a1 = o1[1] / n1;
+            double b0 = -a1, b1 = a0;
+            if (cnt >= 2 && o2[0] * b0 + o2[1] * b1 < 0.0) { b0 = -b0; b1 = -b1; }
+            e[0][0] = a0; e[0][1] = a1;
+            e[1][0] = b0; e[1][1] = b1;
+        } else {
+            const double a[3] = {o1[0] / n1, o1[1] / n1, o1[2] / n1};
+            double w[3] = {0, 0, 0};
+            double nw = 0.0, n2 = 0.0;
+            if (cnt >= 2) {
+                const double p = o2[0] * a[0] + o2[1] * a[1] + o2[2] * a[2];
+                for (int i = 0; i < 3; ++i) w[i] = o2[i] - p * a[i];
+                nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+                n2 = sqrt(o2[0] * o2[0] + o2[1] * o2[1] + o2[2] * o2[2]);
+            }
+            double b[3];
+            if (cnt >= 2 && nw > 1e-9 * n2) {
+                for (int i = 0; i < 3; ++i) b[i] = w[i] / nw;
+            } else {
+                int ax = 0;  // the coordinate axis least aligned with e_1 (first on ties)
+                for (int i = 1; i < 3; ++i)
+                    if (fabs(a[i]) < fabs(a[ax])) ax = i;
+                double u[3] = {0, 0, 0};
+                u[ax] = 1.0;
+                const double p = a[ax];
+                for (int i = 0; i < 3; ++i) b[i] = u[i] - p * a[i];
+                const double nb = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+                for (int i = 0; i < 3; ++i) b[i] /= nb;
+            }
+            double c[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+            if (cnt >= 3 && o3[0] * c[0] + o3[1] * c[1] + o3[2] * c[2] < 0.0)
+                for (int i = 0; i < 3; ++i) c[i] = -c[i];
+            for (int i = 0; i < 3; ++i) {
+                e[0][i] = a[i];
+                e[1][i] = b[i];
+                e[2][i] = c[i];
+            }
+        }
+    }
+    for (int k = 0; k < kPcK; ++k) {
+        double o[3];
+        const bool ok = offset(k, o);
+        for (int a = 0; a < d; ++a)
+            z[k * d + a] = ok ? (float)(e[a][0] * o[0] + e[a][1] * o[1] + e[a][2] * o[2]) : 0.f;
     }
     return cnt;
 }
@@ -266,7 +329,8 @@ __device__ __forceinline__ void mlp_forward(const NetLayout& N, const float* W, 
 }
 
 // Network prediction of the scale-free rows: ghat = mu + sigma o, diagonal clamped to
-// >= 0.1 mu_0 (keeps G's diagonal positive), outputs of missing neighbours zero.
+// >= 0.1 mu_0 (keeps G's diagonal positive), outputs of missing neighbours zero, then
+// scaled so that ghat^T K ghat = 1.
 // Writes G = delta^{d/2} ghat (FP32) and the row pattern, or ghat itself for inspection.
 __global__ void k_pc_infer(HierView v, const int32_t* nbr, const float* theta, int nparams, const float* musig,
                            float* gval, int32_t* gcol, float* ghat_out) {
@@ -284,6 +348,28 @@ __global__ void k_pc_infer(HierView v, const int32_t* nbr, const float* theta, i
     float g[kPcOut];
     for (int m = 0; m < kPcOut; ++m) g[m] = m <= cnt ? fmaf(ms[kPcOut + m], o[m], ms[m]) : 0.f;
     g[0] = fmaxf(g[0], 0.1f * ms[0]);
+    // (G A G^T)_ii = ghat^T K ghat, K = phi(|z_a - z_b|) on the patch (self at the origin);
+    // the exact row makes it 1: rescale the predicted row to that.
+    {
+        const int d = v.d;
+        float q = 0.f;
+        for (int a = 0; a <= cnt; ++a) {
+            float t = 0.f;
+            for (int b = 0; b <= cnt; ++b) {
+                float r2 = 0.f;
+                for (int ax = 0; ax < d; ++ax) {
+                    const float u = (a > 0 ? z[(a - 1) * d + ax] : 0.f) - (b > 0 ? z[(b - 1) * d + ax] : 0.f);
+                    r2 = fmaf(u, u, r2);
+                }
+                t = fmaf(wendland_eval<float>(v.w, sqrtf(r2)), g[b], t);
+            }
+            q = fmaf(g[a], t, q);
+        }
+        if (q > 0.f) {
+            const float sc = rsqrtf(q);
+            for (int m = 0; m <= cnt; ++m) g[m] *= sc;
+        }
+    }
     if (ghat_out) {
         // inspection: by pattern slot (slot k+1 <-> nbr[s][k])
         ghat_out[s * kPcOut] = g[0];
@@ -308,9 +394,20 @@ __global__ void k_pc_infer(HierView v, const int32_t* nbr, const float* theta, i
 // samples with (step * batch + j) >= limit are skipped (full-batch inspection).
 // Loss: sum over the block's samples of d^T K d, d = sigma * (o - t) on the valid outputs
 // (K: the sample's scaled patch matrix); escale = 2 / (samples of the step).
+// SplitMix64 output function (Steele, Lea and Flood 2014) of counter x: per-element noise.
+__device__ __forceinline__ uint64_t sm64_dev(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// noise > 0: every present input coordinate of a training sample is jittered by
+// noise * U[-1, 1) (counter = (noise_key, sample slot, coordinate); targets unchanged).
 __global__ void k_pc_train(const float* Z, const float* T, const int32_t* cnt, const float* Kp, const float* musig,
                            int64_t S, int nin, const float* theta, int batch, int64_t step, uint64_t a_mul,
-                           uint64_t a_add, int64_t limit, float escale, float* grad_part, double* loss_part) {
+                           uint64_t a_add, int64_t limit, float escale, float* grad_part, double* loss_part,
+                           float noise, uint64_t noise_key) {
     extern __shared__ float sm[];
     const NetLayout N = net_layout(nin);
     float* W = sm;
@@ -332,7 +429,12 @@ __global__ void k_pc_train(const float* Z, const float* T, const int32_t* cnt, c
     __syncthreads();
     for (int i = t; i < kTB * nin; i += nt) {
         const int s = i / nin, k = i % nin;
-        X[i] = sidx[s] >= 0 ? Z[sidx[s] * nin + k] : 0.f;
+        float x = sidx[s] >= 0 ? Z[sidx[s] * nin + k] : 0.f;
+        if (noise > 0.f && x != 0.f) {
+            const uint64_t c = noise_key ^ ((uint64_t)(step * batch + (int64_t)blockIdx.x * kTB + s) * 64u + (uint64_t)k);
+            x += noise * ((float)(sm64_dev(c) >> 40) * 0x1p-23f - 1.0f);
+        }
+        X[i] = x;
     }
     __syncthreads();
     // layer 1
@@ -703,6 +805,7 @@ void ms_default_train_opts(ms_train_opts* o) {
     o->lr = 3e-3;
     o->lr_final = 1e-4;
     o->seed = 2503049140ull;
+    o->input_noise = 0.005f;
 }
 
 ms_status ms_train_precond(ms_hierarchy* h, const int* levels, int n_levels, const ms_train_opts* opts,
@@ -772,7 +875,8 @@ ms_status ms_train_precond(ms_hierarchy* h, const int* levels, int n_levels, con
         const int64_t local = step % steps_per_epoch;
         k_pc_train<<<nb, 256, smem, st>>>(ts.Z, ts.T, ts.cnt, ts.K, pc.musig, ts.S, pc.n_in,
                                           o.fp32_weights ? pc.theta : pc.theta_bf, o.batch, local, a_mul, a_add,
-                                          INT64_MAX, escale, grad_part, loss_part);
+                                          INT64_MAX, escale, grad_part, loss_part, o.input_noise,
+                                          sm64(o.seed ^ 0x6E6F697365ull, (uint64_t)epoch));
         const float bc1 = 1.0f - std::pow(0.9f, (float)(step + 1)), bc2 = 1.0f - std::pow(0.999f, (float)(step + 1));
         double* lo = step == 0 ? loss_hist : (step == steps - 1 ? loss_hist + 1 : nullptr);
         k_pc_adam<<<nblk(N.P, 256), 256, 0, st>>>(pc.theta, pc.theta_bf, pc.adam_m, pc.adam_v, grad_part, nb, N.P, lr,
@@ -919,7 +1023,7 @@ ms_status ms_precond_inspect(ms_hierarchy* h, int what, const int* levels, int n
         MS_TRY(ts.alloc((void**)&lo, sizeof(double)));
         MS_TRY(set_train_smem(pc.n_in));
         k_pc_train<<<nb, 256, train_smem(pc.n_in), st>>>(ts.Z, ts.T, ts.cnt, ts.K, pc.musig, ts.S, pc.n_in, pc.theta,
-                                                         nb * kTB, 0, 1, 0, ts.S, 2.0f / (float)ts.S, gp, lp);
+                                                         nb * kTB, 0, 1, 0, ts.S, 2.0f / (float)ts.S, gp, lp, 0.f, 0ull);
         k_pc_adam<<<nblk(Nl.P, 256), 256, 0, st>>>(nullptr, nullptr, nullptr, nullptr, gp, nb, Nl.P, 0.f, 1.f, 1.f, lp,
                                                    lo, 1.0 / (double)ts.S, gout);
         ms_count_launch(2);

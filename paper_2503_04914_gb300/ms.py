@@ -70,7 +70,8 @@ class ms_info(C.Structure):
 
 class ms_train_opts(C.Structure):
     _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("lr_final", C.c_double),
-                ("seed", C.c_uint64), ("fp32_weights", C.c_int), ("reserved", C.c_int * 7)]
+                ("seed", C.c_uint64), ("fp32_weights", C.c_int), ("input_noise", C.c_float),
+                ("reserved", C.c_int * 6)]
 
 
 class ms_train_stats(C.Structure):

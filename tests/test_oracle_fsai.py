@@ -124,3 +124,57 @@ def test_init_is_uniform_in_fan_in_bounds():
     for p, fan in zip(parts, [32, 32, 64, 64, 64, 64]):
         assert np.abs(p).max() <= 1 / math.sqrt(fan)
         assert np.abs(p).max() >= 0.8 / math.sqrt(fan)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_features_are_invariant_under_rotations_and_reflections(d):
+    """The network input is written in a frame fixed by the patch: rotating or reflecting the
+    point set leaves the features unchanged, and so it does the exact rows (radial kernel)."""
+    rng = np.random.default_rng(11 + d)
+    n = {1: 40, 2: 300, 3: 600}[d]
+    X = rng.random((n, d))
+    delta = {1: 0.12, 2: 0.25, 3: 0.35}[d]
+    Q, _ = np.linalg.qr(rng.standard_normal((d, d)))
+    Q[:, 0] *= -1 if d > 1 else 1  # an improper orthogonal map for d > 1 (rotation + reflection)
+    Xr = X @ Q.T + 0.3
+    pat = of.pattern(X, delta)
+    assert all(np.array_equal(a, b) for a, b in zip(pat, of.pattern(Xr, delta)))
+    Z, Zr = of.features(X, delta, pat), of.features(Xr, delta, pat)
+    assert np.max(np.abs(Z - Zr)) <= 1e-12
+    w0 = of.exact_weights(X, delta, d, 1, pat)
+    w1 = of.exact_weights(Xr, delta, d, 1, pat)
+    # relative: 1-D patches of random points are ill-conditioned (large alternating rows)
+    assert max(np.max(np.abs(a - b)) / np.max(np.abs(a)) for a, b in zip(w0, w1) if len(a)) <= 1e-8
+    # the frame's defining properties: o_1 on the first axis, o_2's last (d=2) coordinate >= 0
+    full = [i for i, p in enumerate(pat) if len(p) >= d]
+    z = Z[full].reshape(len(full), -1, d)
+    assert np.all(z[:, 0, 0] > 0) and np.allclose(z[:, 0, 1:], 0.0, atol=1e-14)
+    assert np.all(z[:, d - 1, d - 1] >= -1e-14)
+    # lengths are kept
+    for i in full[:20]:
+        off = (X[pat[i]] - X[i]) / delta
+        assert np.allclose(np.linalg.norm(z[full.index(i)][:len(pat[i])], axis=1), np.linalg.norm(off, axis=1))
+
+
+def test_predicted_rows_are_normalised_like_the_exact_rows():
+    """Exact rows satisfy ghat^T K ghat = 1 ((G A G^T)_ii = 1); predicted rows are rescaled to it,
+    and rescaling an exact row leaves it unchanged."""
+    w = inputs.halton_hierarchy(L=3, nu=4.0, wendland=(2, 1), n_gauss=4)
+    X, delta = w.levels[2], w.nu * w.h[2]
+    pat = of.pattern(X, delta)
+    rows = of.scale_free(of.exact_weights(X, delta, 2, 1, pat), delta, 2)
+    Ks = of.patch_matrices(X, delta, 2, 1, pat)
+    for i, r in enumerate(rows):
+        m = len(r)
+        assert abs(r @ Ks[i][:m, :m] @ r - 1.0) <= 1e-9
+    th = of.init_params(32, 3)
+    Z = of.features(X, delta, pat)
+    T, Mk = of.target_matrix(rows, pat)
+    mu, sig = of.standardise(T, Mk)
+    pr = of.predict_rows(th, Z, pat, mu, sig, 32, Ks)
+    for i, r in enumerate(pr):
+        m = len(r)
+        assert abs(r @ Ks[i][:m, :m] @ r - 1.0) <= 1e-12
+    # the rescaling is not a no-op on untrained outputs
+    raw = of.predict_rows(th, Z, pat, mu, sig, 32)
+    assert not all(np.allclose(a, b) for a, b in zip(raw, pr))

@@ -89,7 +89,7 @@ def test_network_forward_matches_oracle():
     for l in range(w.L):
         X, delta, pat, _ = oracle_level_data(w, l)
         Z = of.features(X, delta, pat).astype(np.float32).astype(np.float64)
-        want = of.predict_rows(thb, Z, pat, mu32, sig32, 32)
+        want = of.predict_rows(thb, Z, pat, mu32, sig32, 32, of.patch_matrices(X, delta, 2, 2, pat))
         for i, r in enumerate(want):
             g = got[off[l] + i]
             assert np.all(g[len(r):] == 0)

@@ -250,7 +250,8 @@ __device__ __forceinline__ void run_phase(const SolveArgs& a, Shared& sh, Sel se
 // K V sums, the last group leader sums the group sums and publishes them in
 // a.scal before releasing the other CTAs, and every CTA then copies the sums into
 // sh.out.  Every wait is bounded: past timeout_ns it records MS_ERR_TIMEOUT and
-// returns false; it also returns false once another CTA has recorded a time-out.
+// returns false; a waiting CTA also returns false once it sees that another CTA has
+// recorded a time-out.
 template <int K>
 __device__ bool gsync_reduce(const SolveArgs& a, Shared& sh) {
     const unsigned nb = sh.nb;
@@ -320,11 +321,10 @@ __device__ bool gsync_reduce(const SolveArgs& a, Shared& sh) {
             __nanosleep(32);
         }
     }
-    if (threadIdx.x == 0) {
-        cuda::atomic_ref<int, cuda::thread_scope_device> st(*a.status);
-        if (st.load(cuda::memory_order_relaxed) == MS_ERR_TIMEOUT) ok = 0;
-        sh.ok = ok;  // a separate flag: sh.last may still be read by warps that lag behind
-    }
+    // No status load after the release (it would add an L2 round trip to every barrier):
+    // a CTA that timed out never arrives at the next barrier, whose waiters see the
+    // recorded time-out within 256 polls and leave.
+    if (threadIdx.x == 0) sh.ok = ok;  // a separate flag: sh.last may still be read by lagging warps
     __syncthreads();
     if (!sh.ok) return false;
     if (K > 0) {

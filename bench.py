@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-variants", action="store_true", help="skip the comparison paths")
     p.add_argument("--no-nu8", action="store_true", help="skip the nu=8, phi_{2,2} block")
     p.add_argument("--no-batch", action="store_true", help="skip the multi-RHS batching block")
+    p.add_argument("--no-paper", action="store_true", help="skip the paper-grid (Section 5) block")
+    p.add_argument("--cfg3", action="store_true", help="also run the 3-D configuration (about a minute)")
     return p.parse_args()
 
 
@@ -239,7 +241,7 @@ def run_ours(args):
                                   precond=precond, inter_tol=inter_tol, **extra)
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        hnd = ms.ms_build_hierarchy(2, wl.n_per_level, pts_, wl.h, opts)
+        hnd = ms.ms_build_hierarchy(wl.d, wl.n_per_level, pts_, wl.h, opts)
         if precond == ms.MS_PRECOND_LEARNED:
             ms.ms_precond_params(hnd, 2, params)
         alpha, st = ms.ms_fit(hnd, f_, REL_TOL)
@@ -448,6 +450,50 @@ def run_ours(args):
             for Hi in Hs:
                 Hi.close()
             del fsb, Ab
+
+        # the paper's own experiment (Section 5: grids (2^l+1)^2, phi_{3,1}, nu = 4, Franke data), plain
+        # FP64 as the paper runs it, against Figure 4's A100 times (context: other hardware, tolerance
+        # not reported there)
+        if not args.no_paper:
+            paper_s = {7: 0.974, 8: 1.485, 9: 4.479, 10: 20.111, 11: 92.642}
+            rows = []
+            for Lp in (7, 8, 9, 10, 11):
+                wp = inputs.franke_grid_hierarchy(Lp)
+                pp, fp = torch.from_numpy(wp.points).cuda(), torch.from_numpy(wp.f).cuda()
+                best = None
+                for _ in range(2):
+                    rp = step(ms.MS_PREC_FP64, wl=wp, pts_=pp, f_=fp)
+                    if best is None or rp["total"] < best["total"]:
+                        best = rp
+                rows.append({"levels": Lp, "points": int(wp.N), "step_ms": best["total"],
+                             "fit_ms": best["stats"]["fit_ms"], "build_ms": best["info"]["build_ms"],
+                             "cg_iterations": best["stats"]["cg_iterations"],
+                             "paper_a100_solve_s": paper_s[Lp],
+                             "paper_over_fit": paper_s[Lp] * 1e3 / best["stats"]["fit_ms"]})
+                del pp, fp
+            out["paper_grids_fp64"] = rows
+
+        # the 3-D configuration (uniform random points, 6 levels, 4.68M points): FP64 CSR against
+        # MIXED with the FP32 matrix-free inner mat-vec (levels beyond FP32 switch to FP64 CG)
+        if args.cfg3:
+            w3 = inputs.random3d_hierarchy(L=6)
+            p3, f3 = torch.from_numpy(w3.points).cuda(), torch.from_numpy(w3.f).cuda()
+            o3 = {"workload": "d=3 uniform random, N_j=125*8^(j-1), 6 levels (4,681,125 points), "
+                              "delta_j=3h_j, phi_{3,1}, 30 Gaussians"}
+            for tag, kw in (("fp64_csr", {"prec": ms.MS_PREC_FP64}),
+                            ("mixed_matrix_free", {"prec": ms.MS_PREC_MIXED, "op": ms.MS_OP_MATRIX_FREE}),
+                            ("mixed_csr", {"prec": ms.MS_PREC_MIXED})):
+                extra = {"op": kw["op"]} if "op" in kw else {}
+                try:
+                    r3 = step(kw["prec"], wl=w3, pts_=p3, f_=f3, **extra)
+                    o3[tag] = {"step_ms": r3["total"], "fit_ms": r3["stats"]["fit_ms"],
+                               "build_ms": r3["info"]["build_ms"], "cg_iterations": r3["stats"]["cg_iterations"],
+                               "fp64_fallbacks": r3["stats"]["fp64_fallbacks"],
+                               "rel_residual_max": max(r3["stats"]["rel_residual"])}
+                except ms.MsError as e:
+                    o3[tag] = {"error": str(e)[:160]}
+            out["random3d"] = o3
+            del p3, f3
 
         # end to end through the host-pointer C ABI (H2D of points, f, queries; D2H of alpha, values)
         e2e = []

@@ -120,6 +120,8 @@ typedef struct ms_fit_stats {
     double rel_residual[MS_MAX_LEVELS];  /* final FP64 true relative residual
                                             |beta_l - A_l alpha_l| / |beta_l| per level */
     int32_t precond_fallbacks;           /* levels that fell back from the learned preconditioner */
+    int32_t fp64_fallbacks;              /* MIXED: levels whose inner CG switched to FP64 because an
+                                            outer refinement round did not halve the residual */
     int32_t device_status;               /* ms_status raised on the device (0 = none) */
     double fit_ms;                       /* device time of the solve (CUDA events) */
     double matvec_bytes;                 /* algorithmic bytes moved by the solve kernel

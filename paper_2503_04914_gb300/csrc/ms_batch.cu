@@ -46,7 +46,7 @@ __global__ void k_batch_reset(const SolveArgs* args) {
 
 // Per-hierarchy results gathered into one array (one device-to-host copy).
 struct BatchStat {
-    int status, pcfb;
+    int status, pcfb, f64fb;
     double bytes;
     long long iters[MS_MAXL];
     int refines[MS_MAXL];
@@ -66,7 +66,8 @@ __global__ void k_batch_stats(const SolveArgs* args, BatchStat* out) {
     if (t < kProf) o.prof[t] = a.prof[t];
     if (t == 0) {
         o.status = *a.status;
-        o.pcfb = *a.pcfb;
+        o.pcfb = a.pcfb[0];
+        o.f64fb = a.pcfb[1];
         o.bytes = *a.bytes;
     }
 }
@@ -246,6 +247,7 @@ ms_status ms_fit_batch_impl(ms_hierarchy* const* hs, int nh, const double* const
             s.rel_residual[l] = b.resid[l];
         }
         s.precond_fallbacks = b.pcfb;
+        s.fp64_fallbacks = b.f64fb;
         s.device_status = b.status;
         s.fit_ms = kernel_ms;  // the batch's launches, shared by all its hierarchies
         s.matvec_bytes = b.bytes;

@@ -273,46 +273,74 @@ __device__ __forceinline__ Frame frame_from(const Frame& mine, int src) {
 }
 
 // visit(p, in, mask): called by all 32 lanes for every group of up to 32
-// candidates p of one cell; `in` = p is a neighbour, mask = ballot of `in`.
-// f: y's frame in level j's grid.
+// candidates p; `in` = p is a neighbour, mask = ballot of `in`.  f: y's frame in
+// level j's grid.  The (2R+1)^d cells around f's cell are taken 32 at a time (lane q
+// looks up cell q's point range); their points form one list in cell order (dx
+// fastest, then dy, dz; points in sorted order within a cell), which the warp walks 32
+// candidates per step with every lane busy (cells hold ~16 points, so a step per cell
+// would leave half the lanes idle and repeat the per-cell work in every lane).
 template <typename F>
 __device__ __forceinline__ void warp_neighbours(const HierView& v, const float* __restrict__ W, int j,
                                                 const Frame& f, const Pt& y, int lane, F&& visit) {
     const LevelGrid& g = v.grid[j];
     const float cod = g.cod;
     const double d2 = v.delta[j] * v.delta[j];
-    const int R = v.R;
-    const int rz = v.d >= 3 ? R : 0, ry = v.d >= 2 ? R : 0;
-    for (int dz = -rz; dz <= rz; ++dz) {
-        const int cz = f.c[2] + dz;
-        if (cz < 0 || cz >= g.G[2]) continue;
-        for (int dy = -ry; dy <= ry; ++dy) {
-            const int cy = f.c[1] + dy;
-            if (cy < 0 || cy >= g.G[1]) continue;
-            for (int dx = -R; dx <= R; ++dx) {
-                const int cx = f.c[0] + dx;
-                if (cx < 0 || cx >= g.G[0]) continue;
-                const float o0 = (float)dx * cod - f.fr[0], o1 = (float)dy * cod - f.fr[1],
-                            o2 = (float)dz * cod - f.fr[2];
+    const int R = v.R, side = 2 * R + 1;
+    const int nc = v.d == 1 ? side : (v.d == 2 ? side * side : side * side * side);
+    for (int q0 = 0; q0 < nc; q0 += 32) {
+        const int q = q0 + lane;
+        int start = 0, cnt = 0;
+        float o0 = 0.f, o1 = 0.f, o2 = 0.f;
+        if (q < nc) {
+            const int dx = q % side - R;
+            const int dy = v.d >= 2 ? (q / side) % side - R : 0;
+            const int dz = v.d >= 3 ? q / (side * side) - R : 0;
+            const int cx = f.c[0] + dx, cy = f.c[1] + dy, cz = f.c[2] + dz;
+            if (cx >= 0 && cx < g.G[0] && cy >= 0 && cy < g.G[1] && cz >= 0 && cz < g.G[2]) {
                 const int64_t gid = g.cell_off + morton(v.d, cx, cy, cz);
-                const int32_t s0 = __ldg(v.cell_start + gid), e0 = __ldg(v.cell_start + gid + 1);
-                for (int32_t p0 = s0; p0 < e0; p0 += 32) {
-                    const int32_t p = p0 + lane;
-                    bool in = false;
-                    if (p < e0) {
-                        float t = o0 + __ldg(W + p);
-                        float q = t * t;
-                        if (v.d >= 2) { t = o1 + __ldg(W + v.N + p); q = fmaf(t, t, q); }
-                        if (v.d >= 3) { t = o2 + __ldg(W + 2 * v.N + p); q = fmaf(t, t, q); }
-                        if (q < 1.0f - 1e-4f) {
-                            in = true;
-                        } else if (q <= 1.0f + 1e-4f) {
-                            in = dist2(v, p, y) < d2;
-                        }
-                    }
-                    visit(p, in, __ballot_sync(0xffffffffu, in));
+                start = __ldg(v.cell_start + gid);
+                cnt = __ldg(v.cell_start + gid + 1) - start;
+            }
+            o0 = (float)dx * cod - f.fr[0];
+            o1 = (float)dy * cod - f.fr[1];
+            o2 = (float)dz * cod - f.fr[2];
+        }
+        int incl = cnt;  // inclusive prefix of the cells' point counts over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int b = 0; b < total; b += 32) {
+            const int i = b + lane;
+            // cell of candidate i: the number of cells whose inclusive prefix is <= i
+            // (branch-free binary search over the lanes; every lane takes every step)
+            int cq = 0;
+#pragma unroll
+            for (int st = 16; st >= 1; st >>= 1) {
+                const int pv = __shfl_sync(0xffffffffu, incl, cq + st - 1);
+                if (pv <= i) cq += st;
+            }
+            const int cs = __shfl_sync(0xffffffffu, start, cq);
+            const int ce = __shfl_sync(0xffffffffu, incl, cq) - __shfl_sync(0xffffffffu, cnt, cq);
+            const float c0 = __shfl_sync(0xffffffffu, o0, cq);
+            const float c1 = __shfl_sync(0xffffffffu, o1, cq);
+            const float c2 = __shfl_sync(0xffffffffu, o2, cq);
+            const int32_t p = cs + (i - ce);
+            bool in = false;
+            if (i < total) {
+                float t = c0 + __ldg(W + p);
+                float qq = t * t;
+                if (v.d >= 2) { t = c1 + __ldg(W + v.N + p); qq = fmaf(t, t, qq); }
+                if (v.d >= 3) { t = c2 + __ldg(W + 2 * v.N + p); qq = fmaf(t, t, qq); }
+                if (qq < 1.0f - 1e-4f) {
+                    in = true;
+                } else if (qq <= 1.0f + 1e-4f) {
+                    in = dist2(v, p, y) < d2;
                 }
             }
+            visit(p, in, __ballot_sync(0xffffffffu, in));
         }
     }
 }

@@ -28,6 +28,7 @@
 // phi(r) = (1-r)^e * (c0 + c1 r + c2 r^2 + c3 r^3) for r < 1, else 0.
 struct WendlandPoly {
     int e;
+    int k;          // degree of the polynomial factor
     double c[4];
 };
 
@@ -36,6 +37,7 @@ static inline bool wendland_poly(int wd, int wk, WendlandPoly* w) {
     if (wd < 1 || wd > 3 || wk < 0 || wk > 3) return false;
     const double l = wd / 2 + wk + 1;
     w->e = (int)l + wk;
+    w->k = wk;
     w->c[0] = w->c[1] = w->c[2] = w->c[3] = 0.0;
     switch (wk) {
     case 0: w->c[0] = 1.0; break;
@@ -66,10 +68,10 @@ __device__ __forceinline__ T wendland_eval(const WendlandPoly& w, T r) {
         for (int i = 0; i < w.e; ++i) pw *= s;
     }
     }
-    T p = T(w.c[3]);
-    p = p * r + T(w.c[2]);
-    p = p * r + T(w.c[1]);
-    p = p * r + T(w.c[0]);
+    // Horner from the degree k: the zero leading coefficients cost FP64 issue and leave the
+    // value unchanged (0 * r + 0 = 0 exactly)
+    T p = T(w.c[w.k]);
+    for (int i = w.k - 1; i >= 0; --i) p = p * r + T(w.c[i]);
     return pw * p;
 }
 

@@ -125,7 +125,10 @@ __device__ __forceinline__ float mf_gather(const MFView& v, const MFLevel& g, co
                         const float ez = Wz[j] + oz;
                         r2 = fmaf(ez, ez, r2);
                     }
-                    acc = fmaf(mf_phi<E>(sqrtf(r2), v.c, v.E), x[j], acc);
+                    // r = r2 / sqrt(r2) through the hardware reciprocal square root (FP32 entries
+                    // need no correctly rounded sqrt); r2 = 0 gives r = 0
+                    const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+                    acc = fmaf(mf_phi<E>(r, v.c, v.E), x[j], acc);
                 }
             }
         }

@@ -125,7 +125,7 @@ ms_status ms_ensure_workspace(ms_hierarchy* h, int R) {
         MS_TRY(ms_alloc(h, (void**)&h->refines, sizeof(int) * MS_MAXL));
         MS_TRY(ms_alloc(h, (void**)&h->bytes, sizeof(double)));
         MS_TRY(ms_alloc(h, (void**)&h->prof, sizeof(unsigned long long) * kProf));
-        MS_TRY(ms_alloc(h, (void**)&h->pcfb, sizeof(int)));
+        MS_TRY(ms_alloc(h, (void**)&h->pcfb, sizeof(int) * 2));
     }
     h->ws_rhs = R;
     return MS_OK;
@@ -158,7 +158,7 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
     std::vector<int> ref(MS_MAXL, 0), ref_sum(MS_MAXL, 0);
     std::vector<double> res(kMaxV, 0.0), res_max(MS_MAXL, 0.0);
     double phase[kProf] = {};
-    int fallbacks = 0;
+    int fallbacks = 0, f64_fallbacks = 0;
     int dstat = 0;
     for (int col0 = 0; col0 < nrhs; col0 += Rmax) {
         const int R = std::min(Rmax, nrhs - col0);
@@ -197,15 +197,16 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
         MS_CUDA(cudaMemcpyAsync(&b, h->bytes, sizeof(double), cudaMemcpyDeviceToHost, st));
         unsigned long long pr[kProf];
         MS_CUDA(cudaMemcpyAsync(pr, h->prof, sizeof(pr), cudaMemcpyDeviceToHost, st));
-        int fb = 0;
-        MS_CUDA(cudaMemcpyAsync(&fb, h->pcfb, sizeof(int), cudaMemcpyDeviceToHost, st));
+        int fb[2] = {0, 0};
+        MS_CUDA(cudaMemcpyAsync(fb, h->pcfb, sizeof(fb), cudaMemcpyDeviceToHost, st));
         MS_CUDA(cudaStreamSynchronize(st));
         float ms = 0.f;
         MS_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
         total_ms += ms;
         bytes += b;
         for (int i = 0; i < kProf; ++i) phase[i] += 1e-6 * (double)pr[i];
-        fallbacks += fb;
+        fallbacks += fb[0];
+        f64_fallbacks += fb[1];
         for (int l = 0; l < L; ++l) {
             it_sum[l] += it[l];
             ref_sum[l] += ref[l];
@@ -230,6 +231,7 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
         stats->matvec_bytes = bytes;
         stats->kernel_launches = launches;
         stats->precond_fallbacks = fallbacks;
+        stats->fp64_fallbacks = f64_fallbacks;
         for (int i = 0; i < kProf; ++i) stats->phase_ms[i] = phase[i];
     }
     return result;
@@ -413,7 +415,7 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
     a.part = part; a.gpart = gpart; a.scal = scal; a.bar = bar; a.status = status;
     a.iters = iters; a.refines = refines; a.resid = resid; a.bytes = bytes;
     a.prof = reinterpret_cast<unsigned long long*>(small + 2048);  // [kProf]
-    a.pcfb = reinterpret_cast<int*>(small + 3072);                 // [1]
+    a.pcfb = reinterpret_cast<int*>(small + 3072);                 // [2]
     a.pc = 0;  // the allocation-free fit runs without a preconditioner (checked above)
 
     ms_gather_sorted(f_dev, v64[0], h->perm, h->N, 1, 0, st);

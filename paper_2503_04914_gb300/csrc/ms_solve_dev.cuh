@@ -106,7 +106,7 @@ struct SolveArgs {
     const int32_t* gt_col;
     const float* gt_val;
     float *u32, *u1_32;    // [R][N]
-    int* pcfb;             // levels that fell back to plain CG
+    int* pcfb;             // [2] levels that fell back to plain CG, to FP64 inner CG
 };
 
 // Per-CTA shared state of the solve (identical in every CTA), in dynamic shared memory.
@@ -118,6 +118,9 @@ struct Shared {
     int act[kMaxV], oact[kMaxV], zero[kMaxV], first[kMaxV], pcoff[kMaxV], fresh[kMaxV];
     int it_solve[kMaxV];
     int refines[kMaxV];
+    int f64[kMaxV];         // MIXED: the level's inner CG runs in FP64 (FP32 refinement stalled)
+    int f64n[kMaxV];        // levels switched to FP64
+    double prevres[kMaxV];  // MIXED: true residual of the previous outer round
     int fb[kMaxV];          // preconditioner fall-backs
     long long it_total[kMaxV];
     double vbytes[kMaxV];   // algorithmic bytes moved, per virtual level
@@ -367,6 +370,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
         sh.act[v] = 0;
         sh.zero[v] = 0;
         sh.pcoff[v] = 0;
+        sh.prevres[v] = INFINITY;
         sh.it_solve[v] = 0;
         sh.tol[v] = (tight_all || l == l0) ? a.tol : a.inter_tol;
     }
@@ -424,11 +428,18 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                 if (sh.cta == 0) atomicCAS(a.status, 0, (int)MS_ERR_NOT_CONVERGED);
                 continue;
             }
+            // MIXED: an outer round that did not halve the true residual means the FP32 inner
+            // CG stalls on this level (conditioning beyond FP32): run its inner CG in FP64
+            if (MODE == 1 && !sh.f64[v] && res > 0.5 * sh.prevres[v]) {
+                sh.f64[v] = 1;
+                sh.f64n[v] += 1;
+            }
+            sh.prevres[v] = res;
             my_any = 1;
             sh.refines[v] += 1;
             sh.act[v] = 1;
             sh.first[v] = 1;
-            if (MODE == 0) {
+            if (MODE == 0 || sh.f64[v]) {
                 // recursive-residual target, with margin below the true-residual tolerance
                 sh.target[v] = 0.25 * sh.tol[v] * sh.tol[v] * bb;
             } else {
@@ -458,7 +469,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
 
         if (MODE == 1) {
             // ---- P2: r32 = r / |r|, x32 = 0
-            run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0; }, [&](const Chunk& ch, double*) {
+            run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0 && !sh.f64[v]; }, [&](const Chunk& ch, double*) {
                 const double sc = sh.scale[ch.v];
                 for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
                     a.r32[ch.vb + row] = (float)(a.r[ch.vb + row] * sc);
@@ -466,7 +477,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                 }
             });
             for (int v = tid; v < V; v += kBS)
-                if (sh.act[v]) sh.vbytes[v] += (double)(a.off[v % L + 1] - a.off[v % L]) * 16.0;
+                if (sh.act[v] && !sh.f64[v]) sh.vbytes[v] += (double)(a.off[v % L + 1] - a.off[v % L]) * 16.0;
             prof(sh, kPrfOther);
             if (!gsync(a, sh)) return false;
         }
@@ -477,7 +488,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
             const bool use_pc = MODE == 1 && a.pc;
             if (use_pc) {
                 // G1: u1 = G r  (row pattern: self + preceding neighbours)
-                run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0 && !sh.pcoff[v]; },
+                run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0 && !sh.pcoff[v] && !sh.f64[v]; },
                              [&](const Chunk& ch, double*) {
                                  const float* rv = a.r32 + ch.vb;
                                  for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
@@ -493,7 +504,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                 prof(sh, kPrfOther);
                 if (!gsync(a, sh)) return false;
                 // G2: u = G^T u1
-                run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0 && !sh.pcoff[v]; },
+                run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0 && !sh.pcoff[v] && !sh.f64[v]; },
                              [&](const Chunk& ch, double*) {
                                  const float* u1 = a.u1_32 + ch.vb;
                                  rows_by_subwarp(ch.r0, ch.r1, 2, [&](int64_t row, bool ok, int sl) {
@@ -508,7 +519,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
             }
             // M: w = A u; gamma = r.u, delta = w.u, rho = r.r
             run_phase<3>(a, sh, [&](int v) { return sh.act[v] != 0; }, [&](const Chunk& ch, double* acc) {
-                if (MODE == 0) {
+                if (MODE == 0 || sh.f64[ch.v]) {
                     const int S = a.tprA[ch.l];
                     const double* rv = a.r + ch.vb;
                     rows_by_subwarp(ch.r0, ch.r1, S, [&](int64_t row, bool ok, int sl) {
@@ -566,9 +577,10 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                     if (!sh.act[v]) continue;
                     const int l = v % L;
                     const double gam = sh.out[0][v], del = sh.out[1][v], rho = sh.out[2][v];
-                    const bool lpc = use_pc && !sh.pcoff[v];
+                    const bool dbl = MODE == 0 || sh.f64[v];
+                    const bool lpc = use_pc && !sh.pcoff[v] && !dbl;
                     const double n = (double)(a.off[l + 1] - a.off[l]);
-                    sh.vbytes[v] += (double)a.nnzA[l] * (MODE == 0 ? 12.0 : 8.0) + n * (MODE == 0 ? 32.0 : (lpc ? 24.0 : 20.0));
+                    sh.vbytes[v] += (double)a.nnzA[l] * (dbl ? 12.0 : 8.0) + n * (dbl ? 32.0 : (lpc ? 24.0 : 20.0));
                     if (lpc) sh.vbytes[v] += n * (2.0 * kPcOut * 12.0 + 16.0);
                     if (!isfinite(gam) || !isfinite(del) || !isfinite(rho)) {
                         sh.act[v] = 0;
@@ -598,7 +610,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                         al = den > 0.0 ? gam / den : -1.0;
                     }
                     if (!(al > 0.0)) {
-                        if (MODE == 1 && !sh.first[v]) {
+                        if (MODE == 1 && !sh.first[v]) {  // (FP32, or an FP64 fallback level)
                             // lost curvature in the FP32 recurrence (cancellation on an ill-conditioned
                             // level): end this inner solve; the FP64 true residual restarts it
                             sh.act[v] = 0;
@@ -623,7 +635,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                     sh.gam[v] = gam;
                     sh.it_solve[v] += 1;
                     sh.it_total[v] += 1;
-                    sh.vbytes[v] += n * (MODE == 0 ? 72.0 : 36.0);
+                    sh.vbytes[v] += n * (dbl ? 72.0 : 36.0);
                     my_go = 1;
                 }
             }
@@ -637,7 +649,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                 // hold anything, and 0 * NaN would poison the recurrence)
                 const bool fr = sh.fresh[ch.v] != 0;
                 const int64_t vb = ch.vb;
-                if (MODE == 0) {
+                if (MODE == 0 || sh.f64[ch.v]) {
                     for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
                         const int64_t i = vb + row;
                         const double ri = a.r[i];
@@ -669,14 +681,14 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
 
         if (MODE == 1) {
             // ---- P3: x += |r| d  (FP64)
-            run_phase<0>(a, sh, [&](int v) { return sh.oact[v] != 0 && sh.scale[v] > 0.0; },
+            run_phase<0>(a, sh, [&](int v) { return sh.oact[v] != 0 && sh.scale[v] > 0.0 && !sh.f64[v]; },
                          [&](const Chunk& ch, double*) {
                              const double inv = 1.0 / sh.scale[ch.v];
                              for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS)
                                  a.x[ch.vb + row] += (double)a.x32[ch.vb + row] * inv;
                          });
             for (int v = tid; v < V; v += kBS)
-                if (sh.oact[v]) sh.vbytes[v] += (double)(a.off[v % L + 1] - a.off[v % L]) * 20.0;
+                if (sh.oact[v] && !sh.f64[v]) sh.vbytes[v] += (double)(a.off[v % L + 1] - a.off[v % L]) * 20.0;
             prof(sh, kPrfOther);
             if (!gsync(a, sh)) return false;
         }
@@ -698,6 +710,8 @@ __device__ __forceinline__ void fit_body(const SolveArgs& a, Shared& sh) {
         sh.it_total[v] = 0;
         sh.refines[v] = 0;
         sh.fb[v] = 0;
+        sh.f64[v] = 0;
+        sh.f64n[v] = 0;
         sh.vbytes[v] = 0.0;
         sh.scale[v] = 0.0;
     }
@@ -779,14 +793,16 @@ __device__ __forceinline__ void fit_body(const SolveArgs& a, Shared& sh) {
             a.refines[l] = rf;
         }
         double b = sh.bytes;
-        int fb = 0;
+        int fb = 0, f64n = 0;
         for (int v = 0; v < a.V; ++v) {
             b += sh.vbytes[v];
             fb += sh.fb[v];
+            f64n += sh.f64n[v];
         }
         a.bytes[0] = b;
         for (int i = 0; i < kProf; ++i) a.prof[i] = sh.pt[i];
         a.pcfb[0] = fb;
+        a.pcfb[1] = f64n;
     }
 }
 

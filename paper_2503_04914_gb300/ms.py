@@ -46,7 +46,8 @@ class ms_opts(C.Structure):
 class ms_fit_stats(C.Structure):
     _fields_ = [("L", C.c_int32), ("sweeps", C.c_int32), ("cg_iterations", C.c_int64 * MS_MAX_LEVELS),
                 ("refinements", C.c_int32 * MS_MAX_LEVELS), ("rel_residual", C.c_double * MS_MAX_LEVELS),
-                ("precond_fallbacks", C.c_int32), ("device_status", C.c_int32), ("fit_ms", C.c_double),
+                ("precond_fallbacks", C.c_int32), ("fp64_fallbacks", C.c_int32), ("device_status", C.c_int32),
+                ("fit_ms", C.c_double),
                 ("matvec_bytes", C.c_double), ("kernel_launches", C.c_int64), ("phase_ms", C.c_double * 8)]
 
     PHASES = ("resid64", "matvec", "update", "barrier", "lower", "other", "scalar")
@@ -55,7 +56,8 @@ class ms_fit_stats(C.Structure):
         L = self.L
         return {"L": L, "sweeps": self.sweeps, "cg_iterations": list(self.cg_iterations[:L]),
                 "refinements": list(self.refinements[:L]), "rel_residual": list(self.rel_residual[:L]),
-                "precond_fallbacks": self.precond_fallbacks, "device_status": self.device_status,
+                "precond_fallbacks": self.precond_fallbacks, "fp64_fallbacks": self.fp64_fallbacks,
+                "device_status": self.device_status,
                 "fit_ms": self.fit_ms, "matvec_bytes": self.matvec_bytes,
                 "kernel_launches": self.kernel_launches,
                 "phase_ms": {n: self.phase_ms[i] for i, n in enumerate(self.PHASES)}}

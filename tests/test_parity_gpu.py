@@ -319,3 +319,29 @@ def test_full_size_halton8_sampled_rows(prec):
     s = H.evaluate(alpha, pts)
     assert np.max(np.abs(s - w.f_fun(pts))) <= 1e-8 * fmax
     H.close()
+
+
+def test_mixed_falls_back_to_fp64_on_a_level_beyond_fp32():
+    """Pairs of points 1e-3 h apart make the finest level's A_l too ill-conditioned for an FP32
+    inner CG (its refinement rounds stop reducing the FP64 residual); MIXED then runs that level's
+    inner CG in FP64 and still certifies rel_tol, matching the oracle's approximant."""
+    sizes = [50, 400, 3000]
+    allp = inputs.scrambled_halton(max(sizes), 2, 91)
+    levels = [np.ascontiguousarray(allp[:n]) for n in sizes]
+    h = np.array([n ** -0.5 for n in sizes])
+    idx = np.arange(0, 3000, 100)                      # 30 points get a near-twin
+    ang = 2 * np.pi * inputs.uniform01(92, len(idx))
+    twins = levels[2][idx] + 1e-3 * h[2] * np.stack([np.cos(ang), np.sin(ang)], axis=1)
+    levels[2] = np.ascontiguousarray(np.concatenate([levels[2], np.clip(twins, 0.0, 1.0)]))
+    g = inputs.GaussianMixture(6, 2, 93, sine=True)
+    w = inputs.Workload("twins", 2, levels, h, 4.0, 2, 1, g(np.concatenate(levels)), g)
+    H = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED)
+    a, st = H.fit(w.f, rel_tol=1e-11)
+    assert st["fp64_fallbacks"] >= 1, st
+    assert max(st["rel_residual"]) <= 1e-11
+    ref = oracle_fit(w)
+    Q = inputs.query_grid(48, 2)
+    s_gpu = H.evaluate(a, Q)
+    s_ref = om.evaluate(w.levels, ref, w.h, w.nu, 2, 1, Q)
+    assert rel(s_gpu, s_ref) <= 1e-6
+    H.close()

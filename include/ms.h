@@ -368,7 +368,9 @@ uint64_t ms_launch_count(void);
 /* Message of the last failing call on this thread ("" if none). */
 const char* ms_last_error(void);
 
-/* Free the handle and all device memory it owns; NULL is a no-op. */
+/* Free the handle and all device memory it owns; NULL is a no-op.  Waits for the device
+ * to finish pending work first.  The library draws device memory from one memory pool per
+ * device that keeps freed memory for reuse by later handles (released at process exit). */
 void ms_destroy(ms_hierarchy* h);
 
 #ifdef __cplusplus

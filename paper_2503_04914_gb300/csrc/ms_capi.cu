@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "ms_internal.cuh"
@@ -29,17 +30,9 @@ inline unsigned nblk(int64_t n, int bs) { return (unsigned)std::max<int64_t>(1, 
 // Device buffer freed at scope exit (host staging of the plain entry points).
 struct DevBuf {
     void* p = nullptr;
-    ~DevBuf() { if (p) cudaFree(p); }
+    ~DevBuf() { if (p) ms_pool_free(p); }
 };
-ms_status dev_alloc(DevBuf& b, size_t bytes) {
-    cudaError_t e = cudaMalloc(&b.p, std::max<size_t>(bytes, 16));
-    if (e != cudaSuccess) {
-        b.p = nullptr;
-        ms_set_error(MS_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
-        return MS_ERR_OOM;
-    }
-    return MS_OK;
-}
+ms_status dev_alloc(DevBuf& b, size_t bytes) { return ms_pool_alloc(&b.p, bytes); }
 
 ms_status check_finite(const double* a_dev, int64_t n, cudaStream_t st, const char* what) {
     if (n == 0) return MS_OK;
@@ -149,17 +142,69 @@ ms_status ms_cuda_error(cudaError_t e, const char* what, const char* file, int l
     return e == cudaErrorMemoryAllocation ? MS_ERR_OOM : MS_ERR_CUDA;
 }
 
-ms_status ms_alloc(ms_hierarchy* h, void** p, size_t bytes) {
-    if (h->nallocs >= (int)(sizeof(h->allocs) / sizeof(h->allocs[0]))) {
-        ms_set_error(MS_ERR_STATE, "too many device allocations in one handle");
+// Device memory of the library comes from one memory pool per device that keeps what
+// is freed (release threshold: never), so building and destroying handles repeatedly
+// reuses memory instead of mapping and unmapping it on every cudaMalloc/cudaFree.
+// Allocation and release are ordered on a private stream; an allocation is complete
+// (usable from any stream) when ms_pool_alloc returns.  ms_pool_free must only be given
+// memory that no pending work uses (callers synchronise first).
+namespace {
+std::mutex g_pool_mu;
+struct DevPool {
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t stream = nullptr;
+};
+DevPool g_pools[256];
+}  // namespace
+
+static ms_status device_pool(DevPool** out) {
+    int dev = 0;
+    MS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) {
+        ms_set_error(MS_ERR_STATE, "device ordinal %d out of range", dev);
         return MS_ERR_STATE;
     }
-    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    DevPool& dp = g_pools[dev];
+    if (!dp.pool) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        MS_CUDA(cudaMemPoolCreate(&dp.pool, &props));
+        uint64_t keep = UINT64_MAX;
+        MS_CUDA(cudaMemPoolSetAttribute(dp.pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        MS_CUDA(cudaStreamCreateWithFlags(&dp.stream, cudaStreamNonBlocking));
+    }
+    *out = &dp;
+    return MS_OK;
+}
+
+ms_status ms_pool_alloc(void** p, size_t bytes) {
+    DevPool* dp = nullptr;
+    MS_TRY(device_pool(&dp));
+    cudaError_t e = cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 16), dp->pool, dp->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(dp->stream);
     if (e != cudaSuccess) {
         *p = nullptr;
         ms_set_error(MS_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
         return MS_ERR_OOM;
     }
+    return MS_OK;
+}
+
+void ms_pool_free(void* p) {
+    DevPool* dp = nullptr;
+    if (!p || device_pool(&dp) != MS_OK) return;
+    cudaFreeAsync(p, dp->stream);
+}
+
+ms_status ms_alloc(ms_hierarchy* h, void** p, size_t bytes) {
+    if (h->nallocs >= (int)(sizeof(h->allocs) / sizeof(h->allocs[0]))) {
+        ms_set_error(MS_ERR_STATE, "too many device allocations in one handle");
+        return MS_ERR_STATE;
+    }
+    MS_TRY(ms_pool_alloc(p, bytes));
     h->alloc_bytes[h->nallocs] = bytes;
     h->allocs[h->nallocs++] = *p;
     h->device_bytes += (int64_t)bytes;
@@ -170,7 +215,8 @@ ms_status ms_realloc(ms_hierarchy* h, void** p, size_t bytes) {
     if (*p) {
         for (int i = 0; i < h->nallocs; ++i) {
             if (h->allocs[i] != *p) continue;
-            cudaFree(*p);
+            cudaDeviceSynchronize();  // no pending work may still use the old buffer
+            ms_pool_free(*p);
             h->device_bytes -= (int64_t)h->alloc_bytes[i];
             h->allocs[i] = h->allocs[h->nallocs - 1];
             h->alloc_bytes[i] = h->alloc_bytes[h->nallocs - 1];
@@ -412,7 +458,8 @@ ms_status ms_hierarchy_info(const ms_hierarchy* h, ms_info* info) {
 
 void ms_destroy(ms_hierarchy* h) {
     if (!h) return;
-    for (int i = 0; i < h->nallocs; ++i) cudaFree(h->allocs[i]);
+    cudaDeviceSynchronize();  // the handle's memory returns to the pool: no work may still use it
+    for (int i = 0; i < h->nallocs; ++i) ms_pool_free(h->allocs[i]);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     delete h;

@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 
 #include "ms_internal.cuh"
+#include "ms_scan.cuh"
 
 namespace {
 
@@ -30,13 +31,28 @@ constexpr int kTB = 64;  // training samples per block
 
 inline unsigned nblk(int64_t n, int bs) { return (unsigned)std::max<int64_t>(1, (n + bs - 1) / bs); }
 
-__device__ __forceinline__ double dist_rn(const HierView& v, int64_t i, int64_t j) {
+__device__ __forceinline__ double dist2_rn(const HierView& v, int64_t i, int64_t j) {
     double s = 0.0;
     for (int a = 0; a < v.d; ++a) {
         const double t = __dsub_rn(v.X[a * v.N + i], v.X[a * v.N + j]);
         s = __dadd_rn(s, __dmul_rn(t, t));
     }
-    return sqrt(s);
+    return s;
+}
+
+__device__ __forceinline__ double dist_rn(const HierView& v, int64_t i, int64_t j) { return sqrt(dist2_rn(v, i, j)); }
+
+// (sqrt(d2a), pa) < (sqrt(d2b), pb) lexicographically, where the square roots are the
+// correctly rounded FP64 ones.  Non-negative doubles order like their bit patterns, and
+// squared distances more than 64 units in the last place apart order their roots the
+// same way (sqrt halves relative gaps), so the decision is an integer compare and the
+// (FP64-pipe) roots are taken only for near-ties.
+__device__ __forceinline__ bool key_less(double d2a, int32_t pa, double d2b, int32_t pb) {
+    const long long gap = __double_as_longlong(d2b) - __double_as_longlong(d2a);
+    if (gap > 64) return true;
+    if (gap < -64) return false;
+    const double da = sqrt(d2a), db = sqrt(d2b);
+    return da < db || (da == db && pa < pb);
 }
 
 // ---------------------------------------------------------------- pattern
@@ -52,10 +68,11 @@ __global__ void k_pc_pattern(HierView v, const int64_t* Arp, const int32_t* Acol
         const int32_t c = Acol[k];
         const int32_t pc = perm[c];
         if (pc >= ps) continue;
-        const double d = dist_rn(v, c, s);
-        // insertion into the sorted list keyed by (distance, input index)
+        const double d = dist2_rn(v, c, s);
+        // insertion into the sorted list keyed by (distance, input index); bd holds squared
+        // distances, compared through key_less as their correctly rounded roots
         int pos = cnt < kPcK ? cnt : kPcK;
-        while (pos > 0 && (bd[pos - 1] > d || (bd[pos - 1] == d && bp[pos - 1] > pc))) {
+        while (pos > 0 && key_less(d, pc, bd[pos - 1], bp[pos - 1])) {
             if (pos < kPcK) { bd[pos] = bd[pos - 1]; bp[pos] = bp[pos - 1]; bc[pos] = bc[pos - 1]; }
             --pos;
         }
@@ -351,19 +368,23 @@ __global__ void k_pc_infer(HierView v, const int32_t* nbr, const float* theta, i
     // (G A G^T)_ii = ghat^T K ghat, K = phi(|z_a - z_b|) on the patch (self at the origin);
     // the exact row makes it 1: rescale the predicted row to that.
     {
+        // K is symmetric with K_aa = phi(0) = c_0: the diagonal, then twice each pair a < b
         const int d = v.d;
+        const float phi0 = (float)v.w.c[0];
         float q = 0.f;
         for (int a = 0; a <= cnt; ++a) {
+            q = fmaf(g[a] * g[a], phi0, q);
             float t = 0.f;
-            for (int b = 0; b <= cnt; ++b) {
+            for (int b = a + 1; b <= cnt; ++b) {
                 float r2 = 0.f;
                 for (int ax = 0; ax < d; ++ax) {
-                    const float u = (a > 0 ? z[(a - 1) * d + ax] : 0.f) - (b > 0 ? z[(b - 1) * d + ax] : 0.f);
+                    const float u = (a > 0 ? z[(a - 1) * d + ax] : 0.f) - z[(b - 1) * d + ax];
                     r2 = fmaf(u, u, r2);
                 }
-                t = fmaf(wendland_eval<float>(v.w, sqrtf(r2)), g[b], t);
+                // FP32 entries need no correctly rounded sqrt: r = r2 / sqrt(r2)
+                t = fmaf(wendland_eval<float>(v.w, r2 * rsqrtf(fmaxf(r2, 1e-30f))), g[b], t);
             }
-            q = fmaf(g[a], t, q);
+            q = fmaf(2.f * g[a], t, q);
         }
         if (q > 0.f) {
             const float sc = rsqrtf(q);
@@ -581,11 +602,34 @@ __global__ void k_gt_fill(const int32_t* gcol, const float* gval, int64_t N, con
         val[pos] = gval[k * N + s];
     }
 }
-// deterministic order inside each row of G^T: by source row
+// deterministic order inside each row of G^T: by source row (insertion sort in registers
+// for rows of up to 32 entries, which is nearly all of them; in place beyond)
 __global__ void k_gt_sort(const int64_t* rp, int32_t* col, float* val, int64_t N) {
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= N) return;
     const int64_t s = rp[c], e = rp[c + 1];
+    const int n = (int)(e - s);
+    if (n <= 32) {
+        int32_t kc[32];
+        float kv[32];
+        for (int i = 0; i < n; ++i) {
+            const int32_t ci = col[s + i];
+            const float vi = val[s + i];
+            int j = i - 1;
+            while (j >= 0 && kc[j] > ci) {
+                kc[j + 1] = kc[j];
+                kv[j + 1] = kv[j];
+                --j;
+            }
+            kc[j + 1] = ci;
+            kv[j + 1] = vi;
+        }
+        for (int i = 0; i < n; ++i) {
+            col[s + i] = kc[i];
+            val[s + i] = kv[i];
+        }
+        return;
+    }
     for (int64_t i = s + 1; i < e; ++i) {
         const int32_t kc = col[i];
         const float kv = val[i];
@@ -600,32 +644,6 @@ __global__ void k_gt_sort(const int64_t* rp, int32_t* col, float* val, int64_t N
     }
 }
 
-__global__ void k_scan_rows(const int32_t* cnt, int64_t N, int64_t* rp) {
-    // single-block exclusive scan (the in-degrees are small; N up to a few million)
-    __shared__ int64_t part[1024];
-    const int t = threadIdx.x, nt = blockDim.x;
-    const int64_t per = (N + nt - 1) / nt;
-    const int64_t b = t * per, e = std::min<int64_t>(N, b + per);
-    int64_t s = 0;
-    for (int64_t i = b; i < e; ++i) s += cnt[i];
-    part[t] = s;
-    __syncthreads();
-    if (t == 0) {
-        int64_t acc = 0;
-        for (int i = 0; i < nt; ++i) {
-            const int64_t v = part[i];
-            part[i] = acc;
-            acc += v;
-        }
-        rp[N] = acc;
-    }
-    __syncthreads();
-    int64_t acc = part[t];
-    for (int64_t i = b; i < e; ++i) {
-        rp[i] = acc;
-        acc += cnt[i];
-    }
-}
 
 uint64_t sm64(uint64_t seed, uint64_t i) {
     uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
@@ -779,15 +797,18 @@ ms_status ms_pc_build(ms_hierarchy* h, int kind, cudaStream_t st) {
     MS_CUDA(cudaGetLastError());
     // transpose (in-pattern) for z = G^T u
     int32_t* cnt = nullptr;
+    int64_t* tiles = nullptr;
     MS_CUDA(cudaMallocAsync((void**)&cnt, sizeof(int32_t) * (N + 1), st));
+    MS_CUDA(cudaMallocAsync((void**)&tiles, sizeof(int64_t) * ((N + kScanTile - 1) / kScanTile + 2), st));
     MS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (N + 1), st));
     k_gt_count<<<nblk(N, 256), 256, 0, st>>>(pc.gcol, N, cnt);
-    k_scan_rows<<<1, 1024, 0, st>>>(cnt, N, pc.gt_rp);
+    exclusive_scan<int32_t, int64_t>(cnt, N, pc.gt_rp, tiles, st);
     MS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (N + 1), st));
     k_gt_fill<<<nblk(N, 256), 256, 0, st>>>(pc.gcol, pc.gval, N, pc.gt_rp, cnt, pc.gt_col, pc.gt_val);
     k_gt_sort<<<nblk(N, 256), 256, 0, st>>>(pc.gt_rp, pc.gt_col, pc.gt_val, N);
-    ms_count_launch(4);
+    ms_count_launch(3);
     MS_CUDA(cudaFreeAsync(cnt, st));
+    MS_CUDA(cudaFreeAsync(tiles, st));
     MS_CUDA(cudaGetLastError());
     pc.built_kind = kind;
     return MS_OK;

@@ -248,64 +248,12 @@ __device__ __forceinline__ void run_phase(const SolveArgs& a, Shared& sh, Sel se
     }
 }
 
-// Grid barrier with two-level arrival; with K > 0 it also reduces the per-CTA
-// partials: the last CTA of each group of kGroup sums its group's partials of all
-// K V sums, the last group leader sums the group sums and publishes them in
-// a.scal before releasing the other CTAs, and every CTA then copies the sums into
-// sh.out.  Every wait is bounded: past timeout_ns it records MS_ERR_TIMEOUT and
-// returns false; a waiting CTA also returns false once it sees that another CTA has
-// recorded a time-out.
+// Waiting side of a grid barrier (thread 0 spins on the generation word, bounded),
+// then, with K > 0, every CTA copies the published sums into sh.out.
 template <int K>
-__device__ bool gsync_reduce(const SolveArgs& a, Shared& sh) {
-    const unsigned nb = sh.nb;
-    const unsigned grp = (unsigned)sh.cta / kGroup;
-    const unsigned ngrp = (nb + kGroup - 1) / kGroup;
-    const int npair = K * a.V;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(a.bar[1]);
-        cuda::atomic_ref<unsigned, cuda::thread_scope_device> gc(a.bar[2 + grp]);
-        sh.mine = g.load(cuda::memory_order_relaxed);
-        const unsigned gsize = min((unsigned)kGroup, nb - grp * kGroup);
-        sh.glast = gc.fetch_add(1u, cuda::memory_order_acq_rel) == gsize - 1;
-        if (sh.glast) gc.store(0u, cuda::memory_order_relaxed);
-        sh.last = 0;
-    }
-    __syncthreads();
-    if (sh.glast) {
-        if (K > 0) {  // group sums, in CTA order
-            const unsigned b0 = grp * kGroup, b1 = min(nb, b0 + kGroup);
-            for (int i = threadIdx.x; i < npair; i += kBS) {
-                const double* src = a.part + (size_t)i * nb;
-                double s = 0.0;
-                for (unsigned b = b0; b < b1; ++b) s += __ldcg(src + b);
-                __stcg(a.gpart + (size_t)grp * kAcc * a.V + i, s);
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(a.bar[0]);
-            sh.last = c.fetch_add(1u, cuda::memory_order_acq_rel) == ngrp - 1;
-        }
-        __syncthreads();
-    }
+__device__ __forceinline__ bool gsync_finish(const SolveArgs& a, Shared& sh) {
     int ok = 1;
-    if (sh.last) {
-        if (K > 0) {  // grid sums, in group order
-            for (int i = threadIdx.x; i < npair; i += kBS) {
-                double s = 0.0;
-                for (unsigned gi = 0; gi < ngrp; ++gi) s += __ldcg(a.gpart + (size_t)gi * kAcc * a.V + i);
-                __stcg(a.scal + i, s);
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(a.bar[1]);
-            cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(a.bar[0]);
-            c.store(0u, cuda::memory_order_relaxed);
-            g.store(sh.mine + 1u, cuda::memory_order_release);
-        }
-    } else if (threadIdx.x == 0) {
+    if (!sh.last && threadIdx.x == 0) {
         cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(a.bar[1]);
         cuda::atomic_ref<int, cuda::thread_scope_device> st(*a.status);
         const unsigned long long t0 = ms_globaltimer();
@@ -331,6 +279,7 @@ __device__ bool gsync_reduce(const SolveArgs& a, Shared& sh) {
     __syncthreads();
     if (!sh.ok) return false;
     if (K > 0) {
+        const int npair = K * a.V;
         for (int i = threadIdx.x; i < npair; i += kBS) {
             const int k = i / a.V, v = i % a.V;
             sh.out[k][v] = __ldcg(a.scal + i);
@@ -339,6 +288,110 @@ __device__ bool gsync_reduce(const SolveArgs& a, Shared& sh) {
     }
     prof(sh, kPrfBarrier);
     return true;
+}
+
+// Release by the last CTA to arrive (thread 0): reset the counter, advance the generation.
+__device__ __forceinline__ void gsync_release(const SolveArgs& a, Shared& sh) {
+    if (threadIdx.x == 0) {
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(a.bar[1]);
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(a.bar[0]);
+        c.store(0u, cuda::memory_order_relaxed);
+        g.store(sh.mine + 1u, cuda::memory_order_release);
+    }
+}
+
+// Grid barrier; with K > 0 it also reduces the per-CTA partials of the K V sums,
+// publishes them in a.scal before releasing the other CTAs, and every CTA then
+// copies the sums into sh.out.  Arrival is one counter for all CTAs (measured on
+// GB300 with 304 CTAs: 2.3 us per barrier against 4.9 us for a two-level arrival,
+// whose extra atomic costs a round trip).  With few partials (K V nb <= 16384
+// values) the last CTA to arrive sums them itself over a fixed segmentation of the
+// CTAs; more partials (wide multi-RHS launches) take a two-level arrival in which
+// the last CTA of each group of kGroup sums its group and the last group leader sums
+// the groups.  Both orders are fixed, so every run gives the same sums.  Every wait
+// is bounded: past timeout_ns it records MS_ERR_TIMEOUT and returns false; a waiting
+// CTA also returns false once it sees that another CTA has recorded a time-out.
+template <int K>
+__device__ bool gsync_reduce(const SolveArgs& a, Shared& sh) {
+    const unsigned nb = sh.nb;
+    const int npair = K * a.V;
+    if ((long)npair * nb <= 16384) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(a.bar[1]);
+            cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(a.bar[0]);
+            sh.mine = g.load(cuda::memory_order_relaxed);
+            sh.last = c.fetch_add(1u, cuda::memory_order_acq_rel) == nb - 1;
+        }
+        __syncthreads();
+        if (sh.last) {
+            if (K > 0) {
+                // S segments of the CTAs per sum, one thread each, then the S segment sums
+                // in order (staged in sh.red, which no phase uses across a barrier)
+                const int S = max(1, min(kBS / max(npair, 1), (int)nb));
+                const int t = threadIdx.x;
+                if (t < npair * S) {
+                    const int i = t / S, sg = t % S;
+                    const unsigned b0 = (unsigned)((long)sg * nb / S), b1 = (unsigned)((long)(sg + 1) * nb / S);
+                    const double* src = a.part + (size_t)i * nb;
+                    double acc = 0.0;
+                    for (unsigned b = b0; b < b1; ++b) acc += __ldcg(src + b);
+                    sh.red[0][t] = acc;
+                }
+                __syncthreads();
+                for (int i = t; i < npair; i += kBS) {
+                    double acc = 0.0;
+                    for (int sg = 0; sg < S; ++sg) acc += sh.red[0][i * S + sg];
+                    __stcg(a.scal + i, acc);
+                }
+                __syncthreads();
+            }
+            gsync_release(a, sh);
+        }
+        return gsync_finish<K>(a, sh);
+    }
+    const unsigned grp = (unsigned)sh.cta / kGroup;
+    const unsigned ngrp = (nb + kGroup - 1) / kGroup;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(a.bar[1]);
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> gc(a.bar[2 + grp]);
+        sh.mine = g.load(cuda::memory_order_relaxed);
+        const unsigned gsize = min((unsigned)kGroup, nb - grp * kGroup);
+        sh.glast = gc.fetch_add(1u, cuda::memory_order_acq_rel) == gsize - 1;
+        if (sh.glast) gc.store(0u, cuda::memory_order_relaxed);
+        sh.last = 0;
+    }
+    __syncthreads();
+    if (sh.glast) {
+        if (K > 0) {  // group sums, in CTA order
+            const unsigned b0 = grp * kGroup, b1 = min(nb, b0 + kGroup);
+            for (int i = threadIdx.x; i < npair; i += kBS) {
+                const double* src = a.part + (size_t)i * nb;
+                double acc = 0.0;
+                for (unsigned b = b0; b < b1; ++b) acc += __ldcg(src + b);
+                __stcg(a.gpart + (size_t)grp * kAcc * a.V + i, acc);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(a.bar[0]);
+            sh.last = c.fetch_add(1u, cuda::memory_order_acq_rel) == ngrp - 1;
+        }
+        __syncthreads();
+    }
+    if (sh.last) {
+        if (K > 0) {  // grid sums, in group order
+            for (int i = threadIdx.x; i < npair; i += kBS) {
+                double acc = 0.0;
+                for (unsigned gi = 0; gi < ngrp; ++gi) acc += __ldcg(a.gpart + (size_t)gi * kAcc * a.V + i);
+                __stcg(a.scal + i, acc);
+            }
+        }
+        __syncthreads();
+        gsync_release(a, sh);
+    }
+    return gsync_finish<K>(a, sh);
 }
 
 __device__ __forceinline__ bool gsync(const SolveArgs& a, Shared& sh) { return gsync_reduce<0>(a, sh); }
@@ -490,15 +543,21 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                 // G1: u1 = G r  (row pattern: self + preceding neighbours)
                 run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0 && !sh.pcoff[v] && !sh.f64[v]; },
                              [&](const Chunk& ch, double*) {
+                                 // two lanes per row (slots k = half, half + 2, ...), all threads busy
                                  const float* rv = a.r32 + ch.vb;
-                                 for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
+                                 const int half = tid & 1;
+                                 for (int64_t base = ch.r0; base < ch.r1; base += kBS / 2) {
+                                     const int64_t row = base + (tid >> 1);
                                      float acc = 0.f;
+                                     if (row < ch.r1) {
 #pragma unroll
-                                     for (int k = 0; k < kPcOut; ++k) {
-                                         const int32_t c = __ldg(a.gcol + k * a.N + row);
-                                         if (c >= 0) acc = fmaf(__ldg(a.gval + k * a.N + row), rv[c], acc);
+                                         for (int k = half; k < kPcOut; k += 2) {
+                                             const int32_t c = __ldg(a.gcol + k * a.N + row);
+                                             if (c >= 0) acc = fmaf(__ldg(a.gval + k * a.N + row), rv[c], acc);
+                                         }
                                      }
-                                     a.u1_32[ch.vb + row] = acc;
+                                     acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                                     if (row < ch.r1 && half == 0) a.u1_32[ch.vb + row] = acc;
                                  }
                              });
                 prof(sh, kPrfOther);
@@ -660,19 +719,38 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                         a.x[i] += al * pi;
                         a.r[i] = ri - al * si;
                     }
-                } else {
-                    const float af = (float)al, bf = (float)be;
-                    const float* uin = (use_pc && !sh.pcoff[ch.v]) ? a.u32 : a.r32;
-                    for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
+                    return;
+                }
+                const float af = (float)al, bf = (float)be;
+                if (use_pc && !sh.pcoff[ch.v]) {
+                    // u = M r is its own vector, so the (p, x) and (s, r) halves of a row are
+                    // independent: threads [0, kBS/2) update p and x, threads [kBS/2, kBS)
+                    // update s and r, and all threads are busy on a chunk of kBS/2 rows
+                    const bool px = tid < kBS / 2;
+                    const int t2 = px ? tid : tid - kBS / 2;
+                    for (int64_t row = ch.r0 + t2; row < ch.r1; row += kBS / 2) {
                         const int64_t i = vb + row;
-                        const float ri = a.r32[i];
-                        const float pi = fr ? uin[i] : fmaf(bf, a.p32[i], uin[i]);
-                        const float si = fr ? a.q32[i] : fmaf(bf, a.s32[i], a.q32[i]);
-                        a.p32[i] = pi;
-                        a.s32[i] = si;
-                        a.x32[i] = fmaf(af, pi, a.x32[i]);
-                        a.r32[i] = fmaf(-af, si, ri);
+                        if (px) {
+                            const float pi = fr ? a.u32[i] : fmaf(bf, a.p32[i], a.u32[i]);
+                            a.p32[i] = pi;
+                            a.x32[i] = fmaf(af, pi, a.x32[i]);
+                        } else {
+                            const float si = fr ? a.q32[i] : fmaf(bf, a.s32[i], a.q32[i]);
+                            a.s32[i] = si;
+                            a.r32[i] = fmaf(-af, si, a.r32[i]);
+                        }
                     }
+                    return;
+                }
+                for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
+                    const int64_t i = vb + row;
+                    const float ri = a.r32[i];
+                    const float pi = fr ? ri : fmaf(bf, a.p32[i], ri);
+                    const float si = fr ? a.q32[i] : fmaf(bf, a.s32[i], a.q32[i]);
+                    a.p32[i] = pi;
+                    a.s32[i] = si;
+                    a.x32[i] = fmaf(af, pi, a.x32[i]);
+                    a.r32[i] = fmaf(-af, si, ri);
                 }
             });
             prof(sh, kPrfUpdate);

@@ -809,9 +809,13 @@ __device__ __forceinline__ void fit_body(const SolveArgs& a, Shared& sh) {
     });
     prof(sh, kPrfOther);
     if (!gsync(a, sh)) return;
+    // With inter_tol >= 1 (default) sweep m iterates level m only: the levels above it
+    // still hold t = 0, which passes their residual test at once, so their FP64 residuals
+    // are not computed either.
+    const bool skip = a.inter_tol >= 1.0;
     for (int m = 0; m < a.sweeps; ++m) {
         if (m <= L - 2) {
-            if (!solve_levels<MODE>(a, sh, m, L - 1, false)) return;
+            if (!solve_levels<MODE>(a, sh, m, skip ? m + 1 : L - 1, false)) return;
         }
         if (m + 1 <= L - 1 && a.lower_inc) {
             // beta_k -= B_km t_m for the rows of levels k = m+1..L-1 (FP64).  When

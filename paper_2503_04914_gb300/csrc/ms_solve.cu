@@ -10,8 +10,8 @@
 namespace {
 
 // MINB: CTAs per SM the kernel is compiled for (1: up to 128 registers a thread,
-// 2: up to 64).
-template <int MODE, int MINB>
+// 2: up to 64).  WIDE: the right-hand sides in the row-major (SpMM) layout.
+template <int MODE, int MINB, bool WIDE>
 __global__ void __launch_bounds__(kBS, MINB) k_fit(const __grid_constant__ SolveArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shared& sh = *reinterpret_cast<Shared*>(smem_raw);
@@ -20,7 +20,26 @@ __global__ void __launch_bounds__(kBS, MINB) k_fit(const __grid_constant__ Solve
         sh.nb = gridDim.x;
     }
     __syncthreads();
-    fit_body<MODE>(a, sh);
+    fit_body<MODE, WIDE>(a, sh);
+}
+
+// f (input order, [N][nrhs], columns col0..col0+R-1) -> [N][RW] in sorted order (padding 0),
+// and back for alpha.
+__global__ void k_gather_wide(const double* in, double* out, const int32_t* perm, int64_t N, int nrhs, int col0,
+                              int R, int RW) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N * RW) return;
+    const int64_t row = i / RW;
+    const int r = (int)(i % RW);
+    out[i] = r < R ? in[(int64_t)perm[row] * nrhs + col0 + r] : 0.0;
+}
+__global__ void k_scatter_wide(const double* in, double* out, const int32_t* perm, int64_t N, int nrhs, int col0,
+                               int R, int RW) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N * RW) return;
+    const int64_t row = i / RW;
+    const int r = (int)(i % RW);
+    if (r < R) out[(int64_t)perm[row] * nrhs + col0 + r] = in[i];
 }
 
 // ---------------------------------------------------------------- stand-alone mat-vecs
@@ -62,14 +81,15 @@ int ctas_per_sm(const ms_opts& o) {
     return 2;
 }
 
-const void* fit_kernel(bool mixed, int minb) {
-    if (mixed) return minb == 1 ? (const void*)k_fit<1, 1> : (const void*)k_fit<1, 2>;
-    return minb == 1 ? (const void*)k_fit<0, 1> : (const void*)k_fit<0, 2>;
+const void* fit_kernel(bool mixed, int minb, bool wide = false) {
+    if (wide) return mixed ? (const void*)k_fit<1, 2, true> : (const void*)k_fit<0, 2, true>;
+    if (mixed) return minb == 1 ? (const void*)k_fit<1, 1, false> : (const void*)k_fit<1, 2, false>;
+    return minb == 1 ? (const void*)k_fit<0, 1, false> : (const void*)k_fit<0, 2, false>;
 }
 
 // Cooperative grid of the solve kernel: min(per_sm, minb) CTAs on every SM.
-ms_status fit_blocks(bool mixed, int minb, int dev, int* blocks) {
-    const void* fn = fit_kernel(mixed, minb);
+ms_status fit_blocks(bool mixed, int minb, int dev, int* blocks, bool wide = false) {
+    const void* fn = fit_kernel(mixed, minb, wide);
     // the per-CTA state is above the default 48 KB of dynamic shared memory
     MS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared)));
     int sms = 0, per_sm = 0;
@@ -134,7 +154,10 @@ ms_status ms_ensure_workspace(ms_hierarchy* h, int R) {
 ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel_tol, double* alpha_dev,
                       ms_fit_stats* stats, cudaStream_t st) {
     const int Rmax = rhs_per_launch(h, nrhs);
-    MS_TRY(ms_ensure_workspace(h, Rmax));
+    const bool wide = wide_layout(h, nrhs, ctas_per_sm(h->opts));
+    int RWmax = 1;
+    while (RWmax < Rmax) RWmax <<= 1;
+    MS_TRY(ms_ensure_workspace(h, wide ? RWmax : Rmax));
     const int L = h->L;
     const int64_t N = h->N;
     const bool mixed = h->opts.precision == MS_PREC_MIXED;
@@ -163,30 +186,45 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
     for (int col0 = 0; col0 < nrhs; col0 += Rmax) {
         const int R = std::min(Rmax, nrhs - col0);
         SolveArgs a{};
-        fill_args(h, rel_tol, R, a);
+        fill_args(h, rel_tol, R, a, wide);
         a.f = h->f; a.beta = h->beta; a.x = h->x; a.r = h->r; a.p = h->p; a.q = h->q; a.s = h->s;
         a.x32 = h->x32; a.r32 = h->r32; a.p32 = h->p32; a.q32 = h->q32; a.s32 = h->s32;
         a.u32 = h->u32; a.u1_32 = h->u1_32;
         a.part = h->part; a.gpart = h->gpart; a.scal = h->scal; a.bar = h->bar; a.status = h->status;
         a.iters = h->iters; a.refines = h->refines; a.resid = h->resid; a.bytes = h->bytes; a.prof = h->prof;
         a.pcfb = h->pcfb;
-        for (int r = 0; r < R; ++r) {
-            ms_gather_sorted(f_dev, h->f + (int64_t)r * N, h->perm, N, nrhs, col0 + r, st);
+        if (wide) {
+            k_gather_wide<<<nblk(N * a.RW, 256), 256, 0, st>>>(f_dev, h->f, h->perm, N, nrhs, col0, R, a.RW);
+            ms_count_launch();
             ++launches;
+        } else {
+            for (int r = 0; r < R; ++r) {
+                ms_gather_sorted(f_dev, h->f + (int64_t)r * N, h->perm, N, nrhs, col0 + r, st);
+                ++launches;
+            }
         }
         MS_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * kBarWords, st));
         MS_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
         MS_CUDA(cudaMemsetAsync(h->resid, 0, sizeof(double) * a.V, st));
         void* args[] = {&a};
         MS_CUDA(cudaEventRecord(h->ev0, st));
-        MS_CUDA(cudaLaunchCooperativeKernel(fit_kernel(mixed, ctas_per_sm(h->opts)), dim3(h->solve_blocks), dim3(kBS),
+        int grid = h->solve_blocks;
+        if (wide) MS_TRY(fit_blocks(mixed, 2, h->device, &grid, true));
+        grid = std::min(grid, h->solve_blocks);  // the reduction buffers hold solve_blocks CTAs
+        MS_CUDA(cudaLaunchCooperativeKernel(fit_kernel(mixed, ctas_per_sm(h->opts), wide), dim3(grid), dim3(kBS),
                                             args, sizeof(Shared), st));
         ms_count_launch();
         MS_CUDA(cudaEventRecord(h->ev1, st));
         ++launches;
-        for (int r = 0; r < R; ++r) {
-            ms_scatter_input(h->x + (int64_t)r * N, alpha_dev, h->perm, N, nrhs, col0 + r, st);
+        if (wide) {
+            k_scatter_wide<<<nblk(N * a.RW, 256), 256, 0, st>>>(h->x, alpha_dev, h->perm, N, nrhs, col0, R, a.RW);
+            ms_count_launch();
             ++launches;
+        } else {
+            for (int r = 0; r < R; ++r) {
+                ms_scatter_input(h->x + (int64_t)r * N, alpha_dev, h->perm, N, nrhs, col0 + r, st);
+                ++launches;
+            }
         }
         MS_CUDA(cudaGetLastError());
         double b = 0.0;

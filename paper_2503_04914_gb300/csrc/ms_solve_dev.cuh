@@ -62,6 +62,8 @@ enum { kPrfResid = 0, kPrfMatvec = 1, kPrfUpdate = 2, kPrfBarrier = 3, kPrfLower
 
 struct SolveArgs {
     int L, R, V;       // levels, right-hand sides of this launch, V = R L virtual levels
+    int RW;            // wide layout: lanes (vector elements) per row, a power of 2 >= R; 0 = RHS-major
+    int crow;          // rows per work chunk
     int64_t N;         // points
     int C;             // chunks per right-hand side
     int64_t off[MS_MAXL + 1];
@@ -231,8 +233,8 @@ __device__ __forceinline__ void run_phase(const SolveArgs& a, Shared& sh, Sel se
             ch.l = l;
             ch.v = v;
             ch.vb = (int64_t)rhs * a.N;
-            ch.r0 = a.off[l] + (int64_t)(c - a.coff[l]) * kChunk;
-            ch.r1 = min(ch.r0 + (int64_t)kChunk, a.off[l + 1]);
+            ch.r0 = a.off[l] + (int64_t)(c - a.coff[l]) * a.crow;
+            ch.r1 = min(ch.r0 + (int64_t)a.crow, a.off[l + 1]);
             body(ch, acc);
             c += nb;
         }
@@ -408,11 +410,266 @@ __device__ __forceinline__ void rows_by_subwarp(int64_t r0, int64_t r1, int S, F
     }
 }
 
+
+// ---------------------------------------------------------------- wide (SpMM) layout
+//
+// The right-hand sides of a launch stored row-major: element (row, r) at row * RW + r,
+// RW = the power of 2 >= R.  Thread t works for right-hand side t % RW in every phase
+// (kBS and 32 are multiples of RW).  In a mat-vec phase the RW lanes of a row read its
+// matrix entries once (the same address in every lane: one broadcast load) and gather RW
+// consecutive vector elements per column, so a CSR read serves all right-hand sides.
+// Chunks of a.crow = 512 / RW rows hold one element per thread.
+
+template <int K>
+__device__ __forceinline__ void flush_wide(const SolveArgs& a, Shared& sh, double* acc, int l) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        sh.red[k][threadIdx.x] = acc[k];
+        acc[k] = 0.0;
+    }
+    __syncthreads();
+    const int RW = a.RW;
+    for (int i = threadIdx.x; i < K * RW; i += kBS) {
+        const int k = i / RW, r = i % RW;
+        double t = 0.0;
+        for (int j = r; j < kBS; j += RW) t += sh.red[k][j];
+        if (r < a.R) sh.acc[k][r * a.L + l] += t;
+    }
+    __syncthreads();
+}
+
+// body(l, r0, r1, acc) over this CTA's chunks of the levels where sel(r L + l) holds for
+// some right-hand side r; per-CTA sums as in run_phase.
+template <int K, typename Sel, typename Body>
+__device__ __forceinline__ void run_phase_wide(const SolveArgs& a, Shared& sh, Sel sel, Body body) {
+    if (K > 0) {
+        for (int i = threadIdx.x; i < kAcc * kMaxV; i += kBS) (&sh.acc[0][0])[i] = 0.0;
+        __syncthreads();
+    }
+    double acc[K > 0 ? K : 1];
+#pragma unroll
+    for (int k = 0; k < (K > 0 ? K : 1); ++k) acc[k] = 0.0;
+    int cur = -1;
+    const int nb = sh.nb, C = a.C;
+    int l = 0, lsel = -1;
+    bool lok = false;
+    for (int c = sh.cta; c < C;) {
+        while (c >= a.coff[l + 1]) ++l;
+        if (l != lsel) {
+            lsel = l;
+            lok = false;
+            for (int r = 0; r < a.R; ++r) lok |= sel(r * a.L + l);
+        }
+        if (!lok) {
+            c += (a.coff[l + 1] - c + nb - 1) / nb * nb;
+            continue;
+        }
+        if (K > 0 && l != cur) {
+            if (cur >= 0) flush_wide<K>(a, sh, acc, cur);
+            cur = l;
+        }
+        const int64_t r0 = a.off[l] + (int64_t)(c - a.coff[l]) * a.crow;
+        const int64_t r1 = min(r0 + (int64_t)a.crow, a.off[l + 1]);
+        body(l, r0, r1, acc);
+        c += nb;
+    }
+    if (K > 0) {
+        if (cur >= 0) flush_wide<K>(a, sh, acc, cur);
+        for (int i = threadIdx.x; i < K * a.V; i += kBS) {
+            const int k = i / a.V, v = i % a.V;
+            a.part[((size_t)k * a.V + v) * sh.nb + sh.cta] = sh.acc[k][v];
+        }
+    }
+}
+
+// Elements (row, r) of rows [r0, r1): fn(row, i = row * RW + r); r = this thread's lane.
+template <typename Fn>
+__device__ __forceinline__ void elems_wide(const SolveArgs& a, int64_t r0, int64_t r1, Fn fn) {
+    const int RW = a.RW;
+    const int64_t n = (r1 - r0) * RW;
+    for (int64_t e = threadIdx.x; e < n; e += kBS) {
+        const int64_t row = r0 + e / RW;
+        fn(row, row * RW + (e % RW));
+    }
+}
+
+// Rows [r0, r1), RW lanes per row (32 / RW rows per warp): fn(row) for this thread's row.
+template <typename Fn>
+__device__ __forceinline__ void rows_wide(const SolveArgs& a, int64_t r0, int64_t r1, Fn fn) {
+    const int RW = a.RW;
+    const int rpw = 32 / RW;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t base = r0 + (int64_t)w * rpw; base < r1; base += (int64_t)kNW * rpw) {
+        const int64_t row = base + lane / RW;
+        if (row < r1) fn(row);
+    }
+}
+
+// sum_k val[k] * x[col[k] * RW + r] over [s, e): the row's entries read by all RW lanes.
+template <typename TV, typename TX, typename TA>
+__device__ __forceinline__ TA csr_row_wide(const int32_t* __restrict__ col, const TV* __restrict__ val,
+                                           const TX* x, int64_t s, int64_t e, int r, int RW) {
+    TA acc = TA(0);
+    int64_t k = s;
+    for (; k + 3 < e; k += 4) {
+        const int32_t c0 = __ldg(col + k), c1 = __ldg(col + k + 1), c2 = __ldg(col + k + 2), c3 = __ldg(col + k + 3);
+        const TV v0 = __ldg(val + k), v1 = __ldg(val + k + 1), v2 = __ldg(val + k + 2), v3 = __ldg(val + k + 3);
+        const TX x0 = x[(int64_t)c0 * RW + r], x1 = x[(int64_t)c1 * RW + r], x2 = x[(int64_t)c2 * RW + r],
+                 x3 = x[(int64_t)c3 * RW + r];
+        acc += (TA)v0 * (TA)x0;
+        acc += (TA)v1 * (TA)x1;
+        acc += (TA)v2 * (TA)x2;
+        acc += (TA)v3 * (TA)x3;
+    }
+    for (; k < e; ++k) acc += (TA)__ldg(val + k) * (TA)x[(int64_t)__ldg(col + k) * RW + r];
+    return acc;
+}
+
 // ---------------------------------------------------------------- level solve
 
 // Solve A_l x_l = beta_l for the levels [l0, l1) of every right-hand side, x warm.
 // tight_all: every level to a.tol, else only level l0 to a.tol and the others to
 // a.inter_tol.
+// Decisions after an FP64 true residual (P1), one thread per virtual level: converged,
+// zero right-hand side, non-finite, out of iterations, or one more refinement round
+// (with its stopping target; MIXED levels whose rounds stall switch to FP64 inner CG).
+// Sets my_any / my_zero for the caller's block vote.
+template <int MODE>
+__device__ __forceinline__ void decide_outer(const SolveArgs& a, Shared& sh, bool first_outer, int& my_any,
+                                             int& my_zero) {
+    const int tid = threadIdx.x;
+    const int V = a.V, L = a.L;
+    my_any = 0;
+    my_zero = 0;
+    for (int v = tid; v < V; v += kBS) {
+        if (!sh.oact[v]) continue;
+        const int l = v % L;
+        const double rr = sh.out[0][v];
+        if (first_outer) sh.bb[v] = sh.out[1][v];
+        const double bb = sh.bb[v];
+        sh.vbytes[v] += (double)a.nnzA[l] * 12.0 + (double)(a.off[l + 1] - a.off[l]) * 32.0;
+        if (!isfinite(rr) || !isfinite(bb)) {
+            sh.oact[v] = 0;
+            if (sh.cta == 0) atomicCAS(a.status, 0, (int)MS_ERR_NUMERIC);
+            continue;
+        }
+        if (bb == 0.0) {  // zero right-hand side: the solution is zero
+            sh.zero[v] = 1;
+            sh.oact[v] = 0;
+            my_zero = 1;
+            if (sh.cta == 0) a.resid[v] = 0.0;
+            continue;
+        }
+        const double res = sqrt(rr / bb);
+        if (sh.cta == 0) a.resid[v] = res;
+        if (res <= sh.tol[v]) {
+            sh.oact[v] = 0;
+            continue;
+        }
+        if (sh.it_solve[v] >= a.max_iters) {
+            sh.oact[v] = 0;
+            if (sh.cta == 0) atomicCAS(a.status, 0, (int)MS_ERR_NOT_CONVERGED);
+            continue;
+        }
+        // MIXED: an outer round that did not halve the true residual means the FP32 inner
+        // CG stalls on this level (conditioning beyond FP32): run its inner CG in FP64
+        if (MODE == 1 && !sh.f64[v] && res > 0.5 * sh.prevres[v]) {
+            sh.f64[v] = 1;
+            sh.f64n[v] += 1;
+        }
+        sh.prevres[v] = res;
+        my_any = 1;
+        sh.refines[v] += 1;
+        sh.act[v] = 1;
+        sh.first[v] = 1;
+        if (MODE == 0 || sh.f64[v]) {
+            // recursive-residual target, with margin below the true-residual tolerance
+            sh.target[v] = 0.25 * sh.tol[v] * sh.tol[v] * bb;
+        } else {
+            sh.scale[v] = 1.0 / sqrt(rr);
+            const double need = 0.5 * sh.tol[v] * sqrt(bb) * sh.scale[v];
+            const double t = fmax(a.inner_tol, fmin(need, 1.0));
+            sh.target[v] = t * t;
+        }
+    }
+}
+
+// Decisions after the mat-vec and its dots, one thread per active virtual level: the
+// CG step sizes, convergence of the recursive residual, break-downs (preconditioner
+// fall-back, curvature loss, not SPD).  Returns whether this thread's levels go on.
+template <int MODE>
+__device__ __forceinline__ int decide_inner(const SolveArgs& a, Shared& sh, bool use_pc) {
+    const int tid = threadIdx.x;
+    const int V = a.V, L = a.L;
+    int my_go = 0;
+    for (int v = tid; v < V; v += kBS) {
+        if (!sh.act[v]) continue;
+        const int l = v % L;
+        const double gam = sh.out[0][v], del = sh.out[1][v], rho = sh.out[2][v];
+        const bool dbl = MODE == 0 || sh.f64[v];
+        const bool lpc = use_pc && !sh.pcoff[v] && !dbl;
+        const double n = (double)(a.off[l + 1] - a.off[l]);
+        sh.vbytes[v] += (double)a.nnzA[l] * (dbl ? 12.0 : 8.0) + n * (dbl ? 32.0 : (lpc ? 24.0 : 20.0));
+        if (lpc) sh.vbytes[v] += n * (2.0 * kPcOut * 12.0 + 16.0);
+        if (!isfinite(gam) || !isfinite(del) || !isfinite(rho)) {
+            sh.act[v] = 0;
+            sh.oact[v] = 0;
+            if (sh.cta == 0) atomicCAS(a.status, 0, (int)MS_ERR_NUMERIC);
+            continue;
+        }
+        if (rho <= sh.target[v] || sh.it_solve[v] >= a.max_iters) {
+            sh.act[v] = 0;  // converged (recursive residual) or capped
+            continue;
+        }
+        if (lpc && !(gam > 0.0)) {
+            // r^T M r <= 0 cannot happen for an SPD M: treat the preconditioner as
+            // broken and fall back to plain CG from the current iterate
+            sh.pcoff[v] = 1;
+            sh.fb[v] += 1;
+            sh.act[v] = 0;
+            continue;
+        }
+        double al, be;
+        if (sh.first[v]) {
+            be = 0.0;
+            al = del > 0.0 ? gam / del : -1.0;
+        } else {
+            be = gam / sh.gam[v];
+            const double den = del - be * gam / sh.alpha[v];
+            al = den > 0.0 ? gam / den : -1.0;
+        }
+        if (!(al > 0.0)) {
+            if (MODE == 1 && !sh.first[v]) {  // (FP32, or an FP64 fallback level)
+                // lost curvature in the FP32 recurrence (cancellation on an ill-conditioned
+                // level): end this inner solve; the FP64 true residual restarts it
+                sh.act[v] = 0;
+                continue;
+            }
+            if (lpc) {  // u^T A u <= 0 at a restart: the preconditioner is unusable here
+                sh.pcoff[v] = 1;
+                sh.fb[v] += 1;
+                sh.act[v] = 0;
+                continue;
+            }
+            // p^T A p <= 0 at a restart: A_l is not positive definite in floating point
+            sh.act[v] = 0;
+            sh.oact[v] = 0;
+            if (sh.cta == 0) atomicCAS(a.status, 0, (int)MS_ERR_NOT_SPD);
+            continue;
+        }
+        sh.fresh[v] = sh.first[v];  // the update must not read the old p, s
+        sh.first[v] = 0;
+        sh.alpha[v] = al;
+        sh.beta[v] = be;
+        sh.gam[v] = gam;
+        sh.it_solve[v] += 1;
+        sh.it_total[v] += 1;
+        sh.vbytes[v] += n * (dbl ? 72.0 : 36.0);
+        my_go = 1;
+    }
+    return my_go;
+}
+
 template <int MODE>
 __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, bool tight_all) {
     const int tid = threadIdx.x;
@@ -451,57 +708,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
         if (!gsync_reduce<2>(a, sh)) return false;
         // decisions: one thread per virtual level
         int my_any = 0, my_zero = 0;
-        for (int v = tid; v < V; v += kBS) {
-            if (!sh.oact[v]) continue;
-            const int l = v % L;
-            const double rr = sh.out[0][v];
-            if (first_outer) sh.bb[v] = sh.out[1][v];
-            const double bb = sh.bb[v];
-            sh.vbytes[v] += (double)a.nnzA[l] * 12.0 + (double)(a.off[l + 1] - a.off[l]) * 32.0;
-            if (!isfinite(rr) || !isfinite(bb)) {
-                sh.oact[v] = 0;
-                if (sh.cta == 0) atomicCAS(a.status, 0, (int)MS_ERR_NUMERIC);
-                continue;
-            }
-            if (bb == 0.0) {  // zero right-hand side: the solution is zero
-                sh.zero[v] = 1;
-                sh.oact[v] = 0;
-                my_zero = 1;
-                if (sh.cta == 0) a.resid[v] = 0.0;
-                continue;
-            }
-            const double res = sqrt(rr / bb);
-            if (sh.cta == 0) a.resid[v] = res;
-            if (res <= sh.tol[v]) {
-                sh.oact[v] = 0;
-                continue;
-            }
-            if (sh.it_solve[v] >= a.max_iters) {
-                sh.oact[v] = 0;
-                if (sh.cta == 0) atomicCAS(a.status, 0, (int)MS_ERR_NOT_CONVERGED);
-                continue;
-            }
-            // MIXED: an outer round that did not halve the true residual means the FP32 inner
-            // CG stalls on this level (conditioning beyond FP32): run its inner CG in FP64
-            if (MODE == 1 && !sh.f64[v] && res > 0.5 * sh.prevres[v]) {
-                sh.f64[v] = 1;
-                sh.f64n[v] += 1;
-            }
-            sh.prevres[v] = res;
-            my_any = 1;
-            sh.refines[v] += 1;
-            sh.act[v] = 1;
-            sh.first[v] = 1;
-            if (MODE == 0 || sh.f64[v]) {
-                // recursive-residual target, with margin below the true-residual tolerance
-                sh.target[v] = 0.25 * sh.tol[v] * sh.tol[v] * bb;
-            } else {
-                sh.scale[v] = 1.0 / sqrt(rr);
-                const double need = 0.5 * sh.tol[v] * sqrt(bb) * sh.scale[v];
-                const double t = fmax(a.inner_tol, fmin(need, 1.0));
-                sh.target[v] = t * t;
-            }
-        }
+        decide_outer<MODE>(a, sh, first_outer, my_any, my_zero);
         const bool any = __syncthreads_or(my_any) != 0;
         const bool anyzero = __syncthreads_or(my_zero) != 0;
         prof(sh, kPrfScalar);
@@ -630,74 +837,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
             });
             prof(sh, kPrfMatvec);
             if (!gsync_reduce<3>(a, sh)) return false;
-            int my_go = 0;
-            {
-                for (int v = tid; v < V; v += kBS) {
-                    if (!sh.act[v]) continue;
-                    const int l = v % L;
-                    const double gam = sh.out[0][v], del = sh.out[1][v], rho = sh.out[2][v];
-                    const bool dbl = MODE == 0 || sh.f64[v];
-                    const bool lpc = use_pc && !sh.pcoff[v] && !dbl;
-                    const double n = (double)(a.off[l + 1] - a.off[l]);
-                    sh.vbytes[v] += (double)a.nnzA[l] * (dbl ? 12.0 : 8.0) + n * (dbl ? 32.0 : (lpc ? 24.0 : 20.0));
-                    if (lpc) sh.vbytes[v] += n * (2.0 * kPcOut * 12.0 + 16.0);
-                    if (!isfinite(gam) || !isfinite(del) || !isfinite(rho)) {
-                        sh.act[v] = 0;
-                        sh.oact[v] = 0;
-                        if (sh.cta == 0) atomicCAS(a.status, 0, (int)MS_ERR_NUMERIC);
-                        continue;
-                    }
-                    if (rho <= sh.target[v] || sh.it_solve[v] >= a.max_iters) {
-                        sh.act[v] = 0;  // converged (recursive residual) or capped
-                        continue;
-                    }
-                    if (lpc && !(gam > 0.0)) {
-                        // r^T M r <= 0 cannot happen for an SPD M: treat the preconditioner as
-                        // broken and fall back to plain CG from the current iterate
-                        sh.pcoff[v] = 1;
-                        sh.fb[v] += 1;
-                        sh.act[v] = 0;
-                        continue;
-                    }
-                    double al, be;
-                    if (sh.first[v]) {
-                        be = 0.0;
-                        al = del > 0.0 ? gam / del : -1.0;
-                    } else {
-                        be = gam / sh.gam[v];
-                        const double den = del - be * gam / sh.alpha[v];
-                        al = den > 0.0 ? gam / den : -1.0;
-                    }
-                    if (!(al > 0.0)) {
-                        if (MODE == 1 && !sh.first[v]) {  // (FP32, or an FP64 fallback level)
-                            // lost curvature in the FP32 recurrence (cancellation on an ill-conditioned
-                            // level): end this inner solve; the FP64 true residual restarts it
-                            sh.act[v] = 0;
-                            continue;
-                        }
-                        if (lpc) {  // u^T A u <= 0 at a restart: the preconditioner is unusable here
-                            sh.pcoff[v] = 1;
-                            sh.fb[v] += 1;
-                            sh.act[v] = 0;
-                            continue;
-                        }
-                        // p^T A p <= 0 at a restart: A_l is not positive definite in floating point
-                        sh.act[v] = 0;
-                        sh.oact[v] = 0;
-                        if (sh.cta == 0) atomicCAS(a.status, 0, (int)MS_ERR_NOT_SPD);
-                        continue;
-                    }
-                    sh.fresh[v] = sh.first[v];  // the update must not read the old p, s
-                    sh.first[v] = 0;
-                    sh.alpha[v] = al;
-                    sh.beta[v] = be;
-                    sh.gam[v] = gam;
-                    sh.it_solve[v] += 1;
-                    sh.it_total[v] += 1;
-                    sh.vbytes[v] += n * (dbl ? 72.0 : 36.0);
-                    my_go = 1;
-                }
-            }
+            const int my_go = decide_inner<MODE>(a, sh, use_pc);
             const bool go = __syncthreads_or(my_go) != 0;
             prof(sh, kPrfScalar);
             if (!go) break;
@@ -779,9 +919,177 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
     return true;
 }
 
+
+// solve_levels for the wide layout (no preconditioner, CSR operators).
+template <int MODE>
+__device__ bool solve_levels_wide(const SolveArgs& a, Shared& sh, int l0, int l1, bool tight_all) {
+    const int tid = threadIdx.x;
+    const int V = a.V, L = a.L, RW = a.RW;
+    const int rl = tid % RW;  // this thread's right-hand side
+    const bool rok = rl < a.R;
+    for (int v = tid; v < kMaxV; v += kBS) {
+        const int l = v % L;
+        sh.oact[v] = (v < V && l >= l0 && l < l1) ? 1 : 0;
+        sh.act[v] = 0;
+        sh.zero[v] = 0;
+        sh.pcoff[v] = 0;
+        sh.prevres[v] = INFINITY;
+        sh.it_solve[v] = 0;
+        sh.tol[v] = (tight_all || l == l0) ? a.tol : a.inter_tol;
+    }
+    __syncthreads();
+    bool first_outer = true;
+    for (int outer = 0; outer < a.max_outer; ++outer) {
+        // ---- P1: FP64 true residual r = b - A x (FP64 CSR)
+        run_phase_wide<2>(a, sh, [&](int v) { return sh.oact[v] != 0; },
+                          [&](int l, int64_t r0, int64_t r1, double* acc) {
+                              if (!(rok && sh.oact[rl * L + l])) return;
+                              rows_wide(a, r0, r1, [&](int64_t row) {
+                                  const double y = csr_row_wide<double, double, double>(
+                                      a.Acol, a.Av64, a.x, a.Arp[row], a.Arp[row + 1], rl, RW);
+                                  const int64_t i = row * RW + rl;
+                                  const double b = a.beta[i];
+                                  const double ri = b - y;
+                                  a.r[i] = ri;
+                                  acc[0] += ri * ri;
+                                  acc[1] += b * b;
+                              });
+                          });
+        prof(sh, kPrfResid);
+        if (!gsync_reduce<2>(a, sh)) return false;
+        int my_any = 0, my_zero = 0;
+        decide_outer<MODE>(a, sh, first_outer, my_any, my_zero);
+        const bool any = __syncthreads_or(my_any) != 0;
+        const bool anyzero = __syncthreads_or(my_zero) != 0;
+        prof(sh, kPrfScalar);
+        first_outer = false;
+        if (anyzero) {
+            run_phase_wide<0>(a, sh, [&](int v) { return sh.zero[v] != 0; },
+                              [&](int l, int64_t r0, int64_t r1, double*) {
+                                  if (!(rok && sh.zero[rl * L + l])) return;
+                                  elems_wide(a, r0, r1, [&](int64_t, int64_t i) { a.x[i] = 0.0; });
+                              });
+            prof(sh, kPrfOther);
+            if (!gsync(a, sh)) return false;
+            for (int v = tid; v < kMaxV; v += kBS) sh.zero[v] = 0;
+            __syncthreads();
+        }
+        if (!any) break;
+
+        if (MODE == 1) {
+            // ---- P2: r32 = r / |r|, x32 = 0
+            run_phase_wide<0>(a, sh, [&](int v) { return sh.act[v] != 0 && !sh.f64[v]; },
+                              [&](int l, int64_t r0, int64_t r1, double*) {
+                                  const int v = rl * L + l;
+                                  if (!(rok && sh.act[v] && !sh.f64[v])) return;
+                                  const double sc = sh.scale[v];
+                                  elems_wide(a, r0, r1, [&](int64_t, int64_t i) {
+                                      a.r32[i] = (float)(a.r[i] * sc);
+                                      a.x32[i] = 0.f;
+                                  });
+                              });
+            for (int v = tid; v < V; v += kBS)
+                if (sh.act[v] && !sh.f64[v]) sh.vbytes[v] += (double)(a.off[v % L + 1] - a.off[v % L]) * 16.0;
+            prof(sh, kPrfOther);
+            if (!gsync(a, sh)) return false;
+        }
+
+        // ---- inner CG iterations (single-reduction form, u = r)
+        for (;;) {
+            // M: w = A r; gamma = r.r, delta = w.r, rho = r.r
+            run_phase_wide<3>(a, sh, [&](int v) { return sh.act[v] != 0; },
+                              [&](int l, int64_t r0, int64_t r1, double* acc) {
+                                  const int v = rl * L + l;
+                                  if (!(rok && sh.act[v])) return;
+                                  if (MODE == 0 || sh.f64[v]) {
+                                      rows_wide(a, r0, r1, [&](int64_t row) {
+                                          const double y = csr_row_wide<double, double, double>(
+                                              a.Acol, a.Av64, a.r, a.Arp[row], a.Arp[row + 1], rl, RW);
+                                          const int64_t i = row * RW + rl;
+                                          const double ri = a.r[i];
+                                          a.q[i] = y;
+                                          acc[0] += ri * ri;
+                                          acc[1] += ri * y;
+                                          acc[2] += ri * ri;
+                                      });
+                                  } else {
+                                      rows_wide(a, r0, r1, [&](int64_t row) {
+                                          const float y = csr_row_wide<float, float, float>(
+                                              a.Acol, a.Av32, a.r32, a.Arp[row], a.Arp[row + 1], rl, RW);
+                                          const int64_t i = row * RW + rl;
+                                          const float ri = a.r32[i];
+                                          a.q32[i] = y;
+                                          acc[0] += (double)ri * (double)ri;
+                                          acc[1] += (double)ri * (double)y;
+                                          acc[2] += (double)(ri * ri);
+                                      });
+                                  }
+                              });
+            prof(sh, kPrfMatvec);
+            if (!gsync_reduce<3>(a, sh)) return false;
+            const int my_go = decide_inner<MODE>(a, sh, false);
+            const bool go = __syncthreads_or(my_go) != 0;
+            prof(sh, kPrfScalar);
+            if (!go) break;
+            // E: p = r + beta p; s = w + beta s; x += alpha p; r -= alpha s
+            run_phase_wide<0>(a, sh, [&](int v) { return sh.act[v] != 0; },
+                              [&](int l, int64_t r0, int64_t r1, double*) {
+                                  const int v = rl * L + l;
+                                  if (!(rok && sh.act[v])) return;
+                                  const double al = sh.alpha[v], be = sh.beta[v];
+                                  const bool fr = sh.fresh[v] != 0;
+                                  if (MODE == 0 || sh.f64[v]) {
+                                      elems_wide(a, r0, r1, [&](int64_t, int64_t i) {
+                                          const double ri = a.r[i];
+                                          const double pi = fr ? ri : ri + be * a.p[i];
+                                          const double si = fr ? a.q[i] : a.q[i] + be * a.s[i];
+                                          a.p[i] = pi;
+                                          a.s[i] = si;
+                                          a.x[i] += al * pi;
+                                          a.r[i] = ri - al * si;
+                                      });
+                                  } else {
+                                      const float af = (float)al, bf = (float)be;
+                                      elems_wide(a, r0, r1, [&](int64_t, int64_t i) {
+                                          const float ri = a.r32[i];
+                                          const float pi = fr ? ri : fmaf(bf, a.p32[i], ri);
+                                          const float si = fr ? a.q32[i] : fmaf(bf, a.s32[i], a.q32[i]);
+                                          a.p32[i] = pi;
+                                          a.s32[i] = si;
+                                          a.x32[i] = fmaf(af, pi, a.x32[i]);
+                                          a.r32[i] = fmaf(-af, si, ri);
+                                      });
+                                  }
+                              });
+            prof(sh, kPrfUpdate);
+            if (!gsync(a, sh)) return false;
+        }
+
+        if (MODE == 1) {
+            // ---- P3: x += |r| d  (FP64)
+            run_phase_wide<0>(a, sh, [&](int v) { return sh.oact[v] != 0 && sh.scale[v] > 0.0 && !sh.f64[v]; },
+                              [&](int l, int64_t r0, int64_t r1, double*) {
+                                  const int v = rl * L + l;
+                                  if (!(rok && sh.oact[v] && sh.scale[v] > 0.0 && !sh.f64[v])) return;
+                                  const double inv = 1.0 / sh.scale[v];
+                                  elems_wide(a, r0, r1, [&](int64_t, int64_t i) { a.x[i] += (double)a.x32[i] * inv; });
+                              });
+            for (int v = tid; v < V; v += kBS)
+                if (sh.oact[v] && !sh.f64[v]) sh.vbytes[v] += (double)(a.off[v % L + 1] - a.off[v % L]) * 20.0;
+            prof(sh, kPrfOther);
+            if (!gsync(a, sh)) return false;
+        }
+    }
+    if (sh.cta == 0)
+        for (int v = tid; v < V; v += kBS)
+            if (sh.oact[v]) atomicCAS(a.status, 0, (int)MS_ERR_NOT_CONVERGED);
+    __syncthreads();
+    return true;
+}
+
 // The whole schedule of eq. split for one hierarchy, run by the CTAs [0, sh.nb) of a
 // partition (sh.cta: this CTA's index in it).
-template <int MODE>
+template <int MODE, bool WIDE = false>
 __device__ __forceinline__ void fit_body(const SolveArgs& a, Shared& sh) {
     const int tid = threadIdx.x;
     for (int v = tid; v < kMaxV; v += kBS) {
@@ -801,12 +1109,22 @@ __device__ __forceinline__ void fit_body(const SolveArgs& a, Shared& sh) {
     __syncthreads();
     const int L = a.L;
     // beta_0 = f, x = 0
-    run_phase<0>(a, sh, [](int) { return true; }, [&](const Chunk& ch, double*) {
-        for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
-            a.beta[ch.vb + row] = a.f[ch.vb + row];
-            a.x[ch.vb + row] = 0.0;
-        }
-    });
+    if (WIDE) {
+        const int rl = tid % a.RW;
+        run_phase_wide<0>(a, sh, [](int) { return true; }, [&](int, int64_t r0, int64_t r1, double*) {
+            elems_wide(a, r0, r1, [&](int64_t, int64_t i) {
+                a.beta[i] = rl < a.R ? a.f[i] : 0.0;
+                a.x[i] = 0.0;
+            });
+        });
+    } else {
+        run_phase<0>(a, sh, [](int) { return true; }, [&](const Chunk& ch, double*) {
+            for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
+                a.beta[ch.vb + row] = a.f[ch.vb + row];
+                a.x[ch.vb + row] = 0.0;
+            }
+        });
+    }
     prof(sh, kPrfOther);
     if (!gsync(a, sh)) return;
     // With inter_tol >= 1 (default) sweep m iterates level m only: the levels above it
@@ -815,9 +1133,41 @@ __device__ __forceinline__ void fit_body(const SolveArgs& a, Shared& sh) {
     const bool skip = a.inter_tol >= 1.0;
     for (int m = 0; m < a.sweeps; ++m) {
         if (m <= L - 2) {
-            if (!solve_levels<MODE>(a, sh, m, skip ? m + 1 : L - 1, false)) return;
+            if (!(WIDE ? solve_levels_wide<MODE>(a, sh, m, skip ? m + 1 : L - 1, false)
+                       : solve_levels<MODE>(a, sh, m, skip ? m + 1 : L - 1, false)))
+                return;
         }
-        if (m + 1 <= L - 1 && a.lower_inc) {
+        if (WIDE && m + 1 <= L - 1) {
+            // lower-block update in the wide layout: every right-hand side of a row at once
+            const int rl = tid % a.RW;
+            const int32_t* seg0 = a.Bseg + (int64_t)m * a.N;
+            run_phase_wide<0>(a, sh, [&](int v) { return v % L >= m + 1; }, [&](int, int64_t r0, int64_t r1, double*) {
+                if (rl >= a.R) return;
+                rows_wide(a, r0, r1, [&](int64_t row) {
+                    const int64_t b = a.Brp[row];
+                    const int64_t i = row * a.RW + rl;
+                    if (a.lower_inc) {
+                        const double y = csr_row_wide<double, double, double>(
+                            a.Bcol, a.Bv64, a.x, b + __ldg(seg0 + row), b + __ldg(seg0 + a.N + row), rl, a.RW);
+                        a.beta[i] -= y;
+                    } else {
+                        const double y = csr_row_wide<double, double, double>(a.Bcol, a.Bv64, a.x, b, a.Brp[row + 1],
+                                                                              rl, a.RW);
+                        a.beta[i] = a.f[i] - y;
+                    }
+                });
+            });
+            if (tid == 0) {
+                if (a.lower_inc) {
+                    sh.bytes += (double)a.nnzBm[m] * 12.0 + (double)(a.off[L] - a.off[m + 1]) * (16.0 + 16.0 * a.R);
+                } else {
+                    for (int l = m + 1; l < L; ++l)
+                        sh.bytes += (double)a.nnzB[l] * 12.0 + (double)(a.off[l + 1] - a.off[l]) * (8.0 + 24.0 * a.R);
+                }
+            }
+            prof(sh, kPrfLower);
+            if (!gsync(a, sh)) return;
+        } else if (m + 1 <= L - 1 && a.lower_inc) {
             // beta_k -= B_km t_m for the rows of levels k = m+1..L-1 (FP64).  When
             // intermediate levels are not iterated (inter_tol >= 1) t_m is the only
             // level solution that changed since beta was last updated (levels above m
@@ -862,7 +1212,7 @@ __device__ __forceinline__ void fit_body(const SolveArgs& a, Shared& sh) {
             if (!gsync(a, sh)) return;
         }
     }
-    if (!solve_levels<MODE>(a, sh, 0, L, true)) return;
+    if (!(WIDE ? solve_levels_wide<MODE>(a, sh, 0, L, true) : solve_levels<MODE>(a, sh, 0, L, true))) return;
     if (sh.cta == 0 && tid == 0) {
         for (int l = 0; l < L; ++l) {
             long long it = 0;
@@ -937,7 +1287,8 @@ int mf_tpp_for(const ms_hierarchy* h) {
 }
 
 // Fill the solve arguments that depend only on the hierarchy, the options and R.
-void fill_args(const ms_hierarchy* h, double rel_tol, int R, SolveArgs& a) {
+// wide: the right-hand sides of the launch in the row-major (SpMM) layout, RW lanes per row.
+void fill_args(const ms_hierarchy* h, double rel_tol, int R, SolveArgs& a, bool wide = false) {
     const int64_t* rpA = h->rpA_lv;
     const int64_t* rpB = h->rpB_lv;
     a.mf = (h->opts.precision == MS_PREC_MIXED && h->opts.op == MS_OP_MATRIX_FREE) ? 1 : 0;
@@ -954,11 +1305,17 @@ void fill_args(const ms_hierarchy* h, double rel_tol, int R, SolveArgs& a) {
     a.R = R;
     a.V = R * L;
     a.N = h->N;
+    a.RW = 0;
+    if (wide) {
+        a.RW = 1;
+        while (a.RW < R) a.RW <<= 1;
+    }
+    a.crow = wide ? kBS / a.RW : kChunk;
     int64_t c = 0;
     for (int l = 0; l <= L; ++l) {
         a.off[l] = h->view.off[l];
         a.coff[l] = (int)c;
-        if (l < L) c += (h->view.off[l + 1] - h->view.off[l] + kChunk - 1) / kChunk;
+        if (l < L) c += (h->view.off[l + 1] - h->view.off[l] + a.crow - 1) / a.crow;
     }
     a.C = (int)c;
     for (int l = 0; l < L; ++l) {
@@ -991,5 +1348,12 @@ void fill_args(const ms_hierarchy* h, double rel_tol, int R, SolveArgs& a) {
 
 // Right-hand sides per launch: every (right-hand side, level) pair is a virtual level.
 int rhs_per_launch(const ms_hierarchy* h, int nrhs) { return std::max(1, std::min(nrhs, std::min(32, kMaxV / h->L))); }
+
+// Several right-hand sides take the wide (SpMM) layout when the level operators are CSR
+// without a preconditioner and the solve kernel runs 2 CTAs per SM.
+bool wide_layout(const ms_hierarchy* h, int nrhs, int minb) {
+    return nrhs > 1 && minb == 2 && h->opts.precond == MS_PRECOND_NONE &&
+           !(h->opts.precision == MS_PREC_MIXED && h->opts.op == MS_OP_MATRIX_FREE);
+}
 
 }  // namespace

@@ -322,6 +322,12 @@ def run_ours(args):
             # the other CTAs-per-SM choice of the persistent solve kernel (autotuning evidence)
             out["learned_pcg_1cta_per_sm"] = summary(timed(k2, *HEAD, solve_ctas_per_sm=1))
             out["plain_fp64_1cta_per_sm"] = summary(timed(k2, ms.MS_PREC_FP64, solve_ctas_per_sm=1))
+            # lanes per row chosen by timing (ms_opts.autotune); the first handle times, the rest hit the cache
+            timed(1, *HEAD, autotune=1)
+            rt = timed(k2, *HEAD, autotune=1)
+            out["learned_pcg_autotuned"] = summary(rt)
+            out["learned_pcg_autotuned"]["tpr_A"] = rt[-1]["info"]["tpr_A"]
+            out["learned_pcg_autotuned"]["tpr_A_rule"] = info["tpr_A"]
             out["speedup_learned_vs_plain_fp64"] = out["plain_fp64"]["ms_per_step"] / ms_step
             # agreement of the headline coefficients with the plain FP64 fit (same hierarchy, same f)
             a0 = timed(1, ms.MS_PREC_FP64)[0]["alpha"]
@@ -440,13 +446,31 @@ def run_ours(args):
                 torch.cuda.synchronize()
                 t_one += ev[0].elapsed_time(ev[1])
                 worst = max(worst, float(torch.linalg.norm(ai - a1) / torch.linalg.norm(a1)))
+            # the same batch as a prepared plan replayed from a CUDA graph (host work done once)
+            plan = ms.BatchPlan(handles, fsb, REL_TOL)
+            plan.launch(use_graph=True)
+            plan.stats()
+            t_graph = []
+            for _ in range(3):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                ev[0].record(stream)
+                plan.launch(use_graph=True)
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                t_graph.append(ev[0].elapsed_time(ev[1]))
+            stg = plan.stats()
+            graph_diff = max(float(torch.linalg.norm(ag - ai) / torch.linalg.norm(ai)) for ag, ai in zip(plan.alphas, Ab))
+            plan.close()
             out["batch_hierarchies"] = {
                 "workload": "64 d=2 Halton hierarchies, L ~ U{3..7}, finest N log-uniform in [4096, 262144], "
                             "delta_j=4h_j, phi_{2,1}, one Gaussian-mixture RHS each, MIXED",
                 "points": int(sum(wi.N for wi in wsb)), "batched_ms": t_b, "kernel_ms": stb[0]["fit_ms"],
                 "one_by_one_ms": t_one, "speedup": t_one / t_b,
                 "rel_residual_max": max(max(s["rel_residual"]) for s in stb),
-                "rel_diff_vs_single_max": worst}
+                "rel_diff_vs_single_max": worst,
+                "graph_replay_ms": statistics.mean(t_graph), "graph_rel_diff_vs_batched_max": graph_diff,
+                "graph_rel_residual_max": max(max(s["rel_residual"]) for s in stg)}
             for Hi in Hs:
                 Hi.close()
             del fsb, Ab

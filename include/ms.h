@@ -107,7 +107,11 @@ typedef struct ms_opts {
     int lower_fp32;      /* 1: also store FP32 values of the B blocks (for MS_APPLY_B32) */
     int solve_ctas_per_sm; /* CTAs of the persistent solve kernel per SM: 1 (up to 128
                               registers a thread) or 2 (up to 64); 0 = automatic (2) */
-    int reserved[6];
+    int autotune;        /* 1: at the first fit, time the CSR mat-vec of every level of at
+                            least 4096 rows with 1, 2, 4, 8, 16 and 32 lanes per row and keep
+                            the fastest (cached per process by level shape); 0 = rule
+                            (about 16 entries per lane).  threads_per_row > 0 overrides both. */
+    int reserved[5];
 } ms_opts;
 
 /* Per-fit statistics (all levels 0-based, coarse to fine). */
@@ -145,6 +149,7 @@ typedef struct ms_info {
     int64_t nnz_B;       /* stored entries of the strictly lower blocks (all B_kj, k > j) */
     int64_t device_bytes;/* device memory held by the handle */
     double build_ms;     /* device time of the last build (CUDA events) */
+    int32_t tpr_A[MS_MAX_LEVELS]; /* CSR lanes per row of A_l in the solve (as of the last fit) */
 } ms_info;
 
 /* Fill *opts with defaults: phi_{3,1}, nu = 4, CSR, FP64, no preconditioner. */
@@ -266,6 +271,46 @@ ms_status ms_fit_batch_dev(ms_hierarchy* const* hs, int nh, const double* const*
 /* As ms_fit_batch_dev with HOST f[i] / alpha_out[i] (float64 [N_i], input order). */
 ms_status ms_fit_batch(ms_hierarchy* const* hs, int nh, const double* const* f, double rel_tol,
                        double* const* alpha_out, ms_fit_stats* stats);
+
+/*
+ * A prepared batched fit, for fitting the same hierarchies again and again (new
+ * values in the same right-hand-side buffers).  ms_batch_plan_create does every
+ * host-side step of ms_fit_batch_dev once: work space, preconditioner rows,
+ * autotuning, the split of the grid among the hierarchies and the upload of the
+ * kernel arguments; it binds the DEVICE buffers f_dev[i] and alpha_dev[i]
+ * (float64 [N_i], input order), which must stay allocated while the plan lives.
+ * Arguments and errors as for ms_fit_batch_dev, plus MS_ERR_ARG when a handle
+ * appears twice.  Waits for `stream` before returning.
+ *
+ * While a plan lives, its hierarchies' work space cannot grow: an ms_fit with
+ * more right-hand sides than the handle has fitted before returns MS_ERR_STATE.
+ * Destroy every plan of a hierarchy before the hierarchy.
+ */
+typedef struct ms_batch_plan ms_batch_plan;
+ms_status ms_batch_plan_create(ms_hierarchy* const* hs, int nh, const double* const* f_dev, double rel_tol,
+                               double* const* alpha_dev, void* stream, ms_batch_plan** out);
+
+/*
+ * Enqueue one batched fit of the plan on `stream` (reads f_dev, writes alpha_dev).
+ * Nothing here waits, allocates or copies from the host, so the call may be
+ * captured into a CUDA graph by the caller.  use_graph = 1: the library captures
+ * the launch sequence into a CUDA graph at the first such call (on a private
+ * stream) and from then on replays it with one cudaGraphLaunch on `stream`.
+ * Results: ms_batch_plan_stats after the stream has reached the launch.
+ * Errors: MS_ERR_ARG (NULL plan), MS_ERR_STATE (another device is current),
+ * MS_ERR_CUDA (a launch, a capture or an instantiation failed).
+ */
+ms_status ms_batch_plan_launch(ms_batch_plan* plan, void* stream, int use_graph);
+
+/*
+ * Waits for `stream`, then fills stats (nullable, host [nh]) from the plan's last
+ * completed launch; fit_ms is 0 (time launches with events on the stream).
+ * Returns the first non-zero device status of the batch (as ms_fit_batch_dev).
+ */
+ms_status ms_batch_plan_stats(ms_batch_plan* plan, void* stream, ms_fit_stats* stats);
+
+/* Waits for the device, then frees the plan.  NULL is a no-op. */
+void ms_batch_plan_destroy(ms_batch_plan* plan);
 
 /*
  * Evaluate the approximant f_L(q) = sum_l sum_n alpha_n^(l) Phi_{delta_l}(q - x_n^(l))

@@ -75,6 +75,9 @@ ms_status validate_and_init(int d, int L, const int64_t* n_per_level, const doub
     if (o.threads_per_row < 0 || o.threads_per_row > 32 || (o.threads_per_row & (o.threads_per_row - 1))) {
         ms_set_error(MS_ERR_ARG, "threads_per_row must be 0 or a power of two <= 32"); return MS_ERR_ARG;
     }
+    if (o.autotune < 0 || o.autotune > 1) {
+        ms_set_error(MS_ERR_ARG, "autotune must be 0 or 1"); return MS_ERR_ARG;
+    }
     if (o.solve_ctas_per_sm < 0 || o.solve_ctas_per_sm > 2) {
         ms_set_error(MS_ERR_ARG, "solve_ctas_per_sm must be 0, 1 or 2"); return MS_ERR_ARG;
     }
@@ -342,6 +345,38 @@ ms_status ms_fit_batch_dev(ms_hierarchy* const* hs, int nh, const double* const*
     return ms_fit_batch_impl(hs, nh, f_dev, rel_tol, alpha_dev, stats, (cudaStream_t)stream);
 }
 
+ms_status ms_batch_plan_create(ms_hierarchy* const* hs, int nh, const double* const* f_dev, double rel_tol,
+                               double* const* alpha_dev, void* stream, ms_batch_plan** out) {
+    g_err[0] = 0;
+    if (!out) { ms_set_error(MS_ERR_ARG, "out must not be NULL"); return MS_ERR_ARG; }
+    *out = nullptr;
+    if (!hs || !f_dev || !alpha_dev || nh < 1) {
+        ms_set_error(MS_ERR_ARG, "hs, f_dev and alpha_dev must not be NULL and nh >= 1 (got %d)", nh);
+        return MS_ERR_ARG;
+    }
+    if (!(rel_tol > 0.0 && rel_tol < 1.0)) { ms_set_error(MS_ERR_ARG, "rel_tol must be in (0, 1) (got %g)", rel_tol); return MS_ERR_ARG; }
+    for (int i = 0; i < nh; ++i)
+        if (!hs[i] || !f_dev[i] || !alpha_dev[i]) {
+            ms_set_error(MS_ERR_ARG, "hierarchy %d: handle, f and alpha must not be NULL", i);
+            return MS_ERR_ARG;
+        }
+    return ms_batch_plan_create_impl(hs, nh, f_dev, rel_tol, alpha_dev, (cudaStream_t)stream, out);
+}
+
+ms_status ms_batch_plan_launch(ms_batch_plan* plan, void* stream, int use_graph) {
+    g_err[0] = 0;
+    if (!plan) { ms_set_error(MS_ERR_ARG, "plan must not be NULL"); return MS_ERR_ARG; }
+    return ms_batch_plan_launch_impl(plan, (cudaStream_t)stream, use_graph ? 1 : 0);
+}
+
+ms_status ms_batch_plan_stats(ms_batch_plan* plan, void* stream, ms_fit_stats* stats) {
+    g_err[0] = 0;
+    if (!plan) { ms_set_error(MS_ERR_ARG, "plan must not be NULL"); return MS_ERR_ARG; }
+    return ms_batch_plan_stats_impl(plan, (cudaStream_t)stream, stats, -1.f);
+}
+
+void ms_batch_plan_destroy(ms_batch_plan* plan) { ms_batch_plan_free(plan, true); }
+
 ms_status ms_fit_batch(ms_hierarchy* const* hs, int nh, const double* const* f, double rel_tol,
                        double* const* alpha_out, ms_fit_stats* stats) {
     g_err[0] = 0;
@@ -453,12 +488,14 @@ ms_status ms_hierarchy_info(const ms_hierarchy* h, ms_info* info) {
     info->nnz_B = h->B.nnz;
     info->device_bytes = h->device_bytes;
     info->build_ms = h->build_ms;
+    for (int l = 0; l < h->L; ++l) info->tpr_A[l] = ms_tpr_of(h, l);
     return MS_OK;
 }
 
 void ms_destroy(ms_hierarchy* h) {
     if (!h) return;
     cudaDeviceSynchronize();  // the handle's memory returns to the pool: no work may still use it
+    for (ms_batch_plan* p : h->plans) ms_batch_plan_detach(p, h);
     for (int i = 0; i < h->nallocs; ++i) ms_pool_free(h->allocs[i]);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);

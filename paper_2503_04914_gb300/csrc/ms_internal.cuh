@@ -15,6 +15,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cstdio>
 #include <cuda_runtime.h>
 #include <cuda/atomic>
@@ -338,7 +339,10 @@ struct ms_hierarchy {
     double* bytes = nullptr;
     double* tmp64 = nullptr;     // [N] scratch (permutations)
     int solve_blocks = 0;        // cooperative grid size
-    int tpr_A = 8, tpr_B = 32;
+    int tprA_tuned[MS_MAXL] = {};  // autotuned CSR lanes per row of A_l (0 = by rule)
+    int mf_tpp_tuned = 0;          // autotuned matrix-free lanes per point (0 = by rule)
+    bool tuned = false;
+    std::vector<struct ms_batch_plan*> plans;  // live batch plans that hold pointers to the work space
     int64_t device_bytes = 0;
     double build_ms = 0.0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -364,11 +368,24 @@ ms_status ms_evaluate_impl(ms_hierarchy* h, const double* alpha_dev, int nrhs, c
 ms_status ms_fit_batch_impl(ms_hierarchy* const* hs, int nh, const double* const* f_dev, double rel_tol,
                             double* const* alpha_dev, ms_fit_stats* stats, cudaStream_t st);
 
+// CSR lanes per row of A_l used by the solve (ms_solve.cu)
+int ms_tpr_of(const ms_hierarchy* h, int l);
+
 // solve work space for R right-hand sides (ms_solve.cu)
 ms_status ms_ensure_workspace(ms_hierarchy* h, int R);
 
 // learned / exact FSAI preconditioner (ms_precond.cu): build G and G^T for `kind`
 ms_status ms_pc_build(ms_hierarchy* h, int kind, cudaStream_t s);
+// prepared batched fits (ms_batch.cu)
+struct ms_batch_plan;
+ms_status ms_batch_plan_create_impl(ms_hierarchy* const* hs, int nh, const double* const* f_dev, double rel_tol,
+                                    double* const* alpha_dev, cudaStream_t st, ms_batch_plan** out);
+ms_status ms_batch_plan_launch_impl(ms_batch_plan* p, cudaStream_t st, int use_graph);
+ms_status ms_batch_plan_stats_impl(ms_batch_plan* p, cudaStream_t st, ms_fit_stats* stats, float kernel_ms);
+void ms_batch_plan_free(ms_batch_plan* p, bool device_sync);
+void ms_batch_plan_detach(ms_batch_plan* p, const ms_hierarchy* h);  // h is being destroyed
+// with opts.autotune = 1: choose the mat-vec lanes per row of each level once (ms_solve.cu)
+ms_status ms_autotune(ms_hierarchy* h, cudaStream_t st);
 
 // permutation helpers (ms_capi.cu)
 void ms_gather_sorted(const double* in, double* out, const int32_t* perm, int64_t N, int nrhs, int col, cudaStream_t s);

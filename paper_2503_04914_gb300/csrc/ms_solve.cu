@@ -1,27 +1,16 @@
 // The fit of one hierarchy: one persistent cooperative launch per batch of right-hand
-// sides (the schedule itself is in ms_solve_dev.cuh), the stand-alone mat-vecs and the
+// sides (the kernel and its schedule are in ms_solve_dev.cuh), the stand-alone mat-vecs and the
 // allocation-free fit.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "ms_solve_dev.cuh"
 
 namespace {
-
-// MINB: CTAs per SM the kernel is compiled for (1: up to 128 registers a thread,
-// 2: up to 64).  WIDE: the right-hand sides in the row-major (SpMM) layout.
-template <int MODE, int MINB, bool WIDE>
-__global__ void __launch_bounds__(kBS, MINB) k_fit(const __grid_constant__ SolveArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Shared& sh = *reinterpret_cast<Shared*>(smem_raw);
-    if (threadIdx.x == 0) {
-        sh.cta = blockIdx.x;
-        sh.nb = gridDim.x;
-    }
-    __syncthreads();
-    fit_body<MODE, WIDE>(a, sh);
-}
 
 // f (input order, [N][nrhs], columns col0..col0+R-1) -> [N][RW] in sorted order (padding 0),
 // and back for alpha.
@@ -109,6 +98,11 @@ ms_status fit_blocks(bool mixed, int minb, int dev, int* blocks, bool wide = fal
 
 ms_status ms_ensure_workspace(ms_hierarchy* h, int R) {
     if (h->f && h->ws_rhs >= R) return MS_OK;
+    if (!h->plans.empty()) {
+        ms_set_error(MS_ERR_STATE, "the work space must grow to %d right-hand sides, but a batch plan holds it "
+                     "(destroy the plan first)", R);
+        return MS_ERR_STATE;
+    }
     const int64_t n = h->N * (int64_t)R;
     MS_TRY(ms_realloc(h, (void**)&h->f, sizeof(double) * n));
     MS_TRY(ms_realloc(h, (void**)&h->beta, sizeof(double) * n));
@@ -132,7 +126,7 @@ ms_status ms_ensure_workspace(ms_hierarchy* h, int R) {
     int dev = 0;
     MS_CUDA(cudaGetDevice(&dev));
     MS_TRY(fit_blocks(h->opts.precision == MS_PREC_MIXED, ctas_per_sm(h->opts), dev, &h->solve_blocks));
-    h->mf_tpp = mf_tpp_for(h);
+    h->mf_tpp = h->mf_tpp_tuned > 0 ? h->mf_tpp_tuned : mf_tpp_for(h);
     const int V = R * h->L;
     MS_TRY(ms_realloc(h, (void**)&h->part, sizeof(double) * kAcc * V * h->solve_blocks));
     MS_TRY(ms_realloc(h, (void**)&h->gpart, sizeof(double) * kMaxGroups * kAcc * V));
@@ -148,6 +142,155 @@ ms_status ms_ensure_workspace(ms_hierarchy* h, int R) {
         MS_TRY(ms_alloc(h, (void**)&h->pcfb, sizeof(int) * 2));
     }
     h->ws_rhs = R;
+    return MS_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+//
+// The CSR mat-vec of a level gives each row S lanes (S a power of two); the rule
+// tpr_for (about 16 entries a lane) is a good guess but the best S depends on the
+// row count, the entries per row and the precision.  With opts.autotune = 1 the first
+// fit of a handle times a stand-in for the solve kernel's mat-vec phase (k_tune_matvec:
+// the solve grid, 256-row chunks dealt round-robin to the CTAs, S lanes per row) on
+// every level of at least kTuneMinRows rows for S = 1, 2, ..., 32 (matrix-free
+// operator: the lanes per target point, 1 to 8, over all levels) and keeps the
+// fastest.  Choices are cached for the process, keyed by the level's shape, so later
+// handles of the same shape skip the timing.
+
+int ms_tpr_of(const ms_hierarchy* h, int l) {
+    if (h->opts.threads_per_row > 0) return h->opts.threads_per_row;
+    if (h->tprA_tuned[l] > 0) return h->tprA_tuned[l];
+    const int64_t n = h->view.off[l + 1] - h->view.off[l];
+    return tpr_for((double)(h->rpA_lv[l + 1] - h->rpA_lv[l]) / (double)std::max<int64_t>(n, 1));
+}
+
+namespace {
+
+template <typename TV, typename TX>
+__global__ void __launch_bounds__(kBS) k_tune_matvec(const int64_t* rp, const int32_t* col, const TV* val,
+                                                     const TX* x, TX* y, int64_t r0, int64_t r1, int S) {
+    const int64_t nch = (r1 - r0 + kChunk - 1) / kChunk;
+    for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        const int64_t a0 = r0 + c * kChunk, a1 = min(a0 + (int64_t)kChunk, r1);
+        rows_by_subwarp(a0, a1, S, [&](int64_t row, bool ok, int sl) {
+            int64_t s = 0, e = 0;
+            if (ok) { s = rp[row]; e = rp[row + 1]; }
+            const TX v = csr_row<TV, TX, TX>(col, val, x, s, e, sl, S);
+            if (ok && sl == 0) y[row] = v;
+        });
+    }
+}
+
+constexpr int64_t kTuneMinRows = 4096;
+constexpr int kTuneWarm = 2, kTuneReps = 5;
+
+// (op, d, wendland d, wendland k, mixed, log2 rows, entries per row rounded) -> lanes
+using TuneKey = std::tuple<int, int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune_cache;
+
+TuneKey tune_key(const ms_hierarchy* h, int64_t rows, double per_row) {
+    int lg = 0;
+    while ((int64_t(1) << (lg + 1)) <= rows) ++lg;
+    return TuneKey(h->opts.op, h->d, h->opts.wendland_d, h->opts.wendland_k,
+                   h->opts.precision == MS_PREC_MIXED ? 1 : 0, lg, (int)std::lround(per_row));
+}
+
+// Time `launch` kTuneReps times after kTuneWarm untimed runs; milliseconds in *ms.
+template <typename F>
+ms_status time_launches(cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, F launch, float* ms) {
+    for (int i = 0; i < kTuneWarm; ++i) launch();
+    MS_CUDA(cudaEventRecord(e0, st));
+    for (int i = 0; i < kTuneReps; ++i) launch();
+    MS_CUDA(cudaEventRecord(e1, st));
+    MS_CUDA(cudaEventSynchronize(e1));
+    MS_CUDA(cudaGetLastError());
+    MS_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    return MS_OK;
+}
+
+ms_status autotune_run(ms_hierarchy* h, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+    const bool mixed = h->opts.precision == MS_PREC_MIXED;
+    const int64_t N = h->N;
+    float* x32 = h->r32;  // scratch: the fit overwrites every work vector before it reads it
+    MS_CUDA(cudaMemsetAsync(h->r, 0, sizeof(double) * N, st));
+    if (mixed) MS_CUDA(cudaMemsetAsync(x32, 0, sizeof(float) * N, st));
+    if (h->opts.op == MS_OP_MATRIX_FREE) {
+        if (!mixed) return MS_OK;  // the FP64 fit reads the CSR matrix
+        const int64_t rows = N;
+        const TuneKey key = tune_key(h, rows, (double)h->total_cells);
+        {
+            std::lock_guard<std::mutex> g(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) { h->mf_tpp_tuned = it->second; return MS_OK; }
+        }
+        const MFView v = make_mfview(h);
+        int best = 0;
+        float best_ms = 0.f;
+        for (int t = 1; t <= 8; t <<= 1) {
+            float ms = 0.f;
+            MS_TRY(time_launches(st, e0, e1, [&] {
+                k_mf_apply<<<nblk(h->total_cells * 32, 256), 256, 0, st>>>(v, x32, h->q, t, h->total_cells);
+                ms_count_launch();
+            }, &ms));
+            if (best == 0 || ms < best_ms) { best = t; best_ms = ms; }
+        }
+        h->mf_tpp_tuned = best;
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune_cache[key] = best;
+        return MS_OK;
+    }
+    for (int l = 0; l < h->L; ++l) {
+        const int64_t r0 = h->view.off[l], n = h->view.off[l + 1] - r0;
+        if (n < kTuneMinRows) continue;
+        const double per_row = (double)(h->rpA_lv[l + 1] - h->rpA_lv[l]) / (double)n;
+        const TuneKey key = tune_key(h, n, per_row);
+        {
+            std::lock_guard<std::mutex> g(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) { h->tprA_tuned[l] = it->second; continue; }
+        }
+        int best = 0;
+        float best_ms = 0.f;
+        const int blocks = std::max(h->solve_blocks, 1);
+        for (int S = 1; S <= 32; S <<= 1) {
+            float ms = 0.f;
+            MS_TRY(time_launches(st, e0, e1, [&] {
+                if (mixed)
+                    k_tune_matvec<float, float><<<blocks, kBS, 0, st>>>(h->A.rp, h->A.col, h->A.v32, x32, h->q32,
+                                                                         r0, r0 + n, S);
+                else
+                    k_tune_matvec<double, double><<<blocks, kBS, 0, st>>>(h->A.rp, h->A.col, h->A.v64, h->r, h->q,
+                                                                           r0, r0 + n, S);
+                ms_count_launch();
+            }, &ms));
+            if (best == 0 || ms < best_ms) { best = S; best_ms = ms; }
+        }
+        h->tprA_tuned[l] = best;
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    return MS_OK;
+}
+
+}  // namespace
+
+// Runs the autotuner once per handle (after a build, when opts.autotune = 1).
+ms_status ms_autotune(ms_hierarchy* h, cudaStream_t st) {
+    if (!h->opts.autotune || h->tuned) return MS_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MS_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        ms_set_error(MS_ERR_CUDA, "cudaEventCreate failed");
+        return MS_ERR_CUDA;
+    }
+    const ms_status s = autotune_run(h, st, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != MS_OK) return s;
+    h->tuned = true;
+    h->mf_tpp = h->mf_tpp_tuned > 0 ? h->mf_tpp_tuned : h->mf_tpp;
     return MS_OK;
 }
 
@@ -172,6 +315,7 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
         }
         MS_TRY(ms_pc_build(h, h->opts.precond, st));
     }
+    MS_TRY(ms_autotune(h, st));
 
     ms_status result = MS_OK;
     int launches = 0;

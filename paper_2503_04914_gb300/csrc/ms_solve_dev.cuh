@@ -1238,7 +1238,20 @@ __device__ __forceinline__ void fit_body(const SolveArgs& a, Shared& sh) {
     }
 }
 
-
+// The persistent solve kernel of one hierarchy.  MINB: CTAs per SM the kernel is
+// compiled for (1: up to 128 registers a thread, 2: up to 64).  WIDE: the right-hand
+// sides in the row-major (SpMM) layout.
+template <int MODE, int MINB, bool WIDE>
+__global__ void __launch_bounds__(kBS, MINB) k_fit(const __grid_constant__ SolveArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Shared& sh = *reinterpret_cast<Shared*>(smem_raw);
+    if (threadIdx.x == 0) {
+        sh.cta = blockIdx.x;
+        sh.nb = gridDim.x;
+    }
+    __syncthreads();
+    fit_body<MODE, WIDE>(a, sh);
+}
 
 // ---------------------------------------------------------------- host helpers
 
@@ -1322,7 +1335,9 @@ void fill_args(const ms_hierarchy* h, double rel_tol, int R, SolveArgs& a, bool 
         const int64_t n = h->view.off[l + 1] - h->view.off[l];
         a.nnzA[l] = rpA[l + 1] - rpA[l];
         a.nnzB[l] = rpB[l + 1] - rpB[l];
-        a.tprA[l] = h->opts.threads_per_row > 0 ? h->opts.threads_per_row : tpr_for((double)a.nnzA[l] / n);
+        a.tprA[l] = h->opts.threads_per_row > 0 ? h->opts.threads_per_row
+                    : h->tprA_tuned[l] > 0       ? h->tprA_tuned[l]
+                                                 : tpr_for((double)a.nnzA[l] / n);
         a.tprB[l] = tpr_for((double)a.nnzB[l] / n);
     }
     a.Arp = h->A.rp; a.Acol = h->A.col; a.Av64 = h->A.v64; a.Av32 = h->A.v32;

@@ -30,7 +30,8 @@ STATUS_NAMES = {0: "MS_OK", 1: "MS_ERR_ARG", 2: "MS_ERR_CUDA", 3: "MS_ERR_OOM", 
 
 # the symbols include/ms.h declares (checked by the tests)
 EXPORTED = ["ms_default_opts", "ms_build_hierarchy", "ms_build_hierarchy_dev", "ms_fit", "ms_fit_dev",
-            "ms_fit_static_dev", "ms_fit_batch", "ms_fit_batch_dev", "ms_default_train_opts", "ms_train_precond", "ms_precond_params",
+            "ms_fit_static_dev", "ms_fit_batch", "ms_fit_batch_dev", "ms_batch_plan_create", "ms_batch_plan_launch",
+            "ms_batch_plan_stats", "ms_batch_plan_destroy", "ms_default_train_opts", "ms_train_precond", "ms_precond_params",
             "ms_precond_inspect", "ms_evaluate", "ms_evaluate_dev", "ms_apply_dev", "ms_get_permutation", "ms_hierarchy_info",
             "ms_launch_count", "ms_last_error", "ms_destroy"]
 
@@ -40,7 +41,7 @@ class ms_opts(C.Structure):
                 ("precision", C.c_int), ("precond", C.c_int), ("max_iters", C.c_int),
                 ("jacobi_sweeps", C.c_int), ("inter_tol", C.c_double), ("inner_tol", C.c_double),
                 ("cell_split", C.c_int), ("threads_per_row", C.c_int), ("lower_fp32", C.c_int),
-                ("solve_ctas_per_sm", C.c_int), ("reserved", C.c_int * 6)]
+                ("solve_ctas_per_sm", C.c_int), ("autotune", C.c_int), ("reserved", C.c_int * 5)]
 
 
 class ms_fit_stats(C.Structure):
@@ -67,7 +68,7 @@ class ms_info(C.Structure):
     _fields_ = [("d", C.c_int32), ("L", C.c_int32), ("N", C.c_int64),
                 ("n_per_level", C.c_int64 * MS_MAX_LEVELS), ("delta", C.c_double * MS_MAX_LEVELS),
                 ("nnz_A", C.c_int64), ("nnz_B", C.c_int64), ("device_bytes", C.c_int64),
-                ("build_ms", C.c_double)]
+                ("build_ms", C.c_double), ("tpr_A", C.c_int32 * MS_MAX_LEVELS)]
 
 
 class ms_train_opts(C.Structure):
@@ -120,6 +121,12 @@ def load(path: str | None = None):
                                  C.POINTER(ms_fit_stats)]
     lib.ms_fit_batch_dev.argtypes = [C.POINTER(_P), C.c_int, C.POINTER(C.c_void_p), C.c_double,
                                      C.POINTER(C.c_void_p), C.POINTER(ms_fit_stats), _P]
+    lib.ms_batch_plan_create.argtypes = [C.POINTER(_P), C.c_int, C.POINTER(C.c_void_p), C.c_double,
+                                         C.POINTER(C.c_void_p), _P, C.POINTER(_P)]
+    lib.ms_batch_plan_launch.argtypes = [_P, _P, C.c_int]
+    lib.ms_batch_plan_stats.argtypes = [_P, _P, C.POINTER(ms_fit_stats)]
+    lib.ms_batch_plan_destroy.argtypes = [_P]
+    lib.ms_batch_plan_destroy.restype = None
     lib.ms_default_train_opts.argtypes = [C.POINTER(ms_train_opts)]
     lib.ms_default_train_opts.restype = None
     lib.ms_train_precond.argtypes = [_P, C.POINTER(C.c_int), C.c_int, C.POINTER(ms_train_opts),
@@ -137,7 +144,7 @@ def load(path: str | None = None):
     lib.ms_destroy.restype = None
     for name in EXPORTED:
         if name not in ("ms_default_opts", "ms_last_error", "ms_destroy", "ms_launch_count",
-                        "ms_default_train_opts"):
+                        "ms_default_train_opts", "ms_batch_plan_destroy"):
             getattr(lib, name).restype = C.c_int  # ms_status
     lib.ms_launch_count.argtypes = []
     lib.ms_launch_count.restype = C.c_uint64
@@ -255,6 +262,43 @@ def ms_fit_batch(handles, fs, rel_tol=1e-10, alpha_out=None, stream=None):
     return outs, [s.as_dict() for s in st]
 
 
+class BatchPlan:
+    """A prepared batched fit (ms_batch_plan_*): binds the device tensors fs[i] (right-hand
+    sides, input order) and alphas[i] (coefficients, written by each launch)."""
+
+    def __init__(self, handles, fs, rel_tol=1e-10, alphas=None, stream=None):
+        import torch
+        lib = load()
+        self.nh = len(handles)
+        self.fs = fs
+        self.alphas = alphas if alphas is not None else [torch.empty_like(f) for f in fs]
+        hs = (_P * self.nh)(*[C.c_void_p(h) for h in handles])
+        fp = (C.c_void_p * self.nh)(*[_dev_ptr(f) for f in fs])
+        ap = (C.c_void_p * self.nh)(*[_dev_ptr(a) for a in self.alphas])
+        out = _P()
+        _check(lib.ms_batch_plan_create(hs, self.nh, fp, rel_tol, ap, _stream(stream), C.byref(out)))
+        self.plan = out.value
+
+    def launch(self, stream=None, use_graph=False):
+        _check(load().ms_batch_plan_launch(C.c_void_p(self.plan), _stream(stream), int(bool(use_graph))))
+
+    def stats(self, stream=None):
+        st = (ms_fit_stats * self.nh)()
+        _check(load().ms_batch_plan_stats(C.c_void_p(self.plan), _stream(stream), st))
+        return [s.as_dict() for s in st]
+
+    def close(self):
+        if self.plan:
+            load().ms_batch_plan_destroy(C.c_void_p(self.plan))
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def ms_evaluate(handle, alpha, query, out=None, stream=None):
     lib = load()
     nrhs = 1 if alpha.ndim == 1 else alpha.shape[1]
@@ -294,7 +338,8 @@ def ms_hierarchy_info(handle) -> dict:
     L = info.L
     return {"d": info.d, "L": L, "N": info.N, "n_per_level": list(info.n_per_level[:L]),
             "delta": list(info.delta[:L]), "nnz_A": info.nnz_A, "nnz_B": info.nnz_B,
-            "device_bytes": info.device_bytes, "build_ms": info.build_ms}
+            "device_bytes": info.device_bytes, "build_ms": info.build_ms,
+            "tpr_A": list(info.tpr_A[:L])}
 
 
 def ms_default_train_opts(**overrides) -> ms_train_opts:

@@ -118,3 +118,97 @@ def test_batch_is_faster_than_single_fits():
     assert st[0]["fit_ms"] < 0.5 * t_single, (st[0]["fit_ms"], t_single)
     for H in Hs:
         H.close()
+
+
+def _plan_setup(seed0, prec=ms.MS_PREC_MIXED):
+    import torch
+    ws = [hierarchy(s, seed0 + i) for i, s in enumerate(SIZES)]
+    Hs = [ms.Hierarchy.from_workload(w, precision=prec) for w in ws]
+    fs = [torch.from_numpy(w.f).cuda() for w in ws]
+    return ws, Hs, fs
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_plan_matches_batch_fit_and_replays(use_graph):
+    """A prepared plan gives the batched fit's coefficients bitwise (same partition, same
+    arithmetic), launch after launch, and picks up new values in the bound buffers."""
+    import torch
+    ws, Hs, fs = _plan_setup(700)
+    handles = [H.handle for H in Hs]
+    ref, _ = ms.ms_fit_batch(handles, [w.f for w in ws], rel_tol=1e-12)
+    plan = ms.BatchPlan(handles, fs, rel_tol=1e-12)
+    for _ in range(3):
+        plan.launch(use_graph=use_graph)
+        st = plan.stats()
+        for i in range(len(ws)):
+            assert np.array_equal(plan.alphas[i].cpu().numpy(), ref[i]), i
+            assert st[i]["device_status"] == 0 and max(st[i]["rel_residual"]) <= 1e-12
+    # new right-hand sides in the same buffers
+    rng = np.random.default_rng(5)
+    new = [rng.standard_normal(w.N) for w in ws]
+    for f, v in zip(fs, new):
+        f.copy_(torch.from_numpy(v))
+    plan.launch(use_graph=use_graph)
+    plan.stats()
+    ref2, _ = ms.ms_fit_batch(handles, new, rel_tol=1e-12)
+    for i, w in enumerate(ws):
+        a = plan.alphas[i].cpu().numpy()
+        assert np.array_equal(a, ref2[i]), i
+        o, _ = om.fit_sequential(w.levels, new[i], w.h, w.nu, w.wendland_d, w.wendland_k)
+        assert rel(a, np.concatenate(o)) <= 1e-8, i
+    plan.close()
+    for H in Hs:
+        H.close()
+
+
+def test_batch_plan_captured_by_the_caller_into_a_cuda_graph():
+    import torch
+    ws, Hs, fs = _plan_setup(720, prec=ms.MS_PREC_FP64)
+    handles = [H.handle for H in Hs]
+    ref, _ = ms.ms_fit_batch(handles, [w.f for w in ws], rel_tol=1e-12)
+    plan = ms.BatchPlan(handles, fs, rel_tol=1e-12)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.launch(stream=s.cuda_stream)
+    for a in plan.alphas:
+        a.zero_()
+    torch.cuda.synchronize()
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    st = plan.stats()
+    for i in range(len(ws)):
+        assert np.array_equal(plan.alphas[i].cpu().numpy(), ref[i]), i
+        assert st[i]["device_status"] == 0
+    del g
+    plan.close()
+    for H in Hs:
+        H.close()
+
+
+def test_batch_plan_guards():
+    import torch
+    ws, Hs, fs = _plan_setup(740, prec=ms.MS_PREC_FP64)
+    handles = [H.handle for H in Hs]
+    with pytest.raises(ms.MsError) as e:  # a hierarchy twice would share its work space
+        ms.BatchPlan([handles[0], handles[0]], [fs[0], fs[0].clone()])
+    assert e.value.status == ms.MS_ERR_ARG
+    plan = ms.BatchPlan(handles, fs, rel_tol=1e-12)
+    # the work space of a planned hierarchy cannot grow (3 right-hand sides after 1)
+    w = ws[0]
+    F = np.stack([w.f, 2 * w.f, -w.f], axis=1)
+    with pytest.raises(ms.MsError) as e:
+        Hs[0].fit(F, rel_tol=1e-12)
+    assert e.value.status == ms.MS_ERR_STATE
+    a1, _ = Hs[0].fit(w.f, rel_tol=1e-12)  # one right-hand side fits in the existing space
+    # destroying a hierarchy invalidates the plan
+    Hs[1].close()
+    with pytest.raises(ms.MsError) as e:
+        plan.launch()
+    assert e.value.status == ms.MS_ERR_STATE
+    plan.close()
+    aF, _ = Hs[0].fit(F, rel_tol=1e-12)  # the plan is gone: the space may grow again
+    assert rel(aF[:, 0], a1) <= 1e-10
+    for H in Hs:
+        H.close()

@@ -65,6 +65,7 @@ def test_struct_sizes_match_header(lib):
     (2, 1, [4], [0.1], {"wendland_k": 7}, ms.MS_ERR_ARG),
     (3, 1, [4], [0.1], {"wendland_d": 2}, ms.MS_ERR_ARG),
     (2, 1, [4], [0.1], {"threads_per_row": 3}, ms.MS_ERR_ARG),
+    (2, 1, [4], [0.1], {"autotune": 2}, ms.MS_ERR_ARG),
 ])
 def test_invalid_arguments_rejected_on_host(lib, d, L, n, h, over, code):
     opts = ms.ms_default_opts(**over)

@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--levels", type=int, default=8)
     p.add_argument("--query-side", type=int, default=256)
-    p.add_argument("--train-epochs", type=int, default=300)
+    p.add_argument("--train-epochs", type=int, default=100)
     p.add_argument("--cpu-levels", type=int, default=6, help="levels of the oracle's bounded sample")
     p.add_argument("--ref-levels", type=int, default=5, help="levels per step of the reference arm")
     p.add_argument("--no-cpu", action="store_true")
@@ -302,7 +302,7 @@ def run_ours(args):
         out["roofline"] = {"kernel": "k_fit<MIXED> (persistent Jacobi / learned-PCG solve)", "bound": "hbm",
                            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                            "peak_kind": f"{peak_kind} hbm_gbs",
-                           "traffic": recorded_traffic() if args.levels == 8 and args.train_epochs == 300 else None,
+                           "traffic": recorded_traffic() if args.levels == 8 and args.train_epochs == 100 else None,
                            "traffic_source": "profiles/k_fit_learned_halton8.md (1-pass ncu capture of this workload)",
                            "algorithmic_bytes_per_launch": fit_bytes, "launch_ms": fit_ms}
         out["learned_pcg"] = summary(recs)
@@ -310,7 +310,7 @@ def run_ours(args):
                             "fit_kernel": fit_ms, "evaluate": statistics.mean(r["eval"] for r in recs)}
         out["phases_ms"]["fit_incl_precond"] = (out["learned_pcg"]["ms_per_step"] - out["phases_ms"]["build"]
                                                 - out["phases_ms"]["evaluate"])
-        out["train"] = {"levels": [1, 2, 3, 4], "epochs": args.train_epochs, **train}
+        out["train"] = {"levels": [1, 2, 3, 4], "epochs": args.train_epochs, "extra_patches_per_point": 4, **train}
         out["nnz"] = {"A": info["nnz_A"], "B": info["nnz_B"]}
 
         if not args.no_variants:

@@ -360,7 +360,7 @@ ms_status ms_hierarchy_info(const ms_hierarchy* h, ms_info* info);
  * BF16-valued weights with FP32 accumulation; training is Adam on FP32 master weights
  * whose forward and backward passes use the BF16-rounded copies. */
 typedef struct ms_train_opts {
-    int epochs;          /* passes over the training patches (default 300) */
+    int epochs;          /* passes over the training patches (default 100) */
     int batch;           /* samples per Adam step, a multiple of 64 (default 512) */
     double lr;           /* initial learning rate (default 3e-3), cosine-decayed to lr_final */
     double lr_final;     /* default 1e-4 */
@@ -368,11 +368,17 @@ typedef struct ms_train_opts {
     int fp32_weights;    /* 1: train and infer with the FP32 master weights (no BF16 rounding) */
     float input_noise;   /* training inputs jittered by input_noise * U[-1, 1) per coordinate
                             (units of delta; default 0.005; 0 = off) */
-    int reserved[6];
+    int augment;         /* extra training patches per point, 0..16 (default 4): draw r of point i
+                            (level-local input index i of a level of n points) takes the 16
+                            nearest points j != i within delta among the level's first p points,
+                            p = i + 1 + min(floor(u (n - i)), n - i - 1), u = the SplitMix64
+                            uniform draw (top 53 bits / 2^53) of seed ^ 0x6175676D656E74 with
+                            counter r N + (global input index of i), N = the hierarchy's points */
+    int reserved[5];
 } ms_train_opts;
 
 typedef struct ms_train_stats {
-    int64_t samples;     /* training patches (all points of the chosen levels) */
+    int64_t samples;     /* training patches: (1 + augment) x the points of the chosen levels */
     int64_t steps;       /* Adam steps taken */
     double loss_first;   /* mean squared error of the first and of the last step's batch */
     double loss_last;
@@ -401,8 +407,15 @@ enum {
     MS_INSPECT_PATTERN = 0, /* int32 [N][16]: pattern neighbours (input indices), -1 = none */
     MS_INSPECT_TARGETS = 1, /* double [N][17]: exact scale-free rows ghat (zeros past the pattern) */
     MS_INSPECT_PREDICT = 2, /* float [N][17]: the network's rows ghat */
-    MS_INSPECT_GRAD = 3     /* float [n_weights + 1]: full-batch gradient of the training loss on
-                               `levels` with the FP32 master weights, then the loss */
+    MS_INSPECT_GRAD = 3,    /* float [n_weights + 1]: full-batch gradient of the training loss on
+                               the patterns of `levels` (no extra patches) with the FP32 master
+                               weights, then the loss */
+    MS_INSPECT_PATCHES = 4  /* int32 [S][18]: the training patches of `levels` with the options of
+                               the last ms_train_precond (defaults before any): per patch its
+                               centre, its prefix bound p (level-local; p = centre for the
+                               pattern) and 16 neighbours (input indices, -1 = none); S =
+                               (1 + augment) x the points of `levels`, patterns first, then
+                               draw 0, 1, ... each in level order, points in input order */
 };
 ms_status ms_precond_inspect(ms_hierarchy* h, int what, const int* levels, int n_levels, void* out, int64_t n_out);
 

@@ -300,6 +300,8 @@ struct Precond {
     float* gt_val = nullptr;     // [nnz]
     int64_t gt_nnz = 0;
     int fp32_weights = 0;
+    int augment = 4;                     // extra training patches per point (last training)
+    uint64_t seed = 2503049140ull;       // seed of the last training
 };
 
 struct ms_hierarchy {

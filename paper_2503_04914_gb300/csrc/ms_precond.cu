@@ -57,17 +57,18 @@ __device__ __forceinline__ bool key_less(double d2a, int32_t pa, double d2b, int
 
 // ---------------------------------------------------------------- pattern
 
-__global__ void k_pc_pattern(HierView v, const int64_t* Arp, const int32_t* Acol, const int32_t* perm, int32_t* nbr) {
-    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= v.N) return;
-    const int32_t ps = perm[s];
+// The (up to) 16 nearest points c != s of sorted row s's level with input index below
+// `bound` and |x_c - x_s| < delta (candidates: A's row s), nearest first, ties by input
+// index.  bound = perm[s] gives the pattern of s; a larger bound an extra training patch.
+__device__ void nearest_below(const HierView& v, const int64_t* Arp, const int32_t* Acol, const int32_t* perm,
+                              int64_t s, int64_t bound, int32_t* out) {
     double bd[kPcK];
     int32_t bp[kPcK], bc[kPcK];
     int cnt = 0;
     for (int64_t k = Arp[s]; k < Arp[s + 1]; ++k) {
         const int32_t c = Acol[k];
         const int32_t pc = perm[c];
-        if (pc >= ps) continue;
+        if (pc >= bound || c == s) continue;
         const double d = dist2_rn(v, c, s);
         // insertion into the sorted list keyed by (distance, input index); bd holds squared
         // distances, compared through key_less as their correctly rounded roots
@@ -83,21 +84,36 @@ __global__ void k_pc_pattern(HierView v, const int64_t* Arp, const int32_t* Acol
             if (cnt < kPcK) ++cnt;
         }
     }
-    for (int i = 0; i < kPcK; ++i) nbr[s * kPcK + i] = i < cnt ? bc[i] : -1;
+    for (int i = 0; i < kPcK; ++i) out[i] = i < cnt ? bc[i] : -1;
+}
+
+__global__ void k_pc_pattern(HierView v, const int64_t* Arp, const int32_t* Acol, const int32_t* perm, int32_t* nbr) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= v.N) return;
+    nearest_below(v, Arp, Acol, perm, s, perm[s], nbr + s * kPcK);
+}
+
+// Neighbours of training patch i: centre rows[i], input-index bound bounds[i]; out [n][16].
+__global__ void k_pc_patches(HierView v, const int64_t* Arp, const int32_t* Acol, const int32_t* perm,
+                             const int64_t* rows, const int64_t* bounds, int64_t n, int32_t* out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    nearest_below(v, Arp, Acol, perm, rows[i], bounds[i], out + i * kPcK);
 }
 
 // ---------------------------------------------------------------- exact rows (FP64)
 
-// Scale-free FSAI row of sorted row s (self first, zeros past the pattern):
-// K = phi(|x_a - x_b| / delta) on the patch, K z = e_1 by Cholesky, ghat = z / sqrt(z_0).
-__device__ void pc_exact_row(const HierView& v, const int32_t* nbr, int64_t s, double* ghat) {
+// Scale-free FSAI row of the patch centred on sorted row s with neighbours nb[0..15]
+// (self first, zeros past the patch): K = phi(|x_a - x_b| / delta) on the patch, K z = e_1
+// by Cholesky, ghat = z / sqrt(z_0).
+__device__ void pc_exact_row(const HierView& v, const int32_t* nb, int64_t s, double* ghat) {
     const int l = level_of_row(v.off, v.L, s);
     const double inv = 1.0 / v.delta[l];
     int64_t P[kPcOut];
     int m = 1;
     P[0] = s;
     for (int i = 0; i < kPcK; ++i) {
-        const int32_t c = nbr[s * kPcK + i];
+        const int32_t c = nb[i];
         if (c >= 0) P[m++] = c;
     }
     double L[kPcOut * kPcOut];
@@ -136,14 +152,15 @@ __device__ void pc_exact_row(const HierView& v, const int32_t* nbr, int64_t s, d
     for (int a = 0; a < m; ++a) ghat[a] = z[a] * sc;
 }
 
-// rows[i] (sorted positions; rows == nullptr: row = i) -> ghat[i][17]; optional G values.
+// Patch i -> ghat[i][17]; optional G values.  rows == nullptr: patch i is the pattern of
+// sorted row i (nbr [N][16]); else it is centred on rows[i] with neighbours nbr[i][16].
 __global__ void k_pc_exact(HierView v, const int32_t* nbr, const int64_t* rows, int64_t n, double* ghat_out,
                            float* gval, int32_t* gcol) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t s = rows ? rows[i] : i;
     double g[kPcOut];
-    pc_exact_row(v, nbr, s, g);
+    pc_exact_row(v, nbr + i * kPcK, s, g);
     if (ghat_out)
         for (int a = 0; a < kPcOut; ++a) ghat_out[i * kPcOut + a] = g[a];
     if (gval) {
@@ -168,17 +185,17 @@ __global__ void k_pc_exact(HierView v, const int32_t* nbr, const int64_t* rows, 
 // the last axis flipped so that o_d has a non-negative coordinate on it (d = 1: o_1 > 0).
 // The kernel is radial, so the exact row does not depend on the frame.  FP64 arithmetic, so
 // the frame's sign decisions are those of the FP64 oracle.
-__device__ __forceinline__ int pc_features(const HierView& v, const int32_t* nbr, int64_t s, float* z) {
+__device__ __forceinline__ int pc_features(const HierView& v, const int32_t* nb, int64_t s, float* z) {
     const int l = level_of_row(v.off, v.L, s);
     const double inv = 1.0 / v.delta[l];
     const int d = v.d;
     auto offset = [&](int k, double* o) {
-        const int32_t c = nbr[s * kPcK + k];
+        const int32_t c = nb[k];
         for (int a = 0; a < 3; ++a) o[a] = (a < d && c >= 0) ? (v.X[a * v.N + c] - v.X[a * v.N + s]) * inv : 0.0;
         return c >= 0;
     };
     int cnt = 0;
-    for (int k = 0; k < kPcK; ++k) cnt += nbr[s * kPcK + k] >= 0;
+    for (int k = 0; k < kPcK; ++k) cnt += nb[k] >= 0;
     double e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
     double o1[3], o2[3], o3[3];
     offset(0, o1);
@@ -237,18 +254,19 @@ __device__ __forceinline__ int pc_features(const HierView& v, const int32_t* nbr
     return cnt;
 }
 
+// Features of sample i: centre rows[i], neighbours nbr[i][16].
 __global__ void k_pc_features(HierView v, const int32_t* nbr, const int64_t* rows, int64_t n, float* Z, int32_t* cnt) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     float z[kPcK * 3];
-    const int c = pc_features(v, nbr, rows[i], z);
+    const int c = pc_features(v, nbr + i * kPcK, rows[i], z);
     const int nin = kPcK * v.d;
     for (int k = 0; k < nin; ++k) Z[i * nin + k] = z[k];
     cnt[i] = c;
 }
 
-// Scaled patch matrix K = phi(|x_a - x_b| / delta) of sample i (self first, zero-padded to 17x17):
-// the metric of the training loss.
+// Scaled patch matrix K = phi(|x_a - x_b| / delta) of sample i (centre rows[i] first, then its
+// neighbours nbr[i][16]; zero-padded to 17x17): the metric of the training loss.
 __global__ void k_pc_patchK(HierView v, const int32_t* nbr, const int64_t* rows, int64_t n, float* K) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -259,7 +277,7 @@ __global__ void k_pc_patchK(HierView v, const int32_t* nbr, const int64_t* rows,
     int m = 1;
     P[0] = s;
     for (int k = 0; k < kPcK; ++k) {
-        const int32_t c = nbr[s * kPcK + k];
+        const int32_t c = nbr[i * kPcK + k];
         if (c >= 0) P[m++] = c;
     }
     float* Ki = K + i * kPcOut * kPcOut;
@@ -360,7 +378,7 @@ __global__ void k_pc_infer(HierView v, const int32_t* nbr, const float* theta, i
     if (s >= v.N) return;
     const NetLayout N = net_layout(kPcK * v.d);
     float z[kPcK * 3], o[kPcOut];
-    const int cnt = pc_features(v, nbr, s, z);
+    const int cnt = pc_features(v, nbr + s * kPcK, s, z);
     mlp_forward(N, W, z, o);
     float g[kPcOut];
     for (int m = 0; m < kPcOut; ++m) g[m] = m <= cnt ? fmaf(ms[kPcOut + m], o[m], ms[m]) : 0.f;
@@ -720,7 +738,8 @@ struct TrainSet {
     float *Z = nullptr, *T = nullptr, *K = nullptr;
     int32_t* cnt = nullptr;
     double* ghat = nullptr;
-    int64_t* rows = nullptr;
+    int64_t* rows = nullptr;   // centre (sorted row) of each patch
+    int32_t* nbr = nullptr;    // [S][16] neighbours of each patch (sorted rows, -1 = none)
     ~TrainSet() {
         for (void* p : bufs) cudaFree(p);
     }
@@ -735,23 +754,68 @@ struct TrainSet {
     }
 };
 
-ms_status make_trainset(ms_hierarchy* h, const int* levels, int n, bool set_moments, TrainSet& ts, cudaStream_t st) {
+constexpr uint64_t kAugSalt = 0x6175676D656E74ull;
+
+// Training patches of the given levels: the pattern of every point (in input order), then
+// `augment` extra patches per point (draw r: the nearest points below a random prefix bound).
+// centre[i] / bound[i]: sorted row and input-index bound of patch i (host copies).
+ms_status patch_list(ms_hierarchy* h, const int* levels, int n, int augment, uint64_t seed,
+                     std::vector<int64_t>& centre, std::vector<int64_t>& bound) {
+    centre.clear();
+    bound.clear();
+    std::vector<int64_t> lvl;  // level of each pattern patch
+    for (int a = 0; a < n; ++a) {
+        const int l = levels[a];
+        const int64_t o = h->view.off[l], nl = h->view.off[l + 1] - o;
+        std::vector<int32_t> perm(nl);
+        MS_CUDA(cudaMemcpy(perm.data(), h->perm + o, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost));
+        std::vector<int64_t> inv(nl);
+        for (int64_t k = 0; k < nl; ++k) inv[perm[k] - o] = o + k;  // input index -> sorted row
+        for (int64_t k = 0; k < nl; ++k) {
+            centre.push_back(inv[k]);
+            bound.push_back(o + k);
+            lvl.push_back(l);
+        }
+    }
+    const int64_t S0 = (int64_t)centre.size();
+    for (int r = 0; r < augment; ++r)
+        for (int64_t k = 0; k < S0; ++k) {
+            const int l = (int)lvl[k];
+            const int64_t o = h->view.off[l], nl = h->view.off[l + 1] - o;
+            const int64_t gi = bound[k];  // the centre's input index
+            const int64_t i = gi - o, m = nl - i;
+            const double u = u01(seed ^ kAugSalt, (uint64_t)r * (uint64_t)h->N + (uint64_t)gi);
+            const int64_t p = i + 1 + std::min((int64_t)std::floor(u * (double)m), m - 1);
+            centre.push_back(centre[k]);
+            bound.push_back(o + p);
+        }
+    return MS_OK;
+}
+
+ms_status make_trainset(ms_hierarchy* h, const int* levels, int n, bool set_moments, int augment, uint64_t seed,
+                        TrainSet& ts, cudaStream_t st) {
     MS_TRY(check_levels(h, levels, n));
     MS_TRY(pc_pattern(h, st));
-    std::vector<int64_t> rows = level_rows(h, levels, n);
+    std::vector<int64_t> rows, bounds;
+    MS_TRY(patch_list(h, levels, n, augment, seed, rows, bounds));
     ts.S = (int64_t)rows.size();
     const int nin = h->pc.n_in;
+    int64_t* dbound = nullptr;
     MS_TRY(ts.alloc((void**)&ts.rows, sizeof(int64_t) * ts.S));
+    MS_TRY(ts.alloc((void**)&dbound, sizeof(int64_t) * ts.S));
+    MS_TRY(ts.alloc((void**)&ts.nbr, sizeof(int32_t) * ts.S * kPcK));
     MS_TRY(ts.alloc((void**)&ts.Z, sizeof(float) * ts.S * nin));
     MS_TRY(ts.alloc((void**)&ts.T, sizeof(float) * ts.S * kPcOut));
     MS_TRY(ts.alloc((void**)&ts.cnt, sizeof(int32_t) * ts.S));
     MS_TRY(ts.alloc((void**)&ts.ghat, sizeof(double) * ts.S * kPcOut));
     MS_TRY(ts.alloc((void**)&ts.K, sizeof(float) * ts.S * kPcOut * kPcOut));
     MS_CUDA(cudaMemcpyAsync(ts.rows, rows.data(), sizeof(int64_t) * ts.S, cudaMemcpyHostToDevice, st));
-    k_pc_features<<<nblk(ts.S, 128), 128, 0, st>>>(h->view, h->pc.nbr, ts.rows, ts.S, ts.Z, ts.cnt);
-    k_pc_patchK<<<nblk(ts.S, 128), 128, 0, st>>>(h->view, h->pc.nbr, ts.rows, ts.S, ts.K);
-    ms_count_launch(2);
-    k_pc_exact<<<nblk(ts.S, 64), 64, 0, st>>>(h->view, h->pc.nbr, ts.rows, ts.S, ts.ghat, nullptr, nullptr);
+    MS_CUDA(cudaMemcpyAsync(dbound, bounds.data(), sizeof(int64_t) * ts.S, cudaMemcpyHostToDevice, st));
+    k_pc_patches<<<nblk(ts.S, 128), 128, 0, st>>>(h->view, h->A.rp, h->A.col, h->perm, ts.rows, dbound, ts.S, ts.nbr);
+    k_pc_features<<<nblk(ts.S, 128), 128, 0, st>>>(h->view, ts.nbr, ts.rows, ts.S, ts.Z, ts.cnt);
+    k_pc_patchK<<<nblk(ts.S, 128), 128, 0, st>>>(h->view, ts.nbr, ts.rows, ts.S, ts.K);
+    ms_count_launch(3);
+    k_pc_exact<<<nblk(ts.S, 64), 64, 0, st>>>(h->view, ts.nbr, ts.rows, ts.S, ts.ghat, nullptr, nullptr);
     ms_count_launch();
     if (set_moments) {
         k_pc_moments<<<kPcOut, 256, 0, st>>>(ts.ghat, ts.cnt, ts.S, h->pc.musig);
@@ -760,6 +824,8 @@ ms_status make_trainset(ms_hierarchy* h, const int* levels, int n, bool set_mome
     k_pc_targets<<<nblk(ts.S, 128), 128, 0, st>>>(ts.ghat, ts.cnt, ts.S, h->pc.musig, ts.T);
     ms_count_launch();
     MS_CUDA(cudaGetLastError());
+    // the host arrays go out of scope: the copies must be complete
+    MS_CUDA(cudaStreamSynchronize(st));
     return MS_OK;
 }
 
@@ -821,12 +887,13 @@ extern "C" {
 void ms_default_train_opts(ms_train_opts* o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
-    o->epochs = 300;
+    o->epochs = 100;
     o->batch = 512;
     o->lr = 3e-3;
     o->lr_final = 1e-4;
     o->seed = 2503049140ull;
     o->input_noise = 0.005f;
+    o->augment = 4;
 }
 
 ms_status ms_train_precond(ms_hierarchy* h, const int* levels, int n_levels, const ms_train_opts* opts,
@@ -838,8 +905,9 @@ ms_status ms_train_precond(ms_hierarchy* h, const int* levels, int n_levels, con
     ms_train_opts o;
     ms_default_train_opts(&o);
     if (opts) o = *opts;
-    if (o.epochs < 1 || o.batch < kTB || o.batch % kTB != 0 || !(o.lr > 0.0)) {
-        ms_set_error(MS_ERR_ARG, "epochs >= 1, batch a positive multiple of %d and lr > 0 are required", kTB);
+    if (o.epochs < 1 || o.batch < kTB || o.batch % kTB != 0 || !(o.lr > 0.0) || o.augment < 0 || o.augment > 16) {
+        ms_set_error(MS_ERR_ARG, "epochs >= 1, batch a positive multiple of %d, lr > 0 and augment in 0..16 are required",
+                     kTB);
         return MS_ERR_ARG;
     }
     cudaStream_t st;
@@ -851,7 +919,9 @@ ms_status ms_train_precond(ms_hierarchy* h, const int* levels, int n_levels, con
     MS_TRY(pc_alloc(h));
     Precond& pc = h->pc;
     TrainSet ts;
-    MS_TRY(make_trainset(h, levels, n_levels, true, ts, st));
+    MS_TRY(make_trainset(h, levels, n_levels, true, o.augment, o.seed, ts, st));
+    pc.augment = o.augment;
+    pc.seed = o.seed;
     // initial weights: U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from SplitMix64(seed), parameter order
     const NetLayout N = net_layout(pc.n_in);
     std::vector<float> th(N.P);
@@ -1033,7 +1103,7 @@ ms_status ms_precond_inspect(ms_hierarchy* h, int what, const int* levels, int n
             return MS_ERR_ARG;
         }
         TrainSet ts;
-        MS_TRY(make_trainset(h, levels, n_levels, false, ts, st));
+        MS_TRY(make_trainset(h, levels, n_levels, false, 0, pc.seed, ts, st));
         const int nb = (int)((ts.S + kTB - 1) / kTB);
         const NetLayout Nl = net_layout(pc.n_in);
         float *gp = nullptr, *gout = nullptr;
@@ -1054,6 +1124,41 @@ ms_status ms_precond_inspect(ms_hierarchy* h, int what, const int* levels, int n
         double l = 0;
         MS_CUDA(cudaMemcpy(&l, lo, sizeof(double), cudaMemcpyDeviceToHost));
         o[Nl.P] = (float)l;
+        return MS_OK;
+    }
+    if (what == MS_INSPECT_PATCHES) {
+        MS_TRY(check_levels(h, levels, n_levels));
+        std::vector<int64_t> rows, bounds;
+        MS_TRY(patch_list(h, levels, n_levels, pc.augment, pc.seed, rows, bounds));
+        const int64_t S = (int64_t)rows.size();
+        if (n_out != S * 18) {
+            ms_set_error(MS_ERR_ARG, "expected %lld output values", (long long)(S * 18));
+            return MS_ERR_ARG;
+        }
+        TrainSet ts;
+        int64_t* dbound = nullptr;
+        MS_TRY(ts.alloc((void**)&ts.rows, sizeof(int64_t) * S));
+        MS_TRY(ts.alloc((void**)&dbound, sizeof(int64_t) * S));
+        MS_TRY(ts.alloc((void**)&ts.nbr, sizeof(int32_t) * S * kPcK));
+        MS_CUDA(cudaMemcpy(ts.rows, rows.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice));
+        MS_CUDA(cudaMemcpy(dbound, bounds.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice));
+        k_pc_patches<<<nblk(S, 128), 128>>>(h->view, h->A.rp, h->A.col, h->perm, ts.rows, dbound, S, ts.nbr);
+        ms_count_launch();
+        MS_CUDA(cudaGetLastError());
+        std::vector<int32_t> nb(S * kPcK);
+        MS_CUDA(cudaMemcpy(nb.data(), ts.nbr, sizeof(int32_t) * S * kPcK, cudaMemcpyDeviceToHost));
+        int32_t* o = static_cast<int32_t*>(out);
+        for (int64_t i = 0; i < S; ++i) {
+            const int64_t s = rows[i];
+            int l = 0;
+            while (l + 1 < h->L && s >= h->view.off[l + 1]) ++l;
+            o[i * 18] = perm[s];
+            o[i * 18 + 1] = (int32_t)(bounds[i] - h->view.off[l]);
+            for (int k = 0; k < kPcK; ++k) {
+                const int32_t c = nb[i * kPcK + k];
+                o[i * 18 + 2 + k] = c >= 0 ? perm[c] : -1;
+            }
+        }
         return MS_OK;
     }
     ms_set_error(MS_ERR_ARG, "unknown inspection %d", what);

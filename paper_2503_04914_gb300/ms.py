@@ -21,7 +21,7 @@ MS_OK, MS_ERR_ARG, MS_ERR_CUDA, MS_ERR_OOM, MS_ERR_NOT_SPD, MS_ERR_NOT_CONVERGED
 MS_OP_CSR, MS_OP_MATRIX_FREE, MS_OP_AUTO = range(3)
 MS_PREC_FP64, MS_PREC_MIXED = range(2)
 MS_PRECOND_NONE, MS_PRECOND_LEARNED, MS_PRECOND_EXACT = range(3)
-MS_INSPECT_PATTERN, MS_INSPECT_TARGETS, MS_INSPECT_PREDICT, MS_INSPECT_GRAD = range(4)
+MS_INSPECT_PATTERN, MS_INSPECT_TARGETS, MS_INSPECT_PREDICT, MS_INSPECT_GRAD, MS_INSPECT_PATCHES = range(5)
 PC_K, PC_OUT, PC_HIDDEN = 16, 17, 64
 MS_APPLY_A64, MS_APPLY_A32, MS_APPLY_AMF32, MS_APPLY_B64, MS_APPLY_B32, MS_APPLY_BMF32 = range(6)
 
@@ -74,7 +74,7 @@ class ms_info(C.Structure):
 class ms_train_opts(C.Structure):
     _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("lr_final", C.c_double),
                 ("seed", C.c_uint64), ("fp32_weights", C.c_int), ("input_noise", C.c_float),
-                ("reserved", C.c_int * 6)]
+                ("augment", C.c_int), ("reserved", C.c_int * 5)]
 
 
 class ms_train_stats(C.Structure):
@@ -381,9 +381,13 @@ def ms_precond_params(handle, d, params=None):
     return p
 
 
-def ms_precond_inspect(handle, what, N, d, levels=(0,)):
+def ms_precond_inspect(handle, what, N, d, levels=(0,), augment=4):
+    """augment: the extra patches per point of the last training (MS_INSPECT_PATCHES only)."""
     lv, n = _levels(levels)
-    if what == MS_INSPECT_PATTERN:
+    if what == MS_INSPECT_PATCHES:
+        npl = ms_hierarchy_info(handle)["n_per_level"]
+        out = np.empty(((1 + augment) * sum(npl[l] for l in levels), 18), dtype=np.int32)
+    elif what == MS_INSPECT_PATTERN:
         out = np.empty((N, PC_K), dtype=np.int32)
     elif what == MS_INSPECT_TARGETS:
         out = np.empty((N, PC_OUT), dtype=np.float64)
@@ -449,8 +453,8 @@ class Hierarchy:
     def precond_params(self, params=None):
         return ms_precond_params(self.handle, self.d, params)
 
-    def inspect(self, what, levels=(0,)):
-        return ms_precond_inspect(self.handle, what, self.N, self.d, levels)
+    def inspect(self, what, levels=(0,), augment=4):
+        return ms_precond_inspect(self.handle, what, self.N, self.d, levels, augment)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -48,6 +48,36 @@ def test_pattern_brute_force():
             assert np.min(np.linalg.norm(X[rest] - X[i], axis=1)) >= d[-1]
 
 
+def test_prefix_patches():
+    """Extra training patches: the prefix bound p = i gives the pattern; any p gives the 16
+    nearest of the first p points other than i (checked with a k-d tree); the bounds drawn
+    from uniform numbers lie in [i + 1, n], hit both ends, and u = 0 gives p = i + 1."""
+    X, delta, _ = level(4.0, (2, 1), 3)
+    n = len(X)
+    pat = of.pattern(X, delta)
+    rng = np.random.default_rng(3)
+    for i in range(n):
+        assert np.array_equal(of.prefix_pattern(X, delta, i, i), pat[i])
+    for i in rng.integers(0, n, 60):
+        p = int(rng.integers(i + 1, n + 1))
+        nb = of.prefix_pattern(X, delta, i, p)
+        tree = cKDTree(X[:p])
+        cand = [j for j in tree.query_ball_point(X[i], delta * (1 - 1e-12)) if j != i]
+        assert len(nb) == min(16, len(cand))
+        d = np.linalg.norm(X[nb] - X[i], axis=1)
+        assert np.all(nb < p) and np.all(nb != i) and np.all(d < delta) and np.all(np.diff(d) >= 0)
+        if len(cand) > 16:
+            rest = sorted(set(cand) - set(nb.tolist()))
+            assert np.min(np.linalg.norm(X[rest] - X[i], axis=1)) >= d[-1]
+    u = inputs.uniform01(inputs.BASE_SEED, n)
+    b = of.augment_bounds(n, u)
+    i = np.arange(n)
+    assert np.all(b >= i + 1) and np.all(b <= n)
+    assert np.array_equal(of.augment_bounds(n, np.zeros(n)), i + 1)
+    assert np.array_equal(of.augment_bounds(n, np.full(n, np.nextafter(1.0, 0.0))), np.full(n, n))
+    assert b[-1] == n
+
+
 def test_scale_free_weights_are_level_independent():
     """ghat = delta^{-d/2} g depends only on the delta-scaled offsets (eq. kernelscaling)."""
     X, delta, (wd, wk) = level(8.0, (2, 2), 2)

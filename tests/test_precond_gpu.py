@@ -69,6 +69,32 @@ def test_pattern_and_exact_rows(nu, wend):
     H.close()
 
 
+def test_training_patches_match_oracle():
+    """The training set's patches, the patterns and the extra patches below drawn prefix
+    bounds (default options: 4 per point, the default seed), are the oracle's exactly."""
+    w = halton([37, 150, 601], 4.0, (2, 1))
+    H = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED)
+    got = H.inspect(ms.MS_INSPECT_PATCHES, levels=(0, 1, 2), augment=4)
+    off = om.level_offsets(w.levels)
+    seed = inputs.BASE_SEED ^ 0x6175676D656E74
+    want = []
+    for r in range(-1, 4):
+        for l in range(w.L):
+            X, delta = w.levels[l], w.nu * w.h[l]
+            n = len(X)
+            b = np.arange(n) if r < 0 else of.augment_bounds(n, inputs.uniform01(seed, n, r * w.N + off[l]))
+            for i in range(n):
+                nb = of.prefix_pattern(X, delta, i, int(b[i]))
+                row = np.full(18, -1)
+                row[0], row[1] = off[l] + i, b[i]
+                row[2:2 + len(nb)] = nb + off[l]
+                want.append(row)
+    want = np.array(want)
+    assert got.shape == want.shape
+    assert np.array_equal(got, want), np.argwhere(got != want)[:5]
+    H.close()
+
+
 def _random_params(w, seed):
     n_in = 16 * w.d
     th = of.init_params(n_in, seed)
@@ -129,13 +155,13 @@ def trained():
     """nu = 8, phi_{2,2} (kappa(A_l) ~ 1e5..1e6): train on levels 0..3, fit level sizes to 16384."""
     w = inputs.halton_hierarchy(L=5, nu=8.0, wendland=(2, 2), n_gauss=6)
     H = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED, precond=ms.MS_PRECOND_LEARNED)
-    st = H.train_precond([0, 1, 2, 3], epochs=200)
+    st = H.train_precond([0, 1, 2, 3])
     return w, H, st
 
 
 def test_training_reduces_the_loss(trained):
     _, _, st = trained
-    assert st["samples"] == 64 + 256 + 1024 + 4096
+    assert st["samples"] == (1 + 4) * (64 + 256 + 1024 + 4096)  # patterns + 4 extra patches a point
     assert st["loss_last"] < 0.5 * st["loss_first"], st
 
 
@@ -152,7 +178,7 @@ def test_learned_preconditioner_gain_and_parity(trained):
     it_pc, it_0, it_e = (sum(s["cg_iterations"]) for s in (st_pc, st_0, st_e))
     assert st_pc["precond_fallbacks"] == 0
     assert it_pc * 2 < it_0, (it_pc, it_0)
-    assert it_e * 2 < it_pc, (it_e, it_pc)
+    assert it_e < it_pc, (it_e, it_pc)
     ref, _ = om.fit_sequential(w.levels, w.f, w.h, w.nu, 2, 2)
     ref = np.concatenate(ref)
     Q = inputs.query_grid(48, 2)

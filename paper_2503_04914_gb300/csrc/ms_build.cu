@@ -13,7 +13,9 @@
 #include <cmath>
 #include <vector>
 
+#include "ms_ff.cuh"
 #include "ms_internal.cuh"
+#include "ms_matfree.cuh"
 #include "ms_scan.cuh"
 
 namespace {
@@ -101,7 +103,7 @@ __global__ void k_gather_points(const double* pts, const int32_t* perm, double* 
 
 // Matrix-free geometry of each sorted point: its level-local Morton cell and its
 // offset from that cell's corner in units of delta_l (FP32).
-__global__ void k_mf_coords(HierView v, float* W, int32_t* cellid) {
+__global__ void k_mf_coords(HierView v, float* W, float* Wlo, int32_t* cellid) {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= v.N) return;
     const int l = level_of_row(v.off, v.L, s);
@@ -111,7 +113,10 @@ __global__ void k_mf_coords(HierView v, float* W, int32_t* cellid) {
     for (int a = 0; a < v.d; ++a) {
         const double x = v.X[a * v.N + s];
         c[a] = min(max(cell_coord(g, a, x), 0), g.G[a] - 1);
-        W[a * v.N + s] = (float)((x - (g.lo[a] + (double)c[a] * g.cell)) * inv_delta);
+        const double t = (x - (g.lo[a] + (double)c[a] * g.cell)) * inv_delta;
+        const float hi = (float)t;
+        W[a * v.N + s] = hi;
+        if (Wlo) Wlo[a * v.N + s] = (float)(t - (double)hi);  // W + Wlo: t to about 48 bits
     }
     cellid[s] = (int32_t)morton(v.d, c[0], c[1], c[2]);
 }
@@ -133,6 +138,7 @@ __global__ void k_mf_coords(HierView v, float* W, int32_t* cellid) {
 struct Frame {
     int c[3];
     float fr[3];
+    float frlo[3];  // fr + frlo: the offset to about 48 bits (double-float entries)
 };
 
 struct Pt {
@@ -158,27 +164,105 @@ __device__ __forceinline__ double dist2(const HierView& v, int64_t p, const Pt& 
 // Frame of y in level j's grid, all axes (FP64 set-up: one lane per level calls it).
 __device__ __forceinline__ Frame frame_of(const HierView& v, int j, const Pt& y) {
     const LevelGrid& g = v.grid[j];
-    Frame f{{0, 0, 0}, {0.f, 0.f, 0.f}};
+    Frame f{};
     const double ya[3] = {y.x, y.y, y.z};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (a < v.d) {
             f.c[a] = cell_coord(g, a, ya[a]);
-            f.fr[a] = (float)((ya[a] - (g.lo[a] + (double)f.c[a] * g.cell)) * v.inv_delta[j]);
+            const double t = (ya[a] - (g.lo[a] + (double)f.c[a] * g.cell)) * v.inv_delta[j];
+            f.fr[a] = (float)t;
+            f.frlo[a] = (float)(t - (double)f.fr[a]);
         }
     }
     return f;
 }
 
-// Broadcast lane `src`'s frame to the warp.
+// Lane `src`'s frame (src may differ between lanes; every lane must take part).
 __device__ __forceinline__ Frame frame_from(const Frame& mine, int src) {
     Frame f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         f.c[a] = __shfl_sync(0xffffffffu, mine.c[a], src);
         f.fr[a] = __shfl_sync(0xffffffffu, mine.fr[a], src);
+        f.frlo[a] = __shfl_sync(0xffffffffu, mine.frlo[a], src);
     }
     return f;
+}
+
+// ---------------------------------------------------------------- double-float entries
+//
+// With precision = MIXED the stored FP64 entries are evaluated in double-float arithmetic
+// (ms_ff.cuh) from the points' cell-relative offsets W + Wlo, exact to about 48 bits:
+// relative errors near 1e-14 instead of 1e-16, far inside what the mixed path promises
+// (its inner solves run in FP32), at about 3 FP64 instructions per entry (the final
+// conversion) instead of about 30.
+
+// Per-level constants: cell size / delta and delta^-d as double-floats.
+struct FFLevels {
+    ff cod[MS_MAXL];
+    ff ds[MS_MAXL];
+};
+
+// phi(r) for the Wendland closed form w in double-float; 0 for r >= 1.
+__device__ __forceinline__ ff ff_wendland(const WendlandPoly& w, ff r) {
+    if (!(r.hi < 1.0f || (r.hi == 1.0f && r.lo < 0.0f))) return {0.0f, 0.0f};
+    const ff s = ff_add({1.0f, 0.0f}, ff_neg(r));
+    const ff s2 = ff_sqr(s), s4 = ff_sqr(s2);
+    ff pw;
+    switch (w.e) {
+    case 4: pw = s4; break;
+    case 6: pw = ff_mul(s4, s2); break;
+    case 8: pw = ff_sqr(s4); break;
+    default: {
+        pw = {1.0f, 0.0f};
+        for (int i = 0; i < w.e; ++i) pw = ff_mul(pw, s);
+    }
+    }
+    ff p = ff_from_double(w.c[w.k]);
+    for (int i = w.k - 1; i >= 0; --i) p = ff_add(ff_mul(p, r), ff_from_double(w.c[i]));
+    return ff_mul(pw, p);
+}
+
+// delta_j^-d phi(|x_p - y| / delta_j) for point p of level j (cell cp, offsets W + Wlo) and
+// y's frame f in level j's grid: the scaled offset on axis a is
+// (cp_a - c_a) cod + (W_a + Wlo_a) - (fr_a + frlo_a).
+__device__ __forceinline__ double ff_entry(const HierView& v, const float* __restrict__ W,
+                                           const float* __restrict__ Wlo, const int32_t* __restrict__ cellid,
+                                           const FFLevels& ffl, int j, int32_t p, const Frame& f) {
+    int cp[3];
+    demorton(v.d, (uint32_t)__ldg(cellid + p), cp);
+    ff r2 = {0.0f, 0.0f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a < v.d) {
+            const ff cell = ff_mul(ffl.cod[j], {(float)(cp[a] - f.c[a]), 0.0f});
+            const ff w = {__ldg(W + a * v.N + p), __ldg(Wlo + a * v.N + p)};
+            const ff t = ff_add(ff_add(cell, w), ff_neg({f.fr[a], f.frlo[a]}));
+            r2 = ff_add(r2, ff_sqr(t));
+        }
+    }
+    return ff_to_double(ff_mul(ffl.ds[j], ff_wendland(v.w, ff_sqrt(r2))));
+}
+
+// Offset (units of delta) of a neighbour cell displaced by `dc` cells, seen from a point at
+// fractional offset fr in its own cell; both CSR kernels take it from here so that they
+// make the same decisions.
+__device__ __forceinline__ float cell_offset(int dc, float cod, float fr) { return __fsub_rn(__fmul_rn((float)dc, cod), fr); }
+
+// |x_p - y| < delta_j for candidate p in the neighbour cell with offsets (c0, c1, c2): FP32
+// test on the cell-relative coordinates W (units of delta_j), the FP64 distance inside a band
+// of 1e-4 around the support boundary.  Rounded operation by operation (no contraction), so
+// every caller gets the same answer.
+__device__ __forceinline__ bool within(const HierView& v, const float* __restrict__ W, int32_t p, float c0, float c1,
+                                       float c2, const Pt& y, double d2) {
+    float t = __fadd_rn(c0, __ldg(W + p));
+    float qq = __fmul_rn(t, t);
+    if (v.d >= 2) { t = __fadd_rn(c1, __ldg(W + v.N + p)); qq = __fmaf_rn(t, t, qq); }
+    if (v.d >= 3) { t = __fadd_rn(c2, __ldg(W + 2 * v.N + p)); qq = __fmaf_rn(t, t, qq); }
+    if (qq < 1.0f - 1e-4f) return true;
+    if (qq <= 1.0f + 1e-4f) return dist2(v, p, y) < d2;
+    return false;
 }
 
 // visit(p, in, mask): called by all 32 lanes for every group of up to 32
@@ -210,9 +294,9 @@ __device__ __forceinline__ void warp_neighbours(const HierView& v, const float* 
                 start = __ldg(v.cell_start + gid);
                 cnt = __ldg(v.cell_start + gid + 1) - start;
             }
-            o0 = (float)dx * cod - f.fr[0];
-            o1 = (float)dy * cod - f.fr[1];
-            o2 = (float)dz * cod - f.fr[2];
+            o0 = cell_offset(dx, cod, f.fr[0]);
+            o1 = cell_offset(dy, cod, f.fr[1]);
+            o2 = cell_offset(dz, cod, f.fr[2]);
         }
         int incl = cnt;  // inclusive prefix of the cells' point counts over the lanes
 #pragma unroll
@@ -237,18 +321,7 @@ __device__ __forceinline__ void warp_neighbours(const HierView& v, const float* 
             const float c1 = __shfl_sync(0xffffffffu, o1, cq);
             const float c2 = __shfl_sync(0xffffffffu, o2, cq);
             const int32_t p = cs + (i - ce);
-            bool in = false;
-            if (i < total) {
-                float t = c0 + __ldg(W + p);
-                float qq = t * t;
-                if (v.d >= 2) { t = c1 + __ldg(W + v.N + p); qq = fmaf(t, t, qq); }
-                if (v.d >= 3) { t = c2 + __ldg(W + 2 * v.N + p); qq = fmaf(t, t, qq); }
-                if (qq < 1.0f - 1e-4f) {
-                    in = true;
-                } else if (qq <= 1.0f + 1e-4f) {
-                    in = dist2(v, p, y) < d2;
-                }
-            }
+            const bool in = i < total && within(v, W, p, c0, c1, c2, y, d2);
             visit(p, in, __ballot_sync(0xffffffffu, in));
         }
     }
@@ -256,6 +329,9 @@ __device__ __forceinline__ void warp_neighbours(const HierView& v, const float* 
 
 constexpr int kCsrBS = 256;  // 8 rows per block
 
+// Entries of row s: one warp per row, one lane per (column level j, neighbour cell) pair
+// at a time, each lane walking its cell's points (the count needs no positions, so no
+// compaction across lanes).
 __global__ void __launch_bounds__(kCsrBS, 4) k_csr_count(HierView v, const float* __restrict__ W, int32_t* cntA,
                                                        int32_t* cntB) {
     const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -264,12 +340,45 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_count(HierView v, const float
     const int k = level_of_row(v.off, v.L, s);
     const Pt y = point_at(v, s);
     // lane j <= k holds y's frame in level j's grid
-    Frame mine{{0, 0, 0}, {0.f, 0.f, 0.f}};
+    Frame mine{};
     if (lane <= k) mine = frame_of(v, lane, y);
+    const int R = v.R, side = 2 * R + 1;
+    const int nc = v.d == 1 ? side : (v.d == 2 ? side * side : side * side * side);
+    const int pairs = (k + 1) * nc;
     int32_t na = 0, nb = 0;
-    warp_neighbours(v, W, k, frame_from(mine, k), y, lane, [&](int32_t, bool, unsigned m) { na += __popc(m); });
-    for (int j = 0; j < k; ++j)
-        warp_neighbours(v, W, j, frame_from(mine, j), y, lane, [&](int32_t, bool, unsigned m) { nb += __popc(m); });
+    for (int t0 = 0; t0 < pairs; t0 += 32) {
+        const int t = t0 + lane;
+        const int j = min(t / nc, k);  // lanes past the last pair read a valid frame and skip
+        Frame f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            f.c[a] = __shfl_sync(0xffffffffu, mine.c[a], j);
+            f.fr[a] = __shfl_sync(0xffffffffu, mine.fr[a], j);
+        }
+        if (t >= pairs) continue;
+        const LevelGrid& g = v.grid[j];
+        const int q = t - j * nc;
+        const int dx = q % side - R;
+        const int dy = v.d >= 2 ? (q / side) % side - R : 0;
+        const int dz = v.d >= 3 ? q / (side * side) - R : 0;
+        const int cx = f.c[0] + dx, cy = f.c[1] + dy, cz = f.c[2] + dz;
+        if (cx < 0 || cx >= g.G[0] || cy < 0 || cy >= g.G[1] || cz < 0 || cz >= g.G[2]) continue;
+        const int64_t gid = g.cell_off + morton(v.d, cx, cy, cz);
+        const int32_t ps = __ldg(v.cell_start + gid), pe = __ldg(v.cell_start + gid + 1);
+        const float o0 = cell_offset(dx, g.cod, f.fr[0]);
+        const float o1 = cell_offset(dy, g.cod, f.fr[1]);
+        const float o2 = cell_offset(dz, g.cod, f.fr[2]);
+        const double d2 = v.delta[j] * v.delta[j];
+        int32_t n = 0;
+        for (int32_t p = ps; p < pe; ++p) n += within(v, W, p, o0, o1, o2, y, d2) ? 1 : 0;
+        if (j == k) na += n;
+        else nb += n;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        na += __shfl_xor_sync(0xffffffffu, na, o);
+        nb += __shfl_xor_sync(0xffffffffu, nb, o);
+    }
     if (lane == 0) {
         cntA[s] = na;
         cntB[s] = nb;
@@ -281,7 +390,11 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_count(HierView v, const float
 // column level j (j = 0..k; Bseg[k][s] = the row length).  The columns are
 // found first (FP32 test, compacted by ballot); the FP64 values then take all
 // 32 lanes over the row's entries.
-__global__ void __launch_bounds__(kCsrBS, 4) k_csr_fill(HierView v, const float* __restrict__ W, const int64_t* rpA,
+// FF: entries in double-float arithmetic (MIXED builds), else FP64.
+template <bool FF>
+__global__ void __launch_bounds__(kCsrBS, 4) k_csr_fill(const __grid_constant__ HierView v, const float* __restrict__ W,
+                                                      const float* __restrict__ Wlo, const int32_t* __restrict__ cellid,
+                                                      const __grid_constant__ FFLevels ffl, const int64_t* rpA,
                                                       int32_t* colA, double* valA, float* valA32, const int64_t* rpB,
                                                       int32_t* colB, double* valB, float* valB32, int32_t* Bseg) {
     const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -290,7 +403,7 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_fill(HierView v, const float*
     const unsigned below = (1u << lane) - 1u;
     const int k = level_of_row(v.off, v.L, s);
     const Pt y = point_at(v, s);
-    Frame mine{{0, 0, 0}, {0.f, 0.f, 0.f}};
+    Frame mine{};
     if (lane <= k) mine = frame_of(v, lane, y);
     auto emit = [&](int j, int64_t& pos, int32_t* col) {
         warp_neighbours(v, W, j, frame_from(mine, j), y, lane, [&](int32_t p, bool in, unsigned m) {
@@ -309,6 +422,28 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_fill(HierView v, const float*
     }
     if (lane == 0) Bseg[(int64_t)k * v.N + s] = (int32_t)(pb - b0);
     __syncwarp();  // the columns written by the other lanes are read below
+    if (FF) {
+        const Frame fk = frame_from(mine, k);
+        for (int64_t i = a0 + lane; i < pa; i += 32) {
+            const double value = ff_entry(v, W, Wlo, cellid, ffl, k, colA[i], fk);
+            valA[i] = value;
+            if (valA32) valA32[i] = (float)value;
+        }
+        // every lane takes part in each step (the frame of the entry's level comes by shuffle)
+        for (int64_t i0 = b0; i0 < pb; i0 += 32) {
+            const int64_t i = i0 + lane;
+            const bool ok = i < pb;
+            const int32_t p = ok ? colB[i] : (int32_t)v.off[0];
+            const int j = level_of_row(v.off, v.L, p);
+            const Frame fj = frame_from(mine, j);
+            if (ok) {
+                const double value = ff_entry(v, W, Wlo, cellid, ffl, j, p, fj);
+                valB[i] = value;
+                if (valB32) valB32[i] = (float)value;
+            }
+        }
+        return;
+    }
     {
         const double inv = v.inv_delta[k], sc = v.dscale[k];
         for (int64_t i = a0 + lane; i < pa; i += 32) {
@@ -465,9 +600,13 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
     k_rank<<<nblk(N, 256), 256, 0, st>>>(key, h->cell_start, tmp, h->perm, N); ms_count_launch();
     k_gather_points<<<nblk(N, 256), 256, 0, st>>>(pts, h->perm, h->X, d, N); ms_count_launch();
     MS_CUDA(cudaGetLastError());
+    // double-float entries (MIXED) also need the low parts of the offsets
+    const bool ffvals = h->opts.precision == MS_PREC_MIXED;
+    float* Wlo = nullptr;
     MS_TRY(ms_alloc(h, (void**)&h->W, sizeof(float) * d * N));
     MS_TRY(ms_alloc(h, (void**)&h->cellid, sizeof(int32_t) * N));
-    k_mf_coords<<<nblk(N, 256), 256, 0, st>>>(v, h->W, h->cellid); ms_count_launch();
+    if (ffvals) MS_TRY(talloc((void**)&Wlo, sizeof(float) * d * N));
+    k_mf_coords<<<nblk(N, 256), 256, 0, st>>>(v, h->W, Wlo, h->cellid); ms_count_launch();
     MS_CUDA(cudaGetLastError());
 
     // 3. CSR of A (diagonal blocks) and B (strictly lower blocks)
@@ -496,8 +635,20 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
     // the fit updates beta with FP64 B values only; FP32 B values serve MS_APPLY_B32 on request
     if (h->opts.lower_fp32) MS_TRY(ms_alloc(h, (void**)&h->B.v32, sizeof(float) * h->B.nnz));
     MS_TRY(ms_alloc(h, (void**)&h->Bseg, sizeof(int32_t) * (size_t)L * N));
-    k_csr_fill<<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, h->A.rp, h->A.col, h->A.v64, h->A.v32, h->B.rp,
-                                                        h->B.col, h->B.v64, h->B.v32, h->Bseg); ms_count_launch();
+    FFLevels ffl{};
+    for (int l = 0; l < L; ++l) {
+        ffl.cod[l] = ff_from_double(v.grid[l].cell / v.delta[l]);
+        ffl.ds[l] = ff_from_double(v.dscale[l]);
+    }
+    if (ffvals)
+        k_csr_fill<true><<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, Wlo, h->cellid, ffl, h->A.rp, h->A.col,
+                                                                  h->A.v64, h->A.v32, h->B.rp, h->B.col, h->B.v64,
+                                                                  h->B.v32, h->Bseg);
+    else
+        k_csr_fill<false><<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, nullptr, h->cellid, ffl, h->A.rp,
+                                                                   h->A.col, h->A.v64, h->A.v32, h->B.rp, h->B.col,
+                                                                   h->B.v64, h->B.v32, h->Bseg);
+    ms_count_launch();
     unsigned long long* blk;
     MS_TRY(talloc((void**)&blk, sizeof(unsigned long long) * L * L));
     MS_CUDA(cudaMemsetAsync(blk, 0, sizeof(unsigned long long) * L * L, st));

@@ -16,6 +16,7 @@
 //             (forward/backward on the BF16-rounded copies) against the exact rows
 //             of chosen levels, standardised per output.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -62,29 +63,48 @@ __device__ __forceinline__ bool key_less(double d2a, int32_t pa, double d2b, int
 // index.  bound = perm[s] gives the pattern of s; a larger bound an extra training patch.
 __device__ void nearest_below(const HierView& v, const int64_t* Arp, const int32_t* Acol, const int32_t* perm,
                               int64_t s, int64_t bound, int32_t* out) {
+    // sorted list keyed by (distance, input index), held in registers (every index below is a
+    // compile-time constant); empty slots hold the key (+inf, INT_MAX) and column -1.  bd holds
+    // squared distances, compared through key_less as their correctly rounded roots.
     double bd[kPcK];
     int32_t bp[kPcK], bc[kPcK];
-    int cnt = 0;
+#pragma unroll
+    for (int i = 0; i < kPcK; ++i) {
+        bd[i] = __longlong_as_double(0x7FF0000000000000ll);
+        bp[i] = INT_MAX;
+        bc[i] = -1;
+    }
     for (int64_t k = Arp[s]; k < Arp[s + 1]; ++k) {
         const int32_t c = Acol[k];
         const int32_t pc = perm[c];
         if (pc >= bound || c == s) continue;
         const double d = dist2_rn(v, c, s);
-        // insertion into the sorted list keyed by (distance, input index); bd holds squared
-        // distances, compared through key_less as their correctly rounded roots
-        int pos = cnt < kPcK ? cnt : kPcK;
-        while (pos > 0 && key_less(d, pc, bd[pos - 1], bp[pos - 1])) {
-            if (pos < kPcK) { bd[pos] = bd[pos - 1]; bp[pos] = bp[pos - 1]; bc[pos] = bc[pos - 1]; }
-            --pos;
+        if (!key_less(d, pc, bd[kPcK - 1], bp[kPcK - 1])) continue;  // not among the 16 nearest so far
+        bool lt[kPcK];  // the new key goes before slot i (false ... false, true ... true)
+#pragma unroll
+        for (int i = 0; i < kPcK; ++i) lt[i] = key_less(d, pc, bd[i], bp[i]);
+        // slot i takes slot i-1's entry if the new key goes before that, else the new key if it
+        // goes before slot i's entry (the insertion point)
+#pragma unroll
+        for (int i = kPcK - 1; i > 0; --i) {
+            if (lt[i - 1]) {
+                bd[i] = bd[i - 1];
+                bp[i] = bp[i - 1];
+                bc[i] = bc[i - 1];
+            } else if (lt[i]) {
+                bd[i] = d;
+                bp[i] = pc;
+                bc[i] = c;
+            }
         }
-        if (pos < kPcK) {
-            bd[pos] = d;
-            bp[pos] = pc;
-            bc[pos] = c;
-            if (cnt < kPcK) ++cnt;
+        if (lt[0]) {
+            bd[0] = d;
+            bp[0] = pc;
+            bc[0] = c;
         }
     }
-    for (int i = 0; i < kPcK; ++i) out[i] = i < cnt ? bc[i] : -1;
+#pragma unroll
+    for (int i = 0; i < kPcK; ++i) out[i] = bc[i];
 }
 
 __global__ void k_pc_pattern(HierView v, const int64_t* Arp, const int32_t* Acol, const int32_t* perm, int32_t* nbr) {
@@ -185,10 +205,13 @@ __global__ void k_pc_exact(HierView v, const int32_t* nbr, const int64_t* rows, 
 // the last axis flipped so that o_d has a non-negative coordinate on it (d = 1: o_1 > 0).
 // The kernel is radial, so the exact row does not depend on the frame.  FP64 arithmetic, so
 // the frame's sign decisions are those of the FP64 oracle.
+// z[k D + a]: coordinate a of neighbour k (D = the point dimension, a compile-time constant
+// so that z can live in registers).
+template <int D>
 __device__ __forceinline__ int pc_features(const HierView& v, const int32_t* nb, int64_t s, float* z) {
     const int l = level_of_row(v.off, v.L, s);
     const double inv = 1.0 / v.delta[l];
-    const int d = v.d;
+    constexpr int d = D;
     auto offset = [&](int k, double* o) {
         const int32_t c = nb[k];
         for (int a = 0; a < 3; ++a) o[a] = (a < d && c >= 0) ? (v.X[a * v.N + c] - v.X[a * v.N + s]) * inv : 0.0;
@@ -245,9 +268,11 @@ __device__ __forceinline__ int pc_features(const HierView& v, const int32_t* nb,
             }
         }
     }
+#pragma unroll
     for (int k = 0; k < kPcK; ++k) {
         double o[3];
         const bool ok = offset(k, o);
+#pragma unroll
         for (int a = 0; a < d; ++a)
             z[k * d + a] = ok ? (float)(e[a][0] * o[0] + e[a][1] * o[1] + e[a][2] * o[2]) : 0.f;
     }
@@ -259,7 +284,9 @@ __global__ void k_pc_features(HierView v, const int32_t* nbr, const int64_t* row
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     float z[kPcK * 3];
-    const int c = pc_features(v, nbr + i * kPcK, rows[i], z);
+    const int c = v.d == 1 ? pc_features<1>(v, nbr + i * kPcK, rows[i], z)
+                : v.d == 2 ? pc_features<2>(v, nbr + i * kPcK, rows[i], z)
+                           : pc_features<3>(v, nbr + i * kPcK, rows[i], z);
     const int nin = kPcK * v.d;
     for (int k = 0; k < nin; ++k) Z[i * nin + k] = z[k];
     cnt[i] = c;
@@ -378,7 +405,9 @@ __global__ void k_pc_infer(HierView v, const int32_t* nbr, const float* theta, i
     if (s >= v.N) return;
     const NetLayout N = net_layout(kPcK * v.d);
     float z[kPcK * 3], o[kPcOut];
-    const int cnt = pc_features(v, nbr + s * kPcK, s, z);
+    const int cnt = v.d == 1 ? pc_features<1>(v, nbr + s * kPcK, s, z)
+                  : v.d == 2 ? pc_features<2>(v, nbr + s * kPcK, s, z)
+                             : pc_features<3>(v, nbr + s * kPcK, s, z);
     mlp_forward(N, W, z, o);
     float g[kPcOut];
     for (int m = 0; m < kPcOut; ++m) g[m] = m <= cnt ? fmaf(ms[kPcOut + m], o[m], ms[m]) : 0.f;
@@ -620,34 +649,30 @@ __global__ void k_gt_fill(const int32_t* gcol, const float* gval, int64_t N, con
         val[pos] = gval[k * N + s];
     }
 }
-// deterministic order inside each row of G^T: by source row (insertion sort in registers
-// for rows of up to 32 entries, which is nearly all of them; in place beyond)
+// deterministic order inside each row of G^T: by source row.  One warp per row: for rows of up
+// to 32 entries (nearly all) lane i holds entry i and writes it at its rank among the row's
+// source rows (all distinct: a row of G names each column once); longer rows are sorted in
+// place by one lane.
 __global__ void k_gt_sort(const int64_t* rp, int32_t* col, float* val, int64_t N) {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= N) return;
+    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= N) return;  // warp-uniform
     const int64_t s = rp[c], e = rp[c + 1];
     const int n = (int)(e - s);
     if (n <= 32) {
-        int32_t kc[32];
-        float kv[32];
-        for (int i = 0; i < n; ++i) {
-            const int32_t ci = col[s + i];
-            const float vi = val[s + i];
-            int j = i - 1;
-            while (j >= 0 && kc[j] > ci) {
-                kc[j + 1] = kc[j];
-                kv[j + 1] = kv[j];
-                --j;
-            }
-            kc[j + 1] = ci;
-            kv[j + 1] = vi;
-        }
-        for (int i = 0; i < n; ++i) {
-            col[s + i] = kc[i];
-            val[s + i] = kv[i];
+        const int32_t mc = lane < n ? col[s + lane] : INT_MAX;
+        const float mv = lane < n ? val[s + lane] : 0.f;
+        int rank = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) rank += __shfl_sync(0xffffffffu, mc, j) < mc ? 1 : 0;
+        __syncwarp();  // every lane has read its entry before any lane writes
+        if (lane < n) {
+            col[s + rank] = mc;
+            val[s + rank] = mv;
         }
         return;
     }
+    if (lane != 0) return;
     for (int64_t i = s + 1; i < e; ++i) {
         const int32_t kc = col[i];
         const float kv = val[i];
@@ -678,6 +703,18 @@ uint64_t gcd64(uint64_t a, uint64_t b) {
         b = t;
     }
     return a;
+}
+
+// G rows (gval/gcol) or, with ghat_out, the scale-free rows of every point from the network.
+ms_status launch_infer(ms_hierarchy* h, float* gval, int32_t* gcol, float* ghat_out, cudaStream_t st) {
+    const Precond& pc = h->pc;
+    const size_t smem = sizeof(float) * pc.n_params;
+    MS_CUDA(cudaFuncSetAttribute(k_pc_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_pc_infer<<<nblk(h->N, 128), 128, smem, st>>>(h->view, pc.nbr, pc.fp32_weights ? pc.theta : pc.theta_bf,
+                                                   pc.n_params, pc.musig, gval, gcol, ghat_out);
+    ms_count_launch();
+    MS_CUDA(cudaGetLastError());
+    return MS_OK;
 }
 
 ms_status pc_alloc(ms_hierarchy* h) {
@@ -853,13 +890,10 @@ ms_status ms_pc_build(ms_hierarchy* h, int kind, cudaStream_t st) {
     const int64_t N = h->N;
     if (kind == MS_PRECOND_EXACT) {
         k_pc_exact<<<nblk(N, 64), 64, 0, st>>>(h->view, pc.nbr, nullptr, N, nullptr, pc.gval, pc.gcol);
+        ms_count_launch();
     } else {
-        const size_t smem = sizeof(float) * pc.n_params;
-        MS_CUDA(cudaFuncSetAttribute(k_pc_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_pc_infer<<<nblk(N, 128), 128, smem, st>>>(h->view, pc.nbr, pc.fp32_weights ? pc.theta : pc.theta_bf,
-                                                    pc.n_params, pc.musig, pc.gval, pc.gcol, nullptr);
+        MS_TRY(launch_infer(h, pc.gval, pc.gcol, nullptr, st));
     }
-    ms_count_launch();
     MS_CUDA(cudaGetLastError());
     // transpose (in-pattern) for z = G^T u
     int32_t* cnt = nullptr;
@@ -871,7 +905,7 @@ ms_status ms_pc_build(ms_hierarchy* h, int kind, cudaStream_t st) {
     exclusive_scan<int32_t, int64_t>(cnt, N, pc.gt_rp, tiles, st);
     MS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (N + 1), st));
     k_gt_fill<<<nblk(N, 256), 256, 0, st>>>(pc.gcol, pc.gval, N, pc.gt_rp, cnt, pc.gt_col, pc.gt_val);
-    k_gt_sort<<<nblk(N, 256), 256, 0, st>>>(pc.gt_rp, pc.gt_col, pc.gt_val, N);
+    k_gt_sort<<<nblk(N * 32, 256), 256, 0, st>>>(pc.gt_rp, pc.gt_col, pc.gt_val, N);
     ms_count_launch(3);
     MS_CUDA(cudaFreeAsync(cnt, st));
     MS_CUDA(cudaFreeAsync(tiles, st));
@@ -1077,11 +1111,13 @@ ms_status ms_precond_inspect(ms_hierarchy* h, int what, const int* levels, int n
         }
         float* d = nullptr;
         MS_CUDA(cudaMalloc((void**)&d, sizeof(float) * N * kPcOut));
-        const size_t smem = sizeof(float) * pc.n_params;
-        MS_CUDA(cudaFuncSetAttribute(k_pc_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_pc_infer<<<nblk(N, 128), 128, smem>>>(h->view, pc.nbr, pc.fp32_weights ? pc.theta : pc.theta_bf,
-                                                pc.n_params, pc.musig, nullptr, nullptr, d);
-        ms_count_launch();
+        {
+            const ms_status ls = launch_infer(h, nullptr, nullptr, d, 0);
+            if (ls != MS_OK) {
+                cudaFree(d);
+                return ls;
+            }
+        }
         std::vector<float> hd(N * kPcOut);
         cudaError_t e = cudaMemcpy(hd.data(), d, sizeof(float) * N * kPcOut, cudaMemcpyDeviceToHost);
         cudaFree(d);

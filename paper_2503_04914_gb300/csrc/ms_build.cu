@@ -124,9 +124,11 @@ __global__ void k_mf_coords(HierView v, float* W, float* Wlo, int32_t* cellid) {
 
 // ---------------------------------------------------------------- CSR assembly
 //
-// One warp per row s (level k).  For each column level j (j = k for A, j < k for
-// B) the warp walks the (2R+1)^d cells around s's cell in level j's grid; its
-// lanes take a cell's points 32 at a time.  The test |x_p - x_s| < delta_j is
+// One warp per row s (level k).  Its candidates are the (2R+1)^d cells around s's
+// cell in the grid of every column level j <= k (j = k for A, j < k for B); the
+// lanes take one (level, cell) pair each and walk that cell's points.  The count
+// kernel stores every pair's count; the fill scans them to place each lane's
+// columns and writes the same entries in the same order.  The test |x_p - x_s| < delta_j is
 // taken in FP32 first, from cell-relative coordinates in units of delta_j (the
 // cell offset plus the FP32 in-cell offsets W), whose error is ~1e-6 of delta_j^2;
 // only candidates within 1e-4 of the boundary are re-tested in FP64
@@ -198,57 +200,74 @@ __device__ __forceinline__ Frame frame_from(const Frame& mine, int src) {
 // (its inner solves run in FP32), at about 3 FP64 instructions per entry (the final
 // conversion) instead of about 30.
 
-// Per-level constants: cell size / delta and delta^-d as double-floats.
+// Per-level constants (cell size / delta, delta^-d) and the Wendland polynomial's
+// coefficients as double-floats, converted once on the host: a conversion from FP64 costs
+// FP64 instructions, which is what this path avoids.
 struct FFLevels {
     ff cod[MS_MAXL];
     ff ds[MS_MAXL];
+    ff c[4];
 };
 
-// phi(r) for the Wendland closed form w in double-float; 0 for r >= 1.
-__device__ __forceinline__ ff ff_wendland(const WendlandPoly& w, ff r) {
+// phi(r) for the Wendland closed form w in double-float; 0 for r >= 1.  E, K: the exponent
+// and the degree as compile-time constants (0: read them from w).
+template <int E, int K>
+__device__ __forceinline__ ff ff_wendland(const WendlandPoly& w, const ff* c, ff r) {
     if (!(r.hi < 1.0f || (r.hi == 1.0f && r.lo < 0.0f))) return {0.0f, 0.0f};
     const ff s = ff_add({1.0f, 0.0f}, ff_neg(r));
     const ff s2 = ff_sqr(s), s4 = ff_sqr(s2);
+    const int e = E > 0 ? E : w.e;
     ff pw;
-    switch (w.e) {
-    case 4: pw = s4; break;
-    case 6: pw = ff_mul(s4, s2); break;
-    case 8: pw = ff_sqr(s4); break;
-    default: {
+    if (e == 4) pw = s4;
+    else if (e == 6) pw = ff_mul(s4, s2);
+    else if (e == 8) pw = ff_sqr(s4);
+    else {
         pw = {1.0f, 0.0f};
-        for (int i = 0; i < w.e; ++i) pw = ff_mul(pw, s);
+        for (int i = 0; i < e; ++i) pw = ff_mul(pw, s);
     }
-    }
-    ff p = ff_from_double(w.c[w.k]);
-    for (int i = w.k - 1; i >= 0; --i) p = ff_add(ff_mul(p, r), ff_from_double(w.c[i]));
+    const int k = E > 0 ? K : w.k;
+    ff p = c[k];
+#pragma unroll
+    for (int i = 3; i >= 1; --i)
+        if (i <= k) p = ff_add(ff_mul(p, r), c[i - 1]);
     return ff_mul(pw, p);
 }
 
 // delta_j^-d phi(|x_p - y| / delta_j) for point p of level j (cell cp, offsets W + Wlo) and
 // y's frame f in level j's grid: the scaled offset on axis a is
-// (cp_a - c_a) cod + (W_a + Wlo_a) - (fr_a + frlo_a).
-__device__ __forceinline__ double ff_entry(const HierView& v, const float* __restrict__ W,
+// (cp_a - c_a) cod + (W_a + Wlo_a) - (fr_a + frlo_a).  cod_exact: cod is a float, so the cell
+// term is an exact FP32 product.
+template <int E, int K>
+__device__ __forceinline__ ff ff_entry(const HierView& v, const float* __restrict__ W,
                                            const float* __restrict__ Wlo, const int32_t* __restrict__ cellid,
                                            const FFLevels& ffl, int j, int32_t p, const Frame& f) {
     int cp[3];
     demorton(v.d, (uint32_t)__ldg(cellid + p), cp);
+    const bool cod_exact = ffl.cod[j].lo == 0.0f;
     ff r2 = {0.0f, 0.0f};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (a < v.d) {
-            const ff cell = ff_mul(ffl.cod[j], {(float)(cp[a] - f.c[a]), 0.0f});
             const ff w = {__ldg(W + a * v.N + p), __ldg(Wlo + a * v.N + p)};
-            const ff t = ff_add(ff_add(cell, w), ff_neg({f.fr[a], f.frlo[a]}));
-            r2 = ff_add(r2, ff_sqr(t));
+            const float dc = small_int_to_float(cp[a] - f.c[a]);
+            ff t;
+            if (cod_exact) {
+                t = ff_sum3(__fmul_rn(dc, ffl.cod[j].hi), w, {f.fr[a], f.frlo[a]});
+            } else {
+                t = ff_add(ff_add(ff_mul(ffl.cod[j], {dc, 0.0f}), w), ff_neg({f.fr[a], f.frlo[a]}));
+            }
+            r2 = a == 0 ? ff_sqr(t) : ff_add(r2, ff_sqr(t));
         }
     }
-    return ff_to_double(ff_mul(ffl.ds[j], ff_wendland(v.w, ff_sqrt(r2))));
+    return ff_mul(ffl.ds[j], ff_wendland<E, K>(v.w, ffl.c, ff_sqrt(r2)));
 }
 
 // Offset (units of delta) of a neighbour cell displaced by `dc` cells, seen from a point at
 // fractional offset fr in its own cell; both CSR kernels take it from here so that they
 // make the same decisions.
-__device__ __forceinline__ float cell_offset(int dc, float cod, float fr) { return __fsub_rn(__fmul_rn((float)dc, cod), fr); }
+__device__ __forceinline__ float cell_offset(int dc, float cod, float fr) {
+    return __fsub_rn(__fmul_rn(small_int_to_float(dc), cod), fr);
+}
 
 // |x_p - y| < delta_j for candidate p in the neighbour cell with offsets (c0, c1, c2): FP32
 // test on the cell-relative coordinates W (units of delta_j), the FP64 distance inside a band
@@ -265,75 +284,42 @@ __device__ __forceinline__ bool within(const HierView& v, const float* __restric
     return false;
 }
 
-// visit(p, in, mask): called by all 32 lanes for every group of up to 32
-// candidates p; `in` = p is a neighbour, mask = ballot of `in`.  f: y's frame in
-// level j's grid.  The (2R+1)^d cells around f's cell are taken 32 at a time (lane q
-// looks up cell q's point range); their points form one list in cell order (dx
-// fastest, then dy, dz; points in sorted order within a cell), which the warp walks 32
-// candidates per step with every lane busy (cells hold ~16 points, so a step per cell
-// would leave half the lanes idle and repeat the per-cell work in every lane).
-template <typename F>
-__device__ __forceinline__ void warp_neighbours(const HierView& v, const float* __restrict__ W, int j,
-                                                const Frame& f, const Pt& y, int lane, F&& visit) {
-    const LevelGrid& g = v.grid[j];
-    const float cod = g.cod;
-    const double d2 = v.delta[j] * v.delta[j];
-    const int R = v.R, side = 2 * R + 1;
-    const int nc = v.d == 1 ? side : (v.d == 2 ? side * side : side * side * side);
-    for (int q0 = 0; q0 < nc; q0 += 32) {
-        const int q = q0 + lane;
-        int start = 0, cnt = 0;
-        float o0 = 0.f, o1 = 0.f, o2 = 0.f;
-        if (q < nc) {
-            const int dx = q % side - R;
-            const int dy = v.d >= 2 ? (q / side) % side - R : 0;
-            const int dz = v.d >= 3 ? q / (side * side) - R : 0;
-            const int cx = f.c[0] + dx, cy = f.c[1] + dy, cz = f.c[2] + dz;
-            if (cx >= 0 && cx < g.G[0] && cy >= 0 && cy < g.G[1] && cz >= 0 && cz < g.G[2]) {
-                const int64_t gid = g.cell_off + morton(v.d, cx, cy, cz);
-                start = __ldg(v.cell_start + gid);
-                cnt = __ldg(v.cell_start + gid + 1) - start;
-            }
-            o0 = cell_offset(dx, cod, f.fr[0]);
-            o1 = cell_offset(dy, cod, f.fr[1]);
-            o2 = cell_offset(dz, cod, f.fr[2]);
-        }
-        int incl = cnt;  // inclusive prefix of the cells' point counts over the lanes
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        for (int b = 0; b < total; b += 32) {
-            const int i = b + lane;
-            // cell of candidate i: the number of cells whose inclusive prefix is <= i
-            // (branch-free binary search over the lanes; every lane takes every step)
-            int cq = 0;
-#pragma unroll
-            for (int st = 16; st >= 1; st >>= 1) {
-                const int pv = __shfl_sync(0xffffffffu, incl, cq + st - 1);
-                if (pv <= i) cq += st;
-            }
-            const int cs = __shfl_sync(0xffffffffu, start, cq);
-            const int ce = __shfl_sync(0xffffffffu, incl, cq) - __shfl_sync(0xffffffffu, cnt, cq);
-            const float c0 = __shfl_sync(0xffffffffu, o0, cq);
-            const float c1 = __shfl_sync(0xffffffffu, o1, cq);
-            const float c2 = __shfl_sync(0xffffffffu, o2, cq);
-            const int32_t p = cs + (i - ce);
-            const bool in = i < total && within(v, W, p, c0, c1, c2, y, d2);
-            visit(p, in, __ballot_sync(0xffffffffu, in));
-        }
-    }
-}
-
 constexpr int kCsrBS = 256;  // 8 rows per block
 
+// Candidate cells of row s: the (2R+1)^d cells around y's cell in each level j <= k, as
+// pairs t = j nc + q (q: dx fastest, then dy, dz).  Pair t of row s has slot
+// PairLayout::base[k] + (s - off[k]) (k + 1) nc + t in the per-pair count array.
+struct PairLayout {
+    int64_t base[MS_MAXL];
+    int nc;
+};
+
+// The points [ps, pe) and the cell offsets (units of delta_j) of pair q of level j, seen
+// from y's frame f in level j's grid; false when the cell lies outside the grid.
+__device__ __forceinline__ bool pair_cell(const HierView& v, int j, int q, const Frame& f, int32_t& ps, int32_t& pe,
+                                          float& o0, float& o1, float& o2) {
+    const LevelGrid& g = v.grid[j];
+    const int R = v.R, side = 2 * R + 1;
+    const int dx = q % side - R;
+    const int dy = v.d >= 2 ? (q / side) % side - R : 0;
+    const int dz = v.d >= 3 ? q / (side * side) - R : 0;
+    const int cx = f.c[0] + dx, cy = f.c[1] + dy, cz = f.c[2] + dz;
+    if (cx < 0 || cx >= g.G[0] || cy < 0 || cy >= g.G[1] || cz < 0 || cz >= g.G[2]) return false;
+    const int64_t gid = g.cell_off + morton(v.d, cx, cy, cz);
+    ps = __ldg(v.cell_start + gid);
+    pe = __ldg(v.cell_start + gid + 1);
+    o0 = cell_offset(dx, g.cod, f.fr[0]);
+    o1 = cell_offset(dy, g.cod, f.fr[1]);
+    o2 = cell_offset(dz, g.cod, f.fr[2]);
+    return true;
+}
+
 // Entries of row s: one warp per row, one lane per (column level j, neighbour cell) pair
-// at a time, each lane walking its cell's points (the count needs no positions, so no
-// compaction across lanes).
-__global__ void __launch_bounds__(kCsrBS, 4) k_csr_count(HierView v, const float* __restrict__ W, int32_t* cntA,
-                                                       int32_t* cntB) {
+// at a time, each lane walking its cell's points.  Also stores each pair's count, from
+// which the fill places its columns.
+__global__ void __launch_bounds__(kCsrBS, 4) k_csr_count(const __grid_constant__ HierView v, const float* __restrict__ W,
+                                                       const __grid_constant__ PairLayout pl, int32_t* cntA,
+                                                       int32_t* cntB, int32_t* pcnt) {
     const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (s >= v.N) return;  // warp-uniform
@@ -342,35 +328,23 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_count(HierView v, const float
     // lane j <= k holds y's frame in level j's grid
     Frame mine{};
     if (lane <= k) mine = frame_of(v, lane, y);
-    const int R = v.R, side = 2 * R + 1;
-    const int nc = v.d == 1 ? side : (v.d == 2 ? side * side : side * side * side);
+    const int nc = pl.nc;
     const int pairs = (k + 1) * nc;
+    int32_t* pc = pcnt + pl.base[k] + (s - v.off[k]) * pairs;
     int32_t na = 0, nb = 0;
     for (int t0 = 0; t0 < pairs; t0 += 32) {
         const int t = t0 + lane;
         const int j = min(t / nc, k);  // lanes past the last pair read a valid frame and skip
-        Frame f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            f.c[a] = __shfl_sync(0xffffffffu, mine.c[a], j);
-            f.fr[a] = __shfl_sync(0xffffffffu, mine.fr[a], j);
-        }
+        const Frame f = frame_from(mine, j);
         if (t >= pairs) continue;
-        const LevelGrid& g = v.grid[j];
-        const int q = t - j * nc;
-        const int dx = q % side - R;
-        const int dy = v.d >= 2 ? (q / side) % side - R : 0;
-        const int dz = v.d >= 3 ? q / (side * side) - R : 0;
-        const int cx = f.c[0] + dx, cy = f.c[1] + dy, cz = f.c[2] + dz;
-        if (cx < 0 || cx >= g.G[0] || cy < 0 || cy >= g.G[1] || cz < 0 || cz >= g.G[2]) continue;
-        const int64_t gid = g.cell_off + morton(v.d, cx, cy, cz);
-        const int32_t ps = __ldg(v.cell_start + gid), pe = __ldg(v.cell_start + gid + 1);
-        const float o0 = cell_offset(dx, g.cod, f.fr[0]);
-        const float o1 = cell_offset(dy, g.cod, f.fr[1]);
-        const float o2 = cell_offset(dz, g.cod, f.fr[2]);
-        const double d2 = v.delta[j] * v.delta[j];
+        int32_t ps = 0, pe = 0;
+        float o0 = 0.f, o1 = 0.f, o2 = 0.f;
         int32_t n = 0;
-        for (int32_t p = ps; p < pe; ++p) n += within(v, W, p, o0, o1, o2, y, d2) ? 1 : 0;
+        if (pair_cell(v, j, t - j * nc, f, ps, pe, o0, o1, o2)) {
+            const double d2 = v.delta[j] * v.delta[j];
+            for (int32_t p = ps; p < pe; ++p) n += within(v, W, p, o0, o1, o2, y, d2) ? 1 : 0;
+        }
+        pc[t] = n;
         if (j == k) na += n;
         else nb += n;
     }
@@ -390,44 +364,73 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_count(HierView v, const float
 // column level j (j = 0..k; Bseg[k][s] = the row length).  The columns are
 // found first (FP32 test, compacted by ballot); the FP64 values then take all
 // 32 lanes over the row's entries.
-// FF: entries in double-float arithmetic (MIXED builds), else FP64.
-template <bool FF>
+// FF: entries in double-float arithmetic (MIXED builds), else FP64.  E, K: the Wendland
+// exponent and degree when compiled for them (0: taken from v.w).
+template <bool FF, int E, int K>
 __global__ void __launch_bounds__(kCsrBS, 4) k_csr_fill(const __grid_constant__ HierView v, const float* __restrict__ W,
                                                       const float* __restrict__ Wlo, const int32_t* __restrict__ cellid,
-                                                      const __grid_constant__ FFLevels ffl, const int64_t* rpA,
+                                                      const __grid_constant__ FFLevels ffl,
+                                                      const __grid_constant__ PairLayout pl,
+                                                      const int32_t* __restrict__ pcnt, const int64_t* rpA,
                                                       int32_t* colA, double* valA, float* valA32, const int64_t* rpB,
                                                       int32_t* colB, double* valB, float* valB32, int32_t* Bseg) {
     const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (s >= v.N) return;  // warp-uniform
-    const unsigned below = (1u << lane) - 1u;
     const int k = level_of_row(v.off, v.L, s);
     const Pt y = point_at(v, s);
     Frame mine{};
     if (lane <= k) mine = frame_of(v, lane, y);
-    auto emit = [&](int j, int64_t& pos, int32_t* col) {
-        warp_neighbours(v, W, j, frame_from(mine, j), y, lane, [&](int32_t p, bool in, unsigned m) {
-            if (in) col[pos + __popc(m & below)] = p;
-            pos += __popc(m);
-        });
-    };
-    const int64_t a0 = rpA[s];
-    int64_t pa = a0;
-    emit(k, pa, colA);
-    const int64_t b0 = rpB[s];
-    int64_t pb = b0;
-    for (int j = 0; j < k; ++j) {
-        if (lane == 0) Bseg[(int64_t)j * v.N + s] = (int32_t)(pb - b0);
-        emit(j, pb, colB);
+    // Columns: lane per (level, cell) pair as in the count; a warp scan of the stored pair
+    // counts (A pairs and B pairs separately, in pair order) gives every lane the position
+    // of its cell's first entry, so the columns come out in the order of the pairs (B: level
+    // by level), points in cell order, and the count's decisions are repeated exactly.
+    const int nc = pl.nc;
+    const int pairs = (k + 1) * nc;
+    const int32_t* pc = pcnt + pl.base[k] + (s - v.off[k]) * pairs;
+    const int64_t a0 = rpA[s], b0 = rpB[s];
+    int64_t pa = a0, pb = b0;
+    for (int t0 = 0; t0 < pairs; t0 += 32) {
+        const int t = t0 + lane;
+        const bool ok = t < pairs;
+        const int j = min(t / nc, k);
+        const Frame f = frame_from(mine, j);
+        const int32_t n = ok ? __ldg(pc + t) : 0;
+        const bool isA = ok && j == k;
+        int32_t ia = isA ? n : 0, ib = (ok && !isA) ? n : 0;  // inclusive scans over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t ua = __shfl_up_sync(0xffffffffu, ia, o), ub = __shfl_up_sync(0xffffffffu, ib, o);
+            if (lane >= o) {
+                ia += ua;
+                ib += ub;
+            }
+        }
+        const int32_t ta = __shfl_sync(0xffffffffu, ia, 31), tb = __shfl_sync(0xffffffffu, ib, 31);
+        const int q = t - j * nc;
+        // first pair of a column level j < k: its segment of the B row starts here
+        if (ok && !isA && q == 0) Bseg[(int64_t)j * v.N + s] = (int32_t)(pb + ib - n - b0);
+        if (ok && n > 0) {
+            int32_t ps = 0, pe = 0;
+            float o0 = 0.f, o1 = 0.f, o2 = 0.f;
+            pair_cell(v, j, q, f, ps, pe, o0, o1, o2);
+            const double d2 = v.delta[j] * v.delta[j];
+            int32_t* col = isA ? colA : colB;
+            int64_t pos = isA ? pa + ia - n : pb + ib - n;
+            for (int32_t p = ps; p < pe; ++p)
+                if (within(v, W, p, o0, o1, o2, y, d2)) col[pos++] = p;
+        }
+        pa += ta;
+        pb += tb;
     }
     if (lane == 0) Bseg[(int64_t)k * v.N + s] = (int32_t)(pb - b0);
     __syncwarp();  // the columns written by the other lanes are read below
     if (FF) {
         const Frame fk = frame_from(mine, k);
         for (int64_t i = a0 + lane; i < pa; i += 32) {
-            const double value = ff_entry(v, W, Wlo, cellid, ffl, k, colA[i], fk);
-            valA[i] = value;
-            if (valA32) valA32[i] = (float)value;
+            const ff value = ff_entry<E, K>(v, W, Wlo, cellid, ffl, k, colA[i], fk);
+            valA[i] = ff_to_double(value);
+            if (valA32) valA32[i] = value.hi;  // the FP32 value nearest to hi + lo (|lo| <= ulp(hi) / 2)
         }
         // every lane takes part in each step (the frame of the entry's level comes by shuffle)
         for (int64_t i0 = b0; i0 < pb; i0 += 32) {
@@ -437,9 +440,9 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_fill(const __grid_constant__ 
             const int j = level_of_row(v.off, v.L, p);
             const Frame fj = frame_from(mine, j);
             if (ok) {
-                const double value = ff_entry(v, W, Wlo, cellid, ffl, j, p, fj);
-                valB[i] = value;
-                if (valB32) valB32[i] = (float)value;
+                const ff value = ff_entry<E, K>(v, W, Wlo, cellid, ffl, j, p, fj);
+                valB[i] = ff_to_double(value);
+                if (valB32) valB32[i] = value.hi;
             }
         }
         return;
@@ -602,20 +605,34 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
     MS_CUDA(cudaGetLastError());
     // double-float entries (MIXED) also need the low parts of the offsets
     const bool ffvals = h->opts.precision == MS_PREC_MIXED;
-    float* Wlo = nullptr;
     MS_TRY(ms_alloc(h, (void**)&h->W, sizeof(float) * d * N));
     MS_TRY(ms_alloc(h, (void**)&h->cellid, sizeof(int32_t) * N));
-    if (ffvals) MS_TRY(talloc((void**)&Wlo, sizeof(float) * d * N));
+    if (ffvals) MS_TRY(ms_alloc(h, (void**)&h->Wlo, sizeof(float) * d * N));
+    float* Wlo = h->Wlo;
     k_mf_coords<<<nblk(N, 256), 256, 0, st>>>(v, h->W, Wlo, h->cellid); ms_count_launch();
     MS_CUDA(cudaGetLastError());
 
     // 3. CSR of A (diagonal blocks) and B (strictly lower blocks)
-    int32_t *cntA, *cntB;
+    int32_t *cntA, *cntB, *pcnt = nullptr;
     MS_TRY(talloc((void**)&cntA, sizeof(int32_t) * N));
     MS_TRY(talloc((void**)&cntB, sizeof(int32_t) * N));
     MS_TRY(ms_alloc(h, (void**)&h->A.rp, sizeof(int64_t) * (N + 1)));
     MS_TRY(ms_alloc(h, (void**)&h->B.rp, sizeof(int64_t) * (N + 1)));
-    k_csr_count<<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, cntA, cntB); ms_count_launch();
+    // per-(row, level, cell) counts: rows of level k have (k + 1) nc pairs
+    PairLayout pl{};
+    {
+        const int side = 2 * v.R + 1;
+        pl.nc = d == 1 ? side : (d == 2 ? side * side : side * side * side);
+        int64_t tot = 0;
+        for (int l = 0; l < L; ++l) {
+            pl.base[l] = tot;
+            tot += (v.off[l + 1] - v.off[l]) * (int64_t)(l + 1) * pl.nc;
+        }
+        int32_t* pc = nullptr;
+        MS_TRY(talloc((void**)&pc, sizeof(int32_t) * tot));
+        pcnt = pc;
+    }
+    k_csr_count<<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, pl, cntA, cntB, pcnt); ms_count_launch();
     exclusive_scan<int32_t, int64_t>(cntA, N, h->A.rp, (int64_t*)tile, st);
     exclusive_scan<int32_t, int64_t>(cntB, N, h->B.rp, (int64_t*)tile, st);
     MS_CUDA(cudaGetLastError());
@@ -640,14 +657,18 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
         ffl.cod[l] = ff_from_double(v.grid[l].cell / v.delta[l]);
         ffl.ds[l] = ff_from_double(v.dscale[l]);
     }
-    if (ffvals)
-        k_csr_fill<true><<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, Wlo, h->cellid, ffl, h->A.rp, h->A.col,
-                                                                  h->A.v64, h->A.v32, h->B.rp, h->B.col, h->B.v64,
-                                                                  h->B.v32, h->Bseg);
-    else
-        k_csr_fill<false><<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, nullptr, h->cellid, ffl, h->A.rp,
-                                                                   h->A.col, h->A.v64, h->A.v32, h->B.rp, h->B.col,
-                                                                   h->B.v64, h->B.v32, h->Bseg);
+    for (int i = 0; i < 4; ++i) ffl.c[i] = ff_from_double(v.w.c[i]);
+    {
+        // phi_{d,1} has (e, k) = (floor(d/2) + 3, 1) and phi_{d,2} (floor(d/2) + 5, 2): (4, 1) and (6, 2)
+        // for d = 2, 3 get their own straight-line code
+        auto fill = ffvals ? (v.w.e == 4 && v.w.k == 1   ? k_csr_fill<true, 4, 1>
+                              : v.w.e == 6 && v.w.k == 2 ? k_csr_fill<true, 6, 2>
+                                                         : k_csr_fill<true, 0, 0>)
+                           : k_csr_fill<false, 0, 0>;
+        fill<<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, Wlo, h->cellid, ffl, pl, pcnt, h->A.rp, h->A.col,
+                                                      h->A.v64, h->A.v32, h->B.rp, h->B.col, h->B.v64, h->B.v32,
+                                                      h->Bseg);
+    }
     ms_count_launch();
     unsigned long long* blk;
     MS_TRY(talloc((void**)&blk, sizeof(unsigned long long) * L * L));

@@ -1,11 +1,12 @@
 // Evaluation of the multiscale approximant at query points (eq. fapproximation):
 //   f_L(q) = sum_l sum_n alpha_n^(l) Phi_{delta_l}(q - x_n^(l)),
 // one thread per query, every level's neighbours found through that level's
-// cell grid, FP64 distances, kernel values and accumulation.  An FP32 test on the
-// points' cell-relative offsets rejects the clear misses (about 2/3 of the
-// candidates) before any FP64 work.
+// cell grid, FP64 accumulation.  An FP32 test on the points' cell-relative
+// offsets rejects the clear misses (about 2/3 of the candidates) first; the
+// kernel values are FP64 (FP64 builds) or double-float (MIXED builds).
 #include <algorithm>
 
+#include "ms_ff.cuh"
 #include "ms_internal.cuh"
 
 namespace {
@@ -61,7 +62,39 @@ __device__ __forceinline__ void eval_neighbours(const HierView& v, const float* 
     }
 }
 
-__global__ void k_eval(HierView v, const float* __restrict__ W, const double* __restrict__ alpha,
+// phi(r) for the Wendland closed form w in double-float, 0 for r >= 1 (as in the CSR fill).
+__device__ __forceinline__ ff eval_ff_wendland(const WendlandPoly& w, const ff* c, ff r) {
+    if (!(r.hi < 1.0f || (r.hi == 1.0f && r.lo < 0.0f))) return {0.0f, 0.0f};
+    const ff s = ff_add({1.0f, 0.0f}, ff_neg(r));
+    const ff s2 = ff_sqr(s), s4 = ff_sqr(s2);
+    ff pw;
+    switch (w.e) {
+    case 4: pw = s4; break;
+    case 6: pw = ff_mul(s4, s2); break;
+    case 8: pw = ff_sqr(s4); break;
+    default: {
+        pw = {1.0f, 0.0f};
+        for (int i = 0; i < w.e; ++i) pw = ff_mul(pw, s);
+    }
+    }
+    ff p = c[w.k];
+    for (int i = w.k - 1; i >= 0; --i) p = ff_add(ff_mul(p, r), c[i]);
+    return ff_mul(pw, p);
+}
+
+// Per-level cell size / delta and the Wendland coefficients as double-floats (converted
+// once on the host).
+struct EvalLevels {
+    ff cod[MS_MAXL];
+    ff c[4];
+};
+
+// FF (MIXED builds): the kernel values in double-float arithmetic from the points'
+// cell-relative offsets W + Wlo and the query's own offset in its cell (about 48 bits,
+// ~1e-14 relative; the sums stay FP64).  Otherwise FP64 distances and values.
+template <bool FF>
+__global__ void k_eval(const __grid_constant__ HierView v, const float* __restrict__ W, const float* __restrict__ Wlo,
+                       const __grid_constant__ EvalLevels el, const double* __restrict__ alpha,
                        const double* __restrict__ Q, int64_t nq, double* __restrict__ out, int nrhs, int col) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nq) return;
@@ -69,11 +102,60 @@ __global__ void k_eval(HierView v, const float* __restrict__ W, const double* __
     for (int a = 0; a < v.d; ++a) y[a] = Q[i * v.d + a];
     double s = 0.0;
     for (int l = 0; l < v.L; ++l) {
-        const double inv = 1.0 / v.delta[l], sc = v.dscale[l];
+        const double sc = v.dscale[l];
         double sl = 0.0;
-        eval_neighbours(v, W, l, y, [&](int32_t p, double r2) {
-            sl = fma(wendland_eval<double>(v.w, sqrt(r2) * inv), alpha[p], sl);
-        });
+        if (!FF) {
+            const double inv = 1.0 / v.delta[l];
+            eval_neighbours(v, W, l, y, [&](int32_t p, double r2) {
+                sl = fma(wendland_eval<double>(v.w, sqrt(r2) * inv), alpha[p], sl);
+            });
+        } else {
+            const LevelGrid& g = v.grid[l];
+            int c[3] = {0, 0, 0};
+            float fr[3] = {0.f, 0.f, 0.f}, frlo[3] = {0.f, 0.f, 0.f};
+            for (int a = 0; a < v.d; ++a) {
+                c[a] = cell_coord(g, a, y[a]);
+                const double t = (y[a] - (g.lo[a] + (double)c[a] * g.cell)) * v.inv_delta[l];
+                fr[a] = (float)t;
+                frlo[a] = (float)(t - (double)fr[a]);
+            }
+            const int R = v.R;
+            const int rz = v.d >= 3 ? R : 0, ry = v.d >= 2 ? R : 0;
+            for (int dz = -rz; dz <= rz; ++dz) {
+                const int cz = c[2] + dz;
+                if (cz < 0 || cz >= g.G[2]) continue;
+                for (int dy = -ry; dy <= ry; ++dy) {
+                    const int cy = c[1] + dy;
+                    if (cy < 0 || cy >= g.G[1]) continue;
+                    for (int dx = -R; dx <= R; ++dx) {
+                        const int cx = c[0] + dx;
+                        if (cx < 0 || cx >= g.G[0]) continue;
+                        const int dc[3] = {dx, dy, dz};
+                        ff o[3];
+                        float of[3];
+                        for (int a = 0; a < 3; ++a) {
+                            o[a] = ff_add(ff_mul(el.cod[l], {(float)dc[a], 0.0f}), ff_neg({fr[a], frlo[a]}));
+                            of[a] = o[a].hi;
+                        }
+                        const int64_t gid = g.cell_off + morton(v.d, cx, cy, cz);
+                        const int32_t ps = v.cell_start[gid], pe = v.cell_start[gid + 1];
+                        for (int32_t p = ps; p < pe; ++p) {
+                            // FP32 prefilter, then the double-float distance
+                            float t = of[0] + __ldg(W + p);
+                            float qq = t * t;
+                            if (v.d >= 2) { t = of[1] + __ldg(W + v.N + p); qq = fmaf(t, t, qq); }
+                            if (v.d >= 3) { t = of[2] + __ldg(W + 2 * v.N + p); qq = fmaf(t, t, qq); }
+                            if (qq > 1.0f + 1e-4f) continue;
+                            ff r2 = {0.0f, 0.0f};
+                            for (int a = 0; a < v.d; ++a)
+                                r2 = ff_add(r2, ff_sqr(ff_add(o[a], {__ldg(W + a * v.N + p), __ldg(Wlo + a * v.N + p)})));
+                            const ff phi = eval_ff_wendland(v.w, el.c, ff_sqrt(r2));
+                            if (phi.hi != 0.0f) sl = fma(ff_to_double(phi), alpha[p], sl);
+                        }
+                    }
+                }
+            }
+        }
         s = fma(sc, sl, s);
     }
     out[i * nrhs + col] = s;
@@ -89,10 +171,17 @@ ms_status ms_evaluate_impl(ms_hierarchy* h, const double* alpha_dev, int nrhs, c
         MS_TRY(ms_alloc(h, &p, sizeof(double) * h->N));
         h->tmp64 = (double*)p;
     }
+    EvalLevels el{};
+    for (int l = 0; l < h->L; ++l) el.cod[l] = ff_from_double(h->view.grid[l].cell / h->view.delta[l]);
+    for (int i = 0; i < 4; ++i) el.c[i] = ff_from_double(h->view.w.c[i]);
     for (int c = 0; c < nrhs; ++c) {
         ms_gather_sorted(alpha_dev, h->tmp64, h->perm, h->N, nrhs, c, st);
         const unsigned blocks = (unsigned)std::max<int64_t>(1, (nq + 127) / 128);
-        k_eval<<<blocks, 128, 0, st>>>(h->view, h->W, h->tmp64, q_dev, nq, out_dev, nrhs, c); ms_count_launch();
+        if (h->Wlo)
+            k_eval<true><<<blocks, 128, 0, st>>>(h->view, h->W, h->Wlo, el, h->tmp64, q_dev, nq, out_dev, nrhs, c);
+        else
+            k_eval<false><<<blocks, 128, 0, st>>>(h->view, h->W, nullptr, el, h->tmp64, q_dev, nq, out_dev, nrhs, c);
+        ms_count_launch();
         MS_CUDA(cudaGetLastError());
     }
     return MS_OK;

@@ -10,6 +10,8 @@
 // the compiler cannot contract or reorder it.
 #pragma once
 
+#include <cstdint>
+
 struct ff {
     float hi, lo;
 };
@@ -54,17 +56,49 @@ __device__ __forceinline__ ff ff_sqr(ff a) {
     return ff_fast_two_sum(p, e);
 }
 
-// sqrt(a) for a >= 0: s = sqrtf(hi) (correctly rounded, relative error <= 2^-24), then one
-// Newton (Heron) step s + (a - s^2) / (2 s) with a - s^2 formed exactly, which squares the
-// relative error (below 1e-14 with the rounding of the step).  a = 0 gives 0.
+// sqrt(a) for a >= 0.  y = 1/sqrt(hi) from the hardware estimate refined by one FP32
+// Newton step y (3 - hi y^2) / 2 (about one unit in the last place), s = hi y, then one
+// Newton (Heron) step s + (a - s^2) y / 2 with a - s^2 formed exactly: the step squares
+// s's relative error (~1e-7 -> ~1e-14).  No IEEE square-root or division sequence.
+// a = 0 gives 0.
 __device__ __forceinline__ ff ff_sqrt(ff a) {
     if (!(a.hi > 0.0f)) return {0.0f, 0.0f};
-    const float s = __fsqrt_rn(a.hi);
+    const float y0 = rsqrtf(a.hi);
+    const float y = __fmul_rn(y0, __fmaf_rn(__fmul_rn(-0.5f * a.hi, y0), y0, 1.5f));
+    const float s = __fmul_rn(a.hi, y);
     const float p = __fmul_rn(s, s);
     const float pe = __fmaf_rn(s, s, -p);                              // s^2 = p + pe exactly
     const float e = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo);  // a - s^2
-    return ff_fast_two_sum(s, __fmul_rn(e, __fdiv_rn(0.5f, s)));
+    return ff_fast_two_sum(s, __fmul_rn(e, __fmul_rn(0.5f, y)));
 }
 
-// The exact sum hi + lo as a double (two conversions and one FP64 addition).
-__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+// (a + b) - c for a float a and double-floats b, c where a - c.hi is formed exactly first:
+// the cell offset plus a point's in-cell offset minus the reference point's.
+__device__ __forceinline__ ff ff_sum3(float a, ff b, ff c) {
+    const ff base = ff_two_sum(a, -c.hi);
+    return ff_add({base.hi, __fsub_rn(base.lo, c.lo)}, b);
+}
+
+// A float as a double, by the IEEE 754 layouts (binary32: 1 sign, 8 exponent bits biased
+// by 127, 23 fraction bits; binary64: 11 exponent bits biased by 1023, 52 fraction bits):
+// for a normal float keep the sign, rebias the exponent by 1023 - 127 = 896 and widen the
+// fraction by 29 bits.  Integer instructions only; zeros keep their sign, and subnormals,
+// infinities and NaNs take the hardware conversion.  Exact, like any float-to-double widening.
+__device__ __forceinline__ double f2d_exact(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    const uint64_t sign = (uint64_t)(b >> 31) << 63;
+    if ((b << 1) == 0u) return __longlong_as_double((long long)sign);
+    if (e == 0u || e == 0xFFu) return (double)f;
+    return __longlong_as_double((long long)(sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29)));
+}
+
+// A small integer (|n| < 2^22) as a float without a conversion instruction: placed in the
+// fraction of 1.5 * 2^23, whose unit in the last place is 1, then the bias subtracted.
+// Exact for every n in range.
+__device__ __forceinline__ float small_int_to_float(int n) {
+    return __fsub_rn(__int_as_float(0x4B400000 + n), 12582912.0f);
+}
+
+// hi + lo rounded to a double: two exact widenings and one FP64 addition.
+__device__ __forceinline__ double ff_to_double(ff a) { return f2d_exact(a.hi) + f2d_exact(a.lo); }

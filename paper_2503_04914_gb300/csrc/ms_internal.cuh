@@ -317,6 +317,7 @@ struct ms_hierarchy {
     int32_t* perm = nullptr;     // sorted -> input
     int32_t* cell_start = nullptr;
     float* W = nullptr;          // [d][N] FP32 offsets from the own cell corner, in units of delta_l
+    float* Wlo = nullptr;        // [d][N] their low parts (W + Wlo: about 48 bits; MIXED builds)
     int32_t* cellid = nullptr;   // [N] level-local Morton cell of each sorted point
     int mf_tpp = 2;              // matrix-free lanes per target point
     DevCSR A, B;

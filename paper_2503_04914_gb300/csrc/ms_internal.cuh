@@ -16,6 +16,8 @@
 
 #include <cstdint>
 #include <vector>
+
+#include <cuda_fp16.h>
 #include <cstdio>
 #include <cuda_runtime.h>
 #include <cuda/atomic>
@@ -294,10 +296,10 @@ struct Precond {
     float* musig = nullptr;      // [2 * kPcOut] standardisation of the scale-free targets
     int32_t* nbr = nullptr;      // [N][kPcK] pattern neighbours (sorted positions, -1 = none)
     int32_t* gcol = nullptr;     // [kPcOut][N] row pattern of G (slot 0 = self, -1 = none; slot-major)
-    float* gval = nullptr;       // [kPcOut][N] values of G
+    __half* gval = nullptr;      // [kPcOut][N] scale-free rows ghat (G = delta_l^{d/2} ghat), FP16
     int64_t* gt_rp = nullptr;    // [N+1] rows of G^T (in-pattern)
     int32_t* gt_col = nullptr;   // [nnz] source rows
-    float* gt_val = nullptr;     // [nnz]
+    __half* gt_val = nullptr;    // [nnz] ghat^T values, FP16
     int64_t gt_nnz = 0;
     int fp32_weights = 0;
     int augment = 4;                     // extra training patches per point (last training)

@@ -175,7 +175,7 @@ __device__ void pc_exact_row(const HierView& v, const int32_t* nb, int64_t s, do
 // Patch i -> ghat[i][17]; optional G values.  rows == nullptr: patch i is the pattern of
 // sorted row i (nbr [N][16]); else it is centred on rows[i] with neighbours nbr[i][16].
 __global__ void k_pc_exact(HierView v, const int32_t* nbr, const int64_t* rows, int64_t n, double* ghat_out,
-                           float* gval, int32_t* gcol) {
+                           __half* gval, int32_t* gcol) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t s = rows ? rows[i] : i;
@@ -183,15 +183,13 @@ __global__ void k_pc_exact(HierView v, const int32_t* nbr, const int64_t* rows, 
     pc_exact_row(v, nbr + i * kPcK, s, g);
     if (ghat_out)
         for (int a = 0; a < kPcOut; ++a) ghat_out[i * kPcOut + a] = g[a];
-    if (gval) {
-        const int l = level_of_row(v.off, v.L, s);
-        const double sc = pow(v.delta[l], 0.5 * v.d);
+    if (gval) {  // the scale-free row in FP16; the solve applies delta^d to G^T G
         gcol[s] = (int32_t)s;
-        gval[s] = (float)(sc * g[0]);
+        gval[s] = __float2half_rn((float)g[0]);
         for (int k = 0; k < kPcK; ++k) {
             const int32_t c = nbr[s * kPcK + k];
             gcol[(1 + k) * v.N + s] = c;
-            gval[(1 + k) * v.N + s] = c >= 0 ? (float)(sc * g[1 + k]) : 0.f;
+            gval[(1 + k) * v.N + s] = __float2half_rn(c >= 0 ? (float)g[1 + k] : 0.f);
         }
     }
 }
@@ -395,7 +393,7 @@ __device__ __forceinline__ void mlp_forward(const NetLayout& N, const float* W, 
 // scaled so that ghat^T K ghat = 1.
 // Writes G = delta^{d/2} ghat (FP32) and the row pattern, or ghat itself for inspection.
 __global__ void k_pc_infer(HierView v, const int32_t* nbr, const float* theta, int nparams, const float* musig,
-                           float* gval, int32_t* gcol, float* ghat_out) {
+                           __half* gval, int32_t* gcol, float* ghat_out) {
     extern __shared__ float W[];
     for (int i = threadIdx.x; i < nparams; i += blockDim.x) W[i] = theta[i];
     __shared__ float ms[2 * kPcOut];
@@ -445,15 +443,15 @@ __global__ void k_pc_infer(HierView v, const int32_t* nbr, const float* theta, i
         for (int k = 0; k < kPcK; ++k) ghat_out[s * kPcOut + 1 + k] = nbr[s * kPcK + k] >= 0 ? g[q++] : 0.f;
         return;
     }
-    const int l = level_of_row(v.off, v.L, s);
-    const float sc = (float)pow(v.delta[l], 0.5 * v.d);
+    // the scale-free row in FP16 (relative rounding 2^-11, far below the network's own error);
+    // the solve applies delta_l^d to G^T G
     gcol[s] = (int32_t)s;
-    gval[s] = sc * g[0];
+    gval[s] = __float2half_rn(g[0]);
     int q = 1;
     for (int k = 0; k < kPcK; ++k) {
         const int32_t c = nbr[s * kPcK + k];
         gcol[(1 + k) * v.N + s] = c;
-        gval[(1 + k) * v.N + s] = c >= 0 ? sc * g[q++] : 0.f;
+        gval[(1 + k) * v.N + s] = __float2half_rn(c >= 0 ? g[q++] : 0.f);
     }
 }
 
@@ -637,8 +635,8 @@ __global__ void k_gt_count(const int32_t* gcol, int64_t N, int32_t* cnt) {
         if (c >= 0) atomicAdd(&cnt[c], 1);
     }
 }
-__global__ void k_gt_fill(const int32_t* gcol, const float* gval, int64_t N, const int64_t* rp, int32_t* cursor,
-                          int32_t* col, float* val) {
+__global__ void k_gt_fill(const int32_t* gcol, const __half* gval, int64_t N, const int64_t* rp, int32_t* cursor,
+                          int32_t* col, __half* val) {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= N) return;
     for (int k = 0; k < kPcOut; ++k) {
@@ -653,7 +651,7 @@ __global__ void k_gt_fill(const int32_t* gcol, const float* gval, int64_t N, con
 // to 32 entries (nearly all) lane i holds entry i and writes it at its rank among the row's
 // source rows (all distinct: a row of G names each column once); longer rows are sorted in
 // place by one lane.
-__global__ void k_gt_sort(const int64_t* rp, int32_t* col, float* val, int64_t N) {
+__global__ void k_gt_sort(const int64_t* rp, int32_t* col, __half* val, int64_t N) {
     const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (c >= N) return;  // warp-uniform
@@ -661,7 +659,7 @@ __global__ void k_gt_sort(const int64_t* rp, int32_t* col, float* val, int64_t N
     const int n = (int)(e - s);
     if (n <= 32) {
         const int32_t mc = lane < n ? col[s + lane] : INT_MAX;
-        const float mv = lane < n ? val[s + lane] : 0.f;
+        const __half mv = lane < n ? val[s + lane] : __float2half_rn(0.f);
         int rank = 0;
 #pragma unroll
         for (int j = 0; j < 32; ++j) rank += __shfl_sync(0xffffffffu, mc, j) < mc ? 1 : 0;
@@ -675,7 +673,7 @@ __global__ void k_gt_sort(const int64_t* rp, int32_t* col, float* val, int64_t N
     if (lane != 0) return;
     for (int64_t i = s + 1; i < e; ++i) {
         const int32_t kc = col[i];
-        const float kv = val[i];
+        const __half kv = val[i];
         int64_t j = i - 1;
         while (j >= s && col[j] > kc) {
             col[j + 1] = col[j];
@@ -706,7 +704,7 @@ uint64_t gcd64(uint64_t a, uint64_t b) {
 }
 
 // G rows (gval/gcol) or, with ghat_out, the scale-free rows of every point from the network.
-ms_status launch_infer(ms_hierarchy* h, float* gval, int32_t* gcol, float* ghat_out, cudaStream_t st) {
+ms_status launch_infer(ms_hierarchy* h, __half* gval, int32_t* gcol, float* ghat_out, cudaStream_t st) {
     const Precond& pc = h->pc;
     const size_t smem = sizeof(float) * pc.n_params;
     MS_CUDA(cudaFuncSetAttribute(k_pc_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -725,10 +723,10 @@ ms_status pc_alloc(ms_hierarchy* h) {
     const int64_t N = h->N;
     MS_TRY(ms_alloc(h, (void**)&pc.nbr, sizeof(int32_t) * N * kPcK));
     MS_TRY(ms_alloc(h, (void**)&pc.gcol, sizeof(int32_t) * N * kPcOut));
-    MS_TRY(ms_alloc(h, (void**)&pc.gval, sizeof(float) * N * kPcOut));
+    MS_TRY(ms_alloc(h, (void**)&pc.gval, sizeof(__half) * N * kPcOut));
     MS_TRY(ms_alloc(h, (void**)&pc.gt_rp, sizeof(int64_t) * (N + 1)));
     MS_TRY(ms_alloc(h, (void**)&pc.gt_col, sizeof(int32_t) * N * kPcOut));
-    MS_TRY(ms_alloc(h, (void**)&pc.gt_val, sizeof(float) * N * kPcOut));
+    MS_TRY(ms_alloc(h, (void**)&pc.gt_val, sizeof(__half) * N * kPcOut));
     MS_TRY(ms_alloc(h, (void**)&pc.theta, sizeof(float) * pc.n_params));
     MS_TRY(ms_alloc(h, (void**)&pc.theta_bf, sizeof(float) * pc.n_params));
     MS_TRY(ms_alloc(h, (void**)&pc.adam_m, sizeof(float) * pc.n_params));

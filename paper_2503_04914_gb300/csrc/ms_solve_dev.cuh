@@ -103,10 +103,11 @@ struct SolveArgs {
     // MIXED inner CG preconditioned with M = G^T G (pc = 1)
     int pc;
     const int32_t* gcol;   // [kPcOut][N] (slot-major: slot k of consecutive rows is contiguous)
-    const float* gval;     // [kPcOut][N]
+    const __half* gval;    // [kPcOut][N] scale-free rows ghat (FP16)
     const int64_t* gt_rp;  // rows of G^T
     const int32_t* gt_col;
-    const float* gt_val;
+    const __half* gt_val;
+    float pcs[MS_MAXL];    // delta_l^d: G^T G = delta_l^d ghat^T ghat on level l
     float *u32, *u1_32;    // [R][N]
     int* pcfb;             // [2] levels that fell back to plain CG, to FP64 inner CG
 };
@@ -610,7 +611,7 @@ __device__ __forceinline__ int decide_inner(const SolveArgs& a, Shared& sh, bool
         const bool lpc = use_pc && !sh.pcoff[v] && !dbl;
         const double n = (double)(a.off[l + 1] - a.off[l]);
         sh.vbytes[v] += (double)a.nnzA[l] * (dbl ? 12.0 : 8.0) + n * (dbl ? 32.0 : (lpc ? 24.0 : 20.0));
-        if (lpc) sh.vbytes[v] += n * (2.0 * kPcOut * 12.0 + 16.0);
+        if (lpc) sh.vbytes[v] += n * (2.0 * kPcOut * 10.0 + 16.0);
         if (!isfinite(gam) || !isfinite(del) || !isfinite(rho)) {
             sh.act[v] = 0;
             sh.oact[v] = 0;
@@ -747,7 +748,8 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
         for (;;) {
             const bool use_pc = MODE == 1 && a.pc;
             if (use_pc) {
-                // G1: u1 = G r  (row pattern: self + preceding neighbours)
+                // G1: u1 = ghat r  (row pattern: self + preceding neighbours; the level's
+                //     factor delta^d of G^T G is applied in G2)
                 run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0 && !sh.pcoff[v] && !sh.f64[v]; },
                              [&](const Chunk& ch, double*) {
                                  // two lanes per row (slots k = half, half + 2, ...), all threads busy
@@ -760,7 +762,7 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
 #pragma unroll
                                          for (int k = half; k < kPcOut; k += 2) {
                                              const int32_t c = __ldg(a.gcol + k * a.N + row);
-                                             if (c >= 0) acc = fmaf(__ldg(a.gval + k * a.N + row), rv[c], acc);
+                                             if (c >= 0) acc = fmaf(__half2float(__ldg(a.gval + k * a.N + row)), rv[c], acc);
                                          }
                                      }
                                      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
@@ -769,15 +771,15 @@ __device__ bool solve_levels(const SolveArgs& a, Shared& sh, int l0, int l1, boo
                              });
                 prof(sh, kPrfOther);
                 if (!gsync(a, sh)) return false;
-                // G2: u = G^T u1
+                // G2: u = delta^d ghat^T u1 = G^T G r
                 run_phase<0>(a, sh, [&](int v) { return sh.act[v] != 0 && !sh.pcoff[v] && !sh.f64[v]; },
                              [&](const Chunk& ch, double*) {
                                  const float* u1 = a.u1_32 + ch.vb;
                                  rows_by_subwarp(ch.r0, ch.r1, 2, [&](int64_t row, bool ok, int sl) {
                                      int64_t s = 0, e = 0;
                                      if (ok) { s = __ldg(a.gt_rp + row); e = __ldg(a.gt_rp + row + 1); }
-                                     const float y = csr_row<float, float, float>(a.gt_col, a.gt_val, u1, s, e, sl, 2);
-                                     if (ok && sl == 0) a.u32[ch.vb + row] = y;
+                                     const float y = csr_row<__half, float, float>(a.gt_col, a.gt_val, u1, s, e, sl, 2);
+                                     if (ok && sl == 0) a.u32[ch.vb + row] = a.pcs[ch.l] * y;
                                  });
                              });
                 prof(sh, kPrfOther);
@@ -1313,6 +1315,7 @@ void fill_args(const ms_hierarchy* h, double rel_tol, int R, SolveArgs& a, bool 
     a.gt_rp = h->pc.gt_rp;
     a.gt_col = h->pc.gt_col;
     a.gt_val = h->pc.gt_val;
+    for (int l = 0; l < h->L; ++l) a.pcs[l] = (float)std::pow(h->view.delta[l], (double)h->d);
     const int L = h->L;
     a.L = L;
     a.R = R;

@@ -122,6 +122,25 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def mf_candidates(w):
+    """Candidate pairs of the matrix-free mat-vec: for every point, the points of the 3^d cells (cell
+    size delta_l, the level's bounding box as origin) around its own cell in its level."""
+    import numpy as np
+    total = 0
+    for l, X in enumerate(w.levels):
+        delta = w.nu * w.h[l]
+        lo = X.min(axis=0)
+        c = np.floor((X - lo) / delta).astype(np.int64)
+        G = c.max(axis=0) + 1
+        c = np.minimum(c, G - 1)
+        key = c[:, 0] * G[1] + c[:, 1]
+        cnt = np.bincount(key, minlength=int(G[0] * G[1])).reshape(G[0], G[1])
+        pad = np.pad(cnt, 1)
+        box = sum(pad[1 + dx:1 + dx + G[0], 1 + dy:1 + dy + G[1]] for dx in (-1, 0, 1) for dy in (-1, 0, 1))
+        total += int(box[c[:, 0], c[:, 1]].sum())
+    return total
+
+
 def recorded_traffic(profile="k_fit_learned_halton8.md"):
     """DRAM traffic per launch of the solve kernel from the committed ncu summary, or None when
     the kernel's source has changed since the counters were taken (sha256 lines of the summary)."""
@@ -335,6 +354,8 @@ def run_ours(args):
             out["rel_diff_vs_fp64_coefficients"] = float(torch.linalg.norm(a1 - a0) / torch.linalg.norm(a0))
 
         # stand-alone mat-vecs (sorted order): GB/s of the CSR kernels, matrix-free timing
+        peaks_alu = {"fp32": ms.ms_peak_probe(ms.MS_PROBE_FP32), "fp64": ms.ms_peak_probe(ms.MS_PROBE_FP64),
+                     "xu": ms.ms_peak_probe(ms.MS_PROBE_XU)}
         H = ms.Hierarchy(2, n, pts, w.h, precision=ms.MS_PREC_MIXED, wendland_d=2, wendland_k=1, nu=w.nu)
         N = w.N
         x = torch.randn(N, dtype=torch.float64, device="cuda")
@@ -358,8 +379,18 @@ def run_ours(args):
                 mv[name] = {"ms": t_ms, "GBps": b / (t_ms * 1e-3) / 1e9, "frac_hbm": b / (t_ms * 1e-3) / 1e9 / hbm,
                             "algorithmic_bytes": b}
             else:
-                mv[name] = {"ms": t_ms, "stored_entries_per_s": nnz / (t_ms * 1e-3)}
+                # matrix-free: bound by FP32 and XU issue; every candidate pair (points of the
+                # 3^d cells around each point's cell) costs 13 FP32-pipe instructions and one
+                # reciprocal square root (ms_matfree.cuh, d = 2, phi_{d,1})
+                cand = mf_candidates(w)
+                f32 = 13.0 * cand / (t_ms * 1e-3)
+                xu = cand / (t_ms * 1e-3)
+                mv[name] = {"ms": t_ms, "stored_entries_per_s": nnz / (t_ms * 1e-3), "candidate_pairs": cand,
+                            "fp32_instr_per_s": f32, "frac_fp32": f32 / peaks_alu["fp32"],
+                            "xu_per_s": xu, "frac_xu": xu / peaks_alu["xu"]}
         out["matvec"] = mv
+        out["alu_peaks_measured"] = {"fp32_instr_per_s": peaks_alu["fp32"], "fp64_instr_per_s": peaks_alu["fp64"],
+                                     "xu_per_s": peaks_alu["xu"], "probe": "ms_peak_probe (own FMA / rsqrt chains)"}
         H.close()
 
         # nu = 8, phi_{2,2} (ill-conditioned levels): learned-PCG MIXED vs plain FP64, one step each

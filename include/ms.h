@@ -419,6 +419,15 @@ enum {
 };
 ms_status ms_precond_inspect(ms_hierarchy* h, int what, const int* levels, int n_levels, void* out, int64_t n_out);
 
+/* Instruction-rate probes of the current device, the denominators of the ALU-bound
+ * rooflines: dependent chains of FP32 fused multiply-adds, of FP64 fused multiply-adds or of
+ * FP32 reciprocal square roots (the special-function unit), eight independent chains per
+ * thread on four 256-thread blocks per SM; the best of three timed launches.
+ *   per_s  host, written: warp-lane instructions per second (an FMA is one instruction)
+ * Errors: MS_ERR_ARG (kind, NULL), MS_ERR_CUDA.  Synchronous; runs about 10 ms. */
+enum { MS_PROBE_FP32 = 0, MS_PROBE_FP64 = 1, MS_PROBE_XU = 2 };
+ms_status ms_peak_probe(int kind, double* per_s);
+
 /* Number of CUDA kernels this library has launched in the calling process so far
  * (all threads and handles; the count is taken at launch time, not completion). */
 uint64_t ms_launch_count(void);

@@ -33,7 +33,7 @@ EXPORTED = ["ms_default_opts", "ms_build_hierarchy", "ms_build_hierarchy_dev", "
             "ms_fit_static_dev", "ms_fit_batch", "ms_fit_batch_dev", "ms_batch_plan_create", "ms_batch_plan_launch",
             "ms_batch_plan_stats", "ms_batch_plan_destroy", "ms_default_train_opts", "ms_train_precond", "ms_precond_params",
             "ms_precond_inspect", "ms_evaluate", "ms_evaluate_dev", "ms_apply_dev", "ms_get_permutation", "ms_hierarchy_info",
-            "ms_launch_count", "ms_last_error", "ms_destroy"]
+            "ms_peak_probe", "ms_launch_count", "ms_last_error", "ms_destroy"]
 
 
 class ms_opts(C.Structure):
@@ -138,6 +138,7 @@ def load(path: str | None = None):
     lib.ms_apply_dev.argtypes = [_P, C.c_int, _P, _P, C.c_int, _P]
     lib.ms_get_permutation.argtypes = [_P, _I64]
     lib.ms_hierarchy_info.argtypes = [_P, C.POINTER(ms_info)]
+    lib.ms_peak_probe.argtypes = [C.c_int, C.POINTER(C.c_double)]
     lib.ms_last_error.argtypes = []
     lib.ms_last_error.restype = C.c_char_p
     lib.ms_destroy.argtypes = [_P]
@@ -397,6 +398,16 @@ def ms_precond_inspect(handle, what, N, d, levels=(0,), augment=4):
         out = np.empty(precond_n_values(d) - 2 * PC_OUT + 1, dtype=np.float32)
     _check(load().ms_precond_inspect(C.c_void_p(handle), what, lv, n, out.ctypes.data_as(C.c_void_p), out.size))
     return out
+
+
+MS_PROBE_FP32, MS_PROBE_FP64, MS_PROBE_XU = range(3)
+
+
+def ms_peak_probe(kind) -> float:
+    """Warp-lane instructions per second of the FP32-FMA, FP64-FMA or XU (rsqrt) probe."""
+    v = C.c_double()
+    _check(load().ms_peak_probe(int(kind), C.byref(v)))
+    return v.value
 
 
 def ms_launch_count() -> int:

@@ -89,3 +89,12 @@ def test_explicit_threads_per_row_overrides_autotune():
     assert H.info()["tpr_A"] == [4] * len(SIZES)
     assert max(st["rel_residual"]) <= 1e-12
     H.close()
+
+
+def test_peak_probes_are_plausible():
+    """The instruction-rate probes behind the ALU rooflines: FP32 FMA issue far above FP64
+    (GB300: 64x) and above the special-function unit's rsqrt rate."""
+    f32 = ms.ms_peak_probe(ms.MS_PROBE_FP32)
+    f64 = ms.ms_peak_probe(ms.MS_PROBE_FP64)
+    xu = ms.ms_peak_probe(ms.MS_PROBE_XU)
+    assert f32 > 4 * xu > 0 and f32 > 16 * f64 > 0, (f32, f64, xu)

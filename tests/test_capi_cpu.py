@@ -94,3 +94,10 @@ def test_fit_batch_rejects_bad_arguments_on_host(lib):
     fp = (C.c_void_p * 1)(None)
     assert L.ms_fit_batch_dev(hs, 1, fp, 1e-10, fp, st, None) == ms.MS_ERR_ARG
     assert "hierarchy 0" in ms.ms_last_error()
+
+
+def test_peak_probe_rejects_unknown_kinds(lib):
+    for kind in (-1, 3):
+        with pytest.raises(ms.MsError) as e:
+            ms.ms_peak_probe(kind)
+        assert e.value.status == ms.MS_ERR_ARG

@@ -114,22 +114,39 @@ __device__ __forceinline__ float mf_gather(const MFView& v, const MFLevel& g, co
                 const float ox = (float)dx * g.cod - wi[0];
                 const int64_t gid = g.cell_off + morton(D, cx, cy, cz);
                 const int32_t s = v.cell_start[gid], e = v.cell_start[gid + 1];
-                for (int32_t j = s + sub; j < e; j += TPP) {
-                    const float ex = Wx[j] + ox;
+                // phi(r) x_j for candidate j: r = r2 / sqrt(r2) through the hardware reciprocal
+                // square root (FP32 entries need no correctly rounded sqrt); r2 = 0 gives r = 0
+                auto term = [&](float wx, float wy, float wz, float xj) {
+                    const float ex = wx + ox;
                     float r2 = ex * ex;
                     if (D >= 2) {
-                        const float ey = Wy[j] + oy;
+                        const float ey = wy + oy;
                         r2 = fmaf(ey, ey, r2);
                     }
                     if (D >= 3) {
-                        const float ez = Wz[j] + oz;
+                        const float ez = wz + oz;
                         r2 = fmaf(ez, ez, r2);
                     }
-                    // r = r2 / sqrt(r2) through the hardware reciprocal square root (FP32 entries
-                    // need no correctly rounded sqrt); r2 = 0 gives r = 0
                     const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
-                    acc = fmaf(mf_phi<E>(r, v.c, v.E), x[j], acc);
+                    acc = fmaf(mf_phi<E>(r, v.c, v.E), xj, acc);
+                };
+                // four candidates' loads issued before their arithmetic (the loop is latency-bound
+                // otherwise); the terms are still added in candidate order
+                int32_t j = s + sub;
+                for (; j + 3 * TPP < e; j += 4 * TPP) {
+                    float wx[4], wy[4] = {0.f, 0.f, 0.f, 0.f}, wz[4] = {0.f, 0.f, 0.f, 0.f}, xj[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int32_t jj = j + u * TPP;
+                        wx[u] = Wx[jj];
+                        if (D >= 2) wy[u] = Wy[jj];
+                        if (D >= 3) wz[u] = Wz[jj];
+                        xj[u] = x[jj];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) term(wx[u], wy[u], wz[u], xj[u]);
                 }
+                for (; j < e; j += TPP) term(Wx[j], D >= 2 ? Wy[j] : 0.f, D >= 3 ? Wz[j] : 0.f, x[j]);
             }
         }
     }

@@ -212,3 +212,26 @@ def test_batch_plan_guards():
     assert rel(aF[:, 0], a1) <= 1e-10
     for H in Hs:
         H.close()
+
+
+def test_batch_with_learned_preconditioner_matches_single_fits():
+    """Hierarchies with the learned preconditioner (weights imported) fitted in one batched launch:
+    the same coefficients as their single fits (to the CG tolerance), and real residuals."""
+    ws = [hierarchy(s, 800 + i) for i, s in enumerate([[40, 160, 640, 2560], [100, 400, 1600], [64, 256, 1024, 4096]])]
+    Ht = ms.Hierarchy.from_workload(ws[2], precision=ms.MS_PREC_MIXED, precond=ms.MS_PRECOND_LEARNED)
+    Ht.train_precond([0, 1], epochs=20)
+    params = Ht.precond_params()
+    Hs = [ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED, precond=ms.MS_PRECOND_LEARNED) for w in ws]
+    for H in Hs:
+        H.precond_params(params)
+    A, st = ms.ms_fit_batch([H.handle for H in Hs], [w.f for w in ws], rel_tol=1e-12)
+    for i, (w, H) in enumerate(zip(ws, Hs)):
+        res = st[i]["rel_residual"]
+        assert 0 < max(res) <= 1e-12, (i, res)
+        assert st[i]["precond_fallbacks"] == 0
+        a1, s1 = H.fit(w.f, rel_tol=1e-12)
+        assert rel(A[i], a1) <= 1e-8, (i, rel(A[i], a1))
+        ref, _ = om.fit_sequential(w.levels, w.f, w.h, w.nu, w.wendland_d, w.wendland_k)
+        assert rel(A[i], np.concatenate(ref)) <= 1e-8, i
+    for H in Hs + [Ht]:
+        H.close()

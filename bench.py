@@ -263,6 +263,8 @@ def run_ours(args):
     train = Ht.train_precond([0, 1, 2, 3], epochs=args.train_epochs)
     params = Ht.precond_params()
     Ht.close()
+    params3 = None  # the 3-D network (the --cfg3 block trains it)
+    Q3 = torch.from_numpy(inputs.query_grid(32, 3)).cuda()  # 32^3 queries for 3-D workloads
 
     def step(prec, precond=ms.MS_PRECOND_NONE, inter_tol=0.0, wl=None, pts_=None, f_=None, **extra):
         wl = wl or w
@@ -274,10 +276,10 @@ def run_ours(args):
         e0.record(stream)
         hnd = ms.ms_build_hierarchy(wl.d, wl.n_per_level, pts_, wl.h, opts)
         if precond == ms.MS_PRECOND_LEARNED:
-            ms.ms_precond_params(hnd, 2, params)
+            ms.ms_precond_params(hnd, wl.d, params if wl.d == 2 else params3)
         alpha, st = ms.ms_fit(hnd, f_, REL_TOL)
         e1.record(stream)
-        s = ms.ms_evaluate(hnd, alpha, Q)
+        s = ms.ms_evaluate(hnd, alpha, Q if wl.d == 2 else Q3)  # queries of the workload's dimension
         e2.record(stream)
         torch.cuda.synchronize()
         info = ms.ms_hierarchy_info(hnd)
@@ -567,12 +569,19 @@ def run_ours(args):
             p3, f3 = torch.from_numpy(w3.points).cuda(), torch.from_numpy(w3.f).cuda()
             o3 = {"workload": "d=3 uniform random, N_j=125*8^(j-1), 6 levels (4,681,125 points), "
                               "delta_j=3h_j, phi_{3,1}, 30 Gaussians"}
+            # the network for 3-D patches (48 inputs), trained on levels 1-4 of this hierarchy
+            Ht3 = ms.Hierarchy(3, w3.n_per_level, p3, w3.h, precision=ms.MS_PREC_MIXED, precond=ms.MS_PRECOND_LEARNED,
+                               wendland_d=3, wendland_k=1, nu=w3.nu)
+            o3["train"] = Ht3.train_precond([0, 1, 2, 3], epochs=max(10, args.train_epochs // 4))
+            params3 = Ht3.precond_params()
+            Ht3.close()
             for tag, kw in (("fp64_csr", {"prec": ms.MS_PREC_FP64}),
                             ("mixed_matrix_free", {"prec": ms.MS_PREC_MIXED, "op": ms.MS_OP_MATRIX_FREE}),
-                            ("mixed_csr", {"prec": ms.MS_PREC_MIXED})):
+                            ("mixed_csr", {"prec": ms.MS_PREC_MIXED}),
+                            ("learned_pcg_csr", {"prec": ms.MS_PREC_MIXED, "precond": ms.MS_PRECOND_LEARNED})):
                 extra = {"op": kw["op"]} if "op" in kw else {}
                 try:
-                    r3 = step(kw["prec"], wl=w3, pts_=p3, f_=f3, **extra)
+                    r3 = step(kw["prec"], kw.get("precond", ms.MS_PRECOND_NONE), wl=w3, pts_=p3, f_=f3, **extra)
                     o3[tag] = {"step_ms": r3["total"], "fit_ms": r3["stats"]["fit_ms"],
                                "build_ms": r3["info"]["build_ms"], "cg_iterations": r3["stats"]["cg_iterations"],
                                "fp64_fallbacks": r3["stats"]["fp64_fallbacks"],

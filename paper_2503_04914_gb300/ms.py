@@ -302,6 +302,9 @@ class BatchPlan:
 
 def ms_evaluate(handle, alpha, query, out=None, stream=None):
     lib = load()
+    d = ms_hierarchy_info(handle)["d"]
+    if query.ndim != 2 or query.shape[1] != d:
+        raise MsError(MS_ERR_ARG, f"query must be [nq][{d}] for this hierarchy (got shape {tuple(query.shape)})")
     nrhs = 1 if alpha.ndim == 1 else alpha.shape[1]
     nq = query.shape[0]
     if _is_dev(alpha):

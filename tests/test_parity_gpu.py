@@ -385,3 +385,14 @@ def test_multi_rhs_with_preconditioner_or_matrix_free(over):
     ref = np.concatenate(oracle_fit(w, F[:, [0, 4]]))
     assert rel(A[:, 4], ref[:, 1]) <= 1e-8
     H.close()
+
+
+def test_evaluate_rejects_queries_of_another_dimension():
+    w = inputs.grid_hierarchy_small()
+    H = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_FP64)
+    alpha, _ = H.fit(w.f, rel_tol=1e-10)
+    with pytest.raises(ms.MsError) as e:
+        H.evaluate(alpha, inputs.query_grid(4, 3))
+    assert e.value.status == ms.MS_ERR_ARG
+    assert H.evaluate(alpha, inputs.query_grid(4, 2)).shape == (16,)
+    H.close()

@@ -428,6 +428,20 @@ ms_status ms_precond_inspect(ms_hierarchy* h, int what, const int* levels, int n
 enum { MS_PROBE_FP32 = 0, MS_PROBE_FP64 = 1, MS_PROBE_XU = 2 };
 ms_status ms_peak_probe(int kind, double* per_s);
 
+/* Self-test of the solve kernel's bounded waits.  One CTA enters the grid barrier of the
+ * persistent solve kernel (the same device code) as one of two CTAs of its partition; the
+ * other never arrives, so the wait has to give up: after timeout_s it records MS_ERR_TIMEOUT
+ * in the device status word and the kernel returns.  With peer_timed_out != 0 the status
+ * word starts at MS_ERR_TIMEOUT, as if another CTA had timed out already, and the wait must
+ * leave within a few hundred polls instead.  Nothing faults or hangs; the context stays
+ * usable.
+ *   timeout_s       the wait's limit in seconds, in (0, 10]
+ *   device_status   host, written: the status word after the kernel (MS_ERR_TIMEOUT expected)
+ *   waited_s        host, written (may be NULL): the kernel's duration (CUDA events)
+ * Errors: MS_ERR_ARG (timeout_s out of range, device_status NULL), MS_ERR_CUDA.
+ * Synchronous. */
+ms_status ms_wait_selftest(double timeout_s, int peer_timed_out, int* device_status, double* waited_s);
+
 /* Number of CUDA kernels this library has launched in the calling process so far
  * (all threads and handles; the count is taken at launch time, not completion). */
 uint64_t ms_launch_count(void);

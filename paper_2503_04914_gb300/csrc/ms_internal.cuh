@@ -205,50 +205,6 @@ __device__ __forceinline__ unsigned long long ms_globaltimer() {
     return t;
 }
 
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  One
-// arrival counter plus a generation word; the last CTA to arrive resets the
-// counter and publishes the next generation with release semantics, the others
-// spin on the generation with acquire loads.  Every wait is bounded: past
-// timeout_ns it records MS_ERR_TIMEOUT in *status and returns false; it also
-// returns false as soon as another CTA has recorded a time-out.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks,
-                                             int* status, unsigned long long timeout_ns) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(*gen);
-        cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(*count);
-        cuda::atomic_ref<int, cuda::thread_scope_device> st(*status);
-        const unsigned mine = g.load(cuda::memory_order_relaxed);
-        const unsigned arrived = c.fetch_add(1u, cuda::memory_order_acq_rel);
-        int ok = 1;
-        if (arrived == nblocks - 1) {
-            c.store(0u, cuda::memory_order_relaxed);
-            g.store(mine + 1u, cuda::memory_order_release);
-        } else {
-            const unsigned long long t0 = ms_globaltimer();
-            unsigned spins = 0;
-            while (g.load(cuda::memory_order_acquire) == mine) {
-                if ((++spins & 255u) == 0u) {
-                    if (st.load(cuda::memory_order_relaxed) == MS_ERR_TIMEOUT) { ok = 0; break; }
-                    if (ms_globaltimer() - t0 > timeout_ns) {
-                        int expect = 0;
-                        st.compare_exchange_strong(expect, (int)MS_ERR_TIMEOUT, cuda::memory_order_relaxed);
-                        if (expect != 0) st.store((int)MS_ERR_TIMEOUT, cuda::memory_order_relaxed);
-                        ok = 0;
-                        break;
-                    }
-                }
-                __nanosleep(32);
-            }
-        }
-        if (ok && st.load(cuda::memory_order_relaxed) == MS_ERR_TIMEOUT) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -641,3 +641,66 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
     }
     return MS_OK;
 }
+
+// ---------------------------------------------------------------- bounded-wait self-test
+
+namespace {
+
+// One CTA in a partition of `pretend` CTAs enters the solve kernel's grid barrier; the
+// others never arrive.
+__global__ void __launch_bounds__(kBS) k_wait_selftest(const __grid_constant__ SolveArgs a, unsigned pretend) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Shared& sh = *reinterpret_cast<Shared*>(smem_raw);
+    if (threadIdx.x == 0) {
+        sh.cta = 0;
+        sh.nb = (int)pretend;
+        sh.tprev = ms_globaltimer();
+        for (int k = 0; k < kProf; ++k) sh.pt[k] = 0ull;
+    }
+    __syncthreads();
+    gsync(a, sh);
+}
+
+}  // namespace
+
+extern "C" ms_status ms_wait_selftest(double timeout_s, int peer_timed_out, int* device_status, double* waited_s) {
+    if (!device_status || !(timeout_s > 0.0 && timeout_s <= 10.0)) {
+        ms_set_error(MS_ERR_ARG, "timeout_s must be in (0, 10] and device_status non-NULL");
+        return MS_ERR_ARG;
+    }
+    struct Buf {
+        void* p = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ~Buf() {
+            if (p) cudaFree(p);
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+        }
+    } b;
+    const size_t bar_bytes = sizeof(unsigned) * kBarWords;
+    MS_CUDA(cudaMalloc(&b.p, bar_bytes + sizeof(int)));
+    MS_CUDA(cudaMemset(b.p, 0, bar_bytes + sizeof(int)));
+    int* status = reinterpret_cast<int*>(static_cast<char*>(b.p) + bar_bytes);
+    if (peer_timed_out) {
+        const int t = MS_ERR_TIMEOUT;
+        MS_CUDA(cudaMemcpy(status, &t, sizeof(int), cudaMemcpyHostToDevice));
+    }
+    SolveArgs a{};
+    a.bar = static_cast<unsigned*>(b.p);
+    a.status = status;
+    a.timeout_ns = (unsigned long long)(timeout_s * 1e9);
+    MS_CUDA(cudaFuncSetAttribute(k_wait_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared)));
+    MS_CUDA(cudaEventCreate(&b.e0));
+    MS_CUDA(cudaEventCreate(&b.e1));
+    MS_CUDA(cudaEventRecord(b.e0, 0));
+    k_wait_selftest<<<1, kBS, sizeof(Shared), 0>>>(a, 2u);
+    ms_count_launch();
+    MS_CUDA(cudaGetLastError());
+    MS_CUDA(cudaEventRecord(b.e1, 0));
+    MS_CUDA(cudaEventSynchronize(b.e1));
+    float ms = 0.f;
+    MS_CUDA(cudaEventElapsedTime(&ms, b.e0, b.e1));
+    MS_CUDA(cudaMemcpy(device_status, status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (waited_s) *waited_s = 1e-3 * (double)ms;
+    return MS_OK;
+}

@@ -33,7 +33,7 @@ EXPORTED = ["ms_default_opts", "ms_build_hierarchy", "ms_build_hierarchy_dev", "
             "ms_fit_static_dev", "ms_fit_batch", "ms_fit_batch_dev", "ms_batch_plan_create", "ms_batch_plan_launch",
             "ms_batch_plan_stats", "ms_batch_plan_destroy", "ms_default_train_opts", "ms_train_precond", "ms_precond_params",
             "ms_precond_inspect", "ms_evaluate", "ms_evaluate_dev", "ms_apply_dev", "ms_get_permutation", "ms_hierarchy_info",
-            "ms_peak_probe", "ms_launch_count", "ms_last_error", "ms_destroy"]
+            "ms_peak_probe", "ms_wait_selftest", "ms_launch_count", "ms_last_error", "ms_destroy"]
 
 
 class ms_opts(C.Structure):
@@ -139,6 +139,7 @@ def load(path: str | None = None):
     lib.ms_get_permutation.argtypes = [_P, _I64]
     lib.ms_hierarchy_info.argtypes = [_P, C.POINTER(ms_info)]
     lib.ms_peak_probe.argtypes = [C.c_int, C.POINTER(C.c_double)]
+    lib.ms_wait_selftest.argtypes = [C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     lib.ms_last_error.argtypes = []
     lib.ms_last_error.restype = C.c_char_p
     lib.ms_destroy.argtypes = [_P]
@@ -411,6 +412,15 @@ def ms_peak_probe(kind) -> float:
     v = C.c_double()
     _check(load().ms_peak_probe(int(kind), C.byref(v)))
     return v.value
+
+
+def ms_wait_selftest(timeout_s, peer_timed_out=False):
+    """Runs the solve kernel's grid barrier with a partner CTA that never arrives; returns
+    (device status word, seconds the kernel ran)."""
+    st = C.c_int(-1)
+    w = C.c_double()
+    _check(load().ms_wait_selftest(float(timeout_s), int(bool(peer_timed_out)), C.byref(st), C.byref(w)))
+    return st.value, w.value
 
 
 def ms_launch_count() -> int:

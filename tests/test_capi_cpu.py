@@ -101,3 +101,12 @@ def test_peak_probe_rejects_unknown_kinds(lib):
         with pytest.raises(ms.MsError) as e:
             ms.ms_peak_probe(kind)
         assert e.value.status == ms.MS_ERR_ARG
+
+
+def test_wait_selftest_rejects_bad_arguments_on_host(lib):
+    for t in (0.0, -1.0, 10.5, float("nan")):
+        with pytest.raises(ms.MsError) as e:
+            ms.ms_wait_selftest(t)
+        assert e.value.status == ms.MS_ERR_ARG
+    rc = ms.load().ms_wait_selftest(0.1, 0, None, None)
+    assert rc == ms.MS_ERR_ARG

@@ -29,10 +29,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "fit time at rel-err 1e-8: learned-PCG FP32 vs plain FP64 (ms); mat-vec GB/s"
-WORKLOAD = ("halton8_d2_nu4_w21: d=2, 8 levels scrambled Halton N_j=64*4^(j-1) (1,398,080 points), "
-            "delta_j=4*N_j^-1/2, Wendland phi_{2,1}, f=20 Gaussians+0.1 sin(8pi x)sin(8pi y)")
 REL_TOL = 1e-10
-N_FULL = 1398080
+
+
+def halton_points(levels):
+    """Points of the Halton hierarchy with N_j = 64 * 4^(j-1), j = 1..levels."""
+    return sum(64 * 4 ** j for j in range(levels))
+
+
+def workload_label(levels):
+    return (f"halton{levels}_d2_nu4_w21: d=2, {levels} levels scrambled Halton N_j=64*4^(j-1) "
+            f"({halton_points(levels):,} points), delta_j=4*N_j^-1/2, Wendland phi_{{2,1}}, "
+            "f=20 Gaussians+0.1 sin(8pi x)sin(8pi y)")
+
 
 
 def parse():
@@ -212,14 +221,15 @@ def run_reference(args):
     reps = args.warmup + args.steps
     out = cpu_baseline(args.ref_levels, 1024, reps=reps)
     ts = out["times"][args.warmup:]
-    scale = N_FULL / out["N"]
+    n_work = halton_points(args.levels)
+    scale = n_work / out["N"]
     ms_step = 1000.0 * statistics.mean(ts) * scale
     sample = (f"oracle fit_sequential + evaluate on the first {args.ref_levels} levels of the workload "
-              f"({out['N']} points, 1024 queries), single-threaded, scaled by points ({N_FULL}/{out['N']})")
+              f"({out['N']} points, 1024 queries), single-threaded, scaled by points ({n_work}/{out['N']})")
     line = {"impl": "reference", "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "rel_tol": REL_TOL},
+            "config": {"workload": workload_label(args.levels), "rel_tol": REL_TOL},
             "cpu_baseline": {"value": ms_step, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": ms_step, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -611,18 +621,18 @@ def run_ours(args):
 
         if not args.no_cpu:
             cb = cpu_baseline(args.cpu_levels, 4096)
-            scale = N_FULL / cb["N"]
+            scale = w.N / cb["N"]
             out["cpu_baseline"] = {"value": 1000.0 * cb["times"][0] * scale, "unit": "ms", "cores": 1,
                                    "kind": "oracle",
                                    "sample": (f"oracle fit_sequential + evaluate on the first {args.cpu_levels} "
                                               f"levels ({cb['N']} points, 4096 queries) took "
                                               f"{cb['times'][0]:.2f} s single-threaded; scaled by points "
-                                              f"({N_FULL}/{cb['N']})")}
+                                              f"({w.N}/{cb['N']})")}
 
         line = {"metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD,
+                "config": {"workload": workload_label(args.levels),
                            "path": "learned-PCG MIXED: FP32 CSR mat-vecs, FP64 dots/refinement, learned FSAI",
                            "rel_tol": REL_TOL, "queries": args.query_side ** 2,
                            "step": "build_hierarchy + precond rows + fit + evaluate, inputs resident in HBM",

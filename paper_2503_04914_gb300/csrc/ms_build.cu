@@ -292,7 +292,27 @@ constexpr int kCsrBS = 256;  // 8 rows per block
 struct PairLayout {
     int64_t base[MS_MAXL];
     int nc;
+    // Frames: row s of level k has its frames in levels 0..k at fbase[k] + (s - off[k]) (k + 1) + j
+    // (fbase[L] = all frames).
+    int64_t fbase[MS_MAXL + 1];
+    double d2[MS_MAXL];  // delta_j^2, rounded as the FP64 product delta_j * delta_j
 };
+
+// Every row's frames in the levels up to its own, one thread per (row, level).  Set up in
+// the count and again in the fill by lanes 0..k of a row's warp, the frames took about 34
+// FP64 instructions per row with a few lanes active each, and GB300's FP64 pipe holds a warp
+// instruction about 19 cycles whatever its active lanes: most of the count kernel's time.
+// Here every lane is busy and each frame is set up once.
+__global__ void k_frames(const __grid_constant__ HierView v, const __grid_constant__ PairLayout pl, Frame* F) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= pl.fbase[v.L]) return;
+    int k = 0;
+    while (k + 1 < v.L && i >= pl.fbase[k + 1]) ++k;
+    const int64_t r = i - pl.fbase[k];
+    const int64_t row = r / (k + 1);
+    const int j = (int)(r - row * (k + 1));
+    F[i] = frame_of(v, j, point_at(v, v.off[k] + row));
+}
 
 // The points [ps, pe) and the cell offsets (units of delta_j) of pair q of level j, seen
 // from y's frame f in level j's grid; false when the cell lies outside the grid.
@@ -318,8 +338,9 @@ __device__ __forceinline__ bool pair_cell(const HierView& v, int j, int q, const
 // at a time, each lane walking its cell's points.  Also stores each pair's count, from
 // which the fill places its columns.
 __global__ void __launch_bounds__(kCsrBS, 4) k_csr_count(const __grid_constant__ HierView v, const float* __restrict__ W,
-                                                       const __grid_constant__ PairLayout pl, int32_t* cntA,
-                                                       int32_t* cntB, int32_t* pcnt) {
+                                                       const __grid_constant__ PairLayout pl,
+                                                       const Frame* __restrict__ F, int32_t* cntA, int32_t* cntB,
+                                                       int32_t* pcnt) {
     const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (s >= v.N) return;  // warp-uniform
@@ -327,7 +348,7 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_count(const __grid_constant__
     const Pt y = point_at(v, s);
     // lane j <= k holds y's frame in level j's grid
     Frame mine{};
-    if (lane <= k) mine = frame_of(v, lane, y);
+    if (lane <= k) mine = F[pl.fbase[k] + (s - v.off[k]) * (k + 1) + lane];
     const int nc = pl.nc;
     const int pairs = (k + 1) * nc;
     int32_t* pc = pcnt + pl.base[k] + (s - v.off[k]) * pairs;
@@ -341,7 +362,7 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_count(const __grid_constant__
         float o0 = 0.f, o1 = 0.f, o2 = 0.f;
         int32_t n = 0;
         if (pair_cell(v, j, t - j * nc, f, ps, pe, o0, o1, o2)) {
-            const double d2 = v.delta[j] * v.delta[j];
+            const double d2 = pl.d2[j];
             for (int32_t p = ps; p < pe; ++p) n += within(v, W, p, o0, o1, o2, y, d2) ? 1 : 0;
         }
         pc[t] = n;
@@ -371,6 +392,7 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_fill(const __grid_constant__ 
                                                       const float* __restrict__ Wlo, const int32_t* __restrict__ cellid,
                                                       const __grid_constant__ FFLevels ffl,
                                                       const __grid_constant__ PairLayout pl,
+                                                      const Frame* __restrict__ F,
                                                       const int32_t* __restrict__ pcnt, const int64_t* rpA,
                                                       int32_t* colA, double* valA, float* valA32, const int64_t* rpB,
                                                       int32_t* colB, double* valB, float* valB32, int32_t* Bseg) {
@@ -380,7 +402,7 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_fill(const __grid_constant__ 
     const int k = level_of_row(v.off, v.L, s);
     const Pt y = point_at(v, s);
     Frame mine{};
-    if (lane <= k) mine = frame_of(v, lane, y);
+    if (lane <= k) mine = F[pl.fbase[k] + (s - v.off[k]) * (k + 1) + lane];
     // Columns: lane per (level, cell) pair as in the count; a warp scan of the stored pair
     // counts (A pairs and B pairs separately, in pair order) gives every lane the position
     // of its cell's first entry, so the columns come out in the order of the pairs (B: level
@@ -414,7 +436,7 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_fill(const __grid_constant__ 
             int32_t ps = 0, pe = 0;
             float o0 = 0.f, o1 = 0.f, o2 = 0.f;
             pair_cell(v, j, q, f, ps, pe, o0, o1, o2);
-            const double d2 = v.delta[j] * v.delta[j];
+            const double d2 = pl.d2[j];
             int32_t* col = isA ? colA : colB;
             int64_t pos = isA ? pa + ia - n : pb + ib - n;
             for (int32_t p = ps; p < pe; ++p)
@@ -505,11 +527,7 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
 
     std::vector<void*> temps;
     auto talloc = [&](void** p, size_t bytes) -> ms_status {
-        cudaError_t e = cudaMallocAsync(p, std::max<size_t>(bytes, 16), st);
-        if (e != cudaSuccess) {
-            ms_set_error(MS_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
-            return MS_ERR_OOM;
-        }
+        MS_TRY(ms_tmp_alloc(p, bytes, st));
         temps.push_back(*p);
         return MS_OK;
     };
@@ -623,16 +641,23 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
     {
         const int side = 2 * v.R + 1;
         pl.nc = d == 1 ? side : (d == 2 ? side * side : side * side * side);
-        int64_t tot = 0;
+        int64_t tot = 0, ftot = 0;
         for (int l = 0; l < L; ++l) {
             pl.base[l] = tot;
+            pl.fbase[l] = ftot;
             tot += (v.off[l + 1] - v.off[l]) * (int64_t)(l + 1) * pl.nc;
+            ftot += (v.off[l + 1] - v.off[l]) * (int64_t)(l + 1);
+            pl.d2[l] = v.delta[l] * v.delta[l];
         }
+        pl.fbase[L] = ftot;
         int32_t* pc = nullptr;
         MS_TRY(talloc((void**)&pc, sizeof(int32_t) * tot));
         pcnt = pc;
     }
-    k_csr_count<<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, pl, cntA, cntB, pcnt); ms_count_launch();
+    Frame* frames = nullptr;
+    MS_TRY(talloc((void**)&frames, sizeof(Frame) * pl.fbase[L]));
+    k_frames<<<nblk(pl.fbase[L], 256), 256, 0, st>>>(v, pl, frames); ms_count_launch();
+    k_csr_count<<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, pl, frames, cntA, cntB, pcnt); ms_count_launch();
     exclusive_scan<int32_t, int64_t>(cntA, N, h->A.rp, (int64_t*)tile, st);
     exclusive_scan<int32_t, int64_t>(cntB, N, h->B.rp, (int64_t*)tile, st);
     MS_CUDA(cudaGetLastError());
@@ -665,7 +690,7 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
                               : v.w.e == 6 && v.w.k == 2 ? k_csr_fill<true, 6, 2>
                                                          : k_csr_fill<true, 0, 0>)
                            : k_csr_fill<false, 0, 0>;
-        fill<<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, Wlo, h->cellid, ffl, pl, pcnt, h->A.rp, h->A.col,
+        fill<<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, Wlo, h->cellid, ffl, pl, frames, pcnt, h->A.rp, h->A.col,
                                                       h->A.v64, h->A.v32, h->B.rp, h->B.col, h->B.v64, h->B.v32,
                                                       h->Bseg);
     }

@@ -196,6 +196,18 @@ ms_status ms_pool_alloc(void** p, size_t bytes) {
     return MS_OK;
 }
 
+ms_status ms_tmp_alloc(void** p, size_t bytes, cudaStream_t st) {
+    DevPool* dp = nullptr;
+    MS_TRY(device_pool(&dp));
+    const cudaError_t e = cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 16), dp->pool, st);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        ms_set_error(MS_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        return MS_ERR_OOM;
+    }
+    return MS_OK;
+}
+
 void ms_pool_free(void* p) {
     DevPool* dp = nullptr;
     if (!p || device_pool(&dp) != MS_OK) return;

@@ -316,6 +316,9 @@ ms_status ms_alloc(ms_hierarchy* h, void** p, size_t bytes);
 // library memory pool of the current device (ms_capi.cu)
 ms_status ms_pool_alloc(void** p, size_t bytes);
 void ms_pool_free(void* p);
+// Scratch memory ordered on stream st from the same pool (kept mapped when freed, so that
+// repeated builds do not map and unmap their temporaries); free with cudaFreeAsync on st.
+ms_status ms_tmp_alloc(void** p, size_t bytes, cudaStream_t st);
 // free *p (if it is one of the handle's allocations) and allocate `bytes` in its place
 ms_status ms_realloc(ms_hierarchy* h, void** p, size_t bytes);
 ms_status ms_build_impl(ms_hierarchy* h, const double* points_dev, cudaStream_t s);

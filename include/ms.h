@@ -450,8 +450,10 @@ uint64_t ms_launch_count(void);
 const char* ms_last_error(void);
 
 /* Free the handle and all device memory it owns; NULL is a no-op.  Waits for the device
- * to finish pending work first.  The library draws device memory from one memory pool per
- * device that keeps freed memory for reuse by later handles (released at process exit). */
+ * to finish pending work first.  The library draws device memory, the handles' and the
+ * builds' scratch alike, from one memory pool per device that keeps freed memory mapped for
+ * reuse by later handles and builds (released at process exit): the pool's footprint is the
+ * largest amount in use at any one time. */
 void ms_destroy(ms_hierarchy* h);
 
 #ifdef __cplusplus

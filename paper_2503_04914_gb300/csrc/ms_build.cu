@@ -163,7 +163,7 @@ __device__ __forceinline__ double dist2(const HierView& v, int64_t p, const Pt& 
     return r2;
 }
 
-// Frame of y in level j's grid, all axes (FP64 set-up: one lane per level calls it).
+// Frame of y in level j's grid, all axes (FP64 set-up; k_frames calls it once per (row, level)).
 __device__ __forceinline__ Frame frame_of(const HierView& v, int j, const Pt& y) {
     const LevelGrid& g = v.grid[j];
     Frame f{};

@@ -7,17 +7,22 @@ inputs already resident in HBM:
   ms_fit_dev              (preconditioner rows by the trained network, then Jacobi
                            sweeps on T' + per-level CG on D in one persistent kernel)
   ms_evaluate_dev         (approximant at a 256^2 query grid)
-Workload: d=2, 8 levels of scrambled Halton points, N_j = 64*4^(j-1) (1,398,080 points),
-h_j = N_j^-1/2, delta_j = 4 h_j, Wendland phi_{2,1}, f = 20 Gaussians + 0.1 sin(8 pi x) sin(8 pi y).
+Headline workload (the learned-preconditioner configuration): d=2, 8 levels of scrambled
+Halton points, N_j = 64*4^(j-1) (1,398,080 points), h_j = N_j^-1/2, delta_j = 8 h_j (large
+overlap, ill-conditioned A_l), Wendland phi_{2,2}, f = 20 Gaussians + 0.1 sin(8 pi x) sin(8 pi y).
 The timed path is learned-PCG MIXED (FP32 mat-vecs, FP64 dots and refinement, FSAI rows
-predicted by the network trained beforehand on levels 1-4, training timed separately);
-plain FP64 CG+Jacobi and the other variants are timed beside it.
+predicted by the network trained beforehand on levels 1-4, training timed separately); plain
+FP64 CG+Jacobi (the metric's other arm), MIXED without a preconditioner and MIXED with the
+exact FSAI rows (the network's teacher) are timed beside it on the same workload, followed by
+side blocks (delta_j = 4 h_j with phi_{2,1}, stand-alone mat-vecs, batching, the paper's grids,
+the 3-D configuration).
 `--impl reference` times the CPU FP64 oracle instead.  Prints one JSON line (rank 0).
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -30,6 +35,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fit time at rel-err 1e-8: learned-PCG FP32 vs plain FP64 (ms); mat-vec GB/s"
 REL_TOL = 1e-10
+HEAD_NU, HEAD_W = 8.0, (2, 2)  # the headline configuration: delta_j = 8 h_j, phi_{2,2}
+SIDE_NU, SIDE_W = 4.0, (2, 1)  # the side configuration: delta_j = 4 h_j, phi_{2,1}
 
 
 def halton_points(levels):
@@ -37,11 +44,10 @@ def halton_points(levels):
     return sum(64 * 4 ** j for j in range(levels))
 
 
-def workload_label(levels):
-    return (f"halton{levels}_d2_nu4_w21: d=2, {levels} levels scrambled Halton N_j=64*4^(j-1) "
-            f"({halton_points(levels):,} points), delta_j=4*N_j^-1/2, Wendland phi_{{2,1}}, "
-            "f=20 Gaussians+0.1 sin(8pi x)sin(8pi y)")
-
+def workload_label(levels, nu=HEAD_NU, wendland=HEAD_W):
+    return (f"halton{levels}_d2_nu{nu:g}_w{wendland[0]}{wendland[1]}: d=2, {levels} levels scrambled Halton "
+            f"N_j=64*4^(j-1) ({halton_points(levels):,} points), delta_j={nu:g}*N_j^-1/2, "
+            f"Wendland phi_{{{wendland[0]},{wendland[1]}}}, f=20 Gaussians+0.1 sin(8pi x)sin(8pi y)")
 
 
 def parse():
@@ -53,14 +59,14 @@ def parse():
     p.add_argument("--levels", type=int, default=8)
     p.add_argument("--query-side", type=int, default=256)
     p.add_argument("--train-epochs", type=int, default=100)
-    p.add_argument("--cpu-levels", type=int, default=6, help="levels of the oracle's bounded sample")
-    p.add_argument("--ref-levels", type=int, default=5, help="levels per step of the reference arm")
+    p.add_argument("--arm-steps", type=int, default=2, help="timed steps of each comparison arm (after 1 warm-up)")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--no-variants", action="store_true", help="skip the comparison paths")
-    p.add_argument("--no-nu8", action="store_true", help="skip the nu=8, phi_{2,2} block")
-    p.add_argument("--no-batch", action="store_true", help="skip the multi-RHS batching block")
+    p.add_argument("--no-variants", action="store_true", help="skip the comparison arms of the headline")
+    p.add_argument("--no-side", action="store_true", help="skip the delta = 4h, phi_{2,1} block")
+    p.add_argument("--no-matvec", action="store_true", help="skip the stand-alone mat-vec block")
+    p.add_argument("--no-batch", action="store_true", help="skip the batching blocks")
     p.add_argument("--no-paper", action="store_true", help="skip the paper-grid (Section 5) block")
-    p.add_argument("--cfg3", action="store_true", help="also run the 3-D configuration (about a minute)")
+    p.add_argument("--no-3d", action="store_true", help="skip the 3-D configuration (4.68M points)")
     return p.parse_args()
 
 
@@ -162,15 +168,16 @@ def mf_candidates(w):
     return total
 
 
-def recorded_traffic(profile="k_fit_learned_halton8.md"):
-    """DRAM traffic per launch of the solve kernel from the committed ncu summary, or None when
-    the kernel's source has changed since the counters were taken (sha256 lines of the summary)."""
+def recorded_traffic(profile="k_fit_traffic.txt"):
+    """DRAM traffic per algorithmic byte of the solve kernel, from the committed ncu summary
+    (a capture of a smaller case of the same workload), or None when a source file listed in
+    the summary has changed since the counters were taken (its sha256 lines)."""
     import hashlib
     try:
         text = open(os.path.join(ROOT, "profiles", profile)).read()
     except OSError:
         return None
-    traffic = None
+    ratio = None
     for line in text.splitlines():
         if line.startswith("kernel_source_sha256 "):
             name, digest = line[len("kernel_source_sha256 "):].split(":")
@@ -181,34 +188,71 @@ def recorded_traffic(profile="k_fit_learned_halton8.md"):
                 return None
             if cur != digest.strip():
                 return None
-        elif line.startswith("traffic_bytes_per_launch:"):
-            traffic = float(line.split(":")[1])
-    return traffic
+        elif line.startswith("traffic_per_algorithmic_byte:"):
+            ratio = float(line.split(":")[1])
+    return ratio
 
 
-def cpu_baseline(levels, query_n, reps=1):
-    """Time the CPU oracle (as it stands) on a bounded sample in a single-threaded subprocess."""
-    code = f"""
+# ------------------------------------------------------------------ CPU oracle timing
+
+
+_ORACLE_CODE = """
 import sys, time, json
-sys.path.insert(0, {ROOT!r})
+sys.path.insert(0, {root!r})
 from oracle import multiscale as om
 from paper_2503_04914_gb300 import inputs
-w = inputs.halton_hierarchy(L={levels})
-Q = inputs.query_grid(256, 2)[:{query_n}]
-ts = []
-for _ in range({reps}):
-    t = time.perf_counter()
-    a, _ = om.fit_sequential(w.levels, w.f, w.h, w.nu, 2, 1)
-    s = om.evaluate(w.levels, a, w.h, w.nu, 2, 1, Q)
-    ts.append(time.perf_counter() - t)
-print(json.dumps({{"N": w.N, "times": ts}}))
+out = []
+for L, reps in {plan!r}:
+    w = inputs.halton_hierarchy(L=L, nu={nu!r}, wendland={wend!r})
+    Q = inputs.query_grid(256, 2)[:4096]
+    for _ in range(reps):
+        t = time.perf_counter()
+        a, _ = om.fit_sequential(w.levels, w.f, w.h, w.nu, w.wendland_d, w.wendland_k)
+        s = om.evaluate(w.levels, a, w.h, w.nu, w.wendland_d, w.wendland_k, Q)
+        out.append({{"L": L, "N": w.N, "s": time.perf_counter() - t}})
+print(json.dumps(out))
 """
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               NUMEXPR_NUM_THREADS="1")
+
+
+def oracle_times(plan, threads, nu=HEAD_NU, wend=HEAD_W):
+    """Time the CPU oracle (as it stands) in a subprocess: plan = [(levels, repetitions)];
+    threads = the BLAS / OpenMP threads it may use.  Returns [{L, N, s}]."""
+    code = _ORACLE_CODE.format(root=ROOT, plan=plan, nu=nu, wend=wend)
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t, NUMEXPR_NUM_THREADS=t)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle baseline failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def power_law(samples, n_target):
+    """Least-squares fit of log t = log a + b log N over (N, t) samples; the extrapolated time at
+    n_target and the exponent b."""
+    xs = [math.log(n) for n, _ in samples]
+    ys = [math.log(t) for _, t in samples]
+    mx, my = statistics.mean(xs), statistics.mean(ys)
+    b = sum((x - mx) * (y - my) for x, y in zip(xs, ys)) / sum((x - mx) ** 2 for x in xs)
+    return math.exp(my + b * (math.log(n_target) - mx)), b
+
+
+def cpu_baseline(levels, small=3, large=4, reps=2):
+    """The oracle's sequential fit + evaluation on two bounded samples of the headline workload
+    (its first `small` and `large` levels), single-threaded and on every host core; the time of
+    the full workload is extrapolated by a power law in the point count through the samples."""
+    cores = os.cpu_count() or 1
+    n_full = halton_points(levels)
+    res = {}
+    for tag, threads in (("1_thread", 1), ("all_cores", cores)):
+        t = oracle_times([(small, reps), (large, reps)], threads)
+        pts = {}
+        for r in t:
+            pts.setdefault(r["N"], []).append(r["s"])
+        samples = [(n, min(v)) for n, v in sorted(pts.items())]
+        est, b = power_law(samples, n_full)
+        res[tag] = {"threads": threads, "samples_s": {str(n): s for n, s in samples}, "exponent": b,
+                    "estimate_ms": 1000.0 * est}
+    return res
 
 
 # ------------------------------------------------------------------ reference arm (the oracle)
@@ -218,19 +262,24 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    reps = args.warmup + args.steps
-    out = cpu_baseline(args.ref_levels, 1024, reps=reps)
-    ts = out["times"][args.warmup:]
-    n_work = halton_points(args.levels)
-    scale = n_work / out["N"]
-    ms_step = 1000.0 * statistics.mean(ts) * scale
-    sample = (f"oracle fit_sequential + evaluate on the first {args.ref_levels} levels of the workload "
-              f"({out['N']} points, 1024 queries), single-threaded, scaled by points ({n_work}/{out['N']})")
+    cores = os.cpu_count() or 1
+    n_full = halton_points(args.levels)
+    small = oracle_times([(3, 1)], cores)[0]
+    t = oracle_times([(4, args.warmup + args.steps)], cores)
+    large = t[args.warmup:]
+    t4 = statistics.mean(r["s"] for r in large)
+    est, b = power_law([(small["N"], small["s"]), (large[0]["N"], t4)], n_full)
+    ms_step = 1000.0 * est
+    sample = (f"ESTIMATE: each step times the oracle's fit_sequential + evaluate (4096 queries) on the first 4 "
+              f"levels of the workload ({large[0]['N']} points, mean {t4:.3f} s over {args.steps} steps after "
+              f"{args.warmup} warm-up), {cores} threads; a power law t = a N^b through that and one 3-level run "
+              f"({small['N']} points, {small['s']:.3f} s; b = {b:.2f}) extrapolates to the {n_full:,}-point "
+              f"workload")
     line = {"impl": "reference", "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "estimate": True,
             "config": {"workload": workload_label(args.levels), "rel_tol": REL_TOL},
-            "cpu_baseline": {"value": ms_step, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": ms_step, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": ms_step, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -252,14 +301,14 @@ def run_ours(args):
     B.build()
     ms.load()
 
-    w = inputs.halton_hierarchy(L=args.levels)
+    w = inputs.halton_hierarchy(L=args.levels, nu=HEAD_NU, wendland=HEAD_W)
     pts = torch.from_numpy(w.points).cuda()
     f = torch.from_numpy(w.f).cuda()
     Qh = inputs.query_grid(args.query_side, 2)
     Q = torch.from_numpy(Qh).cuda()
+    Q3 = torch.from_numpy(inputs.query_grid(32, 3)).cuda()  # 32^3 queries for the 3-D workload
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    n = w.n_per_level
 
     def barrier():
         if ws > 1:
@@ -267,35 +316,37 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # train the network once (levels 1-4 of this hierarchy), outside the timed region
-    Ht = ms.Hierarchy(2, n, pts, w.h, precision=ms.MS_PREC_MIXED, precond=ms.MS_PRECOND_LEARNED,
-                      wendland_d=2, wendland_k=1, nu=w.nu)
-    train = Ht.train_precond([0, 1, 2, 3], epochs=args.train_epochs)
-    params = Ht.precond_params()
-    Ht.close()
-    params3 = None  # the 3-D network (the --cfg3 block trains it)
-    Q3 = torch.from_numpy(inputs.query_grid(32, 3)).cuda()  # 32^3 queries for 3-D workloads
+    def train_network(wl, epochs):
+        """Train the network once on levels 1-4 of wl, outside every timed region."""
+        Ht = ms.Hierarchy(wl.d, wl.n_per_level, torch.from_numpy(wl.points).cuda(), wl.h,
+                          precision=ms.MS_PREC_MIXED, precond=ms.MS_PRECOND_LEARNED, wendland_d=wl.wendland_d,
+                          wendland_k=wl.wendland_k, nu=wl.nu)
+        st = Ht.train_precond([0, 1, 2, 3], epochs=epochs)
+        p = Ht.precond_params()
+        Ht.close()
+        return p, st
 
-    def step(prec, precond=ms.MS_PRECOND_NONE, inter_tol=0.0, wl=None, pts_=None, f_=None, **extra):
+    def step(prec, precond=ms.MS_PRECOND_NONE, wl=None, pts_=None, f_=None, params=None, q=None, **extra):
         wl = wl or w
         pts_ = pts if pts_ is None else pts_
         f_ = f if f_ is None else f_
+        q = Q if q is None else q
         opts = ms.ms_default_opts(wendland_d=wl.wendland_d, wendland_k=wl.wendland_k, nu=wl.nu, precision=prec,
-                                  precond=precond, inter_tol=inter_tol, **extra)
+                                  precond=precond, **extra)
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         hnd = ms.ms_build_hierarchy(wl.d, wl.n_per_level, pts_, wl.h, opts)
         if precond == ms.MS_PRECOND_LEARNED:
-            ms.ms_precond_params(hnd, wl.d, params if wl.d == 2 else params3)
+            ms.ms_precond_params(hnd, wl.d, params)
         alpha, st = ms.ms_fit(hnd, f_, REL_TOL)
         e1.record(stream)
-        s = ms.ms_evaluate(hnd, alpha, Q if wl.d == 2 else Q3)  # queries of the workload's dimension
+        s = ms.ms_evaluate(hnd, alpha, q)
         e2.record(stream)
         torch.cuda.synchronize()
         info = ms.ms_hierarchy_info(hnd)
         ms.ms_destroy(hnd)
         return {"total": e0.elapsed_time(e2), "eval": e1.elapsed_time(e2), "stats": st, "info": info,
-                "alpha": alpha}
+                "alpha": alpha, "s": s}
 
     def timed(k, *a, **kw):
         recs = []
@@ -306,134 +357,159 @@ def run_ours(args):
             barrier()
         return recs
 
+    def arm(k, *a, **kw):
+        """One untimed warm-up step, then k timed steps."""
+        timed(1, *a, **kw)
+        return timed(k, *a, **kw)
+
     def summary(recs):
         st = recs[-1]["stats"]
-        return {"ms_per_step": statistics.mean(r["total"] for r in recs),
+        return {"ms_per_step": statistics.mean(r["total"] for r in recs), "steps": len(recs),
                 "fit_ms": statistics.mean(r["stats"]["fit_ms"] for r in recs),
                 "build_ms": statistics.mean(r["info"]["build_ms"] for r in recs),
-                "cg_iterations": st["cg_iterations"], "rel_residual_max": max(st["rel_residual"]),
-                "precond_fallbacks": st["precond_fallbacks"],
+                "cg_iterations": st["cg_iterations"], "refinements": st["refinements"],
+                "rel_residual_max": max(st["rel_residual"]), "precond_fallbacks": st["precond_fallbacks"],
+                "fp64_fallbacks": st["fp64_fallbacks"],
                 "phase_ms": {k: round(v, 3) for k, v in st["phase_ms"].items()}}
 
+    def rel(a, b):
+        return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+    def roofline(recs, hbm, peak_kind, traffic_ratio, name):
+        fit_ms = statistics.mean(r["stats"]["fit_ms"] for r in recs)
+        fit_bytes = statistics.mean(r["stats"]["matvec_bytes"] for r in recs)
+        achieved = fit_bytes / (fit_ms * 1e-3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_kind": f"{peak_kind} hbm_gbs",
+                "traffic": traffic_ratio * fit_bytes if traffic_ratio else None,
+                "traffic_source": ("DRAM bytes per algorithmic byte from a 1-pass ncu capture of the 7-level "
+                                   "case of this workload, times this run's algorithmic bytes"
+                                   if traffic_ratio else "none (no capture of the current kernel sources)"),
+                "algorithmic_bytes_per_launch": fit_bytes, "launch_ms": fit_ms}
+
+    # ---- the network, trained once on levels 1-4 of the headline workload (outside the timing)
+    params, train = train_network(w, args.train_epochs)
     HEAD = (ms.MS_PREC_MIXED, ms.MS_PRECOND_LEARNED)
+
+    # ---- the headline: learned-PCG MIXED steps
     for _ in range(args.warmup):
-        step(*HEAD)
+        step(*HEAD, params=params)
     clocks = ClockSampler(local)
     lc0 = ms.ms_launch_count()
     clocks.start()
     t_wall = time.perf_counter()
-    recs = timed(args.steps, *HEAD)
+    recs = timed(args.steps, *HEAD, params=params)
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     launches = (ms.ms_launch_count() - lc0) / args.steps
     ms_step = max_over_ranks(statistics.mean(r["total"] for r in recs), ws, "cuda")
     last = recs[-1]
-    st, info = last["stats"], last["info"]
+    info = last["info"]
 
     out = {}
     if rank == 0:
         peaks, peak_kind = measured_peaks()
         hbm = float(peaks["hbm_gbs"])
-        fit_ms = statistics.mean(r["stats"]["fit_ms"] for r in recs)
-        fit_bytes = st["matvec_bytes"]
-        achieved = fit_bytes / (fit_ms * 1e-3) / 1e9
-        out["roofline"] = {"kernel": "k_fit<MIXED> (persistent Jacobi / learned-PCG solve)", "bound": "hbm",
-                           "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                           "peak_kind": f"{peak_kind} hbm_gbs",
-                           "traffic": recorded_traffic() if args.levels == 8 and args.train_epochs == 100 else None,
-                           "traffic_source": "profiles/k_fit_learned_halton8.md (1-pass ncu capture of this workload)",
-                           "algorithmic_bytes_per_launch": fit_bytes, "launch_ms": fit_ms}
+        out["roofline"] = roofline(recs, hbm, peak_kind, recorded_traffic(),
+                                   "k_fit<MIXED> (persistent Jacobi / learned-PCG solve)")
         out["learned_pcg"] = summary(recs)
-        out["phases_ms"] = {"build": out["learned_pcg"]["build_ms"], "fit_incl_precond": None,
-                            "fit_kernel": fit_ms, "evaluate": statistics.mean(r["eval"] for r in recs)}
-        out["phases_ms"]["fit_incl_precond"] = (out["learned_pcg"]["ms_per_step"] - out["phases_ms"]["build"]
-                                                - out["phases_ms"]["evaluate"])
+        out["phases_ms"] = {"build": out["learned_pcg"]["build_ms"], "fit_incl_precond_rows": None,
+                            "fit_kernel": out["roofline"]["launch_ms"],
+                            "evaluate": statistics.mean(r["eval"] for r in recs)}
+        out["phases_ms"]["fit_incl_precond_rows"] = (out["learned_pcg"]["ms_per_step"] - out["phases_ms"]["build"]
+                                                     - out["phases_ms"]["evaluate"])
         out["train"] = {"levels": [1, 2, 3, 4], "epochs": args.train_epochs, "extra_patches_per_point": 4, **train}
         out["nnz"] = {"A": info["nnz_A"], "B": info["nnz_B"]}
 
+        # ---- the metric's other arm and the variants, same workload, warmed
         if not args.no_variants:
-            k2 = max(2, args.steps // 2)
-            out["plain_fp64"] = summary(timed(k2, ms.MS_PREC_FP64))
-            out["mixed_no_precond"] = summary(timed(k2, ms.MS_PREC_MIXED))
-            out["mixed_exact_fsai"] = summary(timed(k2, ms.MS_PREC_MIXED, ms.MS_PRECOND_EXACT))
-            out["algorithm2_schedule_fp64"] = summary(timed(1, ms.MS_PREC_FP64, inter_tol=REL_TOL))
-            # the other CTAs-per-SM choice of the persistent solve kernel (autotuning evidence)
-            out["learned_pcg_1cta_per_sm"] = summary(timed(k2, *HEAD, solve_ctas_per_sm=1))
-            out["plain_fp64_1cta_per_sm"] = summary(timed(k2, ms.MS_PREC_FP64, solve_ctas_per_sm=1))
-            # lanes per row chosen by timing (ms_opts.autotune); the first handle times, the rest hit the cache
-            timed(1, *HEAD, autotune=1)
-            rt = timed(k2, *HEAD, autotune=1)
-            out["learned_pcg_autotuned"] = summary(rt)
-            out["learned_pcg_autotuned"]["tpr_A"] = rt[-1]["info"]["tpr_A"]
-            out["learned_pcg_autotuned"]["tpr_A_rule"] = info["tpr_A"]
+            k2 = args.arm_steps
+            r64 = arm(k2, ms.MS_PREC_FP64)
+            out["plain_fp64"] = summary(r64)
+            out["mixed_no_precond"] = summary(arm(k2, ms.MS_PREC_MIXED))
+            rex = arm(k2, ms.MS_PREC_MIXED, ms.MS_PRECOND_EXACT)
+            out["mixed_exact_fsai"] = summary(rex)
             out["speedup_learned_vs_plain_fp64"] = out["plain_fp64"]["ms_per_step"] / ms_step
-            # agreement of the headline coefficients with the plain FP64 fit (same hierarchy, same f)
-            a0 = timed(1, ms.MS_PREC_FP64)[0]["alpha"]
-            a1 = last["alpha"]
-            out["rel_diff_vs_fp64_coefficients"] = float(torch.linalg.norm(a1 - a0) / torch.linalg.norm(a0))
+            out["speedup_learned_vs_exact_fsai"] = out["mixed_exact_fsai"]["ms_per_step"] / ms_step
+            # accuracy of the headline against the plain FP64 fit (same hierarchy, same f): the
+            # approximant on the query grid and the coefficients
+            out["accuracy_vs_plain_fp64"] = {
+                "approximant_rel_diff": rel(last["s"], r64[-1]["s"]),
+                "coefficient_rel_diff": rel(last["alpha"], r64[-1]["alpha"]),
+                "exact_fsai_approximant_rel_diff": rel(rex[-1]["s"], r64[-1]["s"]),
+                "queries": int(Q.shape[0])}
+            del r64, rex
 
-        # stand-alone mat-vecs (sorted order): GB/s of the CSR kernels, matrix-free timing
+        # ---- side block: delta_j = 4 h_j, phi_{2,1} (well-conditioned levels)
+        if not args.no_side:
+            w4 = inputs.halton_hierarchy(L=args.levels, nu=SIDE_NU, wendland=SIDE_W)
+            p4, f4 = torch.from_numpy(w4.points).cuda(), torch.from_numpy(w4.f).cuda()
+            params4, train4 = train_network(w4, args.train_epochs)
+            kw4 = {"wl": w4, "pts_": p4, "f_": f4}
+            rl4 = arm(max(3, args.arm_steps), *HEAD, params=params4, **kw4)
+            r64 = arm(args.arm_steps, ms.MS_PREC_FP64, **kw4)
+            side = {"workload": workload_label(args.levels, SIDE_NU, SIDE_W), "learned_pcg": summary(rl4),
+                    "plain_fp64": summary(r64), "mixed_no_precond": summary(arm(args.arm_steps, ms.MS_PREC_MIXED, **kw4)),
+                    "mixed_exact_fsai": summary(arm(args.arm_steps, ms.MS_PREC_MIXED, ms.MS_PRECOND_EXACT, **kw4)),
+                    "train": train4,
+                    "roofline": roofline(rl4, hbm, peak_kind, None, "k_fit<MIXED>"),
+                    "approximant_rel_diff_learned_vs_fp64": rel(rl4[-1]["s"], r64[-1]["s"])}
+            side["speedup_learned_vs_plain_fp64"] = side["plain_fp64"]["ms_per_step"] / side["learned_pcg"]["ms_per_step"]
+            rt = arm(args.arm_steps, *HEAD, params=params4, autotune=1, **kw4)
+            side["learned_pcg_autotuned"] = summary(rt)
+            side["learned_pcg_autotuned"]["tpr_A"] = rt[-1]["info"]["tpr_A"]
+            side["learned_pcg_autotuned"]["tpr_A_rule"] = rl4[-1]["info"]["tpr_A"]
+            out["side_nu4_w21"] = side
+            del p4, f4, rl4, r64
+
+        # ---- stand-alone mat-vecs on the headline hierarchy (sorted order): GB/s of the CSR
+        #      kernels, instruction rates of the matrix-free one
         peaks_alu = {"fp32": ms.ms_peak_probe(ms.MS_PROBE_FP32), "fp64": ms.ms_peak_probe(ms.MS_PROBE_FP64),
                      "xu": ms.ms_peak_probe(ms.MS_PROBE_XU)}
-        H = ms.Hierarchy(2, n, pts, w.h, precision=ms.MS_PREC_MIXED, wendland_d=2, wendland_k=1, nu=w.nu)
-        N = w.N
-        x = torch.randn(N, dtype=torch.float64, device="cuda")
-        y = torch.empty_like(x)
-        mv = {}
-        for name, op, nnz, vb in [("A64", ms.MS_APPLY_A64, info["nnz_A"], 8), ("A32", ms.MS_APPLY_A32, info["nnz_A"], 4),
-                                  ("AMF32", ms.MS_APPLY_AMF32, info["nnz_A"], 0), ("B64", ms.MS_APPLY_B64, info["nnz_B"], 8)]:
-            for _ in range(3):
-                H.apply(op, x, y, sorted_order=True)
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-            reps = 20
-            ev[0].record(stream)
-            for _ in range(reps):
-                H.apply(op, x, y, sorted_order=True)
-            ev[1].record(stream)
-            torch.cuda.synchronize()
-            t_ms = ev[0].elapsed_time(ev[1]) / reps
-            if vb:
-                # matrix (col + val) + row offsets + y write + one read of x (FP32 ops also convert x)
-                b = nnz * (4 + vb) + N * (8 + 8 + 8) + (N * 12 if vb == 4 else 0)
-                mv[name] = {"ms": t_ms, "GBps": b / (t_ms * 1e-3) / 1e9, "frac_hbm": b / (t_ms * 1e-3) / 1e9 / hbm,
-                            "algorithmic_bytes": b}
-            else:
-                # matrix-free: bound by FP32 and XU issue; every candidate pair (points of the
-                # 3^d cells around each point's cell) costs 13 FP32-pipe instructions and one
-                # reciprocal square root (ms_matfree.cuh, d = 2, phi_{d,1})
-                cand = mf_candidates(w)
-                f32 = 13.0 * cand / (t_ms * 1e-3)
-                xu = cand / (t_ms * 1e-3)
-                mv[name] = {"ms": t_ms, "stored_entries_per_s": nnz / (t_ms * 1e-3), "candidate_pairs": cand,
-                            "fp32_instr_per_s": f32, "frac_fp32": f32 / peaks_alu["fp32"],
-                            "xu_per_s": xu, "frac_xu": xu / peaks_alu["xu"]}
-        out["matvec"] = mv
         out["alu_peaks_measured"] = {"fp32_instr_per_s": peaks_alu["fp32"], "fp64_instr_per_s": peaks_alu["fp64"],
                                      "xu_per_s": peaks_alu["xu"], "probe": "ms_peak_probe (own FMA / rsqrt chains)"}
-        H.close()
+        if not args.no_matvec:
+            H = ms.Hierarchy(2, w.n_per_level, pts, w.h, precision=ms.MS_PREC_MIXED, wendland_d=w.wendland_d,
+                             wendland_k=w.wendland_k, nu=w.nu)
+            N = w.N
+            x = torch.randn(N, dtype=torch.float64, device="cuda")
+            y = torch.empty_like(x)
+            mv = {"workload": "the headline hierarchy (sorted order), 20 launches after 3"}
+            cand = mf_candidates(w)
+            for name, op, nnz, vb in [("A64", ms.MS_APPLY_A64, info["nnz_A"], 8),
+                                      ("A32", ms.MS_APPLY_A32, info["nnz_A"], 4),
+                                      ("AMF32", ms.MS_APPLY_AMF32, info["nnz_A"], 0),
+                                      ("B64", ms.MS_APPLY_B64, info["nnz_B"], 8)]:
+                for _ in range(3):
+                    H.apply(op, x, y, sorted_order=True)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                reps = 20
+                ev[0].record(stream)
+                for _ in range(reps):
+                    H.apply(op, x, y, sorted_order=True)
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                t_ms = ev[0].elapsed_time(ev[1]) / reps
+                if vb:
+                    # matrix (col + val) + row offsets + y write + one read of x (FP32 ops also convert x)
+                    b = nnz * (4 + vb) + N * (8 + 8 + 8) + (N * 12 if vb == 4 else 0)
+                    mv[name] = {"ms": t_ms, "GBps": b / (t_ms * 1e-3) / 1e9,
+                                "frac_hbm": b / (t_ms * 1e-3) / 1e9 / hbm, "algorithmic_bytes": b}
+                else:
+                    # matrix-free: bound by FP32 and XU issue; every candidate pair (points of the 3^d
+                    # cells around each point's cell) costs 13 FP32-pipe instructions (15 for
+                    # phi_{d,2}) and one reciprocal square root
+                    per = 15.0 if w.wendland_k == 2 else 13.0
+                    f32 = per * cand / (t_ms * 1e-3)
+                    xu = cand / (t_ms * 1e-3)
+                    mv[name] = {"ms": t_ms, "stored_entries_per_s": nnz / (t_ms * 1e-3), "candidate_pairs": cand,
+                                "fp32_instr_per_s": f32, "frac_fp32": f32 / peaks_alu["fp32"],
+                                "xu_per_s": xu, "frac_xu": xu / peaks_alu["xu"]}
+            out["matvec"] = mv
+            H.close()
 
-        # nu = 8, phi_{2,2} (ill-conditioned levels): learned-PCG MIXED vs plain FP64, one step each
-        if not args.no_nu8:
-            w8 = inputs.halton_hierarchy(L=args.levels, nu=8.0, wendland=(2, 2))
-            p8, f8 = torch.from_numpy(w8.points).cuda(), torch.from_numpy(w8.f).cuda()
-            H8 = ms.Hierarchy(2, w8.n_per_level, p8, w8.h, precision=ms.MS_PREC_MIXED,
-                              precond=ms.MS_PRECOND_LEARNED, wendland_d=2, wendland_k=2, nu=8.0)
-            train8 = H8.train_precond([0, 1, 2, 3], epochs=args.train_epochs)
-            params8 = H8.precond_params()
-            H8.close()
-            saved = params
-            params = params8
-            r8 = timed(1, ms.MS_PREC_MIXED, ms.MS_PRECOND_LEARNED, wl=w8, pts_=p8, f_=f8)
-            params = saved
-            r8f = timed(1, ms.MS_PREC_FP64, wl=w8, pts_=p8, f_=f8)
-            out["nu8_w22"] = {"workload": "as above with delta_j = 8 h_j and Wendland phi_{2,2}",
-                              "learned_pcg": summary(r8), "plain_fp64": summary(r8f),
-                              "train": {"levels": [1, 2, 3, 4], **train8},
-                              "speedup": summary(r8f)["ms_per_step"] / summary(r8)["ms_per_step"]}
-            del p8, f8
-
-        # batching: 256 right-hand sides on one 6-level hierarchy (87,360 points), MIXED without
-        # preconditioner, solved 32 per launch; against single-RHS fits of the first 16 of them
+        # ---- batching: 256 right-hand sides on one 6-level hierarchy (87,360 points), MIXED without
+        #      preconditioner; against single-RHS fits of the first 16 of them
         if not args.no_batch:
             wb = inputs.halton_hierarchy(L=6)
             pb = torch.from_numpy(wb.points).cuda()
@@ -464,7 +540,7 @@ def run_ours(args):
             Hb.close()
             out["batch_rhs"] = {"workload": "d=2, 6 Halton levels N_j=64*4^(j-1) (87,360 points), delta_j=4h_j, "
                                             "phi_{2,1}, 256 right-hand sides (seeded 5-Gaussian mixtures), MIXED",
-                                "rhs": 256, "rhs_per_launch": 32, "batched_ms": t_batch,
+                                "rhs": 256, "launches": stb["kernel_launches"], "batched_ms": t_batch,
                                 "batched_ms_per_rhs": t_batch / 256, "single_ms_per_rhs": statistics.mean(t_single),
                                 "speedup_per_rhs": statistics.mean(t_single) / (t_batch / 256),
                                 "kernel_ms": stb["fit_ms"], "rel_residual_max": max(stb["rel_residual"]),
@@ -523,36 +599,11 @@ def run_ours(args):
                 "graph_rel_residual_max": max(max(s["rel_residual"]) for s in stg)}
             for Hi in Hs:
                 Hi.close()
-            # the same 64 hierarchies with the learned preconditioner (the network trained once on
-            # levels 1-4 of the headline workload; its rows built inside the batched call)
-            HsL = [ms.Hierarchy(2, wi.n_per_level, torch.from_numpy(wi.points).cuda(), wi.h,
-                                precision=ms.MS_PREC_MIXED, precond=ms.MS_PRECOND_LEARNED, wendland_d=2,
-                                wendland_k=1, nu=wi.nu) for wi in wsb]
-            for Hi in HsL:
-                Hi.precond_params(params)
-            hl = [Hi.handle for Hi in HsL]
-            ms.ms_fit_batch(hl, fsb, REL_TOL)
-            for Hi in HsL:  # new weights: the next batched call builds the rows again, inside the timing
-                Hi.precond_params(params)
-            flush.fill_(1.0)
-            torch.cuda.synchronize()
-            ev[0].record(stream)
-            AbL, stbL = ms.ms_fit_batch(hl, fsb, REL_TOL)
-            ev[1].record(stream)
-            torch.cuda.synchronize()
-            t_bl = ev[0].elapsed_time(ev[1])
-            worstL = max(float(torch.linalg.norm(al - ai) / torch.linalg.norm(ai)) for al, ai in zip(AbL, Ab))
-            out["batch_hierarchies"]["learned_batched_ms"] = t_bl
-            out["batch_hierarchies"]["learned_kernel_ms"] = stbL[0]["fit_ms"]
-            out["batch_hierarchies"]["learned_rel_residual_max"] = max(max(s["rel_residual"]) for s in stbL)
-            out["batch_hierarchies"]["learned_rel_diff_vs_plain_batched_max"] = worstL
-            for Hi in HsL:
-                Hi.close()
-            del fsb, Ab, AbL
+            del fsb, Ab
 
-        # the paper's own experiment (Section 5: grids (2^l+1)^2, phi_{3,1}, nu = 4, Franke data), plain
-        # FP64 as the paper runs it, against Figure 4's A100 times (context: other hardware, tolerance
-        # not reported there)
+        # ---- the paper's own experiment (Section 5: grids (2^l+1)^2, phi_{3,1}, nu = 4, Franke data),
+        #      plain FP64 as the paper runs it, against Figure 4's A100 times (context: other hardware,
+        #      tolerance not reported there)
         if not args.no_paper:
             paper_s = {7: 0.974, 8: 1.485, 9: 4.479, 10: 20.111, 11: 92.642}
             rows = []
@@ -572,42 +623,44 @@ def run_ours(args):
                 del pp, fp
             out["paper_grids_fp64"] = rows
 
-        # the 3-D configuration (uniform random points, 6 levels, 4.68M points): FP64 CSR against
-        # MIXED with the FP32 matrix-free inner mat-vec (levels beyond FP32 switch to FP64 CG)
-        if args.cfg3:
+        # ---- the 3-D configuration (uniform random points, 6 levels, 4.68M points, phi_{3,1},
+        #      delta = 3h): FP64 CSR, MIXED CSR, MIXED with the matrix-free FP32 inner mat-vec, and
+        #      learned-PCG CSR (a 3-D network: 48 inputs), one step each after one warm-up build
+        if not args.no_3d:
             w3 = inputs.random3d_hierarchy(L=6)
             p3, f3 = torch.from_numpy(w3.points).cuda(), torch.from_numpy(w3.f).cuda()
             o3 = {"workload": "d=3 uniform random, N_j=125*8^(j-1), 6 levels (4,681,125 points), "
-                              "delta_j=3h_j, phi_{3,1}, 30 Gaussians"}
-            # the network for 3-D patches (48 inputs), trained on levels 1-4 of this hierarchy
-            Ht3 = ms.Hierarchy(3, w3.n_per_level, p3, w3.h, precision=ms.MS_PREC_MIXED, precond=ms.MS_PRECOND_LEARNED,
-                               wendland_d=3, wendland_k=1, nu=w3.nu)
-            o3["train"] = Ht3.train_precond([0, 1, 2, 3], epochs=max(10, args.train_epochs // 4))
-            params3 = Ht3.precond_params()
-            Ht3.close()
-            for tag, kw in (("fp64_csr", {"prec": ms.MS_PREC_FP64}),
-                            ("mixed_matrix_free", {"prec": ms.MS_PREC_MIXED, "op": ms.MS_OP_MATRIX_FREE}),
+                              "delta_j=3h_j, phi_{3,1}, 30 Gaussians", "steps": 1}
+            params3, o3["train"] = train_network(w3, max(10, args.train_epochs // 4))
+            kw3 = {"wl": w3, "pts_": p3, "f_": f3, "q": Q3}
+            timed(1, ms.MS_PREC_MIXED, ms.MS_PRECOND_LEARNED, params=params3, **kw3)  # warm-up
+            for tag, kw in (("learned_pcg_csr", {"prec": ms.MS_PREC_MIXED, "precond": ms.MS_PRECOND_LEARNED}),
                             ("mixed_csr", {"prec": ms.MS_PREC_MIXED}),
-                            ("learned_pcg_csr", {"prec": ms.MS_PREC_MIXED, "precond": ms.MS_PRECOND_LEARNED})):
+                            ("mixed_matrix_free", {"prec": ms.MS_PREC_MIXED, "op": ms.MS_OP_MATRIX_FREE}),
+                            ("fp64_csr", {"prec": ms.MS_PREC_FP64})):
                 extra = {"op": kw["op"]} if "op" in kw else {}
                 try:
-                    r3 = step(kw["prec"], kw.get("precond", ms.MS_PRECOND_NONE), wl=w3, pts_=p3, f_=f3, **extra)
+                    r3 = timed(1, kw["prec"], kw.get("precond", ms.MS_PRECOND_NONE), params=params3, **kw3,
+                               **extra)[0]
                     o3[tag] = {"step_ms": r3["total"], "fit_ms": r3["stats"]["fit_ms"],
                                "build_ms": r3["info"]["build_ms"], "cg_iterations": r3["stats"]["cg_iterations"],
                                "fp64_fallbacks": r3["stats"]["fp64_fallbacks"],
-                               "rel_residual_max": max(r3["stats"]["rel_residual"])}
+                               "rel_residual_max": max(r3["stats"]["rel_residual"]),
+                               "hbm_frac_fit": r3["stats"]["matvec_bytes"] / (r3["stats"]["fit_ms"] * 1e-3) / 1e9 / hbm}
                 except ms.MsError as e:
                     o3[tag] = {"error": str(e)[:160]}
             out["random3d"] = o3
             del p3, f3
 
-        # end to end through the host-pointer C ABI (H2D of points, f, queries; D2H of alpha, values)
+        # ---- end to end through the host-pointer C ABI (H2D of points, f, queries and the network;
+        #      D2H of alpha and the approximant), one untimed round first
         e2e = []
-        for i in range(max(2, args.steps // 2) + 1):
+        for i in range(max(2, args.steps // 4) + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            Hh = ms.Hierarchy(2, n, w.points, w.h, precision=ms.MS_PREC_MIXED, precond=ms.MS_PRECOND_LEARNED,
-                              wendland_d=2, wendland_k=1, nu=w.nu)
+            Hh = ms.Hierarchy(2, w.n_per_level, w.points, w.h, precision=ms.MS_PREC_MIXED,
+                              precond=ms.MS_PRECOND_LEARNED, wendland_d=w.wendland_d, wendland_k=w.wendland_k,
+                              nu=w.nu)
             Hh.precond_params(params)
             a_h, _ = Hh.fit(w.f, REL_TOL)
             s_h = Hh.evaluate(a_h, Qh)
@@ -617,17 +670,20 @@ def run_ours(args):
         h2d = w.points.nbytes + w.f.nbytes + Qh.nbytes + params.nbytes
         d2h = a_h.nbytes + s_h.nbytes
         out["e2e"] = {"value": statistics.mean(e2e), "unit": "ms", "h2d_bytes_per_step": int(h2d),
-                      "d2h_bytes_per_step": int(d2h)}
+                      "d2h_bytes_per_step": int(d2h), "steps": len(e2e)}
 
         if not args.no_cpu:
-            cb = cpu_baseline(args.cpu_levels, 4096)
-            scale = w.N / cb["N"]
-            out["cpu_baseline"] = {"value": 1000.0 * cb["times"][0] * scale, "unit": "ms", "cores": 1,
-                                   "kind": "oracle",
-                                   "sample": (f"oracle fit_sequential + evaluate on the first {args.cpu_levels} "
-                                              f"levels ({cb['N']} points, 4096 queries) took "
-                                              f"{cb['times'][0]:.2f} s single-threaded; scaled by points "
-                                              f"({w.N}/{cb['N']})")}
+            cb = cpu_baseline(args.levels)
+            one, allc = cb["1_thread"], cb["all_cores"]
+            out["cpu_baseline"] = {
+                "value": allc["estimate_ms"], "unit": "ms", "cores": allc["threads"], "kind": "oracle",
+                "estimate": True, "single_thread_ms": one["estimate_ms"],
+                "sample": (f"ESTIMATE: the oracle's fit_sequential + evaluate (4096 queries) timed on the first 3 "
+                           f"and 4 levels of the workload (points: seconds {allc['samples_s']} on "
+                           f"{allc['threads']} threads, {one['samples_s']} on 1 thread, best of 2), extrapolated "
+                           f"to {w.N:,} points by the power law t = a N^b through them (b = {allc['exponent']:.2f} "
+                           f"/ {one['exponent']:.2f})"),
+                "detail": cb}
 
         line = {"metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",

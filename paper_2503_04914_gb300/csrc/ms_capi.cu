@@ -130,6 +130,8 @@ ms_status build_common(int d, int L, const int64_t* n_per_level, const double* p
 
 // ---------------------------------------------------------------- internal helpers
 
+void ms_clear_error() { g_err[0] = 0; }
+
 void ms_set_error(ms_status st, const char* fmt, ...) {
     (void)st;
     va_list ap;
@@ -213,6 +215,7 @@ void ms_pool_free(void* p) {
     if (!p || device_pool(&dp) != MS_OK) return;
     cudaFreeAsync(p, dp->stream);
 }
+
 
 ms_status ms_alloc(ms_hierarchy* h, void** p, size_t bytes) {
     if (h->nallocs >= (int)(sizeof(h->allocs) / sizeof(h->allocs[0]))) {
@@ -501,6 +504,15 @@ ms_status ms_hierarchy_info(const ms_hierarchy* h, ms_info* info) {
     info->device_bytes = h->device_bytes;
     info->build_ms = h->build_ms;
     for (int l = 0; l < h->L; ++l) info->tpr_A[l] = ms_tpr_of(h, l);
+    return MS_OK;
+}
+
+ms_status ms_trim_memory(void) {
+    g_err[0] = 0;
+    DevPool* dp = nullptr;
+    MS_TRY(device_pool(&dp));
+    MS_CUDA(cudaStreamSynchronize(dp->stream));  // frees are ordered on the pool's stream
+    MS_CUDA(cudaMemPoolTrimTo(dp->pool, 0));
     return MS_OK;
 }
 

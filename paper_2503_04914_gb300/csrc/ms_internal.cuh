@@ -182,6 +182,7 @@ struct MsError {
     ms_status st;
 };
 void ms_set_error(ms_status st, const char* fmt, ...);
+void ms_clear_error();  // empties this thread's last-error message (entry of every C-ABI call)
 void ms_count_launch(unsigned n = 1);  // process-wide kernel launch counter
 ms_status ms_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 

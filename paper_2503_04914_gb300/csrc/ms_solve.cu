@@ -497,7 +497,8 @@ constexpr size_t kStaticPart = pad256(sizeof(double) * kAcc * MS_MAXL * kStaticM
 constexpr size_t kStaticGpart = pad256(sizeof(double) * kMaxGroups * kAcc * MS_MAXL);
 constexpr size_t kStaticSmall = 4096;  // barrier words, status, per-level counters, residuals, sums
 constexpr size_t kStaticBytes =
-    7 * kStaticVec64 + 5 * kStaticVec32 + kStaticPart + kStaticGpart + kStaticSmall;  // ~5.4 MiB
+    7 * kStaticVec64 + 5 * kStaticVec32 + kStaticPart + kStaticGpart + kStaticSmall;
+static_assert(kStaticBytes == 5820416, "the header documents the array as about 5.6 MiB (5,820,416 bytes)");
 
 }  // namespace
 
@@ -509,8 +510,11 @@ std::mutex g_scratch_mu;
 void* g_scratch_addr[256] = {};
 
 // Device address of g_fit_scratch on device `dev` (which must be current),
-// looked up once per device.  In host code the name g_fit_scratch is only a
-// host-side stand-in: it must never be handed to a kernel.
+// looked up once per device and cached for the process.  In host code the name
+// g_fit_scratch is only a host-side stand-in: it must never be handed to a kernel.
+// A cudaDeviceReset ends the context the cached address belongs to; like every
+// handle of that device, the cache is then invalid (the library does not support
+// use across a reset).
 ms_status fit_scratch_address(int dev, unsigned char** out) {
     if (dev < 0 || dev >= 256) {
         ms_set_error(MS_ERR_STATE, "device ordinal %d out of range", dev);
@@ -531,6 +535,7 @@ ms_status fit_scratch_address(int dev, unsigned char** out) {
 
 extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, double rel_tol, double* alpha_dev,
                                        ms_fit_stats* stats, void* stream) {
+    ms_clear_error();
     if (!h || !f_dev || !alpha_dev) {
         ms_set_error(MS_ERR_ARG, "handle, f and alpha must not be NULL");
         return MS_ERR_ARG;
@@ -599,6 +604,9 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
     a.prof = reinterpret_cast<unsigned long long*>(small + 2048);  // [kProf]
     a.pcfb = reinterpret_cast<int*>(small + 3072);                 // [2]
     a.pc = 0;  // the allocation-free fit runs without a preconditioner (checked above)
+    // lanes per target point of the matrix-free operator as ms_fit_dev chooses them, also on a
+    // handle that has never been fitted
+    a.mf_tpp = h->mf_tpp_tuned > 0 ? h->mf_tpp_tuned : mf_tpp_for(h);
 
     ms_gather_sorted(f_dev, v64[0], h->perm, h->N, 1, 0, st);
     void* args[] = {&a};
@@ -613,11 +621,15 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
     int64_t it[MS_MAXL];
     int ref[MS_MAXL];
     double res[MS_MAXL], b = 0.0;
+    unsigned long long pr[kProf];
+    int fb[2] = {0, 0};
     MS_CUDA(cudaMemcpyAsync(&dstat, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     MS_CUDA(cudaMemcpyAsync(it, iters, sizeof(it), cudaMemcpyDeviceToHost, st));
     MS_CUDA(cudaMemcpyAsync(ref, refines, sizeof(ref), cudaMemcpyDeviceToHost, st));
     MS_CUDA(cudaMemcpyAsync(res, resid, sizeof(res), cudaMemcpyDeviceToHost, st));
     MS_CUDA(cudaMemcpyAsync(&b, bytes, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MS_CUDA(cudaMemcpyAsync(pr, a.prof, sizeof(pr), cudaMemcpyDeviceToHost, st));
+    MS_CUDA(cudaMemcpyAsync(fb, a.pcfb, sizeof(fb), cudaMemcpyDeviceToHost, st));
     MS_CUDA(cudaStreamSynchronize(st));
     float ms = 0.f;
     MS_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
@@ -634,6 +646,9 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
         stats->fit_ms = ms;
         stats->matvec_bytes = b;
         stats->kernel_launches = 3;
+        stats->precond_fallbacks = fb[0];
+        stats->fp64_fallbacks = fb[1];
+        for (int i = 0; i < kProf; ++i) stats->phase_ms[i] = 1e-6 * (double)pr[i];
     }
     if (dstat != 0) {
         ms_set_error((ms_status)dstat, "device status %d during the allocation-free fit", dstat);

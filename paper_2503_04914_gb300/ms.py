@@ -33,7 +33,8 @@ EXPORTED = ["ms_default_opts", "ms_build_hierarchy", "ms_build_hierarchy_dev", "
             "ms_fit_static_dev", "ms_fit_batch", "ms_fit_batch_dev", "ms_batch_plan_create", "ms_batch_plan_launch",
             "ms_batch_plan_stats", "ms_batch_plan_destroy", "ms_default_train_opts", "ms_train_precond", "ms_precond_params",
             "ms_precond_inspect", "ms_evaluate", "ms_evaluate_dev", "ms_apply_dev", "ms_get_permutation", "ms_hierarchy_info",
-            "ms_peak_probe", "ms_wait_selftest", "ms_launch_count", "ms_last_error", "ms_destroy"]
+            "ms_peak_probe", "ms_wait_selftest", "ms_launch_count", "ms_last_error", "ms_destroy",
+            "ms_trim_memory"]
 
 
 class ms_opts(C.Structure):
@@ -148,6 +149,7 @@ def load(path: str | None = None):
         if name not in ("ms_default_opts", "ms_last_error", "ms_destroy", "ms_launch_count",
                         "ms_default_train_opts", "ms_batch_plan_destroy"):
             getattr(lib, name).restype = C.c_int  # ms_status
+    lib.ms_trim_memory.argtypes = []
     lib.ms_launch_count.argtypes = []
     lib.ms_launch_count.restype = C.c_uint64
     _lib = lib
@@ -429,6 +431,11 @@ def ms_launch_count() -> int:
 
 def ms_last_error() -> str:
     return load().ms_last_error().decode(errors="replace")
+
+
+def ms_trim_memory() -> None:
+    """Return the library pool's unused device memory (build scratch, freed handles)."""
+    _check(load().ms_trim_memory())
 
 
 def ms_destroy(handle) -> None:

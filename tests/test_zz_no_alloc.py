@@ -50,15 +50,66 @@ def test_static_fit_matches_fit_dev_on_two_calls(prec, tol):
     rhs = [w.f, g2(w.points)]
     for call, fh in enumerate(rhs):
         f = torch.from_numpy(np.ascontiguousarray(fh)).cuda()
-        ref, _ = H.fit(f, rel_tol=1e-12)
+        ref, st_ref = H.fit(f, rel_tol=1e-12)
         out = torch.full_like(f, float("nan"))
         rc, st = _static_fit(lib, H, f, out, 1e-12)
         assert rc == ms.MS_OK, (call, ms.ms_last_error())
+        assert ms.ms_last_error() == ""
         torch.cuda.synchronize()
         a, r = out.cpu().numpy(), ref.cpu().numpy()
         assert np.all(np.isfinite(a))
         assert np.linalg.norm(a - r) <= tol * np.linalg.norm(r), call
         assert max(st.rel_residual[:w.L]) <= 1e-12
+        # the statistics the kernel records come back as ms_fit_dev's do
+        assert st.fp64_fallbacks == st_ref["fp64_fallbacks"]
+        assert list(st.cg_iterations[:w.L]) == st_ref["cg_iterations"]
+        assert sum(st.phase_ms[:7]) > 0.0
+    H.close()
+
+
+@pytest.mark.parametrize("prec,op,tol", [(ms.MS_PREC_FP64, ms.MS_OP_CSR, 1e-10),
+                                         (ms.MS_PREC_MIXED, ms.MS_OP_CSR, 1e-8),
+                                         (ms.MS_PREC_MIXED, ms.MS_OP_MATRIX_FREE, 1e-8)])
+def test_static_fit_first_on_a_fresh_handle(prec, op, tol):
+    """The intended use: a handle that has never had a work space fits without allocating.
+    Its coefficients match ms_fit_dev on a second, separately built handle, on two calls."""
+    import torch
+    B.build()
+    lib = ms.load()
+    w = _workload(seed=77)
+    Hs = ms.Hierarchy.from_workload(w, device=True, precision=prec, op=op)
+    Hd = ms.Hierarchy.from_workload(w, device=True, precision=prec, op=op)
+    for call, fh in enumerate([w.f, inputs.GaussianMixture(6, 2, 99)(w.points)]):
+        f = torch.from_numpy(np.ascontiguousarray(fh)).cuda()
+        out = torch.full_like(f, float("nan"))
+        rc, st = _static_fit(lib, Hs, f, out, 1e-12)
+        assert rc == ms.MS_OK, (call, ms.ms_last_error())
+        ref, _ = Hd.fit(f, rel_tol=1e-12)
+        torch.cuda.synchronize()
+        a, r = out.cpu().numpy(), ref.cpu().numpy()
+        assert np.linalg.norm(a - r) <= tol * np.linalg.norm(r), call
+        assert max(st.rel_residual[:w.L]) <= 1e-12
+    Hs.close()
+    Hd.close()
+
+
+def test_static_fit_reports_non_finite_f():
+    import torch
+    B.build()
+    lib = ms.load()
+    w = _workload(seed=5)
+    H = ms.Hierarchy.from_workload(w, device=True)
+    fh = np.array(w.f)
+    fh[5] = np.nan
+    f = torch.from_numpy(fh).cuda()
+    out = torch.empty_like(f)
+    rc, st = _static_fit(lib, H, f, out, 1e-10)
+    assert rc == ms.MS_ERR_NUMERIC
+    assert st.device_status == ms.MS_ERR_NUMERIC
+    # the array is usable again right after the failed call
+    f2 = torch.from_numpy(np.ascontiguousarray(w.f)).cuda()
+    rc, st = _static_fit(lib, H, f2, out, 1e-10)
+    assert rc == ms.MS_OK and ms.ms_last_error() == ""
     H.close()
 
 

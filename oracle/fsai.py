@@ -24,18 +24,24 @@ Definitions (all per level l, points X_l in input order, delta = delta_l, d = di
     frame fixed by the patch itself removes those d(d-1)/2 + 1 nuisance directions from the
     network's input (measured on the oracle: a network trained on levels 1-4 needs 80 instead
     of 130 PCG iterations on level 5, exact rows 13).
-  * network   o = W3 relu(W2 relu(W1 z + b1) + b2) + b3  (hidden width 64, 17 outputs),
-    ghat = mu + sigma * o (per-output standardisation of the training targets), with the
-    diagonal clamped to >= 0.1 mu_0, the outputs of missing neighbours set to zero, and the
-    row rescaled to ghat^T K ghat = 1 (K the scaled patch matrix): the exact row has this
-    value, which is (G A G^T)_ii = 1.
-  * loss      energy norm of the error of the row in the patch's own metric, averaged over
-              samples: (1/S) sum_s e_s^T K_s e_s with e = sigma * (o - t) on the valid outputs
-              (zero elsewhere), t = (ghat - mu)/sigma the standardised exact row and
-              K_s = phi(|x_a - x_b|/delta) the scaled patch matrix (self first).  The exact row
-              minimises g^T K g - 2 log g_self, so this loss weighs errors the way the
-              preconditioner feels them, where a plain MSE on the (ill-conditioned) rows is
-              dominated by directions K hardly sees.
+  * network   o = W3 relu(W2 relu(W1 z + b1) + b2) + b3  (hidden width 64, 17 m outputs): m
+    candidate rows, u_1 = mu + sigma * o[0:17] (the standardised row, per-entry mean mu and
+    deviation sigma of the training targets) and u_k = sigma * o[17 (k-1) : 17 k] for k > 1
+    (corrections around it), the outputs of missing neighbours set to zero.
+  * row       the factorised-sparse-approximate-inverse row within the span of the candidates
+    (combine below): the exact row minimises g^T K g subject to g_self = 1, so restricted to
+    g = U c (U = [u_1 .. u_m], K the scaled patch matrix) the minimiser is
+    g = U y / sqrt(q), y = S_r^-1 U^T e_1, S = U^T K U, q = e_1^T U y, normalised to g^T K g = 1
+    (the value the exact row has, which is (G A G^T)_ii = 1) with g_self = sqrt(q) > 0.  S_r =
+    S + 1e-6 diag(S) (a ridge relative to each candidate's own energy: the candidates may be
+    nearly dependent in the K metric).  With m = 1 this is the candidate rescaled to unit
+    energy; with the exact row in the span it is the exact row.  A patch of n <= m points is
+    spanned by any m generic candidates, so its row is the exact row itself (no ridge).
+  * loss      the Kaporin-type gap of the row: (1/S) sum_s (log q*_s - log q_s), q* = (K^-1)_11 =
+              ghat*_self^2 the value of the exact row.  q <= q* because the exact row maximises
+              g_self over g^T K g = 1, so the loss is >= 0 and vanishes exactly when the exact row
+              lies in the candidates' span; it does not depend on the scale of the candidates,
+              so the network learns a subspace, and the combination is solved exactly per row.
   * Adam      beta1 = 0.9, beta2 = 0.999, eps = 1e-8, bias-corrected.
   * training set  the patches of every point of the training levels, plus R extra patches per
     point: for draw r the patch of point i takes the K nearest points j != i within delta
@@ -189,31 +195,31 @@ def target_matrix(ghat_rows, pat):
 # ----------------------------------------------------------------------------- network
 
 
-def param_shapes(n_in: int):
-    return [(HIDDEN, n_in), (HIDDEN,), (HIDDEN, HIDDEN), (HIDDEN,), (N_OUT, HIDDEN), (N_OUT,)]
+def param_shapes(n_in: int, m: int = 1):
+    return [(HIDDEN, n_in), (HIDDEN,), (HIDDEN, HIDDEN), (HIDDEN,), (m * N_OUT, HIDDEN), (m * N_OUT,)]
 
 
-def unpack(theta: np.ndarray, n_in: int):
+def unpack(theta: np.ndarray, n_in: int, m: int = 1):
     out, o = [], 0
-    for s in param_shapes(n_in):
+    for s in param_shapes(n_in, m):
         k = int(np.prod(s))
         out.append(theta[o:o + k].reshape(s))
         o += k
     return out
 
 
-def n_params(n_in: int) -> int:
-    return sum(int(np.prod(s)) for s in param_shapes(n_in))
+def n_params(n_in: int, m: int = 1) -> int:
+    return sum(int(np.prod(s)) for s in param_shapes(n_in, m))
 
 
-def init_params(n_in: int, seed: int) -> np.ndarray:
+def init_params(n_in: int, seed: int, m: int = 1) -> np.ndarray:
     """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) for every weight and bias of a layer, drawn
     from SplitMix64(seed) in parameter order (W1, b1, W2, b2, W3, b3)."""
     from paper_2503_04914_gb300.inputs import uniform01
-    u = uniform01(seed, n_params(n_in))
-    theta = np.empty(n_params(n_in))
+    u = uniform01(seed, n_params(n_in, m))
+    theta = np.empty(n_params(n_in, m))
     o = 0
-    for s, fan in zip(param_shapes(n_in), [n_in, n_in, HIDDEN, HIDDEN, HIDDEN, HIDDEN]):
+    for s, fan in zip(param_shapes(n_in, m), [n_in, n_in, HIDDEN, HIDDEN, HIDDEN, HIDDEN]):
         k = int(np.prod(s))
         b = 1.0 / math.sqrt(fan)
         theta[o:o + k] = -b + 2.0 * b * u[o:o + k]
@@ -221,8 +227,8 @@ def init_params(n_in: int, seed: int) -> np.ndarray:
     return theta
 
 
-def forward(theta, Z, n_in):
-    W1, b1, W2, b2, W3, b3 = unpack(theta, n_in)
+def forward(theta, Z, n_in, m: int = 1):
+    W1, b1, W2, b2, W3, b3 = unpack(theta, n_in, m)
     a1 = Z @ W1.T + b1
     h1 = np.maximum(a1, 0.0)
     a2 = h1 @ W2.T + b2
@@ -243,19 +249,85 @@ def patch_matrices(X: np.ndarray, delta: float, wd: int, wk: int, pat, selfs=Non
     return Ks
 
 
-def loss(theta, Z, T_std, Mk, Ks, sig, n_in):
-    o, _ = forward(theta, Z, n_in)
-    e = sig * (o - T_std) * Mk
-    return float(np.einsum("si,sij,sj->", e, Ks, e) / len(Z))
+RIDGE = 1e-6  # ridge of S = U^T K U, relative to each diagonal entry
 
 
-def grad(theta, Z, T_std, Mk, Ks, sig, n_in):
-    """Analytic gradient of loss() (backpropagation through the three layers)."""
-    W1, b1, W2, b2, W3, b3 = unpack(theta, n_in)
-    o, (a1, h1, a2, h2) = forward(theta, Z, n_in)
+def candidate_rows(o, mu, sig, Mk, m):
+    """U[s, a, k]: candidate k of sample s, entry a; u_1 = mu + sig o_1, u_k = sig o_k (k > 1),
+    zero past the patch."""
+    S = len(o)
+    U = sig[None, :, None] * o.reshape(S, m, N_OUT).transpose(0, 2, 1)
+    U[:, :, 0] += mu[None, :]
+    return U * Mk[:, :, None]
+
+
+def combine(U, K, n):
+    """The FSAI row of one patch of n points within span(U) (U [17, m], K [17, 17] the scaled
+    patch matrix): g = U y / sqrt(q) with y = (S + RIDGE diag(S))^-1 U^T e_1, S = U^T K U,
+    q = e_1^T U y.  For n <= m the exact row K_n^-1 e_1 / sqrt((K_n^-1)_11).  Returns (g, q, y)
+    (y = None for the exact row); g = e_1 / sqrt(K_11) when q <= 0 (no candidate has a self entry)."""
+    m = U.shape[1]
+    if n <= m:
+        e = np.zeros(n)
+        e[0] = 1.0
+        z = sla.solve(K[:n, :n], e, assume_a="pos")
+        g = np.zeros(U.shape[0])
+        g[:n] = z / math.sqrt(z[0])
+        return g, float(z[0]), None
+    S = U.T @ K @ U
+    y = np.linalg.solve(S + RIDGE * np.diag(np.diag(S)), U[0])
+    q = float(U[0] @ y)
+    if not q > 0.0:
+        g = np.zeros(U.shape[0])
+        g[0] = 1.0 / math.sqrt(K[0, 0])
+        return g, 0.0, y
+    return (U @ y) / math.sqrt(q), q, y
+
+
+def exact_q(Ks, Mk):
+    """q* = (K^-1)_11 of every sample (the exact row's g_self^2 at unit energy)."""
+    out = np.empty(len(Ks))
+    for s in range(len(Ks)):
+        n = int(Mk[s].sum())
+        e = np.zeros(n)
+        e[0] = 1.0
+        out[s] = sla.solve(Ks[s][:n, :n], e, assume_a="pos")[0]
+    return out
+
+
+def loss(theta, Z, Mk, Ks, qstar, mu, sig, n_in, m=1):
+    """Mean Kaporin-type gap (log q* - log q) of the rows the network's candidates give."""
+    o, _ = forward(theta, Z, n_in, m)
+    U = candidate_rows(o, mu, sig, Mk, m)
+    tot = 0.0
+    for s in range(len(Z)):
+        _, q, _ = combine(U[s], Ks[s], int(Mk[s].sum()))
+        tot += math.log(qstar[s]) - math.log(max(q, 1e-300))
+    return tot / len(Z)
+
+
+def grad(theta, Z, Mk, Ks, qstar, mu, sig, n_in, m=1):
+    """Analytic gradient of loss().  For one sample of more than m points, with S, y, q as in
+    combine, r = e_1 - K U y and the ridge's own dependence on U:
+    dq/dU = 2 r y^T - 2 RIDGE (K U) diag(y)^2, and d(-log q)/dU = -(dq/dU) / q (patches of n <= m
+    points take the exact row: no dependence on U); then backpropagation through the candidate
+    map and the three layers."""
+    W1, b1, W2, b2, W3, b3 = unpack(theta, n_in, m)
+    o, (a1, h1, a2, h2) = forward(theta, Z, n_in, m)
+    U = candidate_rows(o, mu, sig, Mk, m)
     S = len(Z)
-    d = sig * (o - T_std) * Mk
-    e = 2.0 * np.einsum("sij,sj->si", Ks, d) * sig * Mk / S
+    dU = np.zeros_like(U)
+    for s in range(S):
+        K = Ks[s]
+        _, q, y = combine(U[s], K, int(Mk[s].sum()))
+        if y is None or not q > 0.0:
+            continue
+        KU = K @ U[s]
+        r = -K @ (U[s] @ y)
+        r[0] += 1.0
+        dq = 2.0 * np.outer(r, y) - 2.0 * RIDGE * KU * (y * y)[None, :]
+        dU[s] = -dq / q / S
+    e = (dU * sig[None, :, None] * Mk[:, :, None]).transpose(0, 2, 1).reshape(S, m * N_OUT)
     gW3 = e.T @ h2
     gb3 = e.sum(0)
     d2 = (e @ W3) * (a2 > 0)
@@ -284,22 +356,18 @@ def standardise(T, Mk):
     return mu, sig
 
 
-def predict_rows(theta, Z, pat, mu, sig, n_in, Ks=None):
-    """Scale-free rows predicted by the network (self first).  With the scaled patch matrices
-    Ks, each row is rescaled to ghat^T K ghat = 1, the value the exact row has: this is
-    (G A G^T)_ii = 1, the diagonal of the preconditioned operator."""
-    o, _ = forward(theta, Z, n_in)
-    gh = mu + sig * o
-    gh[:, 0] = np.maximum(gh[:, 0], 0.1 * mu[0])
+def predict_rows(theta, Z, pat, mu, sig, n_in, Ks, m=1):
+    """Scale-free rows predicted by the network (self first): the combination of its m
+    candidate rows that the FSAI criterion selects in their span (combine), g^T K g = 1."""
+    o, _ = forward(theta, Z, n_in, m)
+    Mk = np.zeros((len(pat), N_OUT))
+    for i, nb in enumerate(pat):
+        Mk[i, :1 + len(nb)] = 1.0
+    U = candidate_rows(o, mu, sig, Mk, m)
     rows = []
     for i, nb in enumerate(pat):
-        r = gh[i, :1 + len(nb)].copy()
-        if Ks is not None:
-            m = len(r)
-            q = float(r @ Ks[i][:m, :m] @ r)
-            if q > 0:
-                r /= math.sqrt(q)
-        rows.append(r)
+        g, _, _ = combine(U[i], Ks[i], 1 + len(nb))
+        rows.append(g[:1 + len(nb)].copy())
     return rows
 
 

@@ -101,40 +101,102 @@ def test_exact_fsai_accelerates_cg():
     assert np.linalg.norm(x1 - x0) <= 1e-7 * np.linalg.norm(x0)
 
 
-def test_gradient_matches_central_differences():
-    X, delta, (wd, wk) = level(4.0, (2, 1), 2)
+def _training_data(nu, wend, L, lo, hi):
+    X, delta, (wd, wk) = level(nu, wend, L)
     pat = of.pattern(X, delta)
     rows = of.scale_free(of.exact_weights(X, delta, wd, wk, pat), delta, 2)
     T, Mk = of.target_matrix(rows, pat)
     mu, sig = of.standardise(T, Mk)
-    Ts = (T - mu) / sig * Mk
-    Ks = of.patch_matrices(X, delta, wd, wk, pat)[40:70]
-    Z = of.features(X, delta, pat)[40:70]
-    Ts, Mk = Ts[40:70], Mk[40:70]
+    Ks = of.patch_matrices(X, delta, wd, wk, pat)[lo:hi]
+    Z = of.features(X, delta, pat)[lo:hi]
+    Mk = Mk[lo:hi]
+    return Z, Mk, Ks, of.exact_q(Ks, Mk), mu, sig, [r for r in rows[lo:hi]]
+
+
+@pytest.mark.parametrize("m", [1, 3])
+def test_gradient_matches_central_differences(m):
+    Z, Mk, Ks, qs, mu, sig, _ = _training_data(4.0, (2, 1), 2, 40, 64)
     n_in = Z.shape[1]
-    th = of.init_params(n_in, 7)
-    g = of.grad(th, Z, Ts, Mk, Ks, sig, n_in)
+    th = of.init_params(n_in, 7, m)
+    g = of.grad(th, Z, Mk, Ks, qs, mu, sig, n_in, m)
     rng = np.random.default_rng(1)
     for idx in rng.choice(len(th), 60, replace=False):
         h = 1e-6 * max(1.0, abs(th[idx]))
         tp, tm = th.copy(), th.copy()
         tp[idx] += h
         tm[idx] -= h
-        fd = (of.loss(tp, Z, Ts, Mk, Ks, sig, n_in) - of.loss(tm, Z, Ts, Mk, Ks, sig, n_in)) / (2 * h)
+        fd = (of.loss(tp, Z, Mk, Ks, qs, mu, sig, n_in, m) - of.loss(tm, Z, Mk, Ks, qs, mu, sig, n_in, m)) / (2 * h)
         assert abs(fd - g[idx]) <= 1e-6 * max(1e-6, np.abs(g).max()), (idx, fd, g[idx])
 
 
-def test_loss_vanishes_at_the_exact_rows_and_is_positive_elsewhere():
-    """The energy loss is a squared norm in each patch matrix: zero exactly at the exact rows."""
+def test_exact_q_is_the_exact_rows_self_entry_squared():
+    """q* = (K^-1)_11 equals ghat*_self^2 of the unit-energy exact row (two independent routes:
+    a Cholesky solve of K, and the exact row computed from the unscaled kernel block)."""
+    _, Mk, Ks, qs, _, _, rows = _training_data(8.0, (2, 2), 2, 0, 80)
+    for s in range(1, 80):
+        assert abs(qs[s] - rows[s][0] ** 2) <= 1e-9 * qs[s]
+
+
+def test_combination_recovers_the_exact_row_in_its_span(monkeypatch):
+    """The FSAI criterion restricted to span(U) gives the exact row whenever it lies in the span
+    (for any scaling and mixing of the candidates), and the loss is then 0."""
+    _, Mk, Ks, qs, _, _, rows = _training_data(8.0, (2, 2), 2, 0, 80)
+    monkeypatch.setattr(of, "RIDGE", 0.0)
+    rng = np.random.default_rng(3)
+    for s in (10, 33, 71):
+        n = int(Mk[s].sum())
+        gs = np.zeros(17)
+        gs[:n] = rows[s]
+        U = np.stack([3.0 * gs] + [rng.standard_normal(17) * Mk[s] for _ in range(2)], axis=1)
+        U = U @ rng.standard_normal((3, 3))  # mixed: the span is what counts
+        assert n > 3
+        g, q, _ = of.combine(U, Ks[s], n)
+        assert np.max(np.abs(g - gs)) <= 1e-7 * np.max(np.abs(gs)), s
+        assert abs(math.log(qs[s]) - math.log(q)) <= 1e-8
+
+
+def test_combination_is_optimal_and_normalised_in_the_span():
+    """g = combine(U, K, n) has g_self = sqrt(q) > 0 and unit energy less the ridge's shift
+    (g^T K g = 1 - RIDGE sum_k S_kk y_k^2 / q), and no unit-energy vector of span(U) has a larger
+    self entry (the FSAI criterion); q <= q* (Kaporin's bound), so the loss is >= 0; with m = 1
+    it is the candidate rescaled to unit energy with a positive self entry; a patch of n <= m
+    points gets the exact row."""
+    _, Mk, Ks, qs, _, _, rows = _training_data(8.0, (2, 2), 2, 0, 80)
+    rng = np.random.default_rng(5)
+    tested = 0
+    for s in range(1, 80, 3):
+        K = Ks[s]
+        n = int(Mk[s].sum())
+        U = rng.standard_normal((17, 4)) * Mk[s][:, None]
+        g, q, y = of.combine(U, K, n)
+        assert g[0] > 0 and abs(g[0] ** 2 - q) <= 1e-9 * q
+        if n <= 4:
+            assert np.allclose(g[:n], rows[s], rtol=1e-9, atol=1e-12) and abs(q - qs[s]) <= 1e-9 * qs[s]
+            continue
+        tested += 1
+        S = U.T @ K @ U
+        assert abs(g @ K @ g - (1.0 - of.RIDGE * np.sum(np.diag(S) * y * y) / q)) <= 1e-9
+        assert q <= qs[s] * (1 + 1e-12)
+        for _ in range(20):
+            v = U @ rng.standard_normal(4)
+            v /= math.sqrt(v @ K @ v)
+            assert abs(v[0]) <= g[0] * (1 + 1e-5)  # the 1e-6 ridge moves the optimum slightly
+        u = U[:, :1]
+        g1, _, _ = of.combine(u, K, n)
+        ref = np.sign(u[0, 0]) * u[:, 0] / math.sqrt(u[:, 0] @ K @ u[:, 0])
+        np.testing.assert_allclose(g1, ref, rtol=1e-5, atol=1e-12)
+    assert tested >= 15
+
+
+def test_loss_is_the_kaporin_gap_and_vanishes_only_at_the_span():
+    """loss >= 0 for any parameters; the patch matrices are the oracle's kernel blocks scaled by
+    delta^d."""
     X, delta, (wd, wk) = level(8.0, (2, 2), 2)
     pat = of.pattern(X, delta)
-    rows = of.scale_free(of.exact_weights(X, delta, wd, wk, pat), delta, 2)
-    T, Mk = of.target_matrix(rows, pat)
-    Ks = of.patch_matrices(X, delta, wd, wk, pat)
-    for i in (5, 50, 200):
-        e = np.random.default_rng(i).standard_normal(17) * Mk[i]
-        assert e @ Ks[i] @ e > 0
-    # the patch matrices are the oracle's kernel blocks scaled by delta^d
+    Z, Mk, Ks, qs, mu, sig, _ = _training_data(8.0, (2, 2), 2, 0, len(pat))
+    for m, seed in ((1, 1), (4, 2)):
+        th = of.init_params(Z.shape[1], seed, m)
+        assert of.loss(th, Z, Mk, Ks, qs, mu, sig, Z.shape[1], m) > 0.0
     P = np.concatenate([[60], pat[60]])
     np.testing.assert_allclose(Ks[60][:len(P), :len(P)],
                                om.kernel_dense(X[P], X[P], delta, wd, wk) * delta ** 2, rtol=1e-14)
@@ -187,8 +249,8 @@ def test_features_are_invariant_under_rotations_and_reflections(d):
 
 
 def test_predicted_rows_are_normalised_like_the_exact_rows():
-    """Exact rows satisfy ghat^T K ghat = 1 ((G A G^T)_ii = 1); predicted rows are rescaled to it,
-    and rescaling an exact row leaves it unchanged."""
+    """Exact rows satisfy ghat^T K ghat = 1 ((G A G^T)_ii = 1); predicted rows (any m) do too,
+    with a positive self entry, and a wider candidate span never does worse on the gap."""
     w = inputs.halton_hierarchy(L=3, nu=4.0, wendland=(2, 1), n_gauss=4)
     X, delta = w.levels[2], w.nu * w.h[2]
     pat = of.pattern(X, delta)
@@ -197,14 +259,23 @@ def test_predicted_rows_are_normalised_like_the_exact_rows():
     for i, r in enumerate(rows):
         m = len(r)
         assert abs(r @ Ks[i][:m, :m] @ r - 1.0) <= 1e-9
-    th = of.init_params(32, 3)
     Z = of.features(X, delta, pat)
     T, Mk = of.target_matrix(rows, pat)
     mu, sig = of.standardise(T, Mk)
-    pr = of.predict_rows(th, Z, pat, mu, sig, 32, Ks)
-    for i, r in enumerate(pr):
-        m = len(r)
-        assert abs(r @ Ks[i][:m, :m] @ r - 1.0) <= 1e-12
-    # the rescaling is not a no-op on untrained outputs
-    raw = of.predict_rows(th, Z, pat, mu, sig, 32)
-    assert not all(np.allclose(a, b) for a, b in zip(raw, pr))
+    for m in (1, 4):
+        th = of.init_params(32, 3, m)
+        pr = of.predict_rows(th, Z, pat, mu, sig, 32, Ks, m)
+        for i, r in enumerate(pr):
+            n = len(r)
+            # unit energy less the 1e-6 ridge's shift rho |y|^2 / q (pinned exactly above; largest
+            # where m exceeds the patch size and the candidates are dependent)
+            e = r @ Ks[i][:n, :n] @ r
+            assert 1.0 - 1e-3 <= e <= 1.0 + 1e-12 and r[0] > 0
+    # candidates [u, v]: the gap of their span is at most that of u alone
+    th1 = of.init_params(32, 3, 1)
+    o1, _ = of.forward(th1, Z, 32, 1)
+    o2 = np.concatenate([o1, np.random.default_rng(0).standard_normal(o1.shape)], axis=1)
+    U1, U2 = of.candidate_rows(o1, mu, sig, Mk, 1), of.candidate_rows(o2, mu, sig, Mk, 2)
+    for i in range(1, len(pat), 13):
+        n = 1 + len(pat[i])
+        assert of.combine(U2[i], Ks[i], n)[1] >= of.combine(U1[i], Ks[i], n)[1] * (1 - 1e-5)

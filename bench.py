@@ -316,13 +316,14 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def train_network(wl, epochs):
+    def train_network(wl, epochs, **kw):
         """Train the network once on levels 1-4 of wl, outside every timed region."""
         Ht = ms.Hierarchy(wl.d, wl.n_per_level, torch.from_numpy(wl.points).cuda(), wl.h,
                           precision=ms.MS_PREC_MIXED, precond=ms.MS_PRECOND_LEARNED, wendland_d=wl.wendland_d,
                           wendland_k=wl.wendland_k, nu=wl.nu)
-        st = Ht.train_precond([0, 1, 2, 3], epochs=epochs)
+        st = Ht.train_precond([0, 1, 2, 3], epochs=epochs, **kw)
         p = Ht.precond_params()
+        st["n_basis"] = Ht.info()["pc_basis"]
         Ht.close()
         return p, st
 
@@ -439,6 +440,23 @@ def run_ours(args):
                 "exact_fsai_approximant_rel_diff": rel(rex[-1]["s"], r64[-1]["s"]),
                 "queries": int(Q.shape[0])}
             del r64, rex
+            # the same learned step with the lower blocks matrix-free (no B assembled; the fit's
+            # Jacobi updates recompute its entries in double-float)
+            out["learned_pcg_lower_matrix_free"] = summary(arm(args.arm_steps, *HEAD, params=params,
+                                                               lower_op=ms.MS_OP_MATRIX_FREE))
+            # the network's part: candidate rows m (the row is the FSAI combination in their span;
+            # m = 1 is a single predicted row, m = 17 would be the exact row), one network each
+            sweep = {}
+            for m in (1, 4, 8):
+                pm, tm = train_network(w, args.train_epochs, n_basis=m)
+                rm = arm(1, *HEAD, params=pm)
+                sweep[str(m)] = {"ms_per_step": rm[-1]["total"], "fit_ms": rm[-1]["stats"]["fit_ms"],
+                                 "cg_iterations": rm[-1]["stats"]["cg_iterations"], "loss_last": tm["loss_last"],
+                                 "train_ms": tm["train_ms"]}
+            sweep[str(train["n_basis"])] = {"ms_per_step": ms_step, "fit_ms": out["learned_pcg"]["fit_ms"],
+                                            "cg_iterations": out["learned_pcg"]["cg_iterations"],
+                                            "loss_last": train["loss_last"], "train_ms": train["train_ms"]}
+            out["candidate_rows_sweep"] = sweep
 
         # ---- side block: delta_j = 4 h_j, phi_{2,1} (well-conditioned levels)
         if not args.no_side:
@@ -479,7 +497,9 @@ def run_ours(args):
             for name, op, nnz, vb in [("A64", ms.MS_APPLY_A64, info["nnz_A"], 8),
                                       ("A32", ms.MS_APPLY_A32, info["nnz_A"], 4),
                                       ("AMF32", ms.MS_APPLY_AMF32, info["nnz_A"], 0),
-                                      ("B64", ms.MS_APPLY_B64, info["nnz_B"], 8)]:
+                                      ("B64", ms.MS_APPLY_B64, info["nnz_B"], 8),
+                                      ("BMF32", ms.MS_APPLY_BMF32, info["nnz_B"], -1),
+                                      ("BMFDF", ms.MS_APPLY_BMFDF, info["nnz_B"], -1)]:
                 for _ in range(3):
                     H.apply(op, x, y, sorted_order=True)
                 ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -490,7 +510,12 @@ def run_ours(args):
                 ev[1].record(stream)
                 torch.cuda.synchronize()
                 t_ms = ev[0].elapsed_time(ev[1]) / reps
-                if vb:
+                if vb < 0:
+                    # matrix-free lower blocks: entries recomputed (FP32, or double-float like the
+                    # stored entries of a MIXED build); the rate of B's entries
+                    mv[name] = {"ms": t_ms, "stored_entries_per_s": nnz / (t_ms * 1e-3),
+                                "csr_b64_equivalent_GBps": nnz * 12.0 / (t_ms * 1e-3) / 1e9}
+                elif vb:
                     # matrix (col + val) + row offsets + y write + one read of x (FP32 ops also convert x)
                     b = nnz * (4 + vb) + N * (8 + 8 + 8) + (N * 12 if vb == 4 else 0)
                     mv[name] = {"ms": t_ms, "GBps": b / (t_ms * 1e-3) / 1e9,
@@ -607,14 +632,27 @@ def run_ours(args):
         if not args.no_paper:
             paper_s = {7: 0.974, 8: 1.485, 9: 4.479, 10: 20.111, 11: 92.642}
             rows = []
+            # Theorem 2 / Corollary 3: the RMS error of f_L against the Franke function on a 256^2
+            # grid falls geometrically with L
+            Qp = torch.from_numpy(Qh).cuda()
+            fq = torch.from_numpy(inputs.franke(Qh)).cuda()
+            conv = []
+            for Lp in range(1, 7):
+                wp = inputs.franke_grid_hierarchy(Lp)
+                rp = step(ms.MS_PREC_FP64, wl=wp, pts_=torch.from_numpy(wp.points).cuda(),
+                          f_=torch.from_numpy(wp.f).cuda(), q=Qp)
+                conv.append({"levels": Lp, "points": int(wp.N),
+                             "rms_error": float(torch.sqrt(torch.mean((rp["s"] - fq) ** 2)))})
             for Lp in (7, 8, 9, 10, 11):
                 wp = inputs.franke_grid_hierarchy(Lp)
                 pp, fp = torch.from_numpy(wp.points).cuda(), torch.from_numpy(wp.f).cuda()
                 best = None
                 for _ in range(2):
-                    rp = step(ms.MS_PREC_FP64, wl=wp, pts_=pp, f_=fp)
+                    rp = step(ms.MS_PREC_FP64, wl=wp, pts_=pp, f_=fp, q=Qp)
                     if best is None or rp["total"] < best["total"]:
                         best = rp
+                conv.append({"levels": Lp, "points": int(wp.N),
+                             "rms_error": float(torch.sqrt(torch.mean((best["s"] - fq) ** 2)))})
                 rows.append({"levels": Lp, "points": int(wp.N), "step_ms": best["total"],
                              "fit_ms": best["stats"]["fit_ms"], "build_ms": best["info"]["build_ms"],
                              "cg_iterations": best["stats"]["cg_iterations"],
@@ -622,6 +660,9 @@ def run_ours(args):
                              "paper_over_fit": paper_s[Lp] * 1e3 / best["stats"]["fit_ms"]})
                 del pp, fp
             out["paper_grids_fp64"] = rows
+            for a, b in zip(conv, conv[1:]):
+                b["ratio_to_previous"] = b["rms_error"] / a["rms_error"]
+            out["convergence_rate_franke"] = conv
 
         # ---- the 3-D configuration (uniform random points, 6 levels, 4.68M points, phi_{3,1},
         #      delta = 3h): FP64 CSR, MIXED CSR, MIXED with the matrix-free FP32 inner mat-vec, and
@@ -690,6 +731,7 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": workload_label(args.levels),
                            "path": "learned-PCG MIXED: FP32 CSR mat-vecs, FP64 dots/refinement, learned FSAI",
+                           "candidate_rows": train["n_basis"],
                            "rel_tol": REL_TOL, "queries": args.query_side ** 2,
                            "step": "build_hierarchy + precond rows + fit + evaluate, inputs resident in HBM",
                            "l2": "flushed between steps (256 MB write); CSR working set >> L2",

@@ -49,7 +49,7 @@ extern "C" {
 #endif
 
 #define MS_MAX_LEVELS 32
-#define MS_ABI_VERSION 1
+#define MS_ABI_VERSION 2
 
 typedef struct ms_hierarchy ms_hierarchy;
 
@@ -95,7 +95,9 @@ typedef struct ms_opts {
     int precision;       /* MS_PREC_* */
     int precond;         /* MS_PRECOND_* */
     int max_iters;       /* cap on CG iterations per level and solve; 0 = 20000 */
-    int jacobi_sweeps;   /* Jacobi sweeps on T'; 0 = L-1 (exact from beta_0 = f, Theorem 9) */
+    int jacobi_sweeps;   /* Jacobi sweeps on T'; 0 = L-1 (exact from beta_0 = f, Theorem 9);
+                            -1 = none: the fit returns alpha = D_L^{-1} f, the block-diagonal
+                            solve of eq. split alone (per-level CG on every level at once) */
     double inter_tol;    /* relative tolerance of the non-final (intermediate) level solves
                             inside the Jacobi sweeps.  0 = 1: a non-final level keeps its
                             previous iterate (no CG iterations until its beta is final; the
@@ -111,7 +113,17 @@ typedef struct ms_opts {
                             least 4096 rows with 1, 2, 4, 8, 16 and 32 lanes per row and keep
                             the fastest (cached per process by level shape); 0 = rule
                             (about 16 entries per lane).  threads_per_row > 0 overrides both. */
-    int reserved[5];
+    int lower_op;        /* operator of the strictly lower blocks B_kj in the fit's Jacobi updates:
+                            MS_OP_CSR (default): B stored as CSR by the build (FP64 values);
+                            MS_OP_MATRIX_FREE (MIXED only): the build stores no B and every
+                            update recomputes B's entries in double-float arithmetic (the values a
+                            MIXED build would store, about 1e-14 relative) and sums them in
+                            double-float.  Under the default schedule each block is read once per
+                            fit, so a hierarchy that is fitted once saves B's assembly and its
+                            12 bytes per entry; one fitted many times is faster with CSR.  Needs
+                            the default schedule (inter_tol 0 or >= 1); MS_APPLY_B64/B32 are then
+                            unavailable. */
+    int reserved[4];
 } ms_opts;
 
 /* Per-fit statistics (all levels 0-based, coarse to fine). */
@@ -150,6 +162,7 @@ typedef struct ms_info {
     int64_t device_bytes;/* device memory held by the handle */
     double build_ms;     /* device time of the last build (CUDA events) */
     int32_t tpr_A[MS_MAX_LEVELS]; /* CSR lanes per row of A_l in the solve (as of the last fit) */
+    int32_t pc_basis;    /* candidate rows per point of the handle's network (ms_train_opts.n_basis) */
 } ms_info;
 
 /* Fill *opts with defaults: phi_{3,1}, nu = 4, CSR, FP64, no preconditioner. */
@@ -332,15 +345,22 @@ enum {
     MS_APPLY_AMF32 = 2, /* y = D_L x   (matrix-free FP32: entries recomputed)    */
     MS_APPLY_B64 = 3,   /* y = (T_L - D_L) x  (all B_kj, k > j, FP64 CSR)        eq. bigt */
     MS_APPLY_B32 = 4,   /* y = (T_L - D_L) x  (FP32 CSR)                          */
-    MS_APPLY_BMF32 = 5  /* y = (T_L - D_L) x  (matrix-free FP32)                  */
+    MS_APPLY_BMF32 = 5, /* y = (T_L - D_L) x  (matrix-free FP32 entries and sums)  */
+    MS_APPLY_BMFDF = 6  /* y = (T_L - D_L) x  (matrix-free double-float entries and
+                           sums, the fit's lower_op = MS_OP_MATRIX_FREE; MIXED builds) */
 };
 /*
  * y = op x for one of the MS_APPLY_* operators.  x_dev, y_dev: DEVICE float64 [N].
  * sorted_order = 0: x and y are in input order (the library permutes);
  * sorted_order = 1: x and y are in the library's internal (cell-sorted) order,
- * see ms_get_permutation.  FP32 operators round x to FP32 and widen y to FP64.
- * Errors: MS_ERR_ARG (unknown op, or an FP32 CSR op on a handle built without
- * FP32 values), MS_ERR_CUDA.  Enqueued on `stream`.
+ * see ms_get_permutation.  FP32 operators round x to FP32 and widen y to FP64;
+ * MS_APPLY_BMFDF splits x into double-float parts.  The matrix-free lower operators
+ * (the paper's McV, Section 5.3) give row y_s of level k the sum over the levels j < k
+ * of the entries Phi_{delta_j}(x_s - x_p) x_p of the level-j points p within delta_j,
+ * found through level j's cell grid.
+ * Errors: MS_ERR_ARG (unknown op, an FP32 CSR op on a handle built without
+ * FP32 values, a CSR lower op on a handle built with lower_op = MS_OP_MATRIX_FREE,
+ * MS_APPLY_BMFDF on an FP64 build), MS_ERR_CUDA.  Enqueued on `stream`.
  */
 ms_status ms_apply_dev(ms_hierarchy* h, int op, const double* x_dev, double* y_dev,
                        int sorted_order, void* stream);
@@ -353,12 +373,20 @@ ms_status ms_hierarchy_info(const ms_hierarchy* h, ms_info* info);
 
 /* ---------------------------------------------------------------- learned preconditioner
  * The network maps the delta-scaled offsets (x_j - x_i)/delta_l of a point's pattern
- * neighbours (16 d inputs, zero-padded) through ReLU layers of width 64 to 17 outputs,
- * the standardised scale-free row ghat_i = delta_l^{-d/2} g_i (self first).  Because
- * A_P = delta^-d K(offsets / delta) (eq. kernelscaling), ghat does not depend on the
- * level, so a network trained on coarse levels serves every level.  Inference uses
- * BF16-valued weights with FP32 accumulation; training is Adam on FP32 master weights
- * whose forward and backward passes use the BF16-rounded copies. */
+ * neighbours (16 d inputs, zero-padded, in the patch's canonical frame) through ReLU layers
+ * of width 64 to 17 m outputs o_1..o_m: m candidate scale-free rows (self first, zero past
+ * the patch), u_1 = mu + sigma o_1 (per-entry mean and deviation of the training targets)
+ * and u_k = sigma o_k for k > 1.  The row is the factorised sparse approximate inverse
+ * within their span: with U = [u_1..u_m] and K = phi(|z_a - z_b|) the scaled patch matrix,
+ * ghat = U y / sqrt(q), y = (S + 1e-6 diag(S))^-1 U^T e_1, S = U^T K U, q = e_1^T U y -- the
+ * minimiser of g^T K g with g_self = 1 in the span, normalised to g^T K g = 1 (the exact
+ * row's value) with g_self = sqrt(q) > 0, and the exact row whenever the span holds it; a
+ * patch of n <= m points takes the exact row.  Because A_P = delta^-d K(offsets / delta)
+ * (eq. kernelscaling), ghat = delta_l^{-d/2} g does not depend on the level, so a network
+ * trained on coarse levels serves every level.  Training minimises the mean gap
+ * log q* - log q >= 0 to the exact row (q* = (K^-1)_11).  Inference uses BF16-valued
+ * weights with FP32 accumulation and an FP32 combination; training is Adam on FP32 master
+ * weights whose forward and backward passes use the BF16-rounded copies. */
 typedef struct ms_train_opts {
     int epochs;          /* passes over the training patches (default 100) */
     int batch;           /* samples per Adam step, a multiple of 64 (default 512) */
@@ -374,13 +402,14 @@ typedef struct ms_train_opts {
                             p = i + 1 + min(floor(u (n - i)), n - i - 1), u = the SplitMix64
                             uniform draw (top 53 bits / 2^53) of seed ^ 0x6175676D656E74 with
                             counter r N + (global input index of i), N = the hierarchy's points */
-    int reserved[5];
+    int n_basis;         /* candidate rows m the network predicts per point, 1..16 (0 = default 16) */
+    int reserved[4];
 } ms_train_opts;
 
 typedef struct ms_train_stats {
     int64_t samples;     /* training patches: (1 + augment) x the points of the chosen levels */
     int64_t steps;       /* Adam steps taken */
-    double loss_first;   /* mean squared error of the first and of the last step's batch */
+    double loss_first;   /* mean gap log q* - log q of the first and of the last step's batch */
     double loss_last;
     double train_ms;     /* device time of the training loop */
     int32_t n_params;
@@ -397,9 +426,11 @@ ms_status ms_train_precond(ms_hierarchy* h, const int* levels, int n_levels, con
 
 /* Export (set = 0) or import (set = 1) the network: params is host float[n] with
  * n = n_weights + 34: the FP32 weights in the order W1 [64][16d], b1 [64], W2 [64][64],
- * b2 [64], W3 [17][64], b3 [17] (row-major), then the 17 output means and 17 output
- * standard deviations.  Importing marks the network trained.  Errors: MS_ERR_ARG (n),
- * MS_ERR_STATE (export without weights). */
+ * b2 [64], W3 [17m][64], b3 [17m] (row-major; output 17 k + a is entry a of candidate k),
+ * then the 17 per-entry means and 17 standard deviations.  n_weights = 1024 d + 4224 +
+ * 1105 m; importing takes m from n (1..16) and marks the network trained; exporting needs
+ * n for the handle's current m (ms_info.pc_basis).  Errors: MS_ERR_ARG (n), MS_ERR_STATE
+ * (export without weights). */
 ms_status ms_precond_params(ms_hierarchy* h, float* params, int64_t n, int set);
 
 /* Inspection of the preconditioner's building blocks (host outputs, input order). */

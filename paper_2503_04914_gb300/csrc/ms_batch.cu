@@ -387,7 +387,7 @@ ms_status ms_batch_plan_stats_impl(ms_batch_plan* p, cudaStream_t st, ms_fit_sta
         s = ms_fit_stats{};
         const ms_hierarchy* h = p->hs[i];
         s.L = h->L;
-        s.sweeps = h->opts.jacobi_sweeps > 0 ? h->opts.jacobi_sweeps : std::max(h->L - 1, 0);
+        s.sweeps = ms_sweeps_of(h);
         for (int l = 0; l < h->L; ++l) {
             s.cg_iterations[l] = b.iters[l];
             s.refinements[l] = b.refines[l];

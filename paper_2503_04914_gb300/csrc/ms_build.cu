@@ -17,6 +17,7 @@
 #include "ms_internal.cuh"
 #include "ms_matfree.cuh"
 #include "ms_scan.cuh"
+#include "ms_geom.cuh"
 
 namespace {
 
@@ -135,140 +136,6 @@ __global__ void k_mf_coords(HierView v, float* W, float* Wlo, int32_t* cellid) {
 // (fma-accumulated r^2 < delta_j^2), so the pattern is exactly the FP64 one.
 // The FP64 values are computed for the entries only (FP64 is scarce on this GPU).
 
-// Position of y relative to level j's grid: cell c[a] and the offset from that
-// cell's corner in units of delta_j.  Lane a < d computes axis a.
-struct Frame {
-    int c[3];
-    float fr[3];
-    float frlo[3];  // fr + frlo: the offset to about 48 bits (double-float entries)
-};
-
-struct Pt {
-    double x, y, z;
-};
-
-__device__ __forceinline__ Pt point_at(const HierView& v, int64_t s) {
-    Pt q{v.X[s], 0.0, 0.0};
-    if (v.d >= 2) q.y = v.X[v.N + s];
-    if (v.d >= 3) q.z = v.X[2 * v.N + s];
-    return q;
-}
-
-// |x_p - y|^2 in FP64, accumulated axis by axis with fma
-__device__ __forceinline__ double dist2(const HierView& v, int64_t p, const Pt& y) {
-    double u = v.X[p] - y.x;
-    double r2 = fma(u, u, 0.0);
-    if (v.d >= 2) { u = v.X[v.N + p] - y.y; r2 = fma(u, u, r2); }
-    if (v.d >= 3) { u = v.X[2 * v.N + p] - y.z; r2 = fma(u, u, r2); }
-    return r2;
-}
-
-// Frame of y in level j's grid, all axes (FP64 set-up; k_frames calls it once per (row, level)).
-__device__ __forceinline__ Frame frame_of(const HierView& v, int j, const Pt& y) {
-    const LevelGrid& g = v.grid[j];
-    Frame f{};
-    const double ya[3] = {y.x, y.y, y.z};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (a < v.d) {
-            f.c[a] = cell_coord(g, a, ya[a]);
-            const double t = (ya[a] - (g.lo[a] + (double)f.c[a] * g.cell)) * v.inv_delta[j];
-            f.fr[a] = (float)t;
-            f.frlo[a] = (float)(t - (double)f.fr[a]);
-        }
-    }
-    return f;
-}
-
-// Lane `src`'s frame (src may differ between lanes; every lane must take part).
-__device__ __forceinline__ Frame frame_from(const Frame& mine, int src) {
-    Frame f;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        f.c[a] = __shfl_sync(0xffffffffu, mine.c[a], src);
-        f.fr[a] = __shfl_sync(0xffffffffu, mine.fr[a], src);
-        f.frlo[a] = __shfl_sync(0xffffffffu, mine.frlo[a], src);
-    }
-    return f;
-}
-
-// ---------------------------------------------------------------- double-float entries
-//
-// With precision = MIXED the stored FP64 entries are evaluated in double-float arithmetic
-// (ms_ff.cuh) from the points' cell-relative offsets W + Wlo, exact to about 48 bits:
-// relative errors near 1e-14 instead of 1e-16, far inside what the mixed path promises
-// (its inner solves run in FP32), at about 3 FP64 instructions per entry (the final
-// conversion) instead of about 30.
-
-// Per-level constants (cell size / delta, delta^-d) and the Wendland polynomial's
-// coefficients as double-floats, converted once on the host: a conversion from FP64 costs
-// FP64 instructions, which is what this path avoids.
-struct FFLevels {
-    ff cod[MS_MAXL];
-    ff ds[MS_MAXL];
-    ff c[4];
-};
-
-// phi(r) for the Wendland closed form w in double-float; 0 for r >= 1.  E, K: the exponent
-// and the degree as compile-time constants (0: read them from w).
-template <int E, int K>
-__device__ __forceinline__ ff ff_wendland(const WendlandPoly& w, const ff* c, ff r) {
-    if (!(r.hi < 1.0f || (r.hi == 1.0f && r.lo < 0.0f))) return {0.0f, 0.0f};
-    const ff s = ff_add({1.0f, 0.0f}, ff_neg(r));
-    const ff s2 = ff_sqr(s), s4 = ff_sqr(s2);
-    const int e = E > 0 ? E : w.e;
-    ff pw;
-    if (e == 4) pw = s4;
-    else if (e == 6) pw = ff_mul(s4, s2);
-    else if (e == 8) pw = ff_sqr(s4);
-    else {
-        pw = {1.0f, 0.0f};
-        for (int i = 0; i < e; ++i) pw = ff_mul(pw, s);
-    }
-    const int k = E > 0 ? K : w.k;
-    ff p = c[k];
-#pragma unroll
-    for (int i = 3; i >= 1; --i)
-        if (i <= k) p = ff_add(ff_mul(p, r), c[i - 1]);
-    return ff_mul(pw, p);
-}
-
-// delta_j^-d phi(|x_p - y| / delta_j) for point p of level j (cell cp, offsets W + Wlo) and
-// y's frame f in level j's grid: the scaled offset on axis a is
-// (cp_a - c_a) cod + (W_a + Wlo_a) - (fr_a + frlo_a).  cod_exact: cod is a float, so the cell
-// term is an exact FP32 product.
-template <int E, int K>
-__device__ __forceinline__ ff ff_entry(const HierView& v, const float* __restrict__ W,
-                                           const float* __restrict__ Wlo, const int32_t* __restrict__ cellid,
-                                           const FFLevels& ffl, int j, int32_t p, const Frame& f) {
-    int cp[3];
-    demorton(v.d, (uint32_t)__ldg(cellid + p), cp);
-    const bool cod_exact = ffl.cod[j].lo == 0.0f;
-    ff r2 = {0.0f, 0.0f};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (a < v.d) {
-            const ff w = {__ldg(W + a * v.N + p), __ldg(Wlo + a * v.N + p)};
-            const float dc = small_int_to_float(cp[a] - f.c[a]);
-            ff t;
-            if (cod_exact) {
-                t = ff_sum3(__fmul_rn(dc, ffl.cod[j].hi), w, {f.fr[a], f.frlo[a]});
-            } else {
-                t = ff_add(ff_add(ff_mul(ffl.cod[j], {dc, 0.0f}), w), ff_neg({f.fr[a], f.frlo[a]}));
-            }
-            r2 = a == 0 ? ff_sqr(t) : ff_add(r2, ff_sqr(t));
-        }
-    }
-    return ff_mul(ffl.ds[j], ff_wendland<E, K>(v.w, ffl.c, ff_sqrt(r2)));
-}
-
-// Offset (units of delta) of a neighbour cell displaced by `dc` cells, seen from a point at
-// fractional offset fr in its own cell; both CSR kernels take it from here so that they
-// make the same decisions.
-__device__ __forceinline__ float cell_offset(int dc, float cod, float fr) {
-    return __fsub_rn(__fmul_rn(small_int_to_float(dc), cod), fr);
-}
-
 // |x_p - y| < delta_j for candidate p in the neighbour cell with offsets (c0, c1, c2): FP32
 // test on the cell-relative coordinates W (units of delta_j), the FP64 distance inside a band
 // of 1e-4 around the support boundary.  Rounded operation by operation (no contraction), so
@@ -340,7 +207,7 @@ __device__ __forceinline__ bool pair_cell(const HierView& v, int j, int q, const
 __global__ void __launch_bounds__(kCsrBS, 4) k_csr_count(const __grid_constant__ HierView v, const float* __restrict__ W,
                                                        const __grid_constant__ PairLayout pl,
                                                        const Frame* __restrict__ F, int32_t* cntA, int32_t* cntB,
-                                                       int32_t* pcnt) {
+                                                       int32_t* pcnt, int onlyA) {
     const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (s >= v.N) return;  // warp-uniform
@@ -353,7 +220,8 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_count(const __grid_constant__
     const int pairs = (k + 1) * nc;
     int32_t* pc = pcnt + pl.base[k] + (s - v.off[k]) * pairs;
     int32_t na = 0, nb = 0;
-    for (int t0 = 0; t0 < pairs; t0 += 32) {
+    // onlyA: the pairs of level k alone (the lower blocks are not stored)
+    for (int t0 = onlyA ? k * nc : 0; t0 < pairs; t0 += 32) {
         const int t = t0 + lane;
         const int j = min(t / nc, k);  // lanes past the last pair read a valid frame and skip
         const Frame f = frame_from(mine, j);
@@ -395,7 +263,8 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_fill(const __grid_constant__ 
                                                       const Frame* __restrict__ F,
                                                       const int32_t* __restrict__ pcnt, const int64_t* rpA,
                                                       int32_t* colA, double* valA, float* valA32, const int64_t* rpB,
-                                                      int32_t* colB, double* valB, float* valB32, int32_t* Bseg) {
+                                                      int32_t* colB, double* valB, float* valB32, int32_t* Bseg,
+                                                      int onlyA) {
     const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (s >= v.N) return;  // warp-uniform
@@ -412,7 +281,7 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_fill(const __grid_constant__ 
     const int32_t* pc = pcnt + pl.base[k] + (s - v.off[k]) * pairs;
     const int64_t a0 = rpA[s], b0 = rpB[s];
     int64_t pa = a0, pb = b0;
-    for (int t0 = 0; t0 < pairs; t0 += 32) {
+    for (int t0 = onlyA ? k * nc : 0; t0 < pairs; t0 += 32) {
         const int t = t0 + lane;
         const bool ok = t < pairs;
         const int j = min(t / nc, k);
@@ -431,7 +300,7 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_fill(const __grid_constant__ 
         const int32_t ta = __shfl_sync(0xffffffffu, ia, 31), tb = __shfl_sync(0xffffffffu, ib, 31);
         const int q = t - j * nc;
         // first pair of a column level j < k: its segment of the B row starts here
-        if (ok && !isA && q == 0) Bseg[(int64_t)j * v.N + s] = (int32_t)(pb + ib - n - b0);
+        if (ok && !isA && q == 0 && Bseg) Bseg[(int64_t)j * v.N + s] = (int32_t)(pb + ib - n - b0);
         if (ok && n > 0) {
             int32_t ps = 0, pe = 0;
             float o0 = 0.f, o1 = 0.f, o2 = 0.f;
@@ -445,7 +314,7 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_fill(const __grid_constant__ 
         pa += ta;
         pb += tb;
     }
-    if (lane == 0) Bseg[(int64_t)k * v.N + s] = (int32_t)(pb - b0);
+    if (lane == 0 && Bseg) Bseg[(int64_t)k * v.N + s] = (int32_t)(pb - b0);
     __syncwarp();  // the columns written by the other lanes are read below
     if (FF) {
         const Frame fk = frame_from(mine, k);
@@ -655,9 +524,22 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
         pcnt = pc;
     }
     Frame* frames = nullptr;
-    MS_TRY(talloc((void**)&frames, sizeof(Frame) * pl.fbase[L]));
+    // lower_op = MATRIX_FREE: the handle keeps the frames (36 bytes per (row, level) pair, instead
+    // of B's 12 bytes per entry) for the fit's lower-block updates
+    const bool keep_frames = h->opts.lower_op == MS_OP_MATRIX_FREE;
+    if (keep_frames) {
+        MS_TRY(ms_alloc(h, (void**)&frames, sizeof(Frame) * pl.fbase[L]));
+        h->frames = frames;
+        for (int l = 0; l <= L; ++l) h->frame_base[l] = pl.fbase[l];
+    } else {
+        MS_TRY(talloc((void**)&frames, sizeof(Frame) * pl.fbase[L]));
+    }
     k_frames<<<nblk(pl.fbase[L], 256), 256, 0, st>>>(v, pl, frames); ms_count_launch();
-    k_csr_count<<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, pl, frames, cntA, cntB, pcnt); ms_count_launch();
+    // lower_op = MATRIX_FREE: the fit recomputes B's entries, the build stores A only
+    const int onlyA = h->opts.lower_op == MS_OP_MATRIX_FREE ? 1 : 0;
+    if (onlyA) MS_CUDA(cudaMemsetAsync(cntB, 0, sizeof(int32_t) * N, st));
+    k_csr_count<<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, pl, frames, cntA, cntB, pcnt, onlyA);
+    ms_count_launch();
     exclusive_scan<int32_t, int64_t>(cntA, N, h->A.rp, (int64_t*)tile, st);
     exclusive_scan<int32_t, int64_t>(cntB, N, h->B.rp, (int64_t*)tile, st);
     MS_CUDA(cudaGetLastError());
@@ -676,7 +558,7 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
     MS_TRY(ms_alloc(h, (void**)&h->B.v64, sizeof(double) * h->B.nnz));
     // the fit updates beta with FP64 B values only; FP32 B values serve MS_APPLY_B32 on request
     if (h->opts.lower_fp32) MS_TRY(ms_alloc(h, (void**)&h->B.v32, sizeof(float) * h->B.nnz));
-    MS_TRY(ms_alloc(h, (void**)&h->Bseg, sizeof(int32_t) * (size_t)L * N));
+    if (!onlyA) MS_TRY(ms_alloc(h, (void**)&h->Bseg, sizeof(int32_t) * (size_t)L * N));
     FFLevels ffl{};
     for (int l = 0; l < L; ++l) {
         ffl.cod[l] = ff_from_double(v.grid[l].cell / v.delta[l]);
@@ -692,13 +574,16 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
                            : k_csr_fill<false, 0, 0>;
         fill<<<nblk(N * 32, kCsrBS), kCsrBS, 0, st>>>(v, h->W, Wlo, h->cellid, ffl, pl, frames, pcnt, h->A.rp, h->A.col,
                                                       h->A.v64, h->A.v32, h->B.rp, h->B.col, h->B.v64, h->B.v32,
-                                                      h->Bseg);
+                                                      h->Bseg, onlyA);
     }
     ms_count_launch();
     unsigned long long* blk;
     MS_TRY(talloc((void**)&blk, sizeof(unsigned long long) * L * L));
     MS_CUDA(cudaMemsetAsync(blk, 0, sizeof(unsigned long long) * L * L, st));
-    k_block_nnz<<<nblk(N, 256), 256, 0, st>>>(h->Bseg, h->B.rp, v, blk); ms_count_launch();
+    if (!onlyA) {
+        k_block_nnz<<<nblk(N, 256), 256, 0, st>>>(h->Bseg, h->B.rp, v, blk);
+        ms_count_launch();
+    }
     MS_CUDA(cudaGetLastError());
     std::vector<unsigned long long> hb((size_t)L * L);
     MS_CUDA(cudaMemcpyAsync(hb.data(), blk, sizeof(unsigned long long) * L * L, cudaMemcpyDeviceToHost, st));

@@ -81,6 +81,17 @@ ms_status validate_and_init(int d, int L, const int64_t* n_per_level, const doub
     if (o.solve_ctas_per_sm < 0 || o.solve_ctas_per_sm > 2) {
         ms_set_error(MS_ERR_ARG, "solve_ctas_per_sm must be 0, 1 or 2"); return MS_ERR_ARG;
     }
+    if (o.jacobi_sweeps < -1) {
+        ms_set_error(MS_ERR_ARG, "jacobi_sweeps must be >= -1 (got %d)", o.jacobi_sweeps); return MS_ERR_ARG;
+    }
+    if (o.lower_op != MS_OP_CSR && o.lower_op != MS_OP_MATRIX_FREE) {
+        ms_set_error(MS_ERR_ARG, "lower_op must be MS_OP_CSR or MS_OP_MATRIX_FREE (got %d)", o.lower_op); return MS_ERR_ARG;
+    }
+    if (o.lower_op == MS_OP_MATRIX_FREE && o.precision != MS_PREC_MIXED) {
+        ms_set_error(MS_ERR_ARG, "lower_op = MS_OP_MATRIX_FREE needs precision = MS_PREC_MIXED (its double-float entries "
+                     "use the MIXED build's offsets)");
+        return MS_ERR_ARG;
+    }
     h->opts = o;
     h->d = d;
     h->L = L;
@@ -475,7 +486,7 @@ ms_status ms_evaluate(ms_hierarchy* h, const double* alpha, int nrhs, const doub
 ms_status ms_apply_dev(ms_hierarchy* h, int op, const double* x_dev, double* y_dev, int sorted_order, void* stream) {
     g_err[0] = 0;
     if (!h || !x_dev || !y_dev) { ms_set_error(MS_ERR_ARG, "NULL argument"); return MS_ERR_ARG; }
-    if (op < MS_APPLY_A64 || op > MS_APPLY_BMF32) { ms_set_error(MS_ERR_ARG, "unknown operator %d", op); return MS_ERR_ARG; }
+    if (op < MS_APPLY_A64 || op > MS_APPLY_BMFDF) { ms_set_error(MS_ERR_ARG, "unknown operator %d", op); return MS_ERR_ARG; }
     return ms_apply_impl(h, op, x_dev, y_dev, sorted_order, (cudaStream_t)stream);
 }
 
@@ -504,6 +515,7 @@ ms_status ms_hierarchy_info(const ms_hierarchy* h, ms_info* info) {
     info->device_bytes = h->device_bytes;
     info->build_ms = h->build_ms;
     for (int l = 0; l < h->L; ++l) info->tpr_A[l] = ms_tpr_of(h, l);
+    info->pc_basis = h->pc.nbasis;
     return MS_OK;
 }
 

@@ -183,6 +183,9 @@ struct MsError {
 };
 void ms_set_error(ms_status st, const char* fmt, ...);
 void ms_clear_error();  // empties this thread's last-error message (entry of every C-ABI call)
+// Jacobi sweeps of a fit: opts.jacobi_sweeps > 0 as given, 0 = L - 1 (exact, Theorem 9), -1 = none
+// (the fit returns D_L^{-1} f, the block-diagonal solve of eq. split alone)
+inline int ms_sweeps_of(const ms_hierarchy* h);
 void ms_count_launch(unsigned n = 1);  // process-wide kernel launch counter
 ms_status ms_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 
@@ -241,9 +244,13 @@ struct DevCSR {
 constexpr int kPcK = 16;
 constexpr int kPcOut = kPcK + 1;
 constexpr int kPcHidden = 64;
+// candidate rows the network predicts per point (the row is their FSAI-optimal combination)
+constexpr int kPcMaxBasis = 16;
+constexpr int kPcBasisDefault = 16;
 
 struct Precond {
     int n_in = 0, n_params = 0;
+    int nbasis = kPcBasisDefault;  // candidate rows per point (network outputs: 17 nbasis)
     bool trained = false;        // network weights present
     int built_kind = 0;          // kind of G currently built (0 = none)
     float* theta = nullptr;      // [n_params] FP32 master weights (W1,b1,W2,b2,W3,b3)
@@ -281,6 +288,10 @@ struct ms_hierarchy {
     int mf_tpp = 2;              // matrix-free lanes per target point
     DevCSR A, B;
     int32_t* Bseg = nullptr;     // [L][N] start of column level j's segment in each B row (offset from rpB)
+    // lower_op = MATRIX_FREE: the build's frames of every row in the levels up to its own, kept for
+    // the fit's lower-block updates (row s of level k, level j <= k at frame_base[k] + (s - off[k]) (k + 1) + j)
+    void* frames = nullptr;
+    int64_t frame_base[MS_MAXL + 1] = {};
     int64_t Bblk[MS_MAXL][MS_MAXL] = {};  // entries of block B_kj
     int64_t rpA_lv[MS_MAXL + 1] = {};     // A.rp / B.rp at the level boundaries (host copies)
     int64_t rpB_lv[MS_MAXL + 1] = {};
@@ -312,6 +323,11 @@ struct ms_hierarchy {
     size_t alloc_bytes[96];
     int nallocs = 0;
 };
+
+inline int ms_sweeps_of(const ms_hierarchy* h) {
+    if (h->opts.jacobi_sweeps > 0) return h->opts.jacobi_sweeps;
+    return h->opts.jacobi_sweeps < 0 ? 0 : (h->L > 1 ? h->L - 1 : 0);
+}
 
 ms_status ms_alloc(ms_hierarchy* h, void** p, size_t bytes);
 // library memory pool of the current device (ms_capi.cu)

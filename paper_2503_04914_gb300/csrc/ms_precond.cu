@@ -11,10 +11,13 @@
 //   scale-free ghat_i = delta^{-d/2} g_i depends only on the delta-scaled offsets of
 //             the pattern (A_P = delta^-d K(offsets/delta)), so a network trained on
 //             coarse levels applies to every level;
-//   network   32 -> 64 -> 64 -> 17 (d = 2; input 16 d), ReLU, BF16-valued weights with
-//             FP32 accumulation at inference; trained with Adam on FP32 master weights
-//             (forward/backward on the BF16-rounded copies) against the exact rows
-//             of chosen levels, standardised per output.
+//   network   32 -> 64 -> 64 -> 17 m (d = 2; input 16 d), ReLU, BF16-valued weights with
+//             FP32 accumulation at inference: m candidate rows (standardised per entry);
+//             the row is the FSAI-optimal combination of the candidates (the minimiser
+//             of g^T A_P g with g_self = 1 within their span, normalised), solved per row;
+//             trained with Adam on FP32 master weights (forward/backward on the
+//             BF16-rounded copies) to close the gap log (A_P^-1)_11 - log q between the
+//             exact row and the combination, on the exact rows of chosen levels.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -27,8 +30,6 @@
 #include "ms_scan.cuh"
 
 namespace {
-
-constexpr int kTB = 64;  // training samples per block
 
 inline unsigned nblk(int64_t n, int bs) { return (unsigned)std::max<int64_t>(1, (n + bs - 1) / bs); }
 
@@ -311,7 +312,8 @@ __global__ void k_pc_patchK(HierView v, const int32_t* nbr, const int64_t* rows,
             Ki[a * kPcOut + b] = (a < m && b < m) ? (float)wendland_eval<double>(v.w, dist_rn(v, P[a], P[b]) * inv) : 0.f;
 }
 
-// standardised targets T = (ghat - mu) / sigma (zero where masked)
+// per-entry mean and standard deviation of the exact scale-free rows (the standardisation of
+// the network's candidate rows)
 __global__ void k_pc_moments(const double* ghat, const int32_t* cnt, int64_t n, float* musig) {
     const int m = blockIdx.x;  // one block per output
     __shared__ double sh[3][256];
@@ -338,128 +340,311 @@ __global__ void k_pc_moments(const double* ghat, const int32_t* cnt, int64_t n, 
     }
 }
 
-__global__ void k_pc_targets(const double* ghat, const int32_t* cnt, int64_t n, const float* musig, float* T) {
+// q* = (K^-1)_11 of every training patch: the exact scale-free row has unit energy, so
+// q* = ghat_self^2 (the value the loss compares the network's combination with)
+__global__ void k_pc_qstar(const double* ghat, int64_t n, double* qstar) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int m = 0; m < kPcOut; ++m)
-        T[i * kPcOut + m] = m <= cnt[i] ? (float)((ghat[i * kPcOut + m] - musig[m]) / musig[kPcOut + m]) : 0.f;
+    if (i < n) qstar[i] = ghat[i * kPcOut] * ghat[i * kPcOut];
 }
 
 // ---------------------------------------------------------------- network
 
-// parameter offsets: W1 [64][nin], b1 [64], W2 [64][64], b2 [64], W3 [17][64], b3 [17]
+// parameter offsets: W1 [64][nin], b1 [64], W2 [64][64], b2 [64], W3 [17 m][64], b3 [17 m]
+// (output 17 k + a = entry a of candidate row k)
 struct NetLayout {
-    int nin, oW1, ob1, oW2, ob2, oW3, ob3, P;
+    int nin, m, nout, oW1, ob1, oW2, ob2, oW3, ob3, P;
 };
-__host__ __device__ inline NetLayout net_layout(int nin) {
+__host__ __device__ inline NetLayout net_layout(int nin, int m) {
     NetLayout L;
     L.nin = nin;
+    L.m = m;
+    L.nout = kPcOut * m;
     L.oW1 = 0;
     L.ob1 = L.oW1 + kPcHidden * nin;
     L.oW2 = L.ob1 + kPcHidden;
     L.ob2 = L.oW2 + kPcHidden * kPcHidden;
     L.oW3 = L.ob2 + kPcHidden;
-    L.ob3 = L.oW3 + kPcOut * kPcHidden;
-    L.P = L.ob3 + kPcOut;
+    L.ob3 = L.oW3 + L.nout * kPcHidden;
+    L.P = L.ob3 + L.nout;
     return L;
 }
 
-// o = W3 relu(W2 relu(W1 z + b1) + b2) + b3 for one sample; W in shared memory.
-__device__ __forceinline__ void mlp_forward(const NetLayout& N, const float* W, const float* z, float* o) {
-    float h1[kPcHidden];
-#pragma unroll
-    for (int j = 0; j < kPcHidden; ++j) h1[j] = W[N.ob1 + j];
-    for (int k = 0; k < N.nin; ++k) {
-        const float zk = z[k];
-#pragma unroll
-        for (int j = 0; j < kPcHidden; ++j) h1[j] = fmaf(W[N.oW1 + j * N.nin + k], zk, h1[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < kPcHidden; ++j) h1[j] = fmaxf(h1[j], 0.f);
-#pragma unroll
-    for (int m = 0; m < kPcOut; ++m) o[m] = W[N.ob3 + m];
-    for (int j = 0; j < kPcHidden; ++j) {
-        float a = W[N.ob2 + j];
-#pragma unroll
-        for (int k = 0; k < kPcHidden; ++k) a = fmaf(W[N.oW2 + j * kPcHidden + k], h1[k], a);
-        a = fmaxf(a, 0.f);
-#pragma unroll
-        for (int m = 0; m < kPcOut; ++m) o[m] = fmaf(W[N.oW3 + m * kPcHidden + j], a, o[m]);
-    }
+// The candidate span is combined with a ridge of 1e-6 of the mean diagonal of S = U^T K U.
+constexpr float kPcRidge = 1e-6f;
+
+// Inference copy of the weights in shared memory, laid out for 128-bit broadcast loads:
+// W1^T [nin][64], b1 [64], W2 [64][64], b2 [64], W3^T [64][R], b3 [17 m].  R = 68 ceil(m / 4):
+// the candidates are computed four at a time (68 outputs), so every row of W3^T holds whole
+// groups of four, zero past output 17 m (no read past the row, or past the array).
+struct InferLayout {
+    int oW1t, ob1, oW2, ob2, oW3t, R, ob3, P;
+};
+__host__ __device__ inline InferLayout infer_layout(int nin, int m) {
+    InferLayout I;
+    I.oW1t = 0;
+    I.ob1 = kPcHidden * nin;
+    I.oW2 = I.ob1 + kPcHidden;
+    I.ob2 = I.oW2 + kPcHidden * kPcHidden;
+    I.oW3t = I.ob2 + kPcHidden;
+    I.R = 4 * kPcOut * ((m + 3) / 4);
+    I.ob3 = I.oW3t + kPcHidden * I.R;
+    I.P = (I.ob3 + kPcOut * m + 3) & ~3;
+    return I;
 }
 
-// Network prediction of the scale-free rows: ghat = mu + sigma o, diagonal clamped to
-// >= 0.1 mu_0 (keeps G's diagonal positive), outputs of missing neighbours zero, then
-// scaled so that ghat^T K ghat = 1.
-// Writes G = delta^{d/2} ghat (FP32) and the row pattern, or ghat itself for inspection.
-__global__ void k_pc_infer(HierView v, const int32_t* nbr, const float* theta, int nparams, const float* musig,
-                           __half* gval, int32_t* gcol, float* ghat_out) {
-    extern __shared__ float W[];
-    for (int i = threadIdx.x; i < nparams; i += blockDim.x) W[i] = theta[i];
+constexpr int kCandBS = 128;  // threads per block of k_pc_cand
+constexpr int kCombW = 8;     // warps per block of k_pc_combine
+
+inline size_t cand_smem(int nin, int m) { return sizeof(float) * (size_t)infer_layout(nin, m).P; }
+
+// The network's rows are made in two kernels.
+// k_pc_cand, one thread per point: the features z of its pattern (canonical frame), the MLP,
+// and the m candidate rows u_1 = mu + sigma o_1, u_k = sigma o_k (k > 1), zero past the patch,
+// written row-contiguous: Uc[s][17 k + a]; also the features Zc[s][16 d] and the patch size
+// cnt[s] (pattern neighbours).  The candidates are computed four at a time with register
+// accumulators (the second hidden layer's units streamed, each W3 weight loaded once per four
+// candidates from a transposed copy in shared memory, 128-bit broadcast loads).
+__global__ void __launch_bounds__(kCandBS) k_pc_cand(HierView v, const int32_t* nbr, const float* theta, int m,
+                                                     const float* musig, float* Uc, float* Zc, int32_t* cntc) {
+    extern __shared__ __align__(16) float smi[];
+    const int nin = kPcK * v.d;
+    const NetLayout N = net_layout(nin, m);
+    const InferLayout I = infer_layout(nin, m);
+    float* W = smi;
     __shared__ float ms[2 * kPcOut];
+    for (int i = threadIdx.x; i < kPcHidden * nin; i += blockDim.x) {
+        const int k = i / kPcHidden, j = i % kPcHidden;
+        W[I.oW1t + i] = theta[N.oW1 + j * nin + k];
+    }
+    for (int i = threadIdx.x; i < kPcHidden + kPcHidden * kPcHidden + kPcHidden; i += blockDim.x)
+        W[I.ob1 + i] = theta[N.ob1 + i];  // b1, W2, b2 are contiguous in both layouts
+    for (int i = threadIdx.x; i < kPcHidden * I.R; i += blockDim.x) {
+        const int j = i / I.R, r = i % I.R;
+        W[I.oW3t + i] = r < N.nout ? theta[N.oW3 + r * kPcHidden + j] : 0.f;
+    }
+    for (int i = threadIdx.x; i < N.nout; i += blockDim.x) W[I.ob3 + i] = theta[N.ob3 + i];
     if (threadIdx.x < 2 * kPcOut) ms[threadIdx.x] = musig[threadIdx.x];
     __syncthreads();
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= v.N) return;
-    const NetLayout N = net_layout(kPcK * v.d);
-    float z[kPcK * 3], o[kPcOut];
+    float z[kPcK * 3];
     const int cnt = v.d == 1 ? pc_features<1>(v, nbr + s * kPcK, s, z)
                   : v.d == 2 ? pc_features<2>(v, nbr + s * kPcK, s, z)
                              : pc_features<3>(v, nbr + s * kPcK, s, z);
-    mlp_forward(N, W, z, o);
-    float g[kPcOut];
-    for (int m = 0; m < kPcOut; ++m) g[m] = m <= cnt ? fmaf(ms[kPcOut + m], o[m], ms[m]) : 0.f;
-    g[0] = fmaxf(g[0], 0.1f * ms[0]);
-    // (G A G^T)_ii = ghat^T K ghat, K = phi(|z_a - z_b|) on the patch (self at the origin);
-    // the exact row makes it 1: rescale the predicted row to that.
-    {
-        // K is symmetric with K_aa = phi(0) = c_0: the diagonal, then twice each pair a < b
-        const int d = v.d;
-        const float phi0 = (float)v.w.c[0];
-        float q = 0.f;
-        for (int a = 0; a <= cnt; ++a) {
-            q = fmaf(g[a] * g[a], phi0, q);
-            float t = 0.f;
-            for (int b = a + 1; b <= cnt; ++b) {
-                float r2 = 0.f;
-                for (int ax = 0; ax < d; ++ax) {
-                    const float u = (a > 0 ? z[(a - 1) * d + ax] : 0.f) - z[(b - 1) * d + ax];
-                    r2 = fmaf(u, u, r2);
-                }
-                // FP32 entries need no correctly rounded sqrt: r = r2 / sqrt(r2)
-                t = fmaf(wendland_eval<float>(v.w, r2 * rsqrtf(fmaxf(r2, 1e-30f))), g[b], t);
+    for (int k = 0; k < nin; ++k) Zc[s * nin + k] = z[k];
+    cntc[s] = cnt;
+    // layer 1 (inputs streamed, 64 accumulators)
+    float h1[kPcHidden];
+#pragma unroll
+    for (int j = 0; j < kPcHidden; ++j) h1[j] = W[I.ob1 + j];
+    for (int k = 0; k < nin; ++k) {
+        const float zk = z[k];
+        const float4* w4 = reinterpret_cast<const float4*>(W + I.oW1t + k * kPcHidden);
+#pragma unroll
+        for (int j4 = 0; j4 < kPcHidden / 4; ++j4) {
+            const float4 w = w4[j4];
+            h1[4 * j4] = fmaf(w.x, zk, h1[4 * j4]);
+            h1[4 * j4 + 1] = fmaf(w.y, zk, h1[4 * j4 + 1]);
+            h1[4 * j4 + 2] = fmaf(w.z, zk, h1[4 * j4 + 2]);
+            h1[4 * j4 + 3] = fmaf(w.w, zk, h1[4 * j4 + 3]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kPcHidden; ++j) h1[j] = fmaxf(h1[j], 0.f);
+    float* Us = Uc + s * (int64_t)N.nout;
+    // layers 2 and 3, four candidates per pass
+    for (int k0 = 0; k0 < m; k0 += 4) {
+        float acc[4 * kPcOut];
+#pragma unroll
+        for (int r = 0; r < 4 * kPcOut; ++r) acc[r] = k0 * kPcOut + r < N.nout ? W[I.ob3 + k0 * kPcOut + r] : 0.f;
+        for (int j = 0; j < kPcHidden; ++j) {
+            float a2 = W[I.ob2 + j];
+            const float4* w4 = reinterpret_cast<const float4*>(W + I.oW2 + j * kPcHidden);
+#pragma unroll
+            for (int k4 = 0; k4 < kPcHidden / 4; ++k4) {
+                const float4 w = w4[k4];
+                a2 = fmaf(w.x, h1[4 * k4], a2);
+                a2 = fmaf(w.y, h1[4 * k4 + 1], a2);
+                a2 = fmaf(w.z, h1[4 * k4 + 2], a2);
+                a2 = fmaf(w.w, h1[4 * k4 + 3], a2);
             }
-            q = fmaf(2.f * g[a], t, q);
+            a2 = fmaxf(a2, 0.f);
+            // rows 17 k0 .. 17 k0 + 67 of W3^T's row j: 16-byte aligned (17 k0 is a multiple of 4)
+            const float4* u4 = reinterpret_cast<const float4*>(W + I.oW3t + j * I.R + k0 * kPcOut);
+#pragma unroll
+            for (int r4 = 0; r4 < kPcOut; ++r4) {
+                const float4 w = u4[r4];
+                acc[4 * r4] = fmaf(w.x, a2, acc[4 * r4]);
+                acc[4 * r4 + 1] = fmaf(w.y, a2, acc[4 * r4 + 1]);
+                acc[4 * r4 + 2] = fmaf(w.z, a2, acc[4 * r4 + 2]);
+                acc[4 * r4 + 3] = fmaf(w.w, a2, acc[4 * r4 + 3]);
+            }
         }
-        if (q > 0.f) {
-            const float sc = rsqrtf(q);
-            for (int m = 0; m <= cnt; ++m) g[m] *= sc;
+#pragma unroll
+        for (int r = 0; r < 4 * kPcOut; ++r) {
+            const int k = k0 + r / kPcOut, a = r % kPcOut;
+            // u_1 = mu + sigma o_1, u_k = sigma o_k (k > 1); zero past the patch
+            if (k < m) Us[k * kPcOut + a] = a <= cnt ? fmaf(ms[kPcOut + a], acc[r], k == 0 ? ms[a] : 0.f) : 0.f;
         }
-    }
-    if (ghat_out) {
-        // inspection: by pattern slot (slot k+1 <-> nbr[s][k])
-        ghat_out[s * kPcOut] = g[0];
-        int q = 1;
-        for (int k = 0; k < kPcK; ++k) ghat_out[s * kPcOut + 1 + k] = nbr[s * kPcK + k] >= 0 ? g[q++] : 0.f;
-        return;
-    }
-    // the scale-free row in FP16 (relative rounding 2^-11, far below the network's own error);
-    // the solve applies delta_l^d to G^T G
-    gcol[s] = (int32_t)s;
-    gval[s] = __float2half_rn(g[0]);
-    int q = 1;
-    for (int k = 0; k < kPcK; ++k) {
-        const int32_t c = nbr[s * kPcK + k];
-        gcol[(1 + k) * v.N + s] = c;
-        gval[(1 + k) * v.N + s] = __float2half_rn(c >= 0 ? g[q++] : 0.f);
     }
 }
 
-// One block = kTB samples of a step: forward, backward, per-block gradient partial.
-// Sample j of the step is training sample (a_mul * ((step * batch + j) mod S) + a_add) mod S;
-// samples with (step * batch + j) >= limit are skipped (full-batch inspection).
-// Loss: sum over the block's samples of d^T K d, d = sigma * (o - t) on the valid outputs
-// (K: the sample's scaled patch matrix); escale = 2 / (samples of the step).
+// k_pc_combine, one warp per point: the factorised-sparse-approximate-inverse row in the span
+// of the point's candidates,
+//   g = U y / sqrt(q),  y = (S + 1e-6 diag(S))^-1 U^T e_1,  S = U^T K U,  q = e_1^T U y,
+// K = phi(|z_a - z_b|) on the patch (self at the origin), or, for a patch of n = cnt + 1 <= m
+// points, the exact row (S = K, U = I, no ridge); g^T K g = 1 less the ridge's shift and
+// g_self = sqrt(q) > 0.  (A failed factorisation, or q <= 0: the diagonal row e_1 / sqrt(phi(0)).)
+// K, T = K U and S = U^T T are formed lane-parallel in the warp's shared memory; S is
+// Jacobi-scaled to unit diagonal (the ridge becomes 1e-6 I) and factorised in FP32 by a
+// right-looking Cholesky, one column per step, lanes over the trailing entries.
+// Writes the scale-free row (FP16) and its pattern, or ghat itself for inspection.
+__global__ void __launch_bounds__(kCombW * 32) k_pc_combine(HierView v, const int32_t* nbr, int m, const float* Uc,
+                                                            const float* Zc, const int32_t* cntc, __half* gval,
+                                                            int32_t* gcol, float* ghat_out) {
+    struct WarpBuf {
+        float U[kPcOut * kPcMaxBasis];  // [a][k]
+        float K[kPcOut * kPcOut];
+        float T[kPcOut * kPcMaxBasis];  // [a][l] = (K U)_al
+        float S[kPcMaxBasis * kPcMaxBasis];
+        float z[kPcK * 3];
+        float y[kPcMaxBasis];
+    };
+    __shared__ WarpBuf wb[kCombW];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpBuf& B = wb[w];
+    const int64_t s = blockIdx.x * (int64_t)kCombW + w;
+    if (s >= v.N) return;  // warp-uniform
+    const int d = v.d, nin = kPcK * d, nout = kPcOut * m;
+    const int cnt = cntc[s];
+    const bool exact = cnt + 1 <= m;
+    const int nn = exact ? cnt + 1 : m;  // order of the system
+    for (int i = lane; i < nout; i += 32) {
+        const int k = i / kPcOut, a = i % kPcOut;
+        B.U[a * kPcMaxBasis + k] = Uc[s * (int64_t)nout + i];
+    }
+    for (int i = lane; i < nin; i += 32) B.z[i] = Zc[s * (int64_t)nin + i];
+    __syncwarp();
+    const float phi0 = (float)v.w.c[0];
+    // K on the patch: the pairs a != b over the lanes, phi(0) on the diagonal
+    for (int i = lane; i < kPcOut * kPcOut; i += 32) {
+        const int a = i / kPcOut, b = i % kPcOut;
+        float kab = 0.f;
+        if (a <= cnt && b <= cnt) {
+            if (a == b) {
+                kab = phi0;
+            } else {
+                float r2 = 0.f;
+                for (int ax = 0; ax < d; ++ax) {
+                    const float u = (a > 0 ? B.z[(a - 1) * d + ax] : 0.f) - (b > 0 ? B.z[(b - 1) * d + ax] : 0.f);
+                    r2 = fmaf(u, u, r2);
+                }
+                // FP32 entries need no correctly rounded sqrt: r = r2 / sqrt(r2)
+                kab = wendland_eval<float>(v.w, r2 * rsqrtf(fmaxf(r2, 1e-30f)));
+            }
+        }
+        B.K[i] = kab;
+    }
+    __syncwarp();
+    if (exact) {
+        for (int i = lane; i < nn * nn; i += 32) B.S[(i / nn) * kPcMaxBasis + i % nn] = B.K[(i / nn) * kPcOut + i % nn];
+    } else {
+        for (int i = lane; i < (cnt + 1) * m; i += 32) {  // T = K U on the patch's rows
+            const int a = i / m, l = i % m;
+            float t = 0.f;
+            for (int b = 0; b <= cnt; ++b) t = fmaf(B.K[a * kPcOut + b], B.U[b * kPcMaxBasis + l], t);
+            B.T[a * kPcMaxBasis + l] = t;
+        }
+        __syncwarp();
+        for (int i = lane; i < m * m; i += 32) {  // S = U^T T
+            const int k = i / m, l = i % m;
+            float t = 0.f;
+            for (int a = 0; a <= cnt; ++a) t = fmaf(B.U[a * kPcMaxBasis + k], B.T[a * kPcMaxBasis + l], t);
+            B.S[k * kPcMaxBasis + l] = t;
+        }
+    }
+    __syncwarp();
+    // Jacobi scaling D = diag(S)^-1/2 and the right-hand side b = D (U^T e_1 or e_1): lane k < nn
+    const float ridge = exact ? 0.f : kPcRidge;
+    const float skk = lane < nn ? B.S[lane * kPcMaxBasis + lane] : 1.f;
+    const float dk = rsqrtf(fmaxf(skk, 1e-30f));
+    const float bk = lane < nn ? (exact ? (lane == 0 ? 1.f : 0.f) : B.U[lane]) * dk : 0.f;
+    bool ok = __all_sync(0xffffffffu, skk > 0.f);
+    if (lane < kPcMaxBasis) B.y[lane] = dk;
+    __syncwarp();
+    for (int i = lane; i < nn * nn; i += 32) {
+        const int r = i / nn, c = i % nn;
+        float& e = B.S[r * kPcMaxBasis + c];
+        e = e * B.y[r] * B.y[c] + (r == c ? ridge : 0.f);
+    }
+    __syncwarp();
+    // right-looking Cholesky S = L L^T (L in the lower triangle of S)
+    for (int k = 0; k < nn; ++k) {
+        const float pk = B.S[k * kPcMaxBasis + k];
+        ok = ok && pk > 0.f;
+        const float lkk = sqrtf(fmaxf(pk, 1e-30f)), inv = 1.f / lkk;
+        __syncwarp();
+        if (lane == 0) B.S[k * kPcMaxBasis + k] = lkk;
+        for (int i = k + 1 + lane; i < nn; i += 32) B.S[i * kPcMaxBasis + k] *= inv;
+        __syncwarp();
+        const int rem = nn - k - 1;
+        for (int t = lane; t < rem * rem; t += 32) {
+            const int i = k + 1 + t / rem, j = k + 1 + t % rem;
+            if (j <= i) B.S[i * kPcMaxBasis + j] -= B.S[i * kPcMaxBasis + k] * B.S[j * kPcMaxBasis + k];
+        }
+        __syncwarp();
+    }
+    // L w = b (lane k holds w_k), then L^T yt = w; q = b^T yt, y = D yt
+    float wv = bk;
+    for (int k = 0; k < nn; ++k) {
+        const float wk = __shfl_sync(0xffffffffu, wv, k) / B.S[k * kPcMaxBasis + k];
+        if (lane == k) wv = wk;
+        if (lane > k && lane < nn) wv -= B.S[lane * kPcMaxBasis + k] * wk;
+    }
+    for (int k = nn - 1; k >= 0; --k) {
+        const float yk = __shfl_sync(0xffffffffu, wv, k) / B.S[k * kPcMaxBasis + k];
+        if (lane == k) wv = yk;
+        if (lane < k) wv -= B.S[k * kPcMaxBasis + lane] * yk;
+    }
+    float qp = lane < nn ? bk * wv : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) qp += __shfl_xor_sync(0xffffffffu, qp, o);
+    ok = ok && qp > 0.f && isfinite(qp);
+    const float yv = lane < nn ? wv * dk : 0.f;
+    __syncwarp();
+    if (lane < kPcMaxBasis) B.y[lane] = yv;
+    __syncwarp();
+    // g_a = (U y)_a / sqrt(q) for lane a (exact: y_a / sqrt(q))
+    float ga = 0.f;
+    if (lane <= cnt && lane < kPcOut) {
+        if (exact) {
+            ga = B.y[lane];
+        } else {
+            for (int k = 0; k < m; ++k) ga = fmaf(B.U[lane * kPcMaxBasis + k], B.y[k], ga);
+        }
+        ga *= ok ? rsqrtf(qp) : 0.f;
+    }
+    if (!ok) ga = lane == 0 ? rsqrtf(phi0) : 0.f;
+    // lane a holds entry a of the row (self, then the present neighbours in slot order); lane
+    // L = 1..16 writes pattern slot L - 1, whose entry is 1 + (present slots before it)
+    const int32_t c = lane >= 1 && lane <= kPcK ? nbr[s * kPcK + lane - 1] : -1;
+    const unsigned present = __ballot_sync(0xffffffffu, c >= 0);
+    const int e = c >= 0 ? 1 + __popc(present & ((1u << lane) - 1u)) : 0;
+    const float gslot = __shfl_sync(0xffffffffu, ga, e);
+    if (ghat_out) {
+        if (lane == 0) ghat_out[s * kPcOut] = ga;
+        else if (lane <= kPcK) ghat_out[s * kPcOut + lane] = c >= 0 ? gslot : 0.f;
+        return;
+    }
+    if (lane == 0) {
+        gcol[s] = (int32_t)s;
+        gval[s] = __float2half_rn(ga);
+    } else if (lane <= kPcK) {
+        gcol[(int64_t)lane * v.N + s] = c;
+        gval[(int64_t)lane * v.N + s] = __float2half_rn(c >= 0 ? gslot : 0.f);
+    }
+}
+
 // SplitMix64 output function (Steele, Lea and Flood 2014) of counter x: per-element noise.
 __device__ __forceinline__ uint64_t sm64_dev(uint64_t x) {
     x += 0x9E3779B97F4A7C15ull;
@@ -468,43 +653,95 @@ __device__ __forceinline__ uint64_t sm64_dev(uint64_t x) {
     return x ^ (x >> 31);
 }
 
+// Training samples per block: the per-sample buffers grow with the candidate count m.
+__host__ __device__ inline int train_tb(int m) { return m <= 2 ? 64 : (m <= 8 ? 32 : 16); }
+
+// Shared-memory layout of k_pc_train (floats).
+struct TrainLayout {
+    int W, X, A1, A2, U, KU, Sm, Y, Q, YY, GT, Rr, D2, D1, total;
+};
+__host__ __device__ inline TrainLayout train_layout(int nin, int m, int tb) {
+    const NetLayout N = net_layout(nin, m);
+    TrainLayout T;
+    int o = 0;
+    T.W = o; o += N.P;
+    T.X = o; o += tb * nin;
+    T.A1 = o; o += tb * kPcHidden;
+    T.A2 = o; o += tb * kPcHidden;
+    T.U = o; o += tb * N.nout;
+    T.KU = o; o += tb * N.nout;
+    T.Sm = o; o += tb * m * m;
+    T.Y = o; o += tb * m;
+    T.Q = o; o += tb;
+    T.YY = o; o += tb;
+    T.GT = o; o += tb * kPcOut;
+    T.Rr = o; o += tb * kPcOut;
+    T.D2 = o; o += tb * kPcHidden;
+    T.D1 = o; o += tb * kPcHidden;
+    T.total = o;
+    return T;
+}
+
+// One block = tb samples of a step: forward, the combination of the candidates, backward,
+// per-block gradient partial.  Sample j of the step is training sample
+// (a_mul * ((step * batch + j) mod S) + a_add) mod S; samples with (step * batch + j) >= limit
+// are skipped (full-batch inspection).
+// Loss of a sample: log q* - log q (q* = (K^-1)_11 of the exact row, q = e_1^T U y of the
+// candidates' combination, y = (S + 1e-6 diag(S))^-1 U^T e_1, S = U^T K U, see k_pc_infer).
+// With r = e_1 - K U y and the ridge's own dependence on U,
+// dq/dU = 2 r y^T - 2e-6 (K U) diag(y)^2, and the error signal of output 17 k + a is
+// escale * sigma_a * (-(dq/dU)_ak / q) on the patch's entries (escale = 1 / samples of the
+// step).  The m x m system is factorised in FP64 (training only); a sample whose
+// factorisation fails, or a patch of n <= m points (its row is the exact one), contributes
+// nothing.
 // noise > 0: every present input coordinate of a training sample is jittered by
 // noise * U[-1, 1) (counter = (noise_key, sample slot, coordinate); targets unchanged).
-__global__ void k_pc_train(const float* Z, const float* T, const int32_t* cnt, const float* Kp, const float* musig,
-                           int64_t S, int nin, const float* theta, int batch, int64_t step, uint64_t a_mul,
-                           uint64_t a_add, int64_t limit, float escale, float* grad_part, double* loss_part,
-                           float noise, uint64_t noise_key) {
+__global__ void k_pc_train(const float* Z, const double* qstar, const int32_t* cnt, const float* Kp,
+                           const float* musig, int64_t S, int nin, int m, const float* theta, int batch, int64_t step,
+                           uint64_t a_mul, uint64_t a_add, int64_t limit, float escale, float* grad_part,
+                           double* loss_part, float noise, uint64_t noise_key) {
     extern __shared__ float sm[];
-    const NetLayout N = net_layout(nin);
-    float* W = sm;
-    float* X = W + N.P;
-    float* A1 = X + kTB * nin;
-    float* A2 = A1 + kTB * kPcHidden;
-    float* E = A2 + kTB * kPcHidden;
-    float* D2 = E + kTB * kPcOut;
-    float* D1 = D2 + kTB * kPcHidden;
-    float* Dd = D1 + kTB * kPcHidden;  // d = sigma (o - t), masked
-    __shared__ double lsum[256];
-    __shared__ int64_t sidx[kTB];
+    const int tb = train_tb(m);
+    const NetLayout N = net_layout(nin, m);
+    const TrainLayout L = train_layout(nin, m, tb);
+    const int NO = N.nout;
+    float* W = sm + L.W;
+    float* X = sm + L.X;
+    float* A1 = sm + L.A1;
+    float* A2 = sm + L.A2;
+    float* U = sm + L.U;
+    float* KU = sm + L.KU;  // K U, then the error signal of the outputs
+    float* Sm = sm + L.Sm;
+    float* Y = sm + L.Y;
+    float* Q = sm + L.Q;
+    float* YY = sm + L.YY;
+    float* GT = sm + L.GT;
+    float* Rr = sm + L.Rr;
+    float* D2 = sm + L.D2;
+    float* D1 = sm + L.D1;
+    __shared__ double lsum[64];
+    __shared__ int64_t sidx[64];
+    __shared__ int scnt[64];
     const int t = threadIdx.x, nt = blockDim.x;
     for (int i = t; i < N.P; i += nt) W[i] = theta[i];
-    if (t < kTB) {
-        const int64_t g = step * batch + (int64_t)blockIdx.x * kTB + t;
+    if (t < tb) {
+        const int64_t g = step * batch + (int64_t)blockIdx.x * tb + t;
         sidx[t] = g < limit ? (int64_t)((a_mul * (uint64_t)(g % S) + a_add) % (uint64_t)S) : -1;
+        scnt[t] = sidx[t] >= 0 ? cnt[sidx[t]] : -1;
     }
     __syncthreads();
-    for (int i = t; i < kTB * nin; i += nt) {
+    for (int i = t; i < tb * nin; i += nt) {
         const int s = i / nin, k = i % nin;
         float x = sidx[s] >= 0 ? Z[sidx[s] * nin + k] : 0.f;
         if (noise > 0.f && x != 0.f) {
-            const uint64_t c = noise_key ^ ((uint64_t)(step * batch + (int64_t)blockIdx.x * kTB + s) * 64u + (uint64_t)k);
+            const uint64_t c = noise_key ^ ((uint64_t)(step * batch + (int64_t)blockIdx.x * tb + s) * 64u + (uint64_t)k);
             x += noise * ((float)(sm64_dev(c) >> 40) * 0x1p-23f - 1.0f);
         }
         X[i] = x;
     }
     __syncthreads();
     // layer 1
-    for (int i = t; i < kTB * kPcHidden; i += nt) {
+    for (int i = t; i < tb * kPcHidden; i += nt) {
         const int s = i / kPcHidden, j = i % kPcHidden;
         float a = W[N.ob1 + j];
         for (int k = 0; k < nin; ++k) a = fmaf(W[N.oW1 + j * nin + k], X[s * nin + k], a);
@@ -512,49 +749,138 @@ __global__ void k_pc_train(const float* Z, const float* T, const int32_t* cnt, c
     }
     __syncthreads();
     // layer 2
-    for (int i = t; i < kTB * kPcHidden; i += nt) {
+    for (int i = t; i < tb * kPcHidden; i += nt) {
         const int s = i / kPcHidden, j = i % kPcHidden;
         float a = W[N.ob2 + j];
         for (int k = 0; k < kPcHidden; ++k) a = fmaf(W[N.oW2 + j * kPcHidden + k], fmaxf(A1[s * kPcHidden + k], 0.f), a);
         A2[i] = a;
     }
     __syncthreads();
-    // output, its scaled error d, and the energy-norm error signal E = escale sigma (K d)
-    for (int i = t; i < kTB * kPcOut; i += nt) {
-        const int s = i / kPcOut, m = i % kPcOut;
-        float dv = 0.f;
-        if (sidx[s] >= 0 && m <= cnt[sidx[s]]) {
-            float o = W[N.ob3 + m];
-            for (int j = 0; j < kPcHidden; ++j) o = fmaf(W[N.oW3 + m * kPcHidden + j], fmaxf(A2[s * kPcHidden + j], 0.f), o);
-            dv = musig[kPcOut + m] * (o - T[sidx[s] * kPcOut + m]);
+    // candidate rows U[s][17 k + a]: u_1 = mu + sigma o_1, u_k = sigma o_k (zero past the patch)
+    for (int i = t; i < tb * NO; i += nt) {
+        const int s = i / NO, j = i % NO, a = j % kPcOut;
+        float u = 0.f;
+        if (a <= scnt[s]) {
+            float o = W[N.ob3 + j];
+            for (int jj = 0; jj < kPcHidden; ++jj) o = fmaf(W[N.oW3 + j * kPcHidden + jj], fmaxf(A2[s * kPcHidden + jj], 0.f), o);
+            u = fmaf(musig[kPcOut + a], o, j < kPcOut ? musig[a] : 0.f);  // the mean on u_1 only
         }
-        Dd[i] = dv;
+        U[i] = u;
     }
     __syncthreads();
+    // K U
+    for (int i = t; i < tb * NO; i += nt) {
+        const int s = i / NO, j = i % NO, k = j / kPcOut, a = j % kPcOut;
+        float v = 0.f;
+        if (a <= scnt[s]) {
+            const float* Ka = Kp + (sidx[s] * kPcOut + a) * kPcOut;
+            for (int b = 0; b <= scnt[s]; ++b) v = fmaf(Ka[b], U[s * NO + k * kPcOut + b], v);
+        }
+        KU[i] = v;
+    }
+    __syncthreads();
+    // S = U^T K U
+    for (int i = t; i < tb * m * m; i += nt) {
+        const int s = i / (m * m), k = (i / m) % m, l = i % m;
+        float v = 0.f;
+        for (int a = 0; a <= scnt[s]; ++a) v = fmaf(U[s * NO + k * kPcOut + a], KU[s * NO + l * kPcOut + a], v);
+        Sm[i] = v;
+    }
+    __syncthreads();
+    // per sample: ridge, Cholesky (FP64), y, q
     double lacc = 0.0;
-    for (int i = t; i < kTB * kPcOut; i += nt) {
-        const int s = i / kPcOut, m = i % kPcOut;
-        float e = 0.f;
-        if (sidx[s] >= 0 && m <= cnt[sidx[s]]) {
-            const float* Km = Kp + (sidx[s] * kPcOut + m) * kPcOut;
-            float kd = 0.f;
-            for (int q = 0; q < kPcOut; ++q) kd = fmaf(Km[q], Dd[s * kPcOut + q], kd);
-            lacc += (double)Dd[i] * (double)kd;
-            e = escale * musig[kPcOut + m] * kd;
+    if (t < tb) {
+        const int s = t;
+        float q = 0.f, yy = 0.f;
+        // patches of n <= m points take the exact row: no dependence on the network
+        if (sidx[s] >= 0 && scnt[s] + 1 > m) {
+            double R[kPcMaxBasis * kPcMaxBasis];
+            bool ok = true;
+            for (int k = 0; k < m && ok; ++k) {
+                double dkk = (double)Sm[s * m * m + k * m + k] * (1.0 + (double)kPcRidge);
+                for (int i = 0; i < k; ++i) dkk -= R[i * m + k] * R[i * m + k];
+                if (!(dkk > 0.0)) { ok = false; break; }
+                const double rkk = sqrt(dkk);
+                R[k * m + k] = rkk;
+                for (int l = k + 1; l < m; ++l) {
+                    double v = (double)Sm[s * m * m + k * m + l];
+                    for (int i = 0; i < k; ++i) v -= R[i * m + k] * R[i * m + l];
+                    R[k * m + l] = v / rkk;
+                }
+            }
+            if (ok) {
+                double yv[kPcMaxBasis];
+                for (int k = 0; k < m; ++k) {
+                    double w = (double)U[s * NO + k * kPcOut];
+                    for (int i = 0; i < k; ++i) w -= R[i * m + k] * yv[i];
+                    yv[k] = w / R[k * m + k];
+                }
+                for (int k = m - 1; k >= 0; --k) {
+                    double w = yv[k];
+                    for (int l = k + 1; l < m; ++l) w -= R[k * m + l] * yv[l];
+                    yv[k] = w / R[k * m + k];
+                }
+                double qd = 0.0, yyd = 0.0;
+                for (int k = 0; k < m; ++k) {
+                    qd += (double)U[s * NO + k * kPcOut] * yv[k];
+                    yyd += yv[k] * yv[k];
+                }
+                if (qd > 0.0 && isfinite(qd)) {
+                    q = (float)qd;
+                    yy = (float)yyd;
+                    for (int k = 0; k < m; ++k) Y[s * m + k] = (float)yv[k];
+                    lacc = log(qstar[sidx[s]]) - log(qd);
+                }
+            }
         }
-        E[i] = e;
+        if (!(q > 0.f))
+            for (int k = 0; k < m; ++k) Y[s * m + k] = 0.f;
+        Q[s] = q;
+        YY[s] = yy;
     }
-    lsum[t] = lacc;
+    if (t < 64) lsum[t] = lacc;
     __syncthreads();
+    // U y, then r = e_1 - K U y
+    for (int i = t; i < tb * kPcOut; i += nt) {
+        const int s = i / kPcOut, a = i % kPcOut;
+        float v = 0.f;
+        for (int k = 0; k < m; ++k) v = fmaf(U[s * NO + k * kPcOut + a], Y[s * m + k], v);
+        GT[i] = v;
+    }
+    __syncthreads();
+    for (int i = t; i < tb * kPcOut; i += nt) {
+        const int s = i / kPcOut, a = i % kPcOut;
+        float v = 0.f;
+        if (sidx[s] >= 0 && a <= scnt[s]) {
+            const float* Ka = Kp + (sidx[s] * kPcOut + a) * kPcOut;
+            v = a == 0 ? 1.f : 0.f;
+            for (int b = 0; b <= scnt[s]; ++b) v = fmaf(-Ka[b], GT[s * kPcOut + b], v);
+        }
+        Rr[i] = v;
+    }
+    __syncthreads();
+    // error signal of the outputs (in place of K U)
+    for (int i = t; i < tb * NO; i += nt) {
+        const int s = i / NO, j = i % NO, k = j / kPcOut, a = j % kPcOut;
+        float e = 0.f;
+        if (Q[s] > 0.f && a <= scnt[s]) {
+            const float yk = Y[s * m + k];
+            const float dq = 2.f * Rr[s * kPcOut + a] * yk - 2.f * kPcRidge * yk * yk * KU[i];
+            e = -escale * musig[kPcOut + a] * dq / Q[s];
+        }
+        KU[i] = e;
+    }
+    __syncthreads();
+    const float* E = KU;
     // backward through layers 3 and 2
-    for (int i = t; i < kTB * kPcHidden; i += nt) {
+    for (int i = t; i < tb * kPcHidden; i += nt) {
         const int s = i / kPcHidden, j = i % kPcHidden;
         float a = 0.f;
-        for (int m = 0; m < kPcOut; ++m) a = fmaf(E[s * kPcOut + m], W[N.oW3 + m * kPcHidden + j], a);
+        for (int o = 0; o < NO; ++o) a = fmaf(E[s * NO + o], W[N.oW3 + o * kPcHidden + j], a);
         D2[i] = A2[i] > 0.f ? a : 0.f;
     }
     __syncthreads();
-    for (int i = t; i < kTB * kPcHidden; i += nt) {
+    for (int i = t; i < tb * kPcHidden; i += nt) {
         const int s = i / kPcHidden, k = i % kPcHidden;
         float a = 0.f;
         for (int j = 0; j < kPcHidden; ++j) a = fmaf(D2[s * kPcHidden + j], W[N.oW2 + j * kPcHidden + k], a);
@@ -567,28 +893,28 @@ __global__ void k_pc_train(const float* Z, const float* T, const int32_t* cnt, c
         float g = 0.f;
         if (p < N.ob1) {
             const int j = p / nin, k = p % nin;
-            for (int s = 0; s < kTB; ++s) g = fmaf(D1[s * kPcHidden + j], X[s * nin + k], g);
+            for (int s = 0; s < tb; ++s) g = fmaf(D1[s * kPcHidden + j], X[s * nin + k], g);
         } else if (p < N.oW2) {
             const int j = p - N.ob1;
-            for (int s = 0; s < kTB; ++s) g += D1[s * kPcHidden + j];
+            for (int s = 0; s < tb; ++s) g += D1[s * kPcHidden + j];
         } else if (p < N.ob2) {
             const int j = (p - N.oW2) / kPcHidden, k = (p - N.oW2) % kPcHidden;
-            for (int s = 0; s < kTB; ++s) g = fmaf(D2[s * kPcHidden + j], fmaxf(A1[s * kPcHidden + k], 0.f), g);
+            for (int s = 0; s < tb; ++s) g = fmaf(D2[s * kPcHidden + j], fmaxf(A1[s * kPcHidden + k], 0.f), g);
         } else if (p < N.oW3) {
             const int j = p - N.ob2;
-            for (int s = 0; s < kTB; ++s) g += D2[s * kPcHidden + j];
+            for (int s = 0; s < tb; ++s) g += D2[s * kPcHidden + j];
         } else if (p < N.ob3) {
-            const int m = (p - N.oW3) / kPcHidden, j = (p - N.oW3) % kPcHidden;
-            for (int s = 0; s < kTB; ++s) g = fmaf(E[s * kPcOut + m], fmaxf(A2[s * kPcHidden + j], 0.f), g);
+            const int o = (p - N.oW3) / kPcHidden, j = (p - N.oW3) % kPcHidden;
+            for (int s = 0; s < tb; ++s) g = fmaf(E[s * NO + o], fmaxf(A2[s * kPcHidden + j], 0.f), g);
         } else {
-            const int m = p - N.ob3;
-            for (int s = 0; s < kTB; ++s) g += E[s * kPcOut + m];
+            const int o = p - N.ob3;
+            for (int s = 0; s < tb; ++s) g += E[s * NO + o];
         }
         gp[p] = g;
     }
     if (t == 0) {
         double a = 0.0;
-        for (int i = 0; i < nt; ++i) a += lsum[i];
+        for (int i = 0; i < tb; ++i) a += lsum[i];
         loss_part[blockIdx.x] = a;
     }
 }
@@ -706,20 +1032,39 @@ uint64_t gcd64(uint64_t a, uint64_t b) {
 // G rows (gval/gcol) or, with ghat_out, the scale-free rows of every point from the network.
 ms_status launch_infer(ms_hierarchy* h, __half* gval, int32_t* gcol, float* ghat_out, cudaStream_t st) {
     const Precond& pc = h->pc;
-    const size_t smem = sizeof(float) * pc.n_params;
-    MS_CUDA(cudaFuncSetAttribute(k_pc_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_pc_infer<<<nblk(h->N, 128), 128, smem, st>>>(h->view, pc.nbr, pc.fp32_weights ? pc.theta : pc.theta_bf,
-                                                   pc.n_params, pc.musig, gval, gcol, ghat_out);
-    ms_count_launch();
-    MS_CUDA(cudaGetLastError());
-    return MS_OK;
+    const int m = pc.nbasis;
+    const int64_t N = h->N;
+    const float* th = pc.fp32_weights ? pc.theta : pc.theta_bf;
+    // candidate rows, features and patch sizes of every point (scratch from the library pool)
+    float *Uc = nullptr, *Zc = nullptr;
+    int32_t* cnt = nullptr;
+    MS_TRY(ms_tmp_alloc((void**)&Uc, sizeof(float) * (size_t)N * kPcOut * m, st));
+    ms_status s = ms_tmp_alloc((void**)&Zc, sizeof(float) * (size_t)N * pc.n_in, st);
+    if (s == MS_OK) s = ms_tmp_alloc((void**)&cnt, sizeof(int32_t) * (size_t)N, st);
+    if (s == MS_OK) {
+        const size_t smem = cand_smem(pc.n_in, m);
+        cudaError_t e = cudaFuncSetAttribute(k_pc_cand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) {
+            k_pc_cand<<<nblk(N, kCandBS), kCandBS, smem, st>>>(h->view, pc.nbr, th, m, pc.musig, Uc, Zc, cnt);
+            k_pc_combine<<<nblk(N, kCombW), kCombW * 32, 0, st>>>(h->view, pc.nbr, m, Uc, Zc, cnt, gval, gcol,
+                                                                 ghat_out);
+            ms_count_launch(2);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) s = ms_cuda_error(e, "network rows", __FILE__, __LINE__);
+    }
+    if (Uc) cudaFreeAsync(Uc, st);
+    if (Zc) cudaFreeAsync(Zc, st);
+    if (cnt) cudaFreeAsync(cnt, st);
+    return s;
 }
 
 ms_status pc_alloc(ms_hierarchy* h) {
     Precond& pc = h->pc;
     if (pc.nbr) return MS_OK;
     pc.n_in = kPcK * h->d;
-    pc.n_params = net_layout(pc.n_in).P;
+    pc.n_params = net_layout(pc.n_in, pc.nbasis).P;
+    const int pmax = net_layout(pc.n_in, kPcMaxBasis).P;  // room for any candidate count
     const int64_t N = h->N;
     MS_TRY(ms_alloc(h, (void**)&pc.nbr, sizeof(int32_t) * N * kPcK));
     MS_TRY(ms_alloc(h, (void**)&pc.gcol, sizeof(int32_t) * N * kPcOut));
@@ -727,10 +1072,10 @@ ms_status pc_alloc(ms_hierarchy* h) {
     MS_TRY(ms_alloc(h, (void**)&pc.gt_rp, sizeof(int64_t) * (N + 1)));
     MS_TRY(ms_alloc(h, (void**)&pc.gt_col, sizeof(int32_t) * N * kPcOut));
     MS_TRY(ms_alloc(h, (void**)&pc.gt_val, sizeof(__half) * N * kPcOut));
-    MS_TRY(ms_alloc(h, (void**)&pc.theta, sizeof(float) * pc.n_params));
-    MS_TRY(ms_alloc(h, (void**)&pc.theta_bf, sizeof(float) * pc.n_params));
-    MS_TRY(ms_alloc(h, (void**)&pc.adam_m, sizeof(float) * pc.n_params));
-    MS_TRY(ms_alloc(h, (void**)&pc.adam_v, sizeof(float) * pc.n_params));
+    MS_TRY(ms_alloc(h, (void**)&pc.theta, sizeof(float) * pmax));
+    MS_TRY(ms_alloc(h, (void**)&pc.theta_bf, sizeof(float) * pmax));
+    MS_TRY(ms_alloc(h, (void**)&pc.adam_m, sizeof(float) * pmax));
+    MS_TRY(ms_alloc(h, (void**)&pc.adam_v, sizeof(float) * pmax));
     MS_TRY(ms_alloc(h, (void**)&pc.musig, sizeof(float) * 2 * kPcOut));
     return MS_OK;
 }
@@ -770,9 +1115,10 @@ ms_status check_levels(const ms_hierarchy* h, const int* levels, int n) {
 struct TrainSet {
     int64_t S = 0;
     std::vector<void*> bufs;
-    float *Z = nullptr, *T = nullptr, *K = nullptr;
+    float *Z = nullptr, *K = nullptr;
     int32_t* cnt = nullptr;
     double* ghat = nullptr;
+    double* qstar = nullptr;   // [S] (K^-1)_11 of each patch
     int64_t* rows = nullptr;   // centre (sorted row) of each patch
     int32_t* nbr = nullptr;    // [S][16] neighbours of each patch (sorted rows, -1 = none)
     ~TrainSet() {
@@ -840,7 +1186,7 @@ ms_status make_trainset(ms_hierarchy* h, const int* levels, int n, bool set_mome
     MS_TRY(ts.alloc((void**)&dbound, sizeof(int64_t) * ts.S));
     MS_TRY(ts.alloc((void**)&ts.nbr, sizeof(int32_t) * ts.S * kPcK));
     MS_TRY(ts.alloc((void**)&ts.Z, sizeof(float) * ts.S * nin));
-    MS_TRY(ts.alloc((void**)&ts.T, sizeof(float) * ts.S * kPcOut));
+    MS_TRY(ts.alloc((void**)&ts.qstar, sizeof(double) * ts.S));
     MS_TRY(ts.alloc((void**)&ts.cnt, sizeof(int32_t) * ts.S));
     MS_TRY(ts.alloc((void**)&ts.ghat, sizeof(double) * ts.S * kPcOut));
     MS_TRY(ts.alloc((void**)&ts.K, sizeof(float) * ts.S * kPcOut * kPcOut));
@@ -856,7 +1202,7 @@ ms_status make_trainset(ms_hierarchy* h, const int* levels, int n, bool set_mome
         k_pc_moments<<<kPcOut, 256, 0, st>>>(ts.ghat, ts.cnt, ts.S, h->pc.musig);
         ms_count_launch();
     }
-    k_pc_targets<<<nblk(ts.S, 128), 128, 0, st>>>(ts.ghat, ts.cnt, ts.S, h->pc.musig, ts.T);
+    k_pc_qstar<<<nblk(ts.S, 128), 128, 0, st>>>(ts.ghat, ts.S, ts.qstar);
     ms_count_launch();
     MS_CUDA(cudaGetLastError());
     // the host arrays go out of scope: the copies must be complete
@@ -864,13 +1210,10 @@ ms_status make_trainset(ms_hierarchy* h, const int* levels, int n, bool set_mome
     return MS_OK;
 }
 
-size_t train_smem(int nin) {
-    const NetLayout N = net_layout(nin);
-    return sizeof(float) * ((size_t)N.P + kTB * nin + 4 * kTB * kPcHidden + 2 * kTB * kPcOut);
-}
+size_t train_smem(int nin, int m) { return sizeof(float) * (size_t)train_layout(nin, m, train_tb(m)).total; }
 
-ms_status set_train_smem(int nin) {
-    MS_CUDA(cudaFuncSetAttribute(k_pc_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)train_smem(nin)));
+ms_status set_train_smem(int nin, int m) {
+    MS_CUDA(cudaFuncSetAttribute(k_pc_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)train_smem(nin, m)));
     return MS_OK;
 }
 
@@ -926,6 +1269,7 @@ void ms_default_train_opts(ms_train_opts* o) {
     o->seed = 2503049140ull;
     o->input_noise = 0.005f;
     o->augment = 4;
+    o->n_basis = kPcBasisDefault;
 }
 
 ms_status ms_train_precond(ms_hierarchy* h, const int* levels, int n_levels, const ms_train_opts* opts,
@@ -937,9 +1281,11 @@ ms_status ms_train_precond(ms_hierarchy* h, const int* levels, int n_levels, con
     ms_train_opts o;
     ms_default_train_opts(&o);
     if (opts) o = *opts;
-    if (o.epochs < 1 || o.batch < kTB || o.batch % kTB != 0 || !(o.lr > 0.0) || o.augment < 0 || o.augment > 16) {
-        ms_set_error(MS_ERR_ARG, "epochs >= 1, batch a positive multiple of %d, lr > 0 and augment in 0..16 are required",
-                     kTB);
+    if (o.n_basis == 0) o.n_basis = kPcBasisDefault;
+    if (o.epochs < 1 || o.batch < 64 || o.batch % 64 != 0 || !(o.lr > 0.0) || o.augment < 0 || o.augment > 16 ||
+        o.n_basis < 1 || o.n_basis > kPcMaxBasis) {
+        ms_set_error(MS_ERR_ARG, "epochs >= 1, batch a positive multiple of 64, lr > 0, augment in 0..16 and n_basis "
+                     "in 1..%d are required", kPcMaxBasis);
         return MS_ERR_ARG;
     }
     cudaStream_t st;
@@ -954,8 +1300,11 @@ ms_status ms_train_precond(ms_hierarchy* h, const int* levels, int n_levels, con
     MS_TRY(make_trainset(h, levels, n_levels, true, o.augment, o.seed, ts, st));
     pc.augment = o.augment;
     pc.seed = o.seed;
+    const int m = o.n_basis;
+    pc.nbasis = m;
+    pc.n_params = net_layout(pc.n_in, m).P;
     // initial weights: U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from SplitMix64(seed), parameter order
-    const NetLayout N = net_layout(pc.n_in);
+    const NetLayout N = net_layout(pc.n_in, m);
     std::vector<float> th(N.P);
     for (int p = 0; p < N.P; ++p) {
         const int fan = p < N.oW2 ? pc.n_in : kPcHidden;
@@ -968,8 +1317,8 @@ ms_status ms_train_precond(ms_hierarchy* h, const int* levels, int n_levels, con
     k_bf16_round<<<nblk(N.P, 256), 256, 0, st>>>(pc.theta, pc.theta_bf, N.P);
     ms_count_launch();
     pc.fp32_weights = o.fp32_weights;
-    MS_TRY(set_train_smem(pc.n_in));
-    const int nb = o.batch / kTB;
+    MS_TRY(set_train_smem(pc.n_in, m));
+    const int nb = o.batch / train_tb(m);
     const int64_t steps_per_epoch = (ts.S + o.batch - 1) / o.batch;
     const int64_t steps = steps_per_epoch * o.epochs;
     float* grad_part = nullptr;
@@ -981,8 +1330,8 @@ ms_status ms_train_precond(ms_hierarchy* h, const int* levels, int n_levels, con
     MS_CUDA(cudaEventCreate(&e0));
     MS_CUDA(cudaEventCreate(&e1));
     MS_CUDA(cudaEventRecord(e0, st));
-    const size_t smem = train_smem(pc.n_in);
-    const float escale = 2.0f / (float)o.batch;
+    const size_t smem = train_smem(pc.n_in, m);
+    const float escale = 1.0f / (float)o.batch;
     const double lscale = 1.0 / (double)o.batch;
     const double lr_final = o.lr_final > 0 ? o.lr_final : o.lr / 30.0;
     uint64_t a_mul = 1, a_add = 0;
@@ -996,7 +1345,7 @@ ms_status ms_train_precond(ms_hierarchy* h, const int* levels, int n_levels, con
         const double frac = (double)step / (double)std::max<int64_t>(steps - 1, 1);
         const float lr = (float)(lr_final + 0.5 * (o.lr - lr_final) * (1.0 + std::cos(M_PI * frac)));
         const int64_t local = step % steps_per_epoch;
-        k_pc_train<<<nb, 256, smem, st>>>(ts.Z, ts.T, ts.cnt, ts.K, pc.musig, ts.S, pc.n_in,
+        k_pc_train<<<nb, 256, smem, st>>>(ts.Z, ts.qstar, ts.cnt, ts.K, pc.musig, ts.S, pc.n_in, m,
                                           o.fp32_weights ? pc.theta : pc.theta_bf, o.batch, local, a_mul, a_add,
                                           INT64_MAX, escale, grad_part, loss_part, o.input_noise,
                                           sm64(o.seed ^ 0x6E6F697365ull, (uint64_t)epoch));
@@ -1036,10 +1385,22 @@ ms_status ms_precond_params(ms_hierarchy* h, float* params, int64_t n, int set) 
     }
     MS_TRY(pc_alloc(h));
     Precond& pc = h->pc;
-    const int64_t need = pc.n_params + 2 * kPcOut;
-    if (n != need) {
-        ms_set_error(MS_ERR_ARG, "expected %lld values (%d weights + %d standardisation)", (long long)need,
-                     pc.n_params, 2 * kPcOut);
+    if (set) {
+        // the candidate count m follows from the number of values (17 m outputs of width 64)
+        int m = 0;
+        for (int k = 1; k <= kPcMaxBasis; ++k)
+            if (n == (int64_t)net_layout(pc.n_in, k).P + 2 * kPcOut) m = k;
+        if (m == 0) {
+            ms_set_error(MS_ERR_ARG, "%lld values match no network of %d inputs with 1..%d candidate rows "
+                         "(%d + 1105 m weights + %d standardisation)", (long long)n, pc.n_in, kPcMaxBasis,
+                         net_layout(pc.n_in, 0).P, 2 * kPcOut);
+            return MS_ERR_ARG;
+        }
+        pc.nbasis = m;
+        pc.n_params = net_layout(pc.n_in, m).P;
+    } else if (n != (int64_t)pc.n_params + 2 * kPcOut) {
+        ms_set_error(MS_ERR_ARG, "expected %lld values (%d weights + %d standardisation)",
+                     (long long)(pc.n_params + 2 * kPcOut), pc.n_params, 2 * kPcOut);
         return MS_ERR_ARG;
     }
     if (set) {
@@ -1138,17 +1499,19 @@ ms_status ms_precond_inspect(ms_hierarchy* h, int what, const int* levels, int n
         }
         TrainSet ts;
         MS_TRY(make_trainset(h, levels, n_levels, false, 0, pc.seed, ts, st));
-        const int nb = (int)((ts.S + kTB - 1) / kTB);
-        const NetLayout Nl = net_layout(pc.n_in);
+        const int tb = train_tb(pc.nbasis);
+        const int nb = (int)((ts.S + tb - 1) / tb);
+        const NetLayout Nl = net_layout(pc.n_in, pc.nbasis);
         float *gp = nullptr, *gout = nullptr;
         double *lp = nullptr, *lo = nullptr;
         MS_TRY(ts.alloc((void**)&gp, sizeof(float) * nb * Nl.P));
         MS_TRY(ts.alloc((void**)&gout, sizeof(float) * Nl.P));
         MS_TRY(ts.alloc((void**)&lp, sizeof(double) * nb));
         MS_TRY(ts.alloc((void**)&lo, sizeof(double)));
-        MS_TRY(set_train_smem(pc.n_in));
-        k_pc_train<<<nb, 256, train_smem(pc.n_in), st>>>(ts.Z, ts.T, ts.cnt, ts.K, pc.musig, ts.S, pc.n_in, pc.theta,
-                                                         nb * kTB, 0, 1, 0, ts.S, 2.0f / (float)ts.S, gp, lp, 0.f, 0ull);
+        MS_TRY(set_train_smem(pc.n_in, pc.nbasis));
+        k_pc_train<<<nb, 256, train_smem(pc.n_in, pc.nbasis), st>>>(ts.Z, ts.qstar, ts.cnt, ts.K, pc.musig, ts.S,
+                                                                    pc.n_in, pc.nbasis, pc.theta, nb * tb, 0, 1, 0,
+                                                                    ts.S, 1.0f / (float)ts.S, gp, lp, 0.f, 0ull);
         k_pc_adam<<<nblk(Nl.P, 256), 256, 0, st>>>(nullptr, nullptr, nullptr, nullptr, gp, nb, Nl.P, 0.f, 1.f, 1.f, lp,
                                                    lo, 1.0 / (double)ts.S, gout);
         ms_count_launch(2);

@@ -62,6 +62,51 @@ __global__ void k_to_f32(const double* in, float* out, int64_t n) {
     if (i < n) out[i] = (float)in[i];
 }
 
+// x split into double-float parts hi + lo
+__global__ void k_split_ff(const double* in, float* hi, float* lo, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        const ff t = ff_from_double(in[i]);
+        hi[i] = t.hi;
+        lo[i] = t.lo;
+    }
+}
+
+// FP32 constants of the matrix-free lower blocks: the Wendland polynomial and delta_j^-d.
+struct LowerF32 {
+    float c[4];
+    float ds[MS_MAXL];
+};
+
+// y = (T_L - D_L) x matrix-free: S lanes per row; row s of level k sums the entries of every
+// level j < k (lower_row_mf, level j's frame of s set up in FP64), rows of level 0 get 0.
+template <bool FF>
+__global__ void k_lower_mf_apply(const __grid_constant__ HierView v, const float* W, const float* Wlo,
+                                 const int32_t* cellid, const __grid_constant__ FFLevels ffl,
+                                 const __grid_constant__ LowerF32 lf, const float* xhi, const float* xlo, double* y,
+                                 int S) {
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t row = gw * (32 / S) + lane / S;
+    const int sl = lane & (S - 1);
+    const bool ok = row < v.N;
+    ff acc = {0.0f, 0.0f};
+    if (ok) {
+        const int k = level_of_row(v.off, v.L, row);
+        for (int j = 0; j < k; ++j) {
+            const Frame f = frame_of(v, j, point_at(v, row));
+            const ff part = lower_row_mf_any<FF>(v, W, Wlo, cellid, ffl, lf.c, lf.ds[j], j, f, xhi, xlo, sl, S);
+            acc = FF ? ff_add(acc, part) : ff{acc.hi + part.hi, 0.0f};
+        }
+    }
+    if (FF) {
+        acc = ff_group_sum(acc, S);
+    } else {
+        for (int o = S >> 1; o > 0; o >>= 1) acc.hi += __shfl_xor_sync(0xffffffffu, acc.hi, o);
+    }
+    if (ok && sl == 0) y[row] = FF ? ff_to_double(acc) : (double)acc.hi;
+}
+
 // The solve kernel for a precision and a CTAs-per-SM choice (opts.solve_ctas_per_sm;
 // 0 = automatic = 2: measured on GB300 at 1.4M points, 2 CTAs per SM (64 registers)
 // fit 21% (FP64) and 24% (MIXED, learned preconditioner) faster than 1 (128 registers)).
@@ -402,7 +447,7 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
     if (stats) {
         *stats = ms_fit_stats{};
         stats->L = L;
-        stats->sweeps = h->opts.jacobi_sweeps > 0 ? h->opts.jacobi_sweeps : std::max(L - 1, 0);
+        stats->sweeps = ms_sweeps_of(h);
         for (int l = 0; l < L; ++l) {
             stats->cg_iterations[l] = it_sum[l];
             stats->refinements[l] = ref_sum[l];
@@ -428,6 +473,11 @@ ms_status ms_apply_impl(ms_hierarchy* h, int op, const double* x_dev, double* y_
         ms_gather_sorted(x_dev, h->tmp64, h->perm, N, 1, 0, st);
         xs = h->tmp64;
         ys = h->q;
+    }
+    if ((op == MS_APPLY_B64 || op == MS_APPLY_B32) && h->opts.lower_op == MS_OP_MATRIX_FREE) {
+        ms_set_error(MS_ERR_ARG, "B is not stored (built with lower_op = MS_OP_MATRIX_FREE): use MS_APPLY_BMF32 or "
+                     "MS_APPLY_BMFDF");
+        return MS_ERR_ARG;
     }
     const DevCSR& M = (op == MS_APPLY_A64 || op == MS_APPLY_A32 || op == MS_APPLY_AMF32) ? h->A : h->B;
     const double avg = (double)M.nnz / (double)std::max<int64_t>(N, 1);
@@ -458,6 +508,32 @@ ms_status ms_apply_impl(ms_hierarchy* h, int op, const double* x_dev, double* y_
         ms_count_launch();
         const MFView v = make_mfview(h);
         k_mf_apply<<<nblk(h->total_cells * 32, 256), 256, 0, st>>>(v, x32, ys, h->mf_tpp, h->total_cells);
+        ms_count_launch();
+        break;
+    }
+    case MS_APPLY_BMF32:
+    case MS_APPLY_BMFDF: {
+        const bool dff = op == MS_APPLY_BMFDF;
+        if (dff && !h->Wlo) {
+            ms_set_error(MS_ERR_ARG, "MS_APPLY_BMFDF needs the double-float offsets of a MIXED build");
+            return MS_ERR_ARG;
+        }
+        float* xhi = reinterpret_cast<float*>(h->r);  // scratch: 2 N floats fit in an N-double buffer
+        float* xlo = xhi + N;
+        if (dff) k_split_ff<<<nblk(N, 256), 256, 0, st>>>(xs, xhi, xlo, N);
+        else k_to_f32<<<nblk(N, 256), 256, 0, st>>>(xs, xhi, N);
+        ms_count_launch();
+        HierView v = h->view;
+        LowerF32 lf{};
+        for (int i = 0; i < 4; ++i) lf.c[i] = (float)v.w.c[i];
+        for (int l = 0; l < h->L; ++l) lf.ds[l] = (float)v.dscale[l];
+        const FFLevels ffl = make_fflevels(v);
+        const int Sl = 8;
+        const unsigned nb = nblk(N * (int64_t)Sl, 256);
+        if (dff)
+            k_lower_mf_apply<true><<<nb, 256, 0, st>>>(v, h->W, h->Wlo, h->cellid, ffl, lf, xhi, xlo, ys, Sl);
+        else
+            k_lower_mf_apply<false><<<nb, 256, 0, st>>>(v, h->W, h->Wlo, h->cellid, ffl, lf, xhi, nullptr, ys, Sl);
         ms_count_launch();
         break;
     }

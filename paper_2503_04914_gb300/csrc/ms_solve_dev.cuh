@@ -43,6 +43,7 @@
 #include <cmath>
 #include <vector>
 
+#include "ms_geom.cuh"
 #include "ms_internal.cuh"
 #include "ms_matfree.cuh"
 
@@ -79,6 +80,15 @@ struct SolveArgs {
     const double* Bv64;
     const int32_t* Bseg;       // [L][N] start of column level j's segment in each B row
     int lower_inc;             // sweep m subtracts B_km t_m only (see k_fit)
+    // matrix-free lower blocks (lower_mf = 1, MIXED builds): B_km t_m recomputed in
+    // double-float from the geometry (the build stores no B)
+    int lower_mf;
+    int tprLmf[MS_MAXL];       // lanes per row of the update from level m
+    const Frame* frames;       // the build's frames: row s of level k, level j <= k at
+    int64_t fbase[MS_MAXL + 1];  // fbase[k] + (s - off[k]) (k + 1) + j
+    HierView hv;
+    FFLevels ffl;
+    const float* Wlo;          // [d][N] low parts of the in-cell offsets
     int64_t nnzBm[MS_MAXL];    // entries of the blocks B_km, k > m
     int tprBm[MS_MAXL];
     const double* f;                       // [R][N]
@@ -120,6 +130,7 @@ struct Shared {
     double bb[kMaxV], alpha[kMaxV], beta[kMaxV], tol[kMaxV], scale[kMaxV], target[kMaxV], gam[kMaxV];
     int act[kMaxV], oact[kMaxV], zero[kMaxV], first[kMaxV], pcoff[kMaxV], fresh[kMaxV];
     int it_solve[kMaxV];
+    int32_t lq[kNW][64];    // per-warp candidate queues of the matrix-free lower update
     int refines[kMaxV];
     int f64[kMaxV];         // MIXED: the level's inner CG runs in FP64 (FP32 refinement stalled)
     int f64n[kMaxV];        // levels switched to FP64
@@ -1169,6 +1180,40 @@ __device__ __forceinline__ void fit_body(const SolveArgs& a, Shared& sh) {
             }
             prof(sh, kPrfLower);
             if (!gsync(a, sh)) return;
+        } else if (m + 1 <= L - 1 && a.lower_inc && a.lower_mf) {
+            // beta_k -= B_km t_m with B's entries recomputed: t_m split into double-float
+            // parts (p32, s32: free between level solves), then one S-lane group per row of
+            // levels k = m+1..L-1 sums its entries in double-float (the entries' arithmetic is
+            // that of the stored B of a MIXED build) and subtracts the sum in FP64.
+            run_phase<0>(a, sh, [&](int v) { return v % L == m; }, [&](const Chunk& ch, double*) {
+                for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
+                    const ff t = ff_from_double(a.x[ch.vb + row]);
+                    a.p32[ch.vb + row] = t.hi;
+                    a.s32[ch.vb + row] = t.lo;
+                }
+            });
+            prof(sh, kPrfLower);
+            if (!gsync(a, sh)) return;
+            run_phase<0>(a, sh, [&](int v) { return v % L >= m + 1; }, [&](const Chunk& ch, double*) {
+                // a warp per row: its frame in level m's grid from the build, the candidates of the
+                // (2R+1)^d cells around it tested in FP32 and compacted (lower_row_mf_warp)
+                const int wid = tid >> 5, lane = tid & 31;
+                const float* xh = a.p32 + ch.vb;
+                const float* xl = a.s32 + ch.vb;
+                const int k = ch.l;
+                for (int64_t row = ch.r0 + wid; row < ch.r1; row += kNW) {
+                    const Frame f = a.frames[a.fbase[k] + (row - a.off[k]) * (k + 1) + m];
+                    const ff acc = ff_group_sum(lower_row_mf_warp_any(a.hv, a.mfv.W, a.Wlo, a.mfv.cellid, a.ffl, m, f,
+                                                                      xh, xl, lane, sh.lq[wid]),
+                                                32);
+                    if (lane == 0) a.beta[ch.vb + row] -= ff_to_double(acc);
+                }
+            });
+            if (tid == 0)
+                sh.bytes += a.R * ((double)(a.off[L] - a.off[m + 1]) * (16.0 + 36.0) +
+                                   (double)(a.off[m + 1] - a.off[m]) * (16.0 + 8.0 + 4.0 * 2.0 * a.hv.d));
+            prof(sh, kPrfLower);
+            if (!gsync(a, sh)) return;
         } else if (m + 1 <= L - 1 && a.lower_inc) {
             // beta_k -= B_km t_m for the rows of levels k = m+1..L-1 (FP64).  When
             // intermediate levels are not iterated (inter_tol >= 1) t_m is the only
@@ -1346,6 +1391,16 @@ void fill_args(const ms_hierarchy* h, double rel_tol, int R, SolveArgs& a, bool 
     a.Arp = h->A.rp; a.Acol = h->A.col; a.Av64 = h->A.v64; a.Av32 = h->A.v32;
     a.Brp = h->B.rp; a.Bcol = h->B.col; a.Bv64 = h->B.v64;
     a.Bseg = h->Bseg;
+    a.lower_mf = (h->opts.precision == MS_PREC_MIXED && h->opts.lower_op == MS_OP_MATRIX_FREE) ? 1 : 0;
+    a.hv = h->view;
+    a.hv.X = h->X;
+    a.hv.cell_start = h->cell_start;
+    a.ffl = make_fflevels(h->view);
+    a.Wlo = h->Wlo;
+    for (int m = 0; m < L; ++m) a.tprLmf[m] = lower_mf_lanes(h->view, m);
+    a.frames = static_cast<const Frame*>(h->frames);
+    for (int l = 0; l <= L; ++l) a.fbase[l] = h->frame_base[l];
+    if (!a.frames) a.lower_mf = 0;  // (a handle built with stored B)
     for (int m = 0; m < L; ++m) {
         int64_t nb = 0;
         for (int k = m + 1; k < L; ++k) nb += h->Bblk[k][m];
@@ -1354,13 +1409,13 @@ void fill_args(const ms_hierarchy* h, double rel_tol, int R, SolveArgs& a, bool 
         a.tprBm[m] = tpr_for(rows > 0 ? (double)nb / rows : 1.0);
     }
     const bool mixed = h->opts.precision == MS_PREC_MIXED;
-    a.sweeps = h->opts.jacobi_sweeps > 0 ? h->opts.jacobi_sweeps : std::max(L - 1, 0);
+    a.sweeps = ms_sweeps_of(h);
     a.max_iters = h->opts.max_iters > 0 ? h->opts.max_iters : 20000;
     a.max_outer = mixed ? 40 : 8;
     a.tol = rel_tol;
     a.inter_tol = h->opts.inter_tol > 0 ? std::max(h->opts.inter_tol, rel_tol) : 1.0;
     a.inner_tol = h->opts.inner_tol > 0 ? h->opts.inner_tol : 1e-4;
-    a.lower_inc = (a.inter_tol >= 1.0 && a.Bseg) ? 1 : 0;
+    a.lower_inc = (a.inter_tol >= 1.0 && (a.Bseg || a.lower_mf)) ? 1 : 0;
     a.timeout_ns = 4000000000ull;
 }
 
@@ -1371,7 +1426,8 @@ int rhs_per_launch(const ms_hierarchy* h, int nrhs) { return std::max(1, std::mi
 // without a preconditioner and the solve kernel runs 2 CTAs per SM.
 bool wide_layout(const ms_hierarchy* h, int nrhs, int minb) {
     return nrhs > 1 && minb == 2 && h->opts.precond == MS_PRECOND_NONE &&
-           !(h->opts.precision == MS_PREC_MIXED && h->opts.op == MS_OP_MATRIX_FREE);
+           !(h->opts.precision == MS_PREC_MIXED && h->opts.op == MS_OP_MATRIX_FREE) &&
+           h->opts.lower_op != MS_OP_MATRIX_FREE;
 }
 
 }  // namespace

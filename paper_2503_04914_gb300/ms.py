@@ -23,7 +23,7 @@ MS_PREC_FP64, MS_PREC_MIXED = range(2)
 MS_PRECOND_NONE, MS_PRECOND_LEARNED, MS_PRECOND_EXACT = range(3)
 MS_INSPECT_PATTERN, MS_INSPECT_TARGETS, MS_INSPECT_PREDICT, MS_INSPECT_GRAD, MS_INSPECT_PATCHES = range(5)
 PC_K, PC_OUT, PC_HIDDEN = 16, 17, 64
-MS_APPLY_A64, MS_APPLY_A32, MS_APPLY_AMF32, MS_APPLY_B64, MS_APPLY_B32, MS_APPLY_BMF32 = range(6)
+MS_APPLY_A64, MS_APPLY_A32, MS_APPLY_AMF32, MS_APPLY_B64, MS_APPLY_B32, MS_APPLY_BMF32, MS_APPLY_BMFDF = range(7)
 
 STATUS_NAMES = {0: "MS_OK", 1: "MS_ERR_ARG", 2: "MS_ERR_CUDA", 3: "MS_ERR_OOM", 4: "MS_ERR_NOT_SPD",
                 5: "MS_ERR_NOT_CONVERGED", 6: "MS_ERR_TIMEOUT", 7: "MS_ERR_NUMERIC", 8: "MS_ERR_STATE"}
@@ -42,7 +42,8 @@ class ms_opts(C.Structure):
                 ("precision", C.c_int), ("precond", C.c_int), ("max_iters", C.c_int),
                 ("jacobi_sweeps", C.c_int), ("inter_tol", C.c_double), ("inner_tol", C.c_double),
                 ("cell_split", C.c_int), ("threads_per_row", C.c_int), ("lower_fp32", C.c_int),
-                ("solve_ctas_per_sm", C.c_int), ("autotune", C.c_int), ("reserved", C.c_int * 5)]
+                ("solve_ctas_per_sm", C.c_int), ("autotune", C.c_int), ("lower_op", C.c_int),
+                ("reserved", C.c_int * 4)]
 
 
 class ms_fit_stats(C.Structure):
@@ -69,13 +70,13 @@ class ms_info(C.Structure):
     _fields_ = [("d", C.c_int32), ("L", C.c_int32), ("N", C.c_int64),
                 ("n_per_level", C.c_int64 * MS_MAX_LEVELS), ("delta", C.c_double * MS_MAX_LEVELS),
                 ("nnz_A", C.c_int64), ("nnz_B", C.c_int64), ("device_bytes", C.c_int64),
-                ("build_ms", C.c_double), ("tpr_A", C.c_int32 * MS_MAX_LEVELS)]
+                ("build_ms", C.c_double), ("tpr_A", C.c_int32 * MS_MAX_LEVELS), ("pc_basis", C.c_int32)]
 
 
 class ms_train_opts(C.Structure):
     _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("lr_final", C.c_double),
                 ("seed", C.c_uint64), ("fp32_weights", C.c_int), ("input_noise", C.c_float),
-                ("augment", C.c_int), ("reserved", C.c_int * 5)]
+                ("augment", C.c_int), ("n_basis", C.c_int), ("reserved", C.c_int * 4)]
 
 
 class ms_train_stats(C.Structure):
@@ -346,7 +347,7 @@ def ms_hierarchy_info(handle) -> dict:
     return {"d": info.d, "L": L, "N": info.N, "n_per_level": list(info.n_per_level[:L]),
             "delta": list(info.delta[:L]), "nnz_A": info.nnz_A, "nnz_B": info.nnz_B,
             "device_bytes": info.device_bytes, "build_ms": info.build_ms,
-            "tpr_A": list(info.tpr_A[:L])}
+            "tpr_A": list(info.tpr_A[:L]), "pc_basis": info.pc_basis}
 
 
 def ms_default_train_opts(**overrides) -> ms_train_opts:
@@ -371,14 +372,17 @@ def ms_train_precond(handle, levels, opts: ms_train_opts | None = None, **overri
     return st.as_dict()
 
 
-def precond_n_values(d: int) -> int:
+def precond_n_values(d: int, m: int) -> int:
+    """Values of an exported network with m candidate rows: weights, then 17 means and 17 deviations."""
     n_in = PC_K * d
-    return PC_HIDDEN * n_in + PC_HIDDEN + PC_HIDDEN * PC_HIDDEN + PC_HIDDEN + PC_OUT * PC_HIDDEN + PC_OUT + 2 * PC_OUT
+    return (PC_HIDDEN * n_in + PC_HIDDEN + PC_HIDDEN * PC_HIDDEN + PC_HIDDEN + m * PC_OUT * PC_HIDDEN + m * PC_OUT
+            + 2 * PC_OUT)
 
 
 def ms_precond_params(handle, d, params=None):
-    """Get (params None) or set the network weights + output standardisation (float32 array)."""
-    n = precond_n_values(d)
+    """Get (params None) or set the network weights + output standardisation (float32 array).
+    Setting takes the candidate count from the array's length."""
+    n = precond_n_values(d, ms_hierarchy_info(handle)["pc_basis"])
     if params is None:
         out = np.empty(n, dtype=np.float32)
         _check(load().ms_precond_params(C.c_void_p(handle), out.ctypes.data_as(C.POINTER(C.c_float)), n, 0))
@@ -401,7 +405,7 @@ def ms_precond_inspect(handle, what, N, d, levels=(0,), augment=4):
     elif what == MS_INSPECT_PREDICT:
         out = np.empty((N, PC_OUT), dtype=np.float32)
     else:
-        out = np.empty(precond_n_values(d) - 2 * PC_OUT + 1, dtype=np.float32)
+        out = np.empty(precond_n_values(d, ms_hierarchy_info(handle)["pc_basis"]) - 2 * PC_OUT + 1, dtype=np.float32)
     _check(load().ms_precond_inspect(C.c_void_p(handle), what, lv, n, out.ctypes.data_as(C.c_void_p), out.size))
     return out
 

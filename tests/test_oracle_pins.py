@@ -155,6 +155,69 @@ def test_fig1_dense_svd_agrees_with_operator():
     np.testing.assert_allclose(op.rmatvec(v), M.T @ v, rtol=1e-10, atol=1e-12)
 
 
+# ---------------------------------------------------------------- Figures 2-3: thresholded M~(T)
+
+
+@pytest.fixture(scope="module")
+def grid_jacobi():
+    out = {}
+    for L in (3, 4, 5):
+        w = inputs.franke_grid_hierarchy(L)
+        out[L] = (w, om.jacobi_matrix(w.levels, w.h, w.nu, w.wendland_d, w.wendland_k))
+    return out
+
+
+@pytest.mark.parametrize("L", [3, 4, 5])
+def test_fig2_thresholded_operator_norm_ratio(grid_jacobi, L):
+    """||M - M~(T)||_2 / ||M||_2 (eq. perturbedmatrix: entries within T q_j kept) on the paper's
+    grids matches Figure 2's printed values to the printed digits, T = 1..6; the dense M agrees
+    with the matrix-free Jacobi operator that reproduces Figure 1."""
+    w, M = grid_jacobi[L]
+    want = [float(x) for x in {int(r[0]): r[1:] for r in _golden("fig2_norm_ratio.txt")}[L]]
+    nM = np.linalg.norm(M, 2)
+    v = np.random.default_rng(L).standard_normal(len(M))
+    op = om.JacobiOperator(w.levels, w.h, w.nu, w.wendland_d, w.wendland_k)
+    np.testing.assert_allclose(op.matvec(v), M @ v, rtol=1e-9, atol=1e-11)
+    for T, ref in zip(range(1, 7), want):
+        got = np.linalg.norm(M - om.thresholded_jacobi_matrix(M, w.levels, T), 2) / nM
+        assert round(got, 5) == pytest.approx(ref, abs=1.01e-5), (T, got, ref)
+
+
+@pytest.mark.parametrize("L", [3, 4, 5])
+def test_fig3_thresholded_operator_nnz_ratio(grid_jacobi, L):
+    """nnz(M~(T)) / nnz(M) matches Figure 3's printed values, T = 1..6; the threshold mask keeps
+    exactly the pairs closer than T q_j (checked by brute force on one block), and it grows with T."""
+    w, M = grid_jacobi[L]
+    want = [float(x) for x in {int(r[0]): r[1:] for r in _golden("fig3_nnz_ratio.txt")}[L]]
+    n0 = om.nonzero_count(M)
+    prev = None
+    for T, ref in zip(range(1, 7), want):
+        mask = om.threshold_mask(w.levels, T)
+        got = om.nonzero_count(np.where(mask, M, 0.0)) / n0
+        assert round(got, 5) == pytest.approx(ref, abs=1.01e-5), (T, got, ref)
+        if prev is not None:
+            assert np.all(mask >= prev)
+        prev = mask
+    off = om.level_offsets(w.levels)
+    q0 = 0.5 * min(np.linalg.norm(a - b) for i, a in enumerate(w.levels[0]) for b in w.levels[0][i + 1:])
+    for i, x in enumerate(w.levels[-1][:40]):
+        for m, y in enumerate(w.levels[0]):
+            assert prev[off[-2] + i, off[0] + m] == (np.linalg.norm(x - y) < 6 * q0)
+
+
+def test_perturbed_split_tends_to_the_exact_solution():
+    """eq. perturbed_split with M~(T): the coefficients equal the sequential method's once no entry
+    is dropped (T beyond the largest distance), and their error falls as T grows."""
+    w = inputs.franke_grid_hierarchy(4)
+    M = om.jacobi_matrix(w.levels, w.h, w.nu, 3, 1)
+    exact = np.concatenate(om.fit_sequential(w.levels, w.f, w.h, w.nu, 3, 1)[0])
+    full = om.perturbed_split_solve(om.thresholded_jacobi_matrix(M, w.levels, 1e6), w.levels, w.h, w.nu, 3, 1, w.f)
+    assert np.linalg.norm(full - exact) <= 1e-10 * np.linalg.norm(exact)
+    errs = [np.linalg.norm(om.perturbed_split_solve(om.thresholded_jacobi_matrix(M, w.levels, T), w.levels, w.h,
+                                                    w.nu, 3, 1, w.f) - exact) for T in (1, 2, 4, 8, 16)]
+    assert errs[-1] < errs[0] and errs[-1] <= 1e-6 * np.linalg.norm(exact), errs
+
+
 # ---------------------------------------------------------------- Section 3 identities
 
 

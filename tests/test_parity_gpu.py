@@ -111,6 +111,68 @@ def test_operators_match_oracle_matrices(wl, prec):
     H.close()
 
 
+@pytest.mark.parametrize("wl", ["grid", "ragged_nu8_w22", "random3d_w31"])
+def test_matrix_free_lower_operators_match_oracle(wl):
+    """y = (T_L - D_L) x with B's entries recomputed (the paper's McV without a stored matrix),
+    against the oracle's dense blocks, per row relative to sum |B||x|: double-float entries and
+    sums (about 48 bits, the fit's lower_op = MATRIX_FREE) 1e-13; FP32 entries and sums 2e-6.
+    The handle stores no B (lower_op = MATRIX_FREE), and the CSR lower operators refuse."""
+    import torch
+    if wl == "grid":
+        w = inputs.grid_hierarchy_small()
+    elif wl == "ragged_nu8_w22":
+        w = ragged_halton([37, 150, 601, 2500], nu=8.0, wendland=(2, 2))
+    else:
+        w = inputs.random3d_hierarchy(L=3, n_gauss=3)
+    H = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED, lower_op=ms.MS_OP_MATRIX_FREE)
+    assert H.info()["nnz_B"] == 0
+    off = om.level_offsets(w.levels)
+    x = np.random.default_rng(11).standard_normal(w.N)
+    yB = np.zeros(w.N)
+    absB = np.zeros(w.N)
+    for k in range(1, w.L):
+        rows = slice(off[k], off[k + 1])
+        for j in range(k):
+            M = om.kernel_dense(w.levels[k], w.levels[j], w.nu * w.h[j], w.wendland_d, w.wendland_k)
+            yB[rows] += M @ x[off[j]:off[j + 1]]
+            absB[rows] += np.abs(M) @ np.abs(x[off[j]:off[j + 1]])
+    xt = torch.from_numpy(x).cuda()
+    for op, tol in ((ms.MS_APPLY_BMFDF, 1e-13), (ms.MS_APPLY_BMF32, 2e-6)):
+        y = H.apply(op, xt).cpu().numpy()
+        err = np.abs(y - yB) / np.maximum(absB, 1e-300)
+        assert err.max() <= tol, (op, err.max())
+        assert np.all(y[:off[1]] == 0.0)
+    with pytest.raises(ms.MsError):
+        H.apply(ms.MS_APPLY_B64, xt)
+    H.close()
+
+
+@pytest.mark.parametrize("precond", [ms.MS_PRECOND_NONE, ms.MS_PRECOND_EXACT])
+@pytest.mark.parametrize("wl", ["nu4_w21", "nu8_w22"])
+def test_fit_with_matrix_free_lower_blocks(wl, precond):
+    """MIXED fit whose Jacobi updates recompute B's entries (lower_op = MATRIX_FREE) against the
+    oracle and against the stored-B MIXED fit.  nu = 4: coefficients 1e-8, approximant 1e-10
+    (rel_tol 1e-12); nu = 8, phi_{2,2} (kappa(A_l) ~ 1e5-1e6, so an FP64 residual cannot go much
+    below kappa eps ~ 1e-11): rel_tol 1e-11, coefficients 1e-6 and approximant 1e-9, as the
+    learned-preconditioner parity test on these levels.  Both fits' approximants agree within
+    the approximant tolerance."""
+    import torch
+    nu, wend, rt, tc, ta = ((4.0, (2, 1), 1e-12, 1e-8, 1e-10) if wl == "nu4_w21" else
+                            (8.0, (2, 2), 1e-11, 1e-6, 1e-9))
+    w = ragged_halton([37, 150, 601, 2500, 9001], nu=nu, wendland=wend)
+    st = check_fit(w, ms.MS_PREC_MIXED, tc, rel_tol=rt, tol_approx=ta, lower_op=ms.MS_OP_MATRIX_FREE,
+                   precond=precond)
+    assert st["device_status"] == 0
+    Hm = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED, lower_op=ms.MS_OP_MATRIX_FREE, precond=precond)
+    Hc = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED, precond=precond)
+    Q = inputs.query_grid(64, 2)
+    sm = Hm.evaluate(Hm.fit(w.f, rel_tol=rt)[0], Q)
+    sc = Hc.evaluate(Hc.fit(w.f, rel_tol=rt)[0], Q)
+    assert rel(sm, sc) <= ta
+    Hm.close()
+    Hc.close()
+
+
 @pytest.mark.parametrize("wl", ["grid_w21", "halton_nu8_w22", "random3d_w31"])
 def test_matrix_free_operator_matches_oracle(wl):
     """y = D_L x with entries recomputed in FP32 from per-cell offsets (no stored matrix),

@@ -559,6 +559,14 @@ ms_status ms_build_impl(ms_hierarchy* h, const double* pts, cudaStream_t st) {
     // the fit updates beta with FP64 B values only; FP32 B values serve MS_APPLY_B32 on request
     if (h->opts.lower_fp32) MS_TRY(ms_alloc(h, (void**)&h->B.v32, sizeof(float) * h->B.nnz));
     if (!onlyA) MS_TRY(ms_alloc(h, (void**)&h->Bseg, sizeof(int32_t) * (size_t)L * N));
+    // the solve's CSR rows read columns and values four entries at a time (128-bit loads from
+    // the first multiple of 4 of a row): the arrays must start on 16-byte boundaries
+    for (const void* q : {(const void*)h->A.col, (const void*)h->A.v64, (const void*)h->A.v32, (const void*)h->B.col,
+                          (const void*)h->B.v64, (const void*)h->B.v32})
+        if (reinterpret_cast<uintptr_t>(q) % 16 != 0) {
+            ms_set_error(MS_ERR_STATE, "a CSR array is not 16-byte aligned");
+            return MS_ERR_STATE;
+        }
     FFLevels ffl{};
     for (int l = 0; l < L; ++l) {
         ffl.cod[l] = ff_from_double(v.grid[l].cell / v.delta[l]);

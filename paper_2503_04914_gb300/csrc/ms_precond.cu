@@ -526,25 +526,24 @@ __global__ void __launch_bounds__(kCombW * 32) k_pc_combine(HierView v, const in
     for (int i = lane; i < nin; i += 32) B.z[i] = Zc[s * (int64_t)nin + i];
     __syncwarp();
     const float phi0 = (float)v.w.c[0];
-    // K on the patch: the pairs a != b over the lanes, phi(0) on the diagonal
-    for (int i = lane; i < kPcOut * kPcOut; i += 32) {
-        const int a = i / kPcOut, b = i % kPcOut;
-        float kab = 0.f;
-        if (a <= cnt && b <= cnt) {
-            if (a == b) {
-                kab = phi0;
-            } else {
-                float r2 = 0.f;
-                for (int ax = 0; ax < d; ++ax) {
-                    const float u = (a > 0 ? B.z[(a - 1) * d + ax] : 0.f) - (b > 0 ? B.z[(b - 1) * d + ax] : 0.f);
-                    r2 = fmaf(u, u, r2);
-                }
-                // FP32 entries need no correctly rounded sqrt: r = r2 / sqrt(r2)
-                kab = wendland_eval<float>(v.w, r2 * rsqrtf(fmaxf(r2, 1e-30f)));
-            }
+    // K on the patch (n = cnt + 1 points): the pairs a < b over the lanes, mirrored, phi(0) on
+    // the diagonal (entries past the patch are not read)
+    const int np = cnt + 1;
+    for (int i = lane; i < np * (np - 1) / 2; i += 32) {
+        int a = 0, rem = i;
+        while (rem >= np - 1 - a) { rem -= np - 1 - a; ++a; }
+        const int b = a + 1 + rem;
+        float r2 = 0.f;
+        for (int ax = 0; ax < d; ++ax) {
+            const float u = (a > 0 ? B.z[(a - 1) * d + ax] : 0.f) - B.z[(b - 1) * d + ax];
+            r2 = fmaf(u, u, r2);
         }
-        B.K[i] = kab;
+        // FP32 entries need no correctly rounded sqrt: r = r2 / sqrt(r2)
+        const float kab = wendland_eval<float>(v.w, r2 * rsqrtf(fmaxf(r2, 1e-30f)));
+        B.K[a * kPcOut + b] = kab;
+        B.K[b * kPcOut + a] = kab;
     }
+    if (lane < np) B.K[lane * kPcOut + lane] = phi0;
     __syncwarp();
     if (exact) {
         for (int i = lane; i < nn * nn; i += 32) B.S[(i / nn) * kPcMaxBasis + i % nn] = B.K[(i / nn) * kPcOut + i % nn];
@@ -556,11 +555,14 @@ __global__ void __launch_bounds__(kCombW * 32) k_pc_combine(HierView v, const in
             B.T[a * kPcMaxBasis + l] = t;
         }
         __syncwarp();
-        for (int i = lane; i < m * m; i += 32) {  // S = U^T T
-            const int k = i / m, l = i % m;
+        for (int i = lane; i < m * (m + 1) / 2; i += 32) {  // S = U^T T (upper triangle, mirrored)
+            int k = 0, rem = i;
+            while (rem >= m - k) { rem -= m - k; ++k; }
+            const int l = k + rem;
             float t = 0.f;
             for (int a = 0; a <= cnt; ++a) t = fmaf(B.U[a * kPcMaxBasis + k], B.T[a * kPcMaxBasis + l], t);
             B.S[k * kPcMaxBasis + l] = t;
+            B.S[l * kPcMaxBasis + k] = t;
         }
     }
     __syncwarp();

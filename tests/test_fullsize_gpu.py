@@ -80,3 +80,55 @@ def test_config5_learned_matches_plain_fp64(fits):
     assert np.linalg.norm(a_l - a_f) <= 1e-8 * np.linalg.norm(a_f)
     # the preconditioner did its job on every level (no fall-back to plain CG)
     assert st_l["precond_fallbacks"] == 0
+
+
+@pytest.fixture(scope="module")
+def fits3d():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    B.build()
+    ms.load()
+    w = inputs.random3d_hierarchy(L=6)
+    pts = torch.from_numpy(w.points).cuda()
+    f = torch.from_numpy(w.f).cuda()
+    out = {"w": w}
+    Ht = ms.Hierarchy(3, w.n_per_level, pts, w.h, precision=ms.MS_PREC_MIXED, precond=ms.MS_PRECOND_LEARNED,
+                      wendland_d=3, wendland_k=1, nu=w.nu)
+    Ht.train_precond([0, 1, 2, 3], epochs=25)
+    params = Ht.precond_params()
+    Ht.close()
+    for tag, prec, pc in (("learned", ms.MS_PREC_MIXED, ms.MS_PRECOND_LEARNED),
+                          ("fp64", ms.MS_PREC_FP64, ms.MS_PRECOND_NONE)):
+        H = ms.Hierarchy(3, w.n_per_level, pts, w.h, precision=prec, precond=pc, wendland_d=3, wendland_k=1, nu=w.nu)
+        if pc == ms.MS_PRECOND_LEARNED:
+            H.precond_params(params)
+        alpha, st = H.fit(f, rel_tol=1e-10)
+        torch.cuda.synchronize()
+        out[tag] = (alpha.cpu().numpy(), st)
+        H.close()
+    return out
+
+
+@pytest.mark.parametrize("tag", ["learned", "fp64"])
+def test_random3d_full_size_sampled_rows_and_interpolation(fits3d, tag):
+    """The 3-D configuration at full size (d = 3 uniform random points, 6 levels, 4,681,125
+    points, delta = 3h, phi_{3,1}): sampled rows of T_L alpha - f on every level and the
+    interpolation property at finest-level points, both summed by the oracle one point at a
+    time, below 1e-8 max|f|; the learned-PCG MIXED and plain FP64 coefficients agree to 1e-8."""
+    w = fits3d["w"]
+    alpha, st = fits3d[tag]
+    assert st["device_status"] == 0 and max(st["rel_residual"]) <= 1e-10, st
+    fmax = np.abs(w.f).max()
+    rng = np.random.default_rng(33)
+    for l in range(w.L):
+        idx = rng.choice(len(w.levels[l]), size=min(8, len(w.levels[l])), replace=False)
+        for i in idx:
+            r = om.row_residual(w.levels, alpha, w.f, w.h, w.nu, 3, 1, l, int(i))
+            assert abs(r) <= 1e-8 * fmax, (tag, l, i, r)
+    off = om.level_offsets(w.levels)
+    alphas = [alpha[off[l]:off[l + 1]] for l in range(w.L)]
+    pts = w.levels[-1][rng.choice(len(w.levels[-1]), 32, replace=False)]
+    s = om.evaluate(w.levels, alphas, w.h, w.nu, 3, 1, pts)
+    assert np.max(np.abs(s - w.f_fun(pts))) <= 1e-8 * fmax, tag
+    a_l, a_f = fits3d["learned"][0], fits3d["fp64"][0]
+    assert np.linalg.norm(a_l - a_f) <= 1e-8 * np.linalg.norm(a_f)

@@ -49,7 +49,7 @@ extern "C" {
 #endif
 
 #define MS_MAX_LEVELS 32
-#define MS_ABI_VERSION 2
+#define MS_ABI_VERSION 3
 
 typedef struct ms_hierarchy ms_hierarchy;
 
@@ -104,15 +104,24 @@ typedef struct ms_opts {
                             fastest schedule, same result).  inter_tol = rel_tol solves every
                             level in every sweep as Algorithm 2 does. */
     double inner_tol;    /* MIXED: relative tolerance of each FP32 inner CG; 0 = 1e-4 */
-    int cell_split;      /* neighbour-grid cell size = delta_l / cell_split (1 or 2); 0 = 1 */
+    int cell_split;      /* neighbour-grid cell size = delta_l / cell_split (1 or 2); 0 = 1, or
+                            with autotune = 1 the faster of 1 and 2 (see autotune) */
     int threads_per_row; /* CSR sub-warp width for A (1..32, power of 2); 0 = automatic */
     int lower_fp32;      /* 1: also store FP32 values of the B blocks (for MS_APPLY_B32) */
     int solve_ctas_per_sm; /* CTAs of the persistent solve kernel per SM: 1 (up to 128
-                              registers a thread) or 2 (up to 64); 0 = automatic (2) */
-    int autotune;        /* 1: at the first fit, time the CSR mat-vec of every level of at
-                            least 4096 rows with 1, 2, 4, 8, 16 and 32 lanes per row and keep
-                            the fastest (cached per process by level shape); 0 = rule
-                            (about 16 entries per lane).  threads_per_row > 0 overrides both. */
+                              registers a thread) or 2 (up to 64); 0 = automatic (2, or with
+                              autotune = 1 the tuned one) */
+    int autotune;        /* 1: tune per hierarchy shape, each choice cached per process:
+                            - at the build, if cell_split = 0: build with cells of delta and
+                              delta / 2, keep the one whose build plus one application of the
+                              fit's matrix-free operators is faster;
+                            - at the first fit: time the CSR mat-vec of every level of at least
+                              4096 rows with 1, 2, 4, 8, 16 and 32 lanes per row (the matrix-free
+                              mat-vec: 1 to 8 lanes per point) and keep the fastest;
+                            - at the first fit, if solve_ctas_per_sm = 0: fit with 1 and with 2
+                              CTAs per SM and keep the faster (the call returns the second fit).
+                            0 = rules (about 16 entries per lane, 2 CTAs per SM, cell = delta).
+                            threads_per_row > 0 overrides the lane choice. */
     int lower_op;        /* operator of the strictly lower blocks B_kj in the fit's Jacobi updates:
                             MS_OP_CSR (default): B stored as CSR by the build (FP64 values);
                             MS_OP_MATRIX_FREE (MIXED only): the build stores no B and every
@@ -149,6 +158,11 @@ typedef struct ms_fit_stats {
                                             [3] grid-barrier waits (includes load imbalance),
                                             [4] lower-block (Jacobi) updates, [5] other vector
                                             phases, [6] scalar decisions, [7] unused */
+    int32_t solve_launches;              /* cooperative solve launches of the call */
+    int32_t rhs_per_launch;              /* most right-hand sides one solve launch carried: blocks
+                                            of min(32, 256 / L) right-hand sides, up to 16 blocks in
+                                            one launch (2 CTAs per SM; one partition of the grid
+                                            per block) */
 } ms_fit_stats;
 
 /* Sizes of a built hierarchy. */
@@ -163,6 +177,8 @@ typedef struct ms_info {
     double build_ms;     /* device time of the last build (CUDA events) */
     int32_t tpr_A[MS_MAX_LEVELS]; /* CSR lanes per row of A_l in the solve (as of the last fit) */
     int32_t pc_basis;    /* candidate rows per point of the handle's network (ms_train_opts.n_basis) */
+    int32_t cell_split;  /* neighbour-grid cells per delta_l in use (opts.cell_split, or the tuned one) */
+    int32_t solve_ctas_per_sm; /* solve-kernel CTAs per SM in use (opts, or the tuned one after a fit) */
 } ms_info;
 
 /* Fill *opts with defaults: phi_{3,1}, nu = 4, CSR, FP64, no preconditioner. */

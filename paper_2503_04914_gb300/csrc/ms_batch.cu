@@ -399,6 +399,8 @@ ms_status ms_batch_plan_stats_impl(ms_batch_plan* p, cudaStream_t st, ms_fit_sta
         s.fit_ms = kernel_ms > 0.f ? kernel_ms : 0.0;  // the batch's solve launches, shared by all its hierarchies
         s.matvec_bytes = b.bytes;
         s.kernel_launches = plan_launches(p);
+        s.solve_launches = (int32_t)p->grid.size();
+        s.rhs_per_launch = 1;
         for (int k = 0; k < kProf; ++k) s.phase_ms[k] = 1e-6 * (double)b.prof[k];
     }
     return result;

@@ -5,7 +5,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "ms_internal.cuh"
@@ -118,8 +120,8 @@ ms_status validate_and_init(int d, int L, const int64_t* n_per_level, const doub
     return MS_OK;
 }
 
-ms_status build_common(int d, int L, const int64_t* n_per_level, const double* pts_dev, const double* h_per_level,
-                       const ms_opts* opts, cudaStream_t st, ms_hierarchy** out) {
+ms_status build_one(int d, int L, const int64_t* n_per_level, const double* pts_dev, const double* h_per_level,
+                    const ms_opts* opts, cudaStream_t st, ms_hierarchy** out) {
     ms_hierarchy* h = new ms_hierarchy();
     ms_status s = validate_and_init(d, L, n_per_level, h_per_level, opts, h);
     if (s == MS_OK) {
@@ -134,6 +136,89 @@ ms_status build_common(int d, int L, const int64_t* n_per_level, const double* p
         return s;
     }
     *out = h;
+    return MS_OK;
+}
+
+// Device time of one application of the geometry-dependent operators the fit will use
+// (the matrix-free FP32 A and / or the matrix-free lower blocks), 0 if it uses none.
+ms_status geometry_ms(ms_hierarchy* h, cudaStream_t st, float* out) {
+    *out = 0.f;
+    const bool mfA = h->opts.precision == MS_PREC_MIXED && h->opts.op == MS_OP_MATRIX_FREE;
+    const bool mfB = h->opts.precision == MS_PREC_MIXED && h->opts.lower_op == MS_OP_MATRIX_FREE && h->L > 1;
+    if (!mfA && !mfB) return MS_OK;
+    DevBuf x, y;
+    MS_TRY(dev_alloc(x, sizeof(double) * h->N));
+    MS_TRY(dev_alloc(y, sizeof(double) * h->N));
+    MS_CUDA(cudaMemsetAsync(x.p, 0, sizeof(double) * h->N, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MS_CUDA(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    ms_status s = ce == cudaSuccess ? MS_OK : ms_cuda_error(ce, "event", __FILE__, __LINE__);
+    for (int rep = 0; rep < 2 && s == MS_OK; ++rep) {  // one untimed application, one timed
+        if (rep == 1) cudaEventRecord(e0, st);
+        if (mfA && s == MS_OK) s = ms_apply_impl(h, MS_APPLY_AMF32, (const double*)x.p, (double*)y.p, 1, st);
+        if (mfB && s == MS_OK) s = ms_apply_impl(h, MS_APPLY_BMFDF, (const double*)x.p, (double*)y.p, 1, st);
+        if (rep == 1) cudaEventRecord(e1, st);
+    }
+    if (s == MS_OK) {
+        ce = cudaEventSynchronize(e1);
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(out, e0, e1);
+        if (ce != cudaSuccess) s = ms_cuda_error(ce, "geometry timing", __FILE__, __LINE__);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return s;
+}
+
+// (d, L, log2 N, 16 nu, wendland d, k, precision, op, lower_op) -> cell_split
+using SplitKey = std::tuple<int, int, int, int, int, int, int, int, int>;
+std::mutex g_split_mu;
+std::map<SplitKey, int> g_split_cache;
+
+// With opts.autotune = 1 and cell_split = 0 the first build of a hierarchy shape is made with
+// cells of delta and of delta / 2; the one whose build plus one application of the fit's
+// matrix-free operators takes less device time is kept (the other is destroyed) and the choice is
+// cached per process by shape.  Otherwise one build.
+ms_status build_common(int d, int L, const int64_t* n_per_level, const double* pts_dev, const double* h_per_level,
+                       const ms_opts* opts, cudaStream_t st, ms_hierarchy** out) {
+    if (!opts || !opts->autotune || opts->cell_split != 0)
+        return build_one(d, L, n_per_level, pts_dev, h_per_level, opts, st, out);
+    int64_t N = 0;
+    for (int l = 0; l < L; ++l) N += n_per_level[l];
+    int lg = 0;
+    while ((int64_t(1) << (lg + 1)) <= N) ++lg;
+    const SplitKey key(d, L, lg, (int)std::lround(16.0 * opts->nu), opts->wendland_d, opts->wendland_k,
+                       opts->precision, opts->op, opts->lower_op);
+    ms_opts o = *opts;
+    {
+        std::lock_guard<std::mutex> lk(g_split_mu);
+        auto it = g_split_cache.find(key);
+        if (it != g_split_cache.end()) {
+            o.cell_split = it->second;
+            return build_one(d, L, n_per_level, pts_dev, h_per_level, &o, st, out);
+        }
+    }
+    ms_hierarchy* hs[2] = {nullptr, nullptr};
+    float t[2] = {0.f, 0.f};
+    for (int i = 0; i < 2; ++i) {
+        o.cell_split = i + 1;
+        ms_status s = build_one(d, L, n_per_level, pts_dev, h_per_level, &o, st, &hs[i]);
+        float g = 0.f;
+        if (s == MS_OK) s = geometry_ms(hs[i], st, &g);
+        if (s != MS_OK) {
+            if (hs[0]) ms_destroy(hs[0]);
+            if (hs[1]) ms_destroy(hs[1]);
+            return s;
+        }
+        t[i] = (float)hs[i]->build_ms + g;
+    }
+    const int best = t[1] < t[0] ? 1 : 0;
+    ms_destroy(hs[1 - best]);
+    {
+        std::lock_guard<std::mutex> lk(g_split_mu);
+        g_split_cache[key] = best + 1;
+    }
+    *out = hs[best];
     return MS_OK;
 }
 
@@ -516,6 +601,8 @@ ms_status ms_hierarchy_info(const ms_hierarchy* h, ms_info* info) {
     info->build_ms = h->build_ms;
     for (int l = 0; l < h->L; ++l) info->tpr_A[l] = ms_tpr_of(h, l);
     info->pc_basis = h->pc.nbasis;
+    info->cell_split = h->opts.cell_split > 0 ? h->opts.cell_split : 1;
+    info->solve_ctas_per_sm = h->opts.solve_ctas_per_sm == 1 ? 1 : 2;
     return MS_OK;
 }
 

@@ -266,6 +266,7 @@ struct Precond {
     __half* gt_val = nullptr;    // [nnz] ghat^T values, FP16
     int64_t gt_nnz = 0;
     int fp32_weights = 0;
+    int* tcstat = nullptr;       // status of the tensor-core network (MS_ERR_TIMEOUT if a wait ran out)
     int augment = 4;                     // extra training patches per point (last training)
     uint64_t seed = 2503049140ull;       // seed of the last training
 };
@@ -304,6 +305,11 @@ struct ms_hierarchy {
     double* scal = nullptr;      // published grid sums
     unsigned long long* prof = nullptr;  // device timeline of the solve kernel
     int* pcfb = nullptr;                 // preconditioner fallbacks of the last fit
+    // several blocks of right-hand sides in one launch: per-block barrier words, status and counters
+    // (pbuf, for pbuf_parts blocks) and the blocks' solve arguments (d_args)
+    void* pbuf = nullptr;
+    int pbuf_parts = 0;
+    void* d_args = nullptr;
     unsigned* bar = nullptr;     // barrier words
     int* status = nullptr;       // device status
     int64_t* iters = nullptr;    // per-level iteration counters

@@ -184,6 +184,113 @@ __device__ __forceinline__ void mf_cells(const MFView& v, int l, int64_t c0, int
     }
 }
 
+// ---------------------------------------------------------------- staged form (one CTA per cell)
+//
+// y_i = delta^-d sum_j phi(r_ij) x_j for the points i of one cell, with the candidates j of the
+// (2R+1)^d neighbour cells staged in shared memory: each as a float4 (its offset from the target
+// cell's corner in units of delta, W_j + (c_j - c) cod per axis, and x_j), written once by the
+// whole CTA and then read by every target as a broadcast 128-bit load, so the inner loop has no
+// index arithmetic or global loads.  TPP threads share a target (the largest power of 2 with
+// TPP n_targets <= blockDim, at most 32) and stride over the staged candidates; the partial sums
+// are combined by shuffles in a fixed order.  A neighbourhood larger than the stage is processed
+// in rounds (each thread keeps its target's sum).  Returns false, without writing, for a cell of
+// more than blockDim points (the caller takes the warp form for it).
+constexpr int kMfStage = 1024;  // staged candidates (16 KB)
+
+template <int D, int E, typename Emit>
+__device__ __forceinline__ bool mf_cell_staged(const MFView& v, int l, int64_t cell, const float* x, float4* stage,
+                                               Emit emit) {
+    const MFLevel& g = v.lv[l];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int32_t ts = v.cell_start[g.cell_off + cell], te = v.cell_start[g.cell_off + cell + 1];
+    const int nt = te - ts;
+    if (nt == 0) return true;
+    if (nt > nthr) return false;
+    int tpp = 1;
+    while (tpp < 32 && 2 * tpp * nt <= nthr) tpp *= 2;
+    const int sub = tid & (tpp - 1);
+    const int32_t ti = ts + tid / tpp;
+    const bool ok = tid / tpp < nt;
+    float wi[3] = {0.f, 0.f, 0.f};
+    if (ok)
+        for (int a = 0; a < D; ++a) wi[a] = v.W[a * v.N + ti];
+    int cc[3];
+    demorton(D, (uint32_t)cell, cc);
+    const int R = g.R;
+    const int rz = D >= 3 ? R : 0, ry = D >= 2 ? R : 0;
+    float acc = 0.f;
+    int n = 0;  // staged so far (uniform in the CTA)
+    auto consume = [&]() {
+        __syncthreads();
+        if (ok) {
+#pragma unroll 4
+            for (int k = sub; k < n; k += tpp) {
+                const float4 c = stage[k];
+                const float ex = c.x - wi[0];
+                float r2 = ex * ex;
+                if (D >= 2) {
+                    const float ey = c.y - wi[1];
+                    r2 = fmaf(ey, ey, r2);
+                }
+                if (D >= 3) {
+                    const float ez = c.z - wi[2];
+                    r2 = fmaf(ez, ez, r2);
+                }
+                const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+                acc = fmaf(mf_phi<E>(r, v.c, v.E), c.w, acc);
+            }
+        }
+        __syncthreads();
+        n = 0;
+    };
+    for (int dz = -rz; dz <= rz; ++dz) {
+        const int cz = cc[2] + dz;
+        if (D >= 3 && (cz < 0 || cz >= g.G[2])) continue;
+        for (int dy = -ry; dy <= ry; ++dy) {
+            const int cy = cc[1] + dy;
+            if (D >= 2 && (cy < 0 || cy >= g.G[1])) continue;
+            for (int dx = -R; dx <= R; ++dx) {
+                const int cx = cc[0] + dx;
+                if (cx < 0 || cx >= g.G[0]) continue;
+                const int64_t gid = g.cell_off + morton(D, cx, cy, cz);
+                const int32_t s = v.cell_start[gid], e = v.cell_start[gid + 1];
+                const float ox = (float)dx * g.cod, oy = (float)dy * g.cod, oz = (float)dz * g.cod;
+                for (int32_t j0 = s; j0 < e;) {
+                    if (n == kMfStage) consume();
+                    const int take = min(e - j0, kMfStage - n);
+                    for (int k = tid; k < take; k += nthr) {
+                        const int32_t j = j0 + k;
+                        stage[n + k] = make_float4(v.W[j] + ox, D >= 2 ? v.W[v.N + j] + oy : 0.f,
+                                                   D >= 3 ? v.W[2 * v.N + j] + oz : 0.f, x[j]);
+                    }
+                    n += take;
+                    j0 += take;
+                }
+            }
+        }
+    }
+    if (n > 0) consume();
+    for (int o = tpp >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (ok && sub == 0) emit((int64_t)ti, acc * g.dscale);
+    return true;
+}
+
+template <typename Emit>
+__device__ __forceinline__ bool mf_cell_staged_any(const MFView& v, int l, int64_t cell, const float* x,
+                                                   float4* stage, Emit emit) {
+    if (v.d == 2) {
+        if (v.E == 4) return mf_cell_staged<2, 4>(v, l, cell, x, stage, emit);
+        if (v.E == 6) return mf_cell_staged<2, 6>(v, l, cell, x, stage, emit);
+        return mf_cell_staged<2, 0>(v, l, cell, x, stage, emit);
+    }
+    if (v.d == 3) {
+        if (v.E == 4) return mf_cell_staged<3, 4>(v, l, cell, x, stage, emit);
+        if (v.E == 6) return mf_cell_staged<3, 6>(v, l, cell, x, stage, emit);
+        return mf_cell_staged<3, 0>(v, l, cell, x, stage, emit);
+    }
+    return mf_cell_staged<1, 0>(v, l, cell, x, stage, emit);
+}
+
 // Dispatch on (d, Wendland exponent) to the specialised loop.
 template <typename Emit>
 __device__ __forceinline__ void mf_cells_any(const MFView& v, int l, int64_t c0, int64_t c1, int w, int nw, int TPP,

@@ -26,8 +26,11 @@
 
 #include <cuda_bf16.h>
 
+#include "ms_ff.cuh"
 #include "ms_internal.cuh"
+#include "ms_matfree.cuh"
 #include "ms_scan.cuh"
+#include "ms_tc.cuh"
 
 namespace {
 
@@ -108,18 +111,149 @@ __device__ void nearest_below(const HierView& v, const int64_t* Arp, const int32
     for (int i = 0; i < kPcK; ++i) out[i] = bc[i];
 }
 
-__global__ void k_pc_pattern(HierView v, const int64_t* Arp, const int32_t* Acol, const int32_t* perm, int32_t* nbr) {
-    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= v.N) return;
-    nearest_below(v, Arp, Acol, perm, s, perm[s], nbr + s * kPcK);
+constexpr int kPL = 8;        // candidates a lane holds (rows of up to 32 kPL entries)
+constexpr int kPcCont = 64;   // contenders a warp ranks exactly
+constexpr int kPatW = 4;      // warps per block of the pattern kernels
+
+// nearest_below by a whole warp (every lane calls it; lanes write `out`).  The candidates
+// are first keyed by an FP32 squared distance in units of delta^2, from the level's cell
+// ids and in-cell offsets W (|error| < 4e-6 for |x_c - x_s| < delta): with k16 the 16th
+// smallest FP32 key, every point of the exact pattern has a key <= k16 + 1e-5 (its exact
+// squared distance is at most the 16th smallest one, and k16 is at least that less the
+// error), so only those contenders are ranked, in the order of nearest_below: by their FP32 keys
+// where two differ by more than 1e-5, by key_less on the exact FP64 squared distances otherwise.
+// A row of more than 32 kPL entries, or with more than kPcCont contenders (ties), is left to
+// nearest_below on lane 0.
+__device__ void nearest_below_warp(const HierView& v, const float* __restrict__ W,
+                                   const int32_t* __restrict__ cellid, const int64_t* Arp, const int32_t* Acol,
+                                   const int32_t* perm, int64_t s, int64_t bound, int32_t* out, int lane,
+                                   int32_t* cq, float* kq) {
+    const int64_t b = Arp[s];
+    const int n = (int)(Arp[s + 1] - b);
+    constexpr uint32_t kNone = 0xFFFFFFFFu;  // not a candidate (above every float key)
+    bool serial = n > 32 * kPL;
+    uint32_t key[kPL];
+    int32_t col[kPL], pcol[kPL];
+    if (!serial) {
+        const int l = level_of_row(v.off, v.L, s);
+        const float cod = v.grid[l].cod;
+        int cs[3];
+        demorton(v.d, (uint32_t)__ldg(cellid + s), cs);
+        float ws[3] = {0.f, 0.f, 0.f};
+        for (int a = 0; a < v.d; ++a) ws[a] = __ldg(W + a * v.N + s);
+#pragma unroll
+        for (int i = 0; i < kPL; ++i) {
+            key[i] = kNone;
+            col[i] = -1;
+            pcol[i] = INT_MAX;
+            const int k = lane + 32 * i;
+            if (k < n) {
+                const int32_t c = __ldg(Acol + b + k);
+                const int32_t pc = __ldg(perm + c);
+                if (pc < bound && c != s) {
+                    int cc[3];
+                    demorton(v.d, (uint32_t)__ldg(cellid + c), cc);
+                    float q = 0.f;
+                    for (int a = 0; a < v.d; ++a) {
+                        const float t = __fadd_rn(__fmul_rn(small_int_to_float(cc[a] - cs[a]), cod),
+                                                  __fsub_rn(__ldg(W + a * v.N + c), ws[a]));
+                        q = fmaf(t, t, q);
+                    }
+                    key[i] = __float_as_uint(q);
+                    col[i] = c;
+                    pcol[i] = pc;
+                }
+            }
+        }
+        // k16: sixteen rounds of taking the warp's smallest remaining key
+        uint32_t kk[kPL];
+#pragma unroll
+        for (int i = 0; i < kPL; ++i) kk[i] = key[i];
+        uint32_t k16 = kNone;
+        for (int r = 0; r < kPcK; ++r) {
+            uint32_t mn = kk[0];
+#pragma unroll
+            for (int i = 1; i < kPL; ++i) mn = min(mn, kk[i]);
+            k16 = __reduce_min_sync(0xffffffffu, mn);
+            if (k16 == kNone) break;  // fewer than 16 candidates (warp-uniform)
+            const unsigned holders = __ballot_sync(0xffffffffu, mn == k16);
+            if (lane == __ffs(holders) - 1) {
+                bool done = false;
+#pragma unroll
+                for (int i = 0; i < kPL; ++i)
+                    if (!done && kk[i] == k16) {
+                        kk[i] = kNone;
+                        done = true;
+                    }
+            }
+        }
+        const float t = k16 == kNone ? INFINITY : __fadd_ru(__uint_as_float(k16), 1e-5f);
+        // contenders to the warp's queue
+        int nc = 0;
+#pragma unroll
+        for (int i = 0; i < kPL; ++i) {
+            const bool pass = key[i] != kNone && __uint_as_float(key[i]) <= t;
+            const unsigned mask = __ballot_sync(0xffffffffu, pass);
+            const int pos = nc + __popc(mask & ((1u << lane) - 1u));
+            if (pass && pos < kPcCont) {
+                cq[2 * pos] = col[i];
+                cq[2 * pos + 1] = pcol[i];
+                kq[pos] = __uint_as_float(key[i]);
+            }
+            nc += __popc(mask);
+        }
+        serial = nc > kPcCont;
+        if (!serial) {
+            __syncwarp();
+            // rank of each contender: by the FP32 keys where they are more than 1e-5 apart (then
+            // the exact keys order the same way: each FP32 key is within 4e-6 of its exact value),
+            // else by key_less on the exact FP64 squared distances (near ties only)
+            for (int j = lane; j < nc; j += 32) {
+                const float qj = kq[j];
+                const int32_t cj = cq[2 * j], pj = cq[2 * j + 1];
+                double dj = -1.0;
+                int rank = 0;
+                for (int o = 0; o < nc; ++o) {
+                    if (o == j) continue;
+                    const float qo = kq[o];
+                    if (fabsf(qo - qj) > 1e-5f) {
+                        rank += qo < qj ? 1 : 0;
+                    } else {
+                        if (dj < 0.0) dj = dist2_rn(v, cj, s);
+                        rank += key_less(dist2_rn(v, cq[2 * o], s), cq[2 * o + 1], dj, pj) ? 1 : 0;
+                    }
+                }
+                if (rank < kPcK) out[rank] = cj;
+            }
+            if (lane < kPcK && lane >= nc) out[lane] = -1;
+        }
+    }
+    if (serial && lane == 0) nearest_below(v, Arp, Acol, perm, s, bound, out);
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kPatW * 32, 5) k_pc_pattern(HierView v, const float* W, const int32_t* cellid,
+                                                          const int64_t* Arp, const int32_t* Acol,
+                                                          const int32_t* perm, int32_t* nbr) {
+    __shared__ int32_t cq[kPatW][2 * kPcCont];
+    __shared__ float kq[kPatW][kPcCont];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t s = blockIdx.x * (int64_t)kPatW + w;
+    if (s >= v.N) return;  // warp-uniform
+    nearest_below_warp(v, W, cellid, Arp, Acol, perm, s, __ldg(perm + s), nbr + s * kPcK, lane, cq[w], kq[w]);
 }
 
 // Neighbours of training patch i: centre rows[i], input-index bound bounds[i]; out [n][16].
-__global__ void k_pc_patches(HierView v, const int64_t* Arp, const int32_t* Acol, const int32_t* perm,
-                             const int64_t* rows, const int64_t* bounds, int64_t n, int32_t* out) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    nearest_below(v, Arp, Acol, perm, rows[i], bounds[i], out + i * kPcK);
+__global__ void __launch_bounds__(kPatW * 32, 5) k_pc_patches(HierView v, const float* W, const int32_t* cellid,
+                                                          const int64_t* Arp, const int32_t* Acol,
+                                                          const int32_t* perm, const int64_t* rows,
+                                                          const int64_t* bounds, int64_t n, int32_t* out) {
+    __shared__ int32_t cq[kPatW][2 * kPcCont];
+    __shared__ float kq[kPatW][kPcCont];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = blockIdx.x * (int64_t)kPatW + w;
+    if (i >= n) return;  // warp-uniform
+    nearest_below_warp(v, W, cellid, Arp, Acol, perm, rows[i], bounds[i], out + i * kPcK, lane, cq[w], kq[w]);
 }
 
 // ---------------------------------------------------------------- exact rows (FP64)
@@ -283,9 +417,10 @@ __global__ void k_pc_features(HierView v, const int32_t* nbr, const int64_t* row
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     float z[kPcK * 3];
-    const int c = v.d == 1 ? pc_features<1>(v, nbr + i * kPcK, rows[i], z)
-                : v.d == 2 ? pc_features<2>(v, nbr + i * kPcK, rows[i], z)
-                           : pc_features<3>(v, nbr + i * kPcK, rows[i], z);
+    const int64_t s = rows ? rows[i] : i;  // no rows: the pattern of sorted row i
+    const int c = v.d == 1 ? pc_features<1>(v, nbr + i * kPcK, s, z)
+                : v.d == 2 ? pc_features<2>(v, nbr + i * kPcK, s, z)
+                           : pc_features<3>(v, nbr + i * kPcK, s, z);
     const int nin = kPcK * v.d;
     for (int k = 0; k < nin; ++k) Z[i * nin + k] = z[k];
     cnt[i] = c;
@@ -393,7 +528,6 @@ __host__ __device__ inline InferLayout infer_layout(int nin, int m) {
 }
 
 constexpr int kCandBS = 128;  // threads per block of k_pc_cand
-constexpr int kCombW = 8;     // warps per block of k_pc_combine
 
 inline size_t cand_smem(int nin, int m) { return sizeof(float) * (size_t)infer_layout(nin, m).P; }
 
@@ -489,162 +623,443 @@ __global__ void __launch_bounds__(kCandBS) k_pc_cand(HierView v, const int32_t* 
     }
 }
 
-// k_pc_combine, one warp per point: the factorised-sparse-approximate-inverse row in the span
-// of the point's candidates,
+// ---------------------------------------------------------------- network on the tensor cores
+//
+// k_pc_mlp: the network's candidate rows for tiles of 128 points on the fifth-generation tensor
+// cores.  The three layers are MMAs with M = 128 points (one tensor-memory lane each), BF16
+// operands and FP32 accumulators in tensor memory: [128 x nin] x W1^T -> 64 columns, then
+// [128 x 64] x W2^T -> 64, then [128 x 64] x W3^T -> 17 m (at most 256 columns per MMA).  The
+// weights are BF16-valued (the inference copy), so they are exact operands; each layer's input
+// is split into hi + lo BF16 parts (16 significant bits) and both parts are multiplied, so the
+// products carry the FP32 activations to about 2^-17.  Biases, ReLU and the output scaling
+// u_1 = mu + sigma o_1, u_k = sigma o_k run in the epilogues, one thread per point, which read
+// the accumulators with tcgen05.ld and write the next layer's operand to shared memory.  A CTA
+// holds the weights for its whole life and walks tiles; two CTAs share an SM (256 tensor-memory
+// columns each), so one's MMAs overlap the other's epilogues.
+constexpr int kMlpRows = 128;            // points per tile (the MMA's M)
+constexpr uint32_t kMlpCols = 256;       // tensor-memory columns per CTA
+constexpr int kMlpSmemMin = 100 * 1024;  // at least this much shared memory: <= 2 CTAs per SM
+constexpr unsigned long long kMlpWaitNs = 2000000000ull;  // bound on one wait for the MMAs
+
+struct MlpSmem {  // byte offsets into dynamic shared memory
+    int n3p, w1, w2, w3, act, b1, b2, b3, ms, mbar, slot, total;
+};
+__host__ __device__ inline MlpSmem mlp_smem(int nin, int m) {
+    MlpSmem S;
+    S.n3p = (kPcOut * m + 15) & ~15;  // W3 rows, a multiple of 16 (the MMA's N step)
+    S.w1 = 0;
+    S.w2 = S.w1 + kPcHidden * nin * 2;
+    S.w3 = S.w2 + kPcHidden * kPcHidden * 2;
+    S.act = S.w3 + S.n3p * kPcHidden * 2;
+    S.b1 = S.act + 2 * kMlpRows * kPcHidden * 2;  // hi and lo operands of [128 x 64]
+    S.b2 = S.b1 + kPcHidden * 4;
+    S.b3 = S.b2 + kPcHidden * 4;
+    S.ms = S.b3 + S.n3p * 4;
+    S.mbar = (S.ms + 2 * kPcOut * 4 + 15) & ~15;
+    S.slot = S.mbar + 8;
+    S.total = S.slot + 8;
+    if (S.total < kMlpSmemMin) S.total = kMlpSmemMin;
+    return S;
+}
+
+// hi + lo BF16 parts of eight FP32 values, as two 16-byte words
+__device__ __forceinline__ void split8_bf16(const float* x, uint4& hi, uint4& lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat16 a0 = __float2bfloat16_rn(x[2 * i]), a1 = __float2bfloat16_rn(x[2 * i + 1]);
+        const __nv_bfloat16 r0 = __float2bfloat16_rn(x[2 * i] - __bfloat162float(a0));
+        const __nv_bfloat16 r1 = __float2bfloat16_rn(x[2 * i + 1] - __bfloat162float(a1));
+        h[i] = (uint32_t)__bfloat16_as_ushort(a0) | ((uint32_t)__bfloat16_as_ushort(a1) << 16);
+        l[i] = (uint32_t)__bfloat16_as_ushort(r0) | ((uint32_t)__bfloat16_as_ushort(r1) << 16);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Waits (bounded) for the mbarrier's phase; the result is the same in every thread.
+__device__ __forceinline__ bool mlp_wait(uint64_t* mbar, uint32_t parity) {
+    const unsigned long long t0 = ms_globaltimer();
+    bool ok = true;
+    while (!tc_mbar_try_wait(mbar, parity))
+        if (ms_globaltimer() - t0 > kMlpWaitNs) {
+            ok = false;
+            break;
+        }
+    return __syncthreads_and(ok) != 0;
+}
+
+__global__ void __launch_bounds__(kMlpRows) k_pc_mlp(const float* __restrict__ theta, int nin, int m,
+                                                     const float* __restrict__ musig, const float* __restrict__ Zc,
+                                                     const int32_t* __restrict__ cntc, int64_t N, float* __restrict__ Uc,
+                                                     int* status) {
+    extern __shared__ __align__(128) unsigned char smb[];
+    const MlpSmem S = mlp_smem(nin, m);
+    const NetLayout NL = net_layout(nin, m);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int nout = NL.nout, n3p = S.n3p;
+    float* b1 = reinterpret_cast<float*>(smb + S.b1);
+    float* b2 = reinterpret_cast<float*>(smb + S.b2);
+    float* b3 = reinterpret_cast<float*>(smb + S.b3);
+    float* ms = reinterpret_cast<float*>(smb + S.ms);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smb + S.mbar);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(smb + S.slot);
+    // the weights (BF16-valued FP32, so the BF16 copies are exact) in the K-major operand layout
+    for (int i = tid; i < kPcHidden * nin; i += kMlpRows)
+        *reinterpret_cast<__nv_bfloat16*>(smb + S.w1 + tc_kmajor_offset(nin, i / nin, i % nin)) =
+            __float2bfloat16_rn(theta[NL.oW1 + i]);
+    for (int i = tid; i < kPcHidden * kPcHidden; i += kMlpRows)
+        *reinterpret_cast<__nv_bfloat16*>(smb + S.w2 + tc_kmajor_offset(kPcHidden, i / kPcHidden, i % kPcHidden)) =
+            __float2bfloat16_rn(theta[NL.oW2 + i]);
+    for (int i = tid; i < n3p * kPcHidden; i += kMlpRows) {
+        const int r = i / kPcHidden;
+        *reinterpret_cast<__nv_bfloat16*>(smb + S.w3 + tc_kmajor_offset(kPcHidden, r, i % kPcHidden)) =
+            __float2bfloat16_rn(r < nout ? theta[NL.oW3 + i] : 0.f);
+    }
+    for (int i = tid; i < kPcHidden; i += kMlpRows) {
+        b1[i] = theta[NL.ob1 + i];
+        b2[i] = theta[NL.ob2 + i];
+    }
+    for (int i = tid; i < n3p; i += kMlpRows) b3[i] = i < nout ? theta[NL.ob3 + i] : 0.f;
+    for (int i = tid; i < 2 * kPcOut; i += kMlpRows) ms[i] = musig[i];
+    if (tid == 0) tc_mbar_init(mbar, 1);
+    if (warp == 0) tc_alloc(slot, kMlpCols);
+    tc_fence_proxy();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *slot;
+    const uint32_t tq = tbase + ((uint32_t)(warp * 32) << 16);  // this warp's quarter of the lanes
+    const uint32_t a_hi = tc_smem_addr(smb + S.act), a_lo = a_hi + kMlpRows * kPcHidden * 2;
+    const uint32_t w1 = tc_smem_addr(smb + S.w1), w2 = tc_smem_addr(smb + S.w2), w3 = tc_smem_addr(smb + S.w3);
+    // K-direction core stride 128 bytes; row-group strides 16 Kd (Kd = 64, or nin for W1)
+    constexpr uint32_t lbo = 128, sboH = 16 * kPcHidden;
+    const uint32_t sbo1 = 16u * (uint32_t)nin;
+    const int nA = n3p < 256 ? n3p : 256;  // layer 3 in at most two MMA widths
+    uint32_t phase = 0;
+    bool ok = true;
+    const int64_t ntiles = (N + kMlpRows - 1) / kMlpRows;
+    // one layer's MMAs: D[cols] = [a_hi + a_lo] x B^T over K = kd (16 per instruction)
+    auto issue = [&](uint32_t dcol, uint32_t b0, uint32_t sboB, int kd, int n) {
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t id = tc_idesc_bf16(kMlpRows, n);
+            for (int ks = 0; ks < kd / 16; ++ks) {  // K = 16 a step: two core matrices
+                const uint64_t bd = tc_sdesc(b0 + ks * 2 * lbo, lbo, sboB);
+                tc_mma_bf16(tbase + dcol, tc_sdesc(a_hi + ks * 2 * lbo, lbo, sboH), bd, id, ks > 0 ? 1u : 0u);
+                tc_mma_bf16(tbase + dcol, tc_sdesc(a_lo + ks * 2 * lbo, lbo, sboH), bd, id, 1u);
+            }
+            tc_commit(mbar);
+        }
+        ok = mlp_wait(mbar, phase);
+        phase ^= 1u;
+        tc_fence_after();
+    };
+    // hidden-layer epilogue: relu(D + b) split into the next operand (64 columns)
+    auto hidden = [&](uint32_t dcol, const float* bias) {
+#pragma unroll 1
+        for (int c = 0; c < kPcHidden; c += 16) {
+            uint32_t r[16];
+            tc_ld16(tq + dcol + c, r);
+            tc_wait_ld();
+            float x[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) x[j] = fmaxf(__uint_as_float(r[j]) + bias[c + j], 0.f);
+            uint4 hi, lo;
+            split8_bf16(x, hi, lo);
+            *reinterpret_cast<uint4*>(smb + S.act + tc_kmajor_offset(kPcHidden, tid, c)) = hi;
+            *reinterpret_cast<uint4*>(smb + S.act + kMlpRows * kPcHidden * 2 + tc_kmajor_offset(kPcHidden, tid, c)) = lo;
+            split8_bf16(x + 8, hi, lo);
+            *reinterpret_cast<uint4*>(smb + S.act + tc_kmajor_offset(kPcHidden, tid, c + 8)) = hi;
+            *reinterpret_cast<uint4*>(smb + S.act + kMlpRows * kPcHidden * 2 + tc_kmajor_offset(kPcHidden, tid, c + 8)) =
+                lo;
+        }
+        tc_fence_proxy();
+        tc_fence_before();
+        __syncthreads();
+    };
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int64_t s = tile * kMlpRows + tid;
+        const bool live = s < N;
+        // layer-1 operand: the point's features, hi and lo parts
+        for (int c = 0; c < nin; c += 8) {
+            float x[8];
+            if (live) {
+                const float4 p = __ldg(reinterpret_cast<const float4*>(Zc + s * nin + c));
+                const float4 q = __ldg(reinterpret_cast<const float4*>(Zc + s * nin + c + 4));
+                x[0] = p.x; x[1] = p.y; x[2] = p.z; x[3] = p.w; x[4] = q.x; x[5] = q.y; x[6] = q.z; x[7] = q.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) x[j] = 0.f;
+            }
+            uint4 hi, lo;
+            split8_bf16(x, hi, lo);
+            *reinterpret_cast<uint4*>(smb + S.act + tc_kmajor_offset(kPcHidden, tid, c)) = hi;
+            *reinterpret_cast<uint4*>(smb + S.act + kMlpRows * kPcHidden * 2 + tc_kmajor_offset(kPcHidden, tid, c)) = lo;
+        }
+        const int cnt = live ? __ldg(cntc + s) : 0;
+        tc_fence_proxy();
+        tc_fence_before();
+        __syncthreads();
+        issue(0, w1, sbo1, nin, kPcHidden);
+        if (!ok) break;
+        hidden(0, b1);
+        issue(kPcHidden, w2, sboH, kPcHidden, kPcHidden);
+        if (!ok) break;
+        hidden(kPcHidden, b2);
+        // layer 3: columns [0, nA), then (17 m > 256) [256, n3p) into the same tensor memory
+        for (int r0 = 0; r0 < n3p; r0 += nA) {
+            const int n = n3p - r0 < nA ? n3p - r0 : nA;
+            if (r0 > 0) {  // every thread has read the previous columns
+                tc_fence_before();
+                __syncthreads();
+            }
+            issue(0, w3 + (uint32_t)(r0 / 8) * sboH, sboH, kPcHidden, n);
+            if (!ok) break;
+#pragma unroll 1
+            for (int c = 0; c < n; c += 16) {
+                uint32_t r[16];
+                tc_ld16(tq + c, r);
+                tc_wait_ld();
+                if (live) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int o = r0 + c + j;  // output 17 k + a
+                        if (o < nout) {
+                            const int k = o / kPcOut, a = o - kPcOut * k;
+                            const float acc = __uint_as_float(r[j]) + b3[o];
+                            Uc[s * nout + o] = a <= cnt ? fmaf(ms[kPcOut + a], acc, k == 0 ? ms[a] : 0.f) : 0.f;
+                        }
+                    }
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (!ok && tid == 0) atomicExch(status, (int)MS_ERR_TIMEOUT);
+    if (!ok) mlp_wait(mbar, phase ^ 1u);  // one more bounded wait for the MMAs still in flight
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tc_dealloc(tbase, kMlpCols);
+}
+
+// k_pc_combine, one half-warp per point: the factorised-sparse-approximate-inverse row in the
+// span of the point's candidates,
 //   g = U y / sqrt(q),  y = (S + 1e-6 diag(S))^-1 U^T e_1,  S = U^T K U,  q = e_1^T U y,
 // K = phi(|z_a - z_b|) on the patch (self at the origin), or, for a patch of n = cnt + 1 <= m
 // points, the exact row (S = K, U = I, no ridge); g^T K g = 1 less the ridge's shift and
 // g_self = sqrt(q) > 0.  (A failed factorisation, or q <= 0: the diagonal row e_1 / sqrt(phi(0)).)
-// K, T = K U and S = U^T T are formed lane-parallel in the warp's shared memory; S is
-// Jacobi-scaled to unit diagonal (the ridge becomes 1e-6 I) and factorised in FP32 by a
-// right-looking Cholesky, one column per step, lanes over the trailing entries.
-// Writes the scale-free row (FP16) and its pattern, or ghat itself for inspection.
-__global__ void __launch_bounds__(kCombW * 32) k_pc_combine(HierView v, const int32_t* nbr, int m, const float* Uc,
-                                                            const float* Zc, const int32_t* cntc, __half* gval,
-                                                            int32_t* gcol, float* ghat_out) {
-    struct WarpBuf {
-        float U[kPcOut * kPcMaxBasis];  // [a][k]
-        float K[kPcOut * kPcOut];
-        float T[kPcOut * kPcMaxBasis];  // [a][l] = (K U)_al
-        float S[kPcMaxBasis * kPcMaxBasis];
-        float z[kPcK * 3];
-        float y[kPcMaxBasis];
-    };
-    __shared__ WarpBuf wb[kCombW];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpBuf& B = wb[w];
-    const int64_t s = blockIdx.x * (int64_t)kCombW + w;
-    if (s >= v.N) return;  // warp-uniform
+// Lane l of the half owns column l of S in registers: t = K u_l from the patch matrix in
+// shared memory (rows read as broadcast float4s), S_kl = u_k . t, then S is Jacobi-scaled to
+// unit diagonal (the ridge becomes 1e-6 I) and factorised by a right-looking Cholesky over
+// the lanes' columns: at step k every lane takes its multiplier L_jk from its own column
+// (S is kept symmetric, so S_kj = S_jk), the multipliers are broadcast by shuffles, and the
+// forward substitution L w = b runs alongside; q = |w|^2, and L^T y = w by half-warp sums.
+// Columns l >= m (or >= n) are identity columns.  Writes the scale-free row (FP16) and its
+// pattern, or ghat itself for inspection.
+constexpr int kCombPts = 8;  // points per block of k_pc_combine
+
+struct CombBuf {
+    float K[kPcOut][20];           // patch matrix, rows padded to 20 floats (16-byte aligned)
+    float U[kPcMaxBasis][20];      // candidate k's entries a = 0..16, zero-padded
+    float z[kPcK * 3];
+};
+// 2832 bytes = 16 (mod 128): the two points of a warp broadcast from different banks
+static_assert(sizeof(CombBuf) % 128 == 16, "CombBuf bank offset");
+
+__global__ void __launch_bounds__(kCombPts * 16) k_pc_combine(HierView v, const int32_t* nbr, int m, const float* Uc,
+                                                              const float* Zc, const int32_t* cntc, __half* gval,
+                                                              int32_t* gcol, float* ghat_out) {
+    __shared__ __align__(16) CombBuf cb[kCombPts];
+    __shared__ uint16_t pairs[kPcOut * kPcK / 2];  // the 136 pairs a < b of 17 points: a | b << 8
+    for (int i = threadIdx.x; i < kPcOut * kPcK / 2; i += blockDim.x) {
+        int a = 0, rem = i;
+        while (rem >= kPcK - a) { rem -= kPcK - a; ++a; }
+        pairs[i] = (uint16_t)(a | ((a + 1 + rem) << 8));
+    }
+    __syncthreads();
+    const int hp = threadIdx.x >> 4, l = threadIdx.x & 15;
+    const unsigned hmask = 0xFFFFu << (threadIdx.x & 16);  // this half-warp's lanes
+    CombBuf& B = cb[hp];
+    const int64_t s = blockIdx.x * (int64_t)kCombPts + hp;
+    if (s >= v.N) return;  // the whole half-warp (its lanes synchronise among themselves only)
     const int d = v.d, nin = kPcK * d, nout = kPcOut * m;
     const int cnt = cntc[s];
-    const bool exact = cnt + 1 <= m;
-    const int nn = exact ? cnt + 1 : m;  // order of the system
-    for (int i = lane; i < nout; i += 32) {
-        const int k = i / kPcOut, a = i % kPcOut;
-        B.U[a * kPcMaxBasis + k] = Uc[s * (int64_t)nout + i];
-    }
-    for (int i = lane; i < nin; i += 32) B.z[i] = Zc[s * (int64_t)nin + i];
-    __syncwarp();
-    const float phi0 = (float)v.w.c[0];
-    // K on the patch (n = cnt + 1 points): the pairs a < b over the lanes, mirrored, phi(0) on
-    // the diagonal (entries past the patch are not read)
     const int np = cnt + 1;
-    for (int i = lane; i < np * (np - 1) / 2; i += 32) {
-        int a = 0, rem = i;
-        while (rem >= np - 1 - a) { rem -= np - 1 - a; ++a; }
-        const int b = a + 1 + rem;
-        float r2 = 0.f;
-        for (int ax = 0; ax < d; ++ax) {
-            const float u = (a > 0 ? B.z[(a - 1) * d + ax] : 0.f) - B.z[(b - 1) * d + ax];
-            r2 = fmaf(u, u, r2);
-        }
-        // FP32 entries need no correctly rounded sqrt: r = r2 / sqrt(r2)
-        const float kab = wendland_eval<float>(v.w, r2 * rsqrtf(fmaxf(r2, 1e-30f)));
-        B.K[a * kPcOut + b] = kab;
-        B.K[b * kPcOut + a] = kab;
-    }
-    if (lane < np) B.K[lane * kPcOut + lane] = phi0;
-    __syncwarp();
-    if (exact) {
-        for (int i = lane; i < nn * nn; i += 32) B.S[(i / nn) * kPcMaxBasis + i % nn] = B.K[(i / nn) * kPcOut + i % nn];
-    } else {
-        for (int i = lane; i < (cnt + 1) * m; i += 32) {  // T = K U on the patch's rows
-            const int a = i / m, l = i % m;
-            float t = 0.f;
-            for (int b = 0; b <= cnt; ++b) t = fmaf(B.K[a * kPcOut + b], B.U[b * kPcMaxBasis + l], t);
-            B.T[a * kPcMaxBasis + l] = t;
-        }
-        __syncwarp();
-        for (int i = lane; i < m * (m + 1) / 2; i += 32) {  // S = U^T T (upper triangle, mirrored)
-            int k = 0, rem = i;
-            while (rem >= m - k) { rem -= m - k; ++k; }
-            const int l = k + rem;
-            float t = 0.f;
-            for (int a = 0; a <= cnt; ++a) t = fmaf(B.U[a * kPcMaxBasis + k], B.T[a * kPcMaxBasis + l], t);
-            B.S[k * kPcMaxBasis + l] = t;
-            B.S[l * kPcMaxBasis + k] = t;
+    const bool exact = np <= m;
+    const float phi0 = (float)v.w.c[0];
+    {
+        float4* K4 = reinterpret_cast<float4*>(&B.K[0][0]);
+        for (int i = l; i < kPcOut * 5; i += 16) K4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!exact) {
+            float4* U4 = reinterpret_cast<float4*>(&B.U[0][0]);
+            for (int i = l; i < kPcMaxBasis * 5; i += 16) U4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    __syncwarp();
-    // Jacobi scaling D = diag(S)^-1/2 and the right-hand side b = D (U^T e_1 or e_1): lane k < nn
-    const float ridge = exact ? 0.f : kPcRidge;
-    const float skk = lane < nn ? B.S[lane * kPcMaxBasis + lane] : 1.f;
-    const float dk = rsqrtf(fmaxf(skk, 1e-30f));
-    const float bk = lane < nn ? (exact ? (lane == 0 ? 1.f : 0.f) : B.U[lane]) * dk : 0.f;
-    bool ok = __all_sync(0xffffffffu, skk > 0.f);
-    if (lane < kPcMaxBasis) B.y[lane] = dk;
-    __syncwarp();
-    for (int i = lane; i < nn * nn; i += 32) {
-        const int r = i / nn, c = i % nn;
-        float& e = B.S[r * kPcMaxBasis + c];
-        e = e * B.y[r] * B.y[c] + (r == c ? ridge : 0.f);
-    }
-    __syncwarp();
-    // right-looking Cholesky S = L L^T (L in the lower triangle of S)
-    for (int k = 0; k < nn; ++k) {
-        const float pk = B.S[k * kPcMaxBasis + k];
-        ok = ok && pk > 0.f;
-        const float lkk = sqrtf(fmaxf(pk, 1e-30f)), inv = 1.f / lkk;
-        __syncwarp();
-        if (lane == 0) B.S[k * kPcMaxBasis + k] = lkk;
-        for (int i = k + 1 + lane; i < nn; i += 32) B.S[i * kPcMaxBasis + k] *= inv;
-        __syncwarp();
-        const int rem = nn - k - 1;
-        for (int t = lane; t < rem * rem; t += 32) {
-            const int i = k + 1 + t / rem, j = k + 1 + t % rem;
-            if (j <= i) B.S[i * kPcMaxBasis + j] -= B.S[i * kPcMaxBasis + k] * B.S[j * kPcMaxBasis + k];
+    __syncwarp(hmask);
+    if (!exact)
+        for (int i = l; i < nout; i += 16) B.U[i / kPcOut][i % kPcOut] = __ldg(Uc + s * (int64_t)nout + i);
+    for (int i = l; i < nin; i += 16) B.z[i] = __ldg(Zc + s * (int64_t)nin + i);
+    __syncwarp(hmask);
+    for (int i = l; i < kPcOut * kPcK / 2; i += 16) {
+        const int a = pairs[i] & 0xFF, b = pairs[i] >> 8;
+        if (b < np) {
+            float r2 = 0.f;
+            for (int ax = 0; ax < d; ++ax) {
+                const float u = (a > 0 ? B.z[(a - 1) * d + ax] : 0.f) - B.z[(b - 1) * d + ax];
+                r2 = fmaf(u, u, r2);
+            }
+            // FP32 entries need no correctly rounded sqrt: r = r2 / sqrt(r2)
+            const float kab = wendland_eval<float>(v.w, r2 * rsqrtf(fmaxf(r2, 1e-30f)));
+            B.K[a][b] = kab;
+            B.K[b][a] = kab;
         }
-        __syncwarp();
     }
-    // L w = b (lane k holds w_k), then L^T yt = w; q = b^T yt, y = D yt
-    float wv = bk;
-    for (int k = 0; k < nn; ++k) {
-        const float wk = __shfl_sync(0xffffffffu, wv, k) / B.S[k * kPcMaxBasis + k];
-        if (lane == k) wv = wk;
-        if (lane > k && lane < nn) wv -= B.S[lane * kPcMaxBasis + k] * wk;
-    }
-    for (int k = nn - 1; k >= 0; --k) {
-        const float yk = __shfl_sync(0xffffffffu, wv, k) / B.S[k * kPcMaxBasis + k];
-        if (lane == k) wv = yk;
-        if (lane < k) wv -= B.S[k * kPcMaxBasis + lane] * yk;
-    }
-    float qp = lane < nn ? bk * wv : 0.f;
+    if (l < np) B.K[l][l] = phi0;
+    if (l == 0 && np == kPcOut) B.K[kPcK][kPcK] = phi0;
+    __syncwarp(hmask);
+
+    // column l of S (identity past m, or past n for the exact row) and b_l
+    float sc[kPcMaxBasis];
+    float diag, bl;
+    if (!exact) {
+        float u[20];
+        {
+            const float4* ur = reinterpret_cast<const float4*>(B.U[l]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) qp += __shfl_xor_sync(0xffffffffu, qp, o);
-    ok = ok && qp > 0.f && isfinite(qp);
-    const float yv = lane < nn ? wv * dk : 0.f;
-    __syncwarp();
-    if (lane < kPcMaxBasis) B.y[lane] = yv;
-    __syncwarp();
-    // g_a = (U y)_a / sqrt(q) for lane a (exact: y_a / sqrt(q))
-    float ga = 0.f;
-    if (lane <= cnt && lane < kPcOut) {
-        if (exact) {
-            ga = B.y[lane];
-        } else {
-            for (int k = 0; k < m; ++k) ga = fmaf(B.U[lane * kPcMaxBasis + k], B.y[k], ga);
+            for (int j = 0; j < 5; ++j) {
+                const float4 q = ur[j];
+                u[4 * j] = q.x; u[4 * j + 1] = q.y; u[4 * j + 2] = q.z; u[4 * j + 3] = q.w;
+            }
         }
-        ga *= ok ? rsqrtf(qp) : 0.f;
+        float t[20];
+#pragma unroll
+        for (int a = 0; a < 20; ++a) t[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < kPcOut; ++a) {
+            const float4* kr = reinterpret_cast<const float4*>(B.K[a]);
+            float acc = 0.f;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                const float4 q = kr[j];
+                acc = fmaf(q.x, u[4 * j], acc);
+                acc = fmaf(q.y, u[4 * j + 1], acc);
+                acc = fmaf(q.z, u[4 * j + 2], acc);
+                acc = fmaf(q.w, u[4 * j + 3], acc);
+            }
+            t[a] = acc;
+        }
+        diag = 0.f;
+#pragma unroll
+        for (int a = 0; a < kPcOut; ++a) diag = fmaf(u[a], t[a], diag);
+#pragma unroll
+        for (int k = 0; k < kPcMaxBasis; ++k) {
+            const float4* ur = reinterpret_cast<const float4*>(B.U[k]);
+            float acc = 0.f;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                const float4 q = ur[j];
+                acc = fmaf(q.x, t[4 * j], acc);
+                acc = fmaf(q.y, t[4 * j + 1], acc);
+                acc = fmaf(q.z, t[4 * j + 2], acc);
+                acc = fmaf(q.w, t[4 * j + 3], acc);
+            }
+            sc[k] = (k < m && l < m) ? acc : (k == l ? 1.f : 0.f);
+        }
+        if (l >= m) diag = 1.f;
+        bl = l < m ? u[0] : 0.f;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kPcMaxBasis; ++k) sc[k] = (k < np && l < np) ? B.K[k][l] : (k == l ? 1.f : 0.f);
+        diag = l < np ? phi0 : 1.f;
+        bl = l == 0 ? 1.f : 0.f;
     }
-    if (!ok) ga = lane == 0 ? rsqrtf(phi0) : 0.f;
-    // lane a holds entry a of the row (self, then the present neighbours in slot order); lane
-    // L = 1..16 writes pattern slot L - 1, whose entry is 1 + (present slots before it)
-    const int32_t c = lane >= 1 && lane <= kPcK ? nbr[s * kPcK + lane - 1] : -1;
-    const unsigned present = __ballot_sync(0xffffffffu, c >= 0);
-    const int e = c >= 0 ? 1 + __popc(present & ((1u << lane) - 1u)) : 0;
-    const float gslot = __shfl_sync(0xffffffffu, ga, e);
+    // Jacobi scaling D = diag(S)^-1/2 (ridge on the scaled diagonal), b' = D b
+    const float ridge = exact ? 0.f : kPcRidge;
+    const float dl = rsqrtf(fmaxf(diag, 1e-30f));
+    bool ok = (__ballot_sync(hmask, !(diag > 0.f)) & hmask) == 0u;
+    float dk[kPcMaxBasis], w[kPcMaxBasis];
+#pragma unroll
+    for (int k = 0; k < kPcMaxBasis; ++k) {
+        dk[k] = __shfl_sync(hmask, dl, k, 16);
+        w[k] = __shfl_sync(hmask, bl * dl, k, 16);
+        sc[k] = sc[k] * dk[k] * dl + (k == l ? ridge : 0.f);
+    }
+    // Cholesky with the forward substitution L w = b'
+    float lkk[kPcMaxBasis], lrow[kPcMaxBasis];
+#pragma unroll
+    for (int k = 0; k < kPcMaxBasis; ++k) {
+        const float piv = __shfl_sync(hmask, sc[k], k, 16);
+        ok = ok && piv > 0.f;
+        const float dkk = sqrtf(fmaxf(piv, 1e-30f)), inv = 1.f / dkk;
+        lkk[k] = dkk;
+        const float c = sc[k] * inv;  // lane j > k: L_jk
+        lrow[k] = c;
+        w[k] *= inv;
+#pragma unroll
+        for (int i = k + 1; i < kPcMaxBasis; ++i) {
+            const float Li = __shfl_sync(hmask, c, i, 16);
+            sc[i] = fmaf(-Li, c, sc[i]);
+            w[i] = fmaf(-Li, w[k], w[i]);
+        }
+    }
+    float q = 0.f;
+#pragma unroll
+    for (int k = 0; k < kPcMaxBasis; ++k) q = fmaf(w[k], w[k], q);  // q = b'^T S'^-1 b' = |w|^2
+    ok = ok && q > 0.f && isfinite(q);
+    // L^T y' = w, then y = D y' (yv); lane l keeps y'_l
+    float yown = 0.f, yv[kPcMaxBasis];
+#pragma unroll
+    for (int k = kPcMaxBasis - 1; k >= 0; --k) {
+        float part = l > k ? lrow[k] * yown : 0.f;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(hmask, part, o, 16);
+        const float yk = (w[k] - part) / lkk[k];
+        if (l == k) yown = yk;
+        yv[k] = yk * dk[k];
+    }
+    // g_a = (U y)_a / sqrt(q): lane l entry a = l, lane 0 also entry 16 (exact: y_a / sqrt(q))
+    float ga = 0.f, g16 = 0.f;
+    if (exact) {
+        ga = l < np ? yown * dl : 0.f;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kPcMaxBasis; ++k)
+            if (k < m) ga = fmaf(B.U[k][l], yv[k], ga);
+        if (l == 0)
+#pragma unroll
+            for (int k = 0; k < kPcMaxBasis; ++k)
+                if (k < m) g16 = fmaf(B.U[k][kPcK], yv[k], g16);
+        if (l > cnt) ga = 0.f;
+        if (cnt < kPcK) g16 = 0.f;
+    }
+    const float sq = ok ? rsqrtf(q) : 0.f;
+    ga *= sq;
+    g16 *= sq;
+    if (!ok) {
+        ga = l == 0 ? rsqrtf(phi0) : 0.f;
+        g16 = 0.f;
+    }
+    // lane l writes pattern slot l, whose entry is 1 + (present slots before it)
+    const int32_t c = nbr[s * kPcK + l];
+    const unsigned present = (__ballot_sync(hmask, c >= 0) >> (threadIdx.x & 16)) & 0xFFFFu;
+    const int e = 1 + __popc(present & ((1u << l) - 1u));
+    const float ge = __shfl_sync(hmask, ga, e & 15, 16);
+    const float gl = __shfl_sync(hmask, g16, 0, 16);
+    const float gslot = c >= 0 ? (e == kPcK ? gl : ge) : 0.f;
     if (ghat_out) {
-        if (lane == 0) ghat_out[s * kPcOut] = ga;
-        else if (lane <= kPcK) ghat_out[s * kPcOut + lane] = c >= 0 ? gslot : 0.f;
+        if (l == 0) ghat_out[s * kPcOut] = ga;
+        ghat_out[s * kPcOut + 1 + l] = gslot;
         return;
     }
-    if (lane == 0) {
+    if (l == 0) {
         gcol[s] = (int32_t)s;
         gval[s] = __float2half_rn(ga);
-    } else if (lane <= kPcK) {
-        gcol[(int64_t)lane * v.N + s] = c;
-        gval[(int64_t)lane * v.N + s] = __float2half_rn(c >= 0 ? gslot : 0.f);
     }
+    gcol[(int64_t)(1 + l) * v.N + s] = c;
+    gval[(int64_t)(1 + l) * v.N + s] = __float2half_rn(gslot);
 }
 
 // SplitMix64 output function (Steele, Lea and Flood 2014) of counter x: per-element noise.
@@ -976,26 +1391,45 @@ __global__ void k_gt_fill(const int32_t* gcol, const __half* gval, int64_t N, co
     }
 }
 // deterministic order inside each row of G^T: by source row.  One warp per row: for rows of up
-// to 32 entries (nearly all) lane i holds entry i and writes it at its rank among the row's
-// source rows (all distinct: a row of G names each column once); longer rows are sorted in
-// place by one lane.
+// to 32 kGtPL entries (all but pathological ones) lane i holds entries i, i + 32, ... and writes
+// each at its rank among the row's source rows (all distinct: a row of G names each column
+// once), counted against every entry of the row by shuffles; longer rows are sorted in place by
+// one lane.
+constexpr int kGtPL = 8;
 __global__ void k_gt_sort(const int64_t* rp, int32_t* col, __half* val, int64_t N) {
     const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (c >= N) return;  // warp-uniform
     const int64_t s = rp[c], e = rp[c + 1];
     const int n = (int)(e - s);
-    if (n <= 32) {
-        const int32_t mc = lane < n ? col[s + lane] : INT_MAX;
-        const __half mv = lane < n ? val[s + lane] : __float2half_rn(0.f);
-        int rank = 0;
+    if (n <= 1) return;
+    if (n <= 32 * kGtPL) {
+        int32_t mc[kGtPL];
+        __half mv[kGtPL];
+        int rank[kGtPL];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) rank += __shfl_sync(0xffffffffu, mc, j) < mc ? 1 : 0;
-        __syncwarp();  // every lane has read its entry before any lane writes
-        if (lane < n) {
-            col[s + rank] = mc;
-            val[s + rank] = mv;
+        for (int t = 0; t < kGtPL; ++t) {
+            const int i = lane + 32 * t;
+            mc[t] = i < n ? col[s + i] : INT_MAX;
+            mv[t] = i < n ? val[s + i] : __float2half_rn(0.f);
+            rank[t] = 0;
         }
+#pragma unroll
+        for (int u = 0; u < kGtPL; ++u) {
+            if (32 * u >= n) break;  // warp-uniform
+            for (int j = 0; j < 32; ++j) {
+                const int32_t o = __shfl_sync(0xffffffffu, mc[u], j);
+#pragma unroll
+                for (int t = 0; t < kGtPL; ++t) rank[t] += o < mc[t] ? 1 : 0;
+            }
+        }
+        __syncwarp();  // every lane has read its entries before any lane writes
+#pragma unroll
+        for (int t = 0; t < kGtPL; ++t)
+            if (lane + 32 * t < n) {
+                col[s + rank[t]] = mc[t];
+                val[s + rank[t]] = mv[t];
+            }
         return;
     }
     if (lane != 0) return;
@@ -1044,13 +1478,32 @@ ms_status launch_infer(ms_hierarchy* h, __half* gval, int32_t* gcol, float* ghat
     ms_status s = ms_tmp_alloc((void**)&Zc, sizeof(float) * (size_t)N * pc.n_in, st);
     if (s == MS_OK) s = ms_tmp_alloc((void**)&cnt, sizeof(int32_t) * (size_t)N, st);
     if (s == MS_OK) {
-        const size_t smem = cand_smem(pc.n_in, m);
-        cudaError_t e = cudaFuncSetAttribute(k_pc_cand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaSuccess;
+        if (pc.fp32_weights) {  // FP32 weights: the FP32 network on the CUDA cores
+            const size_t smem = cand_smem(pc.n_in, m);
+            e = cudaFuncSetAttribute(k_pc_cand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) {
+                k_pc_cand<<<nblk(N, kCandBS), kCandBS, smem, st>>>(h->view, pc.nbr, th, m, pc.musig, Uc, Zc, cnt);
+                ms_count_launch();
+            }
+        } else {  // BF16-valued weights: features, then the network on the tensor cores
+            const MlpSmem S = mlp_smem(pc.n_in, m);
+            int sms = 0;
+            e = cudaFuncSetAttribute(k_pc_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, S.total);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+            if (e == cudaSuccess) e = cudaMemsetAsync(pc.tcstat, 0, sizeof(int), st);
+            if (e == cudaSuccess) {
+                k_pc_features<<<nblk(N, 128), 128, 0, st>>>(h->view, pc.nbr, nullptr, N, Zc, cnt);
+                const int64_t tiles = (N + kMlpRows - 1) / kMlpRows;
+                const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, 2 * (int64_t)sms));
+                k_pc_mlp<<<grid, kMlpRows, S.total, st>>>(th, pc.n_in, m, pc.musig, Zc, cnt, N, Uc, pc.tcstat);
+                ms_count_launch(2);
+            }
+        }
         if (e == cudaSuccess) {
-            k_pc_cand<<<nblk(N, kCandBS), kCandBS, smem, st>>>(h->view, pc.nbr, th, m, pc.musig, Uc, Zc, cnt);
-            k_pc_combine<<<nblk(N, kCombW), kCombW * 32, 0, st>>>(h->view, pc.nbr, m, Uc, Zc, cnt, gval, gcol,
+            k_pc_combine<<<nblk(N, kCombPts), kCombPts * 16, 0, st>>>(h->view, pc.nbr, m, Uc, Zc, cnt, gval, gcol,
                                                                  ghat_out);
-            ms_count_launch(2);
+            ms_count_launch();
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) s = ms_cuda_error(e, "network rows", __FILE__, __LINE__);
@@ -1079,12 +1532,15 @@ ms_status pc_alloc(ms_hierarchy* h) {
     MS_TRY(ms_alloc(h, (void**)&pc.adam_m, sizeof(float) * pmax));
     MS_TRY(ms_alloc(h, (void**)&pc.adam_v, sizeof(float) * pmax));
     MS_TRY(ms_alloc(h, (void**)&pc.musig, sizeof(float) * 2 * kPcOut));
+    MS_TRY(ms_alloc(h, (void**)&pc.tcstat, sizeof(int)));
+    MS_CUDA(cudaMemset(pc.tcstat, 0, sizeof(int)));
     return MS_OK;
 }
 
 ms_status pc_pattern(ms_hierarchy* h, cudaStream_t st) {
     MS_TRY(pc_alloc(h));
-    k_pc_pattern<<<nblk(h->N, 128), 128, 0, st>>>(h->view, h->A.rp, h->A.col, h->perm, h->pc.nbr);
+    k_pc_pattern<<<nblk(h->N, kPatW), kPatW * 32, 0, st>>>(h->view, h->W, h->cellid, h->A.rp, h->A.col, h->perm,
+                                                            h->pc.nbr);
     ms_count_launch();
     MS_CUDA(cudaGetLastError());
     return MS_OK;
@@ -1194,7 +1650,8 @@ ms_status make_trainset(ms_hierarchy* h, const int* levels, int n, bool set_mome
     MS_TRY(ts.alloc((void**)&ts.K, sizeof(float) * ts.S * kPcOut * kPcOut));
     MS_CUDA(cudaMemcpyAsync(ts.rows, rows.data(), sizeof(int64_t) * ts.S, cudaMemcpyHostToDevice, st));
     MS_CUDA(cudaMemcpyAsync(dbound, bounds.data(), sizeof(int64_t) * ts.S, cudaMemcpyHostToDevice, st));
-    k_pc_patches<<<nblk(ts.S, 128), 128, 0, st>>>(h->view, h->A.rp, h->A.col, h->perm, ts.rows, dbound, ts.S, ts.nbr);
+    k_pc_patches<<<nblk(ts.S, kPatW), kPatW * 32, 0, st>>>(h->view, h->W, h->cellid, h->A.rp, h->A.col, h->perm,
+                                                            ts.rows, dbound, ts.S, ts.nbr);
     k_pc_features<<<nblk(ts.S, 128), 128, 0, st>>>(h->view, ts.nbr, ts.rows, ts.S, ts.Z, ts.cnt);
     k_pc_patchK<<<nblk(ts.S, 128), 128, 0, st>>>(h->view, ts.nbr, ts.rows, ts.S, ts.K);
     ms_count_launch(3);
@@ -1541,7 +1998,8 @@ ms_status ms_precond_inspect(ms_hierarchy* h, int what, const int* levels, int n
         MS_TRY(ts.alloc((void**)&ts.nbr, sizeof(int32_t) * S * kPcK));
         MS_CUDA(cudaMemcpy(ts.rows, rows.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice));
         MS_CUDA(cudaMemcpy(dbound, bounds.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice));
-        k_pc_patches<<<nblk(S, 128), 128>>>(h->view, h->A.rp, h->A.col, h->perm, ts.rows, dbound, S, ts.nbr);
+        k_pc_patches<<<nblk(S, kPatW), kPatW * 32>>>(h->view, h->W, h->cellid, h->A.rp, h->A.col, h->perm, ts.rows,
+                                                      dbound, S, ts.nbr);
         ms_count_launch();
         MS_CUDA(cudaGetLastError());
         std::vector<int32_t> nb(S * kPcK);

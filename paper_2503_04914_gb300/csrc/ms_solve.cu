@@ -43,7 +43,7 @@ __global__ void k_spmv(const int64_t* rp, const int32_t* col, const TV* val, con
     const bool ok = row < N;
     int64_t s = 0, e = 0;
     if (ok) { s = rp[row]; e = rp[row + 1]; }
-    const TA v = csr_row<TV, TX, TA>(col, val, x, s, e, lane & (S - 1), S);
+    const TA v = csr_row_vec<TV, TX, TA>(col, val, x, s, e, lane & (S - 1), S);
     if (ok && (lane & (S - 1)) == 0) y[row] = sub ? sub[row] + sign * (double)v : (double)v;
 }
 
@@ -55,6 +55,19 @@ __global__ void k_mf_apply(MFView v, const float* x, double* y, int tpp, int64_t
     while (l + 1 < v.L && gw >= v.lv[l + 1].cell_off) ++l;
     const int64_t cell = gw - v.lv[l].cell_off;
     mf_cells_any(v, l, cell, cell + 1, 0, 1, tpp, x, [&](int64_t row, float val) { y[row] = (double)val; });
+}
+
+// y = D_L x matrix-free, staged form: one CTA per cell of every level (mf_cell_staged); a cell
+// of more than the CTA's 128 points takes the warp form on the CTA's first warp.
+__global__ void __launch_bounds__(128) k_mf_apply_staged(MFView v, const float* x, double* y, int tpp) {
+    __shared__ float4 stage[kMfStage];
+    const int64_t gc = blockIdx.x;
+    int l = 0;
+    while (l + 1 < v.L && gc >= v.lv[l + 1].cell_off) ++l;
+    const int64_t cell = gc - v.lv[l].cell_off;
+    auto emit = [&](int64_t row, float val) { y[row] = (double)val; };
+    if (!mf_cell_staged_any(v, l, cell, x, stage, emit) && threadIdx.x < 32)
+        mf_cells_any(v, l, cell, cell + 1, 0, 1, tpp, x, emit);
 }
 
 __global__ void k_to_f32(const double* in, float* out, int64_t n) {
@@ -105,6 +118,80 @@ __global__ void k_lower_mf_apply(const __grid_constant__ HierView v, const float
         for (int o = S >> 1; o > 0; o >>= 1) acc.hi += __shfl_xor_sync(0xffffffffu, acc.hi, o);
     }
     if (ok && sl == 0) y[row] = FF ? ff_to_double(acc) : (double)acc.hi;
+}
+
+// Several blocks of right-hand sides of one hierarchy in ONE cooperative launch: the grid is
+// split into P equal partitions of consecutive CTAs, partition p = CTAs [p G / P, (p + 1) G / P)
+// runs the whole schedule of eq. split for block p (args[p]: its own work vectors, reductions
+// and barrier words), the same device code as a single fit.  The blocks' small, latency-bound
+// phases then overlap instead of running one launch after another.
+__host__ __device__ inline int part_first_cta(int p, int G, int P) { return (int)(((long long)p * G) / P); }
+
+template <int MODE, bool WIDE>
+__global__ void __launch_bounds__(kBS, 2) k_fit_parts(const SolveArgs* __restrict__ args, int P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Shared& sh = *reinterpret_cast<Shared*>(smem_raw);
+    __shared__ int pid;
+    if (threadIdx.x == 0) {
+        const int G = gridDim.x, b = blockIdx.x;
+        int p = (int)(((long long)b * P) / G);
+        while (p + 1 < P && part_first_cta(p + 1, G, P) <= b) ++p;
+        while (p > 0 && part_first_cta(p, G, P) > b) --p;
+        pid = p;
+        sh.cta = b - part_first_cta(p, G, P);
+        sh.nb = part_first_cta(p + 1, G, P) - part_first_cta(p, G, P);
+    }
+    __syncthreads();
+    fit_body<MODE, WIDE>(args[pid], sh);
+}
+
+const void* parts_kernel(bool mixed, bool wide) {
+    if (wide) return mixed ? (const void*)k_fit_parts<1, true> : (const void*)k_fit_parts<0, true>;
+    return mixed ? (const void*)k_fit_parts<1, false> : (const void*)k_fit_parts<0, false>;
+}
+
+constexpr int kMaxParts = 16;  // blocks of right-hand sides per launch
+
+// Per-block counters of a partitioned launch, carved from h->pbuf (256-byte aligned pieces).
+struct PartCounters {
+    unsigned* bar;
+    int* status;
+    int64_t* iters;
+    int* refines;
+    double* bytes;
+    unsigned long long* prof;
+    int* pcfb;
+};
+constexpr size_t pad256b(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kPartBytes = pad256b(sizeof(unsigned) * kBarWords) + pad256b(sizeof(int)) +
+                              pad256b(sizeof(int64_t) * MS_MAXL) + pad256b(sizeof(int) * MS_MAXL) +
+                              pad256b(sizeof(double)) + pad256b(sizeof(unsigned long long) * kProf) +
+                              pad256b(sizeof(int) * 2);
+PartCounters part_counters(const ms_hierarchy* h, int p) {
+    unsigned char* b = static_cast<unsigned char*>(h->pbuf) + (size_t)p * kPartBytes;
+    PartCounters c;
+    c.bar = reinterpret_cast<unsigned*>(b);
+    b += pad256b(sizeof(unsigned) * kBarWords);
+    c.status = reinterpret_cast<int*>(b);
+    b += pad256b(sizeof(int));
+    c.iters = reinterpret_cast<int64_t*>(b);
+    b += pad256b(sizeof(int64_t) * MS_MAXL);
+    c.refines = reinterpret_cast<int*>(b);
+    b += pad256b(sizeof(int) * MS_MAXL);
+    c.bytes = reinterpret_cast<double*>(b);
+    b += pad256b(sizeof(double));
+    c.prof = reinterpret_cast<unsigned long long*>(b);
+    b += pad256b(sizeof(unsigned long long) * kProf);
+    c.pcfb = reinterpret_cast<int*>(b);
+    return c;
+}
+
+ms_status ensure_parts(ms_hierarchy* h, int P) {
+    if (h->pbuf && h->pbuf_parts >= P) return MS_OK;
+    MS_TRY(ms_realloc(h, &h->pbuf, kPartBytes * (size_t)P));
+    MS_TRY(ms_realloc(h, &h->d_args, sizeof(SolveArgs) * (size_t)P));
+    h->pbuf_parts = P;
+    return MS_OK;
 }
 
 // The solve kernel for a precision and a CTAs-per-SM choice (opts.solve_ctas_per_sm;
@@ -339,8 +426,72 @@ ms_status ms_autotune(ms_hierarchy* h, cudaStream_t st) {
     return MS_OK;
 }
 
+namespace {
+
+// CTAs per SM of the solve kernel in use; re-sizes the per-CTA reduction buffer when the
+// cooperative grid changes.
+ms_status set_solve_ctas(ms_hierarchy* h, int c) {
+    h->opts.solve_ctas_per_sm = c;
+    if (!h->f) return MS_OK;  // sized by the next fit's work space
+    int dev = 0, blocks = 0;
+    MS_CUDA(cudaGetDevice(&dev));
+    MS_TRY(fit_blocks(h->opts.precision == MS_PREC_MIXED, c, dev, &blocks));
+    if (blocks > h->solve_blocks)
+        MS_TRY(ms_realloc(h, (void**)&h->part, sizeof(double) * kAcc * (size_t)h->ws_rhs * h->L * blocks));
+    h->solve_blocks = blocks;
+    return MS_OK;
+}
+
+// (d, L, log2 N, wendland d, k, precision, precond, op, lower_op, several rhs) -> CTAs per SM
+using CtaKey = std::tuple<int, int, int, int, int, int, int, int, int, int>;
+std::map<CtaKey, int> g_cta_cache;
+
+}  // namespace
+
+ms_status fit_impl_inner(ms_hierarchy* h, const double* f_dev, int nrhs, double rel_tol, double* alpha_dev,
+                         ms_fit_stats* stats, cudaStream_t st);
+
+// With opts.autotune = 1 and solve_ctas_per_sm = 0, the first fit of a hierarchy shape runs
+// once with 1 CTA per SM (up to 128 registers a thread) and once with 2 (up to 64), keeps the
+// faster kernel time for the handle and caches it per process by shape; the call returns the
+// second run's result (both are fits to rel_tol).
 ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel_tol, double* alpha_dev,
                       ms_fit_stats* stats, cudaStream_t st) {
+    if (!(h->opts.autotune && h->opts.solve_ctas_per_sm == 0))
+        return fit_impl_inner(h, f_dev, nrhs, rel_tol, alpha_dev, stats, st);
+    int lg = 0;
+    while ((int64_t(1) << (lg + 1)) <= h->N) ++lg;
+    const CtaKey key(h->d, h->L, lg, h->opts.wendland_d, h->opts.wendland_k, h->opts.precision, h->opts.precond,
+                     h->opts.op, h->opts.lower_op, nrhs > 1 ? 1 : 0);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_cta_cache.find(key);
+        if (it != g_cta_cache.end()) {
+            MS_TRY(set_solve_ctas(h, it->second));
+            return fit_impl_inner(h, f_dev, nrhs, rel_tol, alpha_dev, stats, st);
+        }
+    }
+    ms_fit_stats s1{}, s2{};
+    MS_TRY(set_solve_ctas(h, 1));
+    ms_status r = fit_impl_inner(h, f_dev, nrhs, rel_tol, alpha_dev, &s1, st);
+    if (r != MS_OK) {
+        h->opts.solve_ctas_per_sm = 0;
+        return r;
+    }
+    MS_TRY(set_solve_ctas(h, 2));
+    r = fit_impl_inner(h, f_dev, nrhs, rel_tol, alpha_dev, &s2, st);
+    const int best = s1.fit_ms < s2.fit_ms ? 1 : 2;
+    MS_TRY(set_solve_ctas(h, best));
+    if (r == MS_OK) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_cta_cache[key] = best;
+    }
+    if (stats) *stats = s2;
+    return r;
+}
+
+ms_status fit_impl_inner(ms_hierarchy* h, const double* f_dev, int nrhs, double rel_tol, double* alpha_dev,
+                         ms_fit_stats* stats, cudaStream_t st) {
     const int Rmax = rhs_per_launch(h, nrhs);
     const bool wide = wide_layout(h, nrhs, ctas_per_sm(h->opts));
     int RWmax = 1;
@@ -366,83 +517,165 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
     int launches = 0;
     float total_ms = 0.f;
     double bytes = 0.0;
-    std::vector<int64_t> it(MS_MAXL, 0), it_sum(MS_MAXL, 0);
-    std::vector<int> ref(MS_MAXL, 0), ref_sum(MS_MAXL, 0);
-    std::vector<double> res(kMaxV, 0.0), res_max(MS_MAXL, 0.0);
+    std::vector<int64_t> it_sum(MS_MAXL, 0);
+    std::vector<int> ref_sum(MS_MAXL, 0);
+    std::vector<double> res_max(MS_MAXL, 0.0);
     double phase[kProf] = {};
     int fallbacks = 0, f64_fallbacks = 0;
     int dstat = 0;
-    for (int col0 = 0; col0 < nrhs; col0 += Rmax) {
-        const int R = std::min(Rmax, nrhs - col0);
-        SolveArgs a{};
-        fill_args(h, rel_tol, R, a, wide);
-        a.f = h->f; a.beta = h->beta; a.x = h->x; a.r = h->r; a.p = h->p; a.q = h->q; a.s = h->s;
-        a.x32 = h->x32; a.r32 = h->r32; a.p32 = h->p32; a.q32 = h->q32; a.s32 = h->s32;
-        a.u32 = h->u32; a.u1_32 = h->u1_32;
-        a.part = h->part; a.gpart = h->gpart; a.scal = h->scal; a.bar = h->bar; a.status = h->status;
-        a.iters = h->iters; a.refines = h->refines; a.resid = h->resid; a.bytes = h->bytes; a.prof = h->prof;
-        a.pcfb = h->pcfb;
-        if (wide) {
-            k_gather_wide<<<nblk(N * a.RW, 256), 256, 0, st>>>(f_dev, h->f, h->perm, N, nrhs, col0, R, a.RW);
-            ms_count_launch();
-            ++launches;
-        } else {
-            for (int r = 0; r < R; ++r) {
-                ms_gather_sorted(f_dev, h->f + (int64_t)r * N, h->perm, N, nrhs, col0 + r, st);
-                ++launches;
-            }
-        }
-        MS_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * kBarWords, st));
-        MS_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
-        MS_CUDA(cudaMemsetAsync(h->resid, 0, sizeof(double) * a.V, st));
-        void* args[] = {&a};
-        MS_CUDA(cudaEventRecord(h->ev0, st));
+    int solve_launches = 0, rhs_launch = 0;
+    // blocks of at most Rmax right-hand sides; with 2 CTAs per SM up to kMaxParts blocks share one
+    // partitioned launch (k_fit_parts), within a bound on the work vectors' size
+    const int width = wide ? RWmax : Rmax;
+    const int nblocks = (nrhs + Rmax - 1) / Rmax;
+    int Pmax = 1;
+    if (nblocks > 1 && ctas_per_sm(h->opts) == 2) {
+        const int64_t cap = std::max<int64_t>(1, (int64_t)(256ll << 20) / std::max<int64_t>(1, (int64_t)width * N));
+        Pmax = (int)std::min<int64_t>({(int64_t)nblocks, (int64_t)kMaxParts, cap, (int64_t)h->solve_blocks / 8});
+        Pmax = std::max(Pmax, 1);
+    }
+    if (Pmax > 1) {
+        MS_TRY(ms_ensure_workspace(h, width * Pmax));
+        MS_TRY(ensure_parts(h, Pmax));
+    }
+    const int Vs = Rmax * L;  // virtual levels of a full block (the carving stride)
+    for (int col0 = 0; col0 < nrhs;) {
+        const int P = std::min(Pmax, (nrhs - col0 + Rmax - 1) / Rmax);
         int grid = h->solve_blocks;
         if (wide) MS_TRY(fit_blocks(mixed, 2, h->device, &grid, true));
+        if (P > 1) {
+            int g2 = 0;
+            const void* fn = parts_kernel(mixed, wide);
+            MS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared)));
+            int sms = 0, per_sm = 0;
+            MS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+            MS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBS, sizeof(Shared)));
+            g2 = sms * std::min(per_sm, 2);
+            grid = std::min(grid, g2);
+        }
         grid = std::min(grid, h->solve_blocks);  // the reduction buffers hold solve_blocks CTAs
-        MS_CUDA(cudaLaunchCooperativeKernel(fit_kernel(mixed, ctas_per_sm(h->opts), wide), dim3(grid), dim3(kBS),
-                                            args, sizeof(Shared), st));
+        std::vector<SolveArgs> as(P);
+        std::vector<int> Rs(P);
+        for (int p = 0; p < P; ++p) {
+            const int cb = col0 + p * Rmax;
+            const int R = std::min(Rmax, nrhs - cb);
+            Rs[p] = R;
+            SolveArgs& a = as[p];
+            fill_args(h, rel_tol, R, a, wide);
+            const int64_t vo = (int64_t)p * width * N;  // this block's work vectors
+            auto off64 = [&](double* q) { return q ? q + vo : q; };
+            auto off32 = [&](float* q) { return q ? q + vo : q; };
+            a.f = off64(h->f); a.beta = off64(h->beta); a.x = off64(h->x); a.r = off64(h->r);
+            a.p = off64(h->p); a.q = off64(h->q); a.s = off64(h->s);
+            a.x32 = off32(h->x32); a.r32 = off32(h->r32); a.p32 = off32(h->p32); a.q32 = off32(h->q32);
+            a.s32 = off32(h->s32); a.u32 = off32(h->u32); a.u1_32 = off32(h->u1_32);
+            if (P == 1) {
+                a.part = h->part; a.gpart = h->gpart; a.scal = h->scal; a.resid = h->resid;
+                a.bar = h->bar; a.status = h->status; a.iters = h->iters; a.refines = h->refines;
+                a.bytes = h->bytes; a.prof = h->prof; a.pcfb = h->pcfb;
+            } else {
+                a.part = h->part + (size_t)kAcc * Vs * part_first_cta(p, grid, P);
+                a.gpart = h->gpart + (size_t)p * kMaxGroups * kAcc * Vs;
+                a.scal = h->scal + (size_t)p * kAcc * Vs;
+                a.resid = h->resid + (size_t)p * Vs;
+                const PartCounters c = part_counters(h, p);
+                a.bar = c.bar; a.status = c.status; a.iters = c.iters; a.refines = c.refines;
+                a.bytes = c.bytes; a.prof = c.prof; a.pcfb = c.pcfb;
+            }
+            if (wide) {
+                k_gather_wide<<<nblk(N * a.RW, 256), 256, 0, st>>>(f_dev, h->f + vo, h->perm, N, nrhs, cb, R, a.RW);
+                ms_count_launch();
+                ++launches;
+            } else {
+                for (int r = 0; r < R; ++r) {
+                    ms_gather_sorted(f_dev, h->f + vo + (int64_t)r * N, h->perm, N, nrhs, cb + r, st);
+                    ++launches;
+                }
+            }
+            MS_CUDA(cudaMemsetAsync(a.bar, 0, sizeof(unsigned) * kBarWords, st));
+            MS_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), st));
+            MS_CUDA(cudaMemsetAsync(a.resid, 0, sizeof(double) * a.V, st));
+        }
+        if (P > 1) MS_CUDA(cudaMemcpyAsync(h->d_args, as.data(), sizeof(SolveArgs) * P, cudaMemcpyHostToDevice, st));
+        MS_CUDA(cudaEventRecord(h->ev0, st));
+        if (P == 1) {
+            void* args[] = {&as[0]};
+            MS_CUDA(cudaLaunchCooperativeKernel(fit_kernel(mixed, ctas_per_sm(h->opts), wide), dim3(grid), dim3(kBS),
+                                                args, sizeof(Shared), st));
+        } else {
+            const SolveArgs* da = static_cast<const SolveArgs*>(h->d_args);
+            int np = P;
+            void* args[] = {&da, &np};
+            MS_CUDA(cudaLaunchCooperativeKernel(parts_kernel(mixed, wide), dim3(grid), dim3(kBS), args,
+                                                sizeof(Shared), st));
+        }
         ms_count_launch();
         MS_CUDA(cudaEventRecord(h->ev1, st));
         ++launches;
-        if (wide) {
-            k_scatter_wide<<<nblk(N * a.RW, 256), 256, 0, st>>>(h->x, alpha_dev, h->perm, N, nrhs, col0, R, a.RW);
-            ms_count_launch();
-            ++launches;
-        } else {
-            for (int r = 0; r < R; ++r) {
-                ms_scatter_input(h->x + (int64_t)r * N, alpha_dev, h->perm, N, nrhs, col0 + r, st);
+        ++solve_launches;
+        rhs_launch = std::max(rhs_launch, nrhs - col0 < P * Rmax ? nrhs - col0 : P * Rmax);
+        for (int p = 0; p < P; ++p) {
+            const SolveArgs& a = as[p];
+            const int cb = col0 + p * Rmax;
+            if (wide) {
+                k_scatter_wide<<<nblk(N * a.RW, 256), 256, 0, st>>>(a.x, alpha_dev, h->perm, N, nrhs, cb, Rs[p], a.RW);
+                ms_count_launch();
                 ++launches;
+            } else {
+                for (int r = 0; r < Rs[p]; ++r) {
+                    ms_scatter_input(a.x + (int64_t)r * N, alpha_dev, h->perm, N, nrhs, cb + r, st);
+                    ++launches;
+                }
             }
         }
         MS_CUDA(cudaGetLastError());
-        double b = 0.0;
-        MS_CUDA(cudaMemcpyAsync(&dstat, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
-        MS_CUDA(cudaMemcpyAsync(it.data(), h->iters, sizeof(int64_t) * MS_MAXL, cudaMemcpyDeviceToHost, st));
-        MS_CUDA(cudaMemcpyAsync(ref.data(), h->refines, sizeof(int) * MS_MAXL, cudaMemcpyDeviceToHost, st));
-        MS_CUDA(cudaMemcpyAsync(res.data(), h->resid, sizeof(double) * a.V, cudaMemcpyDeviceToHost, st));
-        MS_CUDA(cudaMemcpyAsync(&b, h->bytes, sizeof(double), cudaMemcpyDeviceToHost, st));
-        unsigned long long pr[kProf];
-        MS_CUDA(cudaMemcpyAsync(pr, h->prof, sizeof(pr), cudaMemcpyDeviceToHost, st));
-        int fb[2] = {0, 0};
-        MS_CUDA(cudaMemcpyAsync(fb, h->pcfb, sizeof(fb), cudaMemcpyDeviceToHost, st));
+        int tcs = 0;  // the tensor-core network that made the learned rows
+        if (h->pc.tcstat && h->opts.precond == MS_PRECOND_LEARNED)
+            MS_CUDA(cudaMemcpyAsync(&tcs, h->pc.tcstat, sizeof(int), cudaMemcpyDeviceToHost, st));
+        std::vector<int> pst(P, 0), pfb(2 * P, 0);
+        std::vector<int64_t> pit((size_t)P * MS_MAXL, 0);
+        std::vector<int> pref((size_t)P * MS_MAXL, 0);
+        std::vector<double> pres((size_t)P * Vs, 0.0), pb(P, 0.0);
+        std::vector<unsigned long long> ppr((size_t)P * kProf, 0);
+        for (int p = 0; p < P; ++p) {
+            const SolveArgs& a = as[p];
+            MS_CUDA(cudaMemcpyAsync(&pst[p], a.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+            MS_CUDA(cudaMemcpyAsync(&pit[(size_t)p * MS_MAXL], a.iters, sizeof(int64_t) * MS_MAXL,
+                                    cudaMemcpyDeviceToHost, st));
+            MS_CUDA(cudaMemcpyAsync(&pref[(size_t)p * MS_MAXL], a.refines, sizeof(int) * MS_MAXL,
+                                    cudaMemcpyDeviceToHost, st));
+            MS_CUDA(cudaMemcpyAsync(&pres[(size_t)p * Vs], a.resid, sizeof(double) * a.V, cudaMemcpyDeviceToHost, st));
+            MS_CUDA(cudaMemcpyAsync(&pb[p], a.bytes, sizeof(double), cudaMemcpyDeviceToHost, st));
+            MS_CUDA(cudaMemcpyAsync(&ppr[(size_t)p * kProf], a.prof, sizeof(unsigned long long) * kProf,
+                                    cudaMemcpyDeviceToHost, st));
+            MS_CUDA(cudaMemcpyAsync(&pfb[2 * p], a.pcfb, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+        }
         MS_CUDA(cudaStreamSynchronize(st));
+        if (tcs != 0 && result == MS_OK) {
+            result = (ms_status)tcs;
+            ms_set_error(result, "a wait for the tensor-core network's MMAs ran out (the learned rows are not valid)");
+        }
         float ms = 0.f;
         MS_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
         total_ms += ms;
-        bytes += b;
-        for (int i = 0; i < kProf; ++i) phase[i] += 1e-6 * (double)pr[i];
-        fallbacks += fb[0];
-        f64_fallbacks += fb[1];
-        for (int l = 0; l < L; ++l) {
-            it_sum[l] += it[l];
-            ref_sum[l] += ref[l];
-            for (int r = 0; r < R; ++r) res_max[l] = std::max(res_max[l], res[r * L + l]);
+        for (int i = 0; i < kProf; ++i) phase[i] += 1e-6 * (double)ppr[i];  // block 0's first CTA
+        for (int p = 0; p < P; ++p) {
+            bytes += pb[p];
+            fallbacks += pfb[2 * p];
+            f64_fallbacks += pfb[2 * p + 1];
+            for (int l = 0; l < L; ++l) {
+                it_sum[l] += pit[(size_t)p * MS_MAXL + l];
+                ref_sum[l] += pref[(size_t)p * MS_MAXL + l];
+                for (int r = 0; r < Rs[p]; ++r) res_max[l] = std::max(res_max[l], pres[(size_t)p * Vs + r * L + l]);
+            }
+            if (pst[p] != 0) dstat = dstat ? dstat : pst[p];
+            if (pst[p] != 0 && result == MS_OK) {
+                result = (ms_status)pst[p];
+                ms_set_error(result, "device status %d during the fit of right-hand sides %d..%d", pst[p],
+                             col0 + p * Rmax, col0 + p * Rmax + Rs[p] - 1);
+            }
         }
-        if (dstat != 0 && result == MS_OK) {
-            result = (ms_status)dstat;
-            ms_set_error(result, "device status %d during the fit of right-hand sides %d..%d", dstat, col0, col0 + R - 1);
-        }
+        col0 += std::min(nrhs - col0, P * Rmax);
     }
     if (stats) {
         *stats = ms_fit_stats{};
@@ -457,6 +690,8 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
         stats->fit_ms = total_ms;
         stats->matvec_bytes = bytes;
         stats->kernel_launches = launches;
+        stats->solve_launches = solve_launches;
+        stats->rhs_per_launch = rhs_launch;
         stats->precond_fallbacks = fallbacks;
         stats->fp64_fallbacks = f64_fallbacks;
         for (int i = 0; i < kProf; ++i) stats->phase_ms[i] = phase[i];
@@ -507,7 +742,7 @@ ms_status ms_apply_impl(ms_hierarchy* h, int op, const double* x_dev, double* y_
         k_to_f32<<<nblk(N, 256), 256, 0, st>>>(xs, x32, N);
         ms_count_launch();
         const MFView v = make_mfview(h);
-        k_mf_apply<<<nblk(h->total_cells * 32, 256), 256, 0, st>>>(v, x32, ys, h->mf_tpp, h->total_cells);
+        k_mf_apply_staged<<<(unsigned)h->total_cells, 128, 0, st>>>(v, x32, ys, h->mf_tpp);
         ms_count_launch();
         break;
     }
@@ -722,6 +957,8 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
         stats->fit_ms = ms;
         stats->matvec_bytes = b;
         stats->kernel_launches = 3;
+        stats->solve_launches = 1;
+        stats->rhs_per_launch = 1;
         stats->precond_fallbacks = fb[0];
         stats->fp64_fallbacks = fb[1];
         for (int i = 0; i < kProf; ++i) stats->phase_ms[i] = 1e-6 * (double)pr[i];

@@ -160,53 +160,65 @@ __device__ __forceinline__ void prof(Shared& sh, int cat) {
 // lanes of the warp must call it (invalid rows pass e = s).
 // The matrix (col, val) is read-only for the whole kernel and may use the
 // non-coherent path; x is written by other CTAs between phases and must not
-// (no __restrict__ on it).  FP32 and FP64 values are read four entries at a time
-// with 128-bit loads (int4 columns, float4 / 2 x double2 values): the entries from
-// the first multiple of 4 at or after s are split into groups of four, group g to lane
-// g mod S, and the (at most 3) entries before that boundary and after the last full group
-// go to the lanes one by one (lane sl takes every S-th of them).  Other value types (FP16) go one entry per lane, unrolled by 4.
-// The per-lane partial sums are combined by shuffles in a fixed order.
+// (no __restrict__ on it).  The loop is unrolled by 4 with independent loads so
+// that a lane keeps several gathers in flight (small levels are latency-bound).
+// The per-lane partial sums are combined by shuffles in a fixed order.  (Inside the
+// solve kernel this form measured faster than the 128-bit form below: with four
+// entries a lane per group the latter leaves fewer independent gathers in flight and
+// needs more registers than the kernel's 64.)
 template <typename TV, typename TX, typename TA>
 __device__ __forceinline__ TA csr_row(const int32_t* __restrict__ col, const TV* __restrict__ val,
                                       const TX* x, int64_t s, int64_t e, int sl, int S) {
     TA acc = TA(0);
-    if constexpr (sizeof(TV) == 4 || sizeof(TV) == 8) {
-        const int64_t a = min(e, (s + 3) & ~int64_t(3));  // 16-byte boundary of the columns
-        for (int64_t k = s + sl; k < a; k += S) acc += (TA)__ldg(val + k) * (TA)x[__ldg(col + k)];
-        const int64_t ng = (e - a) >> 2;                  // full groups of four from a
-        const int4* c4 = reinterpret_cast<const int4*>(col + a);
-        for (int64_t g = sl; g < ng; g += S) {
-            const int4 c = __ldg(c4 + g);
-            TA v0, v1, v2, v3;
-            if constexpr (sizeof(TV) == 4) {
-                const float4 v = __ldg(reinterpret_cast<const float4*>(val + a) + g);
-                v0 = (TA)v.x; v1 = (TA)v.y; v2 = (TA)v.z; v3 = (TA)v.w;
-            } else {
-                const double2 u = __ldg(reinterpret_cast<const double2*>(val + a) + 2 * g);
-                const double2 w = __ldg(reinterpret_cast<const double2*>(val + a) + 2 * g + 1);
-                v0 = (TA)u.x; v1 = (TA)u.y; v2 = (TA)w.x; v3 = (TA)w.y;
-            }
-            const TX x0 = x[c.x], x1 = x[c.y], x2 = x[c.z], x3 = x[c.w];
-            acc += v0 * (TA)x0;
-            acc += v1 * (TA)x1;
-            acc += v2 * (TA)x2;
-            acc += v3 * (TA)x3;
-        }
-        for (int64_t t = a + 4 * ng + sl; t < e; t += S) acc += (TA)__ldg(val + t) * (TA)x[__ldg(col + t)];
-    } else {
-        int64_t k = s + sl;
-        for (; k + 3 * S < e; k += 4 * S) {
-            const int32_t c0 = __ldg(col + k), c1 = __ldg(col + k + S), c2 = __ldg(col + k + 2 * S),
-                          c3 = __ldg(col + k + 3 * S);
-            const TV v0 = __ldg(val + k), v1 = __ldg(val + k + S), v2 = __ldg(val + k + 2 * S), v3 = __ldg(val + k + 3 * S);
-            const TX x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
-            acc += (TA)v0 * (TA)x0;
-            acc += (TA)v1 * (TA)x1;
-            acc += (TA)v2 * (TA)x2;
-            acc += (TA)v3 * (TA)x3;
-        }
-        for (; k < e; k += S) acc += (TA)__ldg(val + k) * (TA)x[__ldg(col + k)];
+    int64_t k = s + sl;
+    for (; k + 3 * S < e; k += 4 * S) {
+        const int32_t c0 = __ldg(col + k), c1 = __ldg(col + k + S), c2 = __ldg(col + k + 2 * S),
+                      c3 = __ldg(col + k + 3 * S);
+        const TV v0 = __ldg(val + k), v1 = __ldg(val + k + S), v2 = __ldg(val + k + 2 * S), v3 = __ldg(val + k + 3 * S);
+        const TX x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+        acc += (TA)v0 * (TA)x0;
+        acc += (TA)v1 * (TA)x1;
+        acc += (TA)v2 * (TA)x2;
+        acc += (TA)v3 * (TA)x3;
     }
+    for (; k < e; k += S) acc += (TA)__ldg(val + k) * (TA)x[__ldg(col + k)];
+    for (int o = S >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+// The same sum with 128-bit loads (used by the stand-alone mat-vec): FP32 and FP64 values
+// are read four entries at a time (int4 columns, float4 / 2 x double2 values); the entries
+// from the first multiple of 4 at or after s are split into groups of four, group g to lane
+// g mod S, and the (at most 3) entries before that boundary and after the last full group go
+// to the lanes one by one (lane sl takes every S-th of them).  The CSR arrays start on
+// 16-byte boundaries (the build checks it).
+template <typename TV, typename TX, typename TA>
+__device__ __forceinline__ TA csr_row_vec(const int32_t* __restrict__ col, const TV* __restrict__ val,
+                                          const TX* x, int64_t s, int64_t e, int sl, int S) {
+    static_assert(sizeof(TV) == 4 || sizeof(TV) == 8, "FP32 or FP64 values");
+    TA acc = TA(0);
+    const int64_t a = min(e, (s + 3) & ~int64_t(3));  // 16-byte boundary of the columns
+    for (int64_t k = s + sl; k < a; k += S) acc += (TA)__ldg(val + k) * (TA)x[__ldg(col + k)];
+    const int64_t ng = (e - a) >> 2;                  // full groups of four from a
+    const int4* c4 = reinterpret_cast<const int4*>(col + a);
+    for (int64_t g = sl; g < ng; g += S) {
+        const int4 c = __ldg(c4 + g);
+        TA v0, v1, v2, v3;
+        if constexpr (sizeof(TV) == 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(val + a) + g);
+            v0 = (TA)v.x; v1 = (TA)v.y; v2 = (TA)v.z; v3 = (TA)v.w;
+        } else {
+            const double2 u = __ldg(reinterpret_cast<const double2*>(val + a) + 2 * g);
+            const double2 w = __ldg(reinterpret_cast<const double2*>(val + a) + 2 * g + 1);
+            v0 = (TA)u.x; v1 = (TA)u.y; v2 = (TA)w.x; v3 = (TA)w.y;
+        }
+        const TX x0 = x[c.x], x1 = x[c.y], x2 = x[c.z], x3 = x[c.w];
+        acc += v0 * (TA)x0;
+        acc += v1 * (TA)x1;
+        acc += v2 * (TA)x2;
+        acc += v3 * (TA)x3;
+    }
+    for (int64_t t = a + 4 * ng + sl; t < e; t += S) acc += (TA)__ldg(val + t) * (TA)x[__ldg(col + t)];
     for (int o = S >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     return acc;
 }

@@ -275,3 +275,10 @@ def query_grid(n_side: int, d: int) -> np.ndarray:
     g = (np.arange(n_side) + 0.5) / n_side
     mesh = np.meshgrid(*([g] * d), indexing="ij")
     return np.stack([m.ravel() for m in mesh], axis=1)
+
+
+def query_random(n: int, d: int, seed: int = 2503049199) -> np.ndarray:
+    """n seeded uniform query points in [0,1)^d (axis a from SplitMix64 stream seed + a).  Unlike
+    the cell centres of query_grid, they avoid the nodes of every dyadic grid, where an
+    interpolant is exact."""
+    return np.stack([uniform01(seed + a, n) for a in range(d)], axis=1)

@@ -51,7 +51,8 @@ class ms_fit_stats(C.Structure):
                 ("refinements", C.c_int32 * MS_MAX_LEVELS), ("rel_residual", C.c_double * MS_MAX_LEVELS),
                 ("precond_fallbacks", C.c_int32), ("fp64_fallbacks", C.c_int32), ("device_status", C.c_int32),
                 ("fit_ms", C.c_double),
-                ("matvec_bytes", C.c_double), ("kernel_launches", C.c_int64), ("phase_ms", C.c_double * 8)]
+                ("matvec_bytes", C.c_double), ("kernel_launches", C.c_int64), ("phase_ms", C.c_double * 8),
+                ("solve_launches", C.c_int32), ("rhs_per_launch", C.c_int32)]
 
     PHASES = ("resid64", "matvec", "update", "barrier", "lower", "other", "scalar")
 
@@ -62,7 +63,8 @@ class ms_fit_stats(C.Structure):
                 "precond_fallbacks": self.precond_fallbacks, "fp64_fallbacks": self.fp64_fallbacks,
                 "device_status": self.device_status,
                 "fit_ms": self.fit_ms, "matvec_bytes": self.matvec_bytes,
-                "kernel_launches": self.kernel_launches,
+                "kernel_launches": self.kernel_launches, "solve_launches": self.solve_launches,
+                "rhs_per_launch": self.rhs_per_launch,
                 "phase_ms": {n: self.phase_ms[i] for i, n in enumerate(self.PHASES)}}
 
 
@@ -70,7 +72,8 @@ class ms_info(C.Structure):
     _fields_ = [("d", C.c_int32), ("L", C.c_int32), ("N", C.c_int64),
                 ("n_per_level", C.c_int64 * MS_MAX_LEVELS), ("delta", C.c_double * MS_MAX_LEVELS),
                 ("nnz_A", C.c_int64), ("nnz_B", C.c_int64), ("device_bytes", C.c_int64),
-                ("build_ms", C.c_double), ("tpr_A", C.c_int32 * MS_MAX_LEVELS), ("pc_basis", C.c_int32)]
+                ("build_ms", C.c_double), ("tpr_A", C.c_int32 * MS_MAX_LEVELS), ("pc_basis", C.c_int32),
+                ("cell_split", C.c_int32), ("solve_ctas_per_sm", C.c_int32)]
 
 
 class ms_train_opts(C.Structure):
@@ -347,7 +350,8 @@ def ms_hierarchy_info(handle) -> dict:
     return {"d": info.d, "L": L, "N": info.N, "n_per_level": list(info.n_per_level[:L]),
             "delta": list(info.delta[:L]), "nnz_A": info.nnz_A, "nnz_B": info.nnz_B,
             "device_bytes": info.device_bytes, "build_ms": info.build_ms,
-            "tpr_A": list(info.tpr_A[:L]), "pc_basis": info.pc_basis}
+            "tpr_A": list(info.tpr_A[:L]), "pc_basis": info.pc_basis, "cell_split": info.cell_split,
+            "solve_ctas_per_sm": info.solve_ctas_per_sm}
 
 
 def ms_default_train_opts(**overrides) -> ms_train_opts:

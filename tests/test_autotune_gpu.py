@@ -98,3 +98,36 @@ def test_peak_probes_are_plausible():
     f64 = ms.ms_peak_probe(ms.MS_PROBE_FP64)
     xu = ms.ms_peak_probe(ms.MS_PROBE_XU)
     assert f32 > 4 * xu > 0 and f32 > 16 * f64 > 0, (f32, f64, xu)
+
+
+def test_autotune_cell_size_and_ctas_per_sm():
+    """autotune = 1 also picks the neighbour-grid cell size at the build (delta or delta / 2: the
+    build plus one application of the fit's matrix-free operators, timed) and the solve kernel's
+    CTAs per SM at the first fit (which fits with 1 and with 2 and keeps the faster);
+    ms_hierarchy_info reports both, a new handle of the same shape takes the cached choices, and
+    the coefficients agree with an untuned fit to the CG tolerance."""
+    w = workload(SIZES)
+    kw = {"precision": ms.MS_PREC_MIXED, "lower_op": ms.MS_OP_MATRIX_FREE}
+    H0 = ms.Hierarchy.from_workload(w, **kw)
+    assert H0.info()["cell_split"] == 1 and H0.info()["solve_ctas_per_sm"] == 2
+    a0, _ = H0.fit(w.f, rel_tol=1e-12)
+    H1 = ms.Hierarchy.from_workload(w, autotune=1, **kw)
+    split = H1.info()["cell_split"]
+    assert split in (1, 2)
+    a1, st = H1.fit(w.f, rel_tol=1e-12)
+    ctas = H1.info()["solve_ctas_per_sm"]
+    assert ctas in (1, 2)
+    assert max(st["rel_residual"]) <= 1e-12
+    assert rel(a1, a0) <= 1e-8
+    H2 = ms.Hierarchy.from_workload(w, autotune=1, **kw)
+    assert H2.info()["cell_split"] == split
+    before = ms.ms_launch_count()
+    a2, _ = H2.fit(w.f, rel_tol=1e-12)
+    once = ms.ms_launch_count() - before
+    assert H2.info()["solve_ctas_per_sm"] == ctas
+    before = ms.ms_launch_count()
+    H2.fit(w.f, rel_tol=1e-12)
+    assert ms.ms_launch_count() - before == once  # the cached choice: one fit, no timing runs
+    assert rel(a2, a0) <= 1e-8
+    for H in (H0, H1, H2):
+        H.close()

@@ -58,7 +58,12 @@ def assembled_jacobi(L):
     E = torch.zeros((N, ncol), dtype=torch.float64, device="cuda")
     idx = torch.arange(ncol, device="cuda")
     E[idx, idx] = 1.0
-    Y, st = H.fit(E, rel_tol=1e-13)  # D^{-1} E (input order)
+    # D^{-1} E (input order).  1e-13 where M is compared element-wise with the oracle (L <= 5);
+    # 1e-12 above, where the figures need five digits: with unit-vector columns an FP64 residual
+    # of 1e-13 is near kappa(A_l) eps on the finer grids, and whether a column reaches it
+    # depends on the order of its dot products' sums (1e-13 ran into the iteration cap at L = 6, 7
+    # when blocks of 32 columns shared one partitioned launch)
+    Y, st = H.fit(E, rel_tol=1e-13 if L <= 5 else 1e-12)
     assert st["device_status"] == 0 and st["sweeps"] == 0
     Yt = Y.t().contiguous()
     del E, Y
@@ -117,12 +122,13 @@ def test_figures_1_2_3_through_the_gpu_operators(L):
 def test_convergence_rate_theorem2():
     """Theorem 2 / Corollary 3: ||f - f_L||_{L2} <= C (C_1 mu^tau)^L ||f||, geometric in L.  The
     Franke function fitted on the paper's grids for L = 1..10 (plain FP64, rel_tol 1e-12) and
-    evaluated on a 256^2 query grid: the RMS errors of L <= 6 equal the oracle's (1e-6
-    relative), every level lowers the error, and the least-squares rate over L = 2..10 is below
-    1/2 (mu = 1/2 per level here; the oracle measures per-level ratios of 0.08-0.24, near
-    mu^tau = 2^-2.5 for phi_{3,1} in 2-D)."""
+    evaluated at 65,536 seeded random points (off every grid node: at the cell centres of a
+    256^2 grid, which are nodes of the 9- and 10-level grids, the interpolant is exact): the RMS
+    errors of L <= 6 equal the oracle's (1e-6 relative), every level lowers the error, and the
+    least-squares rate over L = 2..10 is below 1/2 (mu = 1/2 per level here; the oracle measures
+    per-level ratios of 0.08-0.3)."""
     import torch
-    Qh = inputs.query_grid(256, 2)
+    Qh = inputs.query_random(65536, 2)
     Q = torch.from_numpy(Qh).cuda()
     fq = inputs.franke(Qh)
     errs = []
@@ -139,7 +145,7 @@ def test_convergence_rate_theorem2():
             so = om.evaluate(w.levels, al, w.h, w.nu, 3, 1, Qh)
             eo = float(np.sqrt(np.mean((so - fq) ** 2)))
             assert abs(e - eo) <= 1e-6 * eo, (L, e, eo)
-    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert all(b < a for a, b in zip(errs, errs[1:])), f"RMS errors by level: {errs}"
     Ls = np.arange(2, 11)
     rate = float(np.exp(np.polyfit(Ls, np.log(errs[1:]), 1)[0]))
     assert rate < 0.5, (rate, errs)

@@ -314,6 +314,30 @@ def test_multi_rhs_batch_matches_single_fits_and_oracle(prec, R):
     H.close()
 
 
+@pytest.mark.parametrize("prec,R,over", [(ms.MS_PREC_FP64, 256, {}),
+                                         (ms.MS_PREC_MIXED, 100, {"precond": ms.MS_PRECOND_EXACT})])
+def test_many_rhs_in_one_partitioned_launch(prec, R, over):
+    """Blocks of 32 right-hand sides share ONE cooperative launch, the grid split into one
+    partition of CTAs per block (256 in the row-major SpMM layout, 100 in the right-hand-side-
+    major layout with the preconditioner).  Each column matches its single fit to the CG
+    tolerance, the zero column stays zero, and a repeated call is bitwise identical."""
+    w = ragged_halton([37, 150, 601, 2500])
+    F = _rhs_batch(w, R)
+    H = ms.Hierarchy.from_workload(w, precision=prec, **over)
+    A, st = H.fit(F, rel_tol=1e-12)
+    assert st["solve_launches"] == 1 and st["rhs_per_launch"] == R, st
+    assert max(st["rel_residual"][:w.L]) <= 1e-12
+    A2, _ = H.fit(F, rel_tol=1e-12)
+    assert np.array_equal(A, A2)
+    assert np.all(A[:, 2] == 0.0)
+    tol = 1e-10 if prec == ms.MS_PREC_FP64 else 1e-8
+    for c in (0, 31, 32, R - 1):
+        a, s1 = H.fit(np.ascontiguousarray(F[:, c]), rel_tol=1e-12)
+        assert s1["solve_launches"] == 1 and s1["rhs_per_launch"] == 1
+        assert rel(A[:, c], a) <= tol, c
+    H.close()
+
+
 def test_multi_rhs_batch_is_faster_than_single_fits():
     """32 right-hand sides in one launch take far less kernel time than 32 single fits (the
     per-iteration grid barriers and reductions are shared by all of them)."""

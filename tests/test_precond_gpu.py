@@ -106,12 +106,22 @@ def _random_params(w, seed, m):
     return th, mu, sig, np.concatenate([th, mu, sig]).astype(np.float32)
 
 
-@pytest.mark.parametrize("m", [1, 8])
+@pytest.mark.parametrize("m", [1, 8, 16])
 def test_network_forward_matches_oracle(m):
     """Rows of the network (candidates, then their FSAI combination) against the oracle's, on
-    the device's inputs (FP32 features, BF16-valued weights).  The combination runs in FP32 on
+    the device's inputs (FP32 features, BF16-valued weights; the device's network runs on the
+    tensor cores with the layer inputs split into two BF16 parts, and 17 m = 272 outputs take two
+    MMA widths).  788 points: six tiles of 128 and a ragged seventh.  The combination runs in FP32 on
     the device: compared in the patch's own metric, |g - g_ref|_K <= 1e-3 (|g|_K = 1), and the
-    self entry (g_self^2 = q, the quantity the criterion maximises) to 1e-3 relative."""
+    self entry (g_self^2 = q, the quantity the criterion maximises) to 1e-3 relative.  With
+    m = 16 candidates in a 17-point patch, S = U^T K U of these random weights has a condition
+    number near 4e8, above the FP32 rounding of its entries: the directions below the ridge
+    (1e-6 of the diagonal) are fixed by the ridge on both sides only up to that rounding.  The
+    self entry stays at 1e-3 (q is the criterion the combination maximises, so an error in y
+    along those directions changes it only to second order), while the distance in the patch
+    metric, first order in that error, is bounded by 3e-2 (the oracle's own combination in FP32,
+    LAPACK's sgesv on the same candidates, is up to 3e-2 from its FP64 one; candidates perturbed
+    by 2^-17, the BF16 split of the device's activations, move the FP64 rows by 5e-4)."""
     w = halton([37, 150, 601], 8.0, (2, 2))
     H = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED)
     th, mu, sig, p = _random_params(w, 5, m)
@@ -120,6 +130,7 @@ def test_network_forward_matches_oracle(m):
     got = H.inspect(ms.MS_INSPECT_PREDICT)
     off = om.level_offsets(w.levels)
     thb = bf16(th.astype(np.float32)).astype(np.float64)  # the weights the device uses
+    tol = 3e-2 if m == 16 else 1e-3
     mu32, sig32 = mu.astype(np.float32).astype(np.float64), sig.astype(np.float32).astype(np.float64)
     for l in range(w.L):
         X, delta, pat, _ = oracle_level_data(w, l)
@@ -131,7 +142,7 @@ def test_network_forward_matches_oracle(m):
             n = len(r)
             assert np.all(g[n:] == 0)
             e = g[:n] - r
-            assert math.sqrt(max(e @ Ks[i][:n, :n] @ e, 0.0)) <= 1e-3, (l, i)
+            assert math.sqrt(max(e @ Ks[i][:n, :n] @ e, 0.0)) <= tol, (l, i)
             assert abs(g[0] - r[0]) <= 1e-3 * r[0], (l, i)
     # exported parameters round-trip
     np.testing.assert_array_equal(H.precond_params(), p)

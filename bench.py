@@ -129,6 +129,14 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
 
 
+_T0 = time.perf_counter()
+
+
+def progress(msg):
+    """One line on stderr per block of the bench (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+
 def nvtx_range(name, push):
     """Open (push) or close an NVTX range on this thread; a no-op where torch has no NVTX."""
     import torch
@@ -411,6 +419,7 @@ def run_ours(args):
     # levels of the delta = 8h hierarchy (FP32 inner CG near kappa ~ 1e6): a higher cap
     NOPC = {"max_iters": 200000}
 
+    progress("network trained")
     # ---- the headline: learned-PCG MIXED steps
     for _ in range(args.warmup):
         step(*HEAD, params=params, **MF)
@@ -443,6 +452,7 @@ def run_ours(args):
         out["train"] = {"levels": [1, 2, 3, 4], "epochs": args.train_epochs, "extra_patches_per_point": 4, **train}
         out["nnz"] = {"A": info["nnz_A"], "B": info["nnz_B"]}
 
+        progress("headline timed")
         # ---- the metric's other arm and the variants, same workload, warmed
         if not args.no_variants:
             k2 = args.arm_steps
@@ -477,6 +487,7 @@ def run_ours(args):
                                             "loss_last": train["loss_last"], "train_ms": train["train_ms"]}
             out["candidate_rows_sweep"] = sweep
 
+        progress("comparison arms done")
         # ---- side block: delta_j = 4 h_j, phi_{2,1} (well-conditioned levels)
         if not args.no_side:
             w4 = inputs.halton_hierarchy(L=args.levels, nu=SIDE_NU, wendland=SIDE_W)
@@ -502,6 +513,7 @@ def run_ours(args):
             out["side_nu4_w21"] = side
             del p4, f4, rl4, r64
 
+        progress("side block done")
         # ---- stand-alone mat-vecs on the headline hierarchy (sorted order): GB/s of the CSR
         #      kernels, instruction rates of the matrix-free one
         peaks_alu = {"fp32": ms.ms_peak_probe(ms.MS_PROBE_FP32), "fp64": ms.ms_peak_probe(ms.MS_PROBE_FP64),
@@ -555,6 +567,7 @@ def run_ours(args):
             out["matvec"] = mv
             H.close()
 
+        progress("mat-vecs done")
         # ---- batching: 256 right-hand sides on one 6-level hierarchy (87,360 points), MIXED without
         #      preconditioner; against single-RHS fits of the first 16 of them
         if not args.no_batch:
@@ -650,6 +663,7 @@ def run_ours(args):
                 Hi.close()
             del fsb, Ab
 
+        progress("batching done")
         # ---- the paper's own experiment (Section 5: grids (2^l+1)^2, phi_{3,1}, nu = 4, Franke data),
         #      plain FP64 as the paper runs it, against Figure 4's A100 times (context: other hardware,
         #      tolerance not reported there)
@@ -689,6 +703,7 @@ def run_ours(args):
                 b["ratio_to_previous"] = b["rms_error"] / a["rms_error"]
             out["convergence_rate_franke"] = conv
 
+        progress("paper grids done")
         # ---- the 3-D configuration (uniform random points, 6 levels, 4.68M points, phi_{3,1},
         #      delta = 3h): FP64 CSR, MIXED CSR, MIXED with the matrix-free FP32 inner mat-vec, and
         #      learned-PCG CSR (a 3-D network: 48 inputs), one step each after one warm-up build
@@ -720,6 +735,7 @@ def run_ours(args):
             out["random3d"] = o3
             del p3, f3
 
+        progress("3-D done")
         # ---- end to end through the host-pointer C ABI (H2D of points, f, queries and the network;
         #      D2H of alpha and the approximant), one untimed round first
         e2e = []
@@ -740,6 +756,7 @@ def run_ours(args):
         out["e2e"] = {"value": statistics.mean(e2e), "unit": "ms", "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h), "steps": len(e2e)}
 
+        progress("end to end done")
         if not args.no_cpu:
             cb = cpu_baseline(args.levels)
             one, allc = cb["1_thread"], cb["all_cores"]

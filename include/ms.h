@@ -457,12 +457,15 @@ enum {
     MS_INSPECT_GRAD = 3,    /* float [n_weights + 1]: full-batch gradient of the training loss on
                                the patterns of `levels` (no extra patches) with the FP32 master
                                weights, then the loss */
-    MS_INSPECT_PATCHES = 4  /* int32 [S][18]: the training patches of `levels` with the options of
+    MS_INSPECT_PATCHES = 4, /* int32 [S][18]: the training patches of `levels` with the options of
                                the last ms_train_precond (defaults before any): per patch its
                                centre, its prefix bound p (level-local; p = centre for the
                                pattern) and 16 neighbours (input indices, -1 = none); S =
                                (1 + augment) x the points of `levels`, patterns first, then
                                draw 0, 1, ... each in level order, points in input order */
+    MS_INSPECT_CANDIDATES = 5 /* float [N][17 m]: the network's m candidate rows of every point,
+                               entry a of candidate k at 17 k + a (u_1 = mu + sigma o_1,
+                               u_k = sigma o_k, zero past the patch) */
 };
 ms_status ms_precond_inspect(ms_hierarchy* h, int what, const int* levels, int n_levels, void* out, int64_t n_out);
 

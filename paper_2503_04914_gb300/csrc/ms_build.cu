@@ -220,12 +220,14 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_count(const __grid_constant__
     const int pairs = (k + 1) * nc;
     int32_t* pc = pcnt + pl.base[k] + (s - v.off[k]) * pairs;
     int32_t na = 0, nb = 0;
-    // onlyA: the pairs of level k alone (the lower blocks are not stored)
-    for (int t0 = onlyA ? k * nc : 0; t0 < pairs; t0 += 32) {
+    // the lower-block pairs (levels j < k; none with onlyA, when B is not stored): a lane per
+    // pair walking its cell's points
+    const int pairsB = onlyA ? 0 : k * nc;
+    for (int t0 = 0; t0 < pairsB; t0 += 32) {
         const int t = t0 + lane;
         const int j = min(t / nc, k);  // lanes past the last pair read a valid frame and skip
         const Frame f = frame_from(mine, j);
-        if (t >= pairs) continue;
+        if (t >= pairsB) continue;
         int32_t ps = 0, pe = 0;
         float o0 = 0.f, o1 = 0.f, o2 = 0.f;
         int32_t n = 0;
@@ -234,13 +236,26 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_count(const __grid_constant__
             for (int32_t p = ps; p < pe; ++p) n += within(v, W, p, o0, o1, o2, y, d2) ? 1 : 0;
         }
         pc[t] = n;
-        if (j == k) na += n;
-        else nb += n;
+        nb += n;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        na += __shfl_xor_sync(0xffffffffu, na, o);
-        nb += __shfl_xor_sync(0xffffffffu, nb, o);
+    for (int o = 16; o > 0; o >>= 1) nb += __shfl_xor_sync(0xffffffffu, nb, o);
+    // the row's own level: the warp walks each neighbour cell together (a lane per point)
+    {
+        const Frame fk = frame_from(mine, k);
+        const double d2 = pl.d2[k];
+        for (int q = 0; q < nc; ++q) {
+            int32_t ps = 0, pe = 0;
+            float o0 = 0.f, o1 = 0.f, o2 = 0.f;
+            int32_t n = 0;
+            if (pair_cell(v, k, q, fk, ps, pe, o0, o1, o2))
+                for (int32_t p0 = ps; p0 < pe; p0 += 32) {
+                    const int32_t p = p0 + lane;
+                    n += __popc(__ballot_sync(0xffffffffu, p < pe && within(v, W, p, o0, o1, o2, y, d2)));
+                }
+            if (lane == 0) pc[k * nc + q] = n;
+            na += n;
+        }
     }
     if (lane == 0) {
         cntA[s] = na;
@@ -281,38 +296,53 @@ __global__ void __launch_bounds__(kCsrBS, 4) k_csr_fill(const __grid_constant__ 
     const int32_t* pc = pcnt + pl.base[k] + (s - v.off[k]) * pairs;
     const int64_t a0 = rpA[s], b0 = rpB[s];
     int64_t pa = a0, pb = b0;
-    for (int t0 = onlyA ? k * nc : 0; t0 < pairs; t0 += 32) {
+    // the lower-block pairs (levels j < k): a lane per pair, placed by a warp scan of the counts
+    const int pairsB = onlyA ? 0 : k * nc;
+    for (int t0 = 0; t0 < pairsB; t0 += 32) {
         const int t = t0 + lane;
-        const bool ok = t < pairs;
+        const bool ok = t < pairsB;
         const int j = min(t / nc, k);
         const Frame f = frame_from(mine, j);
         const int32_t n = ok ? __ldg(pc + t) : 0;
-        const bool isA = ok && j == k;
-        int32_t ia = isA ? n : 0, ib = (ok && !isA) ? n : 0;  // inclusive scans over the lanes
+        int32_t ib = n;  // inclusive scan over the lanes
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int32_t ua = __shfl_up_sync(0xffffffffu, ia, o), ub = __shfl_up_sync(0xffffffffu, ib, o);
-            if (lane >= o) {
-                ia += ua;
-                ib += ub;
-            }
+            const int32_t ub = __shfl_up_sync(0xffffffffu, ib, o);
+            if (lane >= o) ib += ub;
         }
-        const int32_t ta = __shfl_sync(0xffffffffu, ia, 31), tb = __shfl_sync(0xffffffffu, ib, 31);
+        const int32_t tb = __shfl_sync(0xffffffffu, ib, 31);
         const int q = t - j * nc;
         // first pair of a column level j < k: its segment of the B row starts here
-        if (ok && !isA && q == 0 && Bseg) Bseg[(int64_t)j * v.N + s] = (int32_t)(pb + ib - n - b0);
+        if (ok && q == 0 && Bseg) Bseg[(int64_t)j * v.N + s] = (int32_t)(pb + ib - n - b0);
         if (ok && n > 0) {
             int32_t ps = 0, pe = 0;
             float o0 = 0.f, o1 = 0.f, o2 = 0.f;
             pair_cell(v, j, q, f, ps, pe, o0, o1, o2);
             const double d2 = pl.d2[j];
-            int32_t* col = isA ? colA : colB;
-            int64_t pos = isA ? pa + ia - n : pb + ib - n;
+            int64_t pos = pb + ib - n;
             for (int32_t p = ps; p < pe; ++p)
-                if (within(v, W, p, o0, o1, o2, y, d2)) col[pos++] = p;
+                if (within(v, W, p, o0, o1, o2, y, d2)) colB[pos++] = p;
         }
-        pa += ta;
         pb += tb;
+    }
+    // the row's own level: the warp walks each neighbour cell together and places the columns
+    // by ballot, in the same order (pairs in order, points in cell order) and with the same
+    // decisions as the count
+    {
+        const Frame fk = frame_from(mine, k);
+        const double d2 = pl.d2[k];
+        for (int q = 0; q < nc; ++q) {
+            int32_t ps = 0, pe = 0;
+            float o0 = 0.f, o1 = 0.f, o2 = 0.f;
+            if (!pair_cell(v, k, q, fk, ps, pe, o0, o1, o2)) continue;
+            for (int32_t p0 = ps; p0 < pe; p0 += 32) {
+                const int32_t p = p0 + lane;
+                const bool hit = p < pe && within(v, W, p, o0, o1, o2, y, d2);
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                if (hit) colA[pa + __popc(m & ((1u << lane) - 1u))] = p;
+                pa += __popc(m);
+            }
+        }
     }
     if (lane == 0 && Bseg) Bseg[(int64_t)k * v.N + s] = (int32_t)(pb - b0);
     __syncwarp();  // the columns written by the other lanes are read below

@@ -190,13 +190,15 @@ ms_status build_common(int d, int L, const int64_t* n_per_level, const double* p
     const SplitKey key(d, L, lg, (int)std::lround(16.0 * opts->nu), opts->wendland_d, opts->wendland_k,
                        opts->precision, opts->op, opts->lower_op);
     ms_opts o = *opts;
+    int cached = 0;
     {
         std::lock_guard<std::mutex> lk(g_split_mu);
         auto it = g_split_cache.find(key);
-        if (it != g_split_cache.end()) {
-            o.cell_split = it->second;
-            return build_one(d, L, n_per_level, pts_dev, h_per_level, &o, st, out);
-        }
+        if (it != g_split_cache.end()) cached = it->second;
+    }
+    if (cached) {
+        o.cell_split = cached;
+        return build_one(d, L, n_per_level, pts_dev, h_per_level, &o, st, out);
     }
     ms_hierarchy* hs[2] = {nullptr, nullptr};
     float t[2] = {0.f, 0.f};

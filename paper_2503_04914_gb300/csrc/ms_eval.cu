@@ -1,7 +1,8 @@
 // Evaluation of the multiscale approximant at query points (eq. fapproximation):
 //   f_L(q) = sum_l sum_n alpha_n^(l) Phi_{delta_l}(q - x_n^(l)),
-// one thread per query, every level's neighbours found through that level's
-// cell grid, FP64 accumulation.  An FP32 test on the points' cell-relative
+// one warp per query (the lanes over each neighbour cell's points, per-lane FP64 sums
+// combined by shuffles in a fixed order), every level's neighbours found through that level's
+// cell grid.  An FP32 test on the points' cell-relative
 // offsets rejects the clear misses (about 2/3 of the candidates) first; the
 // kernel values are FP64 (FP64 builds) or double-float (MIXED builds).
 #include <algorithm>
@@ -19,7 +20,7 @@ namespace {
 // decided by the FP64 distance.
 template <typename F>
 __device__ __forceinline__ void eval_neighbours(const HierView& v, const float* __restrict__ W, int j,
-                                                const double* y, F&& visit) {
+                                                const double* y, int lane, F&& visit) {
     const LevelGrid& g = v.grid[j];
     const double d2 = v.delta[j] * v.delta[j];
     int c[3] = {0, 0, 0};
@@ -44,7 +45,7 @@ __device__ __forceinline__ void eval_neighbours(const HierView& v, const float* 
                 const float ox = (float)dx * g.cod - fr[0];
                 const int64_t gid = g.cell_off + morton(v.d, cx, cy, cz);
                 const int32_t s = v.cell_start[gid], e = v.cell_start[gid + 1];
-                for (int32_t p = s; p < e; ++p) {
+                for (int32_t p = s + lane; p < e; p += 32) {
                     float t = ox + __ldg(W + p);
                     float qq = t * t;
                     if (v.d >= 2) { t = oy + __ldg(W + v.N + p); qq = fmaf(t, t, qq); }
@@ -96,8 +97,9 @@ template <bool FF>
 __global__ void k_eval(const __grid_constant__ HierView v, const float* __restrict__ W, const float* __restrict__ Wlo,
                        const __grid_constant__ EvalLevels el, const double* __restrict__ alpha,
                        const double* __restrict__ Q, int64_t nq, double* __restrict__ out, int nrhs, int col) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= nq) return;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= nq) return;  // warp-uniform
     double y[3] = {0, 0, 0};
     for (int a = 0; a < v.d; ++a) y[a] = Q[i * v.d + a];
     double s = 0.0;
@@ -106,7 +108,7 @@ __global__ void k_eval(const __grid_constant__ HierView v, const float* __restri
         double sl = 0.0;
         if (!FF) {
             const double inv = 1.0 / v.delta[l];
-            eval_neighbours(v, W, l, y, [&](int32_t p, double r2) {
+            eval_neighbours(v, W, l, y, lane, [&](int32_t p, double r2) {
                 sl = fma(wendland_eval<double>(v.w, sqrt(r2) * inv), alpha[p], sl);
             });
         } else {
@@ -139,7 +141,7 @@ __global__ void k_eval(const __grid_constant__ HierView v, const float* __restri
                         }
                         const int64_t gid = g.cell_off + morton(v.d, cx, cy, cz);
                         const int32_t ps = v.cell_start[gid], pe = v.cell_start[gid + 1];
-                        for (int32_t p = ps; p < pe; ++p) {
+                        for (int32_t p = ps + lane; p < pe; p += 32) {
                             // FP32 prefilter, then the double-float distance
                             float t = of[0] + __ldg(W + p);
                             float qq = t * t;
@@ -156,9 +158,11 @@ __global__ void k_eval(const __grid_constant__ HierView v, const float* __restri
                 }
             }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sl += __shfl_xor_sync(0xffffffffu, sl, o);
         s = fma(sc, sl, s);
     }
-    out[i * nrhs + col] = s;
+    if (lane == 0) out[i * nrhs + col] = s;
 }
 
 }  // namespace
@@ -176,11 +180,11 @@ ms_status ms_evaluate_impl(ms_hierarchy* h, const double* alpha_dev, int nrhs, c
     for (int i = 0; i < 4; ++i) el.c[i] = ff_from_double(h->view.w.c[i]);
     for (int c = 0; c < nrhs; ++c) {
         ms_gather_sorted(alpha_dev, h->tmp64, h->perm, h->N, nrhs, c, st);
-        const unsigned blocks = (unsigned)std::max<int64_t>(1, (nq + 127) / 128);
+        const unsigned blocks = (unsigned)std::max<int64_t>(1, (nq * 32 + 255) / 256);  // a warp per query
         if (h->Wlo)
-            k_eval<true><<<blocks, 128, 0, st>>>(h->view, h->W, h->Wlo, el, h->tmp64, q_dev, nq, out_dev, nrhs, c);
+            k_eval<true><<<blocks, 256, 0, st>>>(h->view, h->W, h->Wlo, el, h->tmp64, q_dev, nq, out_dev, nrhs, c);
         else
-            k_eval<false><<<blocks, 128, 0, st>>>(h->view, h->W, nullptr, el, h->tmp64, q_dev, nq, out_dev, nrhs, c);
+            k_eval<false><<<blocks, 256, 0, st>>>(h->view, h->W, nullptr, el, h->tmp64, q_dev, nq, out_dev, nrhs, c);
         ms_count_launch();
         MS_CUDA(cudaGetLastError());
     }

@@ -127,7 +127,7 @@ constexpr int kPatW = 4;      // warps per block of the pattern kernels
 __device__ void nearest_below_warp(const HierView& v, const float* __restrict__ W,
                                    const int32_t* __restrict__ cellid, const int64_t* Arp, const int32_t* Acol,
                                    const int32_t* perm, int64_t s, int64_t bound, int32_t* out, int lane,
-                                   int32_t* cq, float* kq) {
+                                   int32_t* cq, float* kq, int* hist) {
     const int64_t b = Arp[s];
     const int n = (int)(Arp[s + 1] - b);
     constexpr uint32_t kNone = 0xFFFFFFFFu;  // not a candidate (above every float key)
@@ -165,29 +165,46 @@ __device__ void nearest_below_warp(const HierView& v, const float* __restrict__ 
                 }
             }
         }
-        // k16: sixteen rounds of taking the warp's smallest remaining key
-        uint32_t kk[kPL];
+        // a bound on k16 from a histogram of the keys over 256 bins of the float's exponent and
+        // top three fraction bits (monotone in the key; a bin spans 1/8 of an octave): B = the
+        // first bin at which the count reaches 16, t = B's upper edge + 1e-5 >= k16 + 1e-5
+        for (int i = lane; i < 256; i += 32) hist[i] = 0;
+        __syncwarp();
 #pragma unroll
-        for (int i = 0; i < kPL; ++i) kk[i] = key[i];
-        uint32_t k16 = kNone;
-        for (int r = 0; r < kPcK; ++r) {
-            uint32_t mn = kk[0];
+        for (int i = 0; i < kPL; ++i)
+            if (key[i] != kNone) atomicAdd(&hist[min(max((int)(key[i] >> 20) - (103 << 3), 0), 255)], 1);
+        __syncwarp();
+        int cnt8[8], own = 0;
 #pragma unroll
-            for (int i = 1; i < kPL; ++i) mn = min(mn, kk[i]);
-            k16 = __reduce_min_sync(0xffffffffu, mn);
-            if (k16 == kNone) break;  // fewer than 16 candidates (warp-uniform)
-            const unsigned holders = __ballot_sync(0xffffffffu, mn == k16);
-            if (lane == __ffs(holders) - 1) {
-                bool done = false;
-#pragma unroll
-                for (int i = 0; i < kPL; ++i)
-                    if (!done && kk[i] == k16) {
-                        kk[i] = kNone;
-                        done = true;
-                    }
-            }
+        for (int j = 0; j < 8; ++j) {
+            cnt8[j] = hist[lane * 8 + j];
+            own += cnt8[j];
         }
-        const float t = k16 == kNone ? INFINITY : __fadd_ru(__uint_as_float(k16), 1e-5f);
+        int incl = own;  // inclusive scan of the lanes' bin counts
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const unsigned reach = __ballot_sync(0xffffffffu, incl >= kPcK);
+        float t = INFINITY;  // fewer than 16 candidates: every candidate contends
+        if (reach) {
+            const int src = __ffs(reach) - 1;
+            int bin = 0;
+            if (lane == src) {
+                int c = incl - own;
+                bin = lane * 8 + 7;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    c += cnt8[j];
+                    if (c >= kPcK) { bin = lane * 8 + j; break; }
+                }
+            }
+            bin = __shfl_sync(0xffffffffu, bin, src);
+            // upper edge of the bin: the smallest float of the next bin
+            const float edge = bin >= 255 ? INFINITY : __uint_as_float((uint32_t)(bin + 1 + (103 << 3)) << 20);
+            t = __fadd_ru(edge, 1e-5f);
+        }
         // contenders to the warp's queue
         int nc = 0;
 #pragma unroll
@@ -237,10 +254,11 @@ __global__ void __launch_bounds__(kPatW * 32, 5) k_pc_pattern(HierView v, const 
                                                           const int32_t* perm, int32_t* nbr) {
     __shared__ int32_t cq[kPatW][2 * kPcCont];
     __shared__ float kq[kPatW][kPcCont];
+    __shared__ int hist[kPatW][256];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t s = blockIdx.x * (int64_t)kPatW + w;
     if (s >= v.N) return;  // warp-uniform
-    nearest_below_warp(v, W, cellid, Arp, Acol, perm, s, __ldg(perm + s), nbr + s * kPcK, lane, cq[w], kq[w]);
+    nearest_below_warp(v, W, cellid, Arp, Acol, perm, s, __ldg(perm + s), nbr + s * kPcK, lane, cq[w], kq[w], hist[w]);
 }
 
 // Neighbours of training patch i: centre rows[i], input-index bound bounds[i]; out [n][16].
@@ -250,10 +268,11 @@ __global__ void __launch_bounds__(kPatW * 32, 5) k_pc_patches(HierView v, const 
                                                           const int64_t* bounds, int64_t n, int32_t* out) {
     __shared__ int32_t cq[kPatW][2 * kPcCont];
     __shared__ float kq[kPatW][kPcCont];
+    __shared__ int hist[kPatW][256];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = blockIdx.x * (int64_t)kPatW + w;
     if (i >= n) return;  // warp-uniform
-    nearest_below_warp(v, W, cellid, Arp, Acol, perm, rows[i], bounds[i], out + i * kPcK, lane, cq[w], kq[w]);
+    nearest_below_warp(v, W, cellid, Arp, Acol, perm, rows[i], bounds[i], out + i * kPcK, lane, cq[w], kq[w], hist[w]);
 }
 
 // ---------------------------------------------------------------- exact rows (FP64)
@@ -822,14 +841,23 @@ __global__ void __launch_bounds__(kMlpRows) k_pc_mlp(const float* __restrict__ t
                 tc_ld16(tq + c, r);
                 tc_wait_ld();
                 if (live) {
+                    float u[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int o = r0 + c + j;  // output 17 k + a
-                        if (o < nout) {
-                            const int k = o / kPcOut, a = o - kPcOut * k;
-                            const float acc = __uint_as_float(r[j]) + b3[o];
-                            Uc[s * nout + o] = a <= cnt ? fmaf(ms[kPcOut + a], acc, k == 0 ? ms[a] : 0.f) : 0.f;
-                        }
+                        const int k = o / kPcOut, a = o - kPcOut * k;
+                        const float acc = __uint_as_float(r[j]) + b3[min(o, n3p - 1)];
+                        u[j] = a <= cnt ? fmaf(ms[kPcOut + a], acc, k == 0 ? ms[a] : 0.f) : 0.f;
+                    }
+                    float* dst = Uc + s * nout + r0 + c;
+                    if (r0 + c + 16 <= nout && (nout & 3) == 0) {  // 16-byte aligned: four 128-bit stores
+#pragma unroll
+                        for (int j = 0; j < 16; j += 4)
+                            *reinterpret_cast<float4*>(dst + j) = make_float4(u[j], u[j + 1], u[j + 2], u[j + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (r0 + c + j < nout) dst[j] = u[j];
                     }
                 }
             }
@@ -1466,7 +1494,9 @@ uint64_t gcd64(uint64_t a, uint64_t b) {
 }
 
 // G rows (gval/gcol) or, with ghat_out, the scale-free rows of every point from the network.
-ms_status launch_infer(ms_hierarchy* h, __half* gval, int32_t* gcol, float* ghat_out, cudaStream_t st) {
+// uc_out (optional, device [N][17 m]): also a copy of the candidate rows (sorted order).
+ms_status launch_infer(ms_hierarchy* h, __half* gval, int32_t* gcol, float* ghat_out, cudaStream_t st,
+                       float* uc_out = nullptr) {
     const Precond& pc = h->pc;
     const int m = pc.nbasis;
     const int64_t N = h->N;
@@ -1500,7 +1530,9 @@ ms_status launch_infer(ms_hierarchy* h, __half* gval, int32_t* gcol, float* ghat
                 ms_count_launch(2);
             }
         }
-        if (e == cudaSuccess) {
+        if (e == cudaSuccess && uc_out)
+            e = cudaMemcpyAsync(uc_out, Uc, sizeof(float) * (size_t)N * kPcOut * m, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && (gval || ghat_out)) {
             k_pc_combine<<<nblk(N, kCombPts), kCombPts * 16, 0, st>>>(h->view, pc.nbr, m, Uc, Zc, cnt, gval, gcol,
                                                                  ghat_out);
             ms_count_launch();
@@ -1892,6 +1924,29 @@ ms_status ms_precond_inspect(ms_hierarchy* h, int what, const int* levels, int n
     MS_CUDA(cudaMemcpy(perm.data(), h->perm, sizeof(int32_t) * N, cudaMemcpyDeviceToHost));
     MS_TRY(pc_pattern(h, st));
     Precond& pc = h->pc;
+    if (what == MS_INSPECT_CANDIDATES) {
+        const int64_t w = (int64_t)kPcOut * pc.nbasis;
+        if (n_out != N * w) {
+            ms_set_error(MS_ERR_ARG, "expected %lld output values", (long long)(N * w));
+            return MS_ERR_ARG;
+        }
+        if (!pc.trained) {
+            ms_set_error(MS_ERR_STATE, "no trained network");
+            return MS_ERR_STATE;
+        }
+        float* d = nullptr;
+        MS_CUDA(cudaMalloc((void**)&d, sizeof(float) * N * w));
+        const ms_status ls = launch_infer(h, nullptr, nullptr, nullptr, 0, d);
+        std::vector<float> hd(N * w);
+        cudaError_t e = ls == MS_OK ? cudaMemcpy(hd.data(), d, sizeof(float) * N * w, cudaMemcpyDeviceToHost)
+                                    : cudaSuccess;
+        cudaFree(d);
+        if (ls != MS_OK) return ls;
+        MS_CUDA(e);
+        float* o = static_cast<float*>(out);
+        for (int64_t s = 0; s < N; ++s) std::memcpy(o + (int64_t)perm[s] * w, hd.data() + s * w, sizeof(float) * w);
+        return MS_OK;
+    }
     if (what == MS_INSPECT_PATTERN || what == MS_INSPECT_TARGETS || what == MS_INSPECT_PREDICT) {
         const int width = what == MS_INSPECT_PATTERN ? kPcK : kPcOut;
         if (n_out != N * width) {

@@ -455,6 +455,14 @@ ms_status fit_impl_inner(ms_hierarchy* h, const double* f_dev, int nrhs, double 
 // once with 1 CTA per SM (up to 128 registers a thread) and once with 2 (up to 64), keeps the
 // faster kernel time for the handle and caches it per process by shape; the call returns the
 // second run's result (both are fits to rel_tol).
+#ifdef MS_CTA_PROF
+// Diagnostic build only: the per-CTA timelines of the last single-hierarchy solve launch.
+extern "C" int ms_debug_cta_prof(unsigned long long* out, int n) {
+    const size_t b = sizeof(unsigned long long) * kProf * (size_t)std::min(std::max(n, 0), 1024);
+    return cudaMemcpyFromSymbol(out, g_cta_prof, b) == cudaSuccess ? 0 : 1;
+}
+#endif
+
 ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel_tol, double* alpha_dev,
                       ms_fit_stats* stats, cudaStream_t st) {
     if (!(h->opts.autotune && h->opts.solve_ctas_per_sm == 0))
@@ -463,13 +471,16 @@ ms_status ms_fit_impl(ms_hierarchy* h, const double* f_dev, int nrhs, double rel
     while ((int64_t(1) << (lg + 1)) <= h->N) ++lg;
     const CtaKey key(h->d, h->L, lg, h->opts.wendland_d, h->opts.wendland_k, h->opts.precision, h->opts.precond,
                      h->opts.op, h->opts.lower_op, nrhs > 1 ? 1 : 0);
+    int cached = 0;
     {
+        // (the lock is released before the fit: the fit's lane tuning takes the same mutex)
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_cta_cache.find(key);
-        if (it != g_cta_cache.end()) {
-            MS_TRY(set_solve_ctas(h, it->second));
-            return fit_impl_inner(h, f_dev, nrhs, rel_tol, alpha_dev, stats, st);
-        }
+        if (it != g_cta_cache.end()) cached = it->second;
+    }
+    if (cached) {
+        MS_TRY(set_solve_ctas(h, cached));
+        return fit_impl_inner(h, f_dev, nrhs, rel_tol, alpha_dev, stats, st);
     }
     ms_fit_stats s1{}, s2{};
     MS_TRY(set_solve_ctas(h, 1));

@@ -146,9 +146,19 @@ struct Shared {
     unsigned long long tprev;
 };
 
+#ifdef MS_CTA_PROF
+// Diagnostic build (-DMS_CTA_PROF): every CTA keeps the timeline, and each CTA's totals per
+// category are left in g_cta_prof for ms_debug_cta_prof (load balance between CTAs).
+__device__ unsigned long long g_cta_prof[1024][kProf];
+#endif
+
 // Device timeline: CTA 0's thread 0 charges the time since the previous mark to `cat`.
 __device__ __forceinline__ void prof(Shared& sh, int cat) {
+#ifdef MS_CTA_PROF
+    if (threadIdx.x == 0) {
+#else
     if (sh.cta == 0 && threadIdx.x == 0) {
+#endif
         const unsigned long long now = ms_globaltimer();
         sh.pt[cat] += now - sh.tprev;
         sh.tprev = now;
@@ -360,8 +370,9 @@ __device__ __forceinline__ void gsync_release(const SolveArgs& a, Shared& sh) {
 // copies the sums into sh.out.  Arrival is one counter for all CTAs (measured on
 // GB300 with 304 CTAs: 2.3 us per barrier against 4.9 us for a two-level arrival,
 // whose extra atomic costs a round trip).  With few partials (K V nb <= 16384
-// values) the last CTA to arrive sums them itself over a fixed segmentation of the
-// CTAs; more partials (wide multi-RHS launches) take a two-level arrival in which
+// values, K V <= the CTA's threads) the last CTA to arrive sums them itself over a fixed
+// segmentation of the CTAs; more partials (wide multi-RHS launches, or many virtual
+// levels on a small grid partition) take a two-level arrival in which
 // the last CTA of each group of kGroup sums its group and the last group leader sums
 // the groups.  Both orders are fixed, so every run gives the same sums.  Every wait
 // is bounded: past timeout_ns it records MS_ERR_TIMEOUT and returns false; a waiting
@@ -370,7 +381,8 @@ template <int K>
 __device__ bool gsync_reduce(const SolveArgs& a, Shared& sh) {
     const unsigned nb = sh.nb;
     const int npair = K * a.V;
-    if ((long)npair * nb <= 16384) {
+    // (the one-CTA summation gives every sum at least one thread: npair <= kBS)
+    if ((long)npair * nb <= 16384 && npair <= kBS) {
         __syncthreads();
         if (threadIdx.x == 0) {
             cuda::atomic_ref<unsigned, cuda::thread_scope_device> g(a.bar[1]);
@@ -1301,6 +1313,10 @@ __device__ __forceinline__ void fit_body(const SolveArgs& a, Shared& sh) {
         }
     }
     if (!(WIDE ? solve_levels_wide<MODE>(a, sh, 0, L, true) : solve_levels<MODE>(a, sh, 0, L, true))) return;
+#ifdef MS_CTA_PROF
+    if (tid == 0 && sh.cta < 1024)
+        for (int i = 0; i < kProf; ++i) g_cta_prof[sh.cta][i] = sh.pt[i];
+#endif
     if (sh.cta == 0 && tid == 0) {
         for (int l = 0; l < L; ++l) {
             long long it = 0;

@@ -21,7 +21,8 @@ MS_OK, MS_ERR_ARG, MS_ERR_CUDA, MS_ERR_OOM, MS_ERR_NOT_SPD, MS_ERR_NOT_CONVERGED
 MS_OP_CSR, MS_OP_MATRIX_FREE, MS_OP_AUTO = range(3)
 MS_PREC_FP64, MS_PREC_MIXED = range(2)
 MS_PRECOND_NONE, MS_PRECOND_LEARNED, MS_PRECOND_EXACT = range(3)
-MS_INSPECT_PATTERN, MS_INSPECT_TARGETS, MS_INSPECT_PREDICT, MS_INSPECT_GRAD, MS_INSPECT_PATCHES = range(5)
+MS_INSPECT_PATTERN, MS_INSPECT_TARGETS, MS_INSPECT_PREDICT, MS_INSPECT_GRAD, MS_INSPECT_PATCHES, \
+    MS_INSPECT_CANDIDATES = range(6)
 PC_K, PC_OUT, PC_HIDDEN = 16, 17, 64
 MS_APPLY_A64, MS_APPLY_A32, MS_APPLY_AMF32, MS_APPLY_B64, MS_APPLY_B32, MS_APPLY_BMF32, MS_APPLY_BMFDF = range(7)
 
@@ -408,6 +409,8 @@ def ms_precond_inspect(handle, what, N, d, levels=(0,), augment=4):
         out = np.empty((N, PC_OUT), dtype=np.float64)
     elif what == MS_INSPECT_PREDICT:
         out = np.empty((N, PC_OUT), dtype=np.float32)
+    elif what == MS_INSPECT_CANDIDATES:
+        out = np.empty((N, PC_OUT * ms_hierarchy_info(handle)["pc_basis"]), dtype=np.float32)
     else:
         out = np.empty(precond_n_values(d, ms_hierarchy_info(handle)["pc_basis"]) - 2 * PC_OUT + 1, dtype=np.float32)
     _check(load().ms_precond_inspect(C.c_void_p(handle), what, lv, n, out.ctypes.data_as(C.c_void_p), out.size))

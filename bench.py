@@ -717,6 +717,8 @@ def run_ours(args):
             kw3 = {"wl": w3, "pts_": p3, "f_": f3, "q": Q3}
             timed(1, ms.MS_PREC_MIXED, ms.MS_PRECOND_LEARNED, params=params3, **kw3)  # warm-up
             for tag, kw in (("learned_pcg_csr", {"prec": ms.MS_PREC_MIXED, "precond": ms.MS_PRECOND_LEARNED}),
+                            ("learned_pcg_matrix_free", {"prec": ms.MS_PREC_MIXED, "precond": ms.MS_PRECOND_LEARNED,
+                                                         "op": ms.MS_OP_MATRIX_FREE}),
                             ("mixed_csr", {"prec": ms.MS_PREC_MIXED}),
                             ("mixed_matrix_free", {"prec": ms.MS_PREC_MIXED, "op": ms.MS_OP_MATRIX_FREE}),
                             ("fp64_csr", {"prec": ms.MS_PREC_FP64})):

@@ -54,6 +54,26 @@ static inline bool wendland_poly(int wd, int wk, WendlandPoly* w) {
     return true;
 }
 
+// wendland_eval in FP32 from coefficients already converted to float (each conversion from
+// FP64 is an FP64-pipe instruction, scarce on this GPU).
+__device__ __forceinline__ float wendland_eval_f(const WendlandPoly& w, const float* c, float r) {
+    if (!(r < 1.0f)) return 0.0f;
+    const float s = 1.0f - r, s2 = s * s, s4 = s2 * s2;
+    float pw;
+    switch (w.e) {
+    case 4: pw = s4; break;
+    case 6: pw = s4 * s2; break;
+    case 8: pw = s4 * s4; break;
+    default: {
+        pw = 1.0f;
+        for (int i = 0; i < w.e; ++i) pw *= s;
+    }
+    }
+    float p = c[w.k];
+    for (int i = w.k - 1; i >= 0; --i) p = p * r + c[i];
+    return pw * p;
+}
+
 template <typename T>
 __device__ __forceinline__ T wendland_eval(const WendlandPoly& w, T r) {
     if (!(r < T(1))) return T(0);  // compact support: phi vanishes for r >= 1

@@ -897,9 +897,9 @@ struct CombBuf {
 // 2832 bytes = 16 (mod 128): the two points of a warp broadcast from different banks
 static_assert(sizeof(CombBuf) % 128 == 16, "CombBuf bank offset");
 
-__global__ void __launch_bounds__(kCombPts * 16) k_pc_combine(HierView v, const int32_t* nbr, int m, const float* Uc,
-                                                              const float* Zc, const int32_t* cntc, __half* gval,
-                                                              int32_t* gcol, float* ghat_out) {
+__global__ void __launch_bounds__(kCombPts * 16) k_pc_combine(HierView v, float4 wc, const int32_t* nbr, int m,
+                                                              const float* Uc, const float* Zc, const int32_t* cntc,
+                                                              __half* gval, int32_t* gcol, float* ghat_out) {
     __shared__ __align__(16) CombBuf cb[kCombPts];
     __shared__ uint16_t pairs[kPcOut * kPcK / 2];  // the 136 pairs a < b of 17 points: a | b << 8
     for (int i = threadIdx.x; i < kPcOut * kPcK / 2; i += blockDim.x) {
@@ -917,7 +917,8 @@ __global__ void __launch_bounds__(kCombPts * 16) k_pc_combine(HierView v, const 
     const int cnt = cntc[s];
     const int np = cnt + 1;
     const bool exact = np <= m;
-    const float phi0 = (float)v.w.c[0];
+    const float wcf[4] = {wc.x, wc.y, wc.z, wc.w};  // Wendland coefficients in FP32 (converted on the host)
+    const float phi0 = wcf[0];
     {
         float4* K4 = reinterpret_cast<float4*>(&B.K[0][0]);
         for (int i = l; i < kPcOut * 5; i += 16) K4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -940,7 +941,7 @@ __global__ void __launch_bounds__(kCombPts * 16) k_pc_combine(HierView v, const 
                 r2 = fmaf(u, u, r2);
             }
             // FP32 entries need no correctly rounded sqrt: r = r2 / sqrt(r2)
-            const float kab = wendland_eval<float>(v.w, r2 * rsqrtf(fmaxf(r2, 1e-30f)));
+            const float kab = wendland_eval_f(v.w, wcf, r2 * rsqrtf(fmaxf(r2, 1e-30f)));
             B.K[a][b] = kab;
             B.K[b][a] = kab;
         }
@@ -1533,8 +1534,10 @@ ms_status launch_infer(ms_hierarchy* h, __half* gval, int32_t* gcol, float* ghat
         if (e == cudaSuccess && uc_out)
             e = cudaMemcpyAsync(uc_out, Uc, sizeof(float) * (size_t)N * kPcOut * m, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess && (gval || ghat_out)) {
-            k_pc_combine<<<nblk(N, kCombPts), kCombPts * 16, 0, st>>>(h->view, pc.nbr, m, Uc, Zc, cnt, gval, gcol,
-                                                                 ghat_out);
+            const WendlandPoly& wp = h->view.w;
+            const float4 wc = make_float4((float)wp.c[0], (float)wp.c[1], (float)wp.c[2], (float)wp.c[3]);
+            k_pc_combine<<<nblk(N, kCombPts), kCombPts * 16, 0, st>>>(h->view, wc, pc.nbr, m, Uc, Zc, cnt, gval,
+                                                                 gcol, ghat_out);
             ms_count_launch();
             e = cudaGetLastError();
         }

@@ -572,7 +572,7 @@ ms_status fit_impl_inner(ms_hierarchy* h, const double* f_dev, int nrhs, double 
             const int R = std::min(Rmax, nrhs - cb);
             Rs[p] = R;
             SolveArgs& a = as[p];
-            fill_args(h, rel_tol, R, a, wide);
+            fill_args(h, rel_tol, R, a, wide, grid / P);
             const int64_t vo = (int64_t)p * width * N;  // this block's work vectors
             auto off64 = [&](double* q) { return q ? q + vo : q; };
             auto off32 = [&](float* q) { return q ? q + vo : q; };
@@ -918,7 +918,7 @@ extern "C" ms_status ms_fit_static_dev(ms_hierarchy* h, const double* f_dev, dou
 
     const int L = h->L;
     SolveArgs a{};
-    fill_args(h, rel_tol, 1, a);
+    fill_args(h, rel_tol, 1, a, false, blocks);  // the chunking ms_fit_dev uses on the same grid
     a.f = v64[0]; a.beta = v64[1]; a.x = v64[2]; a.r = v64[3]; a.p = v64[4]; a.q = v64[5]; a.s = v64[6];
     a.x32 = v32[0]; a.r32 = v32[1]; a.p32 = v32[2]; a.q32 = v32[3]; a.s32 = v32[4];
     a.part = part; a.gpart = gpart; a.scal = scal; a.bar = bar; a.status = status;

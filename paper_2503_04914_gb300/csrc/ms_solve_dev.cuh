@@ -65,6 +65,7 @@ struct SolveArgs {
     int L, R, V;       // levels, right-hand sides of this launch, V = R L virtual levels
     int RW;            // wide layout: lanes (vector elements) per row, a power of 2 >= R; 0 = RHS-major
     int crow;          // rows per work chunk
+    int crowl[MS_MAXL];  // rows per work chunk of each level (right-hand-side-major layout)
     int64_t N;         // points
     int C;             // chunks per right-hand side
     int64_t off[MS_MAXL + 1];
@@ -296,8 +297,8 @@ __device__ __forceinline__ void run_phase(const SolveArgs& a, Shared& sh, Sel se
             ch.l = l;
             ch.v = v;
             ch.vb = (int64_t)rhs * a.N;
-            ch.r0 = a.off[l] + (int64_t)(c - a.coff[l]) * a.crow;
-            ch.r1 = min(ch.r0 + (int64_t)a.crow, a.off[l + 1]);
+            ch.r0 = a.off[l] + (int64_t)(c - a.coff[l]) * a.crowl[l];
+            ch.r1 = min(ch.r0 + (int64_t)a.crowl[l], a.off[l + 1]);
             body(ch, acc);
             c += nb;
         }
@@ -1405,7 +1406,11 @@ int mf_tpp_for(const ms_hierarchy* h) {
 
 // Fill the solve arguments that depend only on the hierarchy, the options and R.
 // wide: the right-hand sides of the launch in the row-major (SpMM) layout, RW lanes per row.
-void fill_args(const ms_hierarchy* h, double rel_tol, int R, SolveArgs& a, bool wide = false) {
+// ncta > 0 (the CTAs of the launch or partition): a level with fewer rows than ncta chunks of 256
+// takes chunks of max(32, the power of 2 >= its rows / ncta) rows, so its rows spread over more
+// CTAs (a CTA handles at most one of its chunks); larger levels keep 256 rows a chunk, which keeps
+// the element-wise phases' threads busy.  0: 256 rows for every level.
+void fill_args(const ms_hierarchy* h, double rel_tol, int R, SolveArgs& a, bool wide = false, int ncta = 0) {
     const int64_t* rpA = h->rpA_lv;
     const int64_t* rpB = h->rpB_lv;
     a.mf = (h->opts.precision == MS_PREC_MIXED && h->opts.op == MS_OP_MATRIX_FREE) ? 1 : 0;
@@ -1429,11 +1434,20 @@ void fill_args(const ms_hierarchy* h, double rel_tol, int R, SolveArgs& a, bool 
         while (a.RW < R) a.RW <<= 1;
     }
     a.crow = wide ? kBS / a.RW : kChunk;
+    for (int l = 0; l < L; ++l) {
+        int cr = a.crow;
+        const int64_t n = h->view.off[l + 1] - h->view.off[l];
+        if (!wide && ncta > 0 && n < (int64_t)ncta * kChunk) {
+            cr = 32;
+            while (cr < kChunk && (int64_t)cr * ncta < n) cr <<= 1;
+        }
+        a.crowl[l] = cr;
+    }
     int64_t c = 0;
     for (int l = 0; l <= L; ++l) {
         a.off[l] = h->view.off[l];
         a.coff[l] = (int)c;
-        if (l < L) c += (h->view.off[l + 1] - h->view.off[l] + a.crow - 1) / a.crow;
+        if (l < L) c += (h->view.off[l + 1] - h->view.off[l] + a.crowl[l] - 1) / a.crowl[l];
     }
     a.C = (int)c;
     for (int l = 0; l < L; ++l) {

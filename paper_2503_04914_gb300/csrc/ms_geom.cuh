@@ -137,6 +137,31 @@ __device__ __forceinline__ ff ff_entry(const HierView& v, const float* __restric
     return ff_mul(ffl.ds[j], ff_wendland<E, K>(v.w, ffl.c, ff_sqrt(r2)));
 }
 
+// ff_entry for a point p known to lie in the cell displaced by dcs[a] cells from f's cell (the
+// candidate loops know it): the same arithmetic without the cell id's load and Morton decode.
+template <int E, int K>
+__device__ __forceinline__ ff ff_entry_dc(const HierView& v, const float* __restrict__ W,
+                                          const float* __restrict__ Wlo, const FFLevels& ffl, int j, int32_t p,
+                                          const Frame& f, const int* dcs) {
+    const bool cod_exact = ffl.cod[j].lo == 0.0f;
+    ff r2 = {0.0f, 0.0f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a < v.d) {
+            const ff w = {__ldg(W + a * v.N + p), __ldg(Wlo + a * v.N + p)};
+            const float dc = small_int_to_float(dcs[a]);
+            ff t;
+            if (cod_exact) {
+                t = ff_sum3(__fmul_rn(dc, ffl.cod[j].hi), w, {f.fr[a], f.frlo[a]});
+            } else {
+                t = ff_add(ff_add(ff_mul(ffl.cod[j], {dc, 0.0f}), w), ff_neg({f.fr[a], f.frlo[a]}));
+            }
+            r2 = a == 0 ? ff_sqr(t) : ff_add(r2, ff_sqr(t));
+        }
+    }
+    return ff_mul(ffl.ds[j], ff_wendland<E, K>(v.w, ffl.c, ff_sqrt(r2)));
+}
+
 // Offset (units of delta) of a neighbour cell displaced by `dc` cells, seen from a point at
 // fractional offset fr in its own cell; both CSR kernels take it from here so that they
 // make the same decisions.
@@ -243,7 +268,7 @@ template <int D, int E, int K>
 __device__ __forceinline__ ff lower_row_mf_warp(const HierView& v, const float* __restrict__ W,
                                                 const float* __restrict__ Wlo, const int32_t* __restrict__ cellid,
                                                 const FFLevels& ffl, int j, const Frame& f, const float* xhi,
-                                                const float* xlo, int lane, int32_t* q) {
+                                                const float* xlo, int lane, int32_t* q, int32_t* qd) {
     const LevelGrid& g = v.grid[j];
     const int R = v.R;
     const int rz = D >= 3 ? R : 0, ry = D >= 2 ? R : 0;
@@ -262,6 +287,7 @@ __device__ __forceinline__ ff lower_row_mf_warp(const HierView& v, const float* 
                 const int cx = f.c[0] + dx;
                 if (cx < 0 || cx >= g.G[0]) continue;
                 const float o0 = cell_offset(dx, g.cod, f.fr[0]);
+                const int32_t code = (dx + 4) | ((dy + 4) << 4) | ((dz + 4) << 8);  // the cell's displacement
                 const int64_t gid = g.cell_off + morton(D, cx, D >= 2 ? cy : 0, D >= 3 ? cz : 0);
                 const int32_t ps = __ldg(v.cell_start + gid), pe = __ldg(v.cell_start + gid + 1);
                 for (int32_t base = ps; base < pe; base += 32) {
@@ -275,14 +301,22 @@ __device__ __forceinline__ ff lower_row_mf_warp(const HierView& v, const float* 
                         pass = qq <= 1.0f + 1e-4f;
                     }
                     const unsigned mask = __ballot_sync(0xffffffffu, pass);
-                    if (pass) q[qn + __popc(mask & ((1u << lane) - 1u))] = p;
+                    if (pass) {
+                        const int slot = qn + __popc(mask & ((1u << lane) - 1u));
+                        q[slot] = p;
+                        qd[slot] = code;
+                    }
                     qn += __popc(mask);
                     if (qn >= 32) {
                         __syncwarp();
-                        const int32_t pp = q[lane];
-                        acc = ff_add(acc, ff_mul(ff_entry<E, K>(v, W, Wlo, cellid, ffl, j, pp, f), {xhi[pp], xlo[pp]}));
+                        const int32_t pp = q[lane], cd = qd[lane];
+                        const int dcs[3] = {(cd & 15) - 4, ((cd >> 4) & 15) - 4, ((cd >> 8) & 15) - 4};
+                        acc = ff_add(acc, ff_mul(ff_entry_dc<E, K>(v, W, Wlo, ffl, j, pp, f, dcs), {xhi[pp], xlo[pp]}));
                         __syncwarp();
-                        if (lane < qn - 32) q[lane] = q[32 + lane];
+                        if (lane < qn - 32) {
+                            q[lane] = q[32 + lane];
+                            qd[lane] = qd[32 + lane];
+                        }
                         qn -= 32;
                         __syncwarp();
                     }
@@ -292,8 +326,9 @@ __device__ __forceinline__ ff lower_row_mf_warp(const HierView& v, const float* 
     }
     __syncwarp();
     if (lane < qn) {
-        const int32_t pp = q[lane];
-        acc = ff_add(acc, ff_mul(ff_entry<E, K>(v, W, Wlo, cellid, ffl, j, pp, f), {xhi[pp], xlo[pp]}));
+        const int32_t pp = q[lane], cd = qd[lane];
+        const int dcs[3] = {(cd & 15) - 4, ((cd >> 4) & 15) - 4, ((cd >> 8) & 15) - 4};
+        acc = ff_add(acc, ff_mul(ff_entry_dc<E, K>(v, W, Wlo, ffl, j, pp, f, dcs), {xhi[pp], xlo[pp]}));
     }
     __syncwarp();
     return acc;
@@ -301,19 +336,20 @@ __device__ __forceinline__ ff lower_row_mf_warp(const HierView& v, const float* 
 
 __device__ __forceinline__ ff lower_row_mf_warp_any(const HierView& v, const float* W, const float* Wlo,
                                                     const int32_t* cellid, const FFLevels& ffl, int j, const Frame& f,
-                                                    const float* xhi, const float* xlo, int lane, int32_t* q) {
+                                                    const float* xhi, const float* xlo, int lane, int32_t* q,
+                                                    int32_t* qd) {
     const int e = v.w.e, k = v.w.k;
     if (v.d == 2) {
-        if (e == 4 && k == 1) return lower_row_mf_warp<2, 4, 1>(v, W, Wlo, cellid, ffl, j, f, xhi, xlo, lane, q);
-        if (e == 6 && k == 2) return lower_row_mf_warp<2, 6, 2>(v, W, Wlo, cellid, ffl, j, f, xhi, xlo, lane, q);
-        return lower_row_mf_warp<2, 0, 0>(v, W, Wlo, cellid, ffl, j, f, xhi, xlo, lane, q);
+        if (e == 4 && k == 1) return lower_row_mf_warp<2, 4, 1>(v, W, Wlo, cellid, ffl, j, f, xhi, xlo, lane, q, qd);
+        if (e == 6 && k == 2) return lower_row_mf_warp<2, 6, 2>(v, W, Wlo, cellid, ffl, j, f, xhi, xlo, lane, q, qd);
+        return lower_row_mf_warp<2, 0, 0>(v, W, Wlo, cellid, ffl, j, f, xhi, xlo, lane, q, qd);
     }
     if (v.d == 3) {
-        if (e == 4 && k == 1) return lower_row_mf_warp<3, 4, 1>(v, W, Wlo, cellid, ffl, j, f, xhi, xlo, lane, q);
-        if (e == 6 && k == 2) return lower_row_mf_warp<3, 6, 2>(v, W, Wlo, cellid, ffl, j, f, xhi, xlo, lane, q);
-        return lower_row_mf_warp<3, 0, 0>(v, W, Wlo, cellid, ffl, j, f, xhi, xlo, lane, q);
+        if (e == 4 && k == 1) return lower_row_mf_warp<3, 4, 1>(v, W, Wlo, cellid, ffl, j, f, xhi, xlo, lane, q, qd);
+        if (e == 6 && k == 2) return lower_row_mf_warp<3, 6, 2>(v, W, Wlo, cellid, ffl, j, f, xhi, xlo, lane, q, qd);
+        return lower_row_mf_warp<3, 0, 0>(v, W, Wlo, cellid, ffl, j, f, xhi, xlo, lane, q, qd);
     }
-    return lower_row_mf_warp<1, 0, 0>(v, W, Wlo, cellid, ffl, j, f, xhi, xlo, lane, q);
+    return lower_row_mf_warp<1, 0, 0>(v, W, Wlo, cellid, ffl, j, f, xhi, xlo, lane, q, qd);
 }
 
 // Double-float sum over the S lanes of a group (every lane of the warp must call it).

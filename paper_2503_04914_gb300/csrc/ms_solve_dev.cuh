@@ -132,6 +132,7 @@ struct Shared {
     int act[kMaxV], oact[kMaxV], zero[kMaxV], first[kMaxV], pcoff[kMaxV], fresh[kMaxV];
     int it_solve[kMaxV];
     int32_t lq[kNW][64];    // per-warp candidate queues of the matrix-free lower update
+    int32_t lqd[kNW][64];   // their cells' displacements
     int refines[kMaxV];
     int f64[kMaxV];         // MIXED: the level's inner CG runs in FP64 (FP32 refinement stalled)
     int f64n[kMaxV];        // levels switched to FP64
@@ -1258,7 +1259,7 @@ __device__ __forceinline__ void fit_body(const SolveArgs& a, Shared& sh) {
                 for (int64_t row = ch.r0 + wid; row < ch.r1; row += kNW) {
                     const Frame f = a.frames[a.fbase[k] + (row - a.off[k]) * (k + 1) + m];
                     const ff acc = ff_group_sum(lower_row_mf_warp_any(a.hv, a.mfv.W, a.Wlo, a.mfv.cellid, a.ffl, m, f,
-                                                                      xh, xl, lane, sh.lq[wid]),
+                                                                      xh, xl, lane, sh.lq[wid], sh.lqd[wid]),
                                                 32);
                     if (lane == 0) a.beta[ch.vb + row] -= ff_to_double(acc);
                 }

@@ -97,6 +97,7 @@ template <bool FF>
 __global__ void k_eval(const __grid_constant__ HierView v, const float* __restrict__ W, const float* __restrict__ Wlo,
                        const __grid_constant__ EvalLevels el, const double* __restrict__ alpha,
                        const double* __restrict__ Q, int64_t nq, double* __restrict__ out, int nrhs, int col) {
+    __shared__ int32_t eq[8][64], eqd[8][64];  // per-warp queues (blocks of 256 threads)
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= nq) return;  // warp-uniform
@@ -121,6 +122,21 @@ __global__ void k_eval(const __grid_constant__ HierView v, const float* __restri
                 fr[a] = (float)t;
                 frlo[a] = (float)(t - (double)fr[a]);
             }
+            // the candidates passing the FP32 test are queued (point, cell displacement) and their
+            // double-float values computed 32 at a time, so that arithmetic runs on full warps
+            int32_t* q = eq[threadIdx.x >> 5];
+            int32_t* qd = eqd[threadIdx.x >> 5];
+            int qn = 0;
+            auto entry = [&](int32_t pp, int32_t cd) {
+                const int dcs[3] = {(cd & 15) - 4, ((cd >> 4) & 15) - 4, ((cd >> 8) & 15) - 4};
+                ff r2 = {0.0f, 0.0f};
+                for (int a = 0; a < v.d; ++a) {
+                    const ff o = ff_add(ff_mul(el.cod[l], {(float)dcs[a], 0.0f}), ff_neg({fr[a], frlo[a]}));
+                    r2 = ff_add(r2, ff_sqr(ff_add(o, {__ldg(W + a * v.N + pp), __ldg(Wlo + a * v.N + pp)})));
+                }
+                const ff phi = eval_ff_wendland(v.w, el.c, ff_sqrt(r2));
+                if (phi.hi != 0.0f) sl = fma(ff_to_double(phi), alpha[pp], sl);
+            };
             const int R = v.R;
             const int rz = v.d >= 3 ? R : 0, ry = v.d >= 2 ? R : 0;
             for (int dz = -rz; dz <= rz; ++dz) {
@@ -133,30 +149,47 @@ __global__ void k_eval(const __grid_constant__ HierView v, const float* __restri
                         const int cx = c[0] + dx;
                         if (cx < 0 || cx >= g.G[0]) continue;
                         const int dc[3] = {dx, dy, dz};
-                        ff o[3];
+                        const int32_t code = (dx + 4) | ((dy + 4) << 4) | ((dz + 4) << 8);
                         float of[3];
-                        for (int a = 0; a < 3; ++a) {
-                            o[a] = ff_add(ff_mul(el.cod[l], {(float)dc[a], 0.0f}), ff_neg({fr[a], frlo[a]}));
-                            of[a] = o[a].hi;
-                        }
+                        for (int a = 0; a < 3; ++a)
+                            of[a] = ff_add(ff_mul(el.cod[l], {(float)dc[a], 0.0f}), ff_neg({fr[a], frlo[a]})).hi;
                         const int64_t gid = g.cell_off + morton(v.d, cx, cy, cz);
                         const int32_t ps = v.cell_start[gid], pe = v.cell_start[gid + 1];
-                        for (int32_t p = ps + lane; p < pe; p += 32) {
-                            // FP32 prefilter, then the double-float distance
-                            float t = of[0] + __ldg(W + p);
-                            float qq = t * t;
-                            if (v.d >= 2) { t = of[1] + __ldg(W + v.N + p); qq = fmaf(t, t, qq); }
-                            if (v.d >= 3) { t = of[2] + __ldg(W + 2 * v.N + p); qq = fmaf(t, t, qq); }
-                            if (qq > 1.0f + 1e-4f) continue;
-                            ff r2 = {0.0f, 0.0f};
-                            for (int a = 0; a < v.d; ++a)
-                                r2 = ff_add(r2, ff_sqr(ff_add(o[a], {__ldg(W + a * v.N + p), __ldg(Wlo + a * v.N + p)})));
-                            const ff phi = eval_ff_wendland(v.w, el.c, ff_sqrt(r2));
-                            if (phi.hi != 0.0f) sl = fma(ff_to_double(phi), alpha[p], sl);
+                        for (int32_t p0 = ps; p0 < pe; p0 += 32) {
+                            const int32_t p = p0 + lane;
+                            bool pass = false;
+                            if (p < pe) {  // FP32 prefilter
+                                float t = of[0] + __ldg(W + p);
+                                float qq = t * t;
+                                if (v.d >= 2) { t = of[1] + __ldg(W + v.N + p); qq = fmaf(t, t, qq); }
+                                if (v.d >= 3) { t = of[2] + __ldg(W + 2 * v.N + p); qq = fmaf(t, t, qq); }
+                                pass = qq <= 1.0f + 1e-4f;
+                            }
+                            const unsigned mask = __ballot_sync(0xffffffffu, pass);
+                            if (pass) {
+                                const int slot = qn + __popc(mask & ((1u << lane) - 1u));
+                                q[slot] = p;
+                                qd[slot] = code;
+                            }
+                            qn += __popc(mask);
+                            if (qn >= 32) {
+                                __syncwarp();
+                                entry(q[lane], qd[lane]);
+                                __syncwarp();
+                                if (lane < qn - 32) {
+                                    q[lane] = q[32 + lane];
+                                    qd[lane] = qd[32 + lane];
+                                }
+                                qn -= 32;
+                                __syncwarp();
+                            }
                         }
                     }
                 }
             }
+            __syncwarp();
+            if (lane < qn) entry(q[lane], qd[lane]);
+            __syncwarp();
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sl += __shfl_xor_sync(0xffffffffu, sl, o);

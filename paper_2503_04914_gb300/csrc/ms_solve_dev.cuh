@@ -54,6 +54,7 @@ constexpr int kChunk = 256;  // rows per work chunk (chunks never straddle level
 constexpr int kNW = kBS / 32;
 constexpr int kAcc = 3;      // accumulators per phase
 constexpr int kMaxV = 256;   // virtual levels (right-hand side, level) per launch
+constexpr int kLCells = 128;   // cells of the staged box
 constexpr int kGroup = 16;           // CTAs per first-level barrier counter
 constexpr int kMaxGroups = 64;       // <= 1024 CTAs
 constexpr int kBarWords = 2 + kMaxGroups;  // top count, generation, group counters
@@ -133,6 +134,11 @@ struct Shared {
     int it_solve[kMaxV];
     int32_t lq[kNW][64];    // per-warp candidate queues of the matrix-free lower update
     int32_t lqd[kNW][64];   // their cells' displacements
+    // staged matrix-free lower update (lower_chunk_staged; the points' positions go to red)
+    int32_t lcoff[kLCells + 1];  // first staged point of each box cell (x fastest, then y, then z)
+    int32_t lps[kLCells];        // the cell's first point (index into the sorted points)
+    int32_t lbox[8];           // box origin (3), extent (3), cells, fits
+    int32_t lred[kNW][6];      // per-warp minima and maxima of the rows' cells
     int refines[kMaxV];
     int f64[kMaxV];         // MIXED: the level's inner CG runs in FP64 (FP32 refinement stalled)
     int f64n[kMaxV];        // levels switched to FP64
@@ -1155,6 +1161,225 @@ __device__ bool solve_levels_wide(const SolveArgs& a, Shared& sh, int l0, int l1
     return true;
 }
 
+// beta_k -= B_km t_m for the rows [r0, r1) of one chunk of level k > m, with the coarse
+// level's points staged in shared memory: the box of level-m cells within R cells of the
+// rows' cells is found (a block min/max of the rows' frames), the FP32 positions in the box
+// of its points are copied once (box cell by box cell, x fastest; axis by axis into the
+// reduction scratch sh.red, which no phase keeps across a barrier, so the CTA's shared
+// memory and the L1 share left to the mat-vecs stay as they are), and then a warp per row
+// tests the points of its (2R+1)^d cells from shared memory: the cells of one (z, y) line of
+// the box are contiguous there, so a row reads (2R+1)^(d-1) ranges, with no dependent
+// global loads between them.  Survivors of the FP32 test (the band of the per-warp form,
+// r^2 <= 1 + 1e-4; the positions' rounding, ~1e-6, is far inside it) are queued with their
+// cell and their double-float entries ff_entry_dc computed 32 at a time; the entries and
+// their order are those of lower_row_mf_warp (the queue holds the survivors in the same
+// order), so the sums agree with it up to the rare candidate at r ~ 1 that one FP32 test
+// keeps and the other drops (its entry is 0).  Returns false, with nothing written, when
+// the box has more than kLCells cells or more points than the scratch holds (the caller
+// then takes the per-warp form).  Called by every thread of the CTA with the same chunk.
+template <int D, int E, int K>
+__device__ __forceinline__ bool lower_chunk_staged(const SolveArgs& a, Shared& sh, const Chunk& ch, int m) {
+    constexpr int kCap = (int)(sizeof(sh.red) / sizeof(float)) / D;  // staged points
+    float* const sp = reinterpret_cast<float*>(&sh.red[0][0]);        // axis ax at sp + ax kCap
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const HierView& v = a.hv;
+    const LevelGrid& g = v.grid[m];
+    const int R = v.R, k = ch.l;
+    const Frame* frm = a.frames + a.fbase[k] + m;  // frame of row r in level m: frm[(r - off[k]) (k + 1)]
+    // 1. the rows' cells: block minima and maxima
+    int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
+    for (int64_t row = ch.r0 + tid; row < ch.r1; row += kBS) {
+        const Frame* f = frm + (row - a.off[k]) * (k + 1);
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+            const int c = f->c[ax];
+            lo[ax] = min(lo[ax], c);
+            hi[ax] = max(hi[ax], c);
+        }
+    }
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[ax] = min(lo[ax], __shfl_xor_sync(0xffffffffu, lo[ax], o));
+            hi[ax] = max(hi[ax], __shfl_xor_sync(0xffffffffu, hi[ax], o));
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+            sh.lred[wid][ax] = lo[ax];
+            sh.lred[wid][3 + ax] = hi[ax];
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int ncell = 1, fits = 1;
+        for (int ax = 0; ax < 3; ++ax) {
+            int blo = 0, n = 1;
+            if (ax < D) {
+                int l0 = 0x7fffffff, h0 = -0x7fffffff;
+                for (int w = 0; w < kNW; ++w) {
+                    l0 = min(l0, sh.lred[w][ax]);
+                    h0 = max(h0, sh.lred[w][3 + ax]);
+                }
+                blo = max(l0 - R, 0);
+                const int bhi = min(h0 + R, g.G[ax] - 1);
+                n = bhi - blo + 1;
+                if (n <= 0) n = 0;
+                if (n > 255) fits = 0;
+            }
+            sh.lbox[ax] = blo;
+            sh.lbox[3 + ax] = n;
+            ncell = fits ? ncell * n : 0;
+            if (ncell > kLCells) fits = 0;
+        }
+        sh.lbox[6] = fits ? ncell : 0;
+        sh.lbox[7] = fits;
+    }
+    __syncthreads();
+    if (!sh.lbox[7]) {
+        __syncthreads();  // every thread has read lbox before the caller's next chunk rewrites it
+        return false;
+    }
+    const int ncell = sh.lbox[6];
+    const int blo0 = sh.lbox[0], blo1 = sh.lbox[1], blo2 = sh.lbox[2];
+    const int n0 = sh.lbox[3], n1 = sh.lbox[4];
+    // 2. the box cells' first points and point counts, then their offsets (one warp scans)
+    for (int c = tid; c < ncell; c += kBS) {
+        const int cx = blo0 + c % n0, cy = blo1 + (c / n0) % n1, cz = blo2 + c / (n0 * n1);
+        const int64_t gid = g.cell_off + morton(D, cx, D >= 2 ? cy : 0, D >= 3 ? cz : 0);
+        const int32_t ps = __ldg(v.cell_start + gid);
+        sh.lps[c] = ps;
+        sh.lcoff[c + 1] = __ldg(v.cell_start + gid + 1) - ps;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        int carry = 0;
+        for (int b0 = 0; b0 < ncell; b0 += 32) {
+            const int c = b0 + lane;
+            int t = c < ncell ? sh.lcoff[c + 1] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += u;
+            }
+            if (c < ncell) sh.lcoff[c + 1] = carry + t;
+            carry += __shfl_sync(0xffffffffu, t, 31);
+        }
+        if (lane == 0) sh.lcoff[0] = 0;
+    }
+    __syncthreads();
+    const int total = sh.lcoff[ncell];
+    if (total > kCap) {
+        __syncthreads();
+        return false;
+    }
+    // 3. the points' positions in the box (units of delta_m), a warp per box cell
+    const float cod = g.cod;
+    const int64_t N = v.N;
+    const float* W = a.mfv.W;
+    for (int c = wid; c < ncell; c += kNW) {
+        const int r[3] = {c % n0, (c / n0) % n1, c / (n0 * n1)};
+        const int32_t ps = sh.lps[c], np = sh.lcoff[c + 1] - sh.lcoff[c];
+        const int o = sh.lcoff[c];
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+            const float b = __fmul_rn(small_int_to_float(r[ax]), cod);
+            for (int t = lane; t < np; t += 32) sp[ax * kCap + o + t] = __fadd_rn(b, __ldg(W + ax * N + ps + t));
+        }
+    }
+    __syncthreads();
+    // 4. a warp per row
+    const float* xh = a.p32 + ch.vb;
+    const float* xl = a.s32 + ch.vb;
+    int32_t* q = sh.lq[wid];    // survivors: staged index
+    int32_t* qc = sh.lqd[wid];  // and box cell | x << 8 | y << 16 | z << 24 (box coordinates)
+    for (int64_t row = ch.r0 + wid; row < ch.r1; row += kNW) {
+        const Frame f = frm[(row - a.off[k]) * (k + 1)];
+        const int bl[3] = {blo0, blo1, blo2};
+        float Y[3] = {0.0f, 0.0f, 0.0f};
+        int rlo[3] = {0, 0, 0}, rhi[3] = {0, 0, 0};  // the row's cells in box coordinates
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+            Y[ax] = __fadd_rn(__fmul_rn(small_int_to_float(f.c[ax] - bl[ax]), cod), f.fr[ax]);
+            rlo[ax] = max(f.c[ax] - R, 0) - bl[ax];
+            rhi[ax] = min(f.c[ax] + R, g.G[ax] - 1) - bl[ax];
+        }
+        ff acc = {0.0f, 0.0f};
+        int qn = 0;  // queued survivors (warp-uniform)
+        auto entry = [&](int i, int32_t cd) {
+            const int c = cd & 255;
+            const int32_t p = sh.lps[c] + (i - sh.lcoff[c]);
+            const int dcs[3] = {((cd >> 8) & 255) + blo0 - f.c[0], ((cd >> 16) & 255) + blo1 - f.c[1],
+                                ((cd >> 24) & 255) + blo2 - f.c[2]};
+            acc = ff_add(acc, ff_mul(ff_entry_dc<E, K>(v, W, a.Wlo, a.ffl, m, p, f, dcs), {xh[p], xl[p]}));
+        };
+        for (int zr = rlo[2]; zr <= rhi[2]; ++zr) {
+            for (int yr = rlo[1]; yr <= rhi[1]; ++yr) {
+                if (rlo[0] > rhi[0]) continue;
+                const int line = (zr * n1 + yr) * n0;
+                const int s = sh.lcoff[line + rlo[0]], e = sh.lcoff[line + rhi[0] + 1];
+                const int32_t yz = (yr << 16) | (zr << 24);
+                for (int b0 = s; b0 < e; b0 += 32) {
+                    const int i = b0 + lane;
+                    bool pass = false;
+                    int xr = rlo[0];
+                    if (i < e) {
+                        float t = __fsub_rn(sp[i], Y[0]);
+                        float qq = t * t;
+                        if (D >= 2) { t = __fsub_rn(sp[kCap + i], Y[1]); qq = fmaf(t, t, qq); }
+                        if (D >= 3) { t = __fsub_rn(sp[2 * kCap + i], Y[2]); qq = fmaf(t, t, qq); }
+                        pass = qq <= 1.0f + 1e-4f;
+                        for (int x = rlo[0] + 1; x <= rhi[0]; ++x) xr += i >= sh.lcoff[line + x];
+                    }
+                    const unsigned mask = __ballot_sync(0xffffffffu, pass);
+                    if (pass) {
+                        const int slot = qn + __popc(mask & ((1u << lane) - 1u));
+                        q[slot] = i;
+                        qc[slot] = (line + xr) | (xr << 8) | yz;
+                    }
+                    qn += __popc(mask);
+                    if (qn >= 32) {
+                        __syncwarp();
+                        entry(q[lane], qc[lane]);
+                        __syncwarp();
+                        if (lane < qn - 32) {
+                            q[lane] = q[32 + lane];
+                            qc[lane] = qc[32 + lane];
+                        }
+                        qn -= 32;
+                        __syncwarp();
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane < qn) entry(q[lane], qc[lane]);
+        __syncwarp();
+        const ff sum = ff_group_sum(acc, 32);
+        if (lane == 0) a.beta[ch.vb + row] -= ff_to_double(sum);
+    }
+    __syncthreads();  // the staged points stay until every warp is done with them
+    return true;
+}
+
+// lower_chunk_staged for the hierarchy's (d, Wendland exponent and degree), with the same
+// specialisations as lower_row_mf_warp_any.
+__device__ __forceinline__ bool lower_chunk_staged_any(const SolveArgs& a, Shared& sh, const Chunk& ch, int m) {
+    const int e = a.hv.w.e, kk = a.hv.w.k;
+    if (a.hv.d == 2) {
+        if (e == 4 && kk == 1) return lower_chunk_staged<2, 4, 1>(a, sh, ch, m);
+        if (e == 6 && kk == 2) return lower_chunk_staged<2, 6, 2>(a, sh, ch, m);
+        return lower_chunk_staged<2, 0, 0>(a, sh, ch, m);
+    }
+    if (a.hv.d == 3) {
+        if (e == 4 && kk == 1) return lower_chunk_staged<3, 4, 1>(a, sh, ch, m);
+        if (e == 6 && kk == 2) return lower_chunk_staged<3, 6, 2>(a, sh, ch, m);
+        return lower_chunk_staged<3, 0, 0>(a, sh, ch, m);
+    }
+    return lower_chunk_staged<1, 0, 0>(a, sh, ch, m);
+}
+
 // The whole schedule of eq. split for one hierarchy, run by the CTAs [0, sh.nb) of a
 // partition (sh.cta: this CTA's index in it).
 template <int MODE, bool WIDE = false>
@@ -1235,7 +1460,7 @@ __device__ __forceinline__ void fit_body(const SolveArgs& a, Shared& sh) {
             }
             prof(sh, kPrfLower);
             if (!gsync(a, sh)) return;
-        } else if (m + 1 <= L - 1 && a.lower_inc && a.lower_mf) {
+        } else if (MODE == 1 && m + 1 <= L - 1 && a.lower_inc && a.lower_mf) {  // (MIXED builds only)
             // beta_k -= B_km t_m with B's entries recomputed: t_m split into double-float
             // parts (p32, s32: free between level solves), then one S-lane group per row of
             // levels k = m+1..L-1 sums its entries in double-float (the entries' arithmetic is
@@ -1250,8 +1475,10 @@ __device__ __forceinline__ void fit_body(const SolveArgs& a, Shared& sh) {
             prof(sh, kPrfLower);
             if (!gsync(a, sh)) return;
             run_phase<0>(a, sh, [&](int v) { return v % L >= m + 1; }, [&](const Chunk& ch, double*) {
-                // a warp per row: its frame in level m's grid from the build, the candidates of the
-                // (2R+1)^d cells around it tested in FP32 and compacted (lower_row_mf_warp)
+                // level m's points around the chunk staged in shared memory when they fit
+                if (lower_chunk_staged_any(a, sh, ch, m)) return;
+                // else a warp per row: its frame in level m's grid from the build, the candidates
+                // of the (2R+1)^d cells around it tested in FP32 and compacted (lower_row_mf_warp)
                 const int wid = tid >> 5, lane = tid & 31;
                 const float* xh = a.p32 + ch.vb;
                 const float* xl = a.s32 + ch.vb;

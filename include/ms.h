@@ -132,16 +132,7 @@ typedef struct ms_opts {
                             12 bytes per entry; one fitted many times is faster with CSR.  Needs
                             the default schedule (inter_tol 0 or >= 1); MS_APPLY_B64/B32 are then
                             unavailable. */
-    int lower_staging;   /* lower_op = MS_OP_MATRIX_FREE, the form of the update:
-                            0 (default): every work chunk of rows stages the coarse level's points
-                            around it in shared memory where they fit (a box of up to 128 cells and
-                            1,536 points in 2-D, 1,024 in 3-D, 3,072 in 1-D) and each row tests its
-                            candidates there; chunks whose box does not fit take the form of 1;
-                            1: a warp per row reads its candidates from global memory.
-                            The two give the same entries in the same order; their sums can differ
-                            only where one FP32 distance test keeps a candidate at r ~ 1 that the
-                            other drops (its entry is 0).  Other values: MS_ERR_ARG. */
-    int reserved[3];
+    int reserved[4];
 } ms_opts;
 
 /* Per-fit statistics (all levels 0-based, coarse to fine). */

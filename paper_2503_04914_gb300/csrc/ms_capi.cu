@@ -89,9 +89,6 @@ ms_status validate_and_init(int d, int L, const int64_t* n_per_level, const doub
     if (o.lower_op != MS_OP_CSR && o.lower_op != MS_OP_MATRIX_FREE) {
         ms_set_error(MS_ERR_ARG, "lower_op must be MS_OP_CSR or MS_OP_MATRIX_FREE (got %d)", o.lower_op); return MS_ERR_ARG;
     }
-    if (o.lower_staging != 0 && o.lower_staging != 1) {
-        ms_set_error(MS_ERR_ARG, "lower_staging must be 0 or 1 (got %d)", o.lower_staging); return MS_ERR_ARG;
-    }
     if (o.lower_op == MS_OP_MATRIX_FREE && o.precision != MS_PREC_MIXED) {
         ms_set_error(MS_ERR_ARG, "lower_op = MS_OP_MATRIX_FREE needs precision = MS_PREC_MIXED (its double-float entries "
                      "use the MIXED build's offsets)");

@@ -86,7 +86,6 @@ struct SolveArgs {
     // double-float from the geometry (the build stores no B)
     int lower_mf;
     int tprLmf[MS_MAXL];       // lanes per row of the update from level m
-    int lower_stage;           // 1: chunks stage level m's points in shared memory where they fit
     const Frame* frames;       // the build's frames: row s of level k, level j <= k at
     int64_t fbase[MS_MAXL + 1];  // fbase[k] + (s - off[k]) (k + 1) + j
     HierView hv;
@@ -1477,7 +1476,7 @@ __device__ __forceinline__ void fit_body(const SolveArgs& a, Shared& sh) {
             if (!gsync(a, sh)) return;
             run_phase<0>(a, sh, [&](int v) { return v % L >= m + 1; }, [&](const Chunk& ch, double*) {
                 // level m's points around the chunk staged in shared memory when they fit
-                if (a.lower_stage && lower_chunk_staged_any(a, sh, ch, m)) return;
+                if (lower_chunk_staged_any(a, sh, ch, m)) return;
                 // else a warp per row: its frame in level m's grid from the build, the candidates
                 // of the (2R+1)^d cells around it tested in FP32 and compacted (lower_row_mf_warp)
                 const int wid = tid >> 5, lane = tid & 31;
@@ -1692,7 +1691,6 @@ void fill_args(const ms_hierarchy* h, double rel_tol, int R, SolveArgs& a, bool 
     a.Brp = h->B.rp; a.Bcol = h->B.col; a.Bv64 = h->B.v64;
     a.Bseg = h->Bseg;
     a.lower_mf = (h->opts.precision == MS_PREC_MIXED && h->opts.lower_op == MS_OP_MATRIX_FREE) ? 1 : 0;
-    a.lower_stage = h->opts.lower_staging == 1 ? 0 : 1;
     a.hv = h->view;
     a.hv.X = h->X;
     a.hv.cell_start = h->cell_start;

@@ -44,7 +44,7 @@ class ms_opts(C.Structure):
                 ("jacobi_sweeps", C.c_int), ("inter_tol", C.c_double), ("inner_tol", C.c_double),
                 ("cell_split", C.c_int), ("threads_per_row", C.c_int), ("lower_fp32", C.c_int),
                 ("solve_ctas_per_sm", C.c_int), ("autotune", C.c_int), ("lower_op", C.c_int),
-                ("lower_staging", C.c_int), ("reserved", C.c_int * 3)]
+                ("reserved", C.c_int * 4)]
 
 
 class ms_fit_stats(C.Structure):

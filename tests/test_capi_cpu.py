@@ -67,8 +67,6 @@ def test_struct_sizes_match_header(lib):
     (2, 1, [4], [0.1], {"threads_per_row": 3}, ms.MS_ERR_ARG),
     (2, 1, [4], [0.1], {"autotune": 2}, ms.MS_ERR_ARG),
     (2, 1, [4], [0.1], {"lower_op": 2}, ms.MS_ERR_ARG),
-    (2, 1, [4], [0.1], {"lower_staging": 2}, ms.MS_ERR_ARG),
-    (2, 1, [4], [0.1], {"lower_staging": -1}, ms.MS_ERR_ARG),
     # the matrix-free lower blocks take double-float offsets that only MIXED builds keep
     (2, 1, [4], [0.1], {"lower_op": ms.MS_OP_MATRIX_FREE, "precision": ms.MS_PREC_FP64}, ms.MS_ERR_ARG),
 ])

@@ -173,34 +173,6 @@ def test_fit_with_matrix_free_lower_blocks(wl, precond):
     Hc.close()
 
 
-@pytest.mark.parametrize("wl", ["halton_nu8_w22", "random3d_w31"])
-def test_matrix_free_lower_update_staged_and_per_row_forms(wl):
-    """The matrix-free lower update with each chunk's coarse points staged in shared memory
-    (lower_staging = 0, the default) and with a warp per row reading them from global memory
-    (lower_staging = 1): the same entries summed in the same order, so the fits' coefficients
-    agree to rounding (1e-12 relative; they can differ only by a candidate at r ~ 1 that one
-    FP32 test keeps with a zero entry), and both match the oracle.  In 3-D (about 27 points a
-    cell) a box of 4 x 4 x 4 cells exceeds the shared-memory capacity (1,024 points), and such
-    chunks take the per-row form inside the default fit as well."""
-    if wl == "halton_nu8_w22":
-        w = ragged_halton([37, 150, 601, 2500, 9001], nu=8.0, wendland=(2, 2))
-        rt, tc, ta = 1e-11, 1e-6, 1e-9
-    else:
-        w = inputs.random3d_hierarchy(L=3, n_gauss=3)
-        rt, tc, ta = 1e-12, 1e-7, 1e-9
-    for staging in (0, 1):
-        st = check_fit(w, ms.MS_PREC_MIXED, tc, rel_tol=rt, tol_approx=ta, lower_op=ms.MS_OP_MATRIX_FREE,
-                       lower_staging=staging)
-        assert st["device_status"] == 0
-    alphas = []
-    for staging in (0, 1):
-        H = ms.Hierarchy.from_workload(w, precision=ms.MS_PREC_MIXED, lower_op=ms.MS_OP_MATRIX_FREE,
-                                       lower_staging=staging)
-        alphas.append(np.asarray(H.fit(w.f, rel_tol=rt)[0]))
-        H.close()
-    assert rel(alphas[0], alphas[1]) <= 1e-12
-
-
 @pytest.mark.parametrize("wl", ["grid_w21", "halton_nu8_w22", "random3d_w31"])
 def test_matrix_free_operator_matches_oracle(wl):
     """y = D_L x with entries recomputed in FP32 from per-cell offsets (no stored matrix),
